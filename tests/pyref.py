@@ -1,0 +1,113 @@
+"""Independent pure-Python restatement of the race definition, for tiny models.
+
+Used only to pin the oracle: it enumerates instances with Python loops and
+Python integers (``//`` floors, ``%`` with a positive modulus is Euclidean) and
+applies the pairwise race predicate directly, without the oracle's cell-level
+shortcut.  Shares no code with ``oracle/`` or the CUDA path.
+"""
+from itertools import product
+
+
+def ev(e, env):
+    op, a = e.op, e.args
+    if op == "const":
+        return a[0]
+    if op == "tid":
+        return env["tid"][a[0]]
+    if op == "bid":
+        return env["bid"][a[0]]
+    if op == "param":
+        return env["params"][a[0]]
+    if op == "iter":
+        return env["iter"][a[0]]
+    if op == "add":
+        return ev(a[0], env) + ev(a[1], env)
+    if op == "mul":
+        return a[0] * ev(a[1], env)
+    if op == "fdiv":
+        return ev(a[0], env) // a[1]
+    if op == "mod":
+        return ev(a[0], env) % a[1]
+    raise ValueError(op)
+
+
+def instances(m):
+    """List of (a, s, e, b, p, t, k) for every in-bounds access instance, and
+    the list of out-of-bounds records (stmt, access, gtid, dimcode)."""
+    gx, gy, gz = m.grid
+    bx_, by_, bz_ = m.block
+    bs = bx_ * by_ * bz_
+    out, oob = [], []
+    for bz, by, bx in product(range(gz), range(gy), range(gx)):
+        b = bx + gx * (by + gy * bz)
+        for tz, ty, tx in product(range(bz_), range(by_), range(bx_)):
+            t = tx + bx_ * (ty + by_ * tz)
+            env = {"tid": (tx, ty, tz), "bid": (bx, by, bz), "params": m.params, "iter": [0] * 8}
+            for si, st in enumerate(m.stmts):
+                def rec(level):
+                    if level == len(st.loops):
+                        if any(ev(g, env) < 0 for g in st.guards):
+                            return
+                        p = ev(st.phase, env)
+                        for ai, ac in enumerate(st.accesses):
+                            arr = m.arrays[ac.array]
+                            bad = False
+                            if not (0 <= p < m.n_phases):
+                                oob.append((si, ai, b * bs + t, 0))
+                                bad = True
+                            e = 0
+                            for d, (ie, ext) in enumerate(zip(ac.index, arr.extents)):
+                                v = ev(ie, env)
+                                if not (0 <= v < ext):
+                                    oob.append((si, ai, b * bs + t, d + 1))
+                                    bad = True
+                                e = e * ext + v
+                            if bad:
+                                continue
+                            s = b if arr.scope == "shared" else 0
+                            out.append((ac.array, s, e, b, p, t, 1 if ac.kind == "W" else 0))
+                        return
+                    lp = st.loops[level]
+                    v = ev(lp.lower, env)
+                    hi = ev(lp.upper, env)
+                    while v < hi:
+                        env["iter"][level] = v
+                        rec(level + 1)
+                        v += lp.step
+                rec(0)
+    return out, oob
+
+
+def race(x, y, bs):
+    """The pair predicate: same cell, different threads, a write, and
+    concurrent (different blocks or the same barrier interval)."""
+    if x[:3] != y[:3]:
+        return False
+    if x[3] * bs + x[5] == y[3] * bs + y[5]:
+        return False
+    if not (x[6] == 1 or y[6] == 1):
+        return False
+    return x[3] != y[3] or x[4] == y[4]
+
+
+def check(m):
+    """(status, racy_cell_count, witness) with witness = (x, y) tuples or None;
+    status 'oob' with the smallest out-of-bounds record instead of a count."""
+    inst, oob = instances(m)
+    if oob:
+        return "oob", min(oob), None
+    bs = m.block_size
+    u = sorted(set(inst))
+    by_cell = {}
+    for x in u:
+        by_cell.setdefault(x[:3], []).append(x)
+    racy = set()
+    best = None
+    for cell, xs in by_cell.items():
+        for i in range(len(xs)):
+            for j in range(i + 1, len(xs)):
+                if race(xs[i], xs[j], bs):
+                    racy.add(cell)
+                    if best is None or (xs[i], xs[j]) < best:
+                        best = (xs[i], xs[j])
+    return "ok", len(racy), best

@@ -1,0 +1,244 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed forms derived by hand (tests/golden/closed_forms.md), the verdict the
+paper states for Ge-SpMM (tests/golden/paper_verdicts.json), an independent
+pure-Python pairwise brute force on tiny random models, and invariances of the
+race definition (thread relabelling, statement order, array padding)."""
+import json
+import os
+
+import pytest
+
+import oracle
+import workloads as w
+from workloads.spec import Expr
+
+from . import pyref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def wit(r):
+    return r.witness
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T", [2, 3, 8, 33, 256])
+def test_neighbor_write_read(T):
+    r = oracle.check(w.neighbor_write_read(T))
+    assert r.status == 0 and r.verdict == 1
+    assert r.racy_cells == T - 1
+    # first racy cell s[1]: thread 0 reads it, thread 1 writes it
+    assert wit(r) == (0, 0, 1, (0, 0, 0, 0), (0, 0, 1, 1))
+
+
+def test_neighbor_write_read_multi_block():
+    r = oracle.check(w.neighbor_write_read(16, n_blocks=5))
+    assert r.racy_cells == 5 * 15
+
+
+def test_reduction_tree():
+    bar = oracle.check(w.reduction_tree(True))
+    assert (bar.status, bar.verdict, bar.racy_cells, bar.instances) == (0, 0, 0, 765)
+    nob = oracle.check(w.reduction_tree(False))
+    assert (nob.verdict, nob.racy_cells, nob.instances) == (1, 127, 765)
+    assert wit(nob) == (0, 0, 1, (0, 0, 0, 0), (0, 0, 1, 1))
+    ld = oracle.check(w.reduction_tree(False, load_phase=True))
+    assert (ld.verdict, ld.racy_cells, ld.instances) == (1, 255, 1277)
+    assert wit(ld) == (0, 0, 1, (0, 0, 0, 0), (0, 0, 1, 1))
+    ldb = oracle.check(w.reduction_tree(True, load_phase=True))
+    assert ldb.racy_cells == 0
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7, 12])
+def test_polyhedral_product(n):
+    r = oracle.check(w.polyhedral_product(n))
+    assert r.racy_cells == 2 * n - 3
+    assert r.verdict == 1
+    # first racy cell C[1]: (thread 0, R) then its first partner (thread 1, W)
+    assert wit(r) == (2, 0, 1, (0, 0, 0, 0), (0, 0, 1, 1))
+    r2 = oracle.check(w.polyhedral_product(n, init_stmt=True))
+    assert r2.racy_cells == 2 * n - 3
+
+
+@pytest.mark.parametrize("pad", [False, True])
+def test_transpose_small(pad):
+    m_bar = w.transpose(pad=pad, barrier=True, n=256)
+    m_nob = w.transpose(pad=pad, barrier=False, n=256)
+    blocks = (256 // 32) ** 2
+    rb = oracle.check(m_bar)
+    assert (rb.verdict, rb.racy_cells, rb.instances) == (0, 0, 2 * 2 * 4 * 256 * blocks)
+    rn = oracle.check(m_nob)
+    assert rn.racy_cells == 992 * blocks
+    # tile (array 2) of block 0, element 1: written by t1, read by t32
+    assert wit(rn) == (2, 0, 1, (0, 0, 1, 1), (0, 0, 32, 0))
+
+
+def test_transpose_full_size():
+    r = oracle.check(w.transpose(pad=False, barrier=False))
+    assert r.instances == 16777216
+    assert r.racy_cells == 4063232
+    assert wit(r) == (2, 0, 1, (0, 0, 1, 1), (0, 0, 32, 0))
+
+
+@pytest.mark.parametrize("L", [1, 31, 32, 33, 70, 100])
+def test_ge_spmm(L):
+    golden = json.load(open(os.path.join(GOLDEN, "paper_verdicts.json")))
+    assert golden["ge_spmm_algorithm2"]["expected_race_free"] is True
+    M, N, K = 3, 64, 4
+    r = oracle.check(w.ge_spmm_uniform(M, N, K, L, trailing_barrier=True))
+    assert r.status == 0 and r.verdict == 0 and r.racy_cells == 0
+    r2 = oracle.check(w.ge_spmm_uniform(M, N, K, L, trailing_barrier=False))
+    assert r2.racy_cells == 2 * min(32, max(0, L - 32)) * M * (N // 32)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_affine_construction(seed):
+    clean = w.random_affine(seed, n_blocks=8, block=64, n_stmts=20, plant=False)
+    r = oracle.check(clean)
+    assert r.status == 0 and r.racy_cells == 0
+    planted = w.random_affine(seed, n_blocks=8, block=64, n_stmts=20, plant=True)
+    rp = oracle.check(planted)
+    assert rp.racy_cells == 8 * 64
+
+
+# --------------------------------------------------------------------------
+# independent brute force on tiny random models
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(150))
+def test_tiny_random_vs_python_bruteforce(seed):
+    m = w.tiny_random(seed)
+    st, cnt, best = pyref.check(m)
+    r = oracle.check(m)
+    rb = oracle.brute(m)
+    assert st == "ok"
+    assert r.status == 0 and rb.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    assert r.verdict == (cnt > 0)
+    inst, _ = pyref.instances(m)
+    assert r.instances == len(inst) and r.distinct == len(set(inst))
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        exp = (x[0], x[1], x[2], (x[3], x[4], x[5], x[6]), (y[3], y[4], y[5], y[6]))
+        assert r.witness == exp
+        assert rb.witness == exp
+
+
+def test_oracle_expand_matches_python():
+    for seed in range(20):
+        m = w.tiny_random(seed)
+        inst, _ = pyref.instances(m)
+        got = [tuple(int(v) for v in row) for row in oracle.expand(m)]
+        assert got == sorted(inst)
+
+
+def test_out_of_bounds_reported():
+    from workloads.spec import Access, Array, Model, Stmt, tid, R, W
+    m = Model((2, 1, 1), (8, 1, 1), [Array("a", "global", (10,))],
+              [Stmt([Access(0, R, (tid.x,))]), Stmt([Access(0, W, (tid.x + 3,))])])
+    st, rec, _ = pyref.check(m)
+    r = oracle.check(m)
+    assert st == "oob" and r.status == oracle.STATUS_OOB
+    assert (r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim) == rec == (1, 0, 7, 1)
+    # an interval outside [0, n_phases)
+    m2 = Model((1, 1, 1), (4, 1, 1), [Array("a", "shared", (4,))],
+               [Stmt([Access(0, W, (tid.x,))], phase=w.const(2))], n_phases=2)
+    r2 = oracle.check(m2)
+    assert r2.status == oracle.STATUS_OOB and (r2.oob_stmt, r2.oob_access, r2.oob_gtid, r2.oob_dim) == (0, 0, 0, 0)
+
+
+def test_invalid_text():
+    r = oracle.check_text("rcmodel 1 grid 1 1")
+    assert r.status == oracle.STATUS_INVALID
+
+
+# --------------------------------------------------------------------------
+# invariances
+# --------------------------------------------------------------------------
+
+def _subst_tid_x(e: Expr, f):
+    if e.op == "tid" and e.args[0] == 0:
+        return f
+    if e.op in ("add",):
+        return Expr("add", _subst_tid_x(e.args[0], f), _subst_tid_x(e.args[1], f))
+    if e.op == "mul":
+        return Expr("mul", e.args[0], _subst_tid_x(e.args[1], f))
+    if e.op in ("fdiv", "mod"):
+        return Expr(e.op, _subst_tid_x(e.args[0], f), e.args[1])
+    return e
+
+
+def _relabel(m, a, c):
+    """Model whose thread x behaves like thread (a*x + c) mod blockDim.x of m
+    (a coprime to blockDim.x, so this is a permutation of each block's threads)."""
+    import copy
+    m2 = copy.deepcopy(m)
+    f = (a * w.tid.x + c) % m.block[0]
+    for st in m2.stmts:
+        st.phase = _subst_tid_x(st.phase, f)
+        st.guards = [_subst_tid_x(g, f) for g in st.guards]
+        for lp in st.loops:
+            lp.lower = _subst_tid_x(lp.lower, f)
+            lp.upper = _subst_tid_x(lp.upper, f)
+        for ac in st.accesses:
+            ac.index = tuple(_subst_tid_x(e, f) for e in ac.index)
+    return m2
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_thread_relabelling_keeps_verdict_and_count(seed):
+    for m in [w.random_affine(seed, n_blocks=4, block=64, n_stmts=12, plant=(seed == 1)),
+              w.reduction_tree(False), w.neighbor_write_read(32), w.tiny_random(seed)]:
+        r = oracle.check(m)
+        for a in (1, 3, 5, 7):
+            if m.block[0] % a == 0 and a != 1:
+                continue
+            import math
+            if math.gcd(a, m.block[0]) != 1:
+                continue
+            r2 = oracle.check(_relabel(m, a, 1))
+            assert (r2.verdict, r2.racy_cells, r2.instances) == (r.verdict, r.racy_cells, r.instances)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_statement_order_keeps_everything(seed):
+    import copy
+    for m in [w.random_affine(seed, n_blocks=4, block=32, n_stmts=10, plant=True), w.tiny_random(seed + 40)]:
+        r = oracle.check(m)
+        m2 = copy.deepcopy(m)
+        m2.stmts = list(reversed(m2.stmts))
+        r2 = oracle.check(m2)
+        assert (r2.verdict, r2.racy_cells, r2.instances, r2.distinct, r2.witness) == \
+               (r.verdict, r.racy_cells, r.instances, r.distinct, r.witness)
+
+
+def test_padding_keeps_count():
+    for bar in (True, False):
+        a = oracle.check(w.transpose(pad=False, barrier=bar, n=128))
+        b = oracle.check(w.transpose(pad=True, barrier=bar, n=128))
+        assert a.racy_cells == b.racy_cells
+
+
+# --------------------------------------------------------------------------
+# planted mistakes must be caught by the pins above (run on the CPU only)
+# --------------------------------------------------------------------------
+
+def test_pins_detect_planted_mistake():
+    """A model whose race definition drops the 'different threads' clause (as a
+    buggy checker would) must disagree with the pairwise brute force."""
+    m = w.reduction_tree(True)
+    inst, _ = pyref.instances(m)
+    u = sorted(set(inst))
+    # buggy predicate: same cell, a write, same interval -- forgets gtid_x != gtid_y
+    buggy = set()
+    for i in range(len(u)):
+        for j in range(i + 1, len(u)):
+            x, y = u[i], u[j]
+            if x[:3] == y[:3] and (x[6] or y[6]) and x[4] == y[4]:
+                buggy.add(x[:3])
+    assert len(buggy) > 0 and oracle.check(m).racy_cells == 0
