@@ -1,0 +1,285 @@
+/*
+ * rc.h -- C ABI of the GB300 concrete-instance SIMT race checker.
+ *
+ * The question (paper, Abstract and Introduction): can two distinct GPU threads
+ * touch the same array cell within one barrier interval, with at least one
+ * write?  The paper answers it symbolically: it writes a kernel's Domain,
+ * Read, Write and Schedule as ISCC integer sets and maps (Section "Using ISCC
+ * in Formal Analysis/Verification") and tests the RaW / WaW / WaR relations
+ * (same cell, at least one write) against the schedule (appendix listing of the
+ * dependence test).  This library answers it concretely: for a model with a
+ * fixed grid and fixed parameters it expands every access instance into a
+ * 64-bit key, groups keys by cell with a radix sort (or a hash table), and
+ * reports whether any cell races, how many cells race and the smallest racing
+ * pair.
+ *
+ * Race rule (the paper orders instances by a sequential Before relation; for
+ * SIMT threads this library reads concurrency as the CUDA barrier rule):
+ *   instances x, y race  iff  same (array, scope instance, element)
+ *                          and gtid_x != gtid_y
+ *                          and (x writes or y writes)
+ *                          and (block_x != block_y or phase_x == phase_y).
+ * A shared array has one instance per block (indexed block-locally), a global
+ * array one for the grid.  The phase of an instance is the number of block
+ * barriers its thread passed before it; blocks are never ordered against each
+ * other.  Count = number of distinct racy cells.  Witness = the
+ * lexicographically smallest racing pair (x, y), x < y, in the order
+ * (array, scope instance, element, block, phase, thread, kind R<W).
+ *
+ * Conventions for every entry point:
+ *  - All calls return an rc_status; none aborts, throws or prints.
+ *  - Pointers named *_dev are device pointers, others are host pointers.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Asynchronous calls only enqueue work on the stream; inputs they read on
+ *    the device must stay valid until the work completes.
+ */
+#ifndef RC_H
+#define RC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* status codes                                                               */
+/* ------------------------------------------------------------------------- */
+typedef enum rc_status {
+  RC_OK = 0,
+  RC_E_INVALID = 1,       /* malformed descriptor or argument                          */
+  RC_E_KEY_OVERFLOW = 2,  /* the packed (cell, phase, block, thread, kind) exceeds 63 bits */
+  RC_E_OOB = 3,           /* an index outside its extent, or a phase outside [0, n_phases) */
+  RC_E_NOMEM = 4,         /* workspace smaller than rc_workspace_size(), or host/device allocation failed */
+  RC_E_TIMEOUT = 5,       /* a bounded device wait expired (the result is not valid)   */
+  RC_E_CUDA = 6,          /* a CUDA runtime call failed                                 */
+  RC_E_NOT_READY = 7,     /* rc_report(wait=0) on work that has not completed           */
+  RC_E_UNSUPPORTED = 8    /* a valid model outside this build's limits (see rc_limits)  */
+} rc_status;
+
+/* Static text for a status code. */
+const char* rc_status_str(rc_status s);
+
+/* ------------------------------------------------------------------------- */
+/* model descriptor                                                           */
+/*                                                                            */
+/* Follows the paper's statement of what a race model needs (Introduction:    */
+/* thread/block ids, barriers and fences, shared-memory arrays, input/output   */
+/* arrays; Methods: the same list as components (1)-(7)) and its ISCC          */
+/* relations: a statement is a labelled code section (the paper's S, T, I, F)  */
+/* with a Domain (loop nest + guards, the Presburger constraints of the Domain */
+/* listings) and Read/Write access relations "Stmt[iters] -> Array[index]"     */
+/* (the Read and Write listings).                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Expression bytecode, evaluated in postfix order on a stack of int64 values
+ * with two's-complement wrapping.  Quasi-affine: the paper's Ge-SpMM model
+ * uses j % 32 (Section "Doing this for Ge-SpMM", Read listing).
+ *   RC_OP_CONST  push imm
+ *   RC_OP_TID    push threadIdx[arg]  (arg 0,1,2 = x,y,z)
+ *   RC_OP_BID    push blockIdx[arg]
+ *   RC_OP_PARAM  push params[arg]
+ *   RC_OP_ITER   push the iterator of loop level arg of the statement (0 = outermost)
+ *   RC_OP_ADD    pop b, pop a, push a + b
+ *   RC_OP_MUL    pop a, push imm * a
+ *   RC_OP_FDIV   pop a, push floor(a / imm)   (imm > 0; rounds toward minus infinity)
+ *   RC_OP_MOD    pop a, push a mod imm        (imm > 0; Euclidean, result in [0, imm))
+ * A well-formed expression leaves exactly one value. */
+enum {
+  RC_OP_CONST = 0, RC_OP_TID = 1, RC_OP_BID = 2, RC_OP_PARAM = 3, RC_OP_ITER = 4,
+  RC_OP_ADD = 5, RC_OP_MUL = 6, RC_OP_FDIV = 7, RC_OP_MOD = 8
+};
+typedef struct rc_insn { int32_t op; int32_t arg; int64_t imm; } rc_insn;
+typedef struct rc_expr { const rc_insn* code; uint32_t len; } rc_expr;
+
+enum { RC_SCOPE_GLOBAL = 0, RC_SCOPE_SHARED = 1 };
+enum { RC_READ = 0, RC_WRITE = 1 };
+
+/* for (v = lower; v < upper; v += step): bounds may use tid, bid, params and
+ * the iterators of outer loops; step > 0. */
+typedef struct rc_loop { rc_expr lower; rc_expr upper; int64_t step; } rc_loop;
+
+/* One access relation: array[index[0]]...[index[ndims-1]], row-major. */
+typedef struct rc_access {
+  uint32_t array;          /* index into rc_model_desc.arrays                     */
+  uint32_t kind;           /* RC_READ or RC_WRITE                                 */
+  const rc_expr* index;    /* ndims expressions (ndims of the array)              */
+} rc_access;
+
+/* A statement instance exists for every thread and every point of the loop
+ * nest at which all guards are >= 0.  phase may use bid, params and the
+ * iterators of loops whose bounds do not depend on tid (a barrier interval is
+ * uniform over the block); a phase that names tid is RC_E_INVALID. */
+typedef struct rc_stmt {
+  rc_expr phase;
+  const rc_loop* loops;     uint32_t n_loops;
+  const rc_expr* guards;    uint32_t n_guards;
+  const rc_access* accesses; uint32_t n_accesses;
+} rc_stmt;
+
+typedef struct rc_array {
+  const char* name;        /* informational, may be NULL                          */
+  uint32_t scope;          /* RC_SCOPE_GLOBAL or RC_SCOPE_SHARED                  */
+  uint32_t ndims;          /* 1..4                                                */
+  int64_t extent[4];       /* sizes of the dimensions, each >= 1                  */
+} rc_array;
+
+typedef struct rc_model_desc {
+  uint32_t grid[3];        /* gridDim  (each >= 1)                                */
+  uint32_t block[3];       /* blockDim (each >= 1)                                */
+  const int64_t* params;   uint32_t n_params;
+  uint32_t n_phases;       /* phases are in [0, n_phases); >= 1                   */
+  const rc_array* arrays;  uint32_t n_arrays;
+  const rc_stmt* stmts;    uint32_t n_stmts;
+} rc_model_desc;
+
+/* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED
+ * beyond them). */
+typedef struct rc_limits {
+  uint32_t max_loops;        /* loop depth per statement                         */
+  uint32_t max_terms;        /* distinct floor-div / mod terms per statement      */
+  uint32_t max_stmts;
+  uint32_t max_accesses;     /* per statement                                     */
+  uint32_t max_phase_bits;
+  uint32_t key_bits;         /* packed key width available                        */
+} rc_limits;
+void rc_get_limits(rc_limits* out);
+
+/* ------------------------------------------------------------------------- */
+/* models                                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct rc_model rc_model;   /* opaque */
+
+/* Validate and lower a descriptor: compile every expression, compute the key
+ * layout and the instance count, and upload the lowered program to the
+ * current CUDA device.  The descriptor is deep-copied: the caller may free it
+ * on return.  Statements whose loop trip counts depend on the thread are
+ * counted on the device (a synchronous count pass on an internal stream).
+ * Errors: RC_E_INVALID (malformed), RC_E_KEY_OVERFLOW, RC_E_UNSUPPORTED,
+ * RC_E_NOMEM, RC_E_CUDA.  On error *out is NULL. */
+rc_status rc_model_create(const rc_model_desc* desc, rc_model** out);
+/* Frees the model's host and device memory.  Work using the model must have
+ * completed.  NULL is ignored. */
+void rc_model_destroy(rc_model* m);
+
+/* Key layout of a lowered model, MSB to LSB: [cell | phase | block | thread |
+ * kind], each field `*_bits` wide at `*_shift`; cell = array_base[a] +
+ * scope_instance * array_cells[a] + element.  Keys are grouped (sorted) on
+ * bits [sort_lo, sort_hi) = (cell, phase); (block, thread, kind) ride along. */
+typedef struct rc_layout {
+  uint32_t kind_shift, thread_shift, block_shift, phase_shift, cell_shift;
+  uint32_t thread_bits, block_bits, phase_bits, cell_bits;
+  uint32_t sort_lo, sort_hi;
+  uint64_t key_slots;        /* keys written by the expansion (valid + padding)  */
+  uint64_t total_cells;
+  uint32_t n_arrays;
+  uint32_t n_threads_per_block;
+  uint64_t n_blocks;
+  uint64_t array_base[64];   /* first linear cell of each array (first 64 arrays) */
+  uint64_t array_cells[64];  /* cells of one scope instance of each array         */
+} rc_layout;
+rc_status rc_model_layout(const rc_model* m, rc_layout* out);
+
+/* ------------------------------------------------------------------------- */
+/* checking                                                                   */
+/* ------------------------------------------------------------------------- */
+enum { RC_PATH_AUTO = 0, RC_PATH_SORT = 1, RC_PATH_HASH = 2 };
+
+typedef struct rc_check_opts {
+  uint32_t path;           /* RC_PATH_*; AUTO = the tuner's choice                */
+  uint32_t digit_bits;     /* radix digit width for the sort path, 0 = auto (<= 8) */
+  uint32_t early_exit;     /* hash path: stop at the first racy cell; the count
+                              is then a lower bound                               */
+  uint32_t test_flags;     /* 0 in normal use; RC_TEST_STALL_LOOKBACK makes every
+                              look-back wait for a status nothing publishes, so the
+                              bounded wait runs out and the check reports
+                              RC_E_TIMEOUT (exercises the timeout path)           */
+  uint64_t spin_limit;     /* iterations of every bounded device wait, 0 = default */
+} rc_check_opts;
+enum { RC_TEST_STALL_LOOKBACK = 1 };
+
+typedef struct rc_inst {
+  uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
+  uint32_t thread;         /* linear thread index in the block tx + bx*(ty + by*tz) */
+  uint32_t kind;           /* RC_READ / RC_WRITE                                   */
+  int64_t phase;
+  uint64_t gtid;           /* block * blockSize + thread                           */
+} rc_inst;
+
+typedef struct rc_result {
+  int32_t status;          /* rc_status of this check                             */
+  int32_t verdict;         /* 1 = some pair races                                 */
+  uint64_t racy_cells;     /* distinct racy cells                                 */
+  uint64_t instances;      /* access instances checked (guards true, duplicates counted) */
+  /* witness (valid when verdict == 1): the racy cell and the smallest pair     */
+  uint32_t w_array;
+  uint32_t w_reserved;
+  uint64_t w_scope;        /* block for a shared array, 0 for a global one        */
+  uint64_t w_addr;         /* row-major element index inside the array            */
+  rc_inst x, y;
+  /* first offending instance when status == RC_E_OOB: the smallest
+   * (stmt, access, gtid, dim) with dim 0 = the phase, d+1 = index dimension d */
+  uint32_t oob_stmt, oob_access;
+  uint64_t oob_gtid;
+  int32_t oob_dim;
+  int32_t reserved2;
+} rc_result;
+
+typedef struct rc_ticket_s* rc_ticket;   /* opaque handle of an enqueued check */
+
+/* Bytes of device workspace rc_check needs for this model and options.
+ * Errors: RC_E_INVALID. */
+rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes);
+
+/* Enqueue one check on `stream`.  `workspace_dev` (>= rc_workspace_size bytes,
+ * 256-byte aligned, caller-owned) is scratch for the keys, histograms and
+ * look-back state; it may be reused by the next check on the same stream.
+ * opts may be NULL (defaults).  *ticket receives a handle for rc_report.
+ * Errors: RC_E_INVALID, RC_E_NOMEM (workspace too small), RC_E_CUDA. */
+rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace_dev,
+                   size_t workspace_bytes, void* stream, rc_ticket* ticket);
+
+/* Bytes of workspace rc_check_batch needs for these n models. */
+rc_status rc_batch_workspace_size(rc_model* const* models, size_t n,
+                                  const rc_check_opts* opts, size_t* bytes);
+
+/* Enqueue a check of n models as one batch; one ticket reports n results in
+ * the order of `models`.  Same workspace and error rules as rc_check. */
+rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts* opts,
+                         void* workspace_dev, size_t workspace_bytes, void* stream,
+                         rc_ticket* ticket);
+
+/* Copy out the result(s) of a ticket: `out` holds 1 (rc_check) or n
+ * (rc_check_batch) records.  wait=1 blocks until the work completes; wait=0
+ * returns RC_E_NOT_READY (ticket still valid) if it has not.  After any other
+ * return the ticket is released.  The return value is RC_OK when the results
+ * were produced; each record's own status tells how its check went. */
+rc_status rc_report(rc_ticket ticket, rc_result* out, int wait);
+
+/* ------------------------------------------------------------------------- */
+/* stage entry points (the hot path one kernel family at a time)              */
+/* ------------------------------------------------------------------------- */
+
+/* Expansion only: writes the model's layout.key_slots keys to keys_dev
+ * (padding slots hold 0xFFFF...FFFF) and the number of valid instances to
+ * *count_dev (uint64).  workspace as for rc_check. */
+rc_status rc_expand_keys(rc_model* m, void* workspace_dev, size_t workspace_bytes,
+                         uint64_t* keys_dev, uint64_t* count_dev, void* stream);
+
+/* Bytes of workspace rc_sort_keys needs for n keys with digit width digit_bits
+ * (0 = 8). */
+rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes);
+
+/* Stable LSD radix sort (onesweep) of n uint64 keys on bits [lo_bit, hi_bit):
+ * reads keys_in_dev, writes keys_out_dev (distinct buffers, n keys each).
+ * Keys with equal bits in the range keep their input order. */
+rc_status rc_sort_keys(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint64_t n,
+                       uint32_t lo_bit, uint32_t hi_bit, uint32_t digit_bits,
+                       void* workspace_dev, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RC_H */

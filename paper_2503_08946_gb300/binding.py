@@ -1,0 +1,503 @@
+"""ctypes binding of the race-checker C ABI (include/rc.h).
+
+Argument marshalling only: every step of the check runs in the CUDA library
+``_build/librc.so``.  There is no fallback: if the library is missing or cannot
+be loaded, :func:`load` raises.  PyTorch supplies device memory (the workspace
+is a ``torch.uint8`` CUDA tensor) and streams.
+
+Functions carry the C names: :func:`rc_model_create`, :func:`rc_model_destroy`,
+:func:`rc_model_layout`, :func:`rc_workspace_size`, :func:`rc_check`,
+:func:`rc_batch_workspace_size`, :func:`rc_check_batch`, :func:`rc_report`,
+:func:`rc_expand_keys`, :func:`rc_sort_workspace_size`, :func:`rc_sort_keys`,
+:func:`rc_status_str`, :func:`rc_get_limits`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from ctypes import (POINTER, Structure, c_char_p, c_int, c_int32, c_int64, c_size_t, c_uint32,
+                    c_uint64, c_void_p)
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librc.so")
+
+# status codes (rc_status)
+RC_OK, RC_E_INVALID, RC_E_KEY_OVERFLOW, RC_E_OOB, RC_E_NOMEM, RC_E_TIMEOUT, RC_E_CUDA, \
+    RC_E_NOT_READY, RC_E_UNSUPPORTED = range(9)
+STATUS_NAMES = {RC_OK: "RC_OK", RC_E_INVALID: "RC_E_INVALID", RC_E_KEY_OVERFLOW: "RC_E_KEY_OVERFLOW",
+                RC_E_OOB: "RC_E_OOB", RC_E_NOMEM: "RC_E_NOMEM", RC_E_TIMEOUT: "RC_E_TIMEOUT",
+                RC_E_CUDA: "RC_E_CUDA", RC_E_NOT_READY: "RC_E_NOT_READY",
+                RC_E_UNSUPPORTED: "RC_E_UNSUPPORTED"}
+RC_OP_CONST, RC_OP_TID, RC_OP_BID, RC_OP_PARAM, RC_OP_ITER, RC_OP_ADD, RC_OP_MUL, RC_OP_FDIV, \
+    RC_OP_MOD = range(9)
+RC_SCOPE_GLOBAL, RC_SCOPE_SHARED = 0, 1
+RC_READ, RC_WRITE = 0, 1
+RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
+RC_TEST_STALL_LOOKBACK = 1
+
+# every entry point declared in include/rc.h
+EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
+           "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
+           "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys"]
+
+
+class RcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+
+
+# ---------------------------------------------------------------------------
+# C structures
+# ---------------------------------------------------------------------------
+class rc_insn(Structure):
+    _fields_ = [("op", c_int32), ("arg", c_int32), ("imm", c_int64)]
+
+
+class rc_expr(Structure):
+    _fields_ = [("code", POINTER(rc_insn)), ("len", c_uint32)]
+
+
+class rc_loop(Structure):
+    _fields_ = [("lower", rc_expr), ("upper", rc_expr), ("step", c_int64)]
+
+
+class rc_access(Structure):
+    _fields_ = [("array", c_uint32), ("kind", c_uint32), ("index", POINTER(rc_expr))]
+
+
+class rc_stmt(Structure):
+    _fields_ = [("phase", rc_expr),
+                ("loops", POINTER(rc_loop)), ("n_loops", c_uint32),
+                ("guards", POINTER(rc_expr)), ("n_guards", c_uint32),
+                ("accesses", POINTER(rc_access)), ("n_accesses", c_uint32)]
+
+
+class rc_array(Structure):
+    _fields_ = [("name", c_char_p), ("scope", c_uint32), ("ndims", c_uint32), ("extent", c_int64 * 4)]
+
+
+class rc_model_desc(Structure):
+    _fields_ = [("grid", c_uint32 * 3), ("block", c_uint32 * 3),
+                ("params", POINTER(c_int64)), ("n_params", c_uint32),
+                ("n_phases", c_uint32),
+                ("arrays", POINTER(rc_array)), ("n_arrays", c_uint32),
+                ("stmts", POINTER(rc_stmt)), ("n_stmts", c_uint32)]
+
+
+class rc_limits(Structure):
+    _fields_ = [("max_loops", c_uint32), ("max_terms", c_uint32), ("max_stmts", c_uint32),
+                ("max_accesses", c_uint32), ("max_phase_bits", c_uint32), ("key_bits", c_uint32)]
+
+
+class rc_layout(Structure):
+    _fields_ = [("kind_shift", c_uint32), ("thread_shift", c_uint32), ("block_shift", c_uint32),
+                ("phase_shift", c_uint32), ("cell_shift", c_uint32),
+                ("thread_bits", c_uint32), ("block_bits", c_uint32), ("phase_bits", c_uint32),
+                ("cell_bits", c_uint32), ("sort_lo", c_uint32), ("sort_hi", c_uint32),
+                ("key_slots", c_uint64), ("total_cells", c_uint64), ("n_arrays", c_uint32),
+                ("n_threads_per_block", c_uint32), ("n_blocks", c_uint64),
+                ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
+
+
+class rc_check_opts(Structure):
+    _fields_ = [("path", c_uint32), ("digit_bits", c_uint32), ("early_exit", c_uint32),
+                ("test_flags", c_uint32), ("spin_limit", c_uint64)]
+
+
+class rc_inst(Structure):
+    _fields_ = [("block", c_uint64), ("thread", c_uint32), ("kind", c_uint32), ("phase", c_int64),
+                ("gtid", c_uint64)]
+
+
+class rc_result(Structure):
+    _fields_ = [("status", c_int32), ("verdict", c_int32), ("racy_cells", c_uint64),
+                ("instances", c_uint64), ("w_array", c_uint32), ("w_reserved", c_uint32),
+                ("w_scope", c_uint64), ("w_addr", c_uint64), ("x", rc_inst), ("y", rc_inst),
+                ("oob_stmt", c_uint32), ("oob_access", c_uint32), ("oob_gtid", c_uint64),
+                ("oob_dim", c_int32), ("reserved2", c_int32)]
+
+
+# ---------------------------------------------------------------------------
+# library loading (no fallback)
+# ---------------------------------------------------------------------------
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load ``_build/librc.so``; raise if it is missing (build it with
+    ``paper_2503_08946_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"race-checker CUDA library not built: {LIB_PATH} is missing")
+        lib = ctypes.CDLL(LIB_PATH)
+        lib.rc_status_str.argtypes = [c_int]
+        lib.rc_status_str.restype = c_char_p
+        lib.rc_get_limits.argtypes = [POINTER(rc_limits)]
+        lib.rc_get_limits.restype = None
+        lib.rc_model_create.argtypes = [POINTER(rc_model_desc), POINTER(c_void_p)]
+        lib.rc_model_create.restype = c_int
+        lib.rc_model_destroy.argtypes = [c_void_p]
+        lib.rc_model_destroy.restype = None
+        lib.rc_model_layout.argtypes = [c_void_p, POINTER(rc_layout)]
+        lib.rc_model_layout.restype = c_int
+        lib.rc_workspace_size.argtypes = [c_void_p, POINTER(rc_check_opts), POINTER(c_size_t)]
+        lib.rc_workspace_size.restype = c_int
+        lib.rc_check.argtypes = [c_void_p, POINTER(rc_check_opts), c_void_p, c_size_t, c_void_p,
+                                 POINTER(c_void_p)]
+        lib.rc_check.restype = c_int
+        lib.rc_batch_workspace_size.argtypes = [POINTER(c_void_p), c_size_t, POINTER(rc_check_opts),
+                                                POINTER(c_size_t)]
+        lib.rc_batch_workspace_size.restype = c_int
+        lib.rc_check_batch.argtypes = [POINTER(c_void_p), c_size_t, POINTER(rc_check_opts), c_void_p,
+                                       c_size_t, c_void_p, POINTER(c_void_p)]
+        lib.rc_check_batch.restype = c_int
+        lib.rc_report.argtypes = [c_void_p, POINTER(rc_result), c_int]
+        lib.rc_report.restype = c_int
+        lib.rc_expand_keys.argtypes = [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]
+        lib.rc_expand_keys.restype = c_int
+        lib.rc_sort_workspace_size.argtypes = [c_uint64, c_uint32, POINTER(c_size_t)]
+        lib.rc_sort_workspace_size.restype = c_int
+        lib.rc_sort_keys.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p,
+                                     c_size_t, c_void_p]
+        lib.rc_sort_keys.restype = c_int
+        _lib = lib
+        return lib
+
+
+def rc_status_str(s: int) -> str:
+    return load().rc_status_str(int(s)).decode()
+
+
+def rc_get_limits() -> dict:
+    lim = rc_limits()
+    load().rc_get_limits(ctypes.byref(lim))
+    return {f: getattr(lim, f) for f, _ in rc_limits._fields_}
+
+
+# ---------------------------------------------------------------------------
+# marshalling of workloads.spec.Model into rc_model_desc
+# ---------------------------------------------------------------------------
+_OPS = {"const": RC_OP_CONST, "tid": RC_OP_TID, "bid": RC_OP_BID, "param": RC_OP_PARAM,
+        "iter": RC_OP_ITER}
+
+
+def _postfix(e, out: list):
+    op, a = e.op, e.args
+    if op == "const":
+        out.append((RC_OP_CONST, 0, int(a[0])))
+    elif op in ("tid", "bid", "param", "iter"):
+        out.append((_OPS[op], int(a[0]), 0))
+    elif op == "add":
+        _postfix(a[0], out)
+        _postfix(a[1], out)
+        out.append((RC_OP_ADD, 0, 0))
+    elif op == "mul":
+        _postfix(a[1], out)
+        out.append((RC_OP_MUL, 0, int(a[0])))
+    elif op == "fdiv":
+        _postfix(a[0], out)
+        out.append((RC_OP_FDIV, 0, int(a[1])))
+    elif op == "mod":
+        _postfix(a[0], out)
+        out.append((RC_OP_MOD, 0, int(a[1])))
+    else:
+        raise ValueError(f"unknown expression node {op}")
+
+
+class _Desc:
+    """Owns the ctypes arrays behind one rc_model_desc."""
+
+    def __init__(self, model):
+        self.keep = []
+        d = rc_model_desc()
+        for i in range(3):
+            d.grid[i] = int(model.grid[i])
+            d.block[i] = int(model.block[i])
+        if model.params:
+            pa = (c_int64 * len(model.params))(*[int(p) for p in model.params])
+            self.keep.append(pa)
+            d.params = ctypes.cast(pa, POINTER(c_int64))
+        d.n_params = len(model.params)
+        d.n_phases = int(model.n_phases)
+        arrs = (rc_array * max(1, len(model.arrays)))()
+        for i, a in enumerate(model.arrays):
+            nm = a.name.encode()
+            self.keep.append(nm)
+            arrs[i].name = nm
+            arrs[i].scope = RC_SCOPE_SHARED if a.scope == "shared" else RC_SCOPE_GLOBAL
+            arrs[i].ndims = len(a.extents)
+            for k, e in enumerate(a.extents[:4]):
+                arrs[i].extent[k] = int(e)
+        self.keep.append(arrs)
+        d.arrays = arrs
+        d.n_arrays = len(model.arrays)
+        stmts = (rc_stmt * max(1, len(model.stmts)))()
+        for i, s in enumerate(model.stmts):
+            st = stmts[i]
+            st.phase = self.expr(s.phase)
+            loops = (rc_loop * max(1, len(s.loops)))()
+            for l, lp in enumerate(s.loops):
+                loops[l].lower = self.expr(lp.lower)
+                loops[l].upper = self.expr(lp.upper)
+                loops[l].step = int(lp.step)
+            self.keep.append(loops)
+            st.loops = loops
+            st.n_loops = len(s.loops)
+            guards = (rc_expr * max(1, len(s.guards)))()
+            for g, ge in enumerate(s.guards):
+                guards[g] = self.expr(ge)
+            self.keep.append(guards)
+            st.guards = guards
+            st.n_guards = len(s.guards)
+            accs = (rc_access * max(1, len(s.accesses)))()
+            for k, ac in enumerate(s.accesses):
+                idx = (rc_expr * max(1, len(ac.index)))()
+                for j, ie in enumerate(ac.index):
+                    idx[j] = self.expr(ie)
+                self.keep.append(idx)
+                accs[k].array = int(ac.array)
+                accs[k].kind = RC_WRITE if ac.kind == "W" else RC_READ
+                accs[k].index = idx
+            self.keep.append(accs)
+            st.accesses = accs
+            st.n_accesses = len(s.accesses)
+        self.keep.append(stmts)
+        d.stmts = stmts
+        d.n_stmts = len(model.stmts)
+        self.desc = d
+
+    def expr(self, e) -> rc_expr:
+        code = []
+        _postfix(e, code)
+        arr = (rc_insn * len(code))(*[rc_insn(o, a, i) for o, a, i in code])
+        self.keep.append(arr)
+        x = rc_expr()
+        x.code = arr
+        x.len = len(code)
+        return x
+
+
+def _opts(opts) -> Optional[rc_check_opts]:
+    if opts is None:
+        return None
+    if isinstance(opts, rc_check_opts):
+        return opts
+    o = rc_check_opts()
+    for k, v in dict(opts).items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor, or an int address."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+class RcModel:
+    """Owning handle of an rc_model; destroyed with the object."""
+
+    def __init__(self, ptr: int, name: str = ""):
+        self.ptr = ptr
+        self.name = name
+
+    def close(self):
+        if self.ptr:
+            load().rc_model_destroy(c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rc_model_create(model) -> RcModel:
+    """Lower a :class:`workloads.spec.Model` (or any object with the same
+    fields) and upload it to the current CUDA device."""
+    lib = load()
+    d = _Desc(model)
+    out = c_void_p()
+    st = lib.rc_model_create(ctypes.byref(d.desc), ctypes.byref(out))
+    if st != RC_OK:
+        raise RcError(st, "rc_model_create")
+    return RcModel(out.value, getattr(model, "name", ""))
+
+
+def rc_model_create_status(model) -> int:
+    """Status of rc_model_create for a model (the model is destroyed again)."""
+    lib = load()
+    d = _Desc(model)
+    out = c_void_p()
+    st = lib.rc_model_create(ctypes.byref(d.desc), ctypes.byref(out))
+    if st == RC_OK:
+        lib.rc_model_destroy(out)
+    return st
+
+
+def rc_model_destroy(m: RcModel):
+    m.close()
+
+
+def rc_model_layout(m: RcModel) -> dict:
+    lay = rc_layout()
+    st = load().rc_model_layout(c_void_p(m.ptr), ctypes.byref(lay))
+    if st != RC_OK:
+        raise RcError(st, "rc_model_layout")
+    d = {f: getattr(lay, f) for f, _ in rc_layout._fields_ if not f.startswith("array_")}
+    d["array_base"] = [lay.array_base[i] for i in range(min(64, lay.n_arrays))]
+    d["array_cells"] = [lay.array_cells[i] for i in range(min(64, lay.n_arrays))]
+    return d
+
+
+def rc_workspace_size(m: RcModel, opts=None) -> int:
+    n = c_size_t()
+    o = _opts(opts)
+    st = load().rc_workspace_size(c_void_p(m.ptr), ctypes.byref(o) if o else None, ctypes.byref(n))
+    if st != RC_OK:
+        raise RcError(st, "rc_workspace_size")
+    return n.value
+
+
+def rc_check(m: RcModel, opts, workspace, stream=None):
+    """Enqueue a check; returns a ticket (opaque int) for :func:`rc_report`."""
+    o = _opts(opts)
+    t = c_void_p()
+    ws_bytes = workspace.numel() * workspace.element_size() if hasattr(workspace, "numel") else 0
+    st = load().rc_check(c_void_p(m.ptr), ctypes.byref(o) if o else None, c_void_p(_ptr(workspace)),
+                         c_size_t(ws_bytes), c_void_p(_stream(stream)), ctypes.byref(t))
+    if st != RC_OK:
+        raise RcError(st, "rc_check")
+    return (t.value, 1)
+
+
+def rc_batch_workspace_size(models: Sequence[RcModel], opts=None) -> int:
+    arr = (c_void_p * max(1, len(models)))(*[m.ptr for m in models])
+    n = c_size_t()
+    o = _opts(opts)
+    st = load().rc_batch_workspace_size(arr, len(models), ctypes.byref(o) if o else None, ctypes.byref(n))
+    if st != RC_OK:
+        raise RcError(st, "rc_batch_workspace_size")
+    return n.value
+
+
+def rc_check_batch(models: Sequence[RcModel], opts, workspace, stream=None):
+    arr = (c_void_p * max(1, len(models)))(*[m.ptr for m in models])
+    o = _opts(opts)
+    t = c_void_p()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().rc_check_batch(arr, len(models), ctypes.byref(o) if o else None, c_void_p(_ptr(workspace)),
+                               c_size_t(ws_bytes), c_void_p(_stream(stream)), ctypes.byref(t))
+    if st != RC_OK:
+        raise RcError(st, "rc_check_batch")
+    return (t.value, len(models))
+
+
+@dataclass
+class Result:
+    status: int
+    verdict: int
+    racy_cells: int
+    instances: int
+    w_array: int
+    w_scope: int
+    w_addr: int
+    x: tuple      # (block, phase, thread, kind)
+    y: tuple
+    oob_stmt: int
+    oob_access: int
+    oob_gtid: int
+    oob_dim: int
+
+    @property
+    def witness(self):
+        """(array, scope instance, element, x=(b, p, t, k), y=(b, p, t, k)) or None."""
+        if not self.verdict:
+            return None
+        return (self.w_array, self.w_scope, self.w_addr, self.x, self.y)
+
+
+def _result(r: rc_result) -> Result:
+    return Result(r.status, r.verdict, r.racy_cells, r.instances, r.w_array, r.w_scope, r.w_addr,
+                  (r.x.block, r.x.phase, r.x.thread, r.x.kind), (r.y.block, r.y.phase, r.y.thread, r.y.kind),
+                  r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim)
+
+
+class NotReady(Exception):
+    pass
+
+
+def rc_report(ticket, wait: bool = True) -> List[Result]:
+    t, n = ticket
+    out = (rc_result * max(1, n))()
+    st = load().rc_report(c_void_p(t), out, 1 if wait else 0)
+    if st == RC_E_NOT_READY:
+        raise NotReady()
+    if st != RC_OK:
+        raise RcError(st, "rc_report")
+    return [_result(out[i]) for i in range(n)]
+
+
+def rc_expand_keys(m: RcModel, workspace, keys, count, stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().rc_expand_keys(c_void_p(m.ptr), c_void_p(_ptr(workspace)), c_size_t(ws_bytes),
+                               c_void_p(_ptr(keys)), c_void_p(_ptr(count)), c_void_p(_stream(stream)))
+    if st != RC_OK:
+        raise RcError(st, "rc_expand_keys")
+
+
+def rc_sort_workspace_size(n: int, digit_bits: int = 0) -> int:
+    b = c_size_t()
+    st = load().rc_sort_workspace_size(c_uint64(n), c_uint32(digit_bits), ctypes.byref(b))
+    if st != RC_OK:
+        raise RcError(st, "rc_sort_workspace_size")
+    return b.value
+
+
+def rc_sort_keys(keys_in, keys_out, n: int, lo_bit: int, hi_bit: int, digit_bits: int, workspace, stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().rc_sort_keys(c_void_p(_ptr(keys_in)), c_void_p(_ptr(keys_out)), c_uint64(n), c_uint32(lo_bit),
+                             c_uint32(hi_bit), c_uint32(digit_bits), c_void_p(_ptr(workspace)),
+                             c_size_t(ws_bytes), c_void_p(_stream(stream)))
+    if st != RC_OK:
+        raise RcError(st, "rc_sort_keys")
+
+
+# ---------------------------------------------------------------------------
+# convenience
+# ---------------------------------------------------------------------------
+def workspace(nbytes: int, device=None):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def check(model, opts=None, device=None, stream=None) -> Result:
+    """Create, check and report one model (allocates its own workspace)."""
+    m = model if isinstance(model, RcModel) else rc_model_create(model)
+    ws = workspace(rc_workspace_size(m, opts), device)
+    t = rc_check(m, opts, ws, stream)
+    return rc_report(t, wait=True)[0]

@@ -1,0 +1,204 @@
+// K1: expansion of access instances into packed 64-bit keys.
+//
+// One work unit = (statement, thread).  For a statement whose loops all have
+// constant trip counts ("dense") the key of iteration j, access a and thread g
+// goes to slot  slot_base + (j * n_acc + a) * T + g,  so the 32 lanes of a warp
+// (consecutive g) store 32 consecutive keys; guard-false and out-of-bounds
+// instances leave the all-ones padding key.  Other statements are first counted
+// per unit (expand_count_kernel, run once when the model is created), and then
+// write their keys contiguously at the scanned unit offsets.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace rc {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) expand_kernel(const DevModel* __restrict__ Mp, uint64_t n_units,
+                                                     uint64_t* __restrict__ keys, DevResult* res) {
+  const DevModel& M = *Mp;
+  const uint64_t T = M.n_threads;
+  unsigned long long count = 0;
+  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n_units;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = (uint32_t)(u / T);
+    const uint64_t g = u - (uint64_t)s * T;
+    const DevStmt& S = M.stmts[s];
+    const ThreadVars tv = thread_vars(M, g);
+    if (S.dense) {
+      uint64_t j = 0;
+      const uint64_t stride = T;
+      walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
+        uint64_t slot = S.slot_base + j * (uint64_t)S.n_acc * stride + g;
+        if (guards_hold(M, S, tv, it, term)) {
+          const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
+          for (int a = 0; a < S.n_acc; ++a) {
+            keys[slot] = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+            slot += stride;
+          }
+          count += (unsigned long long)S.n_acc;
+        } else {
+          for (int a = 0; a < S.n_acc; ++a) {
+            keys[slot] = kSentinel;
+            slot += stride;
+          }
+        }
+        ++j;
+      });
+    } else {
+      uint64_t off = M.unit_offset[S.slot_base + g];
+      walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
+        if (!guards_hold(M, S, tv, it, term)) return;
+        const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
+        for (int a = 0; a < S.n_acc; ++a)
+          keys[off++] = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+        count += (unsigned long long)S.n_acc;
+      });
+    }
+  }
+  count = warp_sum(count);
+  if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
+}
+
+// Keys per (statement, thread) unit of the statements with thread-dependent trip
+// counts: counts[S.slot_base + g] = guard-true points * accesses.
+__global__ void __launch_bounds__(256) count_kernel(const DevModel* __restrict__ Mp, uint64_t n_units,
+                                                    uint64_t* __restrict__ counts) {
+  const DevModel& M = *Mp;
+  const uint64_t T = M.n_threads;
+  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n_units;
+       u += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = (uint32_t)(u / T);
+    const uint64_t g = u - (uint64_t)s * T;
+    const DevStmt& S = M.stmts[s];
+    if (S.dense) continue;
+    const ThreadVars tv = thread_vars(M, g);
+    uint64_t c = 0;
+    walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
+      if (guards_hold(M, S, tv, it, term)) c += (uint64_t)S.n_acc;
+    });
+    counts[S.slot_base + g] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint64 counts (three kernels: tile sums, scan of the tile
+// sums in one block, tile scans plus base)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  uint64_t wbase = 0, tot = 0;
+  for (int i = 0; i < kScanThreads / 32; ++i) {
+    if (i < w) wbase += warp_tot[i];
+    tot += warp_tot[i];
+  }
+  __syncthreads();
+  *total = tot;
+  return wbase + x - v;
+}
+
+__global__ void scan_tile_sums(const uint64_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  uint64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + (uint64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  uint64_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void scan_sums_single(uint64_t* __restrict__ sums, uint64_t n, uint64_t* __restrict__ total_out) {
+  // one block: sequential chunks of kScanThreads
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < n; base += kScanThreads) {
+    uint64_t i = base + threadIdx.x;
+    uint64_t v = i < n ? sums[i] : 0;
+    uint64_t tot;
+    uint64_t ex = block_excl_scan(v, &tot);
+    if (i < n) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void scan_tile_apply(const uint64_t* __restrict__ in, uint64_t n, const uint64_t* __restrict__ sums,
+                                uint64_t add, uint64_t* __restrict__ out) {
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  uint64_t v[kScanItems];
+  uint64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  uint64_t tot;
+  uint64_t ex = block_excl_scan(s, &tot) + sums[blockIdx.x] + add;
+  for (int k = 0; k < kScanItems; ++k) {
+    uint64_t i = base + k;
+    if (i < n) out[i] = ex;
+    ex += v[k];
+  }
+}
+
+int grid_for(uint64_t n_units) {
+  uint64_t g = (n_units + 255) / 256;
+  const uint64_t cap = 152ull * 64;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_expand(const DevModel* dm, uint64_t n_units, uint64_t* keys, DevResult* res,
+                          cudaStream_t st) {
+  if (n_units == 0) return cudaSuccess;
+  expand_kernel<<<grid_for(n_units), 256, 0, st>>>(dm, n_units, keys, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st) {
+  if (n_units == 0) return cudaSuccess;
+  count_kernel<<<grid_for(n_units), 256, 0, st>>>(dm, n_units, counts);
+  return cudaGetLastError();
+}
+
+size_t scan_u64_temp_bytes(uint64_t n) {
+  uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  return (size_t)(tiles + 1) * sizeof(uint64_t);
+}
+
+cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,
+                               uint64_t* total_dev, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, temp);
+  scan_sums_single<<<1, kScanThreads, 0, st>>>(temp, tiles, total_dev);
+  scan_tile_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, temp, add, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rc

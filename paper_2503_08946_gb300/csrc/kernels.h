@@ -1,0 +1,60 @@
+// Host launchers of the race-check kernels (one translation unit per family).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rc_internal.h"
+
+namespace rc {
+
+// expand.cu
+cudaError_t launch_expand(const DevModel* dm, uint64_t n_units, uint64_t* keys, DevResult* res,
+                          cudaStream_t st);
+cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st);
+size_t scan_u64_temp_bytes(uint64_t n);
+cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,
+                               uint64_t* total_dev, cudaStream_t st);
+
+// sort.cu
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per onesweep tile
+constexpr int kRadix = 256;                            // bins of the widest digit (8 bits)
+
+struct SortArgs {
+  const uint64_t* keys_in;
+  uint64_t* keys_out;
+  uint64_t n;
+  uint32_t shift, bits;
+  const unsigned long long* digit_offset;   // kRadix exclusive offsets of this pass
+  unsigned long long* lookback;             // n_tiles x kRadix status words
+  unsigned int* tile_counter;
+  unsigned int epoch;                       // distinct per pass within one check
+  unsigned int wait_epoch;                  // epoch the look-back accepts (== epoch in normal use)
+  unsigned long long spin_limit;
+  unsigned int* err;
+};
+cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
+                             cudaStream_t st);
+cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, uint32_t n_pass,
+                                 cudaStream_t st);
+cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t st);
+size_t sort_workspace_bytes(uint64_t n, uint32_t n_pass);
+
+// scan.cu
+struct ScanArgs {
+  const uint64_t* keys;
+  uint64_t n;
+  uint32_t cell_shift, phase_shift, block_shift, thread_shift;
+  uint32_t phase_bits, block_bits, thread_bits;
+  Summary* summaries;
+  uint32_t n_warps;
+  uint64_t per_warp;
+  DevResult* res;
+  unsigned int* groups;   // (1 << phase_bits) x 5 words for the witness
+};
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
+cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);
+cudaError_t launch_init_result(DevResult* res, cudaStream_t st);
+
+}  // namespace rc

@@ -1,0 +1,421 @@
+// Host lowering of a model descriptor (include/rc.h) into the program the
+// expansion kernels interpret.
+//
+// The descriptor holds the paper's Domain / Read / Write relations made
+// concrete (Section "Using ISCC in Formal Analysis/Verification": labelled code
+// sections, their loop-bound Presburger constraints, and the access relations
+// "Stmt[iters] -> Array[index]"), with quasi-affine floor division / modulo as
+// in the Ge-SpMM model (Section "Doing this for Ge-SpMM", "j % 32").  Lowering
+// folds the parameters into constants, rewrites every expression as a linear
+// row over (tid, bid, iterators, floor-div/mod terms), checks that barrier
+// phases do not depend on the thread, decides per statement whether every loop
+// has a constant trip count ("dense": keys go to fixed slots) and computes the
+// 64-bit key layout [cell | phase | block | thread | kind].
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "rc_internal.h"
+
+namespace rc {
+
+uint32_t bit_length(uint64_t v) {
+  uint32_t n = 0;
+  while (v) { n++; v >>= 1; }
+  return n;
+}
+
+namespace {
+
+// Linear form over tid/bid/iterators/terms with a constant.
+struct Lin {
+  int64_t c0 = 0;
+  int64_t ct[6] = {0, 0, 0, 0, 0, 0};
+  std::map<int32_t, int64_t> v;   // var -> coefficient (var < kMaxLoops: iterator; else term)
+
+  void add(const Lin& o, int64_t k) {
+    c0 = wadd(c0, wmul(k, o.c0));
+    for (int i = 0; i < 6; ++i) ct[i] = wadd(ct[i], wmul(k, o.ct[i]));
+    for (auto& kv : o.v) {
+      int64_t c = wadd(v[kv.first], wmul(k, kv.second));
+      if (c == 0) v.erase(kv.first); else v[kv.first] = c;
+    }
+  }
+  bool is_const() const {
+    for (int i = 0; i < 6; ++i) if (ct[i]) return false;
+    return v.empty();
+  }
+  bool operator<(const Lin& o) const {
+    if (c0 != o.c0) return c0 < o.c0;
+    for (int i = 0; i < 6; ++i) if (ct[i] != o.ct[i]) return ct[i] < o.ct[i];
+    return v < o.v;
+  }
+};
+
+struct TermKey {
+  Lin inner;
+  int32_t op;
+  int64_t d;
+  bool operator<(const TermKey& o) const {
+    if (op != o.op) return op < o.op;
+    if (d != o.d) return d < o.d;
+    return inner < o.inner;
+  }
+};
+
+struct StmtBuilder {
+  const rc_model_desc* desc;
+  std::vector<TermKey> terms;
+  std::map<TermKey, int> term_ids;
+  std::vector<int> term_level;      // iterators needed
+  std::vector<bool> term_tid;       // depends on tid
+  std::vector<bool> loop_tid;       // loop l's iterator varies with tid
+  rc_status err = RC_OK;
+
+  int level_of(const Lin& l) const {
+    int lev = 0;
+    for (auto& kv : l.v) {
+      if (kv.first < kMaxLoops) lev = std::max(lev, kv.first + 1);
+      else lev = std::max(lev, term_level[kv.first - kMaxLoops]);
+    }
+    return lev;
+  }
+  bool depends_on_tid(const Lin& l) const {
+    if (l.ct[0] || l.ct[1] || l.ct[2]) return true;
+    for (auto& kv : l.v) {
+      if (kv.first < kMaxLoops) { if (loop_tid[kv.first]) return true; }
+      else if (term_tid[kv.first - kMaxLoops]) return true;
+    }
+    return false;
+  }
+
+  // Compile one postfix expression; `n_iters` iterators are in scope.
+  bool compile(const rc_expr& e, int n_iters, Lin* out) {
+    if (e.len == 0 || e.code == nullptr) { err = RC_E_INVALID; return false; }
+    std::vector<Lin> st;
+    for (uint32_t i = 0; i < e.len; ++i) {
+      const rc_insn& in = e.code[i];
+      Lin x;
+      switch (in.op) {
+        case RC_OP_CONST: x.c0 = in.imm; st.push_back(x); break;
+        case RC_OP_TID:
+        case RC_OP_BID:
+          if (in.arg < 0 || in.arg > 2) { err = RC_E_INVALID; return false; }
+          x.ct[(in.op == RC_OP_TID ? 0 : 3) + in.arg] = 1;
+          st.push_back(x);
+          break;
+        case RC_OP_PARAM:
+          if (in.arg < 0 || (uint32_t)in.arg >= desc->n_params || !desc->params) { err = RC_E_INVALID; return false; }
+          x.c0 = desc->params[in.arg];
+          st.push_back(x);
+          break;
+        case RC_OP_ITER:
+          if (in.arg < 0 || in.arg >= n_iters) { err = RC_E_INVALID; return false; }
+          x.v[in.arg] = 1;
+          st.push_back(x);
+          break;
+        case RC_OP_ADD: {
+          if (st.size() < 2) { err = RC_E_INVALID; return false; }
+          Lin b = st.back(); st.pop_back();
+          st.back().add(b, 1);
+          break;
+        }
+        case RC_OP_MUL: {
+          if (st.empty()) { err = RC_E_INVALID; return false; }
+          Lin a = st.back();
+          Lin r;
+          r.add(a, in.imm);
+          st.back() = r;
+          break;
+        }
+        case RC_OP_FDIV:
+        case RC_OP_MOD: {
+          if (st.empty() || in.imm <= 0) { err = RC_E_INVALID; return false; }
+          Lin a = st.back();
+          Lin r;
+          if (a.is_const()) {
+            r.c0 = in.op == RC_OP_FDIV ? floor_div(a.c0, in.imm) : euclid_mod(a.c0, in.imm);
+          } else {
+            TermKey k{a, in.op == RC_OP_FDIV ? kFdiv : kMod, in.imm};
+            auto it = term_ids.find(k);
+            int id;
+            if (it == term_ids.end()) {
+              if ((int)terms.size() >= kMaxTerms) { err = RC_E_UNSUPPORTED; return false; }
+              id = (int)terms.size();
+              terms.push_back(k);
+              term_ids[k] = id;
+              term_level.push_back(level_of(a));
+              term_tid.push_back(depends_on_tid(a));
+            } else {
+              id = it->second;
+            }
+            r.v[kMaxLoops + id] = 1;
+          }
+          st.back() = r;
+          break;
+        }
+        default: err = RC_E_INVALID; return false;
+      }
+    }
+    if (st.size() != 1) { err = RC_E_INVALID; return false; }
+    *out = st.back();
+    return true;
+  }
+};
+
+void put_row(const Lin& l, std::vector<Row>* rows, std::vector<LinTerm>* lin) {
+  Row r;
+  r.c0 = l.c0;
+  for (int i = 0; i < 6; ++i) r.ct[i] = l.ct[i];
+  r.off = (int32_t)lin->size();
+  r.nnz = (int32_t)l.v.size();
+  for (auto& kv : l.v) {
+    LinTerm t;
+    t.var = kv.first;
+    t.pad = 0;
+    t.coef = kv.second;
+    lin->push_back(t);
+  }
+  rows->push_back(r);
+}
+
+bool mul_ok(uint64_t a, uint64_t b, uint64_t* r) {
+  if (a != 0 && b > UINT64_MAX / a) return false;
+  *r = a * b;
+  return true;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_ids) {
+  if (!d || !m) return RC_E_INVALID;
+  for (int i = 0; i < 3; ++i)
+    if (d->grid[i] == 0 || d->block[i] == 0) return RC_E_INVALID;
+  if (d->n_phases == 0) return RC_E_INVALID;
+  if (d->n_stmts > (uint32_t)kMaxStmts) return RC_E_UNSUPPORTED;
+  if (d->n_stmts && !d->stmts) return RC_E_INVALID;
+  if (d->n_arrays && !d->arrays) return RC_E_INVALID;
+  if (d->n_params && !d->params) return RC_E_INVALID;
+
+  DevModel& h = m->host;
+  std::memset(&h, 0, sizeof(h));
+  for (int i = 0; i < 3; ++i) { h.grid[i] = d->grid[i]; h.block[i] = d->block[i]; }
+  uint64_t bs = 0, nb = 0, nt = 0;
+  if (!mul_ok((uint64_t)d->block[0] * d->block[1], d->block[2], &bs)) return RC_E_UNSUPPORTED;
+  if (!mul_ok((uint64_t)d->grid[0] * d->grid[1], d->grid[2], &nb)) return RC_E_UNSUPPORTED;
+  if (bs > (1u << 20) || !mul_ok(bs, nb, &nt) || nt >= (1ull << 42)) return RC_E_UNSUPPORTED;
+  h.bs = (uint32_t)bs;
+  h.n_blocks = nb;
+  h.n_threads = nt;
+  h.n_stmts = d->n_stmts;
+  h.n_phases = d->n_phases;
+
+  // arrays and the linear cell space
+  std::vector<DevArray> arrays(d->n_arrays);
+  uint64_t cells_total = 0;
+  m->array_base.assign(d->n_arrays, 0);
+  m->array_cells.assign(d->n_arrays, 0);
+  m->array_shared.assign(d->n_arrays, 0);
+  for (uint32_t a = 0; a < d->n_arrays; ++a) {
+    const rc_array& A = d->arrays[a];
+    if (A.ndims < 1 || A.ndims > (uint32_t)kMaxDims) return RC_E_INVALID;
+    if (A.scope != RC_SCOPE_GLOBAL && A.scope != RC_SCOPE_SHARED) return RC_E_INVALID;
+    DevArray& D = arrays[a];
+    std::memset(&D, 0, sizeof(D));
+    uint64_t c = 1;
+    for (uint32_t k = 0; k < A.ndims; ++k) {
+      if (A.extent[k] < 1) return RC_E_INVALID;
+      if (!mul_ok(c, (uint64_t)A.extent[k], &c) || c >= (1ull << 62)) return RC_E_KEY_OVERFLOW;
+      D.ext[k] = A.extent[k];
+    }
+    D.ndims = (int32_t)A.ndims;
+    D.shared = A.scope == RC_SCOPE_SHARED;
+    D.base = cells_total;
+    D.cells = c;
+    uint64_t span;
+    if (!mul_ok(c, D.shared ? nb : 1, &span) || cells_total + span < cells_total ||
+        cells_total + span >= (1ull << 62))
+      return RC_E_KEY_OVERFLOW;
+    m->array_base[a] = cells_total;
+    m->array_cells[a] = c;
+    m->array_shared[a] = D.shared;
+    cells_total += span;
+  }
+  m->total_cells = cells_total;
+
+  // key layout [cell | phase | block | thread | kind]
+  h.kind_shift = 0;
+  h.thread_shift = 1;
+  h.thread_bits = bit_length(bs - 1);
+  h.block_shift = h.thread_shift + h.thread_bits;
+  h.block_bits = bit_length(nb - 1);
+  h.phase_shift = h.block_shift + h.block_bits;
+  h.phase_bits = bit_length((uint64_t)d->n_phases - 1);
+  if (h.phase_bits > (uint32_t)kMaxPhaseBits) return RC_E_UNSUPPORTED;
+  h.cell_shift = h.phase_shift + h.phase_bits;
+  // one more value than the cells so the all-ones cell field is never a valid cell
+  h.cell_bits = bit_length(cells_total);
+  if (h.cell_shift + h.cell_bits > (uint32_t)kKeyBits) return RC_E_KEY_OVERFLOW;
+  h.sort_lo = h.phase_shift;
+  h.sort_hi = h.cell_shift + h.cell_bits;
+
+  // statements
+  std::vector<DevStmt> stmts(d->n_stmts);
+  std::vector<DevAccess> accs;
+  std::vector<Row> rows;
+  std::vector<LinTerm> lin;
+  std::vector<Term> terms;
+  uint64_t dense_slots = 0;
+  general_ids->clear();
+  for (uint32_t s = 0; s < d->n_stmts; ++s) {
+    const rc_stmt& S = d->stmts[s];
+    DevStmt& D = stmts[s];
+    std::memset(&D, 0, sizeof(D));
+    if (S.n_loops > (uint32_t)kMaxLoops || S.n_accesses > (uint32_t)kMaxAccesses) return RC_E_UNSUPPORTED;
+    if ((S.n_loops && !S.loops) || (S.n_guards && !S.guards) || (S.n_accesses && !S.accesses))
+      return RC_E_INVALID;
+    StmtBuilder b;
+    b.desc = d;
+    b.loop_tid.assign(kMaxLoops, false);
+    std::vector<Lin> lo(S.n_loops), hi(S.n_loops), guards(S.n_guards);
+    Lin phase;
+    bool dense = true;
+    for (uint32_t l = 0; l < S.n_loops; ++l) {
+      if (S.loops[l].step <= 0) return RC_E_INVALID;
+      if (!b.compile(S.loops[l].lower, (int)l, &lo[l])) return b.err;
+      if (!b.compile(S.loops[l].upper, (int)l, &hi[l])) return b.err;
+      b.loop_tid[l] = b.depends_on_tid(lo[l]) || b.depends_on_tid(hi[l]);
+      Lin diff = hi[l];
+      diff.add(lo[l], -1);
+      if (diff.is_const()) {
+        int64_t span = diff.c0;
+        D.trips[l] = span <= 0 ? 0 : (int64_t)(((uint64_t)span + (uint64_t)S.loops[l].step - 1) /
+                                               (uint64_t)S.loops[l].step);
+      } else {
+        dense = false;
+      }
+      D.step[l] = S.loops[l].step;
+    }
+    int nl = (int)S.n_loops;
+    for (uint32_t g = 0; g < S.n_guards; ++g)
+      if (!b.compile(S.guards[g], nl, &guards[g])) return b.err;
+    if (!b.compile(S.phase, nl, &phase)) return b.err;
+    if (b.depends_on_tid(phase)) return RC_E_INVALID;   // a barrier interval is block-uniform
+    std::vector<std::vector<Lin>> idx(S.n_accesses);
+    for (uint32_t a = 0; a < S.n_accesses; ++a) {
+      const rc_access& A = S.accesses[a];
+      if (A.array >= d->n_arrays || (A.kind != RC_READ && A.kind != RC_WRITE) || !A.index)
+        return RC_E_INVALID;
+      idx[a].resize(d->arrays[A.array].ndims);
+      for (uint32_t k = 0; k < d->arrays[A.array].ndims; ++k)
+        if (!b.compile(A.index[k], nl, &idx[a][k])) return b.err;
+    }
+    // emit rows
+    D.n_loops = nl;
+    D.n_guards = (int32_t)S.n_guards;
+    D.n_acc = (int32_t)S.n_accesses;
+    for (int l = 0; l < nl; ++l) {
+      D.row_lower[l] = (int32_t)rows.size(); put_row(lo[l], &rows, &lin);
+      D.row_upper[l] = (int32_t)rows.size(); put_row(hi[l], &rows, &lin);
+    }
+    D.guard_row0 = (int32_t)rows.size();
+    for (auto& g : guards) put_row(g, &rows, &lin);
+    D.row_phase = (int32_t)rows.size();
+    put_row(phase, &rows, &lin);
+    D.acc0 = (int32_t)accs.size();
+    for (uint32_t a = 0; a < S.n_accesses; ++a) {
+      DevAccess da;
+      da.array = (int32_t)S.accesses[a].array;
+      da.kind = (int32_t)S.accesses[a].kind;
+      da.ndims = (int32_t)idx[a].size();
+      da.row0 = (int32_t)rows.size();
+      for (auto& e : idx[a]) put_row(e, &rows, &lin);
+      accs.push_back(da);
+    }
+    D.term0 = (int32_t)terms.size();
+    D.n_terms = (int32_t)b.terms.size();
+    for (size_t q = 0; q < b.terms.size(); ++q) {
+      Term t;
+      t.row = (int32_t)rows.size();
+      put_row(b.terms[q].inner, &rows, &lin);
+      t.op = b.terms[q].op;
+      t.d = b.terms[q].d;
+      t.level = b.term_level[q];
+      t.pad = 0;
+      terms.push_back(t);
+    }
+    D.dense = dense ? 1 : 0;
+    if (dense) {
+      uint64_t it = 1;
+      for (int l = 0; l < nl; ++l)
+        if (!mul_ok(it, (uint64_t)D.trips[l], &it)) return RC_E_UNSUPPORTED;
+      D.n_iter = it;
+      uint64_t slots;
+      if (!mul_ok(it, (uint64_t)S.n_accesses, &slots) || !mul_ok(slots, nt, &slots) ||
+          dense_slots + slots < dense_slots)
+        return RC_E_UNSUPPORTED;
+      D.slot_base = dense_slots;
+      dense_slots += slots;
+    } else {
+      D.n_iter = 0;
+      D.slot_base = (uint64_t)general_ids->size() * nt;   // index of its first unit offset
+      general_ids->push_back((int32_t)s);
+    }
+  }
+  h.dense_slots = dense_slots;
+  h.general_slots = 0;   // filled in after the device count pass
+  m->n_general_stmts = (uint32_t)general_ids->size();
+
+  // program image: header | arrays | stmts | accs | rows | lin | terms (256-aligned sections)
+  size_t off_arrays = align256(sizeof(DevModel));
+  size_t off_stmts = align256(off_arrays + arrays.size() * sizeof(DevArray));
+  size_t off_accs = align256(off_stmts + stmts.size() * sizeof(DevStmt));
+  size_t off_rows = align256(off_accs + accs.size() * sizeof(DevAccess));
+  size_t off_lin = align256(off_rows + rows.size() * sizeof(Row));
+  size_t off_terms = align256(off_lin + lin.size() * sizeof(LinTerm));
+  size_t off_units = align256(off_terms + terms.size() * sizeof(Term));
+  size_t total = off_units;
+  m->program.assign(total, 0);
+  auto put = [&](size_t off, const void* src, size_t n) {
+    if (n) std::memcpy(m->program.data() + off, src, n);
+  };
+  put(off_arrays, arrays.data(), arrays.size() * sizeof(DevArray));
+  put(off_stmts, stmts.data(), stmts.size() * sizeof(DevStmt));
+  put(off_accs, accs.data(), accs.size() * sizeof(DevAccess));
+  put(off_rows, rows.data(), rows.size() * sizeof(Row));
+  put(off_lin, lin.data(), lin.size() * sizeof(LinTerm));
+  put(off_terms, terms.data(), terms.size() * sizeof(Term));
+  // device pointers are stored as offsets here and relocated at upload
+  h.arrays = reinterpret_cast<const DevArray*>(off_arrays);
+  h.stmts = reinterpret_cast<const DevStmt*>(off_stmts);
+  h.accs = reinterpret_cast<const DevAccess*>(off_accs);
+  h.rows = reinterpret_cast<const Row*>(off_rows);
+  h.lin = reinterpret_cast<const LinTerm*>(off_lin);
+  h.terms = reinterpret_cast<const Term*>(off_terms);
+  h.unit_offset = reinterpret_cast<const uint64_t*>(off_units);
+  return RC_OK;
+}
+
+void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp) {
+  std::memset(sp, 0, sizeof(*sp));
+  uint32_t dbits = digit_bits == 0 ? 8 : digit_bits;
+  if (dbits > 8) dbits = 8;
+  if (dbits < 4) dbits = 4;
+  if (hi <= lo) return;
+  uint32_t n = hi - lo;
+  uint32_t passes = (n + dbits - 1) / dbits;
+  uint32_t base = n / passes, extra = n % passes;
+  uint32_t sh = lo;
+  for (uint32_t p = 0; p < passes; ++p) {
+    uint32_t w = base + (p < extra ? 1 : 0);
+    sp->shift[p] = sh;
+    sp->bits[p] = w;
+    sh += w;
+  }
+  sp->n_pass = passes;
+}
+
+}  // namespace rc

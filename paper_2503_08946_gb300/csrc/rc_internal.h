@@ -1,0 +1,350 @@
+// Internal data structures of the race checker: the lowered model program that
+// the expansion kernels interpret, the device-side result record, the
+// workspace plan and the segment-summary monoid of the scan.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/rc.h"
+
+#ifdef __CUDACC__
+#define RC_HD __host__ __device__ __forceinline__
+#else
+#define RC_HD inline
+#endif
+
+namespace rc {
+
+constexpr int kMaxLoops = 8;      // loop depth per statement
+constexpr int kMaxTerms = 16;     // distinct floor-div / mod terms per statement
+constexpr int kMaxStmts = 4096;
+constexpr int kMaxAccesses = 64;  // per statement
+constexpr int kMaxDims = 4;
+constexpr int kMaxPhaseBits = 16;
+constexpr int kKeyBits = 63;      // bit 63 is reserved so 0xFFFF...FFFF is never a valid key
+constexpr uint64_t kSentinel = ~0ull;
+
+// ---------------------------------------------------------------------------
+// lowered program
+//
+// Every expression of a statement (loop bounds, guards, phase, indices and the
+// operands of its floor-div / mod terms) becomes a *row*:
+//     value = c0 + ct . (tid.x, tid.y, tid.z, bid.x, bid.y, bid.z)
+//                + sum_k coef_k * var_k
+// where var_k is an iterator (var < kMaxLoops) or a term (var - kMaxLoops);
+// parameters are folded into the constants.  A term is
+//     term_q = op_q(value(row_q), d_q),   op = floor division or Euclidean mod,
+// evaluated once its iterators are bound (level_q = number of loop levels it
+// needs).
+// ---------------------------------------------------------------------------
+struct LinTerm {
+  int32_t var;
+  int32_t pad;
+  int64_t coef;
+};
+
+struct Row {
+  int64_t c0;
+  int64_t ct[6];
+  int32_t off;   // first LinTerm of this row in the model's pool
+  int32_t nnz;
+};
+
+enum TermOp : int32_t { kFdiv = 0, kMod = 1 };
+
+struct Term {
+  int32_t row;
+  int32_t op;
+  int64_t d;
+  int32_t level;   // iterators 0..level-1 must be bound
+  int32_t pad;
+};
+
+struct DevAccess {
+  int32_t array;
+  int32_t kind;
+  int32_t ndims;
+  int32_t row0;    // first of ndims consecutive index rows
+};
+
+struct DevArray {
+  int64_t ext[kMaxDims];
+  int32_t ndims;
+  int32_t shared;
+  uint64_t base;   // first linear cell
+  uint64_t cells;  // cells of one scope instance
+};
+
+struct DevStmt {
+  int32_t n_loops, n_guards, n_acc, n_terms;
+  int32_t row_lower[kMaxLoops];
+  int32_t row_upper[kMaxLoops];
+  int64_t step[kMaxLoops];
+  int32_t row_phase;
+  int32_t guard_row0;   // guards are rows [guard_row0, guard_row0 + n_guards)
+  int32_t acc0;         // first DevAccess
+  int32_t term0;        // first Term
+  int32_t dense;        // 1 = every loop has a constant trip count
+  int32_t pad;
+  int64_t trips[kMaxLoops];
+  uint64_t n_iter;      // product of trips (dense)
+  uint64_t slot_base;   // dense: first key slot; general: index of its first unit offset
+};
+
+struct DevModel {
+  uint32_t grid[3], block[3];
+  uint32_t bs;            // threads per block
+  uint32_t n_stmts;
+  uint64_t n_blocks;
+  uint64_t n_threads;     // n_blocks * bs
+  int64_t n_phases;
+  // key layout
+  uint32_t kind_shift, thread_shift, block_shift, phase_shift, cell_shift;
+  uint32_t thread_bits, block_bits, phase_bits, cell_bits;
+  uint32_t sort_lo, sort_hi;
+  uint64_t dense_slots;   // keys [0, dense_slots) are written by dense statements
+  uint64_t general_slots; // keys [dense_slots, dense_slots + general_slots) by general ones
+  // pointers into the uploaded program (device addresses)
+  const DevStmt* stmts;
+  const DevAccess* accs;
+  const DevArray* arrays;
+  const Row* rows;
+  const LinTerm* lin;
+  const Term* terms;
+  const uint64_t* unit_offset;  // general statements: offset of each (stmt, gtid) unit
+};
+
+// ---------------------------------------------------------------------------
+// device result record (head of the workspace)
+// ---------------------------------------------------------------------------
+struct DevResult {
+  unsigned long long oob_code;     // min packed (stmt, access, gtid, dimcode); ~0 = none
+  unsigned long long instances;    // guard-true access instances
+  unsigned long long racy_cells;
+  unsigned long long min_start;    // first key position of the first racy cell; ~0 = none
+  unsigned long long seg_end;      // one past its last key
+  unsigned long long cell;         // its cell value
+  unsigned long long x_rank;       // witness x as (p, t, k) packed; ~0 = none
+  unsigned long long y_rank;       // witness y as (b, p, t, k) packed; ~0 = none
+  unsigned int minb, maxb, minWb, maxWb, anyW, err;
+  unsigned long long n_keys;       // keys in the sorted buffer
+  unsigned long long sorted_buf;   // index (0/1) of the buffer that holds the sorted keys
+  unsigned long long pad[4];
+};
+static_assert(sizeof(DevResult) <= 256, "result record must fit its slot");
+
+enum DevError : unsigned int {
+  kErrLookbackTimeout = 1u,
+  kErrHashTimeout = 2u,
+  kErrHashFull = 4u,
+};
+
+// packed out-of-bounds code: stmt (12 bits) | access (6) | gtid (42) | dimcode (3)
+RC_HD unsigned long long oob_pack(uint32_t stmt, uint32_t acc, uint64_t gtid, uint32_t dimcode) {
+  return ((unsigned long long)stmt << 51) | ((unsigned long long)acc << 45) |
+         ((unsigned long long)(gtid & ((1ull << 42) - 1)) << 3) | (unsigned long long)dimcode;
+}
+
+// ---------------------------------------------------------------------------
+// floor division / Euclidean modulo by a positive constant (int64)
+// ---------------------------------------------------------------------------
+RC_HD int64_t floor_div(int64_t a, int64_t d) {
+  int64_t q = a / d;
+  return ((a % d) != 0 && a < 0) ? q - 1 : q;
+}
+RC_HD int64_t euclid_mod(int64_t a, int64_t d) {
+  int64_t r = a % d;
+  return r < 0 ? r + d : r;
+}
+RC_HD int64_t wadd(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
+RC_HD int64_t wmul(int64_t a, int64_t b) { return (int64_t)((uint64_t)a * (uint64_t)b); }
+
+// ---------------------------------------------------------------------------
+// segment-summary monoid of the scan
+//
+// Sorted keys are grouped by cell and, inside a cell, by (cell, phase) "sub"
+// groups.  A cell is racy iff
+//     (min block != max block)  ? (some write in the cell)
+//                               : (some sub group has min thread != max thread
+//                                  and a write),
+// the cell-level form of the pair rule (a multi-block cell races iff it has a
+// write; a single-block cell races iff two threads meet in one barrier
+// interval with a write).  A Summary describes any contiguous run of keys: the
+// piece of its first cell (L), the piece of its last cell (R), and the racy
+// cells strictly inside; combine() concatenates two runs.
+// ---------------------------------------------------------------------------
+struct SubAgg {
+  uint32_t mint, maxt, anyW, pad;
+};
+
+RC_HD SubAgg sub_merge(SubAgg a, SubAgg b) {
+  SubAgg r;
+  r.mint = a.mint < b.mint ? a.mint : b.mint;
+  r.maxt = a.maxt > b.maxt ? a.maxt : b.maxt;
+  r.anyW = a.anyW | b.anyW;
+  r.pad = 0;
+  return r;
+}
+RC_HD bool sub_racy(SubAgg s) { return s.mint != s.maxt && s.anyW; }
+RC_HD SubAgg sub_none() { SubAgg s; s.mint = 0; s.maxt = 0; s.anyW = 0; s.pad = 0; return s; }
+
+// A run of keys that all lie in one cell.
+struct CellPiece {
+  uint64_t cell;
+  uint64_t start;          // position of the run's first key
+  uint32_t minb, maxb;
+  uint32_t anyW;
+  uint32_t first_p, last_p;
+  uint32_t single_sub;     // the run holds one sub group (fs and ls are the same)
+  uint32_t inner;          // OR of sub_racy over sub groups strictly between fs and ls
+  uint32_t pad;
+  SubAgg fs, ls;           // first and last sub group of the run
+};
+
+RC_HD bool piece_racy(const CellPiece& c) {
+  if (c.minb != c.maxb) return c.anyW != 0;
+  return c.inner || sub_racy(c.fs) || sub_racy(c.ls);
+}
+
+// X then Y, both pieces of the same cell.
+RC_HD CellPiece piece_combine(const CellPiece& X, const CellPiece& Y) {
+  CellPiece r;
+  r.cell = X.cell;
+  r.start = X.start;
+  r.minb = X.minb < Y.minb ? X.minb : Y.minb;
+  r.maxb = X.maxb > Y.maxb ? X.maxb : Y.maxb;
+  r.anyW = X.anyW | Y.anyW;
+  r.first_p = X.first_p;
+  r.last_p = Y.last_p;
+  r.pad = 0;
+  if (X.last_p == Y.first_p) {
+    SubAgg m = sub_merge(X.ls, Y.fs);
+    if (X.single_sub && Y.single_sub) {
+      r.single_sub = 1; r.fs = m; r.ls = m; r.inner = 0;
+    } else if (X.single_sub) {
+      r.single_sub = 0; r.fs = m; r.ls = Y.ls; r.inner = Y.inner;
+    } else if (Y.single_sub) {
+      r.single_sub = 0; r.fs = X.fs; r.ls = m; r.inner = X.inner;
+    } else {
+      r.single_sub = 0; r.fs = X.fs; r.ls = Y.ls;
+      r.inner = X.inner | Y.inner | (sub_racy(m) ? 1u : 0u);
+    }
+  } else {
+    r.single_sub = 0;
+    r.fs = X.fs;
+    r.ls = Y.ls;
+    r.inner = X.inner | Y.inner | ((!X.single_sub && sub_racy(X.ls)) ? 1u : 0u) |
+              ((!Y.single_sub && sub_racy(Y.fs)) ? 1u : 0u);
+  }
+  return r;
+}
+
+struct Summary {
+  uint32_t empty;
+  uint32_t single_cell;    // L and R are the same piece
+  uint64_t count;          // racy cells strictly inside (neither L's nor R's cell)
+  uint64_t minstart;       // smallest start of those racy cells, ~0 if none
+  CellPiece L, R;
+};
+
+RC_HD Summary summary_empty() {
+  Summary s;
+  s.empty = 1; s.single_cell = 0; s.count = 0; s.minstart = ~0ull;
+  s.L = CellPiece{}; s.R = CellPiece{};
+  return s;
+}
+
+RC_HD uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+RC_HD Summary summary_combine(const Summary& A, const Summary& B) {
+  if (A.empty) return B;
+  if (B.empty) return A;
+  Summary r;
+  r.empty = 0;
+  if (A.R.cell == B.L.cell) {
+    CellPiece M = piece_combine(A.R, B.L);
+    if (A.single_cell && B.single_cell) {
+      r.single_cell = 1; r.L = M; r.R = M; r.count = 0; r.minstart = ~0ull;
+    } else if (A.single_cell) {
+      r.single_cell = 0; r.L = M; r.R = B.R; r.count = B.count; r.minstart = B.minstart;
+    } else if (B.single_cell) {
+      r.single_cell = 0; r.L = A.L; r.R = M; r.count = A.count; r.minstart = A.minstart;
+    } else {
+      bool mr = piece_racy(M);
+      r.single_cell = 0; r.L = A.L; r.R = B.R;
+      r.count = A.count + B.count + (mr ? 1 : 0);
+      r.minstart = umin64(A.minstart, umin64(B.minstart, mr ? M.start : ~0ull));
+    }
+  } else {
+    r.single_cell = 0;
+    r.L = A.L;
+    r.R = B.R;
+    bool ar = !A.single_cell && piece_racy(A.R);
+    bool bl = !B.single_cell && piece_racy(B.L);
+    r.count = A.count + B.count + (ar ? 1 : 0) + (bl ? 1 : 0);
+    r.minstart = umin64(umin64(A.minstart, B.minstart),
+                        umin64(ar ? A.R.start : ~0ull, bl ? B.L.start : ~0ull));
+  }
+  return r;
+}
+
+// Final count / first racy start of a whole run.
+RC_HD void summary_finish(const Summary& s, uint64_t* count, uint64_t* minstart) {
+  if (s.empty) { *count = 0; *minstart = ~0ull; return; }
+  bool lr = piece_racy(s.L);
+  bool rr = !s.single_cell && piece_racy(s.R);
+  *count = s.count + (lr ? 1 : 0) + (rr ? 1 : 0);
+  uint64_t m = s.minstart;
+  if (rr) m = umin64(m, s.R.start);
+  if (lr) m = umin64(m, s.L.start);
+  *minstart = m;
+}
+
+// ---------------------------------------------------------------------------
+// host-side model and workspace plan
+// ---------------------------------------------------------------------------
+struct SortPlan {
+  uint32_t n_pass;
+  uint32_t shift[16];
+  uint32_t bits[16];
+};
+
+struct WorkspacePlan {
+  size_t result_off;      // DevResult
+  size_t keys_off[2];     // ping-pong key buffers
+  size_t hist_off;        // n_pass x 256 uint64 digit counts
+  size_t digoff_off;      // n_pass x 256 uint64 digit offsets
+  size_t lookback_off;    // n_tiles x 256 uint64 status words (one pass at a time)
+  size_t tilectr_off;     // n_pass uint32 tile counters
+  size_t summ_off;        // scan summaries
+  size_t group_off;       // witness per-phase group summaries
+  size_t zero_lo, zero_hi;  // byte range cleared at the start of a check
+  size_t total;
+  uint64_t n_keys;
+  uint64_t n_tiles;
+  uint32_t scan_warps;
+  SortPlan sort;
+};
+
+struct Model {
+  DevModel host;                  // copy of the device header (device pointers inside)
+  std::vector<uint8_t> program;   // host image of the uploaded program
+  void* dev_program = nullptr;    // device allocation (program + unit offsets)
+  size_t dev_bytes = 0;
+  uint64_t key_slots = 0;
+  uint64_t total_cells = 0;
+  std::vector<uint64_t> array_base, array_cells;
+  std::vector<uint32_t> array_shared;
+  uint32_t n_general_stmts = 0;
+  uint64_t max_iter_per_unit = 0;
+};
+
+// implemented in lower.cpp
+rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);
+void plan_workspace(const Model& m, uint32_t digit_bits, WorkspacePlan* p);
+void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp);
+uint32_t bit_length(uint64_t v);
+
+}  // namespace rc

@@ -1,0 +1,561 @@
+// C ABI of the race checker (include/rc.h): model creation, workspace plan,
+// the enqueued check pipeline and result tickets.
+//
+// rc_check enqueues, on the caller's stream:
+//   clear of the look-back / histogram region -> result init -> K1 expand ->
+//   digit histograms -> per pass K2 onesweep -> K3 scan + fold -> K4 witness ->
+//   device-to-host copy of the result record into the ticket's pinned buffer.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "rc_internal.h"
+
+struct rc_model {
+  rc::Model m;
+};
+
+struct rc_ticket_s {
+  cudaEvent_t done = nullptr;
+  rc::DevResult* host = nullptr;   // pinned, `cap` records
+  size_t cap = 0;
+  size_t n = 0;
+  std::vector<const rc_model*> models;
+  rc_status enqueue_status = RC_OK;
+};
+
+namespace {
+
+std::mutex g_pool_mu;
+std::vector<rc_ticket_s*> g_pool;
+
+rc_ticket_s* ticket_get(size_t n) {
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (size_t i = 0; i < g_pool.size(); ++i) {
+      if (g_pool[i]->cap >= n) {
+        rc_ticket_s* t = g_pool[i];
+        g_pool.erase(g_pool.begin() + (long)i);
+        t->n = n;
+        t->models.assign(n, nullptr);
+        t->enqueue_status = RC_OK;
+        return t;
+      }
+    }
+  }
+  rc_ticket_s* t = new (std::nothrow) rc_ticket_s();
+  if (!t) return nullptr;
+  size_t cap = n < 1 ? 1 : n;
+  if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void**)&t->host, cap * sizeof(rc::DevResult)) != cudaSuccess) {
+    if (t->done) cudaEventDestroy(t->done);
+    delete t;
+    return nullptr;
+  }
+  t->cap = cap;
+  t->n = n;
+  t->models.assign(n, nullptr);
+  return t;
+}
+
+void ticket_put(rc_ticket_s* t) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool.size() < 64) {
+    g_pool.push_back(t);
+  } else {
+    cudaEventDestroy(t->done);
+    cudaFreeHost(t->host);
+    delete t;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+rc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RC_OK : RC_E_CUDA; }
+
+uint32_t scan_warps_for(uint64_t n) {
+  uint64_t w = (n + 2047) / 2048;
+  const uint64_t cap = 152ull * 64;
+  if (w > cap) w = cap;
+  if (w < 1) w = 1;
+  return (uint32_t)w;
+}
+
+}  // namespace
+
+namespace rc {
+
+void plan_workspace(const Model& m, uint32_t digit_bits, WorkspacePlan* p) {
+  std::memset(p, 0, sizeof(*p));
+  plan_sort(m.host.sort_lo, m.host.sort_hi, digit_bits, &p->sort);
+  const uint64_t n = m.key_slots;
+  p->n_keys = n;
+  p->n_tiles = (n + kSortTile - 1) / kSortTile;
+  p->scan_warps = scan_warps_for(n);
+  size_t off = 0;
+  p->result_off = off;
+  off = align256(off + sizeof(DevResult));
+  p->keys_off[0] = off;
+  off = align256(off + n * 8);
+  p->keys_off[1] = off;
+  off = align256(off + n * 8);
+  p->zero_lo = off;
+  p->hist_off = off;
+  off = align256(off + (size_t)16 * kRadix * 8);
+  p->lookback_off = off;
+  off = align256(off + (size_t)p->n_tiles * kRadix * 8);
+  p->tilectr_off = off;
+  off = align256(off + 16 * sizeof(unsigned int));
+  p->zero_hi = off;
+  p->digoff_off = off;
+  off = align256(off + (size_t)16 * kRadix * 8);
+  p->summ_off = off;
+  off = align256(off + (size_t)p->scan_warps * sizeof(Summary));
+  p->group_off = off;
+  off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
+  p->total = off;
+}
+
+}  // namespace rc
+
+namespace {
+
+rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* ws, int sorted_buf) {
+  rc::ScanArgs a;
+  a.keys = reinterpret_cast<const uint64_t*>(ws + p.keys_off[sorted_buf]);
+  a.n = p.n_keys;
+  a.cell_shift = m.host.cell_shift;
+  a.phase_shift = m.host.phase_shift;
+  a.block_shift = m.host.block_shift;
+  a.thread_shift = m.host.thread_shift;
+  a.phase_bits = m.host.phase_bits;
+  a.block_bits = m.host.block_bits;
+  a.thread_bits = m.host.thread_bits;
+  a.summaries = reinterpret_cast<rc::Summary*>(ws + p.summ_off);
+  a.n_warps = p.scan_warps;
+  a.per_warp = ((p.n_keys + p.scan_warps - 1) / p.scan_warps + 31) / 32 * 32;
+  if (a.per_warp == 0) a.per_warp = 32;
+  a.res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  a.groups = reinterpret_cast<unsigned int*>(ws + p.group_off);
+  return a;
+}
+
+// Enqueue the sort of p.n_keys keys from buffer 0; returns the index of the
+// buffer holding the sorted keys.
+rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, uint64_t* buf1,
+                       uint64_t spin_limit, uint32_t test_flags, cudaStream_t st, int* sorted_buf) {
+  uint64_t* bufs[2] = {buf0, buf1};
+  auto* hist = reinterpret_cast<unsigned long long*>(ws + p.hist_off);
+  auto* digoff = reinterpret_cast<unsigned long long*>(ws + p.digoff_off);
+  auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  rc_status s = cuda_status(rc::launch_histogram(bufs[0], p.n_keys, p.sort, hist, st));
+  if (s != RC_OK) return s;
+  s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort.n_pass, st));
+  if (s != RC_OK) return s;
+  int cur = 0;
+  for (uint32_t k = 0; k < p.sort.n_pass; ++k) {
+    rc::SortArgs a;
+    a.keys_in = bufs[cur];
+    a.keys_out = bufs[1 - cur];
+    a.n = p.n_keys;
+    a.shift = p.sort.shift[k];
+    a.bits = p.sort.bits[k];
+    a.digit_offset = digoff + (size_t)k * rc::kRadix;
+    a.lookback = reinterpret_cast<unsigned long long*>(ws + p.lookback_off);
+    a.tile_counter = reinterpret_cast<unsigned int*>(ws + p.tilectr_off) + k;
+    a.epoch = k + 1;
+    // the stall test waits for an epoch no pass ever publishes
+    a.wait_epoch = (test_flags & RC_TEST_STALL_LOOKBACK) ? (k + 1) ^ 0x8000u : k + 1;
+    a.spin_limit = spin_limit;
+    a.err = &res->err;
+    s = cuda_status(rc::launch_onesweep(a, st));
+    if (s != RC_OK) return s;
+    cur = 1 - cur;
+  }
+  *sorted_buf = cur;
+  return RC_OK;
+}
+
+rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
+                        cudaStream_t st, rc::DevResult* host_out) {
+  const rc::Model& m = model->m;
+  rc::WorkspacePlan p;
+  rc::plan_workspace(m, opts ? opts->digit_bits : 0, &p);
+  if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
+  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 22);
+  auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
+  if (s != RC_OK) return s;
+  s = cuda_status(rc::launch_init_result(res, st));
+  if (s != RC_OK) return s;
+  const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
+  s = cuda_status(rc::launch_expand(dm, (uint64_t)m.host.n_stmts * m.host.n_threads,
+                                    reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
+  if (s != RC_OK) return s;
+  int sorted = 0;
+  s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
+                   reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin,
+                   opts ? opts->test_flags : 0u, st, &sorted);
+  if (s != RC_OK) return s;
+  if (p.n_keys > 0) {
+    rc::ScanArgs sa = scan_args(m, p, ws, sorted);
+    s = cuda_status(rc::launch_scan(sa, st));
+    if (s != RC_OK) return s;
+    s = cuda_status(rc::launch_witness(sa, st));
+    if (s != RC_OK) return s;
+  }
+  if (host_out) {
+    s = cuda_status(cudaMemcpyAsync(host_out, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+    if (s != RC_OK) return s;
+  }
+  return RC_OK;
+}
+
+void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->instances = r.instances;
+  if (r.err & rc::kErrLookbackTimeout) {
+    out->status = RC_E_TIMEOUT;
+    return;
+  }
+  if (r.oob_code != ~0ull) {
+    out->status = RC_E_OOB;
+    out->oob_stmt = (uint32_t)(r.oob_code >> 51);
+    out->oob_access = (uint32_t)((r.oob_code >> 45) & 63u);
+    out->oob_gtid = (r.oob_code >> 3) & ((1ull << 42) - 1);
+    out->oob_dim = (int32_t)(r.oob_code & 7u);
+    return;
+  }
+  out->status = RC_OK;
+  out->racy_cells = r.racy_cells;
+  out->verdict = r.racy_cells > 0;
+  if (!out->verdict || r.x_rank == ~0ull || r.y_rank == ~0ull) return;
+  // cell -> (array, scope instance, element)
+  const uint64_t cell = r.cell;
+  size_t a = 0;
+  for (size_t k = 0; k < m.array_base.size(); ++k)
+    if (m.array_base[k] <= cell) a = k;
+  const uint64_t rem = cell - m.array_base[a];
+  out->w_array = (uint32_t)a;
+  out->w_scope = m.array_shared[a] ? rem / m.array_cells[a] : 0;
+  out->w_addr = m.array_shared[a] ? rem % m.array_cells[a] : rem;
+  const uint32_t tb = m.host.thread_bits, pb = m.host.phase_bits;
+  const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1;
+  const uint64_t bs = m.host.bs;
+  out->x.block = r.minb;
+  out->x.kind = (uint32_t)(r.x_rank & 1ull);
+  out->x.thread = (uint32_t)((r.x_rank >> 1) & tmask);
+  out->x.phase = (int64_t)((r.x_rank >> (tb + 1)) & pmask);
+  out->x.gtid = out->x.block * bs + out->x.thread;
+  out->y.kind = (uint32_t)(r.y_rank & 1ull);
+  out->y.thread = (uint32_t)((r.y_rank >> 1) & tmask);
+  out->y.phase = (int64_t)((r.y_rank >> (tb + 1)) & pmask);
+  out->y.block = r.y_rank >> (pb + tb + 1);
+  out->y.gtid = out->y.block * bs + out->y.thread;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rc_status_str(rc_status s) {
+  switch (s) {
+    case RC_OK: return "ok";
+    case RC_E_INVALID: return "invalid descriptor or argument";
+    case RC_E_KEY_OVERFLOW: return "packed key exceeds 63 bits";
+    case RC_E_OOB: return "index or phase out of bounds";
+    case RC_E_NOMEM: return "workspace too small or allocation failed";
+    case RC_E_TIMEOUT: return "bounded device wait expired";
+    case RC_E_CUDA: return "CUDA runtime error";
+    case RC_E_NOT_READY: return "not ready";
+    case RC_E_UNSUPPORTED: return "model outside this build's limits";
+  }
+  return "unknown status";
+}
+
+void rc_get_limits(rc_limits* out) {
+  if (!out) return;
+  out->max_loops = rc::kMaxLoops;
+  out->max_terms = rc::kMaxTerms;
+  out->max_stmts = rc::kMaxStmts;
+  out->max_accesses = rc::kMaxAccesses;
+  out->max_phase_bits = rc::kMaxPhaseBits;
+  out->key_bits = rc::kKeyBits;
+}
+
+rc_status rc_model_create(const rc_model_desc* desc, rc_model** out) {
+  if (!out) return RC_E_INVALID;
+  *out = nullptr;
+  rc_model* mm = new (std::nothrow) rc_model();
+  if (!mm) return RC_E_NOMEM;
+  rc::Model& m = mm->m;
+  std::vector<int32_t> general;
+  rc_status s = rc::lower_model(desc, &m, &general);
+  if (s != RC_OK) {
+    delete mm;
+    return s;
+  }
+  const uint64_t T = m.host.n_threads;
+  const uint64_t n_units_general = (uint64_t)general.size() * T;
+  const size_t prog = m.program.size();
+  const size_t total = prog + (size_t)n_units_general * 8;
+  if (cudaMalloc(&m.dev_program, total) != cudaSuccess) {
+    delete mm;
+    return RC_E_NOMEM;
+  }
+  m.dev_bytes = total;
+  // relocate the section offsets to device addresses
+  uint8_t* base = static_cast<uint8_t*>(m.dev_program);
+  rc::DevModel& h = m.host;
+  h.arrays = reinterpret_cast<const rc::DevArray*>(base + reinterpret_cast<uintptr_t>(h.arrays));
+  h.stmts = reinterpret_cast<const rc::DevStmt*>(base + reinterpret_cast<uintptr_t>(h.stmts));
+  h.accs = reinterpret_cast<const rc::DevAccess*>(base + reinterpret_cast<uintptr_t>(h.accs));
+  h.rows = reinterpret_cast<const rc::Row*>(base + reinterpret_cast<uintptr_t>(h.rows));
+  h.lin = reinterpret_cast<const rc::LinTerm*>(base + reinterpret_cast<uintptr_t>(h.lin));
+  h.terms = reinterpret_cast<const rc::Term*>(base + reinterpret_cast<uintptr_t>(h.terms));
+  h.unit_offset = reinterpret_cast<const uint64_t*>(base + reinterpret_cast<uintptr_t>(h.unit_offset));
+  std::memcpy(m.program.data(), &h, sizeof(h));
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(m.dev_program);
+    delete mm;
+    return RC_E_CUDA;
+  }
+  cudaError_t e = cudaMemcpyAsync(m.dev_program, m.program.data(), prog, cudaMemcpyHostToDevice, st);
+  uint64_t general_slots = 0;
+  if (e == cudaSuccess && n_units_general > 0) {
+    // count the keys of each (statement, thread) unit, then scan them into offsets
+    uint64_t* offs = reinterpret_cast<uint64_t*>(base + prog);
+    void* tmp = nullptr;
+    const size_t tmp_bytes = rc::scan_u64_temp_bytes(n_units_general) + 256;
+    e = cudaMalloc(&tmp, tmp_bytes);
+    if (e == cudaSuccess) {
+      uint64_t* total_dev = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(tmp) + tmp_bytes - 256);
+      e = rc::launch_count(reinterpret_cast<const rc::DevModel*>(m.dev_program),
+                           (uint64_t)m.host.n_stmts * T, offs, st);
+      if (e == cudaSuccess)
+        e = rc::scan_u64_exclusive(offs, offs, n_units_general, h.dense_slots, static_cast<uint64_t*>(tmp),
+                                   total_dev, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&general_slots, total_dev, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      cudaFree(tmp);
+    }
+  }
+  if (e == cudaSuccess) {
+    h.general_slots = general_slots;
+    std::memcpy(m.program.data(), &h, sizeof(h));
+    e = cudaMemcpyAsync(m.dev_program, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaStreamDestroy(st);
+  if (e != cudaSuccess) {
+    cudaFree(m.dev_program);
+    delete mm;
+    return RC_E_CUDA;
+  }
+  m.key_slots = h.dense_slots + h.general_slots;
+  *out = mm;
+  return RC_OK;
+}
+
+void rc_model_destroy(rc_model* m) {
+  if (!m) return;
+  if (m->m.dev_program) cudaFree(m->m.dev_program);
+  delete m;
+}
+
+rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
+  if (!mm || !out) return RC_E_INVALID;
+  const rc::Model& m = mm->m;
+  std::memset(out, 0, sizeof(*out));
+  out->kind_shift = m.host.kind_shift;
+  out->thread_shift = m.host.thread_shift;
+  out->block_shift = m.host.block_shift;
+  out->phase_shift = m.host.phase_shift;
+  out->cell_shift = m.host.cell_shift;
+  out->thread_bits = m.host.thread_bits;
+  out->block_bits = m.host.block_bits;
+  out->phase_bits = m.host.phase_bits;
+  out->cell_bits = m.host.cell_bits;
+  out->sort_lo = m.host.sort_lo;
+  out->sort_hi = m.host.sort_hi;
+  out->key_slots = m.key_slots;
+  out->total_cells = m.total_cells;
+  out->n_arrays = (uint32_t)m.array_base.size();
+  out->n_threads_per_block = m.host.bs;
+  out->n_blocks = m.host.n_blocks;
+  for (size_t a = 0; a < m.array_base.size() && a < 64; ++a) {
+    out->array_base[a] = m.array_base[a];
+    out->array_cells[a] = m.array_cells[a];
+  }
+  return RC_OK;
+}
+
+rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes) {
+  if (!m || !bytes) return RC_E_INVALID;
+  rc::WorkspacePlan p;
+  rc::plan_workspace(m->m, opts ? opts->digit_bits : 0, &p);
+  *bytes = p.total;
+  return RC_OK;
+}
+
+rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+                   rc_ticket* ticket) {
+  if (!m || !ticket) return RC_E_INVALID;
+  *ticket = nullptr;
+  rc_ticket_s* t = ticket_get(1);
+  if (!t) return RC_E_NOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc_status s = enqueue_check(m, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host);
+  if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
+  if (s != RC_OK) {
+    ticket_put(t);
+    return s;
+  }
+  t->models[0] = m;
+  *ticket = t;
+  return RC_OK;
+}
+
+rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_check_opts* opts, size_t* bytes) {
+  if (!bytes || (n && !models)) return RC_E_INVALID;
+  size_t mx = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (!models[i]) return RC_E_INVALID;
+    size_t b;
+    rc_workspace_size(models[i], opts, &b);
+    if (b > mx) mx = b;
+  }
+  *bytes = mx;
+  return RC_OK;
+}
+
+rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, void* workspace,
+                         size_t ws_bytes, void* stream, rc_ticket* ticket) {
+  if (!ticket || (n && !models)) return RC_E_INVALID;
+  *ticket = nullptr;
+  for (size_t i = 0; i < n; ++i)
+    if (!models[i]) return RC_E_INVALID;
+  rc_ticket_s* t = ticket_get(n);
+  if (!t) return RC_E_NOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc_status s = RC_OK;
+  for (size_t i = 0; i < n && s == RC_OK; ++i) {
+    s = enqueue_check(models[i], opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host + i);
+    t->models[i] = models[i];
+  }
+  if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
+  if (s != RC_OK) {
+    ticket_put(t);
+    return s;
+  }
+  *ticket = t;
+  return RC_OK;
+}
+
+rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
+  if (!t || !out) return RC_E_INVALID;
+  if (wait) {
+    if (cudaEventSynchronize(t->done) != cudaSuccess) {
+      ticket_put(t);
+      return RC_E_CUDA;
+    }
+  } else {
+    cudaError_t q = cudaEventQuery(t->done);
+    if (q == cudaErrorNotReady) return RC_E_NOT_READY;
+    if (q != cudaSuccess) {
+      ticket_put(t);
+      return RC_E_CUDA;
+    }
+  }
+  for (size_t i = 0; i < t->n; ++i) decode_result(t->host[i], t->models[i]->m, &out[i]);
+  ticket_put(t);
+  return RC_OK;
+}
+
+rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_t* keys_dev, uint64_t* count_dev,
+                         void* stream) {
+  if (!mm || !keys_dev || !count_dev) return RC_E_INVALID;
+  const rc::Model& m = mm->m;
+  rc::WorkspacePlan p;
+  rc::plan_workspace(m, 0, &p);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  rc_status s = cuda_status(rc::launch_init_result(res, st));
+  if (s != RC_OK) return s;
+  s = cuda_status(rc::launch_expand(reinterpret_cast<const rc::DevModel*>(m.dev_program),
+                                    (uint64_t)m.host.n_stmts * m.host.n_threads, keys_dev, res, st));
+  if (s != RC_OK) return s;
+  return cuda_status(cudaMemcpyAsync(count_dev, &res->instances, 8, cudaMemcpyDeviceToDevice, st));
+}
+
+rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes) {
+  if (!bytes) return RC_E_INVALID;
+  rc::SortPlan sp;
+  rc::plan_sort(0, 64, digit_bits, &sp);
+  const uint64_t n_tiles = (n + rc::kSortTile - 1) / rc::kSortTile;
+  size_t off = align256(sizeof(rc::DevResult));
+  off = align256(off + (size_t)16 * rc::kRadix * 8);       // histograms
+  off = align256(off + (size_t)n_tiles * rc::kRadix * 8);  // look-back
+  off = align256(off + 16 * sizeof(unsigned int));         // tile counters
+  off = align256(off + (size_t)16 * rc::kRadix * 8);       // digit offsets
+  off = align256(off + n * 8);                             // ping-pong buffer
+  *bytes = off;
+  return RC_OK;
+}
+
+rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t lo_bit, uint32_t hi_bit,
+                       uint32_t digit_bits, void* workspace, size_t ws_bytes, void* stream) {
+  if (hi_bit > 64 || lo_bit > hi_bit || (n && (!keys_in || !keys_out)) || keys_in == keys_out) return RC_E_INVALID;
+  size_t need;
+  rc_sort_workspace_size(n, digit_bits, &need);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  if (!ws || ws_bytes < need) return RC_E_NOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc::WorkspacePlan p;
+  std::memset(&p, 0, sizeof(p));
+  rc::plan_sort(lo_bit, hi_bit, digit_bits, &p.sort);
+  p.n_keys = n;
+  p.n_tiles = (n + rc::kSortTile - 1) / rc::kSortTile;
+  size_t off = 0;
+  p.result_off = off;
+  off = align256(off + sizeof(rc::DevResult));
+  p.zero_lo = off;
+  p.hist_off = off;
+  off = align256(off + (size_t)16 * rc::kRadix * 8);
+  p.lookback_off = off;
+  off = align256(off + (size_t)p.n_tiles * rc::kRadix * 8);
+  p.tilectr_off = off;
+  off = align256(off + 16 * sizeof(unsigned int));
+  p.zero_hi = off;
+  p.digoff_off = off;
+  off = align256(off + (size_t)16 * rc::kRadix * 8);
+  const size_t pong = off;
+  if (n == 0) return RC_OK;
+  rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
+  if (s != RC_OK) return s;
+  s = cuda_status(rc::launch_init_result(reinterpret_cast<rc::DevResult*>(ws + p.result_off), st));
+  if (s != RC_OK) return s;
+  // Stage the input in the output buffer and ping-pong with the workspace
+  // buffer; with an odd number of passes the result lands in the workspace
+  // buffer and is copied back.
+  s = cuda_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st));
+  if (s != RC_OK) return s;
+  int sorted = 0;
+  s = enqueue_sort(p, ws, keys_out, reinterpret_cast<uint64_t*>(ws + pong), 1ull << 22, 0u, st, &sorted);
+  if (s != RC_OK) return s;
+  if (sorted == 1) s = cuda_status(cudaMemcpyAsync(keys_out, ws + pong, n * 8, cudaMemcpyDeviceToDevice, st));
+  return s;
+}
+
+}  // extern "C"

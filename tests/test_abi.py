@@ -1,0 +1,114 @@
+"""Boundary tests that need no GPU: the CUDA library builds, loads and exports
+every entry point declared in include/rc.h; the ctypes structures match the C
+layout of rc.h as compiled by gcc; descriptor validation rejects malformed
+models before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import workloads as w
+from workloads.spec import Access, Array, Loop, Model, Stmt, bid, const, it, tid, R, W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rc.h")
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_2503_08946_gb300 import build as b
+    b.build()
+    import paper_2503_08946_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(rc_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(rc):
+    lib = ctypes.CDLL(rc.binding.LIB_PATH)
+    declared = header_functions()
+    assert set(declared) == set(rc.EXPORTS), (declared, rc.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", rc.binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rc_[a-z_]+)\b", out))
+    assert set(declared) <= exported
+
+
+def test_struct_layout_matches_c(rc):
+    b = rc.binding
+    structs = ["rc_insn", "rc_expr", "rc_loop", "rc_access", "rc_stmt", "rc_array", "rc_model_desc",
+               "rc_limits", "rc_layout", "rc_check_opts", "rc_inst", "rc_result"]
+    fields = {s: [f for f, _ in getattr(b, s)._fields_] for s in structs}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for s in structs:
+        lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for f in fields[s]:
+            lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c11", "-o", exe, src], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    c_vals = dict(l.split() for l in out.strip().splitlines())
+    for s in structs:
+        cls = getattr(b, s)
+        assert int(c_vals[s]) == ctypes.sizeof(cls), s
+        for f in fields[s]:
+            assert int(c_vals[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
+
+
+def test_status_strings(rc):
+    for s in range(9):
+        assert rc.rc_status_str(s)
+    lim = rc.rc_get_limits()
+    assert lim["key_bits"] == 63 and lim["max_loops"] >= 2
+
+
+def _status(rc, m):
+    return rc.rc_model_create_status(m)
+
+
+def test_validation_rejects_malformed(rc):
+    ok_arr = [Array("a", "shared", (8,))]
+    # phase that names tid: a barrier interval must be block-uniform
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr, [Stmt([Access(0, W, (tid.x,))], phase=tid.x % 2)], n_phases=2)
+    assert _status(rc, m) == rc.RC_E_INVALID
+    # phase through the iterator of a loop whose bounds depend on tid
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr,
+              [Stmt([Access(0, W, (tid.x,))], loops=[Loop(0, tid.x)], phase=it(0) % 2)], n_phases=2)
+    assert _status(rc, m) == rc.RC_E_INVALID
+    # iterator outside the loop nest
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr, [Stmt([Access(0, W, (it(0),))])])
+    assert _status(rc, m) == rc.RC_E_INVALID
+    # parameter that does not exist
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr, [Stmt([Access(0, W, (w.param(3),))])], params=[1])
+    assert _status(rc, m) == rc.RC_E_INVALID
+    # zero-sized grid / zero phases / bad extent / non-positive step
+    assert _status(rc, Model((0, 1, 1), (8, 1, 1), ok_arr, [])) == rc.RC_E_INVALID
+    assert _status(rc, Model((1, 1, 1), (8, 1, 1), ok_arr, [], n_phases=0)) == rc.RC_E_INVALID
+    assert _status(rc, Model((1, 1, 1), (8, 1, 1), [Array("a", "global", (0,))], [])) == rc.RC_E_INVALID
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr, [Stmt([Access(0, R, (it(0),))], loops=[Loop(0, 4, 0)])])
+    assert _status(rc, m) == rc.RC_E_INVALID
+    # too deep a loop nest
+    deep = [Loop(0, 2) for _ in range(9)]
+    m = Model((1, 1, 1), (8, 1, 1), ok_arr, [Stmt([Access(0, R, (tid.x,))], loops=deep)])
+    assert _status(rc, m) == rc.RC_E_UNSUPPORTED
+
+
+def test_validation_key_overflow(rc):
+    # 2^20 blocks x 1024 threads x 2^40 cells cannot be packed into 63 bits
+    big = [Array("g", "global", (1 << 20, 1 << 20))]
+    m = Model((1 << 20, 1, 1), (1024, 1, 1), big, [Stmt([Access(0, R, (tid.x, bid.x))])], n_phases=4)
+    assert _status(rc, m) == rc.RC_E_KEY_OVERFLOW

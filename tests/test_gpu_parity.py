@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded models: verdict, racy-cell count, instance count and
+witness bit-exact; out-of-bounds reports identical; per-kernel parity of the
+expansion (key multiset) and of the radix sort (stable order)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as w
+from workloads.spec import Access, Array, Loop, Model, Stmt, bid, const, it, tid, R, W
+
+from . import pyref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_08946_gb300 import build as b
+    b.build()
+    oracle.build()
+    import paper_2503_08946_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def compare(rc, model, opts=None, exp=None):
+    got = rc.check(model, opts)
+    exp = exp or oracle.check(model)
+    assert got.status == exp.status, (model.name, got, exp)
+    assert got.instances == exp.instances, (model.name, got.instances, exp.instances)
+    if exp.status == oracle.STATUS_OOB:
+        assert (got.oob_stmt, got.oob_access, got.oob_gtid, got.oob_dim) == \
+               (exp.oob_stmt, exp.oob_access, exp.oob_gtid, exp.oob_dim)
+        return got
+    assert (got.verdict, got.racy_cells) == (exp.verdict, exp.racy_cells), (model.name, got, exp)
+    assert got.witness == exp.witness, (model.name, got.witness, exp.witness)
+    return got
+
+
+# ---------------------------------------------------------------------------
+# whole-path parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T", [1, 2, 3, 31, 32, 33, 256, 1024])
+def test_neighbor(rc, T):
+    compare(rc, w.neighbor_write_read(T))
+    compare(rc, w.neighbor_write_read(T, n_blocks=3))
+
+
+@pytest.mark.parametrize("bar,load", [(True, False), (False, False), (False, True), (True, True)])
+def test_reduction_tree(rc, bar, load):
+    g = compare(rc, w.reduction_tree(bar, load_phase=load))
+    assert g.racy_cells == (0 if bar else (255 if load else 127))
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 12, 64, 300])
+def test_polyhedral_product(rc, n):
+    g = compare(rc, w.polyhedral_product(n))
+    assert g.racy_cells == 2 * n - 3
+    compare(rc, w.polyhedral_product(n, init_stmt=True))
+
+
+@pytest.mark.parametrize("pad", [False, True])
+@pytest.mark.parametrize("bar", [False, True])
+def test_transpose_small(rc, pad, bar):
+    compare(rc, w.transpose(pad=pad, barrier=bar, n=256))
+
+
+@pytest.mark.parametrize("pad", [False, True])
+def test_transpose_full_size(rc, pad):
+    g = compare(rc, w.transpose(pad=pad, barrier=False))
+    assert g.racy_cells == 4063232 and g.instances == 16777216
+    g = compare(rc, w.transpose(pad=pad, barrier=True))
+    assert g.racy_cells == 0
+
+
+@pytest.mark.parametrize("L", [1, 32, 33, 70])
+@pytest.mark.parametrize("bar", [True, False])
+def test_ge_spmm(rc, L, bar):
+    compare(rc, w.ge_spmm_uniform(3, 64, 4, L, trailing_barrier=bar))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_affine_reduced(rc, seed):
+    for plant in (False, True):
+        m = w.random_affine(seed, n_blocks=16, block=256, plant=plant)
+        g = compare(rc, m)
+        assert g.racy_cells == (m.n_threads if plant else 0)
+
+
+@pytest.mark.parametrize("seed", range(300))
+def test_tiny_random(rc, seed):
+    compare(rc, w.tiny_random(seed))
+
+
+@pytest.mark.parametrize("digit_bits", [4, 5, 7, 8])
+def test_digit_widths(rc, digit_bits):
+    opts = {"digit_bits": digit_bits}
+    for m in (w.transpose(barrier=False, n=128), w.random_affine(3, n_blocks=4, block=128, plant=True),
+              w.tiny_random(11)):
+        compare(rc, m, opts)
+
+
+def test_empty_and_degenerate(rc):
+    arr = [Array("a", "global", (4,))]
+    # no statements at all
+    compare(rc, Model((1, 1, 1), (4, 1, 1), arr, []))
+    # every guard false
+    compare(rc, Model((2, 1, 1), (4, 1, 1), arr, [Stmt([Access(0, W, (tid.x,))], guards=[const(-1)])]))
+    # zero-trip loop
+    compare(rc, Model((2, 1, 1), (4, 1, 1), arr, [Stmt([Access(0, W, (tid.x,))], loops=[Loop(3, 3)])]))
+    # one thread, one instance
+    compare(rc, Model((1, 1, 1), (1, 1, 1), arr, [Stmt([Access(0, W, (const(2),))])]))
+    # every thread of every block writes one global cell: one racy cell with all threads in it
+    g = compare(rc, Model((64, 1, 1), (256, 1, 1), [Array("x", "global", (1,))],
+                          [Stmt([Access(0, R, (const(0),))], loops=[Loop(0, 8)]),
+                           Stmt([Access(0, W, (const(0),))])]))
+    assert g.racy_cells == 1
+    # a write by one thread among many readers of one shared cell, in one phase
+    g = compare(rc, Model((3, 1, 1), (128, 1, 1), [Array("s", "shared", (2,))],
+                          [Stmt([Access(0, R, (const(1),))]),
+                           Stmt([Access(0, W, (const(1),))], guards=[const(0) - tid.x + 77])]))
+    assert g.racy_cells == 3
+
+
+def test_out_of_bounds(rc):
+    arr = [Array("a", "global", (10,))]
+    m = Model((2, 1, 1), (8, 1, 1), arr, [Stmt([Access(0, R, (tid.x,))]), Stmt([Access(0, W, (tid.x + 3,))])])
+    g = compare(rc, m)
+    assert g.status == rc.RC_E_OOB
+    m2 = Model((1, 1, 1), (4, 1, 1), [Array("a", "shared", (4,))],
+               [Stmt([Access(0, W, (tid.x,))], phase=const(2))], n_phases=2)
+    compare(rc, m2)
+    m3 = Model((1, 1, 1), (4, 1, 1), [Array("a", "shared", (4, 4))],
+               [Stmt([Access(0, W, (tid.x, tid.x - 2))])])
+    compare(rc, m3)
+
+
+def test_batch_matches_single(rc):
+    models = [w.tiny_random(s) for s in range(20)] + [w.reduction_tree(False), w.neighbor_write_read(64)]
+    handles = [rc.rc_model_create(m) for m in models]
+    ws = rc.workspace(rc.rc_batch_workspace_size(handles))
+    res = rc.rc_report(rc.rc_check_batch(handles, None, ws))
+    for m, g in zip(models, res):
+        exp = oracle.check(m)
+        assert (g.status, g.verdict, g.racy_cells, g.instances) == (exp.status, exp.verdict, exp.racy_cells,
+                                                                   exp.instances)
+        if exp.status == 0:
+            assert g.witness == exp.witness
+
+
+def test_report_not_ready_then_ready(rc):
+    m = rc.rc_model_create(w.random_affine(1, n_blocks=64, block=256))
+    ws = rc.workspace(rc.rc_workspace_size(m))
+    t = rc.rc_check(m, None, ws)
+    got = None
+    try:
+        got = rc.rc_report(t, wait=False)[0]
+    except rc.NotReady:
+        got = rc.rc_report(t, wait=True)[0]
+    assert got.status == 0
+
+
+def test_workspace_too_small(rc):
+    m = rc.rc_model_create(w.neighbor_write_read(32))
+    ws = rc.workspace(rc.rc_workspace_size(m) - 512)
+    with pytest.raises(rc.RcError) as e:
+        rc.rc_check(m, None, ws)
+    assert e.value.status == rc.RC_E_NOMEM
+
+
+def test_lookback_timeout_is_reported_and_context_survives(rc):
+    m = w.random_affine(5, n_blocks=16, block=256)
+    opts = {"test_flags": rc.binding.RC_TEST_STALL_LOOKBACK, "spin_limit": 2000}
+    g = rc.check(m, opts)
+    assert g.status == rc.RC_E_TIMEOUT
+    # the context is still usable and the next check is exact
+    compare(rc, m)
+
+
+# ---------------------------------------------------------------------------
+# per-kernel parity
+# ---------------------------------------------------------------------------
+
+def decode_keys(keys: np.ndarray, lay: dict, model) -> list:
+    keys = keys[keys != np.uint64(0xFFFFFFFFFFFFFFFF)]
+    k = keys.astype(np.uint64)
+
+    def field(shift, bits):
+        return ((k >> np.uint64(shift)) & np.uint64((1 << bits) - 1)).astype(np.int64)
+
+    kind = (k & np.uint64(1)).astype(np.int64)
+    t = field(lay["thread_shift"], lay["thread_bits"])
+    b = field(lay["block_shift"], lay["block_bits"])
+    p = field(lay["phase_shift"], lay["phase_bits"])
+    cell = (k >> np.uint64(lay["cell_shift"])).astype(np.int64)
+    base = np.array(lay["array_base"], dtype=np.int64)
+    cells = np.array(lay["array_cells"], dtype=np.int64)
+    a = np.searchsorted(base, cell, side="right") - 1
+    rem = cell - base[a]
+    shared = np.array([1 if arr.scope == "shared" else 0 for arr in model.arrays], dtype=np.int64)[a]
+    s = np.where(shared == 1, rem // cells[a], 0)
+    e = np.where(shared == 1, rem % cells[a], rem)
+    tup = np.stack([a, s, e, b, p, t, kind], axis=1)
+    order = np.lexsort(tup.T[::-1])
+    return tup[order]
+
+
+@pytest.mark.parametrize("which", ["tiny", "reduction", "transpose", "affine", "gespmm"])
+def test_expand_key_multiset(rc, which):
+    models = {
+        "tiny": [w.tiny_random(s) for s in range(40)],
+        "reduction": [w.reduction_tree(False, load_phase=True)],
+        "transpose": [w.transpose(pad=True, barrier=True, n=128)],
+        "affine": [w.random_affine(2, n_blocks=8, block=128, plant=True)],
+        "gespmm": [w.ge_spmm_uniform(2, 64, 3, 45)],
+    }[which]
+    for model in models:
+        m = rc.rc_model_create(model)
+        lay = rc.rc_model_layout(m)
+        n = lay["key_slots"]
+        ws = rc.workspace(rc.rc_workspace_size(m))
+        keys = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rc.rc_expand_keys(m, ws, keys, cnt)
+        torch.cuda.synchronize()
+        got = decode_keys(keys[:n].cpu().numpy().view(np.uint64), lay, model)
+        exp = oracle.expand(model)
+        assert int(cnt.item()) == len(exp)
+        assert got.shape == exp.shape and np.array_equal(got, exp), model.name
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 33, 4095, 4096, 4097, 100_000, 3_000_001])
+@pytest.mark.parametrize("bits", [(0, 64), (5, 37), (21, 54), (60, 63)])
+def test_sort_stable(rc, n, bits):
+    lo, hi = bits
+    g = torch.Generator().manual_seed(n * 131 + lo)
+    x = torch.randint(-(1 << 62), 1 << 62, (max(n, 1),), generator=g, dtype=torch.int64)[:n]
+    if n > 10:
+        x[: n // 3] = x[: n // 3] & 0xFFFF    # heavy digit collisions
+    keys = x.numpy().view(np.uint64)
+    mask = np.uint64((1 << (hi - lo)) - 1) if hi - lo < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    digit = (keys >> np.uint64(lo)) & mask
+    exp = keys[np.argsort(digit, kind="stable")]
+    din = x.cuda()
+    dout = torch.empty_like(din)
+    for db in (8, 6):
+        ws = rc.workspace(rc.rc_sort_workspace_size(n, db))
+        rc.rc_sort_keys(din, dout, n, lo, hi, db, ws)
+        torch.cuda.synchronize()
+        got = dout.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, exp), (n, bits, db)
