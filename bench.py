@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the concrete-instance race check on GB300.
+
+One step = one full check (expansion, onesweep sort, segmented scan, witness)
+of the seeded random affine kernel model: 4096 blocks x 256 threads, 36
+statements with loop nests of depth <= 2 and trip counts 1-16, 4 arrays in a
+2^30-cell space, 8 barrier intervals, ~1.1e9 access instances (seed 0).  The
+model is resident on the device before the timed region; the key buffers
+(~9 GB each) are far larger than L2, so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): access instances checked per second (G/s)
+over the whole job, the per-kernel HBM roofline of the dominant kernel
+(measured live with CUDA events on the check's stream), the end-to-end rate
+through the public C-ABI calls from host descriptors, the CPU oracle baseline
+on a bounded sample, and the SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun each rank checks its own model (seed + rank): independent
+problems, no collective on the data path (weak scaling); the barrier and the
+max over ranks of the timed region are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("seeded random affine kernel model: 4096 blocks x 256 threads, 36 statements, "
+            "loop depth <= 2, trips 1-16, 4 arrays in a 2^30-cell space, 8 barrier intervals, "
+            "20% floor-div/mod, 30% writes")
+METRIC = "access instances checked/sec (G/s)"
+UNIT = "G inst/s"
+CPU_SAMPLE_BLOCKS = 128       # oracle baseline: same generator and seed, 128 of the 4096 blocks
+REF_STEP_BLOCKS = 32          # reference arm: per-step sample
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sort.cu", "kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2503_08946_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_key():
+    """DRAM bytes per key of one onesweep pass from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_key"])
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons, power = [], [], set(), []
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts) and parts[local_rank].strip().isdigit():
+            return int(parts[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (test infrastructure, timed as it stands)
+# ---------------------------------------------------------------------------
+def oracle_rate(seed: int, blocks: int):
+    import oracle
+    import workloads as w
+    oracle.build()
+    m = w.random_affine(seed, n_blocks=blocks, block=256)
+    t0 = time.perf_counter()
+    r = oracle.check(m)
+    dt = time.perf_counter() - t0
+    return r.instances, dt, m
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    # untimed warm-up steps, then K timed steps, each one oracle check of the sample
+    for _ in range(args.warmup):
+        oracle_rate(args.seed, REF_STEP_BLOCKS)
+    tot_inst, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        n, dt, _ = oracle_rate(args.seed, REF_STEP_BLOCKS)
+        tot_inst += n
+        tot_s += dt
+    value = tot_inst / tot_s / 1e9
+    sample = (f"same generator and seed with {REF_STEP_BLOCKS} of the 4096 blocks "
+              f"({tot_inst // max(1, args.steps)} instances per step)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / max(1, args.steps) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "seed": args.seed, "sample_blocks": REF_STEP_BLOCKS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+
+    seed = args.seed + rank
+    model = w.random_affine(seed, n_blocks=args.blocks)
+    h = rc.rc_model_create(model)
+    lay = rc.rc_model_layout(h)
+    opts = {"digit_bits": args.digit_bits, "flags": rc.binding.RC_OPT_STAGE_TIMES}
+    ws = rc.workspace(rc.rc_workspace_size(h, opts))
+    stream = torch.cuda.current_stream()
+
+    def step(collect):
+        t = rc.rc_check(h, opts, ws, stream)
+        st = rc.rc_ticket_stage_times(t) if collect else None
+        res = rc.rc_report(t)[0]
+        if res.status != rc.RC_OK:
+            raise RuntimeError(f"check failed: {rc.rc_status_str(res.status)}")
+        return res, st
+
+    for _ in range(max(3, args.warmup)):
+        res, _ = step(False)
+    instances = res.instances
+
+    sampler = ClockSampler(gpu_index(local))
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stages = []
+    for _ in range(args.steps):
+        _, st = step(True)
+        stages.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t_max = elapsed_ms
+    total_inst = instances * args.steps
+    if dist:
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ti = torch.tensor([total_inst], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
+        total_inst = float(ti.item())
+    value = total_inst / (t_max / 1e3) / 1e9
+
+    # per-stage means and the roofline of the dominant kernel
+    n_keys = stages[0]["n_keys"]
+    n_pass = len(stages[0]["sort_ms"])
+    mean = lambda xs: sum(xs) / len(xs)
+    st_mean = {
+        "expand_ms": mean([s["expand_ms"] for s in stages]),
+        "histogram_ms": mean([s["histogram_ms"] for s in stages]),
+        "sort_pass_ms": [mean([s["sort_ms"][k] for s in stages]) for k in range(n_pass)],
+        "scan_ms": mean([s["scan_ms"] for s in stages]),
+        "witness_ms": mean([s["witness_ms"] for s in stages]),
+        "check_ms": mean([s["total_ms"] for s in stages]),
+    }
+    pass_ms = mean(st_mean["sort_pass_ms"]) if n_pass else float("nan")
+    totals = {"onesweep": sum(st_mean["sort_pass_ms"]), "expand": st_mean["expand_ms"],
+              "histogram": st_mean["histogram_ms"], "scan": st_mean["scan_ms"]}
+    dominant = max(totals, key=totals.get)
+    peak, peak_kind = load_peaks()
+    # algorithmic bytes per launch: onesweep pass reads and writes every key once (16 B/key)
+    per_launch = {"onesweep": (16.0 * n_keys, pass_ms), "expand": (8.0 * n_keys, st_mean["expand_ms"]),
+                  "histogram": (8.0 * n_keys, st_mean["histogram_ms"]), "scan": (8.0 * n_keys, st_mean["scan_ms"])}
+    alg_bytes, dur_ms = per_launch[dominant]
+    achieved = alg_bytes / (dur_ms / 1e3) / 1e9
+    tpk = ncu_traffic_per_key() if dominant == "onesweep" else None
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "alg_bytes_per_launch": alg_bytes, "launch_ms": dur_ms,
+                "traffic": (tpk * n_keys) if tpk is not None else None}
+    pipeline_bytes = (8 + 8 + 16 * n_pass + 8) * n_keys
+    pipeline = {"alg_bytes_per_key": 8 + 8 + 16 * n_pass + 8,
+                "gbs": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9,
+                "frac": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9 / peak}
+
+    # end to end through the public calls from host descriptors
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 10))
+        for _ in range(n_e2e):
+            hm = rc.rc_model_create(model)          # host lowering + upload of the program
+            t = rc.rc_check(hm, {"digit_bits": args.digit_bits}, ws, stream)
+            r = rc.rc_report(t)[0]                  # device-to-host copy of the result record
+            assert r.status == rc.RC_OK
+            hm.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e_val = instances * n_e2e / dt / 1e9
+        if dist:
+            te = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e_val = instances * world * n_e2e / float(te.item()) / 1e9
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(lay["program_bytes"]),
+               "d2h_bytes_per_step": 256, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, _ = oracle_rate(args.seed, CPU_SAMPLE_BLOCKS)
+        cpu = {"value": n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"same generator and seed with {CPU_SAMPLE_BLOCKS} of the 4096 blocks "
+                         f"({n} instances, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.blocks == 4096 else WORKLOAD.replace("4096 blocks", f"{args.blocks} blocks"),
+                       "seed": args.seed, "instances_per_rank": instances,
+                       "keys": n_keys, "sort_bits": lay["sort_hi"] - lay["sort_lo"], "sort_passes": n_pass,
+                       "path": "sort", "l2": "inputs larger than L2 (key buffers ~9 GB)",
+                       "parallelism": f"independent models per rank x{world}"},
+            "roofline": roofline, "pipeline": pipeline, "stages_ms": st_mean,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": (10 + n_pass) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--blocks", type=int, default=4096,
+                    help="blocks of the model (4096 = the full workload; fewer only for profiling)")
+    ap.add_argument("--digit-bits", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -176,6 +176,7 @@ typedef struct rc_layout {
   uint32_t n_arrays;
   uint32_t n_threads_per_block;
   uint64_t n_blocks;
+  uint64_t program_bytes;    /* bytes of the lowered program uploaded by rc_model_create */
   uint64_t array_base[64];   /* first linear cell of each array (first 64 arrays) */
   uint64_t array_cells[64];  /* cells of one scope instance of each array         */
 } rc_layout;
@@ -195,9 +196,14 @@ typedef struct rc_check_opts {
                               look-back wait for a status nothing publishes, so the
                               bounded wait runs out and the check reports
                               RC_E_TIMEOUT (exercises the timeout path)           */
+  uint32_t flags;          /* RC_OPT_* bits                                       */
+  uint32_t reserved;
   uint64_t spin_limit;     /* iterations of every bounded device wait, 0 = default */
 } rc_check_opts;
 enum { RC_TEST_STALL_LOOKBACK = 1 };
+/* RC_OPT_STAGE_TIMES: record CUDA events between the stages of rc_check on its
+ * stream so rc_ticket_stage_times can report per-stage device times. */
+enum { RC_OPT_STAGE_TIMES = 1 };
 
 typedef struct rc_inst {
   uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
@@ -256,6 +262,23 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
  * return the ticket is released.  The return value is RC_OK when the results
  * were produced; each record's own status tells how its check went. */
 rc_status rc_report(rc_ticket ticket, rc_result* out, int wait);
+
+/* Per-stage device times of a check enqueued with RC_OPT_STAGE_TIMES, in
+ * milliseconds between events recorded on the check's stream.  Call after the
+ * work completed (e.g. rc_report(wait=0) no longer returns RC_E_NOT_READY is
+ * not required: this call waits) and before rc_report releases the ticket.
+ * Errors: RC_E_INVALID (no stage times were recorded), RC_E_CUDA. */
+typedef struct rc_stage_times {
+  float expand_ms;         /* K1 expansion                                         */
+  float histogram_ms;      /* digit histograms + digit offsets                     */
+  float sort_ms[16];       /* K2 onesweep, one entry per pass                      */
+  uint32_t n_sort_passes;
+  float scan_ms;           /* K3 scan + fold                                       */
+  float witness_ms;        /* K4 witness                                           */
+  float total_ms;          /* from the first to the last event                     */
+  uint64_t n_keys;         /* keys sorted and scanned                              */
+} rc_stage_times;
+rc_status rc_ticket_stage_times(rc_ticket ticket, rc_stage_times* out);
 
 /* ------------------------------------------------------------------------- */
 /* stage entry points (the hot path one kernel family at a time)              */

@@ -37,11 +37,12 @@ RC_SCOPE_GLOBAL, RC_SCOPE_SHARED = 0, 1
 RC_READ, RC_WRITE = 0, 1
 RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
 RC_TEST_STALL_LOOKBACK = 1
+RC_OPT_STAGE_TIMES = 1
 
 # every entry point declared in include/rc.h
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
-           "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys"]
+           "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times"]
 
 
 class RcError(RuntimeError):
@@ -100,12 +101,19 @@ class rc_layout(Structure):
                 ("cell_bits", c_uint32), ("sort_lo", c_uint32), ("sort_hi", c_uint32),
                 ("key_slots", c_uint64), ("total_cells", c_uint64), ("n_arrays", c_uint32),
                 ("n_threads_per_block", c_uint32), ("n_blocks", c_uint64),
-                ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
+                ("program_bytes", c_uint64), ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
 
 
 class rc_check_opts(Structure):
     _fields_ = [("path", c_uint32), ("digit_bits", c_uint32), ("early_exit", c_uint32),
-                ("test_flags", c_uint32), ("spin_limit", c_uint64)]
+                ("test_flags", c_uint32), ("flags", c_uint32), ("reserved", c_uint32),
+                ("spin_limit", c_uint64)]
+
+
+class rc_stage_times(Structure):
+    _fields_ = [("expand_ms", ctypes.c_float), ("histogram_ms", ctypes.c_float),
+                ("sort_ms", ctypes.c_float * 16), ("n_sort_passes", c_uint32), ("scan_ms", ctypes.c_float),
+                ("witness_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("n_keys", c_uint64)]
 
 
 class rc_inst(Structure):
@@ -168,6 +176,8 @@ def load():
         lib.rc_sort_keys.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p,
                                      c_size_t, c_void_p]
         lib.rc_sort_keys.restype = c_int
+        lib.rc_ticket_stage_times.argtypes = [c_void_p, POINTER(rc_stage_times)]
+        lib.rc_ticket_stage_times.restype = c_int
         _lib = lib
         return lib
 
@@ -460,6 +470,19 @@ def rc_report(ticket, wait: bool = True) -> List[Result]:
     if st != RC_OK:
         raise RcError(st, "rc_report")
     return [_result(out[i]) for i in range(n)]
+
+
+def rc_ticket_stage_times(ticket) -> dict:
+    """Per-stage device milliseconds of a check enqueued with RC_OPT_STAGE_TIMES
+    (call before rc_report)."""
+    t, _ = ticket
+    st_ = rc_stage_times()
+    st = load().rc_ticket_stage_times(c_void_p(t), ctypes.byref(st_))
+    if st != RC_OK:
+        raise RcError(st, "rc_ticket_stage_times")
+    return {"expand_ms": st_.expand_ms, "histogram_ms": st_.histogram_ms,
+            "sort_ms": [st_.sort_ms[i] for i in range(st_.n_sort_passes)], "scan_ms": st_.scan_ms,
+            "witness_ms": st_.witness_ms, "total_ms": st_.total_ms, "n_keys": st_.n_keys}
 
 
 def rc_expand_keys(m: RcModel, workspace, keys, count, stream=None):

@@ -20,7 +20,27 @@ struct rc_model {
   rc::Model m;
 };
 
+// Events recorded between the stages of one check (RC_OPT_STAGE_TIMES).
+struct StageTimer {
+  static constexpr int kMax = 24;
+  cudaEvent_t ev[kMax] = {};
+  int n = 0;
+  cudaStream_t st = nullptr;
+  bool ok = true;
+  void mark() {
+    if (n >= kMax) { ok = false; return; }
+    if (!ev[n] && cudaEventCreate(&ev[n]) != cudaSuccess) { ok = false; return; }
+    if (cudaEventRecord(ev[n], st) != cudaSuccess) ok = false;
+    ++n;
+  }
+};
+
 struct rc_ticket_s {
+  StageTimer timer;
+  bool timed = false;
+  int i_start = 0, i_expand = 0, i_hist = 0, i_pass0 = 0, i_scan = 0, i_wit = 0;
+  uint32_t n_pass = 0;
+  uint64_t n_keys = 0;
   cudaEvent_t done = nullptr;
   rc::DevResult* host = nullptr;   // pinned, `cap` records
   size_t cap = 0;
@@ -44,6 +64,9 @@ rc_ticket_s* ticket_get(size_t n) {
         t->n = n;
         t->models.assign(n, nullptr);
         t->enqueue_status = RC_OK;
+        t->timed = false;
+        t->timer.n = 0;
+        t->timer.ok = true;
         return t;
       }
     }
@@ -69,6 +92,8 @@ void ticket_put(rc_ticket_s* t) {
     g_pool.push_back(t);
   } else {
     cudaEventDestroy(t->done);
+    for (auto& e : t->timer.ev)
+      if (e) cudaEventDestroy(e);
     cudaFreeHost(t->host);
     delete t;
   }
@@ -148,7 +173,8 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
 // Enqueue the sort of p.n_keys keys from buffer 0; returns the index of the
 // buffer holding the sorted keys.
 rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, uint64_t* buf1,
-                       uint64_t spin_limit, uint32_t test_flags, cudaStream_t st, int* sorted_buf) {
+                       uint64_t spin_limit, uint32_t test_flags, cudaStream_t st, int* sorted_buf,
+                       StageTimer* tm = nullptr) {
   uint64_t* bufs[2] = {buf0, buf1};
   auto* hist = reinterpret_cast<unsigned long long*>(ws + p.hist_off);
   auto* digoff = reinterpret_cast<unsigned long long*>(ws + p.digoff_off);
@@ -157,6 +183,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
   if (s != RC_OK) return s;
   s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort.n_pass, st));
   if (s != RC_OK) return s;
+  if (tm) tm->mark();
   int cur = 0;
   for (uint32_t k = 0; k < p.sort.n_pass; ++k) {
     rc::SortArgs a;
@@ -175,6 +202,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
     a.err = &res->err;
     s = cuda_status(rc::launch_onesweep(a, st));
     if (s != RC_OK) return s;
+    if (tm) tm->mark();
     cur = 1 - cur;
   }
   *sorted_buf = cur;
@@ -182,33 +210,51 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
 }
 
 rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
-                        cudaStream_t st, rc::DevResult* host_out) {
+                        cudaStream_t st, rc::DevResult* host_out, rc_ticket_s* timed = nullptr) {
   const rc::Model& m = model->m;
   rc::WorkspacePlan p;
   rc::plan_workspace(m, opts ? opts->digit_bits : 0, &p);
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
-  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 22);
+  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
   auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  StageTimer* tm = nullptr;
+  if (timed) {
+    tm = &timed->timer;
+    tm->st = st;
+    tm->n = 0;
+    tm->ok = true;
+    timed->timed = true;
+    timed->n_pass = p.sort.n_pass;
+    timed->n_keys = p.n_keys;
+  }
   rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
   if (s != RC_OK) return s;
   s = cuda_status(rc::launch_init_result(res, st));
   if (s != RC_OK) return s;
+  if (tm) { timed->i_start = tm->n; tm->mark(); }
   const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
   s = cuda_status(rc::launch_expand(dm, (uint64_t)m.host.n_stmts * m.host.n_threads,
                                     reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
   if (s != RC_OK) return s;
+  if (tm) { timed->i_expand = tm->n; tm->mark(); }
   int sorted = 0;
+  if (tm) { timed->i_hist = tm->n; timed->i_pass0 = tm->n + 1; }
   s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
                    reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin,
-                   opts ? opts->test_flags : 0u, st, &sorted);
+                   opts ? opts->test_flags : 0u, st, &sorted, tm);
   if (s != RC_OK) return s;
   if (p.n_keys > 0) {
     rc::ScanArgs sa = scan_args(m, p, ws, sorted);
     s = cuda_status(rc::launch_scan(sa, st));
     if (s != RC_OK) return s;
+    if (tm) { timed->i_scan = tm->n; tm->mark(); }
     s = cuda_status(rc::launch_witness(sa, st));
     if (s != RC_OK) return s;
+    if (tm) { timed->i_wit = tm->n; tm->mark(); }
+  } else if (tm) {
+    timed->i_scan = tm->n; tm->mark();
+    timed->i_wit = tm->n; tm->mark();
   }
   if (host_out) {
     s = cuda_status(cudaMemcpyAsync(host_out, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
@@ -391,6 +437,7 @@ rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
   out->n_arrays = (uint32_t)m.array_base.size();
   out->n_threads_per_block = m.host.bs;
   out->n_blocks = m.host.n_blocks;
+  out->program_bytes = m.dev_bytes;
   for (size_t a = 0; a < m.array_base.size() && a < 64; ++a) {
     out->array_base[a] = m.array_base[a];
     out->array_cells[a] = m.array_cells[a];
@@ -413,7 +460,9 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   rc_ticket_s* t = ticket_get(1);
   if (!t) return RC_E_NOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc_status s = enqueue_check(m, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host);
+  const bool want_times = opts && (opts->flags & RC_OPT_STAGE_TIMES);
+  rc_status s = enqueue_check(m, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host,
+                              want_times ? t : nullptr);
   if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
   if (s != RC_OK) {
     ticket_put(t);
@@ -480,6 +529,30 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
   return RC_OK;
 }
 
+rc_status rc_ticket_stage_times(rc_ticket t, rc_stage_times* out) {
+  if (!t || !out || !t->timed || !t->timer.ok) return RC_E_INVALID;
+  if (cudaEventSynchronize(t->done) != cudaSuccess) return RC_E_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  auto ms = [&](int a, int b) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, t->timer.ev[a], t->timer.ev[b]);
+    return v;
+  };
+  out->expand_ms = ms(t->i_start, t->i_expand);
+  out->histogram_ms = ms(t->i_expand, t->i_hist);
+  out->n_sort_passes = t->n_pass;
+  int prev = t->i_hist;
+  for (uint32_t k = 0; k < t->n_pass && k < 16; ++k) {
+    out->sort_ms[k] = ms(prev, t->i_pass0 + (int)k);
+    prev = t->i_pass0 + (int)k;
+  }
+  out->scan_ms = ms(prev, t->i_scan);
+  out->witness_ms = ms(t->i_scan, t->i_wit);
+  out->total_ms = ms(t->i_start, t->i_wit);
+  out->n_keys = t->n_keys;
+  return RC_OK;
+}
+
 rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_t* keys_dev, uint64_t* count_dev,
                          void* stream) {
   if (!mm || !keys_dev || !count_dev) return RC_E_INVALID;
@@ -515,7 +588,7 @@ rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes)
 
 rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t lo_bit, uint32_t hi_bit,
                        uint32_t digit_bits, void* workspace, size_t ws_bytes, void* stream) {
-  if (hi_bit > 64 || lo_bit > hi_bit || (n && (!keys_in || !keys_out)) || keys_in == keys_out) return RC_E_INVALID;
+  if (hi_bit > 64 || lo_bit > hi_bit || (n && (!keys_in || !keys_out || keys_in == keys_out))) return RC_E_INVALID;
   size_t need;
   rc_sort_workspace_size(n, digit_bits, &need);
   uint8_t* ws = static_cast<uint8_t*>(workspace);
@@ -552,7 +625,7 @@ rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, 
   s = cuda_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st));
   if (s != RC_OK) return s;
   int sorted = 0;
-  s = enqueue_sort(p, ws, keys_out, reinterpret_cast<uint64_t*>(ws + pong), 1ull << 22, 0u, st, &sorted);
+  s = enqueue_sort(p, ws, keys_out, reinterpret_cast<uint64_t*>(ws + pong), 1ull << 20, 0u, st, &sorted);
   if (s != RC_OK) return s;
   if (sorted == 1) s = cuda_status(cudaMemcpyAsync(keys_out, ws + pong, n * 8, cudaMemcpyDeviceToDevice, st));
   return s;
