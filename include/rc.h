@@ -301,6 +301,29 @@ rc_status rc_sort_keys(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint
                        uint32_t lo_bit, uint32_t hi_bit, uint32_t digit_bits,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* The same sort for callers that cannot allocate device memory when they sort:
+ * code whose device memory is entirely reserved up front by another allocator
+ * (a framework's caching allocator or a fixed pool), or whose hot path must
+ * not pay the latency and synchronisation of cudaMalloc / cudaFree.  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * The scratch (histograms, look-back words, second key buffer) lives in one
+ * static device array of this library sized for RC_SORT_STATIC_MAX_KEYS keys
+ * (about 8.6 MB); every GPU that loads the library holds it until the process
+ * exits.  The call allocates nothing and calls no allocating routine; the
+ * caller still passes the input and output buffers (device, n uint64 keys
+ * each, distinct).  n > RC_SORT_STATIC_MAX_KEYS returns RC_E_UNSUPPORTED.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array, which
+ * keeps the last call's contents (the counters that must start at zero are
+ * cleared on every call), so calls whose work overlaps on the GPU (different
+ * streams, or host threads on one device) race: serialise them.
+ * Errors: RC_E_INVALID, RC_E_UNSUPPORTED, RC_E_CUDA. */
+#define RC_SORT_STATIC_MAX_KEYS (1u << 20)
+rc_status rc_sort_keys_static(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint64_t n,
+                              uint32_t lo_bit, uint32_t hi_bit, uint32_t digit_bits, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

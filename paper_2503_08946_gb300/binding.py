@@ -42,7 +42,9 @@ RC_OPT_STAGE_TIMES = 1
 # every entry point declared in include/rc.h
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
-           "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times"]
+           "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times",
+           "rc_sort_keys_static"]
+RC_SORT_STATIC_MAX_KEYS = 1 << 20
 
 
 class RcError(RuntimeError):
@@ -176,6 +178,8 @@ def load():
         lib.rc_sort_keys.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p,
                                      c_size_t, c_void_p]
         lib.rc_sort_keys.restype = c_int
+        lib.rc_sort_keys_static.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p]
+        lib.rc_sort_keys_static.restype = c_int
         lib.rc_ticket_stage_times.argtypes = [c_void_p, POINTER(rc_stage_times)]
         lib.rc_ticket_stage_times.restype = c_int
         _lib = lib
@@ -508,6 +512,17 @@ def rc_sort_keys(keys_in, keys_out, n: int, lo_bit: int, hi_bit: int, digit_bits
                              c_size_t(ws_bytes), c_void_p(_stream(stream)))
     if st != RC_OK:
         raise RcError(st, "rc_sort_keys")
+
+
+def rc_sort_keys_static(keys_in, keys_out, n: int, lo_bit: int, hi_bit: int, digit_bits: int, stream=None):
+    """rc_sort_keys without a workspace: the scratch is the library's static device
+    array (at most RC_SORT_STATIC_MAX_KEYS keys), for callers that cannot allocate
+    device memory when they sort.  Calls that overlap on the GPU race."""
+    st = load().rc_sort_keys_static(c_void_p(_ptr(keys_in)), c_void_p(_ptr(keys_out)), c_uint64(n),
+                                    c_uint32(lo_bit), c_uint32(hi_bit), c_uint32(digit_bits),
+                                    c_void_p(_stream(stream)))
+    if st != RC_OK:
+        raise RcError(st, "rc_sort_keys_static")
 
 
 # ---------------------------------------------------------------------------
