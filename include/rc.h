@@ -200,7 +200,8 @@ typedef struct rc_check_opts {
   uint32_t reserved;
   uint64_t spin_limit;     /* iterations of every bounded device wait, 0 = default */
 } rc_check_opts;
-enum { RC_TEST_STALL_LOOKBACK = 1 };
+enum { RC_TEST_STALL_LOOKBACK = 1,
+       RC_TEST_FEW_SCAN_WARPS = 2   /* scan with 3 warps (long ranges per warp) */ };
 /* RC_OPT_STAGE_TIMES: record CUDA events between the stages of rc_check on its
  * stream so rc_ticket_stage_times can report per-stage device times. */
 enum { RC_OPT_STAGE_TIMES = 1 };

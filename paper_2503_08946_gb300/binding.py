@@ -37,6 +37,7 @@ RC_SCOPE_GLOBAL, RC_SCOPE_SHARED = 0, 1
 RC_READ, RC_WRITE = 0, 1
 RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
 RC_TEST_STALL_LOOKBACK = 1
+RC_TEST_FEW_SCAN_WARPS = 2
 RC_OPT_STAGE_TIMES = 1
 
 # every entry point declared in include/rc.h

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CUDA_SOURCES = ["expand.cu", "sort.cu", "scan.cu", "runtime.cu", "sort_static.cu"]
+CUDA_SOURCES = ["expand.cu", "sort.cu", "scan.cu", "runtime.cu", "sort_static.cu", "hash.cu"]
 HOST_SOURCES = ["lower.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -9,61 +9,56 @@
 // write their keys contiguously at the scanned unit offsets.
 #include <cuda_runtime.h>
 
-#include "device_common.cuh"
+#include "expand_core.cuh"
 #include "kernels.h"
 
 namespace rc {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// Sort-path sink: keys go to their slot; guard-false dense slots get padding.
+struct SlotSink {
+  uint64_t* keys;
+  __device__ __forceinline__ void put(uint64_t i, uint64_t key) { keys[i] = key; }
+  __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
+};
+
+// grid: (ceil(T / kExpandThreads), n_stmts); one statement per grid row.
+// Statements with at most kFastLoops loops.
+__global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevModel* __restrict__ Mp,
+                                                                uint64_t* __restrict__ keys, DevResult* res) {
+  __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
+  __shared__ int64_t s_cache[kFastCache * kExpandThreads];
+  const DevModel& M = *Mp;
+  const uint32_t s = blockIdx.y;
+  const DevStmt& S = M.stmts[s];
+  if (S.n_loops > kFastLoops) return;
+  const uint64_t g = (uint64_t)blockIdx.x * kExpandThreads + threadIdx.x;
+  unsigned long long count = 0;
+  if (g < M.n_threads) {
+    FastCtx c;
+    c.M = Mp;
+    c.S = &S;
+    c.tv = thread_vars(M, g);
+    c.tval = s_tval + threadIdx.x;
+    c.cache = s_cache + threadIdx.x;
+    SlotSink sink{keys};
+    expand_unit_dispatch(c, s, g, res, count, sink);
+  }
+  count = warp_sum(count);
+  if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
 }
 
-__global__ void __launch_bounds__(256) expand_kernel(const DevModel* __restrict__ Mp, uint64_t n_units,
-                                                     uint64_t* __restrict__ keys, DevResult* res) {
+// Statements with more than kFastLoops loops: interpreted nest.
+__global__ void __launch_bounds__(kExpandThreads) expand_generic_kernel(const DevModel* __restrict__ Mp,
+                                                                        uint64_t* __restrict__ keys, DevResult* res) {
   const DevModel& M = *Mp;
-  const uint64_t T = M.n_threads;
+  const uint32_t s = blockIdx.y;
+  if (M.stmts[s].n_loops <= kFastLoops) return;
+  const uint64_t g = (uint64_t)blockIdx.x * kExpandThreads + threadIdx.x;
   unsigned long long count = 0;
-  for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n_units;
-       u += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t s = (uint32_t)(u / T);
-    const uint64_t g = u - (uint64_t)s * T;
-    const DevStmt& S = M.stmts[s];
-    const ThreadVars tv = thread_vars(M, g);
-    if (S.dense) {
-      uint64_t j = 0;
-      const uint64_t stride = T;
-      walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
-        uint64_t slot = S.slot_base + j * (uint64_t)S.n_acc * stride + g;
-        if (guards_hold(M, S, tv, it, term)) {
-          const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
-          for (int a = 0; a < S.n_acc; ++a) {
-            keys[slot] = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
-            slot += stride;
-          }
-          count += (unsigned long long)S.n_acc;
-        } else {
-          for (int a = 0; a < S.n_acc; ++a) {
-            keys[slot] = kSentinel;
-            slot += stride;
-          }
-        }
-        ++j;
-      });
-    } else {
-      uint64_t off = M.unit_offset[S.slot_base + g];
-      walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
-        if (!guards_hold(M, S, tv, it, term)) return;
-        const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
-        for (int a = 0; a < S.n_acc; ++a)
-          keys[off++] = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
-        count += (unsigned long long)S.n_acc;
-      });
-    }
-  }
+  SlotSink sink{keys};
+  if (g < M.n_threads) expand_unit_generic(M, s, g, res, count, sink);
   count = warp_sum(count);
   if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
 }
@@ -173,11 +168,18 @@ int grid_for(uint64_t n_units) {
 
 }  // namespace
 
-cudaError_t launch_expand(const DevModel* dm, uint64_t n_units, uint64_t* keys, DevResult* res,
-                          cudaStream_t st) {
-  if (n_units == 0) return cudaSuccess;
-  expand_kernel<<<grid_for(n_units), 256, 0, st>>>(dm, n_units, keys, res);
-  return cudaGetLastError();
+cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
+                          DevResult* res, cudaStream_t st) {
+  if (n_stmts == 0 || n_threads == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n_threads + kExpandThreads - 1) / kExpandThreads), n_stmts);
+  expand_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (has_deep) {
+    expand_generic_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st) {

@@ -8,12 +8,29 @@
 namespace rc {
 
 // expand.cu
-cudaError_t launch_expand(const DevModel* dm, uint64_t n_units, uint64_t* keys, DevResult* res,
-                          cudaStream_t st);
+// has_deep: some statement has more than kFastLoops loops (runs the generic kernel too)
+cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
+                          DevResult* res, cudaStream_t st);
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st);
 size_t scan_u64_temp_bytes(uint64_t n);
 cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,
                                uint64_t* total_dev, cudaStream_t st);
+
+// hash.cu
+struct HashArgs {
+  unsigned long long* gkey;    // group table keys (cell, phase), kEmpty = free
+  unsigned long long* gword;
+  unsigned long long* ckey;    // cell table keys
+  unsigned long long* cword;
+  uint64_t gmask, cmask;       // table sizes - 1 (powers of two)
+  DevResult* res;
+  unsigned int early_exit;
+  unsigned int* stop;
+  uint64_t* filtered;          // keys of the smallest racy cell
+  unsigned long long* n_filtered;
+};
+cudaError_t launch_hash(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, const HashArgs& h,
+                        cudaStream_t st);
 
 // sort.cu
 constexpr int kSortThreads = 256;
@@ -42,14 +59,15 @@ cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t st);
 size_t sort_workspace_bytes(uint64_t n, uint32_t n_pass);
 
 // scan.cu
+constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)
+constexpr uint32_t kScanMaxWarps = 152 * 12 * 4;
 struct ScanArgs {
   const uint64_t* keys;
   uint64_t n;
   uint32_t cell_shift, phase_shift, block_shift, thread_shift;
   uint32_t phase_bits, block_bits, thread_bits;
-  Summary* summaries;
+  Summary* summaries;     // one per warp
   uint32_t n_warps;
-  uint64_t per_warp;
   DevResult* res;
   unsigned int* groups;   // (1 << phase_bits) x 5 words for the witness
 };

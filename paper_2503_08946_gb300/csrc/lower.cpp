@@ -164,8 +164,10 @@ struct StmtBuilder {
   }
 };
 
-void put_row(const Lin& l, std::vector<Row>* rows, std::vector<LinTerm>* lin) {
+void put_row(const Lin& l, std::vector<Row>* rows, std::vector<LinTerm>* lin, int level = 0) {
   Row r;
+  r.level = level;
+  r.cache = -1;
   r.c0 = l.c0;
   for (int i = 0; i < 6; ++i) r.ct[i] = l.ct[i];
   r.off = (int32_t)lin->size();
@@ -300,6 +302,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
       D.step[l] = S.loops[l].step;
     }
     int nl = (int)S.n_loops;
+    if (nl > kFastLoops) m->has_deep_loops = true;
     for (uint32_t g = 0; g < S.n_guards; ++g)
       if (!b.compile(S.guards[g], nl, &guards[g])) return b.err;
     if (!b.compile(S.phase, nl, &phase)) return b.err;
@@ -318,13 +321,21 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     D.n_guards = (int32_t)S.n_guards;
     D.n_acc = (int32_t)S.n_accesses;
     for (int l = 0; l < nl; ++l) {
-      D.row_lower[l] = (int32_t)rows.size(); put_row(lo[l], &rows, &lin);
-      D.row_upper[l] = (int32_t)rows.size(); put_row(hi[l], &rows, &lin);
+      D.row_lower[l] = (int32_t)rows.size(); put_row(lo[l], &rows, &lin, b.level_of(lo[l]));
+      D.row_upper[l] = (int32_t)rows.size(); put_row(hi[l], &rows, &lin, b.level_of(hi[l]));
     }
+    // rows evaluated at every point: guards, phase, indices; the thread-constant
+    // ones (level 0) get a per-thread cache slot
+    int n_cache = 0;
+    auto put_point_row = [&](const Lin& e) {
+      const int lev = b.level_of(e);
+      put_row(e, &rows, &lin, lev);
+      if (lev == 0 && n_cache < kFastCache) rows.back().cache = n_cache++;
+    };
     D.guard_row0 = (int32_t)rows.size();
-    for (auto& g : guards) put_row(g, &rows, &lin);
+    for (auto& g : guards) put_point_row(g);
     D.row_phase = (int32_t)rows.size();
-    put_row(phase, &rows, &lin);
+    put_point_row(phase);
     D.acc0 = (int32_t)accs.size();
     for (uint32_t a = 0; a < S.n_accesses; ++a) {
       DevAccess da;
@@ -332,19 +343,21 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
       da.kind = (int32_t)S.accesses[a].kind;
       da.ndims = (int32_t)idx[a].size();
       da.row0 = (int32_t)rows.size();
-      for (auto& e : idx[a]) put_row(e, &rows, &lin);
+      for (auto& e : idx[a]) put_point_row(e);
       accs.push_back(da);
     }
+    D.n_cache = n_cache;
     D.term0 = (int32_t)terms.size();
     D.n_terms = (int32_t)b.terms.size();
     for (size_t q = 0; q < b.terms.size(); ++q) {
       Term t;
       t.row = (int32_t)rows.size();
-      put_row(b.terms[q].inner, &rows, &lin);
+      put_row(b.terms[q].inner, &rows, &lin, b.term_level[q]);
       t.op = b.terms[q].op;
       t.d = b.terms[q].d;
       t.level = b.term_level[q];
       t.pad = 0;
+      t.magic = fastdiv_magic(t.d);
       terms.push_back(t);
     }
     D.dense = dense ? 1 : 0;

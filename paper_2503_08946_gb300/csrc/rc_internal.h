@@ -25,6 +25,8 @@ constexpr int kMaxDims = 4;
 constexpr int kMaxPhaseBits = 16;
 constexpr int kKeyBits = 63;      // bit 63 is reserved so 0xFFFF...FFFF is never a valid key
 constexpr uint64_t kSentinel = ~0ull;
+constexpr int kFastCache = 16;    // per-thread cached thread-constant rows per statement
+constexpr int kFastLoops = 4;     // loop depth of the compile-time loop nests of the expansion
 
 // ---------------------------------------------------------------------------
 // lowered program
@@ -50,6 +52,8 @@ struct Row {
   int64_t ct[6];
   int32_t off;   // first LinTerm of this row in the model's pool
   int32_t nnz;
+  int32_t level; // loop levels whose iterators it needs (0 = constant per thread)
+  int32_t cache; // slot of its per-thread cached value when level == 0 and used per point, else -1
 };
 
 enum TermOp : int32_t { kFdiv = 0, kMod = 1 };
@@ -60,6 +64,7 @@ struct Term {
   int64_t d;
   int32_t level;   // iterators 0..level-1 must be bound
   int32_t pad;
+  uint64_t magic;  // ceil(2^64 / d) for the multiply-high division (d >= 2), 0 for d == 1
 };
 
 struct DevAccess {
@@ -87,7 +92,7 @@ struct DevStmt {
   int32_t acc0;         // first DevAccess
   int32_t term0;        // first Term
   int32_t dense;        // 1 = every loop has a constant trip count
-  int32_t pad;
+  int32_t n_cache;      // per-thread cached rows (level 0, used at every point)
   int64_t trips[kMaxLoops];
   uint64_t n_iter;      // product of trips (dense)
   uint64_t slot_base;   // dense: first key slot; general: index of its first unit offset
@@ -131,7 +136,10 @@ struct DevResult {
   unsigned int minb, maxb, minWb, maxWb, anyW, err;
   unsigned long long n_keys;       // keys in the sorted buffer
   unsigned long long sorted_buf;   // index (0/1) of the buffer that holds the sorted keys
-  unsigned long long pad[4];
+  unsigned long long hash_cell;    // hash path: smallest racy cell found; ~0 = none
+  unsigned int stop;               // hash path: early-exit flag
+  unsigned int pad0;
+  unsigned long long pad[2];
 };
 static_assert(sizeof(DevResult) <= 256, "result record must fit its slot");
 
@@ -158,6 +166,29 @@ RC_HD int64_t euclid_mod(int64_t a, int64_t d) {
   int64_t r = a % d;
   return r < 0 ? r + d : r;
 }
+// Floor division / Euclidean modulo by a positive invariant divisor using the
+// multiply-high method of Lemire, Kaser and Kurz ("Faster remainder by direct
+// computation", Software: Practice and Experience, 2019): for 0 <= x < 2^32
+// and 2 <= d < 2^32, floor(x / d) = floor(M * x / 2^64) with M = ceil(2^64 / d).
+// Negative numerators use floor(a / d) = -1 - floor((-a - 1) / d).  Values
+// outside [-2^32, 2^32) or divisors >= 2^32 take the plain 64-bit division.
+constexpr int64_t kFastDivLimit = (int64_t)1 << 32;
+inline uint64_t fastdiv_magic(int64_t d) { return d >= 2 && d < kFastDivLimit ? ~0ull / (uint64_t)d + 1 : 0; }
+
+#ifdef __CUDACC__
+__device__ __forceinline__ int64_t fast_floor_div(int64_t a, int64_t d, uint64_t magic) {
+  if (d == 1) return a;
+  if (magic != 0 && a >= -kFastDivLimit && a < kFastDivLimit) {
+    if (a >= 0) return (int64_t)__umul64hi(magic, (uint64_t)a);
+    return -1 - (int64_t)__umul64hi(magic, (uint64_t)(-a - 1));
+  }
+  return floor_div(a, d);
+}
+__device__ __forceinline__ int64_t fast_euclid_mod(int64_t a, int64_t d, uint64_t magic) {
+  return a - fast_floor_div(a, d, magic) * d;
+}
+#endif
+
 RC_HD int64_t wadd(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
 RC_HD int64_t wmul(int64_t a, int64_t b) { return (int64_t)((uint64_t)a * (uint64_t)b); }
 
@@ -326,6 +357,10 @@ struct WorkspacePlan {
   uint64_t n_tiles;
   uint32_t scan_warps;
   SortPlan sort;
+  // hash path
+  bool hash;
+  uint64_t hash_cap;      // slots per table (power of two)
+  size_t gkey_off, gword_off, ckey_off, cword_off, filt_off, nfilt_off;
 };
 
 struct Model {
@@ -338,12 +373,13 @@ struct Model {
   std::vector<uint64_t> array_base, array_cells;
   std::vector<uint32_t> array_shared;
   uint32_t n_general_stmts = 0;
+  bool has_deep_loops = false;    // some statement has more than kFastLoops loops
   uint64_t max_iter_per_unit = 0;
 };
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);
-void plan_workspace(const Model& m, uint32_t digit_bits, WorkspacePlan* p);
+void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p);
 void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp);
 uint32_t bit_length(uint64_t v);
 

@@ -104,8 +104,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 rc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RC_OK : RC_E_CUDA; }
 
 uint32_t scan_warps_for(uint64_t n) {
-  uint64_t w = (n + 2047) / 2048;
-  const uint64_t cap = 152ull * 64;
+  // whole segments of 32 x kScanRun keys per warp, at most kScanMaxWarps warps
+  uint64_t w = (n + 32 * rc::kScanRun - 1) / (32 * rc::kScanRun);
+  const uint64_t cap = rc::kScanMaxWarps;
   if (w > cap) w = cap;
   if (w < 1) w = 1;
   return (uint32_t)w;
@@ -115,11 +116,41 @@ uint32_t scan_warps_for(uint64_t n) {
 
 namespace rc {
 
-void plan_workspace(const Model& m, uint32_t digit_bits, WorkspacePlan* p) {
+// The path a check takes: RC_PATH_HASH on request, otherwise the sort path.
+bool use_hash_path(const Model&, const rc_check_opts* opts) { return opts && opts->path == RC_PATH_HASH; }
+
+void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p) {
   std::memset(p, 0, sizeof(*p));
-  plan_sort(m.host.sort_lo, m.host.sort_hi, digit_bits, &p->sort);
   const uint64_t n = m.key_slots;
   p->n_keys = n;
+  if (use_hash_path(m, opts)) {
+    // tables of at least 1.5x the instances (an upper bound on distinct groups
+    // and cells), the keys of the first racy cell, witness phase groups
+    p->hash = true;
+    uint64_t cap = 1024;
+    while (cap < n + n / 2) cap <<= 1;
+    p->hash_cap = cap;
+    size_t off = 0;
+    p->result_off = off;
+    off = align256(off + sizeof(DevResult));
+    p->gkey_off = off;
+    off = align256(off + cap * 8);
+    p->gword_off = off;
+    off = align256(off + cap * 8);
+    p->ckey_off = off;
+    off = align256(off + cap * 8);
+    p->cword_off = off;
+    off = align256(off + cap * 8);
+    p->filt_off = off;
+    off = align256(off + n * 8);
+    p->nfilt_off = off;
+    off = align256(off + 8);
+    p->group_off = off;
+    off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
+    p->total = off;
+    return;
+  }
+  plan_sort(m.host.sort_lo, m.host.sort_hi, opts ? opts->digit_bits : 0, &p->sort);
   p->n_tiles = (n + kSortTile - 1) / kSortTile;
   p->scan_warps = scan_warps_for(n);
   size_t off = 0;
@@ -139,7 +170,7 @@ void plan_workspace(const Model& m, uint32_t digit_bits, WorkspacePlan* p) {
   p->zero_hi = off;
   p->digoff_off = off;
   off = align256(off + (size_t)16 * kRadix * 8);
-  p->summ_off = off;
+  p->summ_off = off;   // one scan summary per warp
   off = align256(off + (size_t)p->scan_warps * sizeof(Summary));
   p->group_off = off;
   off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
@@ -163,8 +194,6 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.thread_bits = m.host.thread_bits;
   a.summaries = reinterpret_cast<rc::Summary*>(ws + p.summ_off);
   a.n_warps = p.scan_warps;
-  a.per_warp = ((p.n_keys + p.scan_warps - 1) / p.scan_warps + 31) / 32 * 32;
-  if (a.per_warp == 0) a.per_warp = 32;
   a.res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
   a.groups = reinterpret_cast<unsigned int*>(ws + p.group_off);
   return a;
@@ -213,7 +242,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
                         cudaStream_t st, rc::DevResult* host_out, rc_ticket_s* timed = nullptr) {
   const rc::Model& m = model->m;
   rc::WorkspacePlan p;
-  rc::plan_workspace(m, opts ? opts->digit_bits : 0, &p);
+  rc::plan_workspace(m, opts, &p);
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
   const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
@@ -228,13 +257,49 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     timed->n_pass = p.sort.n_pass;
     timed->n_keys = p.n_keys;
   }
-  rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
+  const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
+  rc_status s = cuda_status(rc::launch_init_result(res, st));
   if (s != RC_OK) return s;
-  s = cuda_status(rc::launch_init_result(res, st));
+  if (p.hash) {
+    rc::HashArgs h;
+    h.gkey = reinterpret_cast<unsigned long long*>(ws + p.gkey_off);
+    h.gword = reinterpret_cast<unsigned long long*>(ws + p.gword_off);
+    h.ckey = reinterpret_cast<unsigned long long*>(ws + p.ckey_off);
+    h.cword = reinterpret_cast<unsigned long long*>(ws + p.cword_off);
+    h.gmask = h.cmask = p.hash_cap - 1;
+    h.res = res;
+    h.early_exit = opts && opts->early_exit ? 1u : 0u;
+    h.stop = &res->stop;
+    h.filtered = reinterpret_cast<uint64_t*>(ws + p.filt_off);
+    h.n_filtered = reinterpret_cast<unsigned long long*>(ws + p.nfilt_off);
+    s = cuda_status(cudaMemsetAsync(h.gkey, 0xFF, p.hash_cap * 8, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.ckey, 0xFF, p.hash_cap * 8, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.gword, 0, p.hash_cap * 8, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.cword, 0, p.hash_cap * 8, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.n_filtered, 0, 8, st));
+    if (s != RC_OK) return s;
+    if (tm) { timed->i_start = tm->n; tm->mark(); }
+    s = cuda_status(rc::launch_hash(dm, m.host.n_stmts, m.host.n_threads, h, st));
+    if (s != RC_OK) return s;
+    if (tm) {
+      timed->i_expand = timed->i_hist = timed->i_scan = tm->n;
+      timed->i_pass0 = tm->n;
+      timed->n_pass = 0;
+      tm->mark();
+    }
+    rc::ScanArgs sa = scan_args(m, p, ws, 0);
+    sa.keys = h.filtered;
+    s = cuda_status(rc::launch_witness(sa, st));
+    if (s != RC_OK) return s;
+    if (tm) { timed->i_wit = tm->n; tm->mark(); }
+    if (host_out)
+      s = cuda_status(cudaMemcpyAsync(host_out, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+    return s;
+  }
+  s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
   if (s != RC_OK) return s;
   if (tm) { timed->i_start = tm->n; tm->mark(); }
-  const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
-  s = cuda_status(rc::launch_expand(dm, (uint64_t)m.host.n_stmts * m.host.n_threads,
+  s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
                                     reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
   if (s != RC_OK) return s;
   if (tm) { timed->i_expand = tm->n; tm->mark(); }
@@ -246,6 +311,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   if (s != RC_OK) return s;
   if (p.n_keys > 0) {
     rc::ScanArgs sa = scan_args(m, p, ws, sorted);
+    if (opts && (opts->test_flags & RC_TEST_FEW_SCAN_WARPS) && sa.n_warps > 3) sa.n_warps = 3;
     s = cuda_status(rc::launch_scan(sa, st));
     if (s != RC_OK) return s;
     if (tm) { timed->i_scan = tm->n; tm->mark(); }
@@ -268,6 +334,10 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
   out->instances = r.instances;
   if (r.err & rc::kErrLookbackTimeout) {
     out->status = RC_E_TIMEOUT;
+    return;
+  }
+  if (r.err & rc::kErrHashFull) {
+    out->status = RC_E_NOMEM;
     return;
   }
   if (r.oob_code != ~0ull) {
@@ -448,7 +518,7 @@ rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
 rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes) {
   if (!m || !bytes) return RC_E_INVALID;
   rc::WorkspacePlan p;
-  rc::plan_workspace(m->m, opts ? opts->digit_bits : 0, &p);
+  rc::plan_workspace(m->m, opts, &p);
   *bytes = p.total;
   return RC_OK;
 }
@@ -558,7 +628,7 @@ rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_
   if (!mm || !keys_dev || !count_dev) return RC_E_INVALID;
   const rc::Model& m = mm->m;
   rc::WorkspacePlan p;
-  rc::plan_workspace(m, 0, &p);
+  rc::plan_workspace(m, nullptr, &p);
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -566,7 +636,7 @@ rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_
   rc_status s = cuda_status(rc::launch_init_result(res, st));
   if (s != RC_OK) return s;
   s = cuda_status(rc::launch_expand(reinterpret_cast<const rc::DevModel*>(m.dev_program),
-                                    (uint64_t)m.host.n_stmts * m.host.n_threads, keys_dev, res, st));
+                                    m.host.n_stmts, m.host.n_threads, m.has_deep_loops, keys_dev, res, st));
   if (s != RC_OK) return s;
   return cuda_status(cudaMemcpyAsync(count_dev, &res->instances, 8, cudaMemcpyDeviceToDevice, st));
 }

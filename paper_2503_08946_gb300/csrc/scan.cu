@@ -1,4 +1,4 @@
-// K3: segmented scan of the sorted keys -> racy-cell count and first racy cell;
+// K3: scan of the sorted keys -> racy-cell count and first racy cell;
 // K4: witness (smallest racing pair) inside that cell.
 //
 // The paper's RaW / WaW / WaR relations (appendix listing of the dependence
@@ -8,15 +8,16 @@
 // some phase group has two threads and a write) -- the cell-level form of the
 // pair rule in include/rc.h.
 //
-// K3a: each warp walks a contiguous range 32 keys per step.  Cell and
-//      (cell, phase) group boundaries come from ballots of head flags; per-group
-//      min/max thread and min/max block come from redux.sync over the lanes of
-//      the group (__reduce_min/max_sync with the group's lane mask); a warp-
-//      uniform carry holds the group open at the end of a step.  Cells that
-//      close inside the warp's range are counted there; the range's first and
-//      last cell pieces go to a Summary (rc_internal.h).
-// K3b: one block folds the warp summaries in order, finishes the count and the
-//      first racy cell, and finds that cell's end with a 32-way galloping search.
+// K3a: each warp scans a contiguous range of the sorted keys, 32 keys per
+//      lane per segment, staged through shared memory with coalesced loads.  A
+//      lane folds its run in order: keys that continue the cell open before the
+//      run form its prefix piece, cells that begin and end in the run are
+//      counted at once, and the cell open at the run's end is finished by a
+//      segmented suffix scan of the lanes' prefix pieces (5 shuffle rounds).
+//      The warp's first cell and the cell open at its end go to a Summary
+//      (rc_internal.h).
+// K3b: one block folds the warp summaries in order (count, first racy cell);
+//      one warp finds that cell's end with a 32-way galloping search.
 // K4:  four grid-wide reductions over that one segment: the cell summary
 //      (blocks, write blocks), per-phase groups of its lowest block, the
 //      smallest instance that has a partner (x), and x's smallest partner (y).
@@ -32,15 +33,177 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ unsigned lane_range_mask(int lo, int hi) {
-  // lanes lo..hi inclusive (0 <= lo <= hi <= 31)
-  const unsigned upto = hi >= 31 ? FULL : ((2u << hi) - 1u);
-  return upto & ~((1u << lo) - 1u);
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(FULL, v, o);
+    v = y < v ? y : v;
+  }
+  return v;
+}
+
+// 32-way galloping search by one full warp: first position >= start whose key
+// is not in `cell` (keys[start] is in it).
+__device__ uint64_t warp_cell_end(const uint64_t* keys, uint64_t n, uint32_t cs, uint64_t start, uint64_t cell) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = start, stride = 1;
+  while (true) {
+    const uint64_t q = lo + (uint64_t)(lane + 1) * stride;
+    const bool f = q >= n || (keys[q] >> cs) != cell;
+    const unsigned F = __ballot_sync(FULL, f);
+    if (F) {
+      lo += (uint64_t)(__ffs(F) - 1) * stride;
+      break;
+    }
+    lo += 32 * stride;
+    stride *= 32;
+  }
+  // keys[lo] is in the cell and keys[lo + stride] is not (or is past the end)
+  while (stride > 1) {
+    const uint64_t s2 = (stride + 31) / 32;
+    const uint64_t q = lo + (uint64_t)(lane + 1) * s2;
+    const bool f = q >= lo + stride || q >= n || (keys[q] >> cs) != cell;
+    const unsigned F = __ballot_sync(FULL, f);
+    lo += (uint64_t)(__ffs(F) - 1) * s2;
+    stride = s2;
+  }
+  return lo + 1;
+}
+
+// Compact piece of a cell for the lane-level scan: block range, write flag, and
+// the first / last phase group with the OR of the racy groups in between
+// (the same information as CellPiece in rc_internal.h, packed in 8 words).
+struct Piece {
+  unsigned minb, maxb;
+  unsigned flags;     // bit0 anyW, bit1 single group, bit2 inner racy, bit3 fs write, bit4 ls write, bit5 empty
+  unsigned ps;        // first phase | last phase << 16
+  unsigned fs_min, fs_max, ls_min, ls_max;
+};
+constexpr unsigned kPW = 1u, kPSingle = 2u, kPInner = 4u, kPFsW = 8u, kPLsW = 16u, kPEmpty = 32u;
+
+__device__ __forceinline__ Piece piece_empty() {
+  Piece p;
+  p.minb = p.maxb = 0;
+  p.flags = kPEmpty;
+  p.ps = 0;
+  p.fs_min = p.fs_max = p.ls_min = p.ls_max = 0;
+  return p;
+}
+__device__ __forceinline__ void piece_start(Piece& P, unsigned ph, unsigned t, unsigned b, bool w) {
+  P.minb = P.maxb = b;
+  P.flags = kPSingle | (w ? (kPW | kPFsW | kPLsW) : 0u);
+  P.ps = ph | (ph << 16);
+  P.fs_min = P.fs_max = P.ls_min = P.ls_max = t;
+}
+__device__ __forceinline__ bool ls_racy(const Piece& P) { return P.ls_min != P.ls_max && (P.flags & kPLsW); }
+__device__ __forceinline__ bool fs_racy(const Piece& P) { return P.fs_min != P.fs_max && (P.flags & kPFsW); }
+__device__ __forceinline__ bool cpiece_racy(const Piece& P) {
+  if (P.minb != P.maxb) return (P.flags & kPW) != 0;
+  return (P.flags & kPInner) || fs_racy(P) || ls_racy(P);
+}
+// Add one key.  keep_fs: the piece's first group may continue a group on its
+// left, so it is kept apart instead of folding into `inner` when it closes.
+__device__ __forceinline__ void piece_add(Piece& P, unsigned ph, unsigned t, unsigned b, bool w, bool keep_fs) {
+  if (ph != (P.ps >> 16)) {
+    if ((P.flags & kPSingle) && !keep_fs) {
+      if (fs_racy(P)) P.flags |= kPInner;
+      P.fs_min = P.fs_max = 0;
+      P.flags &= ~kPFsW;
+    } else if (!(P.flags & kPSingle) && ls_racy(P)) {
+      P.flags |= kPInner;
+    }
+    P.flags &= ~(kPSingle | kPLsW);
+    P.ps = (P.ps & 0xFFFFu) | (ph << 16);
+    P.ls_min = P.ls_max = t;
+    if (w) P.flags |= kPLsW;
+  } else {
+    P.ls_min = min(P.ls_min, t);
+    P.ls_max = max(P.ls_max, t);
+    if (w) P.flags |= kPLsW;
+    if (P.flags & kPSingle) {
+      P.fs_min = P.ls_min;
+      P.fs_max = P.ls_max;
+      P.flags = (P.flags & ~kPFsW) | ((P.flags & kPLsW) ? kPFsW : 0u);
+    }
+  }
+  P.minb = min(P.minb, b);
+  P.maxb = max(P.maxb, b);
+  if (w) P.flags |= kPW;
+}
+// X then Y, pieces of one cell (either may be empty).
+__device__ __forceinline__ Piece piece_cat(const Piece& X, const Piece& Y) {
+  if (X.flags & kPEmpty) return Y;
+  if (Y.flags & kPEmpty) return X;
+  Piece r;
+  r.minb = min(X.minb, Y.minb);
+  r.maxb = max(X.maxb, Y.maxb);
+  const unsigned xs = X.flags & kPSingle, ys = Y.flags & kPSingle;
+  unsigned inner = ((X.flags | Y.flags) & kPInner);
+  r.ps = (X.ps & 0xFFFFu) | (Y.ps & 0xFFFF0000u);
+  // merged group when X's last group continues into Y's first group
+  const bool join = (X.ps >> 16) == (Y.ps & 0xFFFFu);
+  unsigned m_min = 0, m_max = 0;
+  bool m_w = false;
+  if (join) {
+    m_min = min(X.ls_min, Y.fs_min);
+    m_max = max(X.ls_max, Y.fs_max);
+    m_w = (X.flags & kPLsW) || (Y.flags & kPFsW);
+  }
+  unsigned fsw, lsw;
+  if (join) {
+    if (xs && ys) {
+      r.fs_min = r.ls_min = m_min; r.fs_max = r.ls_max = m_max; fsw = lsw = m_w;
+    } else if (xs) {
+      r.fs_min = m_min; r.fs_max = m_max; fsw = m_w;
+      r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
+    } else if (ys) {
+      r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
+      r.ls_min = m_min; r.ls_max = m_max; lsw = m_w;
+    } else {
+      r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
+      r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
+      if (m_min != m_max && m_w) inner = kPInner;
+    }
+  } else {
+    r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
+    r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
+    if (!xs && ls_racy(X)) inner = kPInner;
+    if (!ys && fs_racy(Y)) inner = kPInner;
+  }
+  const bool single = join && xs && ys;
+  r.flags = ((X.flags | Y.flags) & kPW) | (single ? kPSingle : 0u) | inner | (fsw ? kPFsW : 0u) | (lsw ? kPLsW : 0u);
+  return r;
+}
+
+__device__ __forceinline__ CellPiece to_cellpiece(const Piece& P, uint64_t cell, uint64_t start) {
+  CellPiece c;
+  c.cell = cell;
+  c.start = start;
+  c.minb = P.minb;
+  c.maxb = P.maxb;
+  c.anyW = (P.flags & kPW) ? 1u : 0u;
+  c.first_p = P.ps & 0xFFFFu;
+  c.last_p = P.ps >> 16;
+  c.single_sub = (P.flags & kPSingle) ? 1u : 0u;
+  c.inner = (P.flags & kPInner) ? 1u : 0u;
+  c.pad = 0;
+  c.fs.mint = P.fs_min; c.fs.maxt = P.fs_max; c.fs.anyW = (P.flags & kPFsW) ? 1u : 0u; c.fs.pad = 0;
+  c.ls.mint = P.ls_min; c.ls.maxt = P.ls_max; c.ls.anyW = (P.flags & kPLsW) ? 1u : 0u; c.ls.pad = 0;
+  return c;
 }
 
 template <class T>
-__device__ __forceinline__ T shfl_T(const T& v, int src) {
+__device__ __forceinline__ T shfl_down_T(const T& v, int delta) {
   static_assert(sizeof(T) % 4 == 0, "shuffle of 4-byte words");
+  T r;
+  const unsigned* pv = reinterpret_cast<const unsigned*>(&v);
+  unsigned* pr = reinterpret_cast<unsigned*>(&r);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) pr[i] = __shfl_down_sync(FULL, pv[i], delta);
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T shfl_idx_T(const T& v, int src) {
   T r;
   const unsigned* pv = reinterpret_cast<const unsigned*>(&v);
   unsigned* pr = reinterpret_cast<unsigned*>(&r);
@@ -49,204 +212,192 @@ __device__ __forceinline__ T shfl_T(const T& v, int src) {
   return r;
 }
 
-__device__ __forceinline__ CellPiece piece_none() {
-  CellPiece c;
-  c.cell = 0; c.start = 0; c.minb = 0; c.maxb = 0; c.anyW = 0; c.first_p = 0; c.last_p = 0;
-  c.single_sub = 1; c.inner = 0; c.pad = 0; c.fs = sub_none(); c.ls = sub_none();
-  return c;
-}
+constexpr int kScanWarps = 4;                 // warps per block of scan_runs_kernel
+constexpr int kRunPad = kScanRun + 1;         // padded per-lane stride in shared memory
+constexpr int kSegKeys = 32 * kScanRun;       // keys per warp segment
 
-__global__ void __launch_bounds__(256) scan_warps_kernel(ScanArgs a) {
-  const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= a.n_warps) return;
-  const uint64_t lo = (uint64_t)wid * a.per_warp;
-  const uint64_t hi = lo + a.per_warp < a.n ? lo + a.per_warp : a.n;
-  if (lo >= hi) {
-    if (lane == 0) a.summaries[wid] = summary_empty();
-    return;
-  }
-  const unsigned tmask = (1u << a.thread_bits) - 1u;
-  const unsigned bmask = (1u << a.block_bits) - 1u;
-  const unsigned pmask = (1u << a.phase_bits) - 1u;
-
-  bool have = false;
-  uint64_t prev_key = 0;
-  CellPiece cur = piece_none();
-  bool cur_is_L = false;
-  bool L_done = false;
-  CellPiece Lp = piece_none();
-  SubAgg L_fs = sub_none();
-  uint64_t count = 0, minstart = ~0ull;
-
-  for (uint64_t base = lo; base < hi; base += 32) {
-    const uint64_t i = base + lane;
-    const bool valid = i < hi;
-    const uint64_t key = valid ? a.keys[i] : 0ull;
-    const uint64_t up = __shfl_up_sync(FULL, key, 1);
-    const uint64_t pk = lane == 0 ? prev_key : up;
-    const bool first = !have && lane == 0;
-    const uint64_t cellv = key >> a.cell_shift;
-    const bool ch = valid && (first || cellv != (pk >> a.cell_shift));
-    const bool sh = valid && (first || (key >> a.phase_shift) != (pk >> a.phase_shift));
-    const unsigned V = __ballot_sync(FULL, valid);
-    const int last = 31 - __clz(V);
-    const unsigned CH = __ballot_sync(FULL, ch);
-    const unsigned SH = __ballot_sync(FULL, sh);
-    const unsigned WB = __ballot_sync(FULL, valid && (key & 1ull));
-    // groups carried from the previous step that end exactly at the step boundary
-    if (have && (SH & 1u)) {
-      const bool was_single = cur.single_sub != 0;
-      if (was_single && cur_is_L) {
-        L_fs = cur.ls;          // first sub group of the warp's first cell: kept apart
-        cur.fs = L_fs;
-      } else if (sub_racy(cur.ls)) {
-        cur.inner = 1;
+// Each warp scans a contiguous range of segments of kSegKeys keys, in order.
+// Per segment every lane folds its run of kScanRun keys: the keys that continue
+// the cell open before the run form its prefix piece; cells that begin and end
+// in the run are counted at once; the cell open at the run's end is finished
+// by a segmented suffix scan over the lanes' prefix pieces (5 shuffle rounds).
+// A cell still open at the segment end is carried to the next segment.  The
+// first cell of the warp's range (it may continue the previous warp's range)
+// and the cell open at its end go to the warp's Summary for the ordered fold.
+__global__ void __launch_bounds__(kScanWarps * 32) scan_runs_kernel(ScanArgs a) {
+  __shared__ uint64_t sk[kScanWarps][32 * kRunPad];
+  const unsigned tm = (1u << a.thread_bits) - 1u;
+  const unsigned bm = (1u << a.block_bits) - 1u;
+  const unsigned pm = (1u << a.phase_bits) - 1u;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t* my = sk[w];
+  const uint64_t n_seg = (a.n + kSegKeys - 1) / kSegKeys;
+  const uint64_t gw = (uint64_t)blockIdx.x * kScanWarps + w;
+  const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
+  const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
+  const uint64_t range_start = seg0 * kSegKeys;
+  unsigned count = 0;
+  unsigned long long minstart = ~0ull;
+  // warp-uniform state
+  bool carry_valid = false;
+  Piece carry = piece_empty();
+  uint64_t carry_cell = 0, carry_start = 0;
+  bool first_closed = false;
+  Piece Lw = piece_empty();
+  uint64_t Lw_cell = 0;
+  for (uint64_t seg = seg0; seg < seg1; ++seg) {
+    const uint64_t S = seg * kSegKeys;
+#pragma unroll
+    for (int i = 0; i < kSegKeys / 64; ++i) {
+      const int j = 2 * (i * 32 + lane);
+      const uint64_t pos = S + j;
+      uint64_t x = ~0ull, y = ~0ull;
+      if (pos + 1 < a.n) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + pos));
+        x = v.x;
+        y = v.y;
+      } else if (pos < a.n) {
+        x = a.keys[pos];
       }
-      cur.single_sub = 0;
-      if (CH & 1u) {
-        if (cur_is_L) {
-          Lp = cur;
-          Lp.single_sub = was_single ? 1u : 0u;
-          Lp.fs = L_fs;
-          Lp.ls = was_single ? L_fs : sub_none();
-          L_done = true;
-        } else {
-          const bool racy = (cur.minb != cur.maxb) ? (cur.anyW != 0) : (cur.inner != 0);
-          if (racy) {
-            count += 1;
-            if (cur.start < minstart) minstart = cur.start;
-          }
+      const int o = (j / kScanRun) * kRunPad + (j % kScanRun);
+      my[o] = x;
+      my[o + 1] = y;
+    }
+    __syncwarp();
+    const uint64_t s = S + (uint64_t)lane * kScanRun;
+    const int len = s < a.n ? (int)min((uint64_t)kScanRun, a.n - s) : 0;
+    const uint64_t* run = my + lane * kRunPad;
+    // cell of the key just before the run (none before the warp's range)
+    uint64_t c_prev = ~0ull;
+    if (lane > 0) c_prev = my[(lane - 1) * kRunPad + kScanRun - 1] >> a.cell_shift;
+    else if (seg != seg0) c_prev = a.keys[S - 1] >> a.cell_shift;
+    Piece PP = piece_empty();       // keys continuing the cell open before the run
+    Piece OC = piece_empty();       // the cell open at the current key
+    uint64_t oc_cell = 0, oc_start = 0;
+    bool has_head = false;
+    bool got_L = false;             // this lane closed the warp range's first cell
+    Piece Lc = piece_empty();
+    uint64_t Lc_cell = 0;
+    for (int q = 0; q < len; ++q) {
+      const uint64_t k = run[q];
+      const uint64_t cc = k >> a.cell_shift;
+      const unsigned ph = (unsigned)(k >> a.phase_shift) & pm;
+      const unsigned t = (unsigned)(k >> a.thread_shift) & tm;
+      const unsigned b = (unsigned)(k >> a.block_shift) & bm;
+      const bool wr = (k & 1ull) != 0;
+      const uint64_t pos = s + q;
+      if (!has_head && cc == c_prev) {
+        if (PP.flags & kPEmpty) piece_start(PP, ph, t, b, wr);
+        else piece_add(PP, ph, t, b, wr, true);
+      } else if (!has_head || cc != oc_cell) {
+        if (has_head) {
+          if (oc_start == range_start) { got_L = true; Lc = OC; Lc_cell = oc_cell; }
+          else if (cpiece_racy(OC)) { ++count; minstart = min(minstart, (unsigned long long)oc_start); }
         }
-        cur_is_L = false;
+        has_head = true;
+        piece_start(OC, ph, t, b, wr);
+        oc_cell = cc;
+        oc_start = pos;
+      } else {
+        piece_add(OC, ph, t, b, wr, oc_start == range_start);
       }
     }
-    const unsigned t = (unsigned)(key >> a.thread_shift) & tmask;
-    const unsigned b = (unsigned)(key >> a.block_shift) & bmask;
-    const unsigned p = (unsigned)(key >> a.phase_shift) & pmask;
-    const unsigned le = lane == 31 ? FULL : ((2u << lane) - 1u);
-
-    const unsigned sle = SH & le;
-    const int s_start = sle ? 31 - __clz(sle) : 0;
-    const bool s_cont = sle == 0;
-    const unsigned sgt = SH & ~le;
-    const int s_end = sgt ? __ffs(sgt) - 2 : last;
-    const unsigned cle = CH & le;
-    const int c_start = cle ? 31 - __clz(cle) : 0;
-    const bool c_cont = cle == 0;
-    const unsigned cgt = CH & ~le;
-    const int c_end = cgt ? __ffs(cgt) - 2 : last;
-
-    SubAgg sa = sub_none();
-    unsigned minb = 0, maxb = 0, cW = 0;
-    if (valid) {
-      const unsigned smask = lane_range_mask(s_start, s_end);
-      const unsigned cmask = lane_range_mask(c_start, c_end);
-      sa.mint = __reduce_min_sync(smask, t);
-      sa.maxt = __reduce_max_sync(smask, t);
-      sa.anyW = (WB & smask) != 0;
-      minb = __reduce_min_sync(cmask, b);
-      maxb = __reduce_max_sync(cmask, b);
-      cW = (WB & cmask) != 0;
+    // suffix scan of the prefix pieces: C = continuation from this lane onward,
+    // stop = it ends in this segment (at a lane that has a head)
+    Piece C = PP;
+    bool stop = has_head || len == 0;
+    bool dead = len == 0;                 // the chain ran into lanes past the end of the keys
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const Piece Cn = shfl_down_T(C, d);
+      const bool sn = __shfl_down_sync(FULL, stop, d);
+      const bool dn = __shfl_down_sync(FULL, dead, d);
+      if (!stop && lane + d < 32) {
+        C = piece_cat(C, Cn);
+        stop = sn;
+        dead = dn;
+      }
     }
-    if (valid && s_cont) sa = sub_merge(cur.ls, sa);
-    if (valid && c_cont) {
-      minb = min(minb, cur.minb);
-      maxb = max(maxb, cur.maxb);
-      cW |= cur.anyW;
+    const Piece Cn1 = shfl_down_T(C, 1);
+    const bool stop1 = __shfl_down_sync(FULL, stop, 1);
+    const bool dead1 = __shfl_down_sync(FULL, dead, 1);
+    // the lane's open cell: finished if its continuation ends inside the segment
+    bool open_at_end = false;
+    Piece total = OC;
+    if (has_head) {
+      const bool has_next = lane < 31;
+      if (has_next) total = piece_cat(OC, Cn1);
+      const bool ended = has_next && stop1 && !dead1;
+      if (ended) {
+        if (oc_start == range_start) { got_L = true; Lc = total; Lc_cell = oc_cell; }
+        else if (cpiece_racy(total)) { ++count; minstart = min(minstart, (unsigned long long)oc_start); }
+      } else {
+        open_at_end = true;
+      }
     }
-    const bool cell_is_L = c_cont ? cur_is_L : (!have && c_start == 0);
-    const bool sub_is_first = s_cont ? (cur.single_sub != 0) : (((CH >> s_start) & 1u) != 0);
-    const bool s_closes = valid && lane == s_end && s_end < last;
-    const bool keep_fs = s_closes && sub_is_first && cell_is_L;
-    const unsigned RS = __ballot_sync(FULL, s_closes && sub_racy(sa) && !keep_fs);
-    const unsigned cmask_all = valid ? lane_range_mask(c_start, c_end) : 0u;
-    const bool inner = ((RS & cmask_all) != 0) || (c_cont && cur.inner);
-    const bool c_closes = valid && lane == c_end && c_end < last;
-    const bool racy_c = (minb != maxb) ? (cW != 0) : inner;
-    const uint64_t my_start = c_cont ? cur.start : base + (uint64_t)c_start;
-
-    // cells that close here (not the warp's first cell)
-    const unsigned RC = __ballot_sync(FULL, c_closes && !cell_is_L && racy_c);
-    count += __popc(RC);
-    if (RC) {
-      const uint64_t s0 = __shfl_sync(FULL, my_start, __ffs(RC) - 1);
-      if (s0 < minstart) minstart = s0;
+    // the warp's carried cell continues into lane 0's prefix chain
+    const Piece C0 = shfl_idx_T(C, 0);
+    const bool stop0 = __shfl_sync(FULL, stop, 0);
+    const bool dead0 = __shfl_sync(FULL, dead, 0);
+    if (carry_valid && !(C0.flags & kPEmpty)) {
+      carry = piece_cat(carry, C0);
+      if (stop0 && !dead0) {
+        // the carried cell ends in this segment
+        if (carry_start == range_start) { first_closed = true; Lw = carry; Lw_cell = carry_cell; }
+        else if (cpiece_racy(carry) && lane == 0) { ++count; minstart = min(minstart, (unsigned long long)carry_start); }
+        carry_valid = false;
+      }
+    } else if (carry_valid && C0.flags & kPEmpty) {
+      // lane 0 begins a new cell (or there are no keys): the carried cell ended at the segment start
+      const bool lane0_has_keys = __shfl_sync(FULL, len, 0) > 0;
+      if (lane0_has_keys) {
+        if (carry_start == range_start) { first_closed = true; Lw = carry; Lw_cell = carry_cell; }
+        else if (cpiece_racy(carry) && lane == 0) { ++count; minstart = min(minstart, (unsigned long long)carry_start); }
+        carry_valid = false;
+      }
     }
-    // the first sub group of the warp's first cell closes here: keep it apart
-    const unsigned KF = __ballot_sync(FULL, keep_fs);
-    if (KF) L_fs = shfl_T(sa, __ffs(KF) - 1);
-    // the warp's first cell closes here
-    const unsigned LC = __ballot_sync(FULL, c_closes && cell_is_L);
-    const unsigned pf = __shfl_sync(FULL, p, c_start);   // phase of the first key of my cell in this step
-    if (LC) {
-      const int f = __ffs(LC) - 1;
-      const bool single = KF && (__ffs(KF) - 1) == f;
-      Lp.cell = __shfl_sync(FULL, cellv, f);
-      Lp.start = lo;
-      Lp.minb = __shfl_sync(FULL, minb, f);
-      Lp.maxb = __shfl_sync(FULL, maxb, f);
-      Lp.anyW = __shfl_sync(FULL, cW, f);
-      const unsigned my_first_p = c_cont ? cur.first_p : pf;
-      Lp.first_p = __shfl_sync(FULL, my_first_p, f);
-      Lp.last_p = __shfl_sync(FULL, p, f);
-      Lp.inner = __shfl_sync(FULL, (unsigned)inner, f);
-      Lp.single_sub = single ? 1u : 0u;
-      Lp.fs = L_fs;
-      Lp.ls = single ? L_fs : sub_none();
-      Lp.pad = 0;
-      L_done = true;
+    // the range's first cell closed inside a lane
+    const unsigned GL = __ballot_sync(FULL, got_L);
+    if (GL) {
+      const int src = __ffs(GL) - 1;
+      Lw = shfl_idx_T(Lc, src);
+      Lw_cell = __shfl_sync(FULL, Lc_cell, src);
+      first_closed = true;
     }
-    // carry: the cell and sub group open at the last valid lane
-    {
-      const uint64_t c_cell = __shfl_sync(FULL, cellv, last);
-      const uint64_t c_st = __shfl_sync(FULL, my_start, last);
-      const unsigned c_minb = __shfl_sync(FULL, minb, last);
-      const unsigned c_maxb = __shfl_sync(FULL, maxb, last);
-      const unsigned c_w = __shfl_sync(FULL, cW, last);
-      const unsigned c_inner = __shfl_sync(FULL, (unsigned)inner, last);
-      const unsigned c_single = __shfl_sync(FULL, (unsigned)sub_is_first, last);
-      const SubAgg c_ls = shfl_T(sa, last);
-      const unsigned c_lastp = __shfl_sync(FULL, p, last);
-      const unsigned c_cont_last = __shfl_sync(FULL, (unsigned)c_cont, last);
-      const unsigned pf_last = __shfl_sync(FULL, pf, last);
-      const unsigned c_firstp = c_cont_last ? cur.first_p : pf_last;
-      const unsigned c_isL = __shfl_sync(FULL, (unsigned)cell_is_L, last);
-      cur.cell = c_cell;
-      cur.start = c_st;
-      cur.minb = c_minb;
-      cur.maxb = c_maxb;
-      cur.anyW = c_w;
-      cur.inner = c_inner;
-      cur.single_sub = c_single;
-      cur.ls = c_ls;
-      cur.last_p = c_lastp;
-      cur.first_p = c_firstp;
-      cur_is_L = c_isL != 0;
-      cur.fs = c_single ? c_ls : (cur_is_L ? L_fs : sub_none());
-      prev_key = __shfl_sync(FULL, key, last);
-      have = true;
+    // new carry: the open cell whose continuation reaches the segment end
+    const unsigned OE = __ballot_sync(FULL, open_at_end);
+    if (OE) {
+      const int src = 31 - __clz(OE);
+      carry = shfl_idx_T(total, src);
+      carry_cell = __shfl_sync(FULL, oc_cell, src);
+      carry_start = __shfl_sync(FULL, oc_start, src);
+      carry_valid = true;
     }
+    __syncwarp();
   }
-  if (lane == 0) {
-    Summary S;
-    S.empty = 0;
-    S.count = count;
-    S.minstart = minstart;
-    if (L_done) {
-      S.single_cell = 0;
-      S.L = Lp;
-      S.R = cur;
-    } else {
-      S.single_cell = 1;
-      S.L = cur;
-      S.R = cur;
+  // warp summary for the ordered fold
+  count = __reduce_add_sync(FULL, count);
+  minstart = warp_min_u64(minstart);
+  if (lane == 0 && gw < a.n_warps) {
+    Summary S = summary_empty();
+    if (carry_valid || first_closed) {
+      S.empty = 0;
+      S.count = count;
+      S.minstart = minstart;
+      if (first_closed) {
+        S.single_cell = 0;
+        S.L = to_cellpiece(Lw, Lw_cell, range_start);
+        S.R = to_cellpiece(carry, carry_cell, carry_start);
+      } else {
+        S.single_cell = 1;
+        S.L = S.R = to_cellpiece(carry, carry_cell, carry_start);
+      }
     }
-    a.summaries[wid] = S;
+    a.summaries[gw] = S;
   }
 }
 
-// One block: fold the warp summaries in order, then locate the first racy cell.
+// One block: fold the warp summaries in order; count and first racy cell.
 constexpr int kFoldThreads = 128;
 
 __global__ void __launch_bounds__(kFoldThreads) scan_fold_kernel(ScanArgs a) {
@@ -259,46 +410,27 @@ __global__ void __launch_bounds__(kFoldThreads) scan_fold_kernel(ScanArgs a) {
   part[threadIdx.x] = s;
   __syncthreads();
   for (int width = 1; width < kFoldThreads; width <<= 1) {
-    if ((threadIdx.x % (2 * width)) == 0) part[threadIdx.x] = summary_combine(part[threadIdx.x], part[threadIdx.x + width]);
+    if ((threadIdx.x % (2 * width)) == 0)
+      part[threadIdx.x] = summary_combine(part[threadIdx.x], part[threadIdx.x + width]);
     __syncthreads();
   }
-  __shared__ unsigned long long s_start;
   if (threadIdx.x == 0) {
     uint64_t cnt, ms;
     summary_finish(part[0], &cnt, &ms);
     a.res->racy_cells = cnt;
     a.res->min_start = ms;
-    s_start = ms;
   }
-  __syncthreads();
-  // end of the first racy cell: 32-way galloping then refinement, warp 0
-  if (threadIdx.x < 32 && s_start != ~0ull) {
-    const int lane = threadIdx.x;
-    const uint64_t target = a.keys[s_start] >> a.cell_shift;
-    uint64_t lo = s_start, stride = 1;
-    auto fails = [&](uint64_t q) { return q >= a.n || (a.keys[q] >> a.cell_shift) != target; };
-    while (true) {
-      const uint64_t q = lo + (uint64_t)(lane + 1) * stride;
-      const unsigned F = __ballot_sync(FULL, fails(q));
-      if (F) {
-        lo += (uint64_t)(__ffs(F) - 1) * stride;
-        break;
-      }
-      lo += 32 * stride;
-      stride *= 32;
-    }
-    // keys[lo] is in the cell and keys[lo + stride] is not (or is past the end)
-    while (stride > 1) {
-      const uint64_t s2 = (stride + 31) / 32;
-      const uint64_t q = lo + (uint64_t)(lane + 1) * s2;
-      const unsigned F = __ballot_sync(FULL, q >= lo + stride || fails(q));
-      lo += (uint64_t)(__ffs(F) - 1) * s2;
-      stride = s2;
-    }
-    if (lane == 0) {
-      a.res->seg_end = lo + 1;
-      a.res->cell = target;
-    }
+}
+
+// One warp: the end of the first racy cell.
+__global__ void scan_finish_kernel(ScanArgs a) {
+  const unsigned long long s = a.res->min_start;
+  if (s == ~0ull) return;
+  const uint64_t cell = a.keys[s] >> a.cell_shift;
+  const uint64_t e = warp_cell_end(a.keys, a.n, a.cell_shift, s, cell);
+  if (threadIdx.x == 0) {
+    a.res->seg_end = e;
+    a.res->cell = cell;
   }
 }
 
@@ -455,6 +587,8 @@ __global__ void init_result_kernel(DevResult* r) {
     r->err = 0;
     r->n_keys = 0;
     r->sorted_buf = 0;
+    r->hash_cell = ~0ull;
+    r->stop = 0;
   }
 }
 
@@ -466,11 +600,13 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st) {
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
-  const unsigned blocks = (a.n_warps * 32 + 255) / 256;
-  scan_warps_kernel<<<blocks, 256, 0, st>>>(a);
+  scan_runs_kernel<<<(a.n_warps + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scan_fold_kernel<<<1, kFoldThreads, 0, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scan_finish_kernel<<<1, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) digit_offsets_kernel(const unsigned long 
 // ---------------------------------------------------------------------------
 // one onesweep pass
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(SortArgs a) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ unsigned int s_tile;
   __shared__ unsigned int warp_hist[kWarps][kRadix];
@@ -108,29 +108,39 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a) {
   const unsigned int dmask = (1u << a.bits) - 1u;
   const uint64_t wbase = tile * kSortTile + (uint64_t)w * (32 * kSortItems);
   uint64_t k[kSortItems];
-  unsigned int d[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-    const bool valid = pos < a.n;
-    k[i] = valid ? a.keys_in[pos] : ~0ull;
-    d[i] = valid ? ((unsigned int)(k[i] >> a.shift) & dmask) : (unsigned int)kRadix;
+    k[i] = pos < a.n ? a.keys_in[pos] : ~0ull;
   }
 
-  // warp-level multi-split ranking, stable in (item, lane) order
+  // Warp-level multi-split ranking, stable in (item, lane) order.  First the
+  // peer masks of all items (independent __match_any_sync, so their latencies
+  // overlap; an out-of-range lane gets a digit no other lane has), then one
+  // pass over the items that turns the masks into ranks through the warp's
+  // shared-memory digit counters (the lowest peer updates the counter).
+  const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
+  unsigned int peers[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+    if (!full_tile && wbase + (uint64_t)i * 32 + lane >= a.n) d = 0x100u | lane;
+    peers[i] = __match_any_sync(0xffffffffu, d);
+  }
   unsigned int r[kSortItems];
   const unsigned int lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const unsigned int peers = __match_any_sync(0xffffffffu, d[i]);
-    const unsigned int leader = __ffs(peers) - 1;
+    const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+    const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
+    const unsigned int leader = __ffs(peers[i]) - 1;
     unsigned int prev = 0;
-    if (lane == leader && d[i] < (unsigned int)kRadix) {
-      prev = warp_hist[w][d[i]];
-      warp_hist[w][d[i]] = prev + __popc(peers);
+    if (lane == leader && valid) {
+      prev = warp_hist[w][d];
+      warp_hist[w][d] = prev + __popc(peers[i]);
     }
-    prev = __shfl_sync(peers, prev, leader);
-    r[i] = prev + __popc(peers & lt);
+    prev = __shfl_sync(0xffffffffu, prev, leader);
+    r[i] = prev + __popc(peers[i] & lt);
     __syncwarp();
   }
   __syncthreads();
@@ -155,8 +165,13 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(SortArgs a) {
 
   // stage the keys in digit order (stable)
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i)
-    if (d[i] < (unsigned int)kRadix) s_keys[tile_excl[d[i]] + warp_hist[w][d[i]] + r[i]] = k[i];
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+    if (pos < a.n) {
+      const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+      s_keys[tile_excl[d] + warp_hist[w][d] + r[i]] = k[i];
+    }
+  }
 
   // decoupled look-back for digit dg
   unsigned long long excl = 0;
@@ -213,6 +228,13 @@ cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long l
 
 cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
+  static bool carveout_set = false;
+  if (!carveout_set) {
+    // as much shared memory as possible: 3 resident blocks of ~44 KB per SM
+    cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    carveout_set = true;
+  }
   const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
   onesweep_kernel<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(a);
   return cudaGetLastError();

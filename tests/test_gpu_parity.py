@@ -126,6 +126,23 @@ def test_empty_and_degenerate(rc):
     assert g.racy_cells == 3
 
 
+@pytest.mark.parametrize("scope", ["shared", "global"])
+@pytest.mark.parametrize("block", [60, 64, 65, 100, 512])
+@pytest.mark.parametrize("writer", [None, (0, 5), (1, 0), (3, 7)])
+def test_long_cells(rc, scope, block, writer):
+    """Cells read by every thread of a block in phases 0 and 1 (2 x block keys
+    per cell and block, many above the scan's long-cell cap), plus one writer
+    thread in some phase: racy iff the writer shares a phase with readers or
+    (global) another block reads the cell."""
+    stmts = [Stmt([Access(0, R, (tid.x % 2,))], loops=[Loop(0, 2)], phase=it(0)),
+             Stmt([Access(0, R, (const(1),))], loops=[Loop(0, 2)], phase=it(0))]
+    if writer is not None:
+        ph, t = writer
+        stmts.append(Stmt([Access(0, W, (const(1),))], guards=[const(t) - tid.x, tid.x - t], phase=const(ph)))
+    m = Model((3, 1, 1), (block, 1, 1), [Array("x", scope, (2,))], stmts, n_phases=4)
+    compare(rc, m)
+
+
 def test_out_of_bounds(rc):
     arr = [Array("a", "global", (10,))]
     m = Model((2, 1, 1), (8, 1, 1), arr, [Stmt([Access(0, R, (tid.x,))]), Stmt([Access(0, W, (tid.x + 3,))])])
@@ -253,3 +270,74 @@ def test_sort_stable(rc, n, bits):
         torch.cuda.synchronize()
         got = dout.cpu().numpy().view(np.uint64)
         assert np.array_equal(got, exp), (n, bits, db)
+
+
+# ---------------------------------------------------------------------------
+# hash path
+# ---------------------------------------------------------------------------
+
+HASH = {"path": 2}
+HASH_EARLY = {"path": 2, "early_exit": 1}
+
+
+def _hash_models():
+    return ([w.tiny_random(s) for s in range(60)] +
+            [w.neighbor_write_read(64, n_blocks=3), w.reduction_tree(False), w.reduction_tree(True),
+             w.polyhedral_product(40), w.transpose(pad=True, barrier=False, n=128),
+             w.transpose(pad=False, barrier=True, n=128), w.ge_spmm_uniform(2, 64, 3, 70, False),
+             w.random_affine(4, n_blocks=8, block=128, plant=True),
+             w.random_affine(4, n_blocks=8, block=128, plant=False)])
+
+
+@pytest.mark.parametrize("i", range(69))
+def test_hash_path_matches_oracle(rc, i):
+    """Without early exit the hash path gives the sort path's full result."""
+    compare(rc, _hash_models()[i], HASH)
+
+
+def _is_racing_witness(model, wit):
+    a, s, e, x, y = wit
+    inst = {tuple(int(v) for v in row) for row in oracle.expand(model)}
+    bs = model.block_size
+    xt = (a, s, e, x[0], x[1], x[2], x[3])
+    yt = (a, s, e, y[0], y[1], y[2], y[3])
+    return xt in inst and yt in inst and pyref.race(xt, yt, bs)
+
+
+@pytest.mark.parametrize("i", range(69))
+def test_hash_early_exit_verdict(rc, i):
+    """With early exit the verdict is exact, the count a lower bound, and the
+    witness a racing pair of the model."""
+    m = _hash_models()[i]
+    exp = oracle.check(m)
+    got = rc.check(m, HASH_EARLY)
+    assert got.status == exp.status and got.instances == exp.instances
+    assert got.verdict == exp.verdict
+    if exp.verdict:
+        assert 1 <= got.racy_cells <= exp.racy_cells
+        assert _is_racing_witness(m, got.witness)
+
+
+def test_hash_path_out_of_bounds(rc):
+    m = Model((2, 1, 1), (8, 1, 1), [Array("a", "global", (10,))],
+              [Stmt([Access(0, R, (tid.x,))]), Stmt([Access(0, W, (tid.x + 3,))])])
+    compare(rc, m, HASH)
+
+
+@pytest.mark.parametrize("i", range(40))
+def test_scan_long_warp_ranges(rc, i):
+    """Few scan warps, so each warp carries cells across many segments."""
+    models = ([w.tiny_random(s) for s in range(25)] +
+              [w.reduction_tree(False, load_phase=True), w.neighbor_write_read(300, n_blocks=5),
+               w.polyhedral_product(120), w.transpose(pad=False, barrier=False, n=128),
+               w.transpose(pad=True, barrier=True, n=128), w.ge_spmm_uniform(2, 64, 5, 90, False),
+               w.random_affine(9, n_blocks=8, block=128, plant=True),
+               w.random_affine(9, n_blocks=8, block=128, plant=False)] +
+              [Model((3, 1, 1), (blk, 1, 1), [Array("x", sc, (2,))],
+                     [Stmt([Access(0, R, (tid.x % 2,))], loops=[Loop(0, 2)], phase=it(0)),
+                      Stmt([Access(0, R, (const(1),))], loops=[Loop(0, 2)], phase=it(0)),
+                      Stmt([Access(0, W, (const(1),))], guards=[const(5) - tid.x, tid.x - 5], phase=const(ph))],
+                     n_phases=4)
+               for sc, blk, ph in [("shared", 700, 1), ("global", 700, 3), ("shared", 1024, 3),
+                                   ("global", 33, 0), ("shared", 65, 2), ("global", 1000, 1), ("shared", 999, 0)]])
+    compare(rc, models[i], {"test_flags": rc.binding.RC_TEST_FEW_SCAN_WARPS})
