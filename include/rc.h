@@ -153,7 +153,10 @@ typedef struct rc_model rc_model;   /* opaque */
 
 /* Validate and lower a descriptor: compile every expression, compute the key
  * layout and the instance count, and upload the lowered program to the
- * current CUDA device.  The descriptor is deep-copied: the caller may free it
+ * current CUDA device.  For a model with at least 2^22 keys the expansion
+ * kernel is generated for the model and compiled with NVRTC (cached per
+ * device by source; environment RC_JIT=0 disables it, RC_JIT=1 forces it for
+ * every model); if NVRTC is not available the interpreted expansion is used.  The descriptor is deep-copied: the caller may free it
  * on return.  Statements whose loop trip counts depend on the thread are
  * counted on the device (a synchronous count pass on an internal stream).
  * Errors: RC_E_INVALID (malformed), RC_E_KEY_OVERFLOW, RC_E_UNSUPPORTED,
@@ -177,10 +180,19 @@ typedef struct rc_layout {
   uint32_t n_threads_per_block;
   uint64_t n_blocks;
   uint64_t program_bytes;    /* bytes of the lowered program uploaded by rc_model_create */
+  uint32_t expand_jit;       /* 1 = the expansion runs a kernel generated for this model   */
+  uint32_t reserved;
   uint64_t array_base[64];   /* first linear cell of each array (first 64 arrays) */
   uint64_t array_cells[64];  /* cells of one scope instance of each array         */
 } rc_layout;
 rc_status rc_model_layout(const rc_model* m, rc_layout* out);
+
+/* Source text of the expansion kernel rc_model_create would generate for this
+ * descriptor: up to cap-1 bytes and a terminating NUL go to buf (may be NULL
+ * when cap is 0); *len receives the full length.  Host lowering only, no
+ * device needed.  Errors: those of lowering (RC_E_INVALID, RC_E_KEY_OVERFLOW,
+ * RC_E_UNSUPPORTED). */
+rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, size_t* len);
 
 /* ------------------------------------------------------------------------- */
 /* checking                                                                   */

@@ -44,7 +44,7 @@ RC_OPT_STAGE_TIMES = 1
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
            "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times",
-           "rc_sort_keys_static"]
+           "rc_sort_keys_static", "rc_kernel_source"]
 RC_SORT_STATIC_MAX_KEYS = 1 << 20
 
 
@@ -104,7 +104,7 @@ class rc_layout(Structure):
                 ("cell_bits", c_uint32), ("sort_lo", c_uint32), ("sort_hi", c_uint32),
                 ("key_slots", c_uint64), ("total_cells", c_uint64), ("n_arrays", c_uint32),
                 ("n_threads_per_block", c_uint32), ("n_blocks", c_uint64),
-                ("program_bytes", c_uint64), ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
+                ("program_bytes", c_uint64), ("expand_jit", c_uint32), ("reserved", c_uint32), ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
 
 
 class rc_check_opts(Structure):
@@ -179,6 +179,8 @@ def load():
         lib.rc_sort_keys.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p,
                                      c_size_t, c_void_p]
         lib.rc_sort_keys.restype = c_int
+        lib.rc_kernel_source.argtypes = [POINTER(rc_model_desc), ctypes.c_char_p, c_size_t, POINTER(c_size_t)]
+        lib.rc_kernel_source.restype = c_int
         lib.rc_sort_keys_static.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p]
         lib.rc_sort_keys_static.restype = c_int
         lib.rc_ticket_stage_times.argtypes = [c_void_p, POINTER(rc_stage_times)]
@@ -376,6 +378,19 @@ def rc_model_create_status(model) -> int:
 
 def rc_model_destroy(m: RcModel):
     m.close()
+
+
+def rc_kernel_source(model) -> str:
+    """Source of the expansion kernel generated for a model (host lowering only)."""
+    lib = load()
+    d = _Desc(model)
+    n = c_size_t()
+    st = lib.rc_kernel_source(ctypes.byref(d.desc), None, 0, ctypes.byref(n))
+    if st != RC_OK:
+        raise RcError(st, "rc_kernel_source")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    lib.rc_kernel_source(ctypes.byref(d.desc), buf, n.value + 1, ctypes.byref(n))
+    return buf.value.decode()
 
 
 def rc_model_layout(m: RcModel) -> dict:

@@ -1,0 +1,326 @@
+// Per-model expansion kernel generated as CUDA C and compiled at run time with
+// NVRTC for sm_103a.
+//
+// The interpreted expansion (expand.cu) reads every coefficient, divisor and
+// array constant from the lowered program at every access instance.  For a
+// large model the same lowered rows are instead written out as source code:
+// each statement becomes a real loop nest with its coefficients, extents and
+// divisors as literals, so the compiler folds constants, hoists the
+// thread-constant expressions out of the loops and turns floor division and
+// modulo by constants into multiply-shift sequences (or masks and shifts for
+// powers of two).  The generated kernel writes exactly the keys of the
+// interpreted one (same slots, same padding, same out-of-bounds report).
+//
+// NVRTC and the CUDA driver entry points are resolved at run time (dlopen and
+// cudaGetDriverEntryPointByVersion), so the library loads on machines without
+// them; rc_model_create then keeps the interpreted expansion.  Compiled
+// kernels are cached per device by their source text.
+#include <cuda.h>
+#include <cuda_runtime_api.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "rc_internal.h"
+
+namespace rc {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// run-time loaded NVRTC and driver entry points
+// ---------------------------------------------------------------------------
+struct Nvrtc {
+  bool ok = false;
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*);
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*);
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*cubin)(nvrtcProgram, char*);
+  nvrtcResult (*destroy)(nvrtcProgram*);
+};
+
+struct Driver {
+  bool ok = false;
+  CUresult (*load)(CUmodule*, const void*);
+  CUresult (*get)(CUfunction*, CUmodule, const char*);
+  CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                     void**, void**);
+};
+
+std::mutex g_jit_mu;
+
+Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static bool tried = false;
+  if (tried) return n;
+  tried = true;
+  const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                         "/usr/local/cuda/lib64/libnvrtc.so"};
+  void* h = nullptr;
+  for (const char* nm : names)
+    if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+  if (!h) return n;
+  n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+  n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+  n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+  n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+  n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+  n.ok = n.create && n.compile && n.cubin_size && n.cubin && n.destroy;
+  return n;
+}
+
+Driver& driver() {
+  static Driver d;
+  static bool tried = false;
+  if (tried) return d;
+  tried = true;
+  auto get = [](const char* sym, void** fn) {
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion(sym, fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+           q == cudaDriverEntryPointSuccess && *fn != nullptr;
+  };
+  void *a = nullptr, *b = nullptr, *c = nullptr;
+  d.ok = get("cuModuleLoadData", &a) && get("cuModuleGetFunction", &b) && get("cuLaunchKernel", &c);
+  d.load = reinterpret_cast<decltype(d.load)>(a);
+  d.get = reinterpret_cast<decltype(d.get)>(b);
+  d.launch = reinterpret_cast<decltype(d.launch)>(c);
+  return d;
+}
+
+std::map<std::string, void*> g_cache;   // (device, source) -> CUfunction
+
+// ---------------------------------------------------------------------------
+// code generation
+// ---------------------------------------------------------------------------
+std::string lit(int64_t v) {
+  if (v == INT64_MIN) return "((long long)0x8000000000000000ull)";
+  return "(" + std::to_string(v) + "LL)";
+}
+std::string ulit(uint64_t v) { return std::to_string(v) + "ull"; }
+
+bool is_pow2(int64_t d) { return d > 0 && (d & (d - 1)) == 0; }
+int log2i(int64_t d) {
+  int k = 0;
+  while ((1ll << k) < d) ++k;
+  return k;
+}
+
+struct Gen {
+  const Model& m;
+  const uint8_t* img;
+  const DevStmt* stmts;
+  const DevAccess* accs;
+  const DevArray* arrays;
+  const Row* rows;
+  const LinTerm* lin;
+  const Term* terms;
+  std::ostringstream o;
+
+  explicit Gen(const Model& mm) : m(mm), img(mm.program.data()) {
+    stmts = reinterpret_cast<const DevStmt*>(img + m.sec_stmts);
+    accs = reinterpret_cast<const DevAccess*>(img + m.sec_accs);
+    arrays = reinterpret_cast<const DevArray*>(img + m.sec_arrays);
+    rows = reinterpret_cast<const Row*>(img + m.sec_rows);
+    lin = reinterpret_cast<const LinTerm*>(img + m.sec_lin);
+    terms = reinterpret_cast<const Term*>(img + m.sec_terms);
+  }
+
+  std::string row(int r) {
+    static const char* tv[6] = {"tx", "ty", "tz", "bx", "by", "bz"};
+    const Row& R = rows[r];
+    std::string e = lit(R.c0);
+    for (int i = 0; i < 6; ++i)
+      if (R.ct[i]) e += " + " + lit(R.ct[i]) + " * " + tv[i];
+    for (int k = 0; k < R.nnz; ++k) {
+      const LinTerm& t = lin[R.off + k];
+      const std::string v = t.var < kMaxLoops ? "i" + std::to_string(t.var) : "q" + std::to_string(t.var - kMaxLoops);
+      e += " + " + lit(t.coef) + " * " + v;
+    }
+    return "(" + e + ")";
+  }
+
+  void emit_terms(const DevStmt& S, int level, const std::string& ind) {
+    for (int q = 0; q < S.n_terms; ++q) {
+      const Term& T = terms[S.term0 + q];
+      if (T.level != level) continue;
+      const std::string a = row(T.row);
+      std::string v;
+      if (T.op == kFdiv) v = is_pow2(T.d) ? "(" + a + " >> " + std::to_string(log2i(T.d)) + ")" : "fdiv_c(" + a + ", " + lit(T.d) + ")";
+      else v = is_pow2(T.d) ? "(" + a + " & " + lit(T.d - 1) + ")" : "mod_c(" + a + ", " + lit(T.d) + ")";
+      o << ind << "const long long q" << q << " = " << v << ";\n";
+    }
+  }
+
+  void emit_stmt(uint32_t s) {
+    const DevStmt& S = stmts[s];
+    const uint64_t T = m.host.n_threads;
+    o << "    case " << s << ": {\n";
+    if (S.dense) o << "      unsigned long long slot = " << ulit(S.slot_base) << " + g;\n";
+    else o << "      unsigned long long off = unit_offset[" << ulit(S.slot_base) << " + g];\n";
+    emit_terms(S, 0, "      ");
+    std::string ind = "      ";
+    for (int l = 0; l < S.n_loops; ++l) {
+      o << ind << "for (long long i" << l << " = " << row(S.row_lower[l]) << "; i" << l << " < " << row(S.row_upper[l])
+        << "; i" << l << " += " << lit(S.step[l]) << ") {\n";
+      ind += "  ";
+      emit_terms(S, l + 1, ind);
+    }
+    // guards
+    std::string gcond = "true";
+    for (int gi = 0; gi < S.n_guards; ++gi) gcond += " && " + row(S.guard_row0 + gi) + " >= 0";
+    o << ind << "if (" << gcond << ") {\n";
+    const std::string in2 = ind + "  ";
+    o << in2 << "const long long ph = " << row(S.row_phase) << ";\n";
+    for (int a = 0; a < S.n_acc; ++a) {
+      const DevAccess& A = accs[S.acc0 + a];
+      const DevArray& arr = arrays[A.array];
+      o << in2 << "{\n";
+      const std::string in3 = in2 + "  ";
+      for (int d = 0; d < A.ndims; ++d) o << in3 << "const long long v" << d << " = " << row(A.row0 + d) << ";\n";
+      o << in3 << "unsigned dc = 0xFFFFFFFFu;\n";
+      o << in3 << "if (ph < 0 || ph >= " << lit(m.host.n_phases) << ") dc = 0u;\n";
+      for (int d = 0; d < A.ndims; ++d)
+        o << in3 << "else if (v" << d << " < 0 || v" << d << " >= " << lit(arr.ext[d]) << ") dc = " << d + 1 << "u;\n";
+      // row-major element index
+      std::string e;
+      for (int d = 0; d < A.ndims; ++d) {
+        int64_t stride = 1;
+        for (int d2 = d + 1; d2 < A.ndims; ++d2) stride *= arr.ext[d2];
+        if (!e.empty()) e += " + ";
+        e += "v" + std::to_string(d) + " * " + lit(stride);
+      }
+      std::string cell = ulit(arr.base) + " + (unsigned long long)(" + e + ")";
+      if (arr.shared) cell += " + b * " + ulit(arr.cells);
+      const uint64_t pack = ((unsigned long long)s << 51) | ((unsigned long long)a << 45);
+      o << in3 << "unsigned long long key;\n";
+      o << in3 << "if (dc != 0xFFFFFFFFu) { atomicMin(oob, " << ulit(pack)
+        << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc); key = ~0ull; }\n";
+      o << in3 << "else key = ((" << cell << ") << " << m.host.cell_shift << ") | ((unsigned long long)ph << "
+        << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind) << ";\n";
+      if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)a * T) << "] = key;\n";
+      else o << in3 << "keys[off + " << a << "] = key;\n";
+      o << in2 << "}\n";
+    }
+    o << in2 << "cnt += " << S.n_acc << ";\n";
+    if (!S.dense) o << in2 << "off += " << S.n_acc << ";\n";
+    o << ind << "}";
+    if (S.dense) {
+      o << " else {\n";
+      for (int a = 0; a < S.n_acc; ++a) o << in2 << "keys[slot + " << ulit((uint64_t)a * T) << "] = ~0ull;\n";
+      o << ind << "}\n";
+      o << ind << "slot += " << ulit((uint64_t)S.n_acc * T) << ";\n";
+    } else {
+      o << "\n";
+    }
+    for (int l = S.n_loops - 1; l >= 0; --l) {
+      ind.resize(ind.size() - 2);
+      o << ind << "}\n";
+    }
+    o << "    } break;\n";
+  }
+
+  std::string source() {
+    const DevModel& h = m.host;
+    o << "// generated expansion kernel\n";
+    o << "__device__ __forceinline__ long long fdiv_c(long long a, long long d) {\n"
+         "  return a >= 0 ? a / d : -1 - (-(a + 1)) / d;\n}\n";
+    o << "__device__ __forceinline__ long long mod_c(long long a, long long d) { return a - fdiv_c(a, d) * d; }\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
+         "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset) {\n";
+    o << "  const unsigned long long g = (unsigned long long)blockIdx.x * 128ull + threadIdx.x;\n";
+    o << "  unsigned long long cnt = 0;\n";
+    o << "  if (g < " << ulit(h.n_threads) << ") {\n";
+    o << "    const unsigned long long b = g / " << ulit(h.bs) << ";\n";
+    o << "    const unsigned t = (unsigned)(g - b * " << ulit(h.bs) << ");\n";
+    o << "    const long long tx = t % " << h.block[0] << "u, ty = (t / " << h.block[0] << "u) % " << h.block[1]
+      << "u, tz = t / " << (uint64_t)h.block[0] * h.block[1] << "u;\n";
+    o << "    const long long bx = (long long)(b % " << ulit(h.grid[0]) << "), by = (long long)((b / " << ulit(h.grid[0])
+      << ") % " << ulit(h.grid[1]) << "), bz = (long long)(b / " << ulit((uint64_t)h.grid[0] * h.grid[1]) << ");\n";
+    o << "    (void)tx; (void)ty; (void)tz; (void)bx; (void)by; (void)bz;\n";
+    o << "    const unsigned long long low = (b << " << h.block_shift << ") | ((unsigned long long)t << "
+      << h.thread_shift << ");\n";
+    o << "    switch (blockIdx.y) {\n";
+    for (uint32_t s = 0; s < h.n_stmts; ++s) emit_stmt(s);
+    o << "    default: break;\n    }\n  }\n";
+    o << "  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);\n";
+    o << "  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(inst, cnt);\n";
+    o << "}\n";
+    return o.str();
+  }
+};
+
+}  // namespace
+
+std::string jit_expand_source(const Model& m) {
+  Gen g(m);
+  return g.source();
+}
+
+// Compile (or fetch from the cache) the model's expansion kernel for the
+// current device.  Returns false if NVRTC, the driver or the compile fails.
+bool jit_expand_build(Model* m) {
+  const char* env = std::getenv("RC_JIT");
+  if (env && env[0] == '0') return false;
+  const bool force = env && env[0] == '1';
+  if (!force && m->key_slots < kJitMinKeys) return false;
+  if (m->host.n_stmts == 0 || m->host.n_threads == 0) return false;
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  Nvrtc& nv = nvrtc();
+  Driver& dr = driver();
+  if (!nv.ok || !dr.ok) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const std::string src = jit_expand_source(*m);
+  const std::string key = std::to_string(dev) + "\n" + src;
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    m->jit_fn = it->second;
+    return true;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+  const std::string arch = "--gpu-architecture=sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
+  nvrtcProgram prog;
+  if (nv.create(&prog, src.c_str(), "rc_expand_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
+  const char* opts[] = {arch.c_str(), "--std=c++17"};
+  bool ok = nv.compile(prog, 2, opts) == NVRTC_SUCCESS;
+  std::vector<char> cubin;
+  if (ok) {
+    size_t n = 0;
+    ok = nv.cubin_size(prog, &n) == NVRTC_SUCCESS && n > 0;
+    if (ok) {
+      cubin.resize(n);
+      ok = nv.cubin(prog, cubin.data()) == NVRTC_SUCCESS;
+    }
+  }
+  nv.destroy(&prog);
+  if (!ok) return false;
+  CUmodule mod;
+  CUfunction fn;
+  if (dr.load(&mod, cubin.data()) != CUDA_SUCCESS) return false;
+  if (dr.get(&fn, mod, "rc_expand_jit") != CUDA_SUCCESS) return false;
+  g_cache[key] = reinterpret_cast<void*>(fn);
+  m->jit_fn = reinterpret_cast<void*>(fn);
+  return true;
+}
+
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st) {
+  Driver& dr = driver();
+  CUfunction fn = reinterpret_cast<CUfunction>(m.jit_fn);
+  unsigned long long* oob = &res->oob_code;
+  unsigned long long* inst = &res->instances;
+  const uint64_t* uo = m.host.unit_offset;
+  void* params[] = {&keys, &oob, &inst, &uo};
+  const unsigned gx = (unsigned)((m.host.n_threads + 127) / 128);
+  const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace rc

@@ -409,6 +409,12 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.lin = reinterpret_cast<const LinTerm*>(off_lin);
   h.terms = reinterpret_cast<const Term*>(off_terms);
   h.unit_offset = reinterpret_cast<const uint64_t*>(off_units);
+  m->sec_arrays = off_arrays;
+  m->sec_stmts = off_stmts;
+  m->sec_accs = off_accs;
+  m->sec_rows = off_rows;
+  m->sec_lin = off_lin;
+  m->sec_terms = off_terms;
   return RC_OK;
 }
 

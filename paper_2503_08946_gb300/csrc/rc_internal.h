@@ -5,7 +5,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <vector>
+
+#include <cuda_runtime_api.h>
 
 #include "../../include/rc.h"
 
@@ -374,8 +377,17 @@ struct Model {
   std::vector<uint32_t> array_shared;
   uint32_t n_general_stmts = 0;
   bool has_deep_loops = false;    // some statement has more than kFastLoops loops
+  // sections of the program image (byte offsets), for the kernel generator
+  size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0;
+  void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null
   uint64_t max_iter_per_unit = 0;
 };
+
+// implemented in jit.cpp
+constexpr uint64_t kJitMinKeys = 1ull << 22;   // models with fewer keys keep the interpreted expansion
+std::string jit_expand_source(const Model& m);
+bool jit_expand_build(Model* m);
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st);
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);

@@ -299,8 +299,11 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
   if (s != RC_OK) return s;
   if (tm) { timed->i_start = tm->n; tm->mark(); }
-  s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
-                                    reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
+  if (m.jit_fn)
+    s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
+  else
+    s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
+                                      reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
   if (s != RC_OK) return s;
   if (tm) { timed->i_expand = tm->n; tm->mark(); }
   int sorted = 0;
@@ -477,6 +480,8 @@ rc_status rc_model_create(const rc_model_desc* desc, rc_model** out) {
     return RC_E_CUDA;
   }
   m.key_slots = h.dense_slots + h.general_slots;
+  // large models get a generated expansion kernel; failure keeps the interpreted one
+  rc::jit_expand_build(&m);
   *out = mm;
   return RC_OK;
 }
@@ -508,9 +513,26 @@ rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
   out->n_threads_per_block = m.host.bs;
   out->n_blocks = m.host.n_blocks;
   out->program_bytes = m.dev_bytes;
+  out->expand_jit = m.jit_fn ? 1u : 0u;
   for (size_t a = 0; a < m.array_base.size() && a < 64; ++a) {
     out->array_base[a] = m.array_base[a];
     out->array_cells[a] = m.array_cells[a];
+  }
+  return RC_OK;
+}
+
+rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, size_t* len) {
+  if (!desc || !len || (cap && !buf)) return RC_E_INVALID;
+  rc::Model m;
+  std::vector<int32_t> general;
+  const rc_status st = rc::lower_model(desc, &m, &general);
+  if (st != RC_OK) return st;
+  const std::string src = rc::jit_expand_source(m);
+  *len = src.size();
+  if (cap) {
+    const size_t n = src.size() < cap - 1 ? src.size() : cap - 1;
+    std::memcpy(buf, src.data(), n);
+    buf[n] = 0;
   }
   return RC_OK;
 }
@@ -635,8 +657,11 @@ rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_
   auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
   rc_status s = cuda_status(rc::launch_init_result(res, st));
   if (s != RC_OK) return s;
-  s = cuda_status(rc::launch_expand(reinterpret_cast<const rc::DevModel*>(m.dev_program),
-                                    m.host.n_stmts, m.host.n_threads, m.has_deep_loops, keys_dev, res, st));
+  if (m.jit_fn)
+    s = cuda_status(rc::jit_expand_launch(m, keys_dev, res, st));
+  else
+    s = cuda_status(rc::launch_expand(reinterpret_cast<const rc::DevModel*>(m.dev_program),
+                                      m.host.n_stmts, m.host.n_threads, m.has_deep_loops, keys_dev, res, st));
   if (s != RC_OK) return s;
   return cuda_status(cudaMemcpyAsync(count_dev, &res->instances, 8, cudaMemcpyDeviceToDevice, st));
 }

@@ -112,3 +112,22 @@ def test_validation_key_overflow(rc):
     big = [Array("g", "global", (1 << 20, 1 << 20))]
     m = Model((1 << 20, 1, 1), (1024, 1, 1), big, [Stmt([Access(0, R, (tid.x, bid.x))])], n_phases=4)
     assert _status(rc, m) == rc.RC_E_KEY_OVERFLOW
+
+
+def test_generated_kernels_compile(rc, tmp_path):
+    """The expansion kernels generated for a few models compile for sm_103a."""
+    import shutil
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    deep = Model((2, 1, 1), (8, 1, 1), [Array("a", "shared", (64,))],
+                 [Stmt([Access(0, W, ((tid.x + it(0) + it(1) + it(2) + it(3) + it(4)) % 64,))],
+                       loops=[Loop(0, 2)] * 5)])
+    for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep]):
+        src = rc.rc_kernel_source(m)
+        assert "rc_expand_jit" in src
+        f = tmp_path / f"k{i}.cu"
+        f.write_text(src)
+        r = subprocess.run([nvcc, "-c", str(f), "-o", str(tmp_path / f"k{i}.o"), "-std=c++17",
+                            "-gencode", "arch=compute_103a,code=sm_103a"], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[:2000]
