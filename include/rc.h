@@ -299,7 +299,11 @@ rc_status rc_ticket_stage_times(rc_ticket ticket, rc_stage_times* out);
 
 /* Expansion only: writes the model's layout.key_slots keys to keys_dev
  * (padding slots hold 0xFFFF...FFFF) and the number of valid instances to
- * *count_dev (uint64).  workspace as for rc_check. */
+ * *count_dev (uint64).  Only accesses to arrays that some statement writes get
+ * a key: a cell that is never written holds no conflicting pair (the race
+ * needs a write: Abstract and Introduction), so
+ * the instances of read-only arrays are bounds-checked and counted but not
+ * emitted.  workspace as for rc_check. */
 rc_status rc_expand_keys(rc_model* m, void* workspace_dev, size_t workspace_bytes,
                          uint64_t* keys_dev, uint64_t* count_dev, void* stream);
 
@@ -322,7 +326,7 @@ rc_status rc_sort_keys(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint
  *
  * The scratch (histograms, look-back words, second key buffer) lives in one
  * static device array of this library sized for RC_SORT_STATIC_MAX_KEYS keys
- * (about 8.6 MB); every GPU that loads the library holds it until the process
+ * (about 12.8 MB); every GPU that loads the library holds it until the process
  * exits.  The call allocates nothing and calls no allocating routine; the
  * caller still passes the input and output buffers (device, n uint64 keys
  * each, distinct).  n > RC_SORT_STATIC_MAX_KEYS returns RC_E_UNSUPPORTED.

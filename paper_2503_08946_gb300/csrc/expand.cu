@@ -2,7 +2,8 @@
 //
 // One work unit = (statement, thread).  For a statement whose loops all have
 // constant trip counts ("dense") the key of iteration j, access a and thread g
-// goes to slot  slot_base + (j * n_acc + a) * T + g,  so the 32 lanes of a warp
+// goes to slot  slot_base + (j * n_key + k) * T + g  (k = the access's key index
+// among the accesses to written arrays),  so the 32 lanes of a warp
 // (consecutive g) store 32 consecutive keys; guard-false and out-of-bounds
 // instances leave the all-ones padding key.  Other statements are first counted
 // per unit (expand_count_kernel, run once when the model is created), and then
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) count_kernel(const DevModel* __restrict__
     const ThreadVars tv = thread_vars(M, g);
     uint64_t c = 0;
     walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
-      if (guards_hold(M, S, tv, it, term)) c += (uint64_t)S.n_acc;
+      if (guards_hold(M, S, tv, it, term)) c += (uint64_t)S.n_key;
     });
     counts[S.slot_base + g] = c;
   }

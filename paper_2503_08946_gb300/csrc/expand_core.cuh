@@ -120,12 +120,14 @@ __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const i
       }
       e = e * (uint64_t)ext + (uint64_t)v;
     }
+    const int kidx = __ldg(&A->key_idx);
+    if (kidx < 0) continue;   // array never written: bounds-checked and counted, no key
     uint64_t key = kSentinel;
     if (!bad) {
       const uint64_t cell = __ldg(&arr->base) + (__ldg(&arr->shared) ? c.tv.b : 0ull) * __ldg(&arr->cells) + e;
       key = (cell << M.cell_shift) | ((uint64_t)phase << M.phase_shift) | low | (uint64_t)kind;
     }
-    sink(a, key);
+    sink(kidx, key);
   }
   return true;
 }
@@ -162,13 +164,13 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
   const uint64_t T = M.n_threads;
   if (S.dense) {
     uint64_t slot = S.slot_base + g;
-    const uint64_t step_pt = (uint64_t)S.n_acc * T;
+    const uint64_t step_pt = (uint64_t)S.n_key * T;
     auto body = [&](const int64_t (&itv)[LA]) {
-      auto put = [&](int a, uint64_t key) { sink.put(slot + (uint64_t)a * T, key); };
+      auto put = [&](int kidx, uint64_t key) { sink.put(slot + (uint64_t)kidx * T, key); };
       if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
         count += (unsigned long long)S.n_acc;
       } else {
-        for (int a = 0; a < S.n_acc; ++a) sink.pad(slot + (uint64_t)a * T);
+        for (int kq = 0; kq < S.n_key; ++kq) sink.pad(slot + (uint64_t)kq * T);
       }
       slot += step_pt;
     };
@@ -176,9 +178,9 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
   } else {
     uint64_t off = M.unit_offset[S.slot_base + g];
     auto body = [&](const int64_t (&itv)[LA]) {
-      auto put = [&](int a, uint64_t key) { sink.put(off + (uint64_t)a, key); };
+      auto put = [&](int kidx, uint64_t key) { sink.put(off + (uint64_t)kidx, key); };
       if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
-        off += (uint64_t)S.n_acc;
+        off += (uint64_t)S.n_key;
         count += (unsigned long long)S.n_acc;
       }
     };
@@ -209,19 +211,17 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
   if (S.dense) {
     uint64_t j = 0;
     walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
-      uint64_t slot = S.slot_base + j * (uint64_t)S.n_acc * T + g;
+      const uint64_t slot = S.slot_base + j * (uint64_t)S.n_key * T + g;
       if (guards_hold(M, S, tv, it, term)) {
         const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
         for (int a = 0; a < S.n_acc; ++a) {
-          sink.put(slot, make_key(M, S, s, a, phase, tv, it, term, &res->oob_code));
-          slot += T;
+          const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+          const int kidx = M.accs[S.acc0 + a].key_idx;
+          if (kidx >= 0) sink.put(slot + (uint64_t)kidx * T, key);
         }
         count += (unsigned long long)S.n_acc;
       } else {
-        for (int a = 0; a < S.n_acc; ++a) {
-          sink.pad(slot);
-          slot += T;
-        }
+        for (int kq = 0; kq < S.n_key; ++kq) sink.pad(slot + (uint64_t)kq * T);
       }
       ++j;
     });
@@ -230,7 +230,12 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
     walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
       if (!guards_hold(M, S, tv, it, term)) return;
       const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
-      for (int a = 0; a < S.n_acc; ++a) sink.put(off++, make_key(M, S, s, a, phase, tv, it, term, &res->oob_code));
+      for (int a = 0; a < S.n_acc; ++a) {
+        const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+        const int kidx = M.accs[S.acc0 + a].key_idx;
+        if (kidx >= 0) sink.put(off + (uint64_t)kidx, key);
+      }
+      off += (uint64_t)S.n_key;
       count += (unsigned long long)S.n_acc;
     });
   }

@@ -204,18 +204,19 @@ struct Gen {
         << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc); key = ~0ull; }\n";
       o << in3 << "else key = ((" << cell << ") << " << m.host.cell_shift << ") | ((unsigned long long)ph << "
         << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind) << ";\n";
-      if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)a * T) << "] = key;\n";
-      else o << in3 << "keys[off + " << a << "] = key;\n";
+      if (A.key_idx < 0) o << in3 << "(void)key;\n";   // array never written: checked, no key
+      else if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)A.key_idx * T) << "] = key;\n";
+      else o << in3 << "keys[off + " << A.key_idx << "] = key;\n";
       o << in2 << "}\n";
     }
     o << in2 << "cnt += " << S.n_acc << ";\n";
-    if (!S.dense) o << in2 << "off += " << S.n_acc << ";\n";
+    if (!S.dense) o << in2 << "off += " << S.n_key << ";\n";
     o << ind << "}";
     if (S.dense) {
       o << " else {\n";
-      for (int a = 0; a < S.n_acc; ++a) o << in2 << "keys[slot + " << ulit((uint64_t)a * T) << "] = ~0ull;\n";
+      for (int kq = 0; kq < S.n_key; ++kq) o << in2 << "keys[slot + " << ulit((uint64_t)kq * T) << "] = ~0ull;\n";
       o << ind << "}\n";
-      o << ind << "slot += " << ulit((uint64_t)S.n_acc * T) << ";\n";
+      o << ind << "slot += " << ulit((uint64_t)S.n_key * T) << ";\n";
     } else {
       o << "\n";
     }

@@ -36,15 +36,16 @@ cudaError_t launch_hash(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;   // keys per onesweep tile
-constexpr int kRadix = 256;                            // bins of the widest digit (8 bits)
+constexpr int kMaxRadixBits = 11;
+constexpr int kMaxRadix = 1 << kMaxRadixBits;           // bins of the widest digit
 
 struct SortArgs {
   const uint64_t* keys_in;
   uint64_t* keys_out;
   uint64_t n;
   uint32_t shift, bits;
-  const unsigned long long* digit_offset;   // kRadix exclusive offsets of this pass
-  unsigned long long* lookback;             // n_tiles x kRadix status words
+  const unsigned long long* digit_offset;   // exclusive offsets of this pass's digits
+  unsigned long long* lookback;             // n_tiles x 2^radix_bits status words
   unsigned int* tile_counter;
   unsigned int epoch;                       // distinct per pass within one check
   unsigned int wait_epoch;                  // epoch the look-back accepts (== epoch in normal use)
@@ -53,10 +54,11 @@ struct SortArgs {
 };
 cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
                              cudaStream_t st);
-cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, uint32_t n_pass,
+cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, const SortPlan& sp,
                                  cudaStream_t st);
-cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t st);
-size_t sort_workspace_bytes(uint64_t n, uint32_t n_pass);
+// radix_bits: counters of the onesweep kernel (radix_bits_for(pass bits))
+cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t st);
+uint32_t radix_bits_for(uint32_t bits);
 
 // scan.cu
 constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)

@@ -264,6 +264,14 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.sort_lo = h.phase_shift;
   h.sort_hi = h.cell_shift + h.cell_bits;
 
+  // arrays that some statement writes; a cell of any other array has no write
+  // and cannot race, so its instances are counted and bounds-checked but make no key
+  std::vector<bool> written(d->n_arrays, false);
+  for (uint32_t s = 0; s < d->n_stmts; ++s)
+    for (uint32_t a = 0; a < d->stmts[s].n_accesses && d->stmts[s].accesses; ++a)
+      if (d->stmts[s].accesses[a].kind == RC_WRITE && d->stmts[s].accesses[a].array < d->n_arrays)
+        written[d->stmts[s].accesses[a].array] = true;
+
   // statements
   std::vector<DevStmt> stmts(d->n_stmts);
   std::vector<DevAccess> accs;
@@ -337,16 +345,20 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     D.row_phase = (int32_t)rows.size();
     put_point_row(phase);
     D.acc0 = (int32_t)accs.size();
+    int n_key = 0;
     for (uint32_t a = 0; a < S.n_accesses; ++a) {
       DevAccess da;
       da.array = (int32_t)S.accesses[a].array;
       da.kind = (int32_t)S.accesses[a].kind;
       da.ndims = (int32_t)idx[a].size();
       da.row0 = (int32_t)rows.size();
+      da.key_idx = written[da.array] ? n_key++ : -1;
+      da.pad = 0;
       for (auto& e : idx[a]) put_point_row(e);
       accs.push_back(da);
     }
     D.n_cache = n_cache;
+    D.n_key = n_key;
     D.term0 = (int32_t)terms.size();
     D.n_terms = (int32_t)b.terms.size();
     for (size_t q = 0; q < b.terms.size(); ++q) {
@@ -367,7 +379,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
         if (!mul_ok(it, (uint64_t)D.trips[l], &it)) return RC_E_UNSUPPORTED;
       D.n_iter = it;
       uint64_t slots;
-      if (!mul_ok(it, (uint64_t)S.n_accesses, &slots) || !mul_ok(slots, nt, &slots) ||
+      if (!mul_ok(it, (uint64_t)n_key, &slots) || !mul_ok(slots, nt, &slots) ||
           dense_slots + slots < dense_slots)
         return RC_E_UNSUPPORTED;
       D.slot_base = dense_slots;
@@ -421,7 +433,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
 void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp) {
   std::memset(sp, 0, sizeof(*sp));
   uint32_t dbits = digit_bits == 0 ? 8 : digit_bits;
-  if (dbits > 8) dbits = 8;
+  if (dbits > 11) dbits = 11;
   if (dbits < 4) dbits = 4;
   if (hi <= lo) return;
   uint32_t n = hi - lo;

@@ -75,6 +75,9 @@ struct DevAccess {
   int32_t kind;
   int32_t ndims;
   int32_t row0;    // first of ndims consecutive index rows
+  int32_t key_idx; // slot of its key among the statement's keyed accesses, -1 when the
+                   // array is never written (its cells cannot race: no key is made)
+  int32_t pad;
 };
 
 struct DevArray {
@@ -87,6 +90,8 @@ struct DevArray {
 
 struct DevStmt {
   int32_t n_loops, n_guards, n_acc, n_terms;
+  int32_t n_key;        // accesses that make keys (arrays some statement writes)
+  int32_t pad_k;
   int32_t row_lower[kMaxLoops];
   int32_t row_upper[kMaxLoops];
   int64_t step[kMaxLoops];
@@ -344,6 +349,12 @@ struct SortPlan {
   uint32_t shift[16];
   uint32_t bits[16];
 };
+// widest digit of a plan (for sizing the look-back words of its passes)
+inline uint32_t plan_max_bits(const SortPlan& sp) {
+  uint32_t b = 8;
+  for (uint32_t p = 0; p < sp.n_pass; ++p) b = sp.bits[p] > b ? sp.bits[p] : b;
+  return b;
+}
 
 struct WorkspacePlan {
   size_t result_off;      // DevResult

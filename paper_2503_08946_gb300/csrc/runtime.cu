@@ -162,14 +162,14 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
   off = align256(off + n * 8);
   p->zero_lo = off;
   p->hist_off = off;
-  off = align256(off + (size_t)16 * kRadix * 8);
+  off = align256(off + (size_t)16 * kMaxRadix * 8);
   p->lookback_off = off;
-  off = align256(off + (size_t)p->n_tiles * kRadix * 8);
+  off = align256(off + (size_t)p->n_tiles * ((size_t)1 << plan_max_bits(p->sort)) * 8);
   p->tilectr_off = off;
   off = align256(off + 16 * sizeof(unsigned int));
   p->zero_hi = off;
   p->digoff_off = off;
-  off = align256(off + (size_t)16 * kRadix * 8);
+  off = align256(off + (size_t)16 * kMaxRadix * 8);
   p->summ_off = off;   // one scan summary per warp
   off = align256(off + (size_t)p->scan_warps * sizeof(Summary));
   p->group_off = off;
@@ -210,7 +210,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
   auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
   rc_status s = cuda_status(rc::launch_histogram(bufs[0], p.n_keys, p.sort, hist, st));
   if (s != RC_OK) return s;
-  s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort.n_pass, st));
+  s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort, st));
   if (s != RC_OK) return s;
   if (tm) tm->mark();
   int cur = 0;
@@ -221,7 +221,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
     a.n = p.n_keys;
     a.shift = p.sort.shift[k];
     a.bits = p.sort.bits[k];
-    a.digit_offset = digoff + (size_t)k * rc::kRadix;
+    a.digit_offset = digoff + (size_t)k * rc::kMaxRadix;
     a.lookback = reinterpret_cast<unsigned long long*>(ws + p.lookback_off);
     a.tile_counter = reinterpret_cast<unsigned int*>(ws + p.tilectr_off) + k;
     a.epoch = k + 1;
@@ -229,7 +229,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
     a.wait_epoch = (test_flags & RC_TEST_STALL_LOOKBACK) ? (k + 1) ^ 0x8000u : k + 1;
     a.spin_limit = spin_limit;
     a.err = &res->err;
-    s = cuda_status(rc::launch_onesweep(a, st));
+    s = cuda_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), st));
     if (s != RC_OK) return s;
     if (tm) tm->mark();
     cur = 1 - cur;
@@ -672,10 +672,10 @@ rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes)
   rc::plan_sort(0, 64, digit_bits, &sp);
   const uint64_t n_tiles = (n + rc::kSortTile - 1) / rc::kSortTile;
   size_t off = align256(sizeof(rc::DevResult));
-  off = align256(off + (size_t)16 * rc::kRadix * 8);       // histograms
-  off = align256(off + (size_t)n_tiles * rc::kRadix * 8);  // look-back
-  off = align256(off + 16 * sizeof(unsigned int));         // tile counters
-  off = align256(off + (size_t)16 * rc::kRadix * 8);       // digit offsets
+  off = align256(off + (size_t)16 * rc::kMaxRadix * 8);                                    // histograms
+  off = align256(off + (size_t)n_tiles * ((size_t)1 << rc::kMaxRadixBits) * 8);             // look-back
+  off = align256(off + 16 * sizeof(unsigned int));                                         // tile counters
+  off = align256(off + (size_t)16 * rc::kMaxRadix * 8);                                    // digit offsets
   off = align256(off + n * 8);                             // ping-pong buffer
   *bytes = off;
   return RC_OK;
@@ -700,14 +700,14 @@ rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, 
   off = align256(off + sizeof(rc::DevResult));
   p.zero_lo = off;
   p.hist_off = off;
-  off = align256(off + (size_t)16 * rc::kRadix * 8);
+  off = align256(off + (size_t)16 * rc::kMaxRadix * 8);
   p.lookback_off = off;
-  off = align256(off + (size_t)p.n_tiles * rc::kRadix * 8);
+  off = align256(off + (size_t)p.n_tiles * ((size_t)1 << rc::kMaxRadixBits) * 8);
   p.tilectr_off = off;
   off = align256(off + 16 * sizeof(unsigned int));
   p.zero_hi = off;
   p.digoff_off = off;
-  off = align256(off + (size_t)16 * rc::kRadix * 8);
+  off = align256(off + (size_t)16 * rc::kMaxRadix * 8);
   const size_t pong = off;
   if (n == 0) return RC_OK;
   rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));

@@ -5,15 +5,19 @@
 // join is a grouping of keys by (cell, phase), done by sorting on those bits.
 // Design (after Adinets & Merrill, "Onesweep: a faster least significant digit
 // radix sort for GPUs", 2022): one upfront pass counts the digits of every pass;
-// then each pass is a single kernel in which a tile of kSortTile keys (1) ranks
-// its keys per digit with warp-level __match_any_sync multi-split into per-warp
-// shared-memory histograms, (2) publishes its per-digit counts, (3) obtains the
-// exclusive per-digit prefix of all earlier tiles by decoupled look-back over
-// their published status words, and (4) scatters the keys, staged in shared
-// memory in digit order so stores of one digit are contiguous.  Tiles are taken
-// in launch order from an atomic counter, so every tile waited on is already
-// running or finished; every wait is bounded by spin_limit and reports
-// kErrLookbackTimeout instead of hanging.
+// then each pass is a single kernel in which a tile of kSortTile keys
+//   (1) ranks its keys per digit, stably: per item (32 keys of a warp) the
+//       lanes sharing a digit are found with __match_any_sync, and the lowest
+//       of them reads the warp's 16-bit digit counter (the group's base rank)
+//       and adds the group size to it;
+//   (2) publishes its per-digit counts, (3) obtains the exclusive per-digit
+//       prefix of all earlier tiles by decoupled look-back over their status
+//       words, and (4) scatters the keys, staged in shared memory in digit
+//       order so the stores of one digit are contiguous.
+// The kernel is templated on the radix (2^8 .. 2^11 bins) so that wide digits
+// take fewer passes.  Tiles are taken in launch order from an atomic counter,
+// so every tile waited on is already running or finished; every wait is
+// bounded by spin_limit and reports kErrLookbackTimeout instead of hanging.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -38,97 +42,121 @@ __device__ __forceinline__ unsigned int lanemask_lt() {
 }
 
 // ---------------------------------------------------------------------------
-// upfront digit histograms of every pass
+// upfront digit histograms of every pass (shared-memory counters, one section
+// of 2^bits[p] per pass)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) histogram_kernel(const uint64_t* __restrict__ keys, uint64_t n,
                                                         SortPlan sp, unsigned long long* __restrict__ hist) {
-  __shared__ unsigned int h[16][kRadix];
-  for (int i = threadIdx.x; i < 16 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+  extern __shared__ unsigned int h[];
+  unsigned base[16];
+  unsigned tot = 0;
+  for (uint32_t p = 0; p < sp.n_pass; ++p) {
+    base[p] = tot;
+    tot += 1u << sp.bits[p];
+  }
+  for (unsigned i = threadIdx.x; i < tot; i += blockDim.x) h[i] = 0;
   __syncthreads();
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
     for (uint32_t p = 0; p < sp.n_pass; ++p) {
       const unsigned int d = (unsigned int)(k >> sp.shift[p]) & ((1u << sp.bits[p]) - 1u);
-      atomicAdd(&h[p][d], 1u);
+      atomicAdd(&h[base[p] + d], 1u);
     }
   }
   __syncthreads();
   for (uint32_t p = 0; p < sp.n_pass; ++p)
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-      if (h[p][d]) atomicAdd(&hist[p * kRadix + d], (unsigned long long)h[p][d]);
+    for (unsigned d = threadIdx.x; d < (1u << sp.bits[p]); d += blockDim.x)
+      if (h[base[p] + d]) atomicAdd(&hist[p * kMaxRadix + d], (unsigned long long)h[base[p] + d]);
 }
 
-__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long v, unsigned long long* total) {
+// Exclusive scan of up to kMaxRadix counts by 256 threads (contiguous digits per thread).
+__device__ __forceinline__ void block_excl_scan_digits(const unsigned long long* in, unsigned long long* out,
+                                                       int n_digits) {
   __shared__ unsigned long long wt[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long x = v;
+  const int dpt = (n_digits + 255) / 256;
+  const int d0 = threadIdx.x * dpt;
+  unsigned long long s = 0;
+  for (int k = 0; k < dpt; ++k)
+    if (d0 + k < n_digits) s += in[d0 + k];
+  unsigned long long x = s;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) wt[w] = x;
   __syncthreads();
-  unsigned long long base = 0, tot = 0;
-  for (int i = 0; i < 8; ++i) {
-    if (i < w) base += wt[i];
-    tot += wt[i];
-  }
-  __syncthreads();
-  if (total) *total = tot;
-  return base + x - v;
+  unsigned long long base = 0;
+  for (int i = 0; i < w; ++i) base += wt[i];
+  unsigned long long run = base + x - s;
+  for (int k = 0; k < dpt; ++k)
+    if (d0 + k < n_digits) {
+      out[d0 + k] = run;
+      run += in[d0 + k];
+    }
 }
 
 __global__ void __launch_bounds__(256) digit_offsets_kernel(const unsigned long long* __restrict__ hist,
-                                                            unsigned long long* __restrict__ digoff) {
+                                                            unsigned long long* __restrict__ digoff, SortPlan sp) {
   const int p = blockIdx.x;
-  const unsigned long long v = hist[p * kRadix + threadIdx.x];
-  digoff[p * kRadix + threadIdx.x] = block_excl_scan256(v, nullptr);
+  block_excl_scan_digits(hist + p * kMaxRadix, digoff + p * kMaxRadix, 1 << sp.bits[p]);
 }
 
 // ---------------------------------------------------------------------------
-// one onesweep pass
+// one onesweep pass with 2^RB counters per warp
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(SortArgs a) {
+template <int RB>
+constexpr size_t onesweep_smem() {
+  // keys | per-warp 16-bit counters | per-digit scatter delta (u64) | per-digit tile offset (u32)
+  return (size_t)kSortTile * 8 + (size_t)(kSortThreads / 32) * (1 << RB) * 2 + (size_t)(1 << RB) * 8 +
+         (size_t)(1 << RB) * 4;
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel(SortArgs a) {
+  constexpr int R = 1 << RB;
+  constexpr int DPT = R / kSortThreads;   // digits per thread in the per-digit phases
   constexpr int kWarps = kSortThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  unsigned short* cnt16 = reinterpret_cast<unsigned short*>(s_keys + kSortTile);   // [kWarps][R]
+  unsigned int* cnt32 = reinterpret_cast<unsigned int*>(cnt16);
+  unsigned long long* delta = reinterpret_cast<unsigned long long*>(cnt16 + kWarps * R);   // [R]
+  unsigned int* tile_excl = reinterpret_cast<unsigned int*>(delta + R);                    // [R]
   __shared__ unsigned int s_tile;
-  __shared__ unsigned int warp_hist[kWarps][kRadix];
-  __shared__ unsigned int tile_excl[kRadix];
-  __shared__ unsigned long long g_base[kRadix];
-  __shared__ uint64_t s_keys[kSortTile];
+  __shared__ unsigned int s_wt[kWarps];
 
   const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-  for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&warp_hist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kWarps * R / 2; i += kSortThreads) cnt32[i] = 0;
   __syncthreads();
   const uint64_t tile = s_tile;
   if (tile >= n_tiles) return;
 
   const unsigned int dmask = (1u << a.bits) - 1u;
   const uint64_t wbase = tile * kSortTile + (uint64_t)w * (32 * kSortItems);
+  const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
   uint64_t k[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-    k[i] = pos < a.n ? a.keys_in[pos] : ~0ull;
+    k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
   }
 
-  // Warp-level multi-split ranking, stable in (item, lane) order.  First the
-  // peer masks of all items (independent __match_any_sync, so their latencies
-  // overlap; an out-of-range lane gets a digit no other lane has), then one
-  // pass over the items that turns the masks into ranks through the warp's
-  // shared-memory digit counters (the lowest peer updates the counter).
-  const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
+  // (1) ranking: peer masks of all items first (independent), then one pass
+  // that turns them into ranks through the warp's counters
   unsigned int peers[kSortItems];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
-    if (!full_tile && wbase + (uint64_t)i * 32 + lane >= a.n) d = 0x100u | lane;
+    if (!full_tile && wbase + (uint64_t)i * 32 + lane >= a.n) d = (unsigned int)R + lane;   // matches no one
     peers[i] = __match_any_sync(0xffffffffu, d);
   }
-  unsigned int r[kSortItems];
+  unsigned short r[kSortItems];
   const unsigned int lt = lanemask_lt();
+  unsigned short* my_cnt = cnt16 + w * R;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
@@ -136,113 +164,165 @@ __global__ void __launch_bounds__(kSortThreads, 3) onesweep_kernel(SortArgs a) {
     const unsigned int leader = __ffs(peers[i]) - 1;
     unsigned int prev = 0;
     if (lane == leader && valid) {
-      prev = warp_hist[w][d];
-      warp_hist[w][d] = prev + __popc(peers[i]);
+      // the leaders of one item hold distinct digits, so their 16-bit
+      // counters are distinct and plain loads and stores suffice
+      prev = my_cnt[d];
+      my_cnt[d] = (unsigned short)(prev + __popc(peers[i]));
     }
     prev = __shfl_sync(0xffffffffu, prev, leader);
-    r[i] = prev + __popc(peers[i] & lt);
+    r[i] = (unsigned short)(prev + __popc(peers[i] & lt));
     __syncwarp();
   }
   __syncthreads();
 
-  // per digit: exclusive offsets of the warps, the tile's count, and its publication
-  const int dg = threadIdx.x;   // kSortThreads == kRadix
-  unsigned int cnt = 0;
+  // (2) per digit: tile count, publication, and the tile's exclusive digit offsets
+  unsigned int cnt[DPT];
+  unsigned int tsum = 0;
 #pragma unroll
-  for (int ww = 0; ww < kWarps; ++ww) {
-    const unsigned int c = warp_hist[ww][dg];
-    warp_hist[ww][dg] = cnt;
-    cnt += c;
+  for (int q = 0; q < DPT; ++q) {
+    const int dg = threadIdx.x * DPT + q;
+    unsigned int c = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) c += cnt16[ww * R + dg];
+    cnt[q] = c;
+    tsum += c;
   }
   volatile unsigned long long* lb = a.lookback;
-  if (tile == 0) lb[dg] = status_word(kFlagPrefix, a.epoch, cnt);
-  else lb[tile * kRadix + dg] = status_word(kFlagAggregate, a.epoch, cnt);
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int dg = threadIdx.x * DPT + q;
+    lb[tile * R + dg] = status_word(tile == 0 ? kFlagPrefix : kFlagAggregate, a.epoch, cnt[q]);
+  }
   {
-    unsigned long long tot;
-    tile_excl[dg] = (unsigned int)block_excl_scan256(cnt, &tot);
+    unsigned int x = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wt[w] = x;
+    __syncthreads();
+    unsigned int base = 0;
+    for (int i = 0; i < w; ++i) base += s_wt[i];
+    unsigned int run = base + x - tsum;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int dg = threadIdx.x * DPT + q;
+      tile_excl[dg] = run;
+      // staging offset of warp ww's keys of digit dg = tile offset + earlier warps' counts
+      unsigned int wrun = run;
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const unsigned int c = cnt16[ww * R + dg];
+        cnt16[ww * R + dg] = (unsigned short)wrun;
+        wrun += c;
+      }
+      run += cnt[q];
+    }
   }
   __syncthreads();
 
   // stage the keys in digit order (stable)
+  const unsigned short* my_off = cnt16 + w * R;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-    if (pos < a.n) {
+    if (full_tile || wbase + (uint64_t)i * 32 + lane < a.n) {
       const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
-      s_keys[tile_excl[d] + warp_hist[w][d] + r[i]] = k[i];
+      s_keys[my_off[d] + r[i]] = k[i];
     }
   }
 
-  // decoupled look-back for digit dg
-  unsigned long long excl = 0;
-  if (tile > 0) {
-    uint64_t j = tile - 1;
-    unsigned long long spins = 0;
-    while (true) {
-      const unsigned long long s = lb[j * kRadix + dg];
-      const unsigned long long flag = s >> 62;
-      const unsigned int ep = (unsigned int)((s >> 46) & 0xFFFFu);
-      if (flag == 0 || ep != (a.wait_epoch & 0xFFFFu)) {
-        if (++spins > a.spin_limit) {
-          atomicOr(a.err, (unsigned int)kErrLookbackTimeout);
-          break;
+  // (3) decoupled look-back for this thread's digits
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int dg = threadIdx.x * DPT + q;
+    unsigned long long excl = 0;
+    if (tile > 0) {
+      uint64_t j = tile - 1;
+      unsigned long long spins = 0;
+      while (true) {
+        const unsigned long long s = lb[j * R + dg];
+        const unsigned long long flag = s >> 62;
+        const unsigned int ep = (unsigned int)((s >> 46) & 0xFFFFu);
+        if (flag == 0 || ep != (a.wait_epoch & 0xFFFFu)) {
+          if (++spins > a.spin_limit) {
+            atomicOr(a.err, (unsigned int)kErrLookbackTimeout);
+            break;
+          }
+          continue;
         }
-        continue;
+        excl += s & kCountMask;
+        if (flag == kFlagPrefix || j == 0) break;
+        --j;
       }
-      excl += s & kCountMask;
-      if (flag == kFlagPrefix || j == 0) break;
-      --j;
+      lb[tile * R + dg] = status_word(kFlagPrefix, a.epoch, excl + cnt[q]);
     }
-    lb[tile * kRadix + dg] = status_word(kFlagPrefix, a.epoch, excl + cnt);
+    // output position of a staged key = delta[digit] + staged position
+    delta[dg] = a.digit_offset[dg] + excl - tile_excl[dg];
   }
-  g_base[dg] = a.digit_offset[dg] + excl;
   __syncthreads();
 
-  // scatter: consecutive staged keys of one digit go to consecutive addresses
+  // (4) scatter: consecutive staged keys of one digit go to consecutive addresses
   const uint64_t t0 = tile * kSortTile;
-  const int n_here = (int)((a.n - t0) < (uint64_t)kSortTile ? (a.n - t0) : (uint64_t)kSortTile);
+  const int n_here = full_tile ? kSortTile : (int)(a.n - t0);
   for (int pos = threadIdx.x; pos < n_here; pos += kSortThreads) {
     const uint64_t key = s_keys[pos];
     const unsigned int dd = (unsigned int)(key >> a.shift) & dmask;
-    a.keys_out[g_base[dd] + (unsigned long long)(pos - (int)tile_excl[dd])] = key;
+    a.keys_out[delta[dd] + (unsigned long long)pos] = key;
   }
+}
+
+template <int RB>
+cudaError_t launch_rb(const SortArgs& a, cudaStream_t st) {
+  static bool attr_set = false;
+  constexpr size_t smem = onesweep_smem<RB>();
+  if (!attr_set) {
+    cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    attr_set = true;
+  }
+  const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
+  onesweep_kernel<RB><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
+uint32_t radix_bits_for(uint32_t bits) { return bits <= 8 ? 8 : bits; }
+
 cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
                              cudaStream_t st) {
   if (n == 0 || sp.n_pass == 0) return cudaSuccess;
+  size_t smem = 0;
+  for (uint32_t p = 0; p < sp.n_pass; ++p) smem += (size_t)4 << sp.bits[p];
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(histogram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kMaxRadix * 4);
+    attr_set = true;
+  }
   uint64_t g = (n + 255) / 256;
   if (g > 152ull * 8) g = 152ull * 8;
-  histogram_kernel<<<(unsigned)g, 256, 0, st>>>(keys, n, sp, hist);
+  histogram_kernel<<<(unsigned)g, 256, smem, st>>>(keys, n, sp, hist);
   return cudaGetLastError();
 }
 
-cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, uint32_t n_pass,
+cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, const SortPlan& sp,
                                  cudaStream_t st) {
-  if (n_pass == 0) return cudaSuccess;
-  digit_offsets_kernel<<<n_pass, 256, 0, st>>>(hist, digoff);
+  if (sp.n_pass == 0) return cudaSuccess;
+  digit_offsets_kernel<<<sp.n_pass, 256, 0, st>>>(hist, digoff, sp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_onesweep(const SortArgs& a, cudaStream_t st) {
+cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  static bool carveout_set = false;
-  if (!carveout_set) {
-    // as much shared memory as possible: 3 resident blocks of ~44 KB per SM
-    cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    carveout_set = true;
+  switch (radix_bits) {
+    case 8: return launch_rb<8>(a, st);
+    case 9: return launch_rb<9>(a, st);
+    case 10: return launch_rb<10>(a, st);
+    case 11: return launch_rb<11>(a, st);
+    default: return cudaErrorInvalidValue;
   }
-  const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
-  onesweep_kernel<<<(unsigned)n_tiles, kSortThreads, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-size_t sort_workspace_bytes(uint64_t n, uint32_t n_pass) {
-  const uint64_t n_tiles = (n + kSortTile - 1) / kSortTile;
-  return (size_t)n_pass * kRadix * 8 * 2 + (size_t)n_tiles * kRadix * 8 + 256;
 }
 
 }  // namespace rc

@@ -21,10 +21,10 @@ constexpr size_t kStaticTiles = (kStaticMaxKeys + rc::kSortTile - 1) / rc::kSort
 // layout: result record | digit histograms | look-back words | tile counters | digit offsets | second key buffer
 constexpr size_t kOffResult = 0;
 constexpr size_t kOffHist = 256;
-constexpr size_t kOffLookback = kOffHist + (size_t)16 * rc::kRadix * 8;
-constexpr size_t kOffTileCtr = kOffLookback + kStaticTiles * rc::kRadix * 8;
+constexpr size_t kOffLookback = kOffHist + (size_t)16 * rc::kMaxRadix * 8;
+constexpr size_t kOffTileCtr = kOffLookback + kStaticTiles * ((size_t)1 << rc::kMaxRadixBits) * 8;
 constexpr size_t kOffDigoff = kOffTileCtr + 256;
-constexpr size_t kOffPong = kOffDigoff + (size_t)16 * rc::kRadix * 8;
+constexpr size_t kOffPong = kOffDigoff + (size_t)16 * rc::kMaxRadix * 8;
 constexpr size_t kScratchBytes = kOffPong + kStaticMaxKeys * 8;
 static_assert(kOffLookback % 256 == 0 && kOffTileCtr % 256 == 0 && kOffDigoff % 256 == 0 &&
                   kOffPong % 256 == 0,
@@ -75,7 +75,7 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
   if (st == RC_OK) st = as_status(rc::launch_init_result(res, cs));
   if (st == RC_OK) st = as_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, cs));
   if (st == RC_OK) st = as_status(rc::launch_histogram(keys_out, n, sp, hist, cs));
-  if (st == RC_OK) st = as_status(rc::launch_digit_offsets(hist, digoff, sp.n_pass, cs));
+  if (st == RC_OK) st = as_status(rc::launch_digit_offsets(hist, digoff, sp, cs));
   uint64_t* bufs[2] = {keys_out, pong};
   int cur = 0;
   for (uint32_t k = 0; k < sp.n_pass && st == RC_OK; ++k) {
@@ -85,14 +85,14 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
     a.n = n;
     a.shift = sp.shift[k];
     a.bits = sp.bits[k];
-    a.digit_offset = digoff + (size_t)k * rc::kRadix;
+    a.digit_offset = digoff + (size_t)k * rc::kMaxRadix;
     a.lookback = reinterpret_cast<unsigned long long*>(s + kOffLookback);
     a.tile_counter = reinterpret_cast<unsigned int*>(s + kOffTileCtr) + k;
     a.epoch = k + 1;
     a.wait_epoch = k + 1;
     a.spin_limit = 1ull << 20;
     a.err = &res->err;
-    st = as_status(rc::launch_onesweep(a, cs));
+    st = as_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), cs));
     cur = 1 - cur;
   }
   if (st == RC_OK && cur == 1) st = as_status(cudaMemcpyAsync(keys_out, pong, n * 8, cudaMemcpyDeviceToDevice, cs));
