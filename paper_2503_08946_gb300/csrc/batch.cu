@@ -1,0 +1,137 @@
+// Batched check: many models in one pipeline.
+//
+// The models of a batch are checked together instead of one pipeline per
+// model.  Every model keeps its own lowered program; the batch gives each model
+// its own range of cells, so that the keys of all models can be sorted and
+// scanned as one array:
+//
+//   batch key = [model's first batch cell + cell | phase | block | thread | kind]
+//
+// with the phase, block and thread fields as wide as the widest model's.  A
+// racy cell of the shared scan is charged to the model whose cell range holds
+// it, and the witness kernels run once per model (blockIdx.y), on the first
+// racy cell of that model.  Models whose combined fields would not fit in 63
+// bits go to separate packs, each checked by its own pipeline in turn.
+//
+// Expansion is one persistent kernel over a work queue: a unit is (model,
+// statement, chunk of kExpandThreads threads), and blocks take units in
+// groups from an atomic counter until the queue is empty.
+#include <cuda_runtime.h>
+
+#include "expand_core.cuh"
+#include "kernels.h"
+
+namespace rc {
+
+namespace {
+
+constexpr int kUnitsPerGrab = 8;
+static_assert(kExpandThreadsHost == kExpandThreads, "host and device chunk sizes agree");
+
+// Keys are re-packed from the model's layout into the batch layout.
+struct BatchSink {
+  uint64_t* keys;
+  uint64_t cell_base;
+  uint32_t mcs, mps, mbs;            // model field shifts (thread field at bit 1)
+  uint64_t pm, bm, tm;               // model field masks
+  uint32_t bcs, bps, bbs;            // batch field shifts
+  __device__ __forceinline__ void put(uint64_t i, uint64_t key) {
+    if (key != kSentinel) {
+      const uint64_t cell = key >> mcs;
+      const uint64_t ph = (key >> mps) & pm, b = (key >> mbs) & bm, t = (key >> 1) & tm;
+      key = ((cell_base + cell) << bcs) | (ph << bps) | (b << bbs) | (t << 1) | (key & 1ull);
+    }
+    keys[i] = key;
+  }
+  __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
+};
+
+__global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchArgs a) {
+  __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
+  __shared__ int64_t s_cache[kFastCache * kExpandThreads];
+  __shared__ unsigned long long s_u;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_u = atomicAdd(a.queue, (unsigned long long)kUnitsPerGrab);
+    __syncthreads();
+    const uint64_t u0 = s_u;
+    if (u0 >= a.n_units) break;
+    const uint64_t u1 = min(a.n_units, u0 + kUnitsPerGrab);
+    for (uint64_t u = u0; u < u1; ++u) {
+      // the model of unit u
+      uint32_t lo = 0, hi = a.n_models;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a.models[mid].unit_base <= u) lo = mid;
+        else hi = mid;
+      }
+      const BatchModel& B = a.models[lo];
+      const uint64_t local = u - B.unit_base;
+      const uint32_t s = (uint32_t)(local / B.n_chunks);
+      const uint64_t g = (local - (uint64_t)s * B.n_chunks) * kExpandThreads + threadIdx.x;
+      const DevModel& M = *B.dm;
+      DevResult* res = a.res + lo;
+      unsigned long long count = 0;
+      if (g < B.n_threads) {
+        BatchSink sink;
+        sink.keys = a.keys + B.key_base;
+        sink.cell_base = B.cell_base;
+        sink.mcs = B.cell_shift;
+        sink.mps = B.phase_shift;
+        sink.mbs = B.block_shift;
+        sink.pm = (1ull << B.phase_bits) - 1;
+        sink.bm = (1ull << B.block_bits) - 1;
+        sink.tm = (1ull << B.thread_bits) - 1;
+        sink.bcs = a.cell_shift;
+        sink.bps = a.phase_shift;
+        sink.bbs = a.block_shift;
+        const DevStmt& S = M.stmts[s];
+        if (S.n_loops > kFastLoops) {
+          expand_unit_generic(M, s, g, res, count, sink);
+        } else {
+          FastCtx c;
+          c.M = B.dm;
+          c.S = &S;
+          c.tv = thread_vars(M, g);
+          c.tval = s_tval + threadIdx.x;
+          c.cache = s_cache + threadIdx.x;
+          expand_unit_dispatch(c, s, g, res, count, sink);
+        }
+      }
+      count = warp_sum(count);
+      if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
+      __syncthreads();   // the shared term columns are reused by the next unit
+    }
+  }
+}
+
+// Errors of a pack's shared stages (sort look-back, scan) reach every model.
+__global__ void batch_errors_kernel(const DevResult* pack, DevResult* res, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned e = pack->err;
+  if (i < n && e) res[i].err |= e;
+}
+
+}  // namespace
+
+cudaError_t launch_batch_errors(const DevResult* pack, DevResult* res, uint32_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  batch_errors_kernel<<<(n + 127) / 128, 128, 0, st>>>(pack, res, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_expand(const BatchArgs& a, cudaStream_t st) {
+  if (a.n_units == 0) return cudaSuccess;
+  int dev = 0, sms = 152, per_sm = 4;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_expand_kernel, kExpandThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  const uint64_t need = (a.n_units + kUnitsPerGrab - 1) / kUnitsPerGrab;
+  if (grid > need) grid = need;
+  batch_expand_kernel<<<(unsigned)grid, kExpandThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rc

@@ -16,6 +16,30 @@ size_t scan_u64_temp_bytes(uint64_t n);
 cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,
                                uint64_t* total_dev, cudaStream_t st);
 
+// batch.cu
+constexpr int kExpandThreadsHost = 128;   // == kExpandThreads of expand_core.cuh
+struct BatchModel {              // one model of a batch (device table entry)
+  const DevModel* dm;
+  uint64_t key_base;             // first slot of the model's keys in the batch key buffer
+  uint64_t cell_base;            // first batch cell of the model
+  uint64_t unit_base;            // first expansion unit of the model
+  uint64_t n_threads;
+  uint32_t n_stmts, n_chunks;    // statements, thread chunks per statement
+  uint32_t cell_shift, phase_shift, block_shift;   // the model's key layout
+  uint32_t phase_bits, block_bits, thread_bits;
+};
+struct BatchArgs {
+  const BatchModel* models;
+  uint32_t n_models;
+  uint64_t n_units;
+  unsigned long long* queue;     // starts at 0
+  uint64_t* keys;                // batch key buffer
+  DevResult* res;                // one per model
+  uint32_t cell_shift, phase_shift, block_shift;   // batch key layout
+};
+cudaError_t launch_batch_expand(const BatchArgs& a, cudaStream_t st);
+cudaError_t launch_batch_errors(const DevResult* pack, DevResult* res, uint32_t n, cudaStream_t st);
+
 // hash.cu
 struct HashArgs {
   unsigned long long* gkey;    // group table keys (cell, phase), kEmpty = free
@@ -68,13 +92,19 @@ struct ScanArgs {
   uint64_t n;
   uint32_t cell_shift, phase_shift, block_shift, thread_shift;
   uint32_t phase_bits, block_bits, thread_bits;
-  Summary* summaries;     // one per warp
-  uint32_t n_warps;
-  DevResult* res;
-  unsigned int* groups;   // (1 << phase_bits) x 5 words for the witness
+  uint32_t n_warps;                    // warps of the cell scan
+  DevResult* res;                      // the result, or one per model of a batch
+  unsigned int* err;                   // error flags of the whole check
+  unsigned int* groups;                // per result: (1 << phase_bits) x 5 words for the witness
+  unsigned long long* long_list;       // first positions of cells handed to the long-cell pass
+  unsigned long long* long_count;      // starts at 0
+  uint64_t long_cap;                   // scan_long_capacity(n, n_warps)
+  const uint64_t* cell_base;           // batch: first batch cell of each model (ascending)
+  uint32_t n_models;                   // batch: number of models (0 = single model)
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);
-cudaError_t launch_init_result(DevResult* res, cudaStream_t st);
+cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n = 1);
+uint64_t scan_long_capacity(uint64_t n, uint32_t n_warps);
 
 }  // namespace rc

@@ -1,6 +1,6 @@
 // Internal data structures of the race checker: the lowered model program that
 // the expansion kernels interpret, the device-side result record, the
-// workspace plan and the segment-summary monoid of the scan.
+// workspace plan and the cell-piece algebra of the long-cell scan.
 #pragma once
 
 #include <cstddef>
@@ -155,6 +155,7 @@ enum DevError : unsigned int {
   kErrLookbackTimeout = 1u,
   kErrHashTimeout = 2u,
   kErrHashFull = 4u,
+  kErrScanLongFull = 8u,
 };
 
 // packed out-of-bounds code: stmt (12 bits) | access (6) | gtid (42) | dimcode (3)
@@ -201,7 +202,7 @@ RC_HD int64_t wadd(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint6
 RC_HD int64_t wmul(int64_t a, int64_t b) { return (int64_t)((uint64_t)a * (uint64_t)b); }
 
 // ---------------------------------------------------------------------------
-// segment-summary monoid of the scan
+// cell pieces of the long-cell scan
 //
 // Sorted keys are grouped by cell and, inside a cell, by (cell, phase) "sub"
 // groups.  A cell is racy iff
@@ -210,9 +211,8 @@ RC_HD int64_t wmul(int64_t a, int64_t b) { return (int64_t)((uint64_t)a * (uint6
 //                                  and a write),
 // the cell-level form of the pair rule (a multi-block cell races iff it has a
 // write; a single-block cell races iff two threads meet in one barrier
-// interval with a write).  A Summary describes any contiguous run of keys: the
-// piece of its first cell (L), the piece of its last cell (R), and the racy
-// cells strictly inside; combine() concatenates two runs.
+// interval with a write).  A CellPiece describes a contiguous run of keys of
+// one cell; piece_combine() concatenates two runs of the same cell.
 // ---------------------------------------------------------------------------
 struct SubAgg {
   uint32_t mint, maxt, anyW, pad;
@@ -280,67 +280,6 @@ RC_HD CellPiece piece_combine(const CellPiece& X, const CellPiece& Y) {
   return r;
 }
 
-struct Summary {
-  uint32_t empty;
-  uint32_t single_cell;    // L and R are the same piece
-  uint64_t count;          // racy cells strictly inside (neither L's nor R's cell)
-  uint64_t minstart;       // smallest start of those racy cells, ~0 if none
-  CellPiece L, R;
-};
-
-RC_HD Summary summary_empty() {
-  Summary s;
-  s.empty = 1; s.single_cell = 0; s.count = 0; s.minstart = ~0ull;
-  s.L = CellPiece{}; s.R = CellPiece{};
-  return s;
-}
-
-RC_HD uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-
-RC_HD Summary summary_combine(const Summary& A, const Summary& B) {
-  if (A.empty) return B;
-  if (B.empty) return A;
-  Summary r;
-  r.empty = 0;
-  if (A.R.cell == B.L.cell) {
-    CellPiece M = piece_combine(A.R, B.L);
-    if (A.single_cell && B.single_cell) {
-      r.single_cell = 1; r.L = M; r.R = M; r.count = 0; r.minstart = ~0ull;
-    } else if (A.single_cell) {
-      r.single_cell = 0; r.L = M; r.R = B.R; r.count = B.count; r.minstart = B.minstart;
-    } else if (B.single_cell) {
-      r.single_cell = 0; r.L = A.L; r.R = M; r.count = A.count; r.minstart = A.minstart;
-    } else {
-      bool mr = piece_racy(M);
-      r.single_cell = 0; r.L = A.L; r.R = B.R;
-      r.count = A.count + B.count + (mr ? 1 : 0);
-      r.minstart = umin64(A.minstart, umin64(B.minstart, mr ? M.start : ~0ull));
-    }
-  } else {
-    r.single_cell = 0;
-    r.L = A.L;
-    r.R = B.R;
-    bool ar = !A.single_cell && piece_racy(A.R);
-    bool bl = !B.single_cell && piece_racy(B.L);
-    r.count = A.count + B.count + (ar ? 1 : 0) + (bl ? 1 : 0);
-    r.minstart = umin64(umin64(A.minstart, B.minstart),
-                        umin64(ar ? A.R.start : ~0ull, bl ? B.L.start : ~0ull));
-  }
-  return r;
-}
-
-// Final count / first racy start of a whole run.
-RC_HD void summary_finish(const Summary& s, uint64_t* count, uint64_t* minstart) {
-  if (s.empty) { *count = 0; *minstart = ~0ull; return; }
-  bool lr = piece_racy(s.L);
-  bool rr = !s.single_cell && piece_racy(s.R);
-  *count = s.count + (lr ? 1 : 0) + (rr ? 1 : 0);
-  uint64_t m = s.minstart;
-  if (rr) m = umin64(m, s.R.start);
-  if (lr) m = umin64(m, s.L.start);
-  *minstart = m;
-}
-
 // ---------------------------------------------------------------------------
 // host-side model and workspace plan
 // ---------------------------------------------------------------------------
@@ -363,7 +302,9 @@ struct WorkspacePlan {
   size_t digoff_off;      // n_pass x 256 uint64 digit offsets
   size_t lookback_off;    // n_tiles x 256 uint64 status words (one pass at a time)
   size_t tilectr_off;     // n_pass uint32 tile counters
-  size_t summ_off;        // scan summaries
+  size_t long_off;        // scan: cells handed to the long-cell pass
+  size_t scanctr_off;     // scan: count of those cells (in the cleared range)
+  uint64_t long_cap;
   size_t group_off;       // witness per-phase group summaries
   size_t zero_lo, zero_hi;  // byte range cleared at the start of a check
   size_t total;

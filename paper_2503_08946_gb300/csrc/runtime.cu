@@ -7,6 +7,7 @@
 //   device-to-host copy of the result record into the ticket's pinned buffer.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -47,6 +48,12 @@ struct rc_ticket_s {
   size_t n = 0;
   std::vector<const rc_model*> models;
   rc_status enqueue_status = RC_OK;
+  // batch: per model, the first batch cell and the batch thread / phase widths
+  // (witness decoding); empty for single checks
+  std::vector<uint64_t> cell_base;
+  std::vector<uint32_t> field_bits;   // thread_bits | phase_bits << 8
+  void* upload = nullptr;             // pinned staging of the batch tables
+  size_t upload_cap = 0;
 };
 
 namespace {
@@ -64,6 +71,8 @@ rc_ticket_s* ticket_get(size_t n) {
         t->n = n;
         t->models.assign(n, nullptr);
         t->enqueue_status = RC_OK;
+        t->cell_base.clear();
+        t->field_bits.clear();
         t->timed = false;
         t->timer.n = 0;
         t->timer.ok = true;
@@ -95,6 +104,7 @@ void ticket_put(rc_ticket_s* t) {
     for (auto& e : t->timer.ev)
       if (e) cudaEventDestroy(e);
     cudaFreeHost(t->host);
+    if (t->upload) cudaFreeHost(t->upload);
     delete t;
   }
 }
@@ -167,11 +177,14 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
   off = align256(off + (size_t)p->n_tiles * ((size_t)1 << plan_max_bits(p->sort)) * 8);
   p->tilectr_off = off;
   off = align256(off + 16 * sizeof(unsigned int));
+  p->scanctr_off = off;
+  off = align256(off + 8);
   p->zero_hi = off;
   p->digoff_off = off;
   off = align256(off + (size_t)16 * kMaxRadix * 8);
-  p->summ_off = off;   // one scan summary per warp
-  off = align256(off + (size_t)p->scan_warps * sizeof(Summary));
+  p->long_cap = scan_long_capacity(n, p->scan_warps);
+  p->long_off = off;   // cells handed to the long-cell pass
+  off = align256(off + (size_t)p->long_cap * 8);
   p->group_off = off;
   off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
   p->total = off;
@@ -192,10 +205,15 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.phase_bits = m.host.phase_bits;
   a.block_bits = m.host.block_bits;
   a.thread_bits = m.host.thread_bits;
-  a.summaries = reinterpret_cast<rc::Summary*>(ws + p.summ_off);
   a.n_warps = p.scan_warps;
   a.res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
+  a.err = &a.res->err;
   a.groups = reinterpret_cast<unsigned int*>(ws + p.group_off);
+  a.long_list = reinterpret_cast<unsigned long long*>(ws + p.long_off);
+  a.long_count = reinterpret_cast<unsigned long long*>(ws + p.scanctr_off);
+  a.long_cap = p.long_cap;
+  a.cell_base = nullptr;
+  a.n_models = 0;
   return a;
 }
 
@@ -332,14 +350,17 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   return RC_OK;
 }
 
-void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
+// cell_base: first batch cell of the model (0 for a single check); tb / pb:
+// thread and phase widths of the keys the witness ranks were taken from.
+void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, uint64_t cell_base, uint32_t tb,
+                   uint32_t pb) {
   std::memset(out, 0, sizeof(*out));
   out->instances = r.instances;
   if (r.err & rc::kErrLookbackTimeout) {
     out->status = RC_E_TIMEOUT;
     return;
   }
-  if (r.err & rc::kErrHashFull) {
+  if (r.err & (rc::kErrHashFull | rc::kErrScanLongFull)) {
     out->status = RC_E_NOMEM;
     return;
   }
@@ -356,7 +377,7 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
   out->verdict = r.racy_cells > 0;
   if (!out->verdict || r.x_rank == ~0ull || r.y_rank == ~0ull) return;
   // cell -> (array, scope instance, element)
-  const uint64_t cell = r.cell;
+  const uint64_t cell = r.cell - cell_base;
   size_t a = 0;
   for (size_t k = 0; k < m.array_base.size(); ++k)
     if (m.array_base[k] <= cell) a = k;
@@ -364,7 +385,6 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
   out->w_array = (uint32_t)a;
   out->w_scope = m.array_shared[a] ? rem / m.array_cells[a] : 0;
   out->w_addr = m.array_shared[a] ? rem % m.array_cells[a] : rem;
-  const uint32_t tb = m.host.thread_bits, pb = m.host.phase_bits;
   const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1;
   const uint64_t bs = m.host.bs;
   out->x.block = r.minb;
@@ -377,6 +397,221 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out) {
   out->y.phase = (int64_t)((r.y_rank >> (tb + 1)) & pmask);
   out->y.block = r.y_rank >> (pb + tb + 1);
   out->y.gtid = out->y.block * bs + out->y.thread;
+}
+
+// ---------------------------------------------------------------------------
+// batched check (batch.cu holds the kernels)
+// ---------------------------------------------------------------------------
+struct BatchPack {
+  size_t i0 = 0, i1 = 0;               // models [i0, i1)
+  uint32_t tb = 0, bb = 0, pb = 0, cell_bits = 0;
+  uint64_t total_cells = 0, n_keys = 0, n_units = 0;
+  rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
+};
+
+struct BatchLayout {
+  std::vector<BatchPack> packs;
+  size_t res_off = 0, packres_off = 0, table_off = 0, cellbase_off = 0, queue_off = 0;
+  size_t upload_bytes = 0;             // table + cell bases, staged through pinned memory
+  size_t total = 0;
+};
+
+uint32_t chunks_of(const rc::Model& m) {
+  return (uint32_t)((m.host.n_threads + rc::kExpandThreadsHost - 1) / rc::kExpandThreadsHost);
+}
+
+rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, BatchLayout* L) {
+  L->packs.clear();
+  BatchPack cur;
+  bool open = false;
+  for (size_t i = 0; i < n; ++i) {
+    const rc::Model& m = models[i]->m;
+    const rc::DevModel& h = m.host;
+    if (open) {
+      const uint32_t tb = std::max(cur.tb, h.thread_bits), bb = std::max(cur.bb, h.block_bits);
+      const uint32_t pb = std::max(cur.pb, h.phase_bits);
+      const uint64_t cells = cur.total_cells + m.total_cells;
+      const uint32_t cb = rc::bit_length(cells);
+      if (cells >= cur.total_cells && 1 + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
+        cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.total_cells = cells; cur.cell_bits = cb;
+        cur.n_keys += m.key_slots;
+        cur.n_units += (uint64_t)h.n_stmts * chunks_of(m);
+        cur.i1 = i + 1;
+        continue;
+      }
+      L->packs.push_back(cur);
+    }
+    cur = BatchPack();
+    cur.i0 = i;
+    cur.i1 = i + 1;
+    cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits;
+    cur.total_cells = m.total_cells;
+    cur.cell_bits = rc::bit_length(m.total_cells);
+    cur.n_keys = m.key_slots;
+    cur.n_units = (uint64_t)h.n_stmts * chunks_of(m);
+    open = true;
+  }
+  if (open) L->packs.push_back(cur);
+  // per-model records and tables, then one pack region sized for the largest pack
+  size_t off = 0;
+  L->res_off = off;
+  off = align256(off + n * sizeof(rc::DevResult));
+  L->packres_off = off;
+  off = align256(off + sizeof(rc::DevResult));
+  L->table_off = off;
+  off = align256(off + n * sizeof(rc::BatchModel));
+  L->cellbase_off = off;
+  off = align256(off + n * 8);
+  L->upload_bytes = L->cellbase_off + n * 8 - L->table_off;
+  L->queue_off = off;
+  off = align256(off + 8);
+  const size_t region = off;
+  size_t need = region;
+  for (BatchPack& k : L->packs) {
+    rc::WorkspacePlan& p = k.p;
+    std::memset(&p, 0, sizeof(p));
+    p.n_keys = k.n_keys;
+    const uint32_t ps = 1 + k.tb + k.bb;
+    plan_sort(ps, ps + k.pb + k.cell_bits, opts ? opts->digit_bits : 0, &p.sort);
+    p.n_tiles = (k.n_keys + rc::kSortTile - 1) / rc::kSortTile;
+    p.scan_warps = scan_warps_for(k.n_keys);
+    size_t o = region;
+    p.result_off = L->packres_off;
+    p.keys_off[0] = o;
+    o = align256(o + k.n_keys * 8);
+    p.keys_off[1] = o;
+    o = align256(o + k.n_keys * 8);
+    p.zero_lo = o;
+    p.hist_off = o;
+    o = align256(o + (size_t)16 * rc::kMaxRadix * 8);
+    p.lookback_off = o;
+    o = align256(o + (size_t)p.n_tiles * ((size_t)1 << rc::plan_max_bits(p.sort)) * 8);
+    p.tilectr_off = o;
+    o = align256(o + 16 * sizeof(unsigned int));
+    p.scanctr_off = o;
+    o = align256(o + 8);
+    p.zero_hi = o;
+    p.digoff_off = o;
+    o = align256(o + (size_t)16 * rc::kMaxRadix * 8);
+    p.long_cap = rc::scan_long_capacity(k.n_keys, p.scan_warps);
+    p.long_off = o;
+    o = align256(o + (size_t)p.long_cap * 8);
+    p.group_off = o;
+    o = align256(o + (k.i1 - k.i0) * ((size_t)1 << k.pb) * 5 * sizeof(unsigned int));
+    p.total = o;
+    need = std::max(need, o);
+  }
+  L->total = need;
+  return RC_OK;
+}
+
+rc_status enqueue_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, uint8_t* ws,
+                        size_t ws_bytes, cudaStream_t st, rc_ticket_s* t) {
+  BatchLayout L;
+  rc_status s = plan_batch(models, n, opts, &L);
+  if (s != RC_OK) return s;
+  if (!ws || ws_bytes < L.total) return RC_E_NOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
+  if (n == 0) return RC_OK;
+  if (t->upload_cap < L.upload_bytes) {
+    if (t->upload) cudaFreeHost(t->upload);
+    t->upload = nullptr;
+    t->upload_cap = 0;
+    if (cudaMallocHost(&t->upload, L.upload_bytes) != cudaSuccess) return RC_E_NOMEM;
+    t->upload_cap = L.upload_bytes;
+  }
+  // model tables (pack-relative cell and key bases)
+  auto* table = static_cast<rc::BatchModel*>(t->upload);
+  auto* cbase = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(t->upload) + (L.cellbase_off - L.table_off));
+  t->cell_base.assign(n, 0);
+  t->field_bits.assign(n, 0);
+  for (const BatchPack& k : L.packs) {
+    uint64_t key_base = 0, cell_base = 0, unit_base = 0;
+    for (size_t i = k.i0; i < k.i1; ++i) {
+      const rc::Model& m = models[i]->m;
+      const rc::DevModel& h = m.host;
+      rc::BatchModel& b = table[i];
+      b.dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
+      b.key_base = key_base;
+      b.cell_base = cell_base;
+      b.unit_base = unit_base;
+      b.n_threads = h.n_threads;
+      b.n_stmts = h.n_stmts;
+      b.n_chunks = chunks_of(m);
+      b.cell_shift = h.cell_shift;
+      b.phase_shift = h.phase_shift;
+      b.block_shift = h.block_shift;
+      b.phase_bits = h.phase_bits;
+      b.block_bits = h.block_bits;
+      b.thread_bits = h.thread_bits;
+      cbase[i] = cell_base;
+      t->cell_base[i] = cell_base;
+      t->field_bits[i] = k.tb | (k.pb << 8);
+      key_base += m.key_slots;
+      cell_base += m.total_cells;
+      unit_base += (uint64_t)h.n_stmts * b.n_chunks;
+    }
+  }
+  auto* res = reinterpret_cast<rc::DevResult*>(ws + L.res_off);
+  auto* pres = reinterpret_cast<rc::DevResult*>(ws + L.packres_off);
+  const auto* dtable = reinterpret_cast<const rc::BatchModel*>(ws + L.table_off);
+  const auto* dcbase = reinterpret_cast<const uint64_t*>(ws + L.cellbase_off);
+  auto* queue = reinterpret_cast<unsigned long long*>(ws + L.queue_off);
+  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
+  s = cuda_status(cudaMemcpyAsync(ws + L.table_off, t->upload, L.upload_bytes, cudaMemcpyHostToDevice, st));
+  if (s == RC_OK) s = cuda_status(rc::launch_init_result(res, st, (uint32_t)n));
+  for (const BatchPack& k : L.packs) {
+    if (s != RC_OK) break;
+    const rc::WorkspacePlan& p = k.p;
+    const uint32_t nm = (uint32_t)(k.i1 - k.i0);
+    s = cuda_status(rc::launch_init_result(pres, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(queue, 0, 8, st));
+    if (s != RC_OK) break;
+    rc::BatchArgs ba;
+    ba.models = dtable + k.i0;
+    ba.n_models = nm;
+    ba.n_units = k.n_units;
+    ba.queue = queue;
+    ba.keys = reinterpret_cast<uint64_t*>(ws + p.keys_off[0]);
+    ba.res = res + k.i0;
+    ba.phase_shift = 1 + k.tb + k.bb;
+    ba.block_shift = 1 + k.tb;
+    ba.cell_shift = ba.phase_shift + k.pb;
+    s = cuda_status(rc::launch_batch_expand(ba, st));
+    if (s != RC_OK) break;
+    int sorted = 0;
+    s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
+                     reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin, opts ? opts->test_flags : 0u, st,
+                     &sorted);
+    if (s != RC_OK) break;
+    rc::ScanArgs sa;
+    sa.keys = reinterpret_cast<const uint64_t*>(ws + p.keys_off[sorted]);
+    sa.n = k.n_keys;
+    sa.cell_shift = ba.cell_shift;
+    sa.phase_shift = ba.phase_shift;
+    sa.block_shift = ba.block_shift;
+    sa.thread_shift = 1;
+    sa.phase_bits = k.pb;
+    sa.block_bits = k.bb;
+    sa.thread_bits = k.tb;
+    sa.n_warps = p.scan_warps;
+    if (opts && (opts->test_flags & RC_TEST_FEW_SCAN_WARPS) && sa.n_warps > 3) sa.n_warps = 3;
+    sa.res = res + k.i0;
+    sa.err = &pres->err;
+    sa.groups = reinterpret_cast<unsigned int*>(ws + p.group_off);
+    sa.long_list = reinterpret_cast<unsigned long long*>(ws + p.long_off);
+    sa.long_count = reinterpret_cast<unsigned long long*>(ws + p.scanctr_off);
+    sa.long_cap = p.long_cap;
+    sa.cell_base = dcbase + k.i0;
+    sa.n_models = nm;
+    s = cuda_status(rc::launch_scan(sa, st));
+    if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
+    if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
+  }
+  if (s == RC_OK)
+    s = cuda_status(cudaMemcpyAsync(t->host, res, n * sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+  return s;
 }
 
 }  // namespace
@@ -565,16 +800,28 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   return RC_OK;
 }
 
+// The batch takes the batched pipeline (batch.cu) unless the hash path is
+// requested; the hash path checks the models one after another.
+bool batch_is_sequential(const rc_check_opts* opts) { return opts && opts->path == RC_PATH_HASH; }
+
 rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_check_opts* opts, size_t* bytes) {
   if (!bytes || (n && !models)) return RC_E_INVALID;
-  size_t mx = 0;
-  for (size_t i = 0; i < n; ++i) {
+  for (size_t i = 0; i < n; ++i)
     if (!models[i]) return RC_E_INVALID;
-    size_t b;
-    rc_workspace_size(models[i], opts, &b);
-    if (b > mx) mx = b;
+  if (batch_is_sequential(opts)) {
+    size_t mx = 0;
+    for (size_t i = 0; i < n; ++i) {
+      size_t b;
+      rc_workspace_size(models[i], opts, &b);
+      if (b > mx) mx = b;
+    }
+    *bytes = mx;
+    return RC_OK;
   }
-  *bytes = mx;
+  BatchLayout L;
+  rc_status s = plan_batch(models, n, opts, &L);
+  if (s != RC_OK) return s;
+  *bytes = L.total;
   return RC_OK;
 }
 
@@ -586,11 +833,14 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
     if (!models[i]) return RC_E_INVALID;
   rc_ticket_s* t = ticket_get(n);
   if (!t) return RC_E_NOMEM;
+  for (size_t i = 0; i < n; ++i) t->models[i] = models[i];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc_status s = RC_OK;
-  for (size_t i = 0; i < n && s == RC_OK; ++i) {
-    s = enqueue_check(models[i], opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host + i);
-    t->models[i] = models[i];
+  if (batch_is_sequential(opts)) {
+    for (size_t i = 0; i < n && s == RC_OK; ++i)
+      s = enqueue_check(models[i], opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host + i);
+  } else {
+    s = enqueue_batch(models, n, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t);
   }
   if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
   if (s != RC_OK) {
@@ -616,7 +866,13 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
       return RC_E_CUDA;
     }
   }
-  for (size_t i = 0; i < t->n; ++i) decode_result(t->host[i], t->models[i]->m, &out[i]);
+  for (size_t i = 0; i < t->n; ++i) {
+    const rc::Model& m = t->models[i]->m;
+    if (t->cell_base.empty())
+      decode_result(t->host[i], m, &out[i], 0, m.host.thread_bits, m.host.phase_bits);
+    else
+      decode_result(t->host[i], m, &out[i], t->cell_base[i], t->field_bits[i] & 0xFFu, t->field_bits[i] >> 8);
+  }
   ticket_put(t);
   return RC_OK;
 }

@@ -4,20 +4,27 @@
 // The paper's RaW / WaW / WaR relations (appendix listing of the dependence
 // test) pair instances on the same cell with at least one write.  After the
 // sort, the instances of a cell are contiguous and grouped by phase.  A cell is
-// racy iff (two blocks meet in it and it has a write) or (inside one block,
-// some phase group has two threads and a write) -- the cell-level form of the
+// racy iff it has a write and (two blocks meet in it, or inside one block some
+// phase group holds two threads and a write) -- the cell-level form of the
 // pair rule in include/rc.h.
 //
-// K3a: each warp scans a contiguous range of the sorted keys, 32 keys per
-//      lane per segment, staged through shared memory with coalesced loads.  A
-//      lane folds its run in order: keys that continue the cell open before the
-//      run form its prefix piece, cells that begin and end in the run are
-//      counted at once, and the cell open at the run's end is finished by a
-//      segmented suffix scan of the lanes' prefix pieces (5 shuffle rounds).
-//      The warp's first cell and the cell open at its end go to a Summary
+// K3a (scan_cells_kernel): each warp owns a contiguous range of segments of
+//      32 x kScanRun keys, staged through shared memory with coalesced loads.
+//      Every cell is folded by exactly one lane, the lane whose run holds the
+//      cell's first key: a lane skips the keys that continue the cell open
+//      before its run, folds the cells that begin in it, and follows its last
+//      cell into the next lanes' runs.  A cell still open at the segment end
+//      is carried by lane 0 into the next segment.  A cell carried over more
+//      than kCarryMaxSegs segments, or still open at the end of the warp's
+//      range, is handed to K3b by its first position.
+// K3b (scan_long_kernel): one block per handed-over cell folds it from its
+//      first key, 2048 keys at a time, as an ordered reduction of CellPieces
 //      (rc_internal.h).
-// K3b: one block folds the warp summaries in order (count, first racy cell);
-//      one warp finds that cell's end with a 32-way galloping search.
+// Counts are added and the first racy cell is the minimum start, so the
+// result does not depend on which lane or block folds a cell.  In a batch
+// (several models' keys sorted together, each model in its own cell range),
+// a racy cell is charged to the model whose range holds it.
+// K3c: one warp per result finds the end of its first racy cell.
 // K4:  four grid-wide reductions over that one segment: the cell summary
 //      (blocks, write blocks), per-phase groups of its lowest block, the
 //      smallest instance that has a partner (x), and x's smallest partner (y).
@@ -32,15 +39,6 @@ namespace rc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(FULL, v, o);
-    v = y < v ? y : v;
-  }
-  return v;
-}
 
 // 32-way galloping search by one full warp: first position >= start whose key
 // is not in `cell` (keys[start] is in it).
@@ -70,188 +68,106 @@ __device__ uint64_t warp_cell_end(const uint64_t* keys, uint64_t n, uint32_t cs,
   return lo + 1;
 }
 
-// Compact piece of a cell for the lane-level scan: block range, write flag, and
-// the first / last phase group with the OR of the racy groups in between
-// (the same information as CellPiece in rc_internal.h, packed in 8 words).
-struct Piece {
-  unsigned minb, maxb;
-  unsigned flags;     // bit0 anyW, bit1 single group, bit2 inner racy, bit3 fs write, bit4 ls write, bit5 empty
-  unsigned ps;        // first phase | last phase << 16
-  unsigned fs_min, fs_max, ls_min, ls_max;
+// Result record of the model whose cell range holds `cell` (batch), else the
+// single result.
+__device__ __forceinline__ DevResult* result_of(const ScanArgs& a, uint64_t cell) {
+  if (a.n_models == 0) return a.res;
+  uint32_t lo = 0, hi = a.n_models;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(&a.cell_base[mid]) <= cell) lo = mid;
+    else hi = mid;
+  }
+  return a.res + lo;
+}
+
+// The cell a lane is folding.  cp = key >> phase_shift (cell and phase), bt =
+// the (block, thread) bits of a key.
+struct CellState {
+  uint64_t cp;       // (cell, phase) of the current phase group
+  uint64_t start;    // position of the cell's first key
+  unsigned bt0;      // (block, thread) of the cell's first key
+  unsigned gbt0;     // (block, thread) of the group's first key
+  unsigned f;        // flags below
 };
-constexpr unsigned kPW = 1u, kPSingle = 2u, kPInner = 4u, kPFsW = 8u, kPLsW = 16u, kPEmpty = 32u;
+constexpr unsigned kFW = 1u, kFMultiB = 2u, kFGMulti = 4u, kFGW = 8u, kFInner = 16u;
 
-__device__ __forceinline__ Piece piece_empty() {
-  Piece p;
-  p.minb = p.maxb = 0;
-  p.flags = kPEmpty;
-  p.ps = 0;
-  p.fs_min = p.fs_max = p.ls_min = p.ls_max = 0;
-  return p;
+__device__ __forceinline__ void cs_start(CellState& s, uint64_t cp, uint64_t pos, unsigned bt, bool w) {
+  s.cp = cp;
+  s.start = pos;
+  s.bt0 = s.gbt0 = bt;
+  s.f = w ? (kFW | kFGW) : 0u;
 }
-__device__ __forceinline__ void piece_start(Piece& P, unsigned ph, unsigned t, unsigned b, bool w) {
-  P.minb = P.maxb = b;
-  P.flags = kPSingle | (w ? (kPW | kPFsW | kPLsW) : 0u);
-  P.ps = ph | (ph << 16);
-  P.fs_min = P.fs_max = P.ls_min = P.ls_max = t;
-}
-__device__ __forceinline__ bool ls_racy(const Piece& P) { return P.ls_min != P.ls_max && (P.flags & kPLsW); }
-__device__ __forceinline__ bool fs_racy(const Piece& P) { return P.fs_min != P.fs_max && (P.flags & kPFsW); }
-__device__ __forceinline__ bool cpiece_racy(const Piece& P) {
-  if (P.minb != P.maxb) return (P.flags & kPW) != 0;
-  return (P.flags & kPInner) || fs_racy(P) || ls_racy(P);
-}
-// Add one key.  keep_fs: the piece's first group may continue a group on its
-// left, so it is kept apart instead of folding into `inner` when it closes.
-__device__ __forceinline__ void piece_add(Piece& P, unsigned ph, unsigned t, unsigned b, bool w, bool keep_fs) {
-  if (ph != (P.ps >> 16)) {
-    if ((P.flags & kPSingle) && !keep_fs) {
-      if (fs_racy(P)) P.flags |= kPInner;
-      P.fs_min = P.fs_max = 0;
-      P.flags &= ~kPFsW;
-    } else if (!(P.flags & kPSingle) && ls_racy(P)) {
-      P.flags |= kPInner;
-    }
-    P.flags &= ~(kPSingle | kPLsW);
-    P.ps = (P.ps & 0xFFFFu) | (ph << 16);
-    P.ls_min = P.ls_max = t;
-    if (w) P.flags |= kPLsW;
-  } else {
-    P.ls_min = min(P.ls_min, t);
-    P.ls_max = max(P.ls_max, t);
-    if (w) P.flags |= kPLsW;
-    if (P.flags & kPSingle) {
-      P.fs_min = P.ls_min;
-      P.fs_max = P.ls_max;
-      P.flags = (P.flags & ~kPFsW) | ((P.flags & kPLsW) ? kPFsW : 0u);
-    }
+// Add a key of the same cell.  Two keys of one phase group with different
+// (block, thread) are two threads; if their blocks differ the cell is
+// multi-block anyway, and then it races iff it has a write.
+__device__ __forceinline__ void cs_add(CellState& s, uint64_t cp, unsigned bt, bool w, uint32_t thread_bits) {
+  unsigned f = s.f;
+  if (((bt ^ s.bt0) >> thread_bits) != 0u) f |= kFMultiB;
+  if (cp != s.cp) {
+    if ((f & (kFGMulti | kFGW)) == (kFGMulti | kFGW)) f |= kFInner;
+    f &= ~(kFGMulti | kFGW);
+    s.cp = cp;
+    s.gbt0 = bt;
+  } else if (bt != s.gbt0) {
+    f |= kFGMulti;
   }
-  P.minb = min(P.minb, b);
-  P.maxb = max(P.maxb, b);
-  if (w) P.flags |= kPW;
+  if (w) f |= kFW | kFGW;
+  s.f = f;
 }
-// X then Y, pieces of one cell (either may be empty).
-__device__ __forceinline__ Piece piece_cat(const Piece& X, const Piece& Y) {
-  if (X.flags & kPEmpty) return Y;
-  if (Y.flags & kPEmpty) return X;
-  Piece r;
-  r.minb = min(X.minb, Y.minb);
-  r.maxb = max(X.maxb, Y.maxb);
-  const unsigned xs = X.flags & kPSingle, ys = Y.flags & kPSingle;
-  unsigned inner = ((X.flags | Y.flags) & kPInner);
-  r.ps = (X.ps & 0xFFFFu) | (Y.ps & 0xFFFF0000u);
-  // merged group when X's last group continues into Y's first group
-  const bool join = (X.ps >> 16) == (Y.ps & 0xFFFFu);
-  unsigned m_min = 0, m_max = 0;
-  bool m_w = false;
-  if (join) {
-    m_min = min(X.ls_min, Y.fs_min);
-    m_max = max(X.ls_max, Y.fs_max);
-    m_w = (X.flags & kPLsW) || (Y.flags & kPFsW);
-  }
-  unsigned fsw, lsw;
-  if (join) {
-    if (xs && ys) {
-      r.fs_min = r.ls_min = m_min; r.fs_max = r.ls_max = m_max; fsw = lsw = m_w;
-    } else if (xs) {
-      r.fs_min = m_min; r.fs_max = m_max; fsw = m_w;
-      r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
-    } else if (ys) {
-      r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
-      r.ls_min = m_min; r.ls_max = m_max; lsw = m_w;
-    } else {
-      r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
-      r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
-      if (m_min != m_max && m_w) inner = kPInner;
-    }
-  } else {
-    r.fs_min = X.fs_min; r.fs_max = X.fs_max; fsw = (X.flags & kPFsW) != 0;
-    r.ls_min = Y.ls_min; r.ls_max = Y.ls_max; lsw = (Y.flags & kPLsW) != 0;
-    if (!xs && ls_racy(X)) inner = kPInner;
-    if (!ys && fs_racy(Y)) inner = kPInner;
-  }
-  const bool single = join && xs && ys;
-  r.flags = ((X.flags | Y.flags) & kPW) | (single ? kPSingle : 0u) | inner | (fsw ? kPFsW : 0u) | (lsw ? kPLsW : 0u);
+__device__ __forceinline__ bool cs_racy(const CellState& s) {
+  const unsigned f = s.f;
+  if (!(f & kFW)) return false;
+  return (f & (kFMultiB | kFInner)) != 0u || (f & (kFGMulti | kFGW)) == (kFGMulti | kFGW);
+}
+__device__ __forceinline__ CellState cs_shfl(const CellState& s, int src) {
+  CellState r;
+  r.cp = __shfl_sync(FULL, s.cp, src);
+  r.start = __shfl_sync(FULL, s.start, src);
+  r.bt0 = __shfl_sync(FULL, s.bt0, src);
+  r.gbt0 = __shfl_sync(FULL, s.gbt0, src);
+  r.f = __shfl_sync(FULL, s.f, src);
   return r;
 }
 
-__device__ __forceinline__ CellPiece to_cellpiece(const Piece& P, uint64_t cell, uint64_t start) {
-  CellPiece c;
-  c.cell = cell;
-  c.start = start;
-  c.minb = P.minb;
-  c.maxb = P.maxb;
-  c.anyW = (P.flags & kPW) ? 1u : 0u;
-  c.first_p = P.ps & 0xFFFFu;
-  c.last_p = P.ps >> 16;
-  c.single_sub = (P.flags & kPSingle) ? 1u : 0u;
-  c.inner = (P.flags & kPInner) ? 1u : 0u;
-  c.pad = 0;
-  c.fs.mint = P.fs_min; c.fs.maxt = P.fs_max; c.fs.anyW = (P.flags & kPFsW) ? 1u : 0u; c.fs.pad = 0;
-  c.ls.mint = P.ls_min; c.ls.maxt = P.ls_max; c.ls.anyW = (P.flags & kPLsW) ? 1u : 0u; c.ls.pad = 0;
-  return c;
+__device__ __forceinline__ void hand_over(const ScanArgs& a, uint64_t start) {
+  const unsigned long long i = atomicAdd(a.long_count, 1ull);
+  if (i < a.long_cap) a.long_list[i] = start;
+  else atomicOr(a.err, (unsigned int)kErrScanLongFull);
 }
 
-template <class T>
-__device__ __forceinline__ T shfl_down_T(const T& v, int delta) {
-  static_assert(sizeof(T) % 4 == 0, "shuffle of 4-byte words");
-  T r;
-  const unsigned* pv = reinterpret_cast<const unsigned*>(&v);
-  unsigned* pr = reinterpret_cast<unsigned*>(&r);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) pr[i] = __shfl_down_sync(FULL, pv[i], delta);
-  return r;
-}
-template <class T>
-__device__ __forceinline__ T shfl_idx_T(const T& v, int src) {
-  T r;
-  const unsigned* pv = reinterpret_cast<const unsigned*>(&v);
-  unsigned* pr = reinterpret_cast<unsigned*>(&r);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) pr[i] = __shfl_sync(FULL, pv[i], src);
-  return r;
-}
-
-constexpr int kScanWarps = 4;                 // warps per block of scan_runs_kernel
+constexpr int kScanWarps = 4;                 // warps per block of scan_cells_kernel
 constexpr int kRunPad = kScanRun + 1;         // padded per-lane stride in shared memory
 constexpr int kSegKeys = 32 * kScanRun;       // keys per warp segment
+constexpr int kCarryMaxSegs = 8;              // longer carried cells go to scan_long_kernel
 
-// Each warp scans a contiguous range of segments of kSegKeys keys, in order.
-// Per segment every lane folds its run of kScanRun keys: the keys that continue
-// the cell open before the run form its prefix piece; cells that begin and end
-// in the run are counted at once; the cell open at the run's end is finished
-// by a segmented suffix scan over the lanes' prefix pieces (5 shuffle rounds).
-// A cell still open at the segment end is carried to the next segment.  The
-// first cell of the warp's range (it may continue the previous warp's range)
-// and the cell open at its end go to the warp's Summary for the ordered fold.
-__global__ void __launch_bounds__(kScanWarps * 32) scan_runs_kernel(ScanArgs a) {
+__device__ __forceinline__ int seg_slot(int j) { return (j / kScanRun) * kRunPad + (j % kScanRun); }
+
+__global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a) {
   __shared__ uint64_t sk[kScanWarps][32 * kRunPad];
-  const unsigned tm = (1u << a.thread_bits) - 1u;
-  const unsigned bm = (1u << a.block_bits) - 1u;
-  const unsigned pm = (1u << a.phase_bits) - 1u;
+  const uint32_t cs = a.cell_shift, ps = a.phase_shift, pb = a.phase_bits, tb = a.thread_bits;
+  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t* my = sk[w];
   const uint64_t n_seg = (a.n + kSegKeys - 1) / kSegKeys;
   const uint64_t gw = (uint64_t)blockIdx.x * kScanWarps + w;
   const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
-  const uint64_t range_start = seg0 * kSegKeys;
-  unsigned count = 0;
-  unsigned long long minstart = ~0ull;
-  // warp-uniform state
-  bool carry_valid = false;
-  Piece carry = piece_empty();
-  uint64_t carry_cell = 0, carry_start = 0;
-  bool first_closed = false;
-  Piece Lw = piece_empty();
-  uint64_t Lw_cell = 0;
+  unsigned long long count = 0, minstart = ~0ull;
+  // cell of the key just before the current segment (none before key 0)
+  uint64_t c_before = ~0ull;
+  if (seg0 > 0 && seg0 < seg1) c_before = a.keys[seg0 * kSegKeys - 1] >> cs;
+  bool carry = false;     // warp-uniform: lane 0 folds a cell begun in an earlier segment
+  int carried = 0;
+  CellState cc;
+  cc.cp = 0; cc.start = 0; cc.bt0 = cc.gbt0 = 0; cc.f = 0;
   for (uint64_t seg = seg0; seg < seg1; ++seg) {
     const uint64_t S = seg * kSegKeys;
 #pragma unroll
     for (int i = 0; i < kSegKeys / 64; ++i) {
       const int j = 2 * (i * 32 + lane);
       const uint64_t pos = S + j;
-      uint64_t x = ~0ull, y = ~0ull;
+      uint64_t x = kSentinel, y = kSentinel;
       if (pos + 1 < a.n) {
         const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + pos));
         x = v.x;
@@ -259,178 +175,206 @@ __global__ void __launch_bounds__(kScanWarps * 32) scan_runs_kernel(ScanArgs a) 
       } else if (pos < a.n) {
         x = a.keys[pos];
       }
-      const int o = (j / kScanRun) * kRunPad + (j % kScanRun);
+      const int o = seg_slot(j);
       my[o] = x;
       my[o + 1] = y;
     }
     __syncwarp();
+    // (1) the carried cell continues over the segment's leading keys
+    if (carry) {
+      int lead = 0;
+      if (lane == 0) {
+        const uint64_t cell = cc.cp >> pb;
+        while (lead < kSegKeys) {
+          const uint64_t k = my[seg_slot(lead)];
+          if (k == kSentinel || (k >> cs) != cell) break;
+          cs_add(cc, k >> ps, (unsigned)(k >> 1) & btm, (k & 1ull) != 0, tb);
+          ++lead;
+        }
+      }
+      lead = __shfl_sync(FULL, lead, 0);
+      if (lead < kSegKeys) {
+        if (lane == 0 && cs_racy(cc)) {
+          if (a.n_models) {
+            DevResult* r = result_of(a, cc.cp >> pb);
+            atomicAdd(&r->racy_cells, 1ull);
+            atomicMin(&r->min_start, (unsigned long long)cc.start);
+          } else {
+            ++count;
+            minstart = min(minstart, (unsigned long long)cc.start);
+          }
+        }
+        carry = false;
+      } else if (++carried > kCarryMaxSegs) {
+        if (lane == 0) hand_over(a, cc.start);
+        carry = false;
+      }
+    }
+    // (2) the cells that begin in this lane's run
     const uint64_t s = S + (uint64_t)lane * kScanRun;
     const int len = s < a.n ? (int)min((uint64_t)kScanRun, a.n - s) : 0;
     const uint64_t* run = my + lane * kRunPad;
-    // cell of the key just before the run (none before the warp's range)
-    uint64_t c_prev = ~0ull;
-    if (lane > 0) c_prev = my[(lane - 1) * kRunPad + kScanRun - 1] >> a.cell_shift;
-    else if (seg != seg0) c_prev = a.keys[S - 1] >> a.cell_shift;
-    Piece PP = piece_empty();       // keys continuing the cell open before the run
-    Piece OC = piece_empty();       // the cell open at the current key
-    uint64_t oc_cell = 0, oc_start = 0;
-    bool has_head = false;
-    bool got_L = false;             // this lane closed the warp range's first cell
-    Piece Lc = piece_empty();
-    uint64_t Lc_cell = 0;
-    for (int q = 0; q < len; ++q) {
+    const uint64_t c_prev = lane > 0 ? (my[(lane - 1) * kRunPad + kScanRun - 1] >> cs) : c_before;
+    CellState st;
+    st.cp = 0; st.start = 0; st.bt0 = st.gbt0 = 0; st.f = 0;
+    bool has = false, term = false;
+    int q = 0;
+    for (; q < len; ++q) {
       const uint64_t k = run[q];
-      const uint64_t cc = k >> a.cell_shift;
-      const unsigned ph = (unsigned)(k >> a.phase_shift) & pm;
-      const unsigned t = (unsigned)(k >> a.thread_shift) & tm;
-      const unsigned b = (unsigned)(k >> a.block_shift) & bm;
+      if (k == kSentinel) { term = true; break; }
+      if ((k >> cs) != c_prev) break;
+    }
+    auto close = [&](const CellState& x) {
+      if (!cs_racy(x)) return;
+      if (a.n_models) {
+        DevResult* r = result_of(a, x.cp >> pb);
+        atomicAdd(&r->racy_cells, 1ull);
+        atomicMin(&r->min_start, (unsigned long long)x.start);
+      } else {
+        ++count;
+        minstart = min(minstart, (unsigned long long)x.start);
+      }
+    };
+    for (; q < len && !term; ++q) {
+      const uint64_t k = run[q];
+      if (k == kSentinel) { term = true; break; }
+      const uint64_t cp = k >> ps;
+      const unsigned bt = (unsigned)(k >> 1) & btm;
       const bool wr = (k & 1ull) != 0;
-      const uint64_t pos = s + q;
-      if (!has_head && cc == c_prev) {
-        if (PP.flags & kPEmpty) piece_start(PP, ph, t, b, wr);
-        else piece_add(PP, ph, t, b, wr, true);
-      } else if (!has_head || cc != oc_cell) {
-        if (has_head) {
-          if (oc_start == range_start) { got_L = true; Lc = OC; Lc_cell = oc_cell; }
-          else if (cpiece_racy(OC)) { ++count; minstart = min(minstart, (unsigned long long)oc_start); }
+      if (!has || (cp >> pb) != (st.cp >> pb)) {
+        if (has) close(st);
+        cs_start(st, cp, s + q, bt, wr);
+        has = true;
+      } else {
+        cs_add(st, cp, bt, wr, tb);
+      }
+    }
+    // (3) the run's last cell continues into the next lanes' runs
+    bool open_end = false;
+    if (has) {
+      if (term || len < kScanRun) {
+        close(st);
+      } else {
+        const uint64_t cell = st.cp >> pb;
+        bool ended = false;
+        for (int j = (lane + 1) * kScanRun; j < kSegKeys; ++j) {
+          const uint64_t k = my[seg_slot(j)];
+          if (k == kSentinel || (k >> cs) != cell) { ended = true; break; }
+          cs_add(st, k >> ps, (unsigned)(k >> 1) & btm, (k & 1ull) != 0, tb);
         }
-        has_head = true;
-        piece_start(OC, ph, t, b, wr);
-        oc_cell = cc;
-        oc_start = pos;
-      } else {
-        piece_add(OC, ph, t, b, wr, oc_start == range_start);
+        if (ended || S + kSegKeys >= a.n) close(st);
+        else open_end = true;
       }
     }
-    // suffix scan of the prefix pieces: C = continuation from this lane onward,
-    // stop = it ends in this segment (at a lane that has a head)
-    Piece C = PP;
-    bool stop = has_head || len == 0;
-    bool dead = len == 0;                 // the chain ran into lanes past the end of the keys
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const Piece Cn = shfl_down_T(C, d);
-      const bool sn = __shfl_down_sync(FULL, stop, d);
-      const bool dn = __shfl_down_sync(FULL, dead, d);
-      if (!stop && lane + d < 32) {
-        C = piece_cat(C, Cn);
-        stop = sn;
-        dead = dn;
-      }
-    }
-    const Piece Cn1 = shfl_down_T(C, 1);
-    const bool stop1 = __shfl_down_sync(FULL, stop, 1);
-    const bool dead1 = __shfl_down_sync(FULL, dead, 1);
-    // the lane's open cell: finished if its continuation ends inside the segment
-    bool open_at_end = false;
-    Piece total = OC;
-    if (has_head) {
-      const bool has_next = lane < 31;
-      if (has_next) total = piece_cat(OC, Cn1);
-      const bool ended = has_next && stop1 && !dead1;
-      if (ended) {
-        if (oc_start == range_start) { got_L = true; Lc = total; Lc_cell = oc_cell; }
-        else if (cpiece_racy(total)) { ++count; minstart = min(minstart, (unsigned long long)oc_start); }
-      } else {
-        open_at_end = true;
-      }
-    }
-    // the warp's carried cell continues into lane 0's prefix chain
-    const Piece C0 = shfl_idx_T(C, 0);
-    const bool stop0 = __shfl_sync(FULL, stop, 0);
-    const bool dead0 = __shfl_sync(FULL, dead, 0);
-    if (carry_valid && !(C0.flags & kPEmpty)) {
-      carry = piece_cat(carry, C0);
-      if (stop0 && !dead0) {
-        // the carried cell ends in this segment
-        if (carry_start == range_start) { first_closed = true; Lw = carry; Lw_cell = carry_cell; }
-        else if (cpiece_racy(carry) && lane == 0) { ++count; minstart = min(minstart, (unsigned long long)carry_start); }
-        carry_valid = false;
-      }
-    } else if (carry_valid && C0.flags & kPEmpty) {
-      // lane 0 begins a new cell (or there are no keys): the carried cell ended at the segment start
-      const bool lane0_has_keys = __shfl_sync(FULL, len, 0) > 0;
-      if (lane0_has_keys) {
-        if (carry_start == range_start) { first_closed = true; Lw = carry; Lw_cell = carry_cell; }
-        else if (cpiece_racy(carry) && lane == 0) { ++count; minstart = min(minstart, (unsigned long long)carry_start); }
-        carry_valid = false;
-      }
-    }
-    // the range's first cell closed inside a lane
-    const unsigned GL = __ballot_sync(FULL, got_L);
-    if (GL) {
-      const int src = __ffs(GL) - 1;
-      Lw = shfl_idx_T(Lc, src);
-      Lw_cell = __shfl_sync(FULL, Lc_cell, src);
-      first_closed = true;
-    }
-    // new carry: the open cell whose continuation reaches the segment end
-    const unsigned OE = __ballot_sync(FULL, open_at_end);
+    // (4) the cell open at the segment end (at most one lane) becomes the carry
+    const unsigned OE = __ballot_sync(FULL, open_end);
     if (OE) {
-      const int src = 31 - __clz(OE);
-      carry = shfl_idx_T(total, src);
-      carry_cell = __shfl_sync(FULL, oc_cell, src);
-      carry_start = __shfl_sync(FULL, oc_start, src);
-      carry_valid = true;
+      cc = cs_shfl(st, __ffs(OE) - 1);
+      carry = true;
+      carried = 0;
     }
+    c_before = my[31 * kRunPad + kScanRun - 1] >> cs;
     __syncwarp();
   }
-  // warp summary for the ordered fold
-  count = __reduce_add_sync(FULL, count);
-  minstart = warp_min_u64(minstart);
-  if (lane == 0 && gw < a.n_warps) {
-    Summary S = summary_empty();
-    if (carry_valid || first_closed) {
-      S.empty = 0;
-      S.count = count;
-      S.minstart = minstart;
-      if (first_closed) {
-        S.single_cell = 0;
-        S.L = to_cellpiece(Lw, Lw_cell, range_start);
-        S.R = to_cellpiece(carry, carry_cell, carry_start);
-      } else {
-        S.single_cell = 1;
-        S.L = S.R = to_cellpiece(carry, carry_cell, carry_start);
-      }
+  // a cell still open at the range end continues past it
+  if (carry && lane == 0) hand_over(a, cc.start);
+  if (a.n_models == 0) {
+    count = __reduce_add_sync(FULL, (unsigned)count);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(FULL, minstart, o);
+      minstart = y < minstart ? y : minstart;
     }
-    a.summaries[gw] = S;
+    if (lane == 0) {
+      if (count) atomicAdd(&a.res->racy_cells, count);
+      if (minstart != ~0ull) atomicMin(&a.res->min_start, minstart);
+    }
   }
 }
 
-// One block: fold the warp summaries in order; count and first racy cell.
-constexpr int kFoldThreads = 128;
+// One key as a CellPiece.
+__device__ __forceinline__ CellPiece key_piece(const ScanArgs& a, uint64_t k, uint64_t cell, uint64_t pos) {
+  CellPiece c;
+  c.cell = cell;
+  c.start = pos;
+  const unsigned b = (unsigned)(k >> a.block_shift) & ((1u << a.block_bits) - 1u);
+  const unsigned t = (unsigned)(k >> a.thread_shift) & ((1u << a.thread_bits) - 1u);
+  const unsigned p = (unsigned)(k >> a.phase_shift) & ((1u << a.phase_bits) - 1u);
+  const unsigned w = (unsigned)(k & 1ull);
+  c.minb = c.maxb = b;
+  c.anyW = w;
+  c.first_p = c.last_p = p;
+  c.single_sub = 1;
+  c.inner = 0;
+  c.pad = 0;
+  c.fs.mint = c.fs.maxt = t;
+  c.fs.anyW = w;
+  c.fs.pad = 0;
+  c.ls = c.fs;
+  return c;
+}
 
-__global__ void __launch_bounds__(kFoldThreads) scan_fold_kernel(ScanArgs a) {
-  __shared__ Summary part[kFoldThreads];
-  const uint32_t per = (a.n_warps + kFoldThreads - 1) / kFoldThreads;
-  const uint32_t b0 = threadIdx.x * per;
-  const uint32_t b1 = min(a.n_warps, b0 + per);
-  Summary s = summary_empty();
-  for (uint32_t k = b0; k < b1; ++k) s = summary_combine(s, a.summaries[k]);
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int width = 1; width < kFoldThreads; width <<= 1) {
-    if ((threadIdx.x % (2 * width)) == 0)
-      part[threadIdx.x] = summary_combine(part[threadIdx.x], part[threadIdx.x + width]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    uint64_t cnt, ms;
-    summary_finish(part[0], &cnt, &ms);
-    a.res->racy_cells = cnt;
-    a.res->min_start = ms;
+constexpr int kLongThreads = 256;
+constexpr int kLongItems = 8;
+
+// One block per handed-over cell: fold it from its first key.
+__global__ void __launch_bounds__(kLongThreads) scan_long_kernel(ScanArgs a) {
+  __shared__ CellPiece part[kLongThreads];
+  __shared__ int part_empty[kLongThreads];
+  const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
+  for (unsigned long long i = blockIdx.x; i < n_long; i += gridDim.x) {
+    const uint64_t start = a.long_list[i];
+    const uint64_t cell = a.keys[start] >> a.cell_shift;
+    CellPiece acc{};
+    bool acc_empty = true;
+    for (uint64_t base = start;; base += (uint64_t)kLongThreads * kLongItems) {
+      CellPiece p{};
+      bool empty = true, end = false;
+      for (int j = 0; j < kLongItems; ++j) {
+        const uint64_t pos = base + (uint64_t)threadIdx.x * kLongItems + j;
+        if (pos >= a.n) { end = true; break; }
+        const uint64_t k = a.keys[pos];
+        if (k == kSentinel || (k >> a.cell_shift) != cell) { end = true; break; }
+        const CellPiece kp = key_piece(a, k, cell, pos);
+        p = empty ? kp : piece_combine(p, kp);
+        empty = false;
+      }
+      part[threadIdx.x] = p;
+      part_empty[threadIdx.x] = empty ? 1 : 0;
+      const bool any_end = __syncthreads_or(end) != 0;
+      for (int width = 1; width < kLongThreads; width <<= 1) {
+        if ((threadIdx.x % (2 * width)) == 0 && !part_empty[threadIdx.x + width]) {
+          part[threadIdx.x] = part_empty[threadIdx.x] ? part[threadIdx.x + width]
+                                                      : piece_combine(part[threadIdx.x], part[threadIdx.x + width]);
+          part_empty[threadIdx.x] = 0;
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0 && !part_empty[0]) {
+        acc = acc_empty ? part[0] : piece_combine(acc, part[0]);
+        acc_empty = false;
+      }
+      __syncthreads();
+      if (any_end) break;
+    }
+    if (threadIdx.x == 0 && !acc_empty && piece_racy(acc)) {
+      DevResult* r = result_of(a, cell);
+      atomicAdd(&r->racy_cells, 1ull);
+      atomicMin(&r->min_start, (unsigned long long)start);
+    }
   }
 }
 
-// One warp: the end of the first racy cell.
+// One warp per result: the end of its first racy cell.
 __global__ void scan_finish_kernel(ScanArgs a) {
-  const unsigned long long s = a.res->min_start;
+  DevResult* r = a.res + blockIdx.x;
+  const unsigned long long s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t cell = a.keys[s] >> a.cell_shift;
   const uint64_t e = warp_cell_end(a.keys, a.n, a.cell_shift, s, cell);
   if (threadIdx.x == 0) {
-    a.res->seg_end = e;
-    a.res->cell = cell;
+    r->seg_end = e;
+    r->cell = cell;
   }
 }
 
@@ -450,18 +394,25 @@ __device__ __forceinline__ Fields fields(const ScanArgs& a, uint64_t key) {
 }
 
 // group record: [mint, maxt, minWt, maxWt, anyW]
+// Each kernel handles result blockIdx.y (one per model of a batch) with the
+// blocks of its x dimension.
+__device__ __forceinline__ unsigned* groups_of(const ScanArgs& a) {
+  return a.groups + (size_t)blockIdx.y * 5u * (1u << a.phase_bits);
+}
+
 __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
-  DevResult* r = a.res;
+  DevResult* r = a.res + blockIdx.y;
   const uint64_t s = r->min_start;
   const uint32_t n_groups = 1u << a.phase_bits;
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
-    a.groups[g * 5 + 0] = 0xffffffffu;
-    a.groups[g * 5 + 1] = 0;
-    a.groups[g * 5 + 2] = 0xffffffffu;
-    a.groups[g * 5 + 3] = 0;
-    a.groups[g * 5 + 4] = 0;
-  }
+  unsigned* groups = groups_of(a);
   if (s == ~0ull) return;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
+    groups[g * 5 + 0] = 0xffffffffu;
+    groups[g * 5 + 1] = 0;
+    groups[g * 5 + 2] = 0xffffffffu;
+    groups[g * 5 + 3] = 0;
+    groups[g * 5 + 4] = 0;
+  }
   const uint64_t e = r->seg_end;
   unsigned minb = 0xffffffffu, maxb = 0, minWb = 0xffffffffu, maxWb = 0, anyW = 0;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -489,7 +440,8 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
 }
 
 __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
-  DevResult* r = a.res;
+  DevResult* r = a.res + blockIdx.y;
+  unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t e = r->seg_end;
@@ -497,7 +449,7 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     if (f.b != b0) continue;
-    unsigned* g = a.groups + f.p * 5;
+    unsigned* g = groups + f.p * 5;
     atomicMin(&g[0], f.t);
     atomicMax(&g[1], f.t);
     if (f.k) {
@@ -509,7 +461,8 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
 }
 
 __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
-  DevResult* r = a.res;
+  DevResult* r = a.res + blockIdx.y;
+  const unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t e = r->seg_end;
@@ -521,7 +474,7 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
     // a partner in another block (global cells; a shared cell has one block)
     const bool cross = f.k ? (b0 != maxb) : (anyW && (minWb != f.b || maxWb != f.b));
     // a partner of another thread in the same block and phase
-    const unsigned* g = a.groups + f.p * 5;
+    const unsigned* g = groups + f.p * 5;
     const bool same = f.k ? (g[0] != g[1]) : (g[4] && (g[2] != f.t || g[3] != f.t));
     if (cross || same) {
       const unsigned long long rank = ((unsigned long long)f.p << (a.thread_bits + 1)) |
@@ -539,7 +492,7 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
 }
 
 __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
-  DevResult* r = a.res;
+  DevResult* r = a.res + blockIdx.y;
   const uint64_t s = r->min_start;
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;
@@ -569,8 +522,10 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&r->y_rank, best);
 }
 
-__global__ void init_result_kernel(DevResult* r) {
-  if (threadIdx.x == 0) {
+__global__ void init_result_kernel(DevResult* res, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    DevResult* r = res + i;
     r->oob_code = ~0ull;
     r->instances = 0;
     r->racy_cells = 0;
@@ -594,29 +549,37 @@ __global__ void init_result_kernel(DevResult* r) {
 
 }  // namespace
 
-cudaError_t launch_init_result(DevResult* res, cudaStream_t st) {
-  init_result_kernel<<<1, 32, 0, st>>>(res);
+cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
+  if (n == 0) return cudaSuccess;
+  init_result_kernel<<<(n + 127) / 128, 128, 0, st>>>(res, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
-  scan_runs_kernel<<<(a.n_warps + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  scan_fold_kernel<<<1, kFoldThreads, 0, st>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  scan_finish_kernel<<<1, 32, 0, st>>>(a);
+  if (a.n > 0) {
+    scan_cells_kernel<<<(a.n_warps + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scan_long_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned nr = a.n_models ? a.n_models : 1u;
+  scan_finish_kernel<<<nr, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st) {
-  const unsigned g = 152 * 2;
+  const dim3 g(a.n_models ? 1u : 152u * 2u, a.n_models ? a.n_models : 1u);
   witness_cell_kernel<<<g, 256, 0, st>>>(a);
   witness_group_kernel<<<g, 256, 0, st>>>(a);
   witness_x_kernel<<<g, 256, 0, st>>>(a);
   witness_y_kernel<<<g, 256, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+uint64_t scan_long_capacity(uint64_t n, uint32_t n_warps) {
+  return n / ((uint64_t)kCarryMaxSegs * kSegKeys) + n_warps + 16;
 }
 
 }  // namespace rc
