@@ -316,7 +316,108 @@ def run_native(args):
                        "parallelism": f"independent models per rank x{world}"},
             "roofline": roofline, "pipeline": pipeline, "stages_ms": st_mean,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": (10 + n_pass) * args.steps,
+            "gpu_launches": (11 + n_pass) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# batched check of many small models vs one check per model
+# ---------------------------------------------------------------------------
+BATCH_WORKLOAD = ("10,000 seeded random models: threads log-uniform 32..65,536 (multiple of 32, block "
+                  "min(T, 256)), 1-8 loop-free access statements, 4 arrays, 8 barrier intervals, 1% planted races")
+
+
+def run_batch(args):
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+    models = w.batch_models(args.batch_models, seed0=args.seed * 1000003 + rank * 100003)
+    handles = [rc.rc_model_create(m) for m in models]
+    opts = {"digit_bits": args.digit_bits}
+    ws = rc.workspace(rc.rc_batch_workspace_size(handles, opts))
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        res = rc.rc_report(rc.rc_check_batch(handles, opts, ws, stream))
+        bad = [r for r in res if r.status != rc.RC_OK]
+        if bad:
+            raise RuntimeError(f"batch check failed: {rc.rc_status_str(bad[0].status)}")
+        return res
+
+    def per_model(ws1):
+        window, out = [], []
+        for h in handles:
+            window.append(rc.rc_check(h, opts, ws1, stream))
+            if len(window) > 32:
+                out.append(rc.rc_report(window.pop(0))[0])
+        out += [rc.rc_report(t)[0] for t in window]
+        return out
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(steps):
+            r = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms, wall * 1e3], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms, wall = float(t[0]), float(t[1]) / 1e3
+        return r, ms, wall
+
+    for _ in range(max(3, args.warmup)):
+        res = batched()
+    inst = sum(r.instances for r in res)
+    sampler = ClockSampler(gpu_index(local))
+    time.sleep(0.25)
+    res, ms, wall = timed(batched, args.steps)
+    clocks = sampler.stop()
+    total = inst * args.steps * world
+    value = total / (ms / 1e3) / 1e9
+
+    # one check per model on one stream, same workspace reused (sized for the largest model)
+    ws1 = rc.workspace(max(rc.rc_workspace_size(h, opts) for h in handles))
+    ref = per_model(ws1)
+    same = all((a.status, a.instances, a.verdict, a.racy_cells, a.witness) ==
+               (b_.status, b_.instances, b_.verdict, b_.racy_cells, b_.witness) for a, b_ in zip(res, ref))
+    pm_steps = max(1, min(3, args.steps))
+    _, pm_ms, pm_wall = timed(lambda: per_model(ws1), pm_steps)
+    pm_value = inst * pm_steps * world / (pm_ms / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC + ", batched", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "models": len(models), "instances_per_rank": inst,
+                       "racy_models": sum(1 for r in res if r.verdict),
+                       "l2": "key buffers larger than L2", "parallelism": f"independent batches per rank x{world}"},
+            "per_model": {"value": pm_value, "unit": UNIT, "ms_per_step": pm_ms / pm_steps, "steps": pm_steps,
+                          "results_identical": same},
+            "speedup_vs_per_model": value / pm_value,
+            "e2e": {"value": total / wall / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * len(models),
+                    "d2h_bytes_per_step": 160 * len(models)},
+            "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -336,9 +437,14 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="affine", choices=["affine", "batch"],
+                    help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models")
+    ap.add_argument("--batch-models", type=int, default=10000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_native(args)
 
 

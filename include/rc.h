@@ -215,8 +215,13 @@ typedef struct rc_check_opts {
 enum { RC_TEST_STALL_LOOKBACK = 1,
        RC_TEST_FEW_SCAN_WARPS = 2   /* scan with 3 warps (long ranges per warp) */ };
 /* RC_OPT_STAGE_TIMES: record CUDA events between the stages of rc_check on its
- * stream so rc_ticket_stage_times can report per-stage device times. */
-enum { RC_OPT_STAGE_TIMES = 1 };
+ * stream so rc_ticket_stage_times can report per-stage device times.
+ * RC_OPT_GRAPH (rc_check_batch): the device work of a batch is captured once
+ * as a CUDA graph per (models, options, workspace) and relaunched as that one
+ * graph on later calls with the same arguments; rc_model_destroy drops the
+ * captured graphs.  Not a library convenience of the paper: the paper has no
+ * batching. */
+enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2 };
 
 typedef struct rc_inst {
   uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
@@ -268,6 +273,23 @@ rc_status rc_batch_workspace_size(rc_model* const* models, size_t n,
 rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts* opts,
                          void* workspace_dev, size_t workspace_bytes, void* stream,
                          rc_ticket* ticket);
+
+/* Autotuner (a library facility; the paper has no counterpart).  Times every
+ * candidate configuration of checking these models -- the sort path with each
+ * distinct number of radix passes (digits of 6..11 bits) and the hash path --
+ * on `stream` with the given workspace (3 runs each, the first one a warm-up),
+ * keeps the fastest whose check succeeded, and records it for the models'
+ * shape class (single model or batch; log2 of the model count, of the key
+ * count, and the width of the sorted key fields).  Later checks and workspace
+ * queries with path = RC_PATH_AUTO use the recorded choice for that class
+ * (else the sort path); a recorded choice that needs more workspace than a
+ * check is given falls back to the sort path.  The call blocks until the timed
+ * runs finish.  *best receives the chosen options (path and digit_bits set).
+ * Candidates that need more workspace than given are skipped; RC_E_NOMEM if
+ * none fits.  Batches (n > 1) time rc_check_batch's pipelines. */
+rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts,
+                  void* workspace_dev, size_t workspace_bytes, void* stream,
+                  rc_check_opts* best);
 
 /* Copy out the result(s) of a ticket: `out` holds 1 (rc_check) or n
  * (rc_check_batch) records.  wait=1 blocks until the work completes; wait=0

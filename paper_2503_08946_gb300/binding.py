@@ -39,12 +39,13 @@ RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
 RC_TEST_STALL_LOOKBACK = 1
 RC_TEST_FEW_SCAN_WARPS = 2
 RC_OPT_STAGE_TIMES = 1
+RC_OPT_GRAPH = 2
 
 # every entry point declared in include/rc.h
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
            "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times",
-           "rc_sort_keys_static", "rc_kernel_source"]
+           "rc_sort_keys_static", "rc_kernel_source", "rc_tune"]
 RC_SORT_STATIC_MAX_KEYS = 1 << 20
 
 
@@ -170,6 +171,9 @@ def load():
         lib.rc_check_batch.argtypes = [POINTER(c_void_p), c_size_t, POINTER(rc_check_opts), c_void_p,
                                        c_size_t, c_void_p, POINTER(c_void_p)]
         lib.rc_check_batch.restype = c_int
+        lib.rc_tune.argtypes = [POINTER(c_void_p), c_size_t, POINTER(rc_check_opts), c_void_p, c_size_t,
+                                c_void_p, POINTER(rc_check_opts)]
+        lib.rc_tune.restype = c_int
         lib.rc_report.argtypes = [c_void_p, POINTER(rc_result), c_int]
         lib.rc_report.restype = c_int
         lib.rc_expand_keys.argtypes = [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]
@@ -445,6 +449,20 @@ def rc_check_batch(models: Sequence[RcModel], opts, workspace, stream=None):
     if st != RC_OK:
         raise RcError(st, "rc_check_batch")
     return (t.value, len(models))
+
+
+def rc_tune(models: Sequence[RcModel], opts, workspace, stream=None) -> dict:
+    """Time the candidate configurations for these models, record the fastest
+    for their shape class (used by path=RC_PATH_AUTO) and return it."""
+    arr = (c_void_p * max(1, len(models)))(*[m.ptr for m in models])
+    o = _opts(opts)
+    best = rc_check_opts()
+    ws_bytes = workspace.numel() * workspace.element_size() if hasattr(workspace, "numel") else 0
+    st = load().rc_tune(arr, len(models), ctypes.byref(o) if o else None, c_void_p(_ptr(workspace)),
+                        c_size_t(ws_bytes), c_void_p(_stream(stream)), ctypes.byref(best))
+    if st != RC_OK:
+        raise RcError(st, "rc_tune")
+    return {f: getattr(best, f) for f, _ in rc_check_opts._fields_}
 
 
 @dataclass

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -505,35 +506,24 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
   return RC_OK;
 }
 
-rc_status enqueue_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, uint8_t* ws,
-                        size_t ws_bytes, cudaStream_t st, rc_ticket_s* t) {
-  BatchLayout L;
-  rc_status s = plan_batch(models, n, opts, &L);
-  if (s != RC_OK) return s;
-  if (!ws || ws_bytes < L.total) return RC_E_NOMEM;
-  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
-  if (n == 0) return RC_OK;
-  if (t->upload_cap < L.upload_bytes) {
-    if (t->upload) cudaFreeHost(t->upload);
-    t->upload = nullptr;
-    t->upload_cap = 0;
-    if (cudaMallocHost(&t->upload, L.upload_bytes) != cudaSuccess) return RC_E_NOMEM;
-    t->upload_cap = L.upload_bytes;
-  }
-  // model tables (pack-relative cell and key bases)
-  auto* table = static_cast<rc::BatchModel*>(t->upload);
-  auto* cbase = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(t->upload) + (L.cellbase_off - L.table_off));
-  t->cell_base.assign(n, 0);
-  t->field_bits.assign(n, 0);
+// Model tables of a batch (pack-relative key, cell and unit bases) into
+// `upload` (L.upload_bytes), and the per-model decoding data.
+void fill_batch_tables(rc_model* const* models, const BatchLayout& L, void* upload, std::vector<uint64_t>* cell_base,
+                       std::vector<uint32_t>* field_bits) {
+  const size_t n = L.packs.empty() ? 0 : L.packs.back().i1;
+  auto* table = static_cast<rc::BatchModel*>(upload);
+  auto* cbase = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(upload) + (L.cellbase_off - L.table_off));
+  cell_base->assign(n, 0);
+  field_bits->assign(n, 0);
   for (const BatchPack& k : L.packs) {
-    uint64_t key_base = 0, cell_base = 0, unit_base = 0;
+    uint64_t key_base = 0, cb = 0, unit_base = 0;
     for (size_t i = k.i0; i < k.i1; ++i) {
       const rc::Model& m = models[i]->m;
       const rc::DevModel& h = m.host;
       rc::BatchModel& b = table[i];
       b.dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
       b.key_base = key_base;
-      b.cell_base = cell_base;
+      b.cell_base = cb;
       b.unit_base = unit_base;
       b.n_threads = h.n_threads;
       b.n_stmts = h.n_stmts;
@@ -544,21 +534,27 @@ rc_status enqueue_batch(rc_model* const* models, size_t n, const rc_check_opts* 
       b.phase_bits = h.phase_bits;
       b.block_bits = h.block_bits;
       b.thread_bits = h.thread_bits;
-      cbase[i] = cell_base;
-      t->cell_base[i] = cell_base;
-      t->field_bits[i] = k.tb | (k.pb << 8);
+      cbase[i] = cb;
+      (*cell_base)[i] = cb;
+      (*field_bits)[i] = k.tb | (k.pb << 8);
       key_base += m.key_slots;
-      cell_base += m.total_cells;
+      cb += m.total_cells;
       unit_base += (uint64_t)h.n_stmts * b.n_chunks;
     }
   }
+}
+
+// Device work of a batch: upload of the tables, then every pack's pipeline.
+// The per-model result records stay in the workspace (L.res_off).
+rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_opts* opts, uint8_t* ws,
+                               const void* upload, cudaStream_t st) {
   auto* res = reinterpret_cast<rc::DevResult*>(ws + L.res_off);
   auto* pres = reinterpret_cast<rc::DevResult*>(ws + L.packres_off);
   const auto* dtable = reinterpret_cast<const rc::BatchModel*>(ws + L.table_off);
   const auto* dcbase = reinterpret_cast<const uint64_t*>(ws + L.cellbase_off);
   auto* queue = reinterpret_cast<unsigned long long*>(ws + L.queue_off);
   const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
-  s = cuda_status(cudaMemcpyAsync(ws + L.table_off, t->upload, L.upload_bytes, cudaMemcpyHostToDevice, st));
+  rc_status s = cuda_status(cudaMemcpyAsync(ws + L.table_off, upload, L.upload_bytes, cudaMemcpyHostToDevice, st));
   if (s == RC_OK) s = cuda_status(rc::launch_init_result(res, st, (uint32_t)n));
   for (const BatchPack& k : L.packs) {
     if (s != RC_OK) break;
@@ -609,9 +605,195 @@ rc_status enqueue_batch(rc_model* const* models, size_t n, const rc_check_opts* 
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
   }
-  if (s == RC_OK)
-    s = cuda_status(cudaMemcpyAsync(t->host, res, n * sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
   return s;
+}
+
+rc_status check_batch_layout(const BatchLayout& L, uint8_t* ws, size_t ws_bytes) {
+  if (!ws || ws_bytes < L.total) return RC_E_NOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
+  return RC_OK;
+}
+
+rc_status enqueue_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, uint8_t* ws,
+                        size_t ws_bytes, cudaStream_t st, rc_ticket_s* t) {
+  BatchLayout L;
+  rc_status s = plan_batch(models, n, opts, &L);
+  if (s == RC_OK) s = check_batch_layout(L, ws, ws_bytes);
+  if (s != RC_OK || n == 0) return s;
+  if (t->upload_cap < L.upload_bytes) {
+    if (t->upload) cudaFreeHost(t->upload);
+    t->upload = nullptr;
+    t->upload_cap = 0;
+    if (cudaMallocHost(&t->upload, L.upload_bytes) != cudaSuccess) return RC_E_NOMEM;
+    t->upload_cap = L.upload_bytes;
+  }
+  fill_batch_tables(models, L, t->upload, &t->cell_base, &t->field_bits);
+  s = enqueue_batch_device(L, n, opts, ws, t->upload, st);
+  if (s == RC_OK)
+    s = cuda_status(cudaMemcpyAsync(t->host, ws + L.res_off, n * sizeof(rc::DevResult), cudaMemcpyDeviceToHost,
+                                    st));
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of a batch (RC_OPT_GRAPH): the device work of one batch
+// signature (models, options, workspace) is captured once and relaunched as
+// one graph; the tables it uploads live in the cache entry.
+// ---------------------------------------------------------------------------
+struct GraphEntry {
+  std::vector<const void*> models;
+  uint32_t digit_bits = 0, test_flags = 0;
+  uint64_t spin = 0;
+  uint8_t* ws = nullptr;
+  size_t ws_bytes = 0;
+  int device = -1;
+  BatchLayout L;
+  void* upload = nullptr;
+  std::vector<uint64_t> cell_base;
+  std::vector<uint32_t> field_bits;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry*> g_graphs;
+constexpr size_t kMaxGraphs = 16;
+
+void graph_entry_free(GraphEntry* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->upload) cudaFreeHost(e->upload);
+  delete e;
+}
+
+void graph_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (GraphEntry* e : g_graphs) graph_entry_free(e);
+  g_graphs.clear();
+}
+
+cudaStream_t capture_stream(int device) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (device < 0 || device >= 64) return nullptr;
+  if (!streams[device] && cudaStreamCreateWithFlags(&streams[device], cudaStreamNonBlocking) != cudaSuccess)
+    return nullptr;
+  return streams[device];
+}
+
+rc_status enqueue_batch_graph(rc_model* const* models, size_t n, const rc_check_opts* opts, uint8_t* ws,
+                              size_t ws_bytes, cudaStream_t st, rc_ticket_s* t) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RC_E_CUDA;
+  const uint32_t db = opts ? opts->digit_bits : 0, tf = opts ? opts->test_flags : 0;
+  const uint64_t spin = opts ? opts->spin_limit : 0;
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  GraphEntry* hit = nullptr;
+  for (GraphEntry* e : g_graphs) {
+    if (e->device == dev && e->ws == ws && e->ws_bytes == ws_bytes && e->digit_bits == db && e->test_flags == tf &&
+        e->spin == spin && e->models.size() == n &&
+        std::equal(e->models.begin(), e->models.end(), models,
+                   [](const void* a, rc_model* b) { return a == static_cast<const void*>(b); })) {
+      hit = e;
+      break;
+    }
+  }
+  if (!hit) {
+    auto* e = new (std::nothrow) GraphEntry();
+    if (!e) return RC_E_NOMEM;
+    e->models.assign(models, models + n);
+    e->digit_bits = db;
+    e->test_flags = tf;
+    e->spin = spin;
+    e->ws = ws;
+    e->ws_bytes = ws_bytes;
+    e->device = dev;
+    rc_status s = plan_batch(models, n, opts, &e->L);
+    if (s == RC_OK) s = check_batch_layout(e->L, ws, ws_bytes);
+    if (s == RC_OK && cudaMallocHost(&e->upload, std::max<size_t>(e->L.upload_bytes, 256)) != cudaSuccess)
+      s = RC_E_NOMEM;
+    if (s != RC_OK) {
+      graph_entry_free(e);
+      return s;
+    }
+    fill_batch_tables(models, e->L, e->upload, &e->cell_base, &e->field_bits);
+    cudaStream_t cs = capture_stream(dev);
+    cudaGraph_t g = nullptr;
+    if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      graph_entry_free(e);
+      return RC_E_CUDA;
+    }
+    s = enqueue_batch_device(e->L, n, opts, ws, e->upload, cs);
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    if (s == RC_OK && ce != cudaSuccess) s = RC_E_CUDA;
+    if (s == RC_OK && cudaGraphInstantiate(&e->exec, g, 0) != cudaSuccess) s = RC_E_CUDA;
+    if (g) cudaGraphDestroy(g);
+    if (s != RC_OK) {
+      graph_entry_free(e);
+      return s;
+    }
+    if (g_graphs.size() >= kMaxGraphs) {
+      graph_entry_free(g_graphs.front());
+      g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(e);
+    hit = e;
+  }
+  t->cell_base = hit->cell_base;
+  t->field_bits = hit->field_bits;
+  if (n == 0) return RC_OK;
+  rc_status s = cuda_status(cudaGraphLaunch(hit->exec, st));
+  if (s == RC_OK)
+    s = cuda_status(cudaMemcpyAsync(t->host, ws + hit->L.res_off, n * sizeof(rc::DevResult),
+                                    cudaMemcpyDeviceToHost, st));
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: path (sort / hash) and radix digit width per shape class
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  uint32_t batch, n_log2, keys_log2, sort_bits;
+  bool operator<(const TuneKey& o) const {
+    if (batch != o.batch) return batch < o.batch;
+    if (n_log2 != o.n_log2) return n_log2 < o.n_log2;
+    if (keys_log2 != o.keys_log2) return keys_log2 < o.keys_log2;
+    return sort_bits < o.sort_bits;
+  }
+};
+struct TuneChoice {
+  uint32_t path, digit_bits;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tuned;
+
+TuneKey tune_key(rc_model* const* models, size_t n) {
+  TuneKey k{};
+  uint64_t keys = 0, cells = 0;
+  uint32_t pb = 0;
+  for (size_t i = 0; i < n; ++i) {
+    keys += models[i]->m.key_slots;
+    cells += models[i]->m.total_cells;
+    pb = std::max(pb, models[i]->m.host.phase_bits);
+  }
+  k.batch = n > 1 ? 1u : 0u;
+  k.n_log2 = rc::bit_length(n);
+  k.keys_log2 = rc::bit_length(keys);
+  k.sort_bits = rc::bit_length(cells) + pb;
+  return k;
+}
+
+// AUTO resolved: the tuned choice of the shape class, else the sort path.
+rc_check_opts resolve_opts(rc_model* const* models, size_t n, const rc_check_opts* opts) {
+  rc_check_opts o{};
+  if (opts) o = *opts;
+  if (o.path != RC_PATH_AUTO) return o;
+  o.path = RC_PATH_SORT;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(tune_key(models, n));
+  if (it != g_tuned.end()) {
+    o.path = it->second.path;
+    if (o.digit_bits == 0) o.digit_bits = it->second.digit_bits;
+  }
+  return o;
 }
 
 }  // namespace
@@ -723,6 +905,7 @@ rc_status rc_model_create(const rc_model_desc* desc, rc_model** out) {
 
 void rc_model_destroy(rc_model* m) {
   if (!m) return;
+  graph_cache_clear();   // captured batches may hold this model's program
   if (m->m.dev_program) cudaFree(m->m.dev_program);
   delete m;
 }
@@ -774,8 +957,10 @@ rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, siz
 
 rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes) {
   if (!m || !bytes) return RC_E_INVALID;
+  rc_model* mm = const_cast<rc_model*>(m);
+  const rc_check_opts o = resolve_opts(&mm, 1, opts);
   rc::WorkspacePlan p;
-  rc::plan_workspace(m->m, opts, &p);
+  rc::plan_workspace(m->m, &o, &p);
   *bytes = p.total;
   return RC_OK;
 }
@@ -788,7 +973,19 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   if (!t) return RC_E_NOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool want_times = opts && (opts->flags & RC_OPT_STAGE_TIMES);
-  rc_status s = enqueue_check(m, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host,
+  rc_check_opts o = resolve_opts(&m, 1, opts);
+  if (opts && opts->path == RC_PATH_AUTO) {
+    // a tuned choice that needs more workspace than given falls back to the sort path
+    size_t need = 0;
+    rc::WorkspacePlan p;
+    rc::plan_workspace(m->m, &o, &p);
+    need = p.total;
+    if (need > ws_bytes) {
+      o = *opts;
+      o.path = RC_PATH_SORT;
+    }
+  }
+  rc_status s = enqueue_check(m, &o, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host,
                               want_times ? t : nullptr);
   if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
   if (s != RC_OK) {
@@ -804,10 +1001,12 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
 // requested; the hash path checks the models one after another.
 bool batch_is_sequential(const rc_check_opts* opts) { return opts && opts->path == RC_PATH_HASH; }
 
-rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_check_opts* opts, size_t* bytes) {
+rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_check_opts* opts_in, size_t* bytes) {
   if (!bytes || (n && !models)) return RC_E_INVALID;
   for (size_t i = 0; i < n; ++i)
     if (!models[i]) return RC_E_INVALID;
+  const rc_check_opts ro = resolve_opts(models, n, opts_in);
+  const rc_check_opts* opts = &ro;
   if (batch_is_sequential(opts)) {
     size_t mx = 0;
     for (size_t i = 0; i < n; ++i) {
@@ -825,12 +1024,22 @@ rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_ch
   return RC_OK;
 }
 
-rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts* opts, void* workspace,
+rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts* opts_in, void* workspace,
                          size_t ws_bytes, void* stream, rc_ticket* ticket) {
   if (!ticket || (n && !models)) return RC_E_INVALID;
   *ticket = nullptr;
   for (size_t i = 0; i < n; ++i)
     if (!models[i]) return RC_E_INVALID;
+  rc_check_opts ro = resolve_opts(models, n, opts_in);
+  if (opts_in && opts_in->path == RC_PATH_AUTO) {
+    size_t need = 0;
+    rc_batch_workspace_size(models, n, &ro, &need);
+    if (need > ws_bytes) {
+      ro = *opts_in;
+      ro.path = RC_PATH_SORT;
+    }
+  }
+  const rc_check_opts* opts = &ro;
   rc_ticket_s* t = ticket_get(n);
   if (!t) return RC_E_NOMEM;
   for (size_t i = 0; i < n; ++i) t->models[i] = models[i];
@@ -839,6 +1048,8 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
   if (batch_is_sequential(opts)) {
     for (size_t i = 0; i < n && s == RC_OK; ++i)
       s = enqueue_check(models[i], opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t->host + i);
+  } else if (opts && (opts->flags & RC_OPT_GRAPH)) {
+    s = enqueue_batch_graph(models, n, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t);
   } else {
     s = enqueue_batch(models, n, opts, static_cast<uint8_t*>(workspace), ws_bytes, st, t);
   }
@@ -848,6 +1059,102 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
     return s;
   }
   *ticket = t;
+  return RC_OK;
+}
+
+rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts, void* workspace, size_t ws_bytes,
+                  void* stream, rc_check_opts* best) {
+  if (!best || !models || n == 0) return RC_E_INVALID;
+  for (size_t i = 0; i < n; ++i)
+    if (!models[i]) return RC_E_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  rc_check_opts base{};
+  if (opts) base = *opts;
+  base.flags &= ~(uint32_t)(RC_OPT_STAGE_TIMES | RC_OPT_GRAPH);
+  base.early_exit = 0;
+  const TuneKey key = tune_key(models, n);
+  const uint32_t sort_bits = n == 1 ? models[0]->m.host.sort_hi - models[0]->m.host.sort_lo : key.sort_bits;
+  // candidates: every distinct number of sort passes for digits of 6..11 bits, and the hash path
+  std::vector<rc_check_opts> cands;
+  std::vector<uint32_t> passes;
+  for (uint32_t d = 6; d <= 11; ++d) {
+    rc::SortPlan sp;
+    rc::plan_sort(0, sort_bits, d, &sp);
+    if (std::find(passes.begin(), passes.end(), sp.n_pass) != passes.end()) continue;
+    passes.push_back(sp.n_pass);
+    rc_check_opts o = base;
+    o.path = RC_PATH_SORT;
+    o.digit_bits = d;
+    cands.push_back(o);
+  }
+  {
+    rc_check_opts o = base;
+    o.path = RC_PATH_HASH;
+    o.digit_bits = 0;
+    cands.push_back(o);
+  }
+  rc_ticket_s* t = ticket_get(n);
+  if (!t) return RC_E_NOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    ticket_put(t);
+    return RC_E_CUDA;
+  }
+  float best_ms = 0.f;
+  bool any = false;
+  rc_check_opts bo = cands[0];
+  rc_status fail = RC_OK;
+  for (const rc_check_opts& c : cands) {
+    size_t need = 0;
+    if (n == 1) rc_workspace_size(models[0], &c, &need);
+    else rc_batch_workspace_size(models, n, &c, &need);
+    if (need > ws_bytes) continue;
+    float ms_min = 0.f;
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) {   // run 0 warms up
+      rc_status s = cuda_status(cudaEventRecord(e0, st));
+      if (s == RC_OK) {
+        if (n == 1) {
+          s = enqueue_check(models[0], &c, ws, ws_bytes, st, t->host);
+        } else if (batch_is_sequential(&c)) {
+          for (size_t i = 0; i < n && s == RC_OK; ++i) s = enqueue_check(models[i], &c, ws, ws_bytes, st, t->host + i);
+        } else {
+          s = enqueue_batch(models, n, &c, ws, ws_bytes, st, t);
+        }
+      }
+      if (s == RC_OK) s = cuda_status(cudaEventRecord(e1, st));
+      if (s == RC_OK) s = cuda_status(cudaEventSynchronize(e1));
+      if (s != RC_OK) {
+        ok = false;
+        if (s == RC_E_CUDA) fail = s;
+        break;
+      }
+      for (size_t i = 0; i < n; ++i)
+        if (t->host[i].err) ok = false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r == 1 || (r > 1 && ms < ms_min)) ms_min = ms;
+    }
+    if (ok && (!any || ms_min < best_ms)) {
+      best_ms = ms_min;
+      bo = c;
+      any = true;
+    }
+    if (fail != RC_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ticket_put(t);
+  if (fail != RC_OK) return fail;
+  if (!any) return RC_E_NOMEM;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = TuneChoice{bo.path, bo.digit_bits};
+  }
+  *best = bo;
+  if (opts) best->flags = opts->flags;
   return RC_OK;
 }
 

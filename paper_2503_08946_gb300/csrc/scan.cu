@@ -10,13 +10,14 @@
 //
 // K3a (scan_cells_kernel): each warp owns a contiguous range of segments of
 //      32 x kScanRun keys, staged through shared memory with coalesced loads.
-//      Every cell is folded by exactly one lane, the lane whose run holds the
-//      cell's first key: a lane skips the keys that continue the cell open
-//      before its run, folds the cells that begin in it, and follows its last
-//      cell into the next lanes' runs.  A cell still open at the segment end
-//      is carried by lane 0 into the next segment.  A cell carried over more
-//      than kCarryMaxSegs segments, or still open at the end of the warp's
-//      range, is handed to K3b by its first position.
+//      Every lane folds its run of kScanRun keys in one pass: the keys that
+//      continue the cell open before the run into a prefix part, the cells
+//      that begin in the run into a fold state (closed ones are counted at
+//      once).  The cell open at a run's end is then completed by merging the
+//      prefix parts of the following lanes (usually one), and a cell open at
+//      the segment end is carried into the next segment.  A cell carried over
+//      more than kCarryMaxSegs segments, or still open at the end of the
+//      warp's range, is handed to K3b by its first position.
 // K3b (scan_long_kernel): one block per handed-over cell folds it from its
 //      first key, 2048 keys at a time, as an ordered reduction of CellPieces
 //      (rc_internal.h).
@@ -81,48 +82,100 @@ __device__ __forceinline__ DevResult* result_of(const ScanArgs& a, uint64_t cell
   return a.res + lo;
 }
 
-// The cell a lane is folding.  cp = key >> phase_shift (cell and phase), bt =
-// the (block, thread) bits of a key.
-struct CellState {
-  uint64_t cp;       // (cell, phase) of the current phase group
-  uint64_t start;    // position of the cell's first key
-  unsigned bt0;      // (block, thread) of the cell's first key
-  unsigned gbt0;     // (block, thread) of the group's first key
+// Fold state of a run of keys of one cell (a whole cell, or a part of one).
+// Keys are compared through masks: same cell iff ((k ^ k') & cell_mask) == 0,
+// same phase group iff ((k ^ k') & group_mask) == 0.  bt = the (block, thread)
+// bits of a key.  The first phase group is kept apart until it closes, so that
+// a part that continues another can be merged into it (merge below).
+struct Fold {
+  uint64_t fk;       // first key
+  uint64_t gk;       // a key of the current (last) phase group
+  uint64_t start;    // position of the first key
+  unsigned bt0;      // bt of the first key
+  unsigned gbt0;     // bt of the current group's first key
   unsigned f;        // flags below
 };
-constexpr unsigned kFW = 1u, kFMultiB = 2u, kFGMulti = 4u, kFGW = 8u, kFInner = 16u;
+constexpr unsigned kFW = 1u;        // some write
+constexpr unsigned kFMB = 2u;       // two blocks
+constexpr unsigned kFGM = 4u;       // current group: two (block, thread)
+constexpr unsigned kFGW = 8u;       // current group: a write
+constexpr unsigned kFIn = 16u;      // a closed group other than the first is racy
+constexpr unsigned kFFO = 32u;      // the first group is still the current group
+constexpr unsigned kFFM = 64u;      // closed first group: two (block, thread)
+constexpr unsigned kFFW = 128u;     // closed first group: a write
 
-__device__ __forceinline__ void cs_start(CellState& s, uint64_t cp, uint64_t pos, unsigned bt, bool w) {
-  s.cp = cp;
+struct FoldCtx {
+  uint64_t group_mask;   // bits of (cell, phase)
+  unsigned btm;          // mask of the (block, thread) bits after >> 1
+  uint32_t tb;           // thread bits
+};
+
+__device__ __forceinline__ unsigned key_bt(const FoldCtx& c, uint64_t k) { return (unsigned)(k >> 1) & c.btm; }
+
+__device__ __forceinline__ void fold_start(Fold& s, uint64_t k, uint64_t pos, unsigned bt) {
+  s.fk = s.gk = k;
   s.start = pos;
   s.bt0 = s.gbt0 = bt;
-  s.f = w ? (kFW | kFGW) : 0u;
+  s.f = kFFO | ((k & 1ull) ? (kFW | kFGW) : 0u);
 }
-// Add a key of the same cell.  Two keys of one phase group with different
-// (block, thread) are two threads; if their blocks differ the cell is
-// multi-block anyway, and then it races iff it has a write.
-__device__ __forceinline__ void cs_add(CellState& s, uint64_t cp, unsigned bt, bool w, uint32_t thread_bits) {
+// close the current group, whose flags are gm / gw
+__device__ __forceinline__ unsigned close_group(unsigned f, bool gm, bool gw) {
+  if (f & kFFO) return (f & ~kFFO) | (gm ? kFFM : 0u) | (gw ? kFFW : 0u);
+  return (gm && gw) ? (f | kFIn) : f;
+}
+// add a key of the same cell
+__device__ __forceinline__ void fold_add(const FoldCtx& c, Fold& s, uint64_t k, unsigned bt) {
   unsigned f = s.f;
-  if (((bt ^ s.bt0) >> thread_bits) != 0u) f |= kFMultiB;
-  if (cp != s.cp) {
-    if ((f & (kFGMulti | kFGW)) == (kFGMulti | kFGW)) f |= kFInner;
-    f &= ~(kFGMulti | kFGW);
-    s.cp = cp;
+  if (((bt ^ s.bt0) >> c.tb) != 0u) f |= kFMB;
+  if (((k ^ s.gk) & c.group_mask) != 0ull) {
+    f = close_group(f, (f & kFGM) != 0u, (f & kFGW) != 0u) & ~(kFGM | kFGW);
+    s.gk = k;
     s.gbt0 = bt;
   } else if (bt != s.gbt0) {
-    f |= kFGMulti;
+    f |= kFGM;
   }
-  if (w) f |= kFW | kFGW;
+  if (k & 1ull) f |= kFW | kFGW;
   s.f = f;
 }
-__device__ __forceinline__ bool cs_racy(const CellState& s) {
+__device__ __forceinline__ bool fold_racy(const Fold& s) {
   const unsigned f = s.f;
   if (!(f & kFW)) return false;
-  return (f & (kFMultiB | kFInner)) != 0u || (f & (kFGMulti | kFGW)) == (kFGMulti | kFGW);
+  if (f & (kFMB | kFIn)) return true;
+  if ((f & (kFGM | kFGW)) == (kFGM | kFGW)) return true;
+  return !(f & kFFO) && (f & (kFFM | kFFW)) == (kFFM | kFFW);
 }
-__device__ __forceinline__ CellState cs_shfl(const CellState& s, int src) {
-  CellState r;
-  r.cp = __shfl_sync(FULL, s.cp, src);
+// s followed by p, a part that continues s's cell
+__device__ __forceinline__ void fold_merge(const FoldCtx& c, Fold& s, const Fold& p) {
+  unsigned f = s.f | (p.f & kFW);
+  if ((p.f & kFMB) || ((p.bt0 ^ s.bt0) >> c.tb) != 0u) f |= kFMB;
+  const bool p_single = (p.f & kFFO) != 0u;       // p holds one group
+  const bool pfm = p_single ? (p.f & kFGM) != 0u : (p.f & kFFM) != 0u;
+  const bool pfw = p_single ? (p.f & kFGW) != 0u : (p.f & kFFW) != 0u;
+  if (((p.fk ^ s.gk) & c.group_mask) == 0ull) {
+    // p's first group continues s's current group
+    const bool gm = (f & kFGM) || pfm || p.bt0 != s.gbt0;
+    const bool gw = (f & kFGW) || pfw;
+    if (p_single) {
+      f = (f & ~(kFGM | kFGW)) | (gm ? kFGM : 0u) | (gw ? kFGW : 0u);
+    } else {
+      f = close_group(f, gm, gw) | (p.f & kFIn);
+      f = (f & ~(kFGM | kFGW)) | (p.f & (kFGM | kFGW));
+      s.gk = p.gk;
+      s.gbt0 = p.gbt0;
+    }
+  } else {
+    f = close_group(f, (f & kFGM) != 0u, (f & kFGW) != 0u);
+    if (!p_single && pfm && pfw) f |= kFIn;
+    f = (f & ~(kFGM | kFGW)) | (p.f & (kFGM | kFGW)) | (p.f & kFIn);
+    s.gk = p.gk;
+    s.gbt0 = p.gbt0;
+  }
+  s.f = f;
+}
+__device__ __forceinline__ Fold fold_shfl(const Fold& s, int src) {
+  Fold r;
+  r.fk = __shfl_sync(FULL, s.fk, src);
+  r.gk = __shfl_sync(FULL, s.gk, src);
   r.start = __shfl_sync(FULL, s.start, src);
   r.bt0 = __shfl_sync(FULL, s.bt0, src);
   r.gbt0 = __shfl_sync(FULL, s.gbt0, src);
@@ -145,8 +198,11 @@ __device__ __forceinline__ int seg_slot(int j) { return (j / kScanRun) * kRunPad
 
 __global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a) {
   __shared__ uint64_t sk[kScanWarps][32 * kRunPad];
-  const uint32_t cs = a.cell_shift, ps = a.phase_shift, pb = a.phase_bits, tb = a.thread_bits;
-  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  FoldCtx c;
+  c.group_mask = ~((1ull << a.phase_shift) - 1ull);
+  c.btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  c.tb = a.thread_bits;
+  const uint64_t cell_mask = ~((1ull << a.cell_shift) - 1ull);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t* my = sk[w];
   const uint64_t n_seg = (a.n + kSegKeys - 1) / kSegKeys;
@@ -154,13 +210,24 @@ __global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a)
   const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
   unsigned long long count = 0, minstart = ~0ull;
-  // cell of the key just before the current segment (none before key 0)
-  uint64_t c_before = ~0ull;
-  if (seg0 > 0 && seg0 < seg1) c_before = a.keys[seg0 * kSegKeys - 1] >> cs;
-  bool carry = false;     // warp-uniform: lane 0 folds a cell begun in an earlier segment
+  auto report = [&](const Fold& x) {
+    if (!fold_racy(x)) return;
+    if (a.n_models) {
+      DevResult* r = result_of(a, x.fk >> a.cell_shift);
+      atomicAdd(&r->racy_cells, 1ull);
+      atomicMin(&r->min_start, (unsigned long long)x.start);
+    } else {
+      ++count;
+      minstart = min(minstart, (unsigned long long)x.start);
+    }
+  };
+  // key just before the current segment (kSentinel: none before the range)
+  uint64_t k_before = kSentinel;
+  if (seg0 > 0 && seg0 < seg1) k_before = a.keys[seg0 * kSegKeys - 1];
+  bool carry = false;    // warp-uniform: a cell begun in an earlier segment is still open
   int carried = 0;
-  CellState cc;
-  cc.cp = 0; cc.start = 0; cc.bt0 = cc.gbt0 = 0; cc.f = 0;
+  Fold cc;
+  cc.fk = cc.gk = 0; cc.start = 0; cc.bt0 = cc.gbt0 = 0; cc.f = 0;
   for (uint64_t seg = seg0; seg < seg1; ++seg) {
     const uint64_t S = seg * kSegKeys;
 #pragma unroll
@@ -180,100 +247,91 @@ __global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a)
       my[o + 1] = y;
     }
     __syncwarp();
-    // (1) the carried cell continues over the segment's leading keys
-    if (carry) {
-      int lead = 0;
-      if (lane == 0) {
-        const uint64_t cell = cc.cp >> pb;
-        while (lead < kSegKeys) {
-          const uint64_t k = my[seg_slot(lead)];
-          if (k == kSentinel || (k >> cs) != cell) break;
-          cs_add(cc, k >> ps, (unsigned)(k >> 1) & btm, (k & 1ull) != 0, tb);
-          ++lead;
+    // (1) fold the run: P = the keys that continue the cell open before the
+    // run, O = the cell begun last in the run (earlier ones are closed here)
+    const uint64_t s = S + (uint64_t)lane * kScanRun;
+    const uint64_t* run = my + lane * kRunPad;
+    const uint64_t kp = lane > 0 ? my[(lane - 1) * kRunPad + kScanRun - 1] : k_before;
+    Fold P, O;
+    P.fk = P.gk = 0; P.start = 0; P.bt0 = P.gbt0 = 0; P.f = 0;
+    O = P;
+    bool hasP = false, hasO = false, term = false;
+    bool in_prefix = kp != kSentinel;
+#pragma unroll 4
+    for (int q = 0; q < kScanRun; ++q) {
+      const uint64_t k = run[q];
+      if (k == kSentinel) term = true;
+      if (term) continue;
+      const unsigned bt = key_bt(c, k);
+      if (in_prefix) {
+        if (((k ^ kp) & cell_mask) == 0ull) {
+          if (hasP) fold_add(c, P, k, bt);
+          else fold_start(P, k, s + q, bt);
+          hasP = true;
+          continue;
         }
+        in_prefix = false;
       }
-      lead = __shfl_sync(FULL, lead, 0);
-      if (lead < kSegKeys) {
-        if (lane == 0 && cs_racy(cc)) {
-          if (a.n_models) {
-            DevResult* r = result_of(a, cc.cp >> pb);
-            atomicAdd(&r->racy_cells, 1ull);
-            atomicMin(&r->min_start, (unsigned long long)cc.start);
-          } else {
-            ++count;
-            minstart = min(minstart, (unsigned long long)cc.start);
-          }
-        }
+      if (hasO && ((k ^ O.fk) & cell_mask) == 0ull) {
+        fold_add(c, O, k, bt);
+      } else {
+        if (hasO) report(O);
+        fold_start(O, k, s + q, bt);
+        hasO = true;
+      }
+    }
+    const bool pfull = hasP && !hasO && !term;   // the prefix fills the whole run
+    // (2) the carried cell continues through the leading prefixes
+    if (carry) {
+      bool open = true;
+      for (int src = 0; src < 32 && open; ++src) {
+        const bool h = __shfl_sync(FULL, hasP, src);
+        const bool full = __shfl_sync(FULL, pfull, src);
+        const Fold ps = fold_shfl(P, src);
+        if (h) fold_merge(c, cc, ps);
+        if (!full) open = false;
+      }
+      if (!open) {
+        if (lane == 0) report(cc);
         carry = false;
       } else if (++carried > kCarryMaxSegs) {
         if (lane == 0) hand_over(a, cc.start);
         carry = false;
       }
     }
-    // (2) the cells that begin in this lane's run
-    const uint64_t s = S + (uint64_t)lane * kScanRun;
-    const int len = s < a.n ? (int)min((uint64_t)kScanRun, a.n - s) : 0;
-    const uint64_t* run = my + lane * kRunPad;
-    const uint64_t c_prev = lane > 0 ? (my[(lane - 1) * kRunPad + kScanRun - 1] >> cs) : c_before;
-    CellState st;
-    st.cp = 0; st.start = 0; st.bt0 = st.gbt0 = 0; st.f = 0;
-    bool has = false, term = false;
-    int q = 0;
-    for (; q < len; ++q) {
-      const uint64_t k = run[q];
-      if (k == kSentinel) { term = true; break; }
-      if ((k >> cs) != c_prev) break;
-    }
-    auto close = [&](const CellState& x) {
-      if (!cs_racy(x)) return;
-      if (a.n_models) {
-        DevResult* r = result_of(a, x.cp >> pb);
-        atomicAdd(&r->racy_cells, 1ull);
-        atomicMin(&r->min_start, (unsigned long long)x.start);
-      } else {
-        ++count;
-        minstart = min(minstart, (unsigned long long)x.start);
-      }
-    };
-    for (; q < len && !term; ++q) {
-      const uint64_t k = run[q];
-      if (k == kSentinel) { term = true; break; }
-      const uint64_t cp = k >> ps;
-      const unsigned bt = (unsigned)(k >> 1) & btm;
-      const bool wr = (k & 1ull) != 0;
-      if (!has || (cp >> pb) != (st.cp >> pb)) {
-        if (has) close(st);
-        cs_start(st, cp, s + q, bt, wr);
-        has = true;
-      } else {
-        cs_add(st, cp, bt, wr, tb);
-      }
-    }
-    // (3) the run's last cell continues into the next lanes' runs
+    // (3) each lane's last cell continues through the following prefixes
+    bool open = hasO;
     bool open_end = false;
-    if (has) {
-      if (term || len < kScanRun) {
-        close(st);
-      } else {
-        const uint64_t cell = st.cp >> pb;
-        bool ended = false;
-        for (int j = (lane + 1) * kScanRun; j < kSegKeys; ++j) {
-          const uint64_t k = my[seg_slot(j)];
-          if (k == kSentinel || (k >> cs) != cell) { ended = true; break; }
-          cs_add(st, k >> ps, (unsigned)(k >> 1) & btm, (k & 1ull) != 0, tb);
+    if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= a.n)) {   // the keys end in this run
+      report(O);
+      open = false;
+    }
+    for (int d = 1; __any_sync(FULL, open); ++d) {
+      const int src = lane + d < 32 ? lane + d : 31;
+      const bool h = __shfl_sync(FULL, hasP, src);
+      const bool full = __shfl_sync(FULL, pfull, src);
+      const Fold ps = fold_shfl(P, src);
+      if (open) {
+        if (lane + d >= 32) {
+          open = false;
+          open_end = true;
+        } else {
+          if (h) fold_merge(c, O, ps);
+          if (!full) {
+            report(O);
+            open = false;
+          }
         }
-        if (ended || S + kSegKeys >= a.n) close(st);
-        else open_end = true;
       }
     }
     // (4) the cell open at the segment end (at most one lane) becomes the carry
     const unsigned OE = __ballot_sync(FULL, open_end);
     if (OE) {
-      cc = cs_shfl(st, __ffs(OE) - 1);
+      cc = fold_shfl(O, __ffs(OE) - 1);
       carry = true;
       carried = 0;
     }
-    c_before = my[31 * kRunPad + kScanRun - 1] >> cs;
+    k_before = my[31 * kRunPad + kScanRun - 1];
     __syncwarp();
   }
   // a cell still open at the range end continues past it

@@ -135,3 +135,40 @@ def test_batch_workspace_too_small(rc):
     with pytest.raises(rc.RcError) as e:
         rc.rc_check_batch(handles, None, ws)
     assert e.value.status == rc.RC_E_NOMEM
+
+
+def test_graph_replay(rc):
+    """RC_OPT_GRAPH: the first call captures the batch as a CUDA graph, later
+    calls relaunch it; every call gives the oracle's results."""
+    models = [w.tiny_random(s) for s in range(400, 430)] + [w.random_affine(9, n_blocks=4, block=128, plant=True)]
+    handles = [rc.rc_model_create(m) for m in models]
+    opts = {"flags": rc.binding.RC_OPT_GRAPH}
+    ws = rc.workspace(rc.rc_batch_workspace_size(handles, opts))
+    exp = [oracle.check(m) for m in models]
+    for _ in range(3):
+        res = rc.rc_report(rc.rc_check_batch(handles, opts, ws))
+        for m, g, e in zip(models, res, exp):
+            assert_same(m, g, e)
+
+
+def test_tuner_choice_is_used(rc):
+    """rc_tune records a choice for the shape class; AUTO checks then give the
+    oracle's results with it, for a single model and for a batch."""
+    m = w.random_affine(5, n_blocks=8, block=256, plant=True)
+    h = rc.rc_model_create(m)
+    ws = rc.workspace(max(rc.rc_workspace_size(h, {"path": 1, "digit_bits": d}) for d in (6, 8, 11)) +
+                      rc.rc_workspace_size(h, {"path": 2}))
+    best = rc.rc_tune([h], None, ws)
+    assert best["path"] in (1, 2)
+    g = rc.rc_report(rc.rc_check(h, {"path": 0}, ws))[0]
+    assert_same(m, g, oracle.check(m))
+
+    models = [w.tiny_random(s) for s in range(500, 540)]
+    hs = [rc.rc_model_create(x) for x in models]
+    need = max(rc.rc_batch_workspace_size(hs, {"path": p, "digit_bits": d}) for p, d in ((1, 6), (1, 11), (2, 0)))
+    wsb = rc.workspace(need)
+    best = rc.rc_tune(hs, None, wsb)
+    assert best["path"] in (1, 2)
+    res = rc.rc_report(rc.rc_check_batch(hs, {"path": 0}, wsb))
+    for x, g in zip(models, res):
+        assert_same(x, g, oracle.check(x))
