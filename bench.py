@@ -425,6 +425,105 @@ def run_batch(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving: Poisson arrivals through the continuous-batching request server
+# ---------------------------------------------------------------------------
+SERVE_WORKLOAD = ("Poisson arrivals at {rate:g} req/s of seeded random models (threads log-uniform 32..65,536, "
+                  "1-8 loop-free access statements, 1% planted races), request server with a {mem} GB "
+                  "workspace pool and {slots} stream slots")
+
+
+def run_serve(args):
+    import threading
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+    stream = w.request_stream(args.requests, rate_hz=args.rate, seed=args.seed + rank)
+    handles = [rc.rc_model_create(m) for _, m in stream]
+    srv = rc.RcServer(memory_bytes=args.pool_gb << 30, slots=args.slots)
+
+    def drain(n, timeout=600.0):
+        got, t0 = {}, time.time()
+        while len(got) < n:
+            for d in srv.poll(cap=4096, wait_ms=20):
+                got[d.request] = d
+            if time.time() - t0 > timeout:
+                raise RuntimeError(f"serving stalled: {len(got)} of {n} finished")
+        return got
+
+    # warm-up: the first requests, all at once
+    warm = [srv.submit(h) for h in handles[:min(200, len(handles))]]
+    drain(len(warm))
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(gpu_index(local))
+    time.sleep(0.25)
+    ids = [None] * len(handles)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, ((t, _), h) in enumerate(zip(stream, handles)):
+            dt = t0 + t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[i] = srv.submit(h)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    got = drain(len(handles))
+    th.join()
+    clocks = sampler.stop()
+    recs = [got[i] for i in ids]
+    bad = [r for r in recs if r.result.status != rc.RC_OK]
+    if bad:
+        raise RuntimeError(f"request failed: {rc.rc_status_str(bad[0].result.status)}")
+    lat = sorted((r.done_s - r.submit_s) * 1e3 for r in recs)
+    q = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))]
+    t_first = min(r.submit_s for r in recs)
+    t_last = max(r.done_s for r in recs)
+    inst = sum(r.result.instances for r in recs)
+    span = t_last - t_first
+    value = inst / span / 1e9
+    if dist:
+        t = torch.tensor([inst, span], dtype=torch.float64, device="cuda")
+        tot = t.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        value = float(tot[0]) / float(mx[1]) / 1e9
+    srv.close()
+    if rank == 0:
+        sizes = [r.batch_size for r in recs]
+        line = {
+            "metric": METRIC + ", served", "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": len(recs), "warmup": len(warm), "ms_per_step": span * 1e3 / len(recs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD.format(rate=args.rate, mem=args.pool_gb, slots=args.slots),
+                       "requests": len(recs), "instances": inst,
+                       "offered_rate_hz": args.rate, "achieved_rate_hz": len(recs) / span,
+                       "l2": "requests are small; pool reused", "parallelism": f"independent streams per rank x{world}"},
+            "latency_ms": {"p50": q(0.50), "p90": q(0.90), "p99": q(0.99), "max": lat[-1],
+                           "mean": sum(lat) / len(lat)},
+            "batch_size": {"mean": sum(sizes) / len(sizes), "max": max(sizes)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 96, "d2h_bytes_per_step": 160},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,14 +536,21 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="affine", choices=["affine", "batch"],
-                    help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models")
+    ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve"],
+                    help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models; "
+                         "serve: Poisson request stream through the request server")
     ap.add_argument("--batch-models", type=int, default=10000)
+    ap.add_argument("--requests", type=int, default=4000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--pool-gb", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_native(args)
 
 

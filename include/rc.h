@@ -291,6 +291,60 @@ rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts,
                   void* workspace_dev, size_t workspace_bytes, void* stream,
                   rc_check_opts* best);
 
+/* ------------------------------------------------------------------------- */
+/* request server (continuous batching; a library facility, the paper has no   */
+/* counterpart)                                                                */
+/* ------------------------------------------------------------------------- */
+
+/* A server owns a pool of device memory and `slots` CUDA streams.  Its
+ * scheduler thread admits queued requests whenever a slot is idle and the pool
+ * has room: the oldest waiting requests, as many as fit the largest free block
+ * (at most max_batch, 0 = 1024), are checked together as one rc_check_batch on
+ * that slot, so batches of different slots overlap on the device.  Each
+ * request's result is the one rc_check gives for its model (the batched
+ * pipeline is exact).  Requests are served in arrival order.  A request that
+ * cannot fit the pool even when it is empty completes with RC_E_NOMEM. */
+typedef struct rc_server rc_server;
+typedef struct rc_server_opts {
+  uint64_t memory_bytes;   /* device pool for workspaces, allocated at creation */
+  uint32_t slots;          /* batches in flight at once (1..64)                  */
+  uint32_t max_batch;      /* requests per batch, 0 = 1024                       */
+  uint32_t digit_bits;     /* radix digit width of the sort, 0 = auto            */
+  uint32_t reserved;
+} rc_server_opts;
+
+typedef struct rc_server_done {
+  uint64_t request;        /* id from rc_server_submit                           */
+  rc_result result;
+  double submit_s;         /* host steady-clock seconds: submission,             */
+  double start_s;          /*   enqueue of its batch,                            */
+  double done_s;           /*   completion seen by the scheduler                 */
+  uint32_t batch_size;     /* requests in its batch                              */
+  uint32_t pad;
+} rc_server_done;
+
+/* Create a server on the current device (allocates the pool, creates the
+ * streams, starts the scheduler thread).  RC_E_INVALID for slots outside
+ * 1..64 or memory_bytes < 256; RC_E_NOMEM if the pool cannot be allocated. */
+rc_status rc_server_create(const rc_server_opts* opts, rc_server** out);
+
+/* Queue a check of `model` (which must stay alive until its result is
+ * polled); *request receives its id.  Thread-safe; does not block on the GPU. */
+rc_status rc_server_submit(rc_server* server, rc_model* model, uint64_t* request);
+
+/* Move up to `cap` finished requests into `out` (*n_out of them), waiting up to
+ * wait_ms milliseconds for one if none is ready.  Returns RC_E_CUDA once a CUDA
+ * error has been seen by the scheduler, else RC_OK. */
+rc_status rc_server_poll(rc_server* server, rc_server_done* out, size_t cap, size_t* n_out,
+                         int wait_ms);
+
+/* Requests waiting for admission and requests in flight. */
+rc_status rc_server_stats(rc_server* server, uint64_t* pending, uint64_t* in_flight);
+
+/* Finish every queued and in-flight request, then free the server (results not
+ * yet polled are dropped). */
+rc_status rc_server_destroy(rc_server* server);
+
 /* Copy out the result(s) of a ticket: `out` holds 1 (rc_check) or n
  * (rc_check_batch) records.  wait=1 blocks until the work completes; wait=0
  * returns RC_E_NOT_READY (ticket still valid) if it has not.  After any other

@@ -13,7 +13,7 @@ in Python with the same names.  The CUDA library must be built
 """
 from .binding import (RC_OK, RC_E_INVALID, RC_E_KEY_OVERFLOW, RC_E_OOB, RC_E_NOMEM, RC_E_TIMEOUT,
                       RC_E_CUDA, RC_E_NOT_READY, RC_E_UNSUPPORTED, RC_PATH_AUTO, RC_PATH_SORT,
-                      RC_PATH_HASH, EXPORTS, NotReady, RcError, RcModel, Result, check, load,
+                      RC_PATH_HASH, EXPORTS, NotReady, RcError, RcModel, RcServer, Result, check, load,
                       rc_batch_workspace_size, rc_check, rc_check_batch, rc_expand_keys, rc_get_limits,
                       rc_model_create, rc_model_create_status, rc_kernel_source, rc_model_destroy, rc_model_layout,
                       rc_report, rc_sort_keys, rc_sort_keys_static, rc_ticket_stage_times, rc_sort_workspace_size, rc_status_str,

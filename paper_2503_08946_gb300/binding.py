@@ -45,7 +45,8 @@ RC_OPT_GRAPH = 2
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
            "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times",
-           "rc_sort_keys_static", "rc_kernel_source", "rc_tune"]
+           "rc_sort_keys_static", "rc_kernel_source", "rc_tune", "rc_server_create",
+           "rc_server_submit", "rc_server_poll", "rc_server_stats", "rc_server_destroy"]
 RC_SORT_STATIC_MAX_KEYS = 1 << 20
 
 
@@ -133,6 +134,17 @@ class rc_result(Structure):
                 ("oob_dim", c_int32), ("reserved2", c_int32)]
 
 
+class rc_server_opts(Structure):
+    _fields_ = [("memory_bytes", c_uint64), ("slots", c_uint32), ("max_batch", c_uint32),
+                ("digit_bits", c_uint32), ("reserved", c_uint32)]
+
+
+class rc_server_done(Structure):
+    _fields_ = [("request", c_uint64), ("result", rc_result), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("batch_size", c_uint32),
+                ("pad", c_uint32)]
+
+
 # ---------------------------------------------------------------------------
 # library loading (no fallback)
 # ---------------------------------------------------------------------------
@@ -174,6 +186,16 @@ def load():
         lib.rc_tune.argtypes = [POINTER(c_void_p), c_size_t, POINTER(rc_check_opts), c_void_p, c_size_t,
                                 c_void_p, POINTER(rc_check_opts)]
         lib.rc_tune.restype = c_int
+        lib.rc_server_create.argtypes = [POINTER(rc_server_opts), POINTER(c_void_p)]
+        lib.rc_server_create.restype = c_int
+        lib.rc_server_submit.argtypes = [c_void_p, c_void_p, POINTER(c_uint64)]
+        lib.rc_server_submit.restype = c_int
+        lib.rc_server_poll.argtypes = [c_void_p, POINTER(rc_server_done), c_size_t, POINTER(c_size_t), c_int]
+        lib.rc_server_poll.restype = c_int
+        lib.rc_server_stats.argtypes = [c_void_p, POINTER(c_uint64), POINTER(c_uint64)]
+        lib.rc_server_stats.restype = c_int
+        lib.rc_server_destroy.argtypes = [c_void_p]
+        lib.rc_server_destroy.restype = c_int
         lib.rc_report.argtypes = [c_void_p, POINTER(rc_result), c_int]
         lib.rc_report.restype = c_int
         lib.rc_expand_keys.argtypes = [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]
@@ -497,6 +519,71 @@ def _result(r: rc_result) -> Result:
 
 class NotReady(Exception):
     pass
+
+
+@dataclass
+class Done:
+    request: int
+    result: "Result"
+    submit_s: float
+    start_s: float
+    done_s: float
+    batch_size: int
+
+
+class RcServer:
+    """Continuous-batching request server (rc_server_* of include/rc.h) on the
+    current device.  Models passed to :meth:`submit` must stay alive until
+    their results are polled."""
+
+    def __init__(self, memory_bytes: int, slots: int = 4, max_batch: int = 0, digit_bits: int = 0):
+        o = rc_server_opts(int(memory_bytes), int(slots), int(max_batch), int(digit_bits), 0)
+        h = c_void_p()
+        st = load().rc_server_create(ctypes.byref(o), ctypes.byref(h))
+        if st != RC_OK:
+            raise RcError(st, "rc_server_create")
+        self.ptr = h.value
+        self._hold = {}
+
+    def submit(self, model: "RcModel") -> int:
+        rid = c_uint64()
+        st = load().rc_server_submit(c_void_p(self.ptr), c_void_p(model.ptr), ctypes.byref(rid))
+        if st != RC_OK:
+            raise RcError(st, "rc_server_submit")
+        self._hold[rid.value] = model
+        return rid.value
+
+    def poll(self, cap: int = 1024, wait_ms: int = 0) -> List[Done]:
+        out = (rc_server_done * max(1, cap))()
+        n = c_size_t()
+        st = load().rc_server_poll(c_void_p(self.ptr), out, cap, ctypes.byref(n), int(wait_ms))
+        if st != RC_OK:
+            raise RcError(st, "rc_server_poll")
+        res = []
+        for i in range(n.value):
+            d = out[i]
+            self._hold.pop(d.request, None)
+            res.append(Done(d.request, _result(d.result), d.submit_s, d.start_s, d.done_s, d.batch_size))
+        return res
+
+    def stats(self):
+        p, f = c_uint64(), c_uint64()
+        load().rc_server_stats(c_void_p(self.ptr), ctypes.byref(p), ctypes.byref(f))
+        return p.value, f.value
+
+    def close(self):
+        if self.ptr:
+            st = load().rc_server_destroy(c_void_p(self.ptr))
+            self.ptr = None
+            self._hold.clear()
+            if st != RC_OK:
+                raise RcError(st, "rc_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rc_report(ticket, wait: bool = True) -> List[Result]:

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 CUDA_INCLUDE = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
 CUDA_SOURCES = ["expand.cu", "sort.cu", "scan.cu", "runtime.cu", "sort_static.cu", "hash.cu", "batch.cu"]
-HOST_SOURCES = ["lower.cpp", "jit.cpp"]
+HOST_SOURCES = ["lower.cpp", "jit.cpp", "server.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + CSRC, "-I" + INCLUDE] + GENCODE
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         jobs.append([nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + flags)
     for src in HOST_SOURCES:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I" + CSRC, "-I" + INCLUDE, "-I" + CUDA_INCLUDE, "-c",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I" + CSRC, "-I" + INCLUDE, "-I" + CUDA_INCLUDE, "-c",
                      os.path.join(CSRC, src), "-o", obj])
 
     def run(cmd):
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in CUDA_SOURCES] + \
            [os.path.join(BUILD, s.replace(".cpp", ".o")) for s in HOST_SOURCES]
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, "-shared", "-o", tmp] + objs + GENCODE + ["-cudart", "static", "-ldl"])
+    run([nvcc, "-shared", "-o", tmp] + objs + GENCODE + ["-cudart", "static", "-ldl", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

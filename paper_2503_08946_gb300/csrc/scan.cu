@@ -247,36 +247,66 @@ __global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a)
       my[o + 1] = y;
     }
     __syncwarp();
-    // (1) fold the run: P = the keys that continue the cell open before the
-    // run, O = the cell begun last in the run (earlier ones are closed here)
+    // (1) fold the run in one pass, with selects rather than branches so that
+    // the lanes of a warp stay converged.  `cur` is the part being folded: first
+    // the keys that continue the cell open before the run (the prefix part P),
+    // then each cell that begins in the run (closed ones are reported at once;
+    // the last one stays open as O).
     const uint64_t s = S + (uint64_t)lane * kScanRun;
     const uint64_t* run = my + lane * kRunPad;
     const uint64_t kp = lane > 0 ? my[(lane - 1) * kRunPad + kScanRun - 1] : k_before;
-    Fold P, O;
+    Fold P, cur;
     P.fk = P.gk = 0; P.start = 0; P.bt0 = P.gbt0 = 0; P.f = 0;
-    O = P;
-    bool hasP = false, hasO = false, term = false;
-    bool in_prefix = kp != kSentinel;
-#pragma unroll 4
+    cur = P;
+    cur.fk = kp;                      // compared against for the prefix
+    bool hasP = false, term = false, cur_empty = true, cur_prefix = true;
+#pragma unroll 8
     for (int q = 0; q < kScanRun; ++q) {
       const uint64_t k = run[q];
-      if (k == kSentinel) term = true;
-      if (term) continue;
+      term |= k == kSentinel;
+      const bool valid = !term;
       const unsigned bt = key_bt(c, k);
-      if (in_prefix) {
-        if (((k ^ kp) & cell_mask) == 0ull) {
-          if (hasP) fold_add(c, P, k, bt);
-          else fold_start(P, k, s + q, bt);
+      const bool same_cell = ((k ^ cur.fk) & cell_mask) == 0ull;
+      const bool do_start = !same_cell || cur_empty;
+      const bool do_close = valid && !same_cell && !cur_empty;
+      if (do_close) {
+        if (cur_prefix) {
+          P = cur;
           hasP = true;
-          continue;
+        } else {
+          report(cur);
         }
-        in_prefix = false;
       }
-      if (hasO && ((k ^ O.fk) & cell_mask) == 0ull) {
-        fold_add(c, O, k, bt);
+      // add to cur (same cell)
+      unsigned f = cur.f;
+      const bool ng = ((k ^ cur.gk) & c.group_mask) != 0ull;
+      const bool gm = (f & kFGM) != 0u, gw = (f & kFGW) != 0u;
+      const unsigned fc = (f & kFFO) ? ((f & ~kFFO) | (gm ? kFFM : 0u) | (gw ? kFFW : 0u))
+                                     : ((gm && gw) ? (f | kFIn) : f);
+      f = ng ? (fc & ~(kFGM | kFGW)) : f;
+      if (((bt ^ cur.bt0) >> c.tb) != 0u) f |= kFMB;
+      if (!ng && bt != cur.gbt0) f |= kFGM;
+      const unsigned wf = (k & 1ull) ? (kFW | kFGW) : 0u;
+      f |= wf;
+      const unsigned fs = kFFO | wf;
+      if (valid) {
+        cur.f = do_start ? fs : f;
+        cur.gk = (do_start || ng) ? k : cur.gk;
+        cur.gbt0 = (do_start || ng) ? bt : cur.gbt0;
+        cur.fk = do_start ? k : cur.fk;
+        cur.bt0 = do_start ? bt : cur.bt0;
+        cur.start = do_start ? s + q : cur.start;
+        cur_prefix = cur_prefix && same_cell;
+        cur_empty = false;
+      }
+    }
+    bool hasO = false;
+    Fold O = cur;
+    if (!cur_empty) {
+      if (cur_prefix) {
+        P = cur;
+        hasP = true;
       } else {
-        if (hasO) report(O);
-        fold_start(O, k, s + q, bt);
         hasO = true;
       }
     }

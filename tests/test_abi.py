@@ -47,7 +47,8 @@ def test_library_exports_every_declared_symbol(rc):
 def test_struct_layout_matches_c(rc):
     b = rc.binding
     structs = ["rc_insn", "rc_expr", "rc_loop", "rc_access", "rc_stmt", "rc_array", "rc_model_desc",
-               "rc_limits", "rc_layout", "rc_check_opts", "rc_inst", "rc_result"]
+               "rc_limits", "rc_layout", "rc_check_opts", "rc_inst", "rc_result", "rc_server_opts",
+               "rc_server_done"]
     fields = {s: [f for f, _ in getattr(b, s)._fields_] for s in structs}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for s in structs:
