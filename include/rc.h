@@ -169,7 +169,9 @@ void rc_model_destroy(rc_model* m);
 /* Key layout of a lowered model, MSB to LSB: [cell | phase | block | thread |
  * kind], each field `*_bits` wide at `*_shift`; cell = array_base[a] +
  * scope_instance * array_cells[a] + element.  Keys are grouped (sorted) on
- * bits [sort_lo, sort_hi) = (cell, phase); (block, thread, kind) ride along. */
+ * bits [sort_lo, sort_hi): the cell alone when the model has at most 16
+ * barrier intervals (the scan then groups a cell's phases itself), else
+ * (cell, phase); the other fields ride along. */
 typedef struct rc_layout {
   uint32_t kind_shift, thread_shift, block_shift, phase_shift, cell_shift;
   uint32_t thread_bits, block_bits, phase_bits, cell_bits;

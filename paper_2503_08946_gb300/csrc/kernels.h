@@ -101,6 +101,7 @@ struct ScanArgs {
   uint64_t long_cap;                   // scan_long_capacity(n, n_warps)
   const uint64_t* cell_base;           // batch: first batch cell of each model (ascending)
   uint32_t n_models;                   // batch: number of models (0 = single model)
+  uint32_t phase_table;                // keys sorted by cell only (phase_bits <= kScanTablePhaseBits)
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);

@@ -261,7 +261,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   // one more value than the cells so the all-ones cell field is never a valid cell
   h.cell_bits = bit_length(cells_total);
   if (h.cell_shift + h.cell_bits > (uint32_t)kKeyBits) return RC_E_KEY_OVERFLOW;
-  h.sort_lo = h.phase_shift;
+  h.sort_lo = h.phase_bits <= kScanTablePhaseBits ? h.cell_shift : h.phase_shift;
   h.sort_hi = h.cell_shift + h.cell_bits;
 
   // arrays that some statement writes; a cell of any other array has no write

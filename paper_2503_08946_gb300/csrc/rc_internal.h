@@ -28,6 +28,10 @@ constexpr int kMaxDims = 4;
 constexpr int kMaxPhaseBits = 16;
 constexpr int kKeyBits = 63;      // bit 63 is reserved so 0xFFFF...FFFF is never a valid key
 constexpr uint64_t kSentinel = ~0ull;
+// Models with at most this many phase bits are sorted by cell only: the scan
+// groups a cell's keys by phase with small per-part tables instead of relying
+// on the sort order (scan.cu).
+constexpr uint32_t kScanTablePhaseBits = 4;
 constexpr int kFastCache = 16;    // per-thread cached thread-constant rows per statement
 constexpr int kFastLoops = 4;     // loop depth of the compile-time loop nests of the expansion
 

@@ -215,6 +215,7 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.long_cap = p.long_cap;
   a.cell_base = nullptr;
   a.n_models = 0;
+  a.phase_table = m.host.phase_bits <= rc::kScanTablePhaseBits ? 1u : 0u;
   return a;
 }
 
@@ -473,7 +474,8 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     std::memset(&p, 0, sizeof(p));
     p.n_keys = k.n_keys;
     const uint32_t ps = 1 + k.tb + k.bb;
-    plan_sort(ps, ps + k.pb + k.cell_bits, opts ? opts->digit_bits : 0, &p.sort);
+    const uint32_t lo = k.pb <= rc::kScanTablePhaseBits ? ps + k.pb : ps;   // cell-only sort with phase tables
+    plan_sort(lo, ps + k.pb + k.cell_bits, opts ? opts->digit_bits : 0, &p.sort);
     p.n_tiles = (k.n_keys + rc::kSortTile - 1) / rc::kSortTile;
     p.scan_warps = scan_warps_for(k.n_keys);
     size_t o = region;
@@ -601,6 +603,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.long_cap = p.long_cap;
     sa.cell_base = dcbase + k.i0;
     sa.n_models = nm;
+    sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
     s = cuda_status(rc::launch_scan(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
@@ -777,7 +780,7 @@ TuneKey tune_key(rc_model* const* models, size_t n) {
   k.batch = n > 1 ? 1u : 0u;
   k.n_log2 = rc::bit_length(n);
   k.keys_log2 = rc::bit_length(keys);
-  k.sort_bits = rc::bit_length(cells) + pb;
+  k.sort_bits = rc::bit_length(cells) + (pb <= rc::kScanTablePhaseBits ? 0u : pb);
   return k;
 }
 

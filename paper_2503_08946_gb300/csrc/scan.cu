@@ -453,6 +453,311 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_kernel(ScanArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Phase-table variants: keys sorted by cell only.  With at most
+// 2^kScanTablePhaseBits barrier intervals the sort leaves out the phase bits,
+// and the phase groups of a cell are tracked in a small table per part
+// instead: for each phase, whether it was seen, the (block, thread) of its
+// first key, whether two (block, thread) met in it and whether it has a write.
+// A cell is racy iff it has a write and (two blocks, or some phase with two
+// (block, thread) and a write) -- the same rule as above, order-free inside
+// the cell.
+// ---------------------------------------------------------------------------
+struct TFold {
+  uint64_t fk;       // first key
+  uint64_t start;    // its position
+  unsigned bt0;      // its (block, thread)
+  unsigned f;        // kTW | kTMB
+  unsigned vmask;    // phases seen
+  unsigned gm;       // phases with two (block, thread)
+  unsigned gw;       // phases with a write
+};
+constexpr unsigned kTW = 1u, kTMB = 2u;
+constexpr int kTabPhases = 1 << kScanTablePhaseBits;
+constexpr int kTabStride = 2 * kTabPhases + 1;     // per lane: prefix table, own table, pad
+
+__device__ __forceinline__ bool tfold_racy(const TFold& x) {
+  return (x.f & kTW) && ((x.f & kTMB) || (x.gm & x.gw) != 0u);
+}
+__device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
+  TFold r;
+  r.fk = __shfl_sync(FULL, s.fk, src);
+  r.start = __shfl_sync(FULL, s.start, src);
+  r.bt0 = __shfl_sync(FULL, s.bt0, src);
+  r.f = __shfl_sync(FULL, s.f, src);
+  r.vmask = __shfl_sync(FULL, s.vmask, src);
+  r.gm = __shfl_sync(FULL, s.gm, src);
+  r.gw = __shfl_sync(FULL, s.gw, src);
+  return r;
+}
+// o (table otab) followed by p (table ptab), a part of the same cell; one lane
+__device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFold& p, const unsigned* ptab,
+                                            uint32_t tb) {
+  unsigned f = o.f | (p.f & kTW);
+  if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
+  unsigned m = p.vmask;
+  while (m) {
+    const int ph = __ffs(m) - 1;
+    const unsigned bit = 1u << ph;
+    m &= m - 1;
+    const unsigned pv = ptab[ph];
+    if (o.vmask & bit) {
+      if ((p.gm & bit) || pv != otab[ph]) o.gm |= bit;
+    } else {
+      otab[ph] = pv;
+      o.vmask |= bit;
+      o.gm |= p.gm & bit;
+    }
+  }
+  o.gw |= p.gw;
+  o.f = f;
+}
+// the warp's carried cell (warp-uniform state, table ctab) followed by p of
+// lane src (table ptab); all lanes, one phase per lane
+__device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const TFold& p, const unsigned* ptab,
+                                                 uint32_t tb) {
+  const int lane = threadIdx.x & 31;
+  unsigned f = o.f | (p.f & kTW);
+  if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
+  bool g = false;
+  if (lane < kTabPhases && (p.vmask >> lane) & 1u) {
+    const unsigned pv = ptab[lane];
+    if ((o.vmask >> lane) & 1u) {
+      g = ((p.gm >> lane) & 1u) || pv != ctab[lane];
+    } else {
+      ctab[lane] = pv;
+      g = (p.gm >> lane) & 1u;
+    }
+  }
+  o.gm |= __ballot_sync(FULL, g);
+  o.vmask |= p.vmask;
+  o.gw |= p.gw;
+  o.f = f;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(ScanArgs a) {
+  __shared__ unsigned tabs[kScanWarps][32 * kTabStride];
+  __shared__ unsigned ctabs[kScanWarps][kTabPhases];
+  const uint32_t ps = a.phase_shift, tb = a.thread_bits;
+  const unsigned pm = (1u << a.phase_bits) - 1u;
+  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  const uint64_t cell_mask = ~((1ull << a.cell_shift) - 1ull);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned* mytab = tabs[w] + lane * kTabStride;     // [0, 16): prefix part, [16, 32): own cells
+  unsigned* ctab = ctabs[w];
+  const uint64_t n_seg = (a.n + kSegKeys - 1) / kSegKeys;
+  const uint64_t gw = (uint64_t)blockIdx.x * kScanWarps + w;
+  const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
+  const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
+  unsigned long long count = 0, minstart = ~0ull;
+  auto report = [&](const TFold& x) {
+    if (!tfold_racy(x)) return;
+    if (a.n_models) {
+      DevResult* r = result_of(a, x.fk >> a.cell_shift);
+      atomicAdd(&r->racy_cells, 1ull);
+      atomicMin(&r->min_start, (unsigned long long)x.start);
+    } else {
+      ++count;
+      minstart = min(minstart, (unsigned long long)x.start);
+    }
+  };
+  bool carry = false;
+  int carried = 0;
+  TFold cc;
+  cc.fk = 0; cc.start = 0; cc.bt0 = 0; cc.f = 0; cc.vmask = cc.gm = cc.gw = 0;
+  for (uint64_t seg = seg0; seg < seg1; ++seg) {
+    const uint64_t S = seg * kSegKeys;
+    // (1) fold the run (prefix part in table 0, own cells in table 1)
+    // each lane reads its own run of kScanRun consecutive keys directly (the
+    // lines of a run are shared by its consecutive loads through L1)
+    const uint64_t s = S + (uint64_t)lane * kScanRun;
+    const uint64_t kp = (s > 0 && s - 1 < a.n) ? __ldg(a.keys + s - 1) : kSentinel;
+    TFold P, cur;
+    P.fk = 0; P.start = 0; P.bt0 = 0; P.f = 0; P.vmask = P.gm = P.gw = 0;
+    cur = P;
+    cur.fk = kp;
+    bool hasP = false, term = false, cur_empty = true, cur_prefix = true;
+#pragma unroll 8
+    for (int q = 0; q < kScanRun; ++q) {
+      const uint64_t k = s + q < a.n ? __ldg(a.keys + s + q) : kSentinel;
+      term |= k == kSentinel;
+      const bool valid = !term;
+      const unsigned bt = (unsigned)(k >> 1) & btm;
+      const unsigned ph = (unsigned)(k >> ps) & pm;
+      const bool same_cell = ((k ^ cur.fk) & cell_mask) == 0ull;
+      const bool do_start = !same_cell || cur_empty;
+      if (valid && !same_cell && !cur_empty) {
+        if (cur_prefix) {
+          P = cur;
+          hasP = true;
+        } else {
+          report(cur);
+        }
+      }
+      const bool np = cur_prefix && same_cell;
+      unsigned* tab = mytab + (np ? 0 : kTabPhases);
+      const unsigned bit = 1u << ph;
+      const unsigned old = tab[ph];
+      const bool seen = !do_start && (cur.vmask & bit);
+      if (valid) {
+        if (!seen) tab[ph] = bt;
+        const unsigned wb = (k & 1ull) ? bit : 0u;
+        cur.gm = (do_start ? 0u : cur.gm) | ((seen && old != bt) ? bit : 0u);
+        cur.vmask = (do_start ? 0u : cur.vmask) | bit;
+        cur.gw = (do_start ? 0u : cur.gw) | wb;
+        unsigned f = do_start ? 0u : cur.f;
+        if (!do_start && ((bt ^ cur.bt0) >> tb) != 0u) f |= kTMB;
+        if (k & 1ull) f |= kTW;
+        cur.f = f;
+        cur.fk = do_start ? k : cur.fk;
+        cur.bt0 = do_start ? bt : cur.bt0;
+        cur.start = do_start ? s + q : cur.start;
+        cur_prefix = np;
+        cur_empty = false;
+      }
+    }
+    bool hasO = false;
+    TFold O = cur;
+    if (!cur_empty) {
+      if (cur_prefix) {
+        P = cur;
+        hasP = true;
+      } else {
+        hasO = true;
+      }
+    }
+    const bool pfull = hasP && !hasO && !term;
+    __syncwarp();
+    // (2) the carried cell continues through the leading prefixes
+    if (carry) {
+      bool open = true;
+      for (int src = 0; src < 32 && open; ++src) {
+        const bool h = __shfl_sync(FULL, hasP, src);
+        const bool full = __shfl_sync(FULL, pfull, src);
+        const TFold pp = tfold_shfl(P, src);
+        if (h) tfold_merge_warp(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
+        if (!full) open = false;
+      }
+      if (!open) {
+        if (lane == 0) report(cc);
+        carry = false;
+      } else if (++carried > kCarryMaxSegs) {
+        if (lane == 0) hand_over(a, cc.start);
+        carry = false;
+      }
+    }
+    // (3) each lane's last cell continues through the following prefixes
+    bool open = hasO;
+    bool open_end = false;
+    if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= a.n)) {
+      report(O);
+      open = false;
+    }
+    for (int d = 1; __any_sync(FULL, open); ++d) {
+      const int src = lane + d < 32 ? lane + d : 31;
+      const bool h = __shfl_sync(FULL, hasP, src);
+      const bool full = __shfl_sync(FULL, pfull, src);
+      const TFold pp = tfold_shfl(P, src);
+      if (open) {
+        if (lane + d >= 32) {
+          open = false;
+          open_end = true;
+        } else {
+          if (h) tfold_merge(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
+          if (!full) {
+            report(O);
+            open = false;
+          }
+        }
+      }
+    }
+    // (4) the cell open at the segment end (at most one lane) becomes the carry
+    const unsigned OE = __ballot_sync(FULL, open_end);
+    if (OE) {
+      const int src = __ffs(OE) - 1;
+      cc = tfold_shfl(O, src);
+      if (lane < kTabPhases) ctab[lane] = tabs[w][src * kTabStride + kTabPhases + lane];
+      carry = true;
+      carried = 0;
+    }
+    __syncwarp();
+  }
+  if (carry && lane == 0) hand_over(a, cc.start);
+  if (a.n_models == 0) {
+    count = __reduce_add_sync(FULL, (unsigned)count);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(FULL, minstart, o);
+      minstart = y < minstart ? y : minstart;
+    }
+    if (lane == 0) {
+      if (count) atomicAdd(&a.res->racy_cells, count);
+      if (minstart != ~0ull) atomicMin(&a.res->min_start, minstart);
+    }
+  }
+}
+
+// One block per handed-over cell, order-free: per-phase min / max (block,
+// thread) and write flags in shared memory.
+__global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs a) {
+  __shared__ unsigned mn[kTabPhases], mx[kTabPhases];
+  __shared__ unsigned s_gw, s_minb, s_maxb, s_w;
+  const unsigned pm = (1u << a.phase_bits) - 1u;
+  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
+  for (unsigned long long i = blockIdx.x; i < n_long; i += gridDim.x) {
+    const uint64_t start = a.long_list[i];
+    const uint64_t cell = a.keys[start] >> a.cell_shift;
+    if (threadIdx.x < kTabPhases) {
+      mn[threadIdx.x] = 0xffffffffu;
+      mx[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+      s_gw = 0;
+      s_minb = 0xffffffffu;
+      s_maxb = 0;
+      s_w = 0;
+    }
+    __syncthreads();
+    for (uint64_t base = start;; base += kLongThreads) {
+      const uint64_t pos = base + threadIdx.x;
+      bool end = pos >= a.n;
+      if (!end) {
+        const uint64_t k = a.keys[pos];
+        end = k == kSentinel || (k >> a.cell_shift) != cell;
+        if (!end) {
+          const unsigned bt = (unsigned)(k >> 1) & btm;
+          const unsigned ph = (unsigned)(k >> a.phase_shift) & pm;
+          atomicMin(&mn[ph], bt);
+          atomicMax(&mx[ph], bt);
+          atomicMin(&s_minb, bt >> a.thread_bits);
+          atomicMax(&s_maxb, bt >> a.thread_bits);
+          if (k & 1ull) {
+            atomicOr(&s_gw, 1u << ph);
+            s_w = 1;
+          }
+        }
+      }
+      if (__syncthreads_or(end)) break;
+    }
+    if (threadIdx.x == 0) {
+      bool racy = false;
+      if (s_w) {
+        racy = s_minb != s_maxb;
+        for (int ph = 0; ph < kTabPhases; ++ph)
+          if (((s_gw >> ph) & 1u) && mn[ph] != mx[ph]) racy = true;
+      }
+      if (racy) {
+        DevResult* r = result_of(a, cell);
+        atomicAdd(&r->racy_cells, 1ull);
+        atomicMin(&r->min_start, (unsigned long long)start);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // One warp per result: the end of its first racy cell.
 __global__ void scan_finish_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.x;
@@ -645,10 +950,13 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   if (a.n > 0) {
-    scan_cells_kernel<<<(a.n_warps + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, st>>>(a);
+    const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
+    if (a.phase_table) scan_cells_table_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
+    else scan_cells_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    scan_long_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
+    if (a.phase_table) scan_long_table_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
+    else scan_long_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

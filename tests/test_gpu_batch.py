@@ -172,3 +172,13 @@ def test_tuner_choice_is_used(rc):
     res = rc.rc_report(rc.rc_check_batch(hs, {"path": 0}, wsb))
     for x, g in zip(models, res):
         assert_same(x, g, oracle.check(x))
+
+
+def test_batch_with_many_phases(rc):
+    """A pack holding a model with more than 16 barrier intervals sorts on the
+    phase bits too; the results do not change."""
+    models = [w.tiny_random(s) for s in range(800, 820)] + \
+             [w.random_affine(s, n_blocks=2, block=128, n_stmts=10, n_phases=40, plant=(s % 2 == 0))
+              for s in range(4)]
+    batch_compare(rc, models)
+    batch_compare(rc, models, {"test_flags": 2})

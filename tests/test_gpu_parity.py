@@ -353,3 +353,15 @@ def test_scan_long_warp_ranges(rc, i):
                for sc, blk, ph in [("shared", 700, 1), ("global", 700, 3), ("shared", 1024, 3),
                                    ("global", 33, 0), ("shared", 65, 2), ("global", 1000, 1), ("shared", 999, 0)]])
     compare(rc, models[i], {"test_flags": rc.binding.RC_TEST_FEW_SCAN_WARPS})
+
+
+@pytest.mark.parametrize("n_phases", [2, 16, 17, 40, 300])
+@pytest.mark.parametrize("seed", range(3))
+def test_phase_counts(rc, n_phases, seed):
+    """Models with at most 16 barrier intervals are sorted by cell only and the
+    scan groups phases with tables; more intervals keep the phase bits in the
+    sort.  Both give the oracle's result (also with long per-warp ranges)."""
+    for plant in (False, True):
+        m = w.random_affine(seed, n_blocks=8, block=128, n_stmts=14, n_phases=n_phases, plant=plant)
+        compare(rc, m)
+        compare(rc, m, {"test_flags": 2})   # RC_TEST_FEW_SCAN_WARPS
