@@ -184,6 +184,7 @@ def run_native(args):
     import workloads as w
     import paper_2503_08946_gb300 as rc
     from paper_2503_08946_gb300 import build as b
+    from paper_2503_08946_gb300 import distributed as D
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -232,16 +233,8 @@ def run_native(args):
         dist.barrier()
     clocks = sampler.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
-    t_max = elapsed_ms
-    total_inst = instances * args.steps
-    if dist:
-        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ti = torch.tensor([total_inst], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
-        total_inst = float(ti.item())
-    value = total_inst / (t_max / 1e3) / 1e9
+    # whole job: instances of all ranks over the slowest rank's time
+    total_inst, t_max, value = D.weak_scaling_rate(instances * args.steps, elapsed_ms, device="cuda")
 
     # per-stage means and the roofline of the dominant kernel
     n_keys = stages[0]["n_keys"]

@@ -213,6 +213,13 @@ typedef struct rc_check_opts {
   uint32_t flags;          /* RC_OPT_* bits                                       */
   uint32_t reserved;
   uint64_t spin_limit;     /* iterations of every bounded device wait, 0 = default */
+  uint64_t cell_lo;        /* partial check: only cells in [cell_lo, cell_hi) of   */
+  uint64_t cell_hi;        /* the key layout count (0 / 0 = all).  Instances of    */
+                           /* other cells are still enumerated, bounds-checked and */
+                           /* counted.  The racy cells of disjoint ranges add up;  */
+                           /* the witness is the one of the lowest racy range      */
+                           /* (a model split across processes or GPUs).  Ignored   */
+                           /* by rc_check_batch.                                   */
 } rc_check_opts;
 enum { RC_TEST_STALL_LOOKBACK = 1,
        RC_TEST_FEW_SCAN_WARPS = 2   /* scan with 3 warps (long ranges per warp) */ };

@@ -17,17 +17,25 @@ namespace rc {
 
 namespace {
 
-// Sort-path sink: keys go to their slot; guard-false dense slots get padding.
+// Sort-path sink: keys go to their slot; guard-false dense slots get padding,
+// and so do keys whose cell lies outside [cell_lo, cell_hi) (a partial check
+// of a cell range).
 struct SlotSink {
   uint64_t* keys;
-  __device__ __forceinline__ void put(uint64_t i, uint64_t key) { keys[i] = key; }
+  uint32_t cell_shift;
+  uint64_t cell_lo, cell_hi;
+  __device__ __forceinline__ void put(uint64_t i, uint64_t key) {
+    const uint64_t c = key >> cell_shift;
+    keys[i] = (c >= cell_lo && c < cell_hi) ? key : kSentinel;
+  }
   __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
 };
 
 // grid: (ceil(T / kExpandThreads), n_stmts); one statement per grid row.
 // Statements with at most kFastLoops loops.
 __global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevModel* __restrict__ Mp,
-                                                                uint64_t* __restrict__ keys, DevResult* res) {
+                                                                uint64_t* __restrict__ keys, DevResult* res,
+                                                                uint64_t cell_lo, uint64_t cell_hi) {
   __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
   __shared__ int64_t s_cache[kFastCache * kExpandThreads];
   const DevModel& M = *Mp;
@@ -43,7 +51,7 @@ __global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevMode
     c.tv = thread_vars(M, g);
     c.tval = s_tval + threadIdx.x;
     c.cache = s_cache + threadIdx.x;
-    SlotSink sink{keys};
+    SlotSink sink{keys, M.cell_shift, cell_lo, cell_hi};
     expand_unit_dispatch(c, s, g, res, count, sink);
   }
   count = warp_sum(count);
@@ -52,13 +60,14 @@ __global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevMode
 
 // Statements with more than kFastLoops loops: interpreted nest.
 __global__ void __launch_bounds__(kExpandThreads) expand_generic_kernel(const DevModel* __restrict__ Mp,
-                                                                        uint64_t* __restrict__ keys, DevResult* res) {
+                                                                        uint64_t* __restrict__ keys, DevResult* res,
+                                                                        uint64_t cell_lo, uint64_t cell_hi) {
   const DevModel& M = *Mp;
   const uint32_t s = blockIdx.y;
   if (M.stmts[s].n_loops <= kFastLoops) return;
   const uint64_t g = (uint64_t)blockIdx.x * kExpandThreads + threadIdx.x;
   unsigned long long count = 0;
-  SlotSink sink{keys};
+  SlotSink sink{keys, M.cell_shift, cell_lo, cell_hi};
   if (g < M.n_threads) expand_unit_generic(M, s, g, res, count, sink);
   count = warp_sum(count);
   if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
@@ -170,14 +179,14 @@ int grid_for(uint64_t n_units) {
 }  // namespace
 
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
-                          DevResult* res, cudaStream_t st) {
+                          DevResult* res, cudaStream_t st, uint64_t cell_lo, uint64_t cell_hi) {
   if (n_stmts == 0 || n_threads == 0) return cudaSuccess;
   const dim3 grid((unsigned)((n_threads + kExpandThreads - 1) / kExpandThreads), n_stmts);
-  expand_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res);
+  expand_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res, cell_lo, cell_hi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (has_deep) {
-    expand_generic_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res);
+    expand_generic_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res, cell_lo, cell_hi);
     e = cudaGetLastError();
   }
   return e;

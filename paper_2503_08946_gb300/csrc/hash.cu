@@ -74,6 +74,7 @@ struct HashSink {
     if (key == kSentinel) return;
     const DevModel& m = *M;
     const uint64_t cell = key >> m.cell_shift;
+    if (cell < h.cell_lo || cell >= h.cell_hi) return;
     const uint64_t cp = key >> m.phase_shift;
     const uint64_t b = (key >> m.block_shift) & ((1ull << m.block_bits) - 1ull);
     const uint64_t t = (key >> m.thread_shift) & ((1ull << m.thread_bits) - 1ull);

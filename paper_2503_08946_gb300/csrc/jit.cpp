@@ -202,8 +202,10 @@ struct Gen {
       o << in3 << "unsigned long long key;\n";
       o << in3 << "if (dc != 0xFFFFFFFFu) { atomicMin(oob, " << ulit(pack)
         << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc); key = ~0ull; }\n";
-      o << in3 << "else key = ((" << cell << ") << " << m.host.cell_shift << ") | ((unsigned long long)ph << "
-        << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind) << ";\n";
+      o << in3 << "else { const unsigned long long cl = " << cell << ";\n";
+      o << in3 << "  key = (cl >= cell_lo && cl < cell_hi) ? ((cl << " << m.host.cell_shift
+        << ") | ((unsigned long long)ph << " << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind)
+        << ") : ~0ull; }\n";
       if (A.key_idx < 0) o << in3 << "(void)key;\n";   // array never written: checked, no key
       else if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)A.key_idx * T) << "] = key;\n";
       else o << in3 << "keys[off + " << A.key_idx << "] = key;\n";
@@ -234,7 +236,8 @@ struct Gen {
          "  return a >= 0 ? a / d : -1 - (-(a + 1)) / d;\n}\n";
     o << "__device__ __forceinline__ long long mod_c(long long a, long long d) { return a - fdiv_c(a, d) * d; }\n";
     o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
-         "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset) {\n";
+         "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
+         "unsigned long long cell_lo, unsigned long long cell_hi) {\n";
     o << "  const unsigned long long g = (unsigned long long)blockIdx.x * 128ull + threadIdx.x;\n";
     o << "  unsigned long long cnt = 0;\n";
     o << "  if (g < " << ulit(h.n_threads) << ") {\n";
@@ -312,13 +315,15 @@ bool jit_expand_build(Model* m) {
   return true;
 }
 
-cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st) {
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo,
+                              uint64_t cell_hi) {
   Driver& dr = driver();
   CUfunction fn = reinterpret_cast<CUfunction>(m.jit_fn);
   unsigned long long* oob = &res->oob_code;
   unsigned long long* inst = &res->instances;
   const uint64_t* uo = m.host.unit_offset;
-  void* params[] = {&keys, &oob, &inst, &uo};
+  unsigned long long lo = cell_lo, hi = cell_hi;
+  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi};
   const unsigned gx = (unsigned)((m.host.n_threads + 127) / 128);
   const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

@@ -9,8 +9,9 @@ namespace rc {
 
 // expand.cu
 // has_deep: some statement has more than kFastLoops loops (runs the generic kernel too)
+// keys whose cell lies outside [cell_lo, cell_hi) are written as padding
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
-                          DevResult* res, cudaStream_t st);
+                          DevResult* res, cudaStream_t st, uint64_t cell_lo = 0, uint64_t cell_hi = ~0ull);
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st);
 size_t scan_u64_temp_bytes(uint64_t n);
 cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,
@@ -52,6 +53,7 @@ struct HashArgs {
   unsigned int* stop;
   uint64_t* filtered;          // keys of the smallest racy cell
   unsigned long long* n_filtered;
+  uint64_t cell_lo, cell_hi;   // only cells in [cell_lo, cell_hi) are inserted
 };
 cudaError_t launch_hash(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, const HashArgs& h,
                         cudaStream_t st);

@@ -343,7 +343,8 @@ struct Model {
 constexpr uint64_t kJitMinKeys = 1ull << 22;   // models with fewer keys keep the interpreted expansion
 std::string jit_expand_source(const Model& m);
 bool jit_expand_build(Model* m);
-cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st);
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo = 0,
+                              uint64_t cell_hi = ~0ull);
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);

@@ -266,6 +266,8 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
   if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
   const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
+  const uint64_t cell_lo = opts ? opts->cell_lo : 0;
+  const uint64_t cell_hi = (opts && opts->cell_hi) ? opts->cell_hi : ~0ull;
   auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
   StageTimer* tm = nullptr;
   if (timed) {
@@ -292,6 +294,8 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     h.stop = &res->stop;
     h.filtered = reinterpret_cast<uint64_t*>(ws + p.filt_off);
     h.n_filtered = reinterpret_cast<unsigned long long*>(ws + p.nfilt_off);
+    h.cell_lo = cell_lo;
+    h.cell_hi = cell_hi;
     s = cuda_status(cudaMemsetAsync(h.gkey, 0xFF, p.hash_cap * 8, st));
     if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.ckey, 0xFF, p.hash_cap * 8, st));
     if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.gword, 0, p.hash_cap * 8, st));
@@ -320,10 +324,11 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   if (s != RC_OK) return s;
   if (tm) { timed->i_start = tm->n; tm->mark(); }
   if (m.jit_fn)
-    s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
+    s = cuda_status(
+        rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
   else
     s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
-                                      reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st));
+                                      reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
   if (s != RC_OK) return s;
   if (tm) { timed->i_expand = tm->n; tm->mark(); }
   int sorted = 0;

@@ -365,3 +365,21 @@ def test_phase_counts(rc, n_phases, seed):
         m = w.random_affine(seed, n_blocks=8, block=128, n_stmts=14, n_phases=n_phases, plant=plant)
         compare(rc, m)
         compare(rc, m, {"test_flags": 2})   # RC_TEST_FEW_SCAN_WARPS
+
+
+@pytest.mark.parametrize("n", [1000, 100_003])
+def test_sort_unaligned_buffers(rc, n):
+    """Key buffers that start 8 bytes past a 16-byte boundary (the histogram
+    then takes its unvectorised path)."""
+    g = torch.Generator().manual_seed(n)
+    x = torch.randint(-(1 << 62), 1 << 62, (n + 1,), generator=g, dtype=torch.int64)
+    keys = x[1:].numpy().view(np.uint64)
+    exp = keys[np.argsort((keys >> np.uint64(3)) & np.uint64((1 << 20) - 1), kind="stable")]
+    din = x.cuda()[1:]
+    dbuf = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    dout = dbuf[1:]
+    assert din.data_ptr() % 16 == 8 and dout.data_ptr() % 16 == 8
+    ws = rc.workspace(rc.rc_sort_workspace_size(n, 8))
+    rc.rc_sort_keys(din, dout, n, 3, 23, 8, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(dout.cpu().numpy().view(np.uint64), exp)
