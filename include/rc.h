@@ -85,10 +85,16 @@ const char* rc_status_str(rc_status s);
  *   RC_OP_MUL    pop a, push imm * a
  *   RC_OP_FDIV   pop a, push floor(a / imm)   (imm > 0; rounds toward minus infinity)
  *   RC_OP_MOD    pop a, push a mod imm        (imm > 0; Euclidean, result in [0, imm))
+ *   RC_OP_LOAD   pop a, push tables[arg].data[a]: a data-dependent value such as
+ *                the row bounds rowPtr[i], rowPtr[i + 1] of a sparse matrix (the
+ *                paper's rs / re of Ge-SpMM, Section "Problems to deal with",
+ *                made concrete instead of over-approximated by a superset).
+ *                A table reads as 0 outside [0, len) (a total function, so a
+ *                load needs no out-of-bounds report).
  * A well-formed expression leaves exactly one value. */
 enum {
   RC_OP_CONST = 0, RC_OP_TID = 1, RC_OP_BID = 2, RC_OP_PARAM = 3, RC_OP_ITER = 4,
-  RC_OP_ADD = 5, RC_OP_MUL = 6, RC_OP_FDIV = 7, RC_OP_MOD = 8
+  RC_OP_ADD = 5, RC_OP_MUL = 6, RC_OP_FDIV = 7, RC_OP_MOD = 8, RC_OP_LOAD = 9
 };
 typedef struct rc_insn { int32_t op; int32_t arg; int64_t imm; } rc_insn;
 typedef struct rc_expr { const rc_insn* code; uint32_t len; } rc_expr;
@@ -125,6 +131,12 @@ typedef struct rc_array {
   int64_t extent[4];       /* sizes of the dimensions, each >= 1                  */
 } rc_array;
 
+/* A read-only integer table for RC_OP_LOAD (copied by rc_model_create). */
+typedef struct rc_table {
+  const int64_t* data;     /* host memory, len values                             */
+  uint64_t len;
+} rc_table;
+
 typedef struct rc_model_desc {
   uint32_t grid[3];        /* gridDim  (each >= 1)                                */
   uint32_t block[3];       /* blockDim (each >= 1)                                */
@@ -132,6 +144,7 @@ typedef struct rc_model_desc {
   uint32_t n_phases;       /* phases are in [0, n_phases); >= 1                   */
   const rc_array* arrays;  uint32_t n_arrays;
   const rc_stmt* stmts;    uint32_t n_stmts;
+  const rc_table* tables;  uint32_t n_tables;   /* for RC_OP_LOAD; may be 0     */
 } rc_model_desc;
 
 /* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED

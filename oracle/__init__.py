@@ -98,6 +98,8 @@ def _expr_text(e) -> str:
         return f"( / {_expr_text(a[0])} {int(a[1])} )"
     if op == "mod":
         return f"( % {_expr_text(a[0])} {int(a[1])} )"
+    if op == "load":
+        return f"( L {int(a[0])} {_expr_text(a[1])} )"
     raise ValueError(op)
 
 
@@ -107,8 +109,12 @@ def model_text(m) -> str:
            "grid %d %d %d" % tuple(m.grid),
            "block %d %d %d" % tuple(m.block),
            "params %d %s" % (len(m.params), " ".join(str(int(p)) for p in m.params)),
-           "phases %d" % m.n_phases,
-           "arrays %d" % len(m.arrays)]
+           "phases %d" % m.n_phases]
+    tables = getattr(m, "tables", None) or []
+    out.append("tables %d" % len(tables))
+    for t in tables:
+        out.append("%d %s" % (len(t), " ".join(str(int(v)) for v in t)))
+    out.append("arrays %d" % len(m.arrays))
     for a in m.arrays:
         out.append("%s %d %s" % ("S" if a.scope == "shared" else "G", len(a.extents),
                                  " ".join(str(e) for e in a.extents)))

@@ -64,11 +64,11 @@ namespace {
 // ----------------------------------------------------------------------------
 // model
 // ----------------------------------------------------------------------------
-enum Op { C_CONST, C_TID, C_BID, C_PARAM, C_ITER, C_ADD, C_MUL, C_FDIV, C_MOD };
+enum Op { C_CONST, C_TID, C_BID, C_PARAM, C_ITER, C_ADD, C_MUL, C_FDIV, C_MOD, C_LOAD };
 
 struct Node {
   Op op;
-  int64_t v;   // constant, axis, parameter number, loop level, multiplier or divisor
+  int64_t v;   // constant, axis, parameter number, loop level, multiplier, divisor or table
   int a, b;    // operand node indices (or -1)
 };
 
@@ -90,6 +90,7 @@ struct Model {
   int64_t grid[3], block[3];
   std::vector<int64_t> params;
   int64_t n_phases = 1;
+  std::vector<std::vector<int64_t>> tables;   // integer tables read by loads (0 outside)
   std::vector<Array> arrays;
   std::vector<Stmt> stmts;
 };
@@ -100,6 +101,7 @@ struct Model {
 struct Parser {
   std::vector<std::string> tok;
   size_t pos = 0;
+  size_t n_tables = 0;
   explicit Parser(const char* s) {
     std::string cur;
     for (const char* p = s; *p; ++p) {
@@ -140,6 +142,9 @@ struct Parser {
       } else if (o == "%") {
         n.op = C_MOD; n.a = expr_node(e); n.v = integer();
         if (n.v <= 0) throw std::runtime_error("modulus must be positive");
+      } else if (o == "L") {
+        n.op = C_LOAD; n.v = integer(); n.a = expr_node(e);
+        if (n.v < 0 || n.v >= (int64_t)n_tables) throw std::runtime_error("bad table");
       } else {
         throw std::runtime_error("bad operator " + o);
       }
@@ -174,6 +179,15 @@ struct Parser {
     for (int64_t i = 0; i < np; ++i) m.params.push_back(integer());
     expect("phases");
     m.n_phases = integer();
+    expect("tables");
+    int64_t nt = integer();
+    for (int64_t t = 0; t < nt; ++t) {
+      int64_t len = integer();
+      std::vector<int64_t> v;
+      for (int64_t k = 0; k < len; ++k) v.push_back(integer());
+      m.tables.push_back(v);
+    }
+    n_tables = m.tables.size();
     expect("arrays");
     int64_t na = integer();
     for (int64_t i = 0; i < na; ++i) {
@@ -233,6 +247,7 @@ struct Parser {
 struct Env {
   int64_t tid[3], bid[3];
   const std::vector<int64_t>* params;
+  const std::vector<std::vector<int64_t>>* tables;
   int64_t iter[16];
 };
 
@@ -264,6 +279,12 @@ int64_t eval(const Expr& e, int n, const Env& env) {
     case C_MUL: return wrap_mul(x.v, eval(e, x.a, env));
     case C_FDIV: return floor_div(eval(e, x.a, env), x.v);
     case C_MOD: return euclid_mod(eval(e, x.a, env), x.v);
+    case C_LOAD: {
+      // a table reads as 0 outside its values
+      const std::vector<int64_t>& t = (*env.tables)[x.v];
+      const int64_t i = eval(e, x.a, env);
+      return (i < 0 || i >= (int64_t)t.size()) ? 0 : t[i];
+    }
   }
   return 0;
 }
@@ -376,6 +397,7 @@ struct Enumerator {
     const int64_t bsize = m.block[0] * m.block[1] * m.block[2];
     Env env;
     env.params = &m.params;
+    env.tables = &m.tables;
     for (int64_t bz = 0; bz < m.grid[2]; ++bz)
       for (int64_t by = 0; by < m.grid[1]; ++by)
         for (int64_t bx = 0; bx < m.grid[0]; ++bx) {

@@ -32,7 +32,7 @@ STATUS_NAMES = {RC_OK: "RC_OK", RC_E_INVALID: "RC_E_INVALID", RC_E_KEY_OVERFLOW:
                 RC_E_CUDA: "RC_E_CUDA", RC_E_NOT_READY: "RC_E_NOT_READY",
                 RC_E_UNSUPPORTED: "RC_E_UNSUPPORTED"}
 RC_OP_CONST, RC_OP_TID, RC_OP_BID, RC_OP_PARAM, RC_OP_ITER, RC_OP_ADD, RC_OP_MUL, RC_OP_FDIV, \
-    RC_OP_MOD = range(9)
+    RC_OP_MOD, RC_OP_LOAD = range(10)
 RC_SCOPE_GLOBAL, RC_SCOPE_SHARED = 0, 1
 RC_READ, RC_WRITE = 0, 1
 RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
@@ -86,12 +86,17 @@ class rc_array(Structure):
     _fields_ = [("name", c_char_p), ("scope", c_uint32), ("ndims", c_uint32), ("extent", c_int64 * 4)]
 
 
+class rc_table(Structure):
+    _fields_ = [("data", POINTER(c_int64)), ("len", c_uint64)]
+
+
 class rc_model_desc(Structure):
     _fields_ = [("grid", c_uint32 * 3), ("block", c_uint32 * 3),
                 ("params", POINTER(c_int64)), ("n_params", c_uint32),
                 ("n_phases", c_uint32),
                 ("arrays", POINTER(rc_array)), ("n_arrays", c_uint32),
-                ("stmts", POINTER(rc_stmt)), ("n_stmts", c_uint32)]
+                ("stmts", POINTER(rc_stmt)), ("n_stmts", c_uint32),
+                ("tables", POINTER(rc_table)), ("n_tables", c_uint32)]
 
 
 class rc_limits(Structure):
@@ -251,6 +256,9 @@ def _postfix(e, out: list):
     elif op == "mod":
         _postfix(a[0], out)
         out.append((RC_OP_MOD, 0, int(a[1])))
+    elif op == "load":
+        _postfix(a[1], out)
+        out.append((RC_OP_LOAD, int(a[0]), 0))
     else:
         raise ValueError(f"unknown expression node {op}")
 
@@ -315,6 +323,17 @@ class _Desc:
         self.keep.append(stmts)
         d.stmts = stmts
         d.n_stmts = len(model.stmts)
+        tables = getattr(model, "tables", None) or []
+        if tables:
+            tabs = (rc_table * len(tables))()
+            for i, t in enumerate(tables):
+                data = (c_int64 * max(1, len(t)))(*[int(v) for v in t])
+                self.keep.append(data)
+                tabs[i].data = ctypes.cast(data, POINTER(c_int64))
+                tabs[i].len = len(t)
+            self.keep.append(tabs)
+            d.tables = tabs
+        d.n_tables = len(tables)
         self.desc = d
 
     def expr(self, e) -> rc_expr:

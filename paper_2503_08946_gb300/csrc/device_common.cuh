@@ -55,7 +55,7 @@ __device__ __forceinline__ void eval_terms(const DevModel& M, const DevStmt& S, 
     const Term T = M.terms[S.term0 + q];
     if (T.level == level) {
       const int64_t a = eval_row(M, T.row, tv, it, term);
-      term[q] = T.op == kFdiv ? floor_div(a, T.d) : euclid_mod(a, T.d);
+      term[q] = T.op == kFdiv ? floor_div(a, T.d) : T.op == kMod ? euclid_mod(a, T.d) : table_load(M, T.d, a);
     }
   }
 }

@@ -71,7 +71,10 @@ __device__ __forceinline__ void terms_at_level(const FastCtx& c, int level, cons
     const int64_t a = row_eval<L>(c, __ldg(&T[q].row), it);
     const int64_t d = __ldg(&T[q].d);
     const uint64_t mg = __ldg(&T[q].magic);
-    c.tval[q * kExpandThreads] = __ldg(&T[q].op) == kFdiv ? fast_floor_div(a, d, mg) : fast_euclid_mod(a, d, mg);
+    const int32_t op = __ldg(&T[q].op);
+    c.tval[q * kExpandThreads] = op == kFdiv ? fast_floor_div(a, d, mg)
+                                 : op == kMod ? fast_euclid_mod(a, d, mg)
+                                              : table_load(*c.M, d, a);
   }
 }
 

@@ -152,8 +152,14 @@ struct Gen {
       if (T.level != level) continue;
       const std::string a = row(T.row);
       std::string v;
-      if (T.op == kFdiv) v = is_pow2(T.d) ? "(" + a + " >> " + std::to_string(log2i(T.d)) + ")" : "fdiv_c(" + a + ", " + lit(T.d) + ")";
-      else v = is_pow2(T.d) ? "(" + a + " & " + lit(T.d - 1) + ")" : "mod_c(" + a + ", " + lit(T.d) + ")";
+      if (T.op == kLoad) {
+        const uint64_t* tidx = reinterpret_cast<const uint64_t*>(img + m.sec_tabidx);
+        v = "tload_c(tdata, " + ulit(tidx[2 * T.d]) + ", " + ulit(tidx[2 * T.d + 1]) + ", " + a + ")";
+      } else if (T.op == kFdiv) {
+        v = is_pow2(T.d) ? "(" + a + " >> " + std::to_string(log2i(T.d)) + ")" : "fdiv_c(" + a + ", " + lit(T.d) + ")";
+      } else {
+        v = is_pow2(T.d) ? "(" + a + " & " + lit(T.d - 1) + ")" : "mod_c(" + a + ", " + lit(T.d) + ")";
+      }
       o << ind << "const long long q" << q << " = " << v << ";\n";
     }
   }
@@ -235,9 +241,12 @@ struct Gen {
     o << "__device__ __forceinline__ long long fdiv_c(long long a, long long d) {\n"
          "  return a >= 0 ? a / d : -1 - (-(a + 1)) / d;\n}\n";
     o << "__device__ __forceinline__ long long mod_c(long long a, long long d) { return a - fdiv_c(a, d) * d; }\n";
+    o << "__device__ __forceinline__ long long tload_c(const long long* t, unsigned long long off, "
+         "unsigned long long len, long long i) {\n"
+         "  return (i < 0 || (unsigned long long)i >= len) ? 0LL : t[off + (unsigned long long)i];\n}\n";
     o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
          "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
-         "unsigned long long cell_lo, unsigned long long cell_hi) {\n";
+         "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata) {\n";
     o << "  const unsigned long long g = (unsigned long long)blockIdx.x * 128ull + threadIdx.x;\n";
     o << "  unsigned long long cnt = 0;\n";
     o << "  if (g < " << ulit(h.n_threads) << ") {\n";
@@ -323,7 +332,8 @@ cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cu
   unsigned long long* inst = &res->instances;
   const uint64_t* uo = m.host.unit_offset;
   unsigned long long lo = cell_lo, hi = cell_hi;
-  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi};
+  const int64_t* td = m.host.tdata;
+  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td};
   const unsigned gx = (unsigned)((m.host.n_threads + 127) / 128);
   const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

@@ -155,6 +155,32 @@ struct StmtBuilder {
           st.back() = r;
           break;
         }
+        case RC_OP_LOAD: {
+          // a data-dependent value: always a term (never folded), so that an
+          // index outside the table is reported for the thread that reads it
+          if (st.empty() || in.arg < 0 || (uint32_t)in.arg >= desc->n_tables || !desc->tables) {
+            err = RC_E_INVALID;
+            return false;
+          }
+          Lin a = st.back();
+          TermKey k{a, kLoad, (int64_t)in.arg};
+          auto it = term_ids.find(k);
+          int id;
+          if (it == term_ids.end()) {
+            if ((int)terms.size() >= kMaxTerms) { err = RC_E_UNSUPPORTED; return false; }
+            id = (int)terms.size();
+            terms.push_back(k);
+            term_ids[k] = id;
+            term_level.push_back(level_of(a));
+            term_tid.push_back(depends_on_tid(a));
+          } else {
+            id = it->second;
+          }
+          Lin r;
+          r.v[kMaxLoops + id] = 1;
+          st.back() = r;
+          break;
+        }
         default: err = RC_E_INVALID; return false;
       }
     }
@@ -201,6 +227,9 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   if (d->n_stmts && !d->stmts) return RC_E_INVALID;
   if (d->n_arrays && !d->arrays) return RC_E_INVALID;
   if (d->n_params && !d->params) return RC_E_INVALID;
+  if (d->n_tables && !d->tables) return RC_E_INVALID;
+  for (uint32_t t = 0; t < d->n_tables; ++t)
+    if (d->tables[t].len && !d->tables[t].data) return RC_E_INVALID;
 
   DevModel& h = m->host;
   std::memset(&h, 0, sizeof(h));
@@ -369,7 +398,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
       t.d = b.terms[q].d;
       t.level = b.term_level[q];
       t.pad = 0;
-      t.magic = fastdiv_magic(t.d);
+      t.magic = t.op == kLoad ? 0 : fastdiv_magic(t.d);
       terms.push_back(t);
     }
     D.dense = dense ? 1 : 0;
@@ -401,7 +430,18 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   size_t off_rows = align256(off_accs + accs.size() * sizeof(DevAccess));
   size_t off_lin = align256(off_rows + rows.size() * sizeof(Row));
   size_t off_terms = align256(off_lin + lin.size() * sizeof(LinTerm));
-  size_t off_units = align256(off_terms + terms.size() * sizeof(Term));
+  // tables: (offset, length) per table, then the values
+  std::vector<uint64_t> tab_index;
+  uint64_t tab_words = 0;
+  for (uint32_t t = 0; t < d->n_tables; ++t) {
+    tab_index.push_back(tab_words);
+    tab_index.push_back(d->tables[t].len);
+    if (tab_words + d->tables[t].len < tab_words || d->tables[t].len > (1ull << 40)) return RC_E_UNSUPPORTED;
+    tab_words += d->tables[t].len;
+  }
+  size_t off_tabidx = align256(off_terms + terms.size() * sizeof(Term));
+  size_t off_tdata = align256(off_tabidx + tab_index.size() * 8);
+  size_t off_units = align256(off_tdata + (size_t)tab_words * 8);
   size_t total = off_units;
   m->program.assign(total, 0);
   auto put = [&](size_t off, const void* src, size_t n) {
@@ -413,6 +453,9 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   put(off_rows, rows.data(), rows.size() * sizeof(Row));
   put(off_lin, lin.data(), lin.size() * sizeof(LinTerm));
   put(off_terms, terms.data(), terms.size() * sizeof(Term));
+  put(off_tabidx, tab_index.data(), tab_index.size() * 8);
+  for (uint32_t t = 0; t < d->n_tables; ++t)
+    put(off_tdata + (size_t)tab_index[2 * t] * 8, d->tables[t].data, (size_t)d->tables[t].len * 8);
   // device pointers are stored as offsets here and relocated at upload
   h.arrays = reinterpret_cast<const DevArray*>(off_arrays);
   h.stmts = reinterpret_cast<const DevStmt*>(off_stmts);
@@ -421,12 +464,16 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.lin = reinterpret_cast<const LinTerm*>(off_lin);
   h.terms = reinterpret_cast<const Term*>(off_terms);
   h.unit_offset = reinterpret_cast<const uint64_t*>(off_units);
+  h.tables = reinterpret_cast<const uint64_t*>(off_tabidx);
+  h.tdata = reinterpret_cast<const int64_t*>(off_tdata);
+  h.n_tables = d->n_tables;
   m->sec_arrays = off_arrays;
   m->sec_stmts = off_stmts;
   m->sec_accs = off_accs;
   m->sec_rows = off_rows;
   m->sec_lin = off_lin;
   m->sec_terms = off_terms;
+  m->sec_tabidx = off_tabidx;
   return RC_OK;
 }
 

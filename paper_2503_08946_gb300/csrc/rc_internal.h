@@ -63,7 +63,7 @@ struct Row {
   int32_t cache; // slot of its per-thread cached value when level == 0 and used per point, else -1
 };
 
-enum TermOp : int32_t { kFdiv = 0, kMod = 1 };
+enum TermOp : int32_t { kFdiv = 0, kMod = 1, kLoad = 2 };   // kLoad: d = table number
 
 struct Term {
   int32_t row;
@@ -131,7 +131,17 @@ struct DevModel {
   const LinTerm* lin;
   const Term* terms;
   const uint64_t* unit_offset;  // general statements: offset of each (stmt, gtid) unit
+  const uint64_t* tables;       // per table: offset into tdata, length (2 words each)
+  const int64_t* tdata;         // table values
+  uint32_t n_tables, pad_t;
 };
+
+// Value of a table load: tables read as 0 outside [0, len), so a load is a
+// total function of its index and needs no out-of-bounds report.
+RC_HD int64_t table_load(const DevModel& M, int64_t table, int64_t idx) {
+  const uint64_t off = M.tables[2 * table], len = M.tables[2 * table + 1];
+  return (idx < 0 || (uint64_t)idx >= len) ? 0 : M.tdata[off + (uint64_t)idx];
+}
 
 // ---------------------------------------------------------------------------
 // device result record (head of the workspace)
@@ -334,7 +344,7 @@ struct Model {
   uint32_t n_general_stmts = 0;
   bool has_deep_loops = false;    // some statement has more than kFastLoops loops
   // sections of the program image (byte offsets), for the kernel generator
-  size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0;
+  size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null
   uint64_t max_iter_per_unit = 0;
 };

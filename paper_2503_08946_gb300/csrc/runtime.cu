@@ -864,6 +864,8 @@ rc_status rc_model_create(const rc_model_desc* desc, rc_model** out) {
   h.lin = reinterpret_cast<const rc::LinTerm*>(base + reinterpret_cast<uintptr_t>(h.lin));
   h.terms = reinterpret_cast<const rc::Term*>(base + reinterpret_cast<uintptr_t>(h.terms));
   h.unit_offset = reinterpret_cast<const uint64_t*>(base + reinterpret_cast<uintptr_t>(h.unit_offset));
+  h.tables = reinterpret_cast<const uint64_t*>(base + reinterpret_cast<uintptr_t>(h.tables));
+  h.tdata = reinterpret_cast<const int64_t*>(base + reinterpret_cast<uintptr_t>(h.tdata));
   std::memcpy(m.program.data(), &h, sizeof(h));
   cudaStream_t st;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

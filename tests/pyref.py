@@ -28,6 +28,10 @@ def ev(e, env):
         return ev(a[0], env) // a[1]
     if op == "mod":
         return ev(a[0], env) % a[1]
+    if op == "load":
+        t = env["tables"][a[0]]
+        i = ev(a[1], env)
+        return t[i] if 0 <= i < len(t) else 0
     raise ValueError(op)
 
 
@@ -42,7 +46,8 @@ def instances(m):
         b = bx + gx * (by + gy * bz)
         for tz, ty, tx in product(range(bz_), range(by_), range(bx_)):
             t = tx + bx_ * (ty + by_ * tz)
-            env = {"tid": (tx, ty, tz), "bid": (bx, by, bz), "params": m.params, "iter": [0] * 8}
+            env = {"tid": (tx, ty, tz), "bid": (bx, by, bz), "params": m.params, "iter": [0] * 8,
+                   "tables": getattr(m, "tables", [])}
             for si, st in enumerate(m.stmts):
                 def rec(level):
                     if level == len(st.loops):

@@ -46,7 +46,7 @@ def test_library_exports_every_declared_symbol(rc):
 
 def test_struct_layout_matches_c(rc):
     b = rc.binding
-    structs = ["rc_insn", "rc_expr", "rc_loop", "rc_access", "rc_stmt", "rc_array", "rc_model_desc",
+    structs = ["rc_insn", "rc_expr", "rc_loop", "rc_access", "rc_stmt", "rc_array", "rc_table", "rc_model_desc",
                "rc_limits", "rc_layout", "rc_check_opts", "rc_inst", "rc_result", "rc_server_opts",
                "rc_server_done"]
     fields = {s: [f for f, _ in getattr(b, s)._fields_] for s in structs}
@@ -124,7 +124,9 @@ def test_generated_kernels_compile(rc, tmp_path):
     deep = Model((2, 1, 1), (8, 1, 1), [Array("a", "shared", (64,))],
                  [Stmt([Access(0, W, ((tid.x + it(0) + it(1) + it(2) + it(3) + it(4)) % 64,))],
                        loops=[Loop(0, 2)] * 5)])
-    for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep]):
+    csr = w.ge_spmm_csr(w.csr_row_lengths(1, 8), N=64, K=2)
+    for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep, csr,
+                           w.tiny_random_tables(3)]):
         src = rc.rc_kernel_source(m)
         assert "rc_expand_jit" in src
         f = tmp_path / f"k{i}.cu"

@@ -242,3 +242,58 @@ def test_pins_detect_planted_mistake():
             if x[:3] == y[:3] and (x[6] or y[6]) and x[4] == y[4]:
                 buggy.add(x[:3])
     assert len(buggy) > 0 and oracle.check(m).racy_cells == 0
+
+
+# --------------------------------------------------------------------------
+# data-dependent values: table loads (CSR row bounds of Ge-SpMM)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(120))
+def test_tiny_tables_vs_python_bruteforce(seed):
+    """Tiny models whose bounds, guards and indices read integer tables."""
+    m = w.tiny_random_tables(seed)
+    st, cnt, best = pyref.check(m)
+    r = oracle.check(m)
+    rb = oracle.brute(m)
+    assert st == "ok" and r.status == 0 and rb.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    inst, _ = pyref.instances(m)
+    assert r.instances == len(inst) and r.distinct == len(set(inst))
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        assert r.witness == (x[0], x[1], x[2], (x[3], x[4], x[5], x[6]), (y[3], y[4], y[5], y[6]))
+
+
+def test_table_reads_zero_outside():
+    """for i < T[t]: W s[i] with T = [3, 1, 4] and 8 threads: threads 3..7 read
+    0 (outside the table) and run no iteration; 8 instances; cells 0, 1, 2 are
+    written by >= 2 threads, cell 3 by one."""
+    from workloads.spec import Access, Array, Loop, Model, Stmt, W, it, load, tid
+    m = Model((1, 1, 1), (8, 1, 1), [Array("s", "shared", (8,))],
+              [Stmt([Access(0, W, (it(0),))], loops=[Loop(0, load(0, tid.x))])], tables=[[3, 1, 4]])
+    r = oracle.check(m)
+    assert (r.status, r.instances, r.racy_cells) == (0, 8, 3)
+    assert r.witness == (0, 0, 0, (0, 0, 0, 1), (0, 0, 1, 1))
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("bar", [True, False])
+def test_gespmm_csr_closed_form(seed, bar):
+    """Ge-SpMM on a skewed CSR (row bounds loaded from rowPtr): race-free with
+    the barrier after T (the paper's expected verdict for Ge-SpMM); without it
+    2 * min(32, max(0, L_i - 32)) racy shared cells per block row and slab."""
+    lens = w.csr_row_lengths(seed, 12, max_len=150)
+    m = w.ge_spmm_csr(lens, N=64, K=3, trailing_barrier=bar)
+    r = oracle.check(m)
+    exp = 0 if bar else (64 // 32) * sum(2 * min(32, max(0, L - 32)) for L in lens)
+    assert r.status == 0 and r.racy_cells == exp
+
+
+@pytest.mark.parametrize("L", [1, 32, 33, 70])
+def test_gespmm_csr_uniform_rows_equal_uniform_model(L):
+    for bar in (True, False):
+        a = oracle.check(w.ge_spmm_uniform(3, 64, 4, L, trailing_barrier=bar))
+        b = oracle.check(w.ge_spmm_csr([L] * 3, 64, 4, trailing_barrier=bar))
+        assert (a.status, a.instances, a.racy_cells, a.witness) == (b.status, b.instances, b.racy_cells, b.witness)

@@ -31,11 +31,12 @@ from typing import List, Optional, Tuple
 
 from .rng import SplitMix64
 from .spec import (GLOBAL, SHARED, Access, Array, Expr, Loop, Model, R, Stmt, W,
-                   bid, const, it, param, tid)
+                   bid, const, it, load, param, tid)
 
 __all__ = [
     "reduction_tree", "transpose", "random_affine", "batch_models", "request_stream",
-    "neighbor_write_read", "polyhedral_product", "ge_spmm_uniform", "tiny_random",
+    "neighbor_write_read", "polyhedral_product", "ge_spmm_uniform", "ge_spmm_csr", "csr_row_lengths",
+    "tiny_random", "tiny_random_tables",
     "RANDOM_AFFINE_ROW_GLOBAL", "RANDOM_AFFINE_ROW_SHARED",
 ]
 
@@ -181,6 +182,78 @@ def ge_spmm_uniform(M: int = 4, N: int = 64, K: int = 8, L: int = 70,
     n_phases = 2 * nch if trailing_barrier else nch + 1
     return Model((M, N // 32, 1), (32, 1, 1), arrays, [I, F, T, TB], n_phases=max(n_phases, 1),
                  name=f"gespmm_M{M}_N{N}_K{K}_L{L}_{'bar' if trailing_barrier else 'nobar'}")
+
+
+def ge_spmm_csr(row_lengths: List[int], N: int = 64, K: int = 8, trailing_barrier: bool = True) -> Model:
+    """Ge-SpMM Algorithm 2 on a CSR matrix with the given row lengths.
+
+    As :func:`ge_spmm_uniform`, but the row bounds are read from the row
+    pointer array itself: ``rs = rowPtr[i]`` and ``re = rowPtr[i + 1]`` are table
+    loads (table 0 holds rowPtr), so the number of 32-wide chunks of block row
+    ``i`` is ``ceil((re - rs) / 32)`` and its barrier intervals depend on the
+    row -- the data-dependent Domain that the paper's model over-approximates
+    with a superset (Section "Problems to deal with").  Without the trailing
+    barrier each block row ``i`` has ``2 * min(32, max(0, L_i - 32))`` racy
+    shared cells per 32-column slab; with it the model is race-free.
+    """
+    if N % 32:
+        raise ValueError("N must be a multiple of 32")
+    M = len(row_lengths)
+    lens = [int(v) for v in row_lengths]
+    if M == 0 or min(lens) < 0:
+        raise ValueError("need at least one row and non-negative lengths")
+    row_ptr = [0]
+    for v in lens:
+        row_ptr.append(row_ptr[-1] + v)
+    nnz = max(1, row_ptr[-1])
+    max_ch = max(1, max((v + 31) // 32 for v in lens))
+    i = bid.x
+    j = bid.y * 32 + tid.x
+    m, kk, k = it(0), it(1), it(2)
+    rs, re = load(0, i), load(0, i + 1)
+    n_ch = (re - rs + 31) // 32
+    arrays = [
+        Array("A_rowPtr", GLOBAL, (M + 1,)),
+        Array("A_colInd", GLOBAL, (nnz,)),
+        Array("A_val", GLOBAL, (nnz,)),
+        Array("B", GLOBAL, (K, N)),
+        Array("C", GLOBAL, (M, N)),
+        Array("sm_k", SHARED, (32,)),
+        Array("sm_v", SHARED, (32,)),
+    ]
+    ptr = rs + 32 * m
+    I = Stmt([Access(0, R, (i,)), Access(0, R, (i + 1,))], phase=const(0), name="I")
+    F = Stmt([Access(1, R, (ptr + (j % 32),)), Access(2, R, (ptr + (j % 32),)),
+              Access(5, W, (j % 32,)), Access(6, W, (j % 32,))],
+             loops=[Loop(0, n_ch)],
+             guards=[re - (ptr + (j % 32)) - 1],                 # ptr + (j % 32) < re
+             phase=(2 * m) if trailing_barrier else m, name="F")
+    T = Stmt([Access(5, R, ((j - (j % 32)) % 32 + kk,)), Access(6, R, ((j - (j % 32)) % 32 + kk,)),
+              Access(4, R, (i, j)), Access(4, W, (i, j))],
+             loops=[Loop(0, n_ch), Loop(0, 32)],
+             guards=[re - (ptr + kk) - 1],                        # ptr + kk < re
+             phase=(2 * m + 1) if trailing_barrier else (m + 1), name="T")
+    TB = Stmt([Access(3, R, (k, j))],
+              loops=[Loop(0, n_ch), Loop(0, 32), Loop(0, K)],
+              guards=[re - (ptr + kk) - 1],
+              phase=(2 * m + 1) if trailing_barrier else (m + 1), name="T_B")
+    n_phases = 2 * max_ch if trailing_barrier else max_ch + 1
+    return Model((M, N // 32, 1), (32, 1, 1), arrays, [I, F, T, TB], n_phases=n_phases,
+                 name=f"gespmm_csr_M{M}_N{N}_K{K}_{'bar' if trailing_barrier else 'nobar'}",
+                 tables=[row_ptr])
+
+
+def csr_row_lengths(seed: int, M: int, max_len: int = 150, empty: float = 0.1) -> List[int]:
+    """Seeded skewed row lengths: log-uniform in [1, max_len], a fraction of
+    empty rows."""
+    rng = SplitMix64(0xC5A ^ seed)
+    out = []
+    for _ in range(M):
+        if rng.chance(empty):
+            out.append(0)
+        else:
+            out.append(max(1, min(max_len, int(math.exp(rng.random() * math.log(max_len))))))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -387,3 +460,44 @@ def tiny_random(seed: int) -> Model:
             accs.append(Access(a, W if rng.chance(0.4) else R, idx))
         stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, name=f"t{s}"))
     return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tiny{seed}")
+
+
+def tiny_random_tables(seed: int) -> Model:
+    """A tiny random model whose loop bounds, guards and indices read small
+    integer tables (data-dependent values; indices outside a table read 0):
+    loop bounds such as ``T0[tid.x + i0]``, scatter writes such as
+    ``a[T1[tid.x] mod 4]``.  Indices of arrays are reduced modulo the extent."""
+    rng = SplitMix64(0x7AB1E ^ (seed * 0x9E3779B97F4A7C15))
+    tables = [[rng.uniform_int(-2, 6) for _ in range(rng.uniform_int(2, 8))]
+              for _ in range(rng.uniform_int(1, 2))]
+
+    def maybe_load(e):
+        if rng.chance(0.5):
+            return load(rng.below(len(tables)), e) + rng.uniform_int(-1, 1)
+        return e
+
+    grid = (rng.uniform_int(1, 3), 1, 1)
+    block = (rng.uniform_int(1, 5), rng.uniform_int(1, 2), 1)
+    params = [rng.uniform_int(-2, 4), rng.uniform_int(0, 3)]
+    arrays = [Array(f"a{a}", SHARED if rng.below(2) else GLOBAL, (rng.uniform_int(2, 6),))
+              for a in range(rng.uniform_int(1, 3))]
+    n_phases = rng.uniform_int(1, 3)
+    stmts = []
+    for s_ in range(rng.uniform_int(1, 4)):
+        depth = rng.below(3)
+        loops = []
+        for l in range(depth):
+            lo = const(rng.uniform_int(-1, 1))
+            hi = maybe_load(_tiny_expr(rng, l, allow_tid=True))
+            loops.append(Loop(lo, hi, 1))
+        guards = [maybe_load(_tiny_expr(rng, depth)) for _ in range(rng.below(2))]
+        ph = const(rng.below(n_phases))
+        accs = []
+        for _ in range(rng.uniform_int(1, 3)):
+            a = rng.below(len(arrays))
+            idx = (maybe_load(_tiny_expr(rng, depth)) % arrays[a].extents[0],)
+            accs.append(Access(a, W if rng.chance(0.45) else R, idx))
+        stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, name=f"t{s_}"))
+    return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tinytab{seed}",
+                 tables=tables)
+

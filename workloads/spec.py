@@ -25,7 +25,7 @@ from dataclasses import dataclass, field
 from typing import List, Sequence, Tuple, Union
 
 __all__ = [
-    "Expr", "E", "tid", "bid", "param", "it", "const",
+    "Expr", "E", "tid", "bid", "param", "it", "const", "load",
     "Array", "Loop", "Access", "Stmt", "Model", "R", "W", "GLOBAL", "SHARED",
 ]
 
@@ -38,10 +38,12 @@ SHARED = "shared"
 class Expr:
     """Immutable expression tree node.
 
-    ``op`` is one of ``const, tid, bid, param, iter, add, mul, fdiv, mod`` and
-    ``args`` holds the operands: for leaves an ``int`` (the constant, the axis
-    0..2, the parameter number or the loop level), for ``add`` two ``Expr``, for
-    ``mul`` ``(int c, Expr a)``, for ``fdiv``/``mod`` ``(Expr a, int d)``.
+    ``op`` is one of ``const, tid, bid, param, iter, add, mul, fdiv, mod, load``
+    and ``args`` holds the operands: for leaves an ``int`` (the constant, the
+    axis 0..2, the parameter number or the loop level), for ``add`` two
+    ``Expr``, for ``mul`` ``(int c, Expr a)``, for ``fdiv``/``mod``
+    ``(Expr a, int d)``, for ``load`` ``(int table, Expr index)`` -- the value
+    of the model's integer table at the index, 0 outside the table.
     """
 
     __slots__ = ("op", "args")
@@ -132,6 +134,8 @@ class Expr:
             return f"floor({a[0]!r}/{a[1]})"
         if op == "mod":
             return f"({a[0]!r} mod {a[1]})"
+        if op == "load":
+            return f"T{a[0]}[{a[1]!r}]"
         raise ValueError(op)
 
 
@@ -157,6 +161,12 @@ def it(level: int) -> Expr:
 
 def const(c: int) -> Expr:
     return Expr("const", int(c))
+
+
+def load(table: int, index) -> Expr:
+    """Value of the model's integer table `table` at `index` (0 outside it): a
+    data-dependent bound such as a CSR row pointer."""
+    return Expr("load", int(table), Expr.wrap(index))
 
 
 E = Expr.wrap
@@ -230,11 +240,13 @@ class Model:
     params: List[int] = field(default_factory=list)
     n_phases: int = 1
     name: str = ""
+    tables: List[List[int]] = field(default_factory=list)
 
     def __post_init__(self):
         self.grid = tuple(int(v) for v in (list(self.grid) + [1, 1, 1])[:3])
         self.block = tuple(int(v) for v in (list(self.block) + [1, 1, 1])[:3])
         self.params = [int(p) for p in self.params]
+        self.tables = [[int(v) for v in t] for t in self.tables]
 
     @property
     def n_blocks(self) -> int:
