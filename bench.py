@@ -330,6 +330,7 @@ def run_batch(args):
     import workloads as w
     import paper_2503_08946_gb300 as rc
     from paper_2503_08946_gb300 import build as b
+    from paper_2503_08946_gb300 import distributed as D
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -341,16 +342,18 @@ def run_batch(args):
     rc.load()
     models = w.batch_models(args.batch_models, seed0=args.seed * 1000003 + rank * 100003)
     handles = [rc.rc_model_create(m) for m in models]
-    opts = {"digit_bits": args.digit_bits}
+    opts = {"digit_bits": args.digit_bits, "flags": rc.binding.RC_OPT_GRAPH}   # captured once, replayed
     ws = rc.workspace(rc.rc_batch_workspace_size(handles, opts))
     stream = torch.cuda.current_stream()
 
-    def batched():
-        res = rc.rc_report(rc.rc_check_batch(handles, opts, ws, stream))
+    def check_results(res):
         bad = [r for r in res if r.status != rc.RC_OK]
         if bad:
             raise RuntimeError(f"batch check failed: {rc.rc_status_str(bad[0].status)}")
         return res
+
+    def batched():
+        return check_results(rc.rc_report(rc.rc_check_batch(handles, opts, ws, stream)))
 
     def per_model(ws1):
         window, out = [], []
@@ -385,32 +388,50 @@ def run_batch(args):
     inst = sum(r.instances for r in res)
     sampler = ClockSampler(gpu_index(local))
     time.sleep(0.25)
-    res, ms, wall = timed(batched, args.steps)
+    # device throughput: the K batches are enqueued back to back (each one graph
+    # launch plus its result copy), so the host work of one overlaps the GPU work
+    # of the previous; the results are decoded after the timed region
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    tickets = [rc.rc_check_batch(handles, opts, ws, stream) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    for t in tickets:
+        res = check_results(rc.rc_report(t))
+    wall = time.perf_counter() - t0   # end to end: enqueue, device work, decoded results
     clocks = sampler.stop()
+    total_i, ms, value = D.weak_scaling_rate(inst * args.steps, ms, device="cuda")
     total = inst * args.steps * world
-    value = total / (ms / 1e3) / 1e9
 
     # one check per model on one stream, same workspace reused (sized for the largest model)
-    ws1 = rc.workspace(max(rc.rc_workspace_size(h, opts) for h in handles))
-    ref = per_model(ws1)
-    same = all((a.status, a.instances, a.verdict, a.racy_cells, a.witness) ==
-               (b_.status, b_.instances, b_.verdict, b_.racy_cells, b_.witness) for a, b_ in zip(res, ref))
-    pm_steps = max(1, min(3, args.steps))
-    _, pm_ms, pm_wall = timed(lambda: per_model(ws1), pm_steps)
-    pm_value = inst * pm_steps * world / (pm_ms / 1e3) / 1e9
+    pm = None
+    if not args.no_per_model:
+        ws1 = rc.workspace(max(rc.rc_workspace_size(h, opts) for h in handles))
+        ref = per_model(ws1)
+        same = all((a.status, a.instances, a.verdict, a.racy_cells, a.witness) ==
+                   (b_.status, b_.instances, b_.verdict, b_.racy_cells, b_.witness) for a, b_ in zip(res, ref))
+        pm_steps = max(1, min(3, args.steps))
+        _, pm_ms, pm_wall = timed(lambda: per_model(ws1), pm_steps)
+        pm_value = inst * pm_steps * world / (pm_ms / 1e3) / 1e9
+        pm = {"value": pm_value, "unit": UNIT, "ms_per_step": pm_ms / pm_steps, "steps": pm_steps,
+              "results_identical": same}
     if rank == 0:
         line = {
             "metric": METRIC + ", batched", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "models": len(models), "instances_per_rank": inst,
-                       "racy_models": sum(1 for r in res if r.verdict),
+                       "racy_models": sum(1 for r in res if r.verdict), "cuda_graph": True,
                        "l2": "key buffers larger than L2", "parallelism": f"independent batches per rank x{world}"},
-            "per_model": {"value": pm_value, "unit": UNIT, "ms_per_step": pm_ms / pm_steps, "steps": pm_steps,
-                          "results_identical": same},
-            "speedup_vs_per_model": value / pm_value,
-            "e2e": {"value": total / wall / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * len(models),
-                    "d2h_bytes_per_step": 160 * len(models)},
+            "per_model": pm,
+            "speedup_vs_per_model": (value / pm["value"]) if pm else None,
+            "e2e": {"value": total / wall / 1e9, "unit": UNIT, "h2d_bytes_per_step": 80 * len(models),
+                    "d2h_bytes_per_step": 136 * len(models)},
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -481,6 +502,17 @@ def run_serve(args):
     bad = [r for r in recs if r.result.status != rc.RC_OK]
     if bad:
         raise RuntimeError(f"request failed: {rc.rc_status_str(bad[0].result.status)}")
+    # capacity: the same requests submitted at once (offered load far above capacity)
+    burst_ids = [srv.submit(h) for h in handles]
+    burst = drain(len(burst_ids))
+    brec = [burst[i] for i in burst_ids]
+    b_span = max(r.done_s for r in brec) - min(r.submit_s for r in brec)
+    b_inst = sum(r.result.instances for r in brec)
+    capacity = {"value": b_inst / b_span / 1e9, "unit": UNIT, "requests_per_s": len(brec) / b_span,
+                "batch_size_mean": sum(r.batch_size for r in brec) / len(brec),
+                "results_equal_to_poisson_run": all(
+                    (a.result.racy_cells, a.result.witness, a.result.instances) ==
+                    (b_.result.racy_cells, b_.result.witness, b_.result.instances) for a, b_ in zip(recs, brec))}
     lat = sorted((r.done_s - r.submit_s) * 1e3 for r in recs)
     q = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))]
     t_first = min(r.submit_s for r in recs)
@@ -509,6 +541,7 @@ def run_serve(args):
             "latency_ms": {"p50": q(0.50), "p90": q(0.90), "p99": q(0.99), "max": lat[-1],
                            "mean": sum(lat) / len(lat)},
             "batch_size": {"mean": sum(sizes) / len(sizes), "max": max(sizes)},
+            "capacity": capacity,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 96, "d2h_bytes_per_step": 160},
             "clocks": clocks,
         }
@@ -534,6 +567,7 @@ def main():
                     help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models; "
                          "serve: Poisson request stream through the request server")
     ap.add_argument("--batch-models", type=int, default=10000)
+    ap.add_argument("--no-per-model", action="store_true", help="batch: skip the one-check-per-model comparison")
     ap.add_argument("--requests", type=int, default=4000)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--pool-gb", type=int, default=8)

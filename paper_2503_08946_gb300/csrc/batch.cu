@@ -14,8 +14,8 @@
 // bits go to separate packs, each checked by its own pipeline in turn.
 //
 // Expansion is one persistent kernel over a work queue: a unit is (model,
-// statement, chunk of kExpandThreads threads), and blocks take units in
-// groups from an atomic counter until the queue is empty.
+// chunk of kExpandThreads threads) with all the model's statements, and blocks
+// take units in groups from an atomic counter until the queue is empty.
 #include <cuda_runtime.h>
 
 #include "expand_core.cuh"
@@ -25,7 +25,7 @@ namespace rc {
 
 namespace {
 
-constexpr int kUnitsPerGrab = 8;
+constexpr int kUnitsPerGrab = 16;
 static_assert(kExpandThreadsHost == kExpandThreads, "host and device chunk sizes agree");
 
 // Keys are re-packed from the model's layout into the batch layout.
@@ -50,25 +50,36 @@ __global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchAr
   __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
   __shared__ int64_t s_cache[kFastCache * kExpandThreads];
   __shared__ unsigned long long s_u;
+  __shared__ uint32_t s_model;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_u = atomicAdd(a.queue, (unsigned long long)kUnitsPerGrab);
+    if (threadIdx.x == 0) {
+      s_u = atomicAdd(a.queue, (unsigned long long)kUnitsPerGrab);
+      // the model of the grab's first unit (binary search once per grab)
+      uint32_t lo = 0, hi = a.n_models;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a.models[mid].unit_base <= s_u) lo = mid;
+        else hi = mid;
+      }
+      s_model = lo;
+    }
     __syncthreads();
     const uint64_t u0 = s_u;
     if (u0 >= a.n_units) break;
     const uint64_t u1 = min(a.n_units, u0 + kUnitsPerGrab);
     for (uint64_t u = u0; u < u1; ++u) {
-      // the model of unit u
-      uint32_t lo = 0, hi = a.n_models;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a.models[mid].unit_base <= u) lo = mid;
-        else hi = mid;
+      // the model of unit u: the grab's units are consecutive, so step forward
+      if (threadIdx.x == 0) {
+        uint32_t m = s_model;
+        while (m + 1 < a.n_models && a.models[m + 1].unit_base <= u) ++m;
+        s_model = m;
       }
+      __syncthreads();
+      const uint32_t lo = s_model;
       const BatchModel& B = a.models[lo];
-      const uint64_t local = u - B.unit_base;
-      const uint32_t s = (uint32_t)(local / B.n_chunks);
-      const uint64_t g = (local - (uint64_t)s * B.n_chunks) * kExpandThreads + threadIdx.x;
+      // one unit = one chunk of kExpandThreads threads of the model, all its statements
+      const uint64_t g = (u - B.unit_base) * kExpandThreads + threadIdx.x;
       const DevModel& M = *B.dm;
       DevResult* res = a.res + lo;
       unsigned long long count = 0;
@@ -85,22 +96,25 @@ __global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchAr
         sink.bcs = a.cell_shift;
         sink.bps = a.phase_shift;
         sink.bbs = a.block_shift;
-        const DevStmt& S = M.stmts[s];
-        if (S.n_loops > kFastLoops) {
-          expand_unit_generic(M, s, g, res, count, sink);
-        } else {
-          FastCtx c;
-          c.M = B.dm;
-          c.S = &S;
-          c.tv = thread_vars(M, g);
-          c.tval = s_tval + threadIdx.x;
-          c.cache = s_cache + threadIdx.x;
-          expand_unit_dispatch(c, s, g, res, count, sink);
+        const ThreadVars tv = thread_vars(M, g);
+        for (uint32_t s = 0; s < B.n_stmts; ++s) {
+          const DevStmt& S = M.stmts[s];
+          if (S.n_loops > kFastLoops) {
+            expand_unit_generic(M, s, g, res, count, sink);
+          } else {
+            FastCtx c;
+            c.M = B.dm;
+            c.S = &S;
+            c.tv = tv;
+            c.tval = s_tval + threadIdx.x;
+            c.cache = s_cache + threadIdx.x;
+            expand_unit_dispatch(c, s, g, res, count, sink);
+          }
         }
       }
       count = warp_sum(count);
       if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
-      __syncthreads();   // the shared term columns are reused by the next unit
+      __syncthreads();   // s_model is rewritten for the next unit
     }
   }
 }

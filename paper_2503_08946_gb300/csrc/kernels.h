@@ -25,7 +25,7 @@ struct BatchModel {              // one model of a batch (device table entry)
   uint64_t cell_base;            // first batch cell of the model
   uint64_t unit_base;            // first expansion unit of the model
   uint64_t n_threads;
-  uint32_t n_stmts, n_chunks;    // statements, thread chunks per statement
+  uint32_t n_stmts, n_chunks;    // statements, thread chunks (expansion units)
   uint32_t cell_shift, phase_shift, block_shift;   // the model's key layout
   uint32_t phase_bits, block_bits, thread_bits;
 };

@@ -442,7 +442,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
       if (cells >= cur.total_cells && 1 + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
         cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.total_cells = cells; cur.cell_bits = cb;
         cur.n_keys += m.key_slots;
-        cur.n_units += (uint64_t)h.n_stmts * chunks_of(m);
+        cur.n_units += chunks_of(m);
         cur.i1 = i + 1;
         continue;
       }
@@ -455,7 +455,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
-    cur.n_units = (uint64_t)h.n_stmts * chunks_of(m);
+    cur.n_units = chunks_of(m);
     open = true;
   }
   if (open) L->packs.push_back(cur);
@@ -546,7 +546,7 @@ void fill_batch_tables(rc_model* const* models, const BatchLayout& L, void* uplo
       (*field_bits)[i] = k.tb | (k.pb << 8);
       key_base += m.key_slots;
       cb += m.total_cells;
-      unit_base += (uint64_t)h.n_stmts * b.n_chunks;
+      unit_base += b.n_chunks;
     }
   }
 }
