@@ -77,6 +77,7 @@ struct SortArgs {
   unsigned int wait_epoch;                  // epoch the look-back accepts (== epoch in normal use)
   unsigned long long spin_limit;
   unsigned int* err;
+  unsigned long long* cursor;               // partition pass: next output position per digit
 };
 cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
                              cudaStream_t st);
@@ -84,6 +85,8 @@ cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long l
                                  cudaStream_t st);
 // radix_bits: counters of the onesweep kernel (radix_bits_for(pass bits))
 cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t st);
+// unstable pass (any order among equal digits); a.cursor starts at the digit offsets
+cudaError_t launch_partition(const SortArgs& a, uint32_t radix_bits, cudaStream_t st);
 uint32_t radix_bits_for(uint32_t bits);
 
 // scan.cu

@@ -314,6 +314,7 @@ struct WorkspacePlan {
   size_t keys_off[2];     // ping-pong key buffers
   size_t hist_off;        // n_pass x 256 uint64 digit counts
   size_t digoff_off;      // n_pass x 256 uint64 digit offsets
+  size_t cursor_off;      // partition pass: next output position per digit
   size_t lookback_off;    // n_tiles x 256 uint64 status words (one pass at a time)
   size_t tilectr_off;     // n_pass uint32 tile counters
   size_t long_off;        // scan: cells handed to the long-cell pass

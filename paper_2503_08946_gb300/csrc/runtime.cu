@@ -183,6 +183,8 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
   p->zero_hi = off;
   p->digoff_off = off;
   off = align256(off + (size_t)16 * kMaxRadix * 8);
+  p->cursor_off = off;
+  off = align256(off + (size_t)kMaxRadix * 8);
   p->long_cap = scan_long_capacity(n, p->scan_warps);
   p->long_off = off;   // cells handed to the long-cell pass
   off = align256(off + (size_t)p->long_cap * 8);
@@ -221,9 +223,12 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
 
 // Enqueue the sort of p.n_keys keys from buffer 0; returns the index of the
 // buffer holding the sorted keys.
+// unstable_first: the first pass may leave equal digits in any order (the
+// input order of a check's keys carries no meaning), so it runs as the
+// look-back-free partition pass.
 rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, uint64_t* buf1,
                        uint64_t spin_limit, uint32_t test_flags, cudaStream_t st, int* sorted_buf,
-                       StageTimer* tm = nullptr) {
+                       StageTimer* tm = nullptr, bool unstable_first = false) {
   uint64_t* bufs[2] = {buf0, buf1};
   auto* hist = reinterpret_cast<unsigned long long*>(ws + p.hist_off);
   auto* digoff = reinterpret_cast<unsigned long long*>(ws + p.digoff_off);
@@ -249,7 +254,14 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
     a.wait_epoch = (test_flags & RC_TEST_STALL_LOOKBACK) ? (k + 1) ^ 0x8000u : k + 1;
     a.spin_limit = spin_limit;
     a.err = &res->err;
-    s = cuda_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), st));
+    a.cursor = nullptr;
+    if (k == 0 && unstable_first && !(test_flags & RC_TEST_STALL_LOOKBACK)) {
+      a.cursor = reinterpret_cast<unsigned long long*>(ws + p.cursor_off);
+      s = cuda_status(cudaMemcpyAsync(a.cursor, a.digit_offset, ((size_t)1 << a.bits) * 8, cudaMemcpyDeviceToDevice, st));
+      if (s == RC_OK) s = cuda_status(rc::launch_partition(a, rc::radix_bits_for(a.bits), st));
+    } else {
+      s = cuda_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), st));
+    }
     if (s != RC_OK) return s;
     if (tm) tm->mark();
     cur = 1 - cur;
@@ -335,7 +347,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   if (tm) { timed->i_hist = tm->n; timed->i_pass0 = tm->n + 1; }
   s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
                    reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin,
-                   opts ? opts->test_flags : 0u, st, &sorted, tm);
+                   opts ? opts->test_flags : 0u, st, &sorted, tm, true);
   if (s != RC_OK) return s;
   if (p.n_keys > 0) {
     rc::ScanArgs sa = scan_args(m, p, ws, sorted);
@@ -501,6 +513,8 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     p.zero_hi = o;
     p.digoff_off = o;
     o = align256(o + (size_t)16 * rc::kMaxRadix * 8);
+    p.cursor_off = o;
+    o = align256(o + (size_t)rc::kMaxRadix * 8);
     p.long_cap = rc::scan_long_capacity(k.n_keys, p.scan_warps);
     p.long_off = o;
     o = align256(o + (size_t)p.long_cap * 8);
@@ -586,7 +600,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     int sorted = 0;
     s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
                      reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin, opts ? opts->test_flags : 0u, st,
-                     &sorted);
+                     &sorted, nullptr, true);
     if (s != RC_OK) break;
     rc::ScanArgs sa;
     sa.keys = reinterpret_cast<const uint64_t*>(ws + p.keys_off[sorted]);

@@ -7,9 +7,9 @@
 // radix sort for GPUs", 2022): one upfront pass counts the digits of every pass;
 // then each pass is a single kernel in which a tile of kSortTile keys
 //   (1) ranks its keys per digit, stably: per item (32 keys of a warp) the
-//       lanes sharing a digit are found with __match_any_sync, and the lowest
-//       of them reads the warp's 16-bit digit counter (the group's base rank)
-//       and adds the group size to it;
+//       lanes sharing a digit are found with one ballot per digit bit, and the
+//       lowest of them reads the warp's 16-bit digit counter (the group's base
+//       rank) and adds the group size to it;
 //   (2) publishes its per-digit counts, (3) obtains the exclusive per-digit
 //       prefix of all earlier tiles by decoupled look-back over their status
 //       words, and (4) scatters the keys, staged in shared memory in digit
@@ -39,6 +39,21 @@ __device__ __forceinline__ unsigned int lanemask_lt() {
   unsigned int m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Lanes of the warp whose digit equals this lane's (among lanes with `valid`
+// set; an invalid lane gets only itself): one ballot per digit bit, ANDed with
+// the bit's sense -- measured cheaper than __match_any_sync on this GPU.
+template <int RB>
+__device__ __forceinline__ unsigned int digit_peers(unsigned int d, bool valid) {
+  unsigned int m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < RB; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned int bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return valid ? m : (1u << (threadIdx.x & 31));
 }
 
 // ---------------------------------------------------------------------------
@@ -145,15 +160,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
     k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
   }
 
-  // (1) ranking: peer masks of all items first (independent), then one pass
-  // that turns them into ranks through the warp's counters
-  unsigned int peers[kSortItems];
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
-    if (!full_tile && wbase + (uint64_t)i * 32 + lane >= a.n) d = (unsigned int)R + lane;   // matches no one
-    peers[i] = __match_any_sync(0xffffffffu, d);
-  }
+  // (1) ranking: per item the peer mask, then the rank through the warp's counters
   unsigned short r[kSortItems];
   const unsigned int lt = lanemask_lt();
   unsigned short* my_cnt = cnt16 + w * R;
@@ -161,16 +168,17 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   for (int i = 0; i < kSortItems; ++i) {
     const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
-    const unsigned int leader = __ffs(peers[i]) - 1;
+    const unsigned int peers = digit_peers<RB>(d, valid);
+    const unsigned int leader = __ffs(peers) - 1;
     unsigned int prev = 0;
     if (lane == leader && valid) {
       // the leaders of one item hold distinct digits, so their 16-bit
       // counters are distinct and plain loads and stores suffice
       prev = my_cnt[d];
-      my_cnt[d] = (unsigned short)(prev + __popc(peers[i]));
+      my_cnt[d] = (unsigned short)(prev + __popc(peers));
     }
     prev = __shfl_sync(0xffffffffu, prev, leader);
-    r[i] = (unsigned short)(prev + __popc(peers[i] & lt));
+    r[i] = (unsigned short)(prev + __popc(peers & lt));
     __syncwarp();
   }
   __syncthreads();
@@ -272,6 +280,119 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   }
 }
 
+// ---------------------------------------------------------------------------
+// unstable partition pass (the first pass of a check's sort: its input is the
+// expansion order, which carries no meaning, so equal digits may come out in
+// any order).  Each tile ranks its keys with block-wide digit counters (the
+// lowest lane of each group adds the group size with one atomic that returns
+// the base), claims each digit's output range from a global cursor (started at
+// the digit's offset), stages the keys in digit order and scatters them.  No
+// look-back and no waiting: tiles are independent.
+// ---------------------------------------------------------------------------
+template <int RB>
+constexpr size_t partition_smem() {
+  return (size_t)kSortTile * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kSortThreads, 3) partition_kernel(SortArgs a) {
+  constexpr int R = 1 << RB;
+  constexpr int DPT = (R + kSortThreads - 1) / kSortThreads;
+  constexpr int kWarps = kSortThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kSortTile);           // [R]
+  unsigned int* excl = cnt + R;                                                       // [R]
+  unsigned long long* delta = reinterpret_cast<unsigned long long*>(excl + R);        // [R]
+  __shared__ unsigned int s_wt[kWarps];
+  const uint64_t tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned int dmask = (1u << a.bits) - 1u;
+  for (int i = threadIdx.x; i < R; i += kSortThreads) cnt[i] = 0;
+  __syncthreads();
+  const uint64_t wbase = tile * kSortTile + (uint64_t)w * (32 * kSortItems);
+  const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
+  uint64_t k[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+    k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
+  }
+  unsigned short r[kSortItems];
+  const unsigned int lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+    const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
+    const unsigned int peers = digit_peers<RB>(d, valid);
+    const unsigned int leader = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if (lane == leader && valid) base = atomicAdd(&cnt[d], (unsigned int)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    r[i] = (unsigned short)(base + __popc(peers & lt));
+  }
+  __syncthreads();
+  // per digit dg = q * kSortThreads + tid: claim the output range, tile offsets
+  unsigned int carry = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int dg = q * kSortThreads + threadIdx.x;
+    const unsigned int c = dg < R ? cnt[dg] : 0u;
+    const unsigned long long claim = c ? atomicAdd(&a.cursor[dg], (unsigned long long)c) : 0ull;
+    unsigned int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wt[w] = x;
+    __syncthreads();
+    unsigned int base = carry, tot = 0;
+    for (int i = 0; i < kWarps; ++i) {
+      if (i < w) base += s_wt[i];
+      tot += s_wt[i];
+    }
+    __syncthreads();
+    if (dg < R) {
+      const unsigned int e = base + x - c;
+      excl[dg] = e;
+      delta[dg] = claim - e;
+    }
+    carry += tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (full_tile || wbase + (uint64_t)i * 32 + lane < a.n) {
+      const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+      s_keys[excl[d] + r[i]] = k[i];
+    }
+  }
+  __syncthreads();
+  const uint64_t t0 = tile * kSortTile;
+  const int n_here = full_tile ? kSortTile : (int)(a.n - t0);
+  for (int pos = threadIdx.x; pos < n_here; pos += kSortThreads) {
+    const uint64_t key = s_keys[pos];
+    const unsigned int dd = (unsigned int)(key >> a.shift) & dmask;
+    a.keys_out[delta[dd] + (unsigned long long)pos] = key;
+  }
+}
+
+template <int RB>
+cudaError_t launch_partition_rb(const SortArgs& a, cudaStream_t st) {
+  static bool attr_set = false;
+  constexpr size_t smem = partition_smem<RB>();
+  if (!attr_set) {
+    cudaFuncSetAttribute(partition_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(partition_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    attr_set = true;
+  }
+  const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
+  partition_kernel<RB><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int RB>
 cudaError_t launch_rb(const SortArgs& a, cudaStream_t st) {
   static bool attr_set = false;
@@ -312,6 +433,17 @@ cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long l
   if (sp.n_pass == 0) return cudaSuccess;
   digit_offsets_kernel<<<sp.n_pass, 256, 0, st>>>(hist, digoff, sp);
   return cudaGetLastError();
+}
+
+cudaError_t launch_partition(const SortArgs& a, uint32_t radix_bits, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  switch (radix_bits) {
+    case 8: return launch_partition_rb<8>(a, st);
+    case 9: return launch_partition_rb<9>(a, st);
+    case 10: return launch_partition_rb<10>(a, st);
+    case 11: return launch_partition_rb<11>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t st) {

@@ -92,6 +92,7 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
     a.wait_epoch = k + 1;
     a.spin_limit = 1ull << 20;
     a.err = &res->err;
+    a.cursor = nullptr;
     st = as_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), cs));
     cur = 1 - cur;
   }
