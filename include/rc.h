@@ -49,7 +49,11 @@ extern "C" {
 typedef enum rc_status {
   RC_OK = 0,
   RC_E_INVALID = 1,       /* malformed descriptor or argument                          */
-  RC_E_KEY_OVERFLOW = 2,  /* the packed (cell, phase, block, thread, kind) exceeds 63 bits */
+  RC_E_KEY_OVERFLOW = 2,  /* the model is too wide even for chunked checks (its cells
+                             need more than 2^20 chunks), or a wide model (see
+                             rc_layout.wide) was given to a call that takes one key
+                             per instance: rc_check_batch, rc_tune, rc_expand_keys,
+                             the hash path                                            */
   RC_E_OOB = 3,           /* an index outside its extent, or a phase outside [0, n_phases) */
   RC_E_NOMEM = 4,         /* workspace smaller than rc_workspace_size(), or host/device allocation failed */
   RC_E_TIMEOUT = 5,       /* a bounded device wait expired (the result is not valid)   */
@@ -196,7 +200,10 @@ typedef struct rc_layout {
   uint64_t n_blocks;
   uint64_t program_bytes;    /* bytes of the lowered program uploaded by rc_model_create */
   uint32_t expand_jit;       /* 1 = the expansion runs a kernel generated for this model   */
-  uint32_t reserved;
+  uint32_t wide;             /* 1 = [cell | phase | block | thread | kind] needs more than
+                                63 bits: rc_check runs the model in cell-range chunks
+                                (RC_OPT_CHUNKED) whose cells are rebased to the chunk
+                                start; cell_bits is then the rebased field's width     */
   uint64_t array_base[64];   /* first linear cell of each array (first 64 arrays) */
   uint64_t array_cells[64];  /* cells of one scope instance of each array         */
 } rc_layout;
@@ -237,13 +244,25 @@ typedef struct rc_check_opts {
 enum { RC_TEST_STALL_LOOKBACK = 1,
        RC_TEST_FEW_SCAN_WARPS = 2   /* scan with 3 warps (long ranges per warp) */ };
 /* RC_OPT_STAGE_TIMES: record CUDA events between the stages of rc_check on its
- * stream so rc_ticket_stage_times can report per-stage device times.
+ * stream so rc_ticket_stage_times can report per-stage device times (not for
+ * chunked checks).
+ * RC_OPT_CHUNKED (rc_check; implied for wide models): a count pass expands the
+ * model and histograms its keys by cell; rc_check then waits for it (one host
+ * synchronisation on `stream`), cuts the checked cell range into chunks whose
+ * keys fit the given workspace and whose rebased cells fit the key, and
+ * enqueues one expansion (keeping and compacting only the chunk's keys), sort,
+ * scan and witness per chunk.  The report merges the chunks: racy cells add
+ * up, the witness is the first racy chunk's (chunks are in cell order).  Any
+ * workspace that holds the keys of the fullest bucket of cells works
+ * (RC_E_NOMEM otherwise); rc_workspace_size gives the size for one chunk of all
+ * keys.  The sort path only (RC_PATH_HASH: RC_E_INVALID, wide: RC_E_KEY_OVERFLOW);
+ * the expansion runs the interpreted kernels.
  * RC_OPT_GRAPH (rc_check_batch): the device work of a batch is captured once
  * as a CUDA graph per (models, options, workspace) and relaunched as that one
  * graph on later calls with the same arguments; rc_model_destroy drops the
  * captured graphs.  Not a library convenience of the paper: the paper has no
  * batching. */
-enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2 };
+enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2, RC_OPT_CHUNKED = 4 };
 
 typedef struct rc_inst {
   uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
@@ -274,15 +293,19 @@ typedef struct rc_result {
 
 typedef struct rc_ticket_s* rc_ticket;   /* opaque handle of an enqueued check */
 
-/* Bytes of device workspace rc_check needs for this model and options.
- * Errors: RC_E_INVALID. */
+/* Bytes of device workspace rc_check needs for this model and options (for a
+ * chunked check: the size that holds all keys in one chunk; smaller ones work,
+ * see RC_OPT_CHUNKED).  Errors: RC_E_INVALID, RC_E_KEY_OVERFLOW. */
 rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes);
 
 /* Enqueue one check on `stream`.  `workspace_dev` (>= rc_workspace_size bytes,
  * 256-byte aligned, caller-owned) is scratch for the keys, histograms and
  * look-back state; it may be reused by the next check on the same stream.
  * opts may be NULL (defaults).  *ticket receives a handle for rc_report.
- * Errors: RC_E_INVALID, RC_E_NOMEM (workspace too small), RC_E_CUDA. */
+ * A chunked check (RC_OPT_CHUNKED, wide models) blocks until its count pass
+ * is done, then enqueues the chunks and returns.
+ * Errors: RC_E_INVALID, RC_E_NOMEM (workspace too small), RC_E_KEY_OVERFLOW,
+ * RC_E_CUDA. */
 rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace_dev,
                    size_t workspace_bytes, void* stream, rc_ticket* ticket);
 

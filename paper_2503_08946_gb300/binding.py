@@ -40,6 +40,7 @@ RC_TEST_STALL_LOOKBACK = 1
 RC_TEST_FEW_SCAN_WARPS = 2
 RC_OPT_STAGE_TIMES = 1
 RC_OPT_GRAPH = 2
+RC_OPT_CHUNKED = 4
 
 # every entry point declared in include/rc.h
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
@@ -111,7 +112,7 @@ class rc_layout(Structure):
                 ("cell_bits", c_uint32), ("sort_lo", c_uint32), ("sort_hi", c_uint32),
                 ("key_slots", c_uint64), ("total_cells", c_uint64), ("n_arrays", c_uint32),
                 ("n_threads_per_block", c_uint32), ("n_blocks", c_uint64),
-                ("program_bytes", c_uint64), ("expand_jit", c_uint32), ("reserved", c_uint32), ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
+                ("program_bytes", c_uint64), ("expand_jit", c_uint32), ("wide", c_uint32), ("array_base", c_uint64 * 64), ("array_cells", c_uint64 * 64)]
 
 
 class rc_check_opts(Structure):

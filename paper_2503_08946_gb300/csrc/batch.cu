@@ -35,7 +35,7 @@ struct BatchSink {
   uint32_t mcs, mps, mbs;            // model field shifts (thread field at bit 1)
   uint64_t pm, bm, tm;               // model field masks
   uint32_t bcs, bps, bbs;            // batch field shifts
-  __device__ __forceinline__ void put(uint64_t i, uint64_t key) {
+  __device__ __forceinline__ void put(uint64_t i, uint64_t key, uint64_t) {
     if (key != kSentinel) {
       const uint64_t cell = key >> mcs;
       const uint64_t ph = (key >> mps) & pm, b = (key >> mbs) & bm, t = (key >> 1) & tm;

@@ -108,9 +108,12 @@ __device__ __forceinline__ bool guards_hold(const DevModel& M, const DevStmt& S,
 
 // The key of access `a` of statement `s` at this point, or kSentinel when the
 // instance is out of bounds (the smallest offending code is folded into *oob).
+// The key of one access instance (kSentinel if it is out of bounds); *cell_out
+// receives its linear cell (all ones if out of bounds), which the key's cell
+// field may not hold whole when the model is wider than one key.
 __device__ __forceinline__ uint64_t make_key(const DevModel& M, const DevStmt& S, uint32_t s, int a,
                                              int64_t phase, const ThreadVars& tv, const int64_t* it,
-                                             const int64_t* term, unsigned long long* oob) {
+                                             const int64_t* term, unsigned long long* oob, uint64_t* cell_out) {
   const DevAccess A = M.accs[S.acc0 + a];
   const DevArray& arr = M.arrays[A.array];
   bool bad = false;
@@ -127,8 +130,10 @@ __device__ __forceinline__ uint64_t make_key(const DevModel& M, const DevStmt& S
     }
     e = e * (uint64_t)arr.ext[d] + (uint64_t)v;
   }
+  *cell_out = ~0ull;
   if (bad) return kSentinel;
   const uint64_t cell = arr.base + (arr.shared ? tv.b : 0ull) * arr.cells + e;
+  *cell_out = cell;
   return (cell << M.cell_shift) | ((uint64_t)phase << M.phase_shift) | (tv.b << M.block_shift) |
          ((uint64_t)tv.t << M.thread_shift) | (uint64_t)A.kind;
 }

@@ -8,12 +8,15 @@
 // instances leave the all-ones padding key.  Other statements are first counted
 // per unit (expand_count_kernel, run once when the model is created), and then
 // write their keys contiguously at the scanned unit offsets.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "expand_core.cuh"
 #include "kernels.h"
 
 namespace rc {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -22,20 +25,62 @@ namespace {
 // of a cell range).
 struct SlotSink {
   uint64_t* keys;
-  uint32_t cell_shift;
   uint64_t cell_lo, cell_hi;
-  __device__ __forceinline__ void put(uint64_t i, uint64_t key) {
-    const uint64_t c = key >> cell_shift;
-    keys[i] = (c >= cell_lo && c < cell_hi) ? key : kSentinel;
+  __device__ __forceinline__ void put(uint64_t i, uint64_t key, uint64_t cell) {
+    keys[i] = (cell >= cell_lo && cell < cell_hi) ? key : kSentinel;
   }
   __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
 };
 
+// Count pass of a chunked check: keys per bucket of 2^bshift cells of the
+// range [lo, lo + span).  The lanes that reach the add together and share the
+// bucket add once.
+struct CountSink {
+  unsigned long long* counts;
+  uint64_t lo, span;
+  uint32_t bshift;
+  __device__ __forceinline__ void put(uint64_t, uint64_t key, uint64_t cell) {
+    if (key == kSentinel || cell - lo >= span) return;
+    const uint64_t bucket = (cell - lo) >> bshift;
+    cg::coalesced_group g = cg::coalesced_threads();
+    const uint64_t b0 = g.shfl(bucket, 0);
+    if (g.all(bucket == b0)) {
+      if (g.thread_rank() == 0) atomicAdd(counts + b0, (unsigned long long)g.size());
+    } else {
+      atomicAdd(counts + bucket, 1ull);
+    }
+  }
+  __device__ __forceinline__ void pad(uint64_t) {}
+};
+
+// Key pass of a chunked check: the keys of cells in [lo, lo + span) are
+// appended (in no particular order) with their cell field rebased to cell - lo,
+// which fits the field even when the model's cells do not.  The lanes that
+// append together reserve their positions with one atomic add; a position at or
+// past `cap` is not written and flags kErrChunkOverflow.
+struct CompactSink {
+  uint64_t* keys;
+  unsigned long long* count;
+  uint64_t cap, lo, span, low_mask;
+  uint32_t cell_shift;
+  unsigned int* err;
+  __device__ __forceinline__ void put(uint64_t, uint64_t key, uint64_t cell) {
+    if (key == kSentinel || cell - lo >= span) return;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(count, (unsigned long long)g.size());
+    const unsigned long long pos = g.shfl(base, 0) + g.thread_rank();
+    if (pos < cap) keys[pos] = ((cell - lo) << cell_shift) | (key & low_mask);
+    else atomicOr(err, (unsigned int)kErrChunkOverflow);
+  }
+  __device__ __forceinline__ void pad(uint64_t) {}
+};
+
 // grid: (ceil(T / kExpandThreads), n_stmts); one statement per grid row.
 // Statements with at most kFastLoops loops.
-__global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevModel* __restrict__ Mp,
-                                                                uint64_t* __restrict__ keys, DevResult* res,
-                                                                uint64_t cell_lo, uint64_t cell_hi) {
+template <class Sink>
+__global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevModel* __restrict__ Mp, DevResult* res,
+                                                                Sink sink) {
   __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
   __shared__ int64_t s_cache[kFastCache * kExpandThreads];
   const DevModel& M = *Mp;
@@ -51,7 +96,6 @@ __global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevMode
     c.tv = thread_vars(M, g);
     c.tval = s_tval + threadIdx.x;
     c.cache = s_cache + threadIdx.x;
-    SlotSink sink{keys, M.cell_shift, cell_lo, cell_hi};
     expand_unit_dispatch(c, s, g, res, count, sink);
   }
   count = warp_sum(count);
@@ -59,18 +103,32 @@ __global__ void __launch_bounds__(kExpandThreads, 4) expand_kernel(const DevMode
 }
 
 // Statements with more than kFastLoops loops: interpreted nest.
+template <class Sink>
 __global__ void __launch_bounds__(kExpandThreads) expand_generic_kernel(const DevModel* __restrict__ Mp,
-                                                                        uint64_t* __restrict__ keys, DevResult* res,
-                                                                        uint64_t cell_lo, uint64_t cell_hi) {
+                                                                        DevResult* res, Sink sink) {
   const DevModel& M = *Mp;
   const uint32_t s = blockIdx.y;
   if (M.stmts[s].n_loops <= kFastLoops) return;
   const uint64_t g = (uint64_t)blockIdx.x * kExpandThreads + threadIdx.x;
   unsigned long long count = 0;
-  SlotSink sink{keys, M.cell_shift, cell_lo, cell_hi};
   if (g < M.n_threads) expand_unit_generic(M, s, g, res, count, sink);
   count = warp_sum(count);
   if ((threadIdx.x & 31) == 0 && count) atomicAdd(&res->instances, count);
+}
+
+template <class Sink>
+cudaError_t launch_expand_sink(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                               DevResult* res, const Sink& sink, cudaStream_t st) {
+  if (n_stmts == 0 || n_threads == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n_threads + kExpandThreads - 1) / kExpandThreads), n_stmts);
+  expand_kernel<Sink><<<grid, kExpandThreads, 0, st>>>(dm, res, sink);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (has_deep) {
+    expand_generic_kernel<Sink><<<grid, kExpandThreads, 0, st>>>(dm, res, sink);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 // Keys per (statement, thread) unit of the statements with thread-dependent trip
@@ -180,16 +238,20 @@ int grid_for(uint64_t n_units) {
 
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
                           DevResult* res, cudaStream_t st, uint64_t cell_lo, uint64_t cell_hi) {
-  if (n_stmts == 0 || n_threads == 0) return cudaSuccess;
-  const dim3 grid((unsigned)((n_threads + kExpandThreads - 1) / kExpandThreads), n_stmts);
-  expand_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res, cell_lo, cell_hi);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (has_deep) {
-    expand_generic_kernel<<<grid, kExpandThreads, 0, st>>>(dm, keys, res, cell_lo, cell_hi);
-    e = cudaGetLastError();
-  }
-  return e;
+  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, SlotSink{keys, cell_lo, cell_hi}, st);
+}
+
+cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                DevResult* res, unsigned long long* counts, uint64_t lo, uint64_t span,
+                                uint32_t bshift, cudaStream_t st) {
+  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, CountSink{counts, lo, span, bshift}, st);
+}
+
+cudaError_t launch_expand_compact(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                  uint32_t cell_shift, uint64_t* keys, unsigned long long* count, uint64_t cap,
+                                  uint64_t lo, uint64_t span, DevResult* res, cudaStream_t st) {
+  CompactSink k{keys, count, cap, lo, span, (1ull << cell_shift) - 1ull, cell_shift, &res->err};
+  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, k, st);
 }
 
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st) {

@@ -97,7 +97,8 @@ __device__ __forceinline__ void nest(const FastCtx& c, int64_t (&it)[LA], Body& 
 }
 
 // One statement instance point: guards, phase, and one key per access, each
-// handed to sink(a, key) (key = kSentinel for an out-of-bounds instance).
+// handed to sink(a, key, cell) (key = kSentinel and cell = all ones for an
+// out-of-bounds instance).
 template <int L, class Sink>
 __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const int64_t (&it)[L], uint64_t low,
                                            unsigned long long* oob, Sink& sink) {
@@ -125,21 +126,21 @@ __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const i
     }
     const int kidx = __ldg(&A->key_idx);
     if (kidx < 0) continue;   // array never written: bounds-checked and counted, no key
-    uint64_t key = kSentinel;
+    uint64_t key = kSentinel, cell = ~0ull;
     if (!bad) {
-      const uint64_t cell = __ldg(&arr->base) + (__ldg(&arr->shared) ? c.tv.b : 0ull) * __ldg(&arr->cells) + e;
+      cell = __ldg(&arr->base) + (__ldg(&arr->shared) ? c.tv.b : 0ull) * __ldg(&arr->cells) + e;
       key = (cell << M.cell_shift) | ((uint64_t)phase << M.phase_shift) | low | (uint64_t)kind;
     }
-    sink(kidx, key);
+    sink(kidx, key, cell);
   }
   return true;
 }
 
-// Expansion of one (statement, thread) unit with loop depth L.  KeySink:
-//   point(key_index_of_point, a, key)  -- a guard-true point
-//   skip(key_index_of_point)           -- a guard-false point
-// where key_index_of_point is the dense slot (dense statements) or the running
-// offset (others); the sink decides where keys go.
+// Expansion of one (statement, thread) unit with loop depth L.  Sink:
+//   put(slot, key, cell)  -- one access instance of a guard-true point
+//   pad(slot)             -- a key slot of a guard-false point (dense statements)
+// where slot is the dense slot (dense statements) or the running offset
+// (others); the sink decides where keys go.
 template <int L, class Sink>
 __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevResult* res,
                                  unsigned long long& count, Sink& sink) {
@@ -169,7 +170,7 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
     uint64_t slot = S.slot_base + g;
     const uint64_t step_pt = (uint64_t)S.n_key * T;
     auto body = [&](const int64_t (&itv)[LA]) {
-      auto put = [&](int kidx, uint64_t key) { sink.put(slot + (uint64_t)kidx * T, key); };
+      auto put = [&](int kidx, uint64_t key, uint64_t cell) { sink.put(slot + (uint64_t)kidx * T, key, cell); };
       if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
         count += (unsigned long long)S.n_acc;
       } else {
@@ -181,7 +182,7 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
   } else {
     uint64_t off = M.unit_offset[S.slot_base + g];
     auto body = [&](const int64_t (&itv)[LA]) {
-      auto put = [&](int kidx, uint64_t key) { sink.put(off + (uint64_t)kidx, key); };
+      auto put = [&](int kidx, uint64_t key, uint64_t cell) { sink.put(off + (uint64_t)kidx, key, cell); };
       if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
         off += (uint64_t)S.n_key;
         count += (unsigned long long)S.n_acc;
@@ -218,9 +219,10 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
       if (guards_hold(M, S, tv, it, term)) {
         const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
         for (int a = 0; a < S.n_acc; ++a) {
-          const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+          uint64_t cell;
+          const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code, &cell);
           const int kidx = M.accs[S.acc0 + a].key_idx;
-          if (kidx >= 0) sink.put(slot + (uint64_t)kidx * T, key);
+          if (kidx >= 0) sink.put(slot + (uint64_t)kidx * T, key, cell);
         }
         count += (unsigned long long)S.n_acc;
       } else {
@@ -234,9 +236,10 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
       if (!guards_hold(M, S, tv, it, term)) return;
       const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
       for (int a = 0; a < S.n_acc; ++a) {
-        const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code);
+        uint64_t cell;
+        const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code, &cell);
         const int kidx = M.accs[S.acc0 + a].key_idx;
-        if (kidx >= 0) sink.put(off + (uint64_t)kidx, key);
+        if (kidx >= 0) sink.put(off + (uint64_t)kidx, key, cell);
       }
       off += (uint64_t)S.n_key;
       count += (unsigned long long)S.n_acc;

@@ -70,10 +70,9 @@ __device__ __forceinline__ bool word_update(unsigned long long* word, uint64_t i
 struct HashSink {
   const DevModel* M;
   HashArgs h;
-  __device__ __forceinline__ void put(uint64_t, uint64_t key) {
+  __device__ __forceinline__ void put(uint64_t, uint64_t key, uint64_t cell) {
     if (key == kSentinel) return;
     const DevModel& m = *M;
-    const uint64_t cell = key >> m.cell_shift;
     if (cell < h.cell_lo || cell >= h.cell_hi) return;
     const uint64_t cp = key >> m.phase_shift;
     const uint64_t b = (key >> m.block_shift) & ((1ull << m.block_bits) - 1ull);
@@ -103,8 +102,8 @@ struct FilterSink {
   uint64_t target;
   uint64_t* out;
   unsigned long long* n_out;
-  __device__ __forceinline__ void put(uint64_t, uint64_t key) {
-    if (key == kSentinel || (key >> M->cell_shift) != target) return;
+  __device__ __forceinline__ void put(uint64_t, uint64_t key, uint64_t cell) {
+    if (key == kSentinel || cell != target) return;
     const unsigned long long i = atomicAdd(n_out, 1ull);
     out[i] = key;
   }

@@ -283,6 +283,7 @@ bool jit_expand_build(Model* m) {
   if (env && env[0] == '0') return false;
   const bool force = env && env[0] == '1';
   if (!force && m->key_slots < kJitMinKeys) return false;
+  if (m->wide) return false;   // chunked checks run the interpreted count and compact passes
   if (m->host.n_stmts == 0 || m->host.n_threads == 0) return false;
   std::lock_guard<std::mutex> lk(g_jit_mu);
   Nvrtc& nv = nvrtc();

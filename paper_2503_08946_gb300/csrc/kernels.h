@@ -12,6 +12,16 @@ namespace rc {
 // keys whose cell lies outside [cell_lo, cell_hi) are written as padding
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
                           DevResult* res, cudaStream_t st, uint64_t cell_lo = 0, uint64_t cell_hi = ~0ull);
+// Count pass of a chunked check: counts[(cell - lo) >> bshift] += keys of the
+// cells in [lo, lo + span) (instances and out-of-bounds reports go to res).
+cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                DevResult* res, unsigned long long* counts, uint64_t lo, uint64_t span,
+                                uint32_t bshift, cudaStream_t st);
+// Key pass of a chunked check: the keys of cells in [lo, lo + span), cell field
+// rebased to cell - lo, appended at keys[*count++] (at most cap).
+cudaError_t launch_expand_compact(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                  uint32_t cell_shift, uint64_t* keys, unsigned long long* count, uint64_t cap,
+                                  uint64_t lo, uint64_t span, DevResult* res, cudaStream_t st);
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st);
 size_t scan_u64_temp_bytes(uint64_t n);
 cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,

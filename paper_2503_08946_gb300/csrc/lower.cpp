@@ -289,7 +289,13 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.cell_shift = h.phase_shift + h.phase_bits;
   // one more value than the cells so the all-ones cell field is never a valid cell
   h.cell_bits = bit_length(cells_total);
-  if (h.cell_shift + h.cell_bits > (uint32_t)kKeyBits) return RC_E_KEY_OVERFLOW;
+  m->wide = h.cell_shift + h.cell_bits > (uint32_t)kKeyBits;
+  if (m->wide) {
+    // checked in cell-range chunks; each chunk's cells are rebased to fit the
+    // field left beside the other fields (at least 2 bits: one cell per chunk)
+    if (h.cell_shift + 2 > (uint32_t)kKeyBits) return RC_E_KEY_OVERFLOW;
+    h.cell_bits = (uint32_t)kKeyBits - h.cell_shift;
+  }
   h.sort_lo = h.phase_bits <= kScanTablePhaseBits ? h.cell_shift : h.phase_shift;
   h.sort_hi = h.cell_shift + h.cell_bits;
 

@@ -170,6 +170,7 @@ enum DevError : unsigned int {
   kErrHashTimeout = 2u,
   kErrHashFull = 4u,
   kErrScanLongFull = 8u,
+  kErrChunkOverflow = 16u,   // a chunk produced more keys than its count pass planned
 };
 
 // packed out-of-bounds code: stmt (12 bits) | access (6) | gtid (42) | dimcode (3)
@@ -344,6 +345,10 @@ struct Model {
   std::vector<uint32_t> array_shared;
   uint32_t n_general_stmts = 0;
   bool has_deep_loops = false;    // some statement has more than kFastLoops loops
+  // the packed key [cell | phase | block | thread | kind] needs more than
+  // kKeyBits: checks run in cell-range chunks whose rebased cell field has
+  // host.cell_bits bits (the width left beside the other fields)
+  bool wide = false;
   // sections of the program image (byte offsets), for the kernel generator
   size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null
@@ -360,6 +365,8 @@ cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cu
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);
 void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p);
+// the sort-path plan for n keys whose cell field has cell_bits bits
+void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits, WorkspacePlan* p);
 void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp);
 uint32_t bit_length(uint64_t v);
 

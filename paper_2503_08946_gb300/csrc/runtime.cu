@@ -55,6 +55,10 @@ struct rc_ticket_s {
   std::vector<uint32_t> field_bits;   // thread_bits | phase_bits << 8
   void* upload = nullptr;             // pinned staging of the batch tables
   size_t upload_cap = 0;
+  // chunked check: host[0] is the count pass, host[1 + k] chunk k, whose
+  // cells start at chunk_lo[k]; the report merges them into one result
+  bool chunked = false;
+  std::vector<uint64_t> chunk_lo;
 };
 
 namespace {
@@ -74,6 +78,8 @@ rc_ticket_s* ticket_get(size_t n) {
         t->enqueue_status = RC_OK;
         t->cell_base.clear();
         t->field_bits.clear();
+        t->chunked = false;
+        t->chunk_lo.clear();
         t->timed = false;
         t->timer.n = 0;
         t->timer.ok = true;
@@ -161,7 +167,15 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
     p->total = off;
     return;
   }
-  plan_sort(m.host.sort_lo, m.host.sort_hi, opts ? opts->digit_bits : 0, &p->sort);
+  plan_workspace_keys(m, opts, n, m.host.cell_bits, p);
+}
+
+void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits,
+                         WorkspacePlan* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n_keys = n;
+  const uint32_t hi = m.host.cell_shift + cell_bits;
+  plan_sort(m.host.sort_lo < hi ? m.host.sort_lo : hi, hi, opts ? opts->digit_bits : 0, &p->sort);
   p->n_tiles = (n + kSortTile - 1) / kSortTile;
   p->scan_warps = scan_warps_for(n);
   size_t off = 0;
@@ -416,6 +430,200 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
   out->y.phase = (int64_t)((r.y_rank >> (tb + 1)) & pmask);
   out->y.block = r.y_rank >> (pb + tb + 1);
   out->y.gtid = out->y.block * bs + out->y.thread;
+}
+
+// ---------------------------------------------------------------------------
+// chunked check: models wider than one key, and checks in a bounded workspace
+// ---------------------------------------------------------------------------
+// A count pass expands the whole model (all instances are counted and
+// bounds-checked) and histograms its keys over buckets of 2^bshift cells of the
+// checked range.  The host then cuts the range into chunks of whole buckets,
+// each with at most `cap` keys (what the workspace holds) and a cell span that
+// fits the key's cell field; each chunk expands the model again, keeping (and
+// compacting) only its own keys with their cells rebased to the chunk start,
+// and runs the ordinary sort, scan and witness stages on them.  A cell races or
+// not on its own, so the chunk counts add up and the smallest racing pair is
+// the one of the first chunk with a race.
+constexpr uint64_t kMaxChunkBuckets = 1ull << 20;
+constexpr size_t kMaxChunks = 1u << 16;
+
+struct ChunkGeometry {
+  uint64_t lo = 0, span = 0;   // checked cell range [lo, lo + span)
+  uint32_t bshift = 0;         // bucket = (cell - lo) >> bshift
+  uint64_t n_buckets = 0;
+  uint64_t max_span = 0;       // cells one chunk may span
+  size_t counts_off = 0, ctr_off = 0, region_off = 0;
+};
+
+rc_status chunk_geometry(const rc::Model& m, const rc_check_opts* opts, ChunkGeometry* g) {
+  uint64_t lo = opts ? opts->cell_lo : 0;
+  uint64_t hi = (opts && opts->cell_hi) ? opts->cell_hi : m.total_cells;
+  if (hi > m.total_cells) hi = m.total_cells;
+  if (lo > hi) lo = hi;
+  g->lo = lo;
+  g->span = hi - lo;
+  const uint32_t cb = m.host.cell_bits;
+  g->max_span = cb >= 63 ? (1ull << 62) : (1ull << cb) - 1ull;
+  uint32_t bs = 0;
+  while (bs < 63 && ((g->span + (1ull << bs) - 1) >> bs) > kMaxChunkBuckets) ++bs;
+  if (bs > 0 && (1ull << bs) > g->max_span) return RC_E_KEY_OVERFLOW;   // would need too many chunks
+  g->bshift = bs;
+  g->n_buckets = g->span ? ((g->span - 1) >> bs) + 1 : 0;
+  g->ctr_off = 0;
+  g->counts_off = 256;
+  g->region_off = align256(g->counts_off + (size_t)(g->n_buckets ? g->n_buckets : 1) * 8);
+  return RC_OK;
+}
+
+// keys one chunk's region can hold in `bytes`
+uint64_t chunk_capacity(const rc::Model& m, const rc_check_opts* opts, size_t bytes, uint64_t upper) {
+  rc::WorkspacePlan p;
+  uint64_t lo = 0, hi = upper;
+  rc::plan_workspace_keys(m, opts, 0, m.host.cell_bits, &p);
+  if (p.total > bytes) return ~0ull;   // not even the fixed part fits
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo + 1) / 2;
+    rc::plan_workspace_keys(m, opts, mid, m.host.cell_bits, &p);
+    if (p.total <= bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+size_t chunked_workspace_size(const rc::Model& m, const rc_check_opts* opts) {
+  ChunkGeometry g;
+  if (chunk_geometry(m, opts, &g) != RC_OK) return 0;
+  rc::WorkspacePlan p;
+  rc::plan_workspace_keys(m, opts, m.key_slots, m.host.cell_bits, &p);
+  return g.region_off + p.total;
+}
+
+bool use_chunked(const rc::Model& m, const rc_check_opts* opts) {
+  return m.wide || (opts && (opts->flags & RC_OPT_CHUNKED));
+}
+
+// Count pass, planning (one host synchronisation) and the enqueued chunks.
+rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
+                          cudaStream_t st, rc_ticket_s** out) {
+  const rc::Model& m = model->m;
+  *out = nullptr;
+  if (opts && opts->path == RC_PATH_HASH) return m.wide ? RC_E_KEY_OVERFLOW : RC_E_INVALID;
+  if (!ws) return RC_E_NOMEM;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return RC_E_INVALID;
+  ChunkGeometry g;
+  rc_status s = chunk_geometry(m, opts, &g);
+  if (s != RC_OK) return s;
+  if (ws_bytes <= g.region_off) return RC_E_NOMEM;
+  const uint64_t cap = chunk_capacity(m, opts, ws_bytes - g.region_off, m.key_slots);
+  if (cap == ~0ull) return RC_E_NOMEM;
+  uint8_t* region = ws + g.region_off;
+  auto* counts = reinterpret_cast<unsigned long long*>(ws + g.counts_off);
+  auto* ctr = reinterpret_cast<unsigned long long*>(ws + g.ctr_off);
+  const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
+  rc::WorkspacePlan p0;
+  rc::plan_workspace_keys(m, opts, 0, m.host.cell_bits, &p0);
+  auto* res = reinterpret_cast<rc::DevResult*>(region + p0.result_off);
+
+  // count pass
+  rc::DevResult r0;
+  std::vector<unsigned long long> hc(g.n_buckets);
+  s = cuda_status(rc::launch_init_result(res, st));
+  if (s == RC_OK && g.n_buckets) s = cuda_status(cudaMemsetAsync(counts, 0, g.n_buckets * 8, st));
+  if (s == RC_OK)
+    s = cuda_status(rc::launch_expand_count(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops, res, counts,
+                                            g.lo, g.span, g.bshift, st));
+  if (s == RC_OK) s = cuda_status(cudaMemcpyAsync(&r0, res, sizeof(r0), cudaMemcpyDeviceToHost, st));
+  if (s == RC_OK && g.n_buckets)
+    s = cuda_status(cudaMemcpyAsync(hc.data(), counts, g.n_buckets * 8, cudaMemcpyDeviceToHost, st));
+  if (s == RC_OK) s = cuda_status(cudaStreamSynchronize(st));
+  if (s != RC_OK) return s;
+
+  // chunks of whole buckets: at most `cap` keys and `max_span` cells each
+  struct Chunk { uint64_t lo, span, n; };
+  std::vector<Chunk> chunks;
+  if (r0.oob_code == ~0ull && r0.err == 0) {
+    const uint64_t per = g.max_span >> g.bshift;   // buckets one chunk may span (>= 1)
+    uint64_t i = 0;
+    while (i < g.n_buckets) {
+      if (hc[i] == 0) { ++i; continue; }
+      if (hc[i] > cap) return RC_E_NOMEM;   // one bucket's keys do not fit the workspace
+      const uint64_t start = i;
+      uint64_t n = 0;
+      while (i < g.n_buckets && i - start < per && n + hc[i] <= cap) n += hc[i++];
+      const uint64_t clo = g.lo + (start << g.bshift);
+      const uint64_t cend = std::min(g.lo + (i << g.bshift), g.lo + g.span);
+      chunks.push_back(Chunk{clo, cend - clo, n});
+      if (chunks.size() > kMaxChunks) return RC_E_NOMEM;
+    }
+  }
+  rc_ticket_s* t = ticket_get(chunks.size() + 1);
+  if (!t) return RC_E_NOMEM;
+  t->models.assign(chunks.size() + 1, model);
+  t->chunked = true;
+  t->host[0] = r0;
+  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
+  for (size_t k = 0; k < chunks.size() && s == RC_OK; ++k) {
+    const Chunk& c = chunks[k];
+    t->chunk_lo.push_back(c.lo);
+    rc::WorkspacePlan p;
+    rc::plan_workspace_keys(m, opts, c.n, std::max<uint32_t>(1u, rc::bit_length(c.span - 1)), &p);
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(region + p.keys_off[0]);
+    uint64_t* k1 = reinterpret_cast<uint64_t*>(region + p.keys_off[1]);
+    s = cuda_status(cudaMemsetAsync(region + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
+    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(ctr, 0, 8, st));
+    if (s == RC_OK) s = cuda_status(rc::launch_init_result(res, st));
+    if (s == RC_OK)
+      s = cuda_status(rc::launch_expand_compact(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
+                                                m.host.cell_shift, k0, ctr, c.n, c.lo, c.span, res, st));
+    int sorted = 0;
+    if (s == RC_OK) s = enqueue_sort(p, region, k0, k1, spin, opts ? opts->test_flags : 0u, st, &sorted, nullptr, true);
+    if (s == RC_OK && c.n > 0) {
+      rc::ScanArgs sa = scan_args(m, p, region, sorted);
+      s = cuda_status(rc::launch_scan(sa, st));
+      if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
+    }
+    if (s == RC_OK)
+      s = cuda_status(cudaMemcpyAsync(t->host + 1 + k, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+  }
+  if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
+  if (s != RC_OK) {
+    ticket_put(t);
+    return s;
+  }
+  *out = t;
+  return RC_OK;
+}
+
+// Merge of a chunked ticket's records into one result.
+void decode_chunked(const rc_ticket_s* t, rc_result* out) {
+  const rc::Model& m = t->models[0]->m;
+  decode_result(t->host[0], m, out, 0, m.host.thread_bits, m.host.phase_bits);
+  if (out->status != RC_OK) return;
+  const uint64_t instances = out->instances;
+  out->racy_cells = 0;
+  out->verdict = 0;
+  bool have_witness = false;
+  for (size_t k = 0; k + 1 < t->n; ++k) {
+    rc_result part;
+    // cell_base = -chunk start: the scan's cells are relative to the chunk
+    decode_result(t->host[1 + k], m, &part, (uint64_t)0 - t->chunk_lo[k], m.host.thread_bits, m.host.phase_bits);
+    if (t->host[1 + k].err & rc::kErrChunkOverflow) part.status = RC_E_NOMEM;
+    if (part.status != RC_OK) {
+      std::memset(out, 0, sizeof(*out));
+      out->status = part.status;
+      out->instances = instances;
+      return;
+    }
+    out->racy_cells += part.racy_cells;
+    if (part.verdict && !have_witness) {
+      const uint64_t racy = out->racy_cells;
+      *out = part;
+      out->racy_cells = racy;
+      have_witness = true;
+    }
+  }
+  out->instances = instances;
+  out->verdict = out->racy_cells > 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -956,6 +1164,7 @@ rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
   out->n_blocks = m.host.n_blocks;
   out->program_bytes = m.dev_bytes;
   out->expand_jit = m.jit_fn ? 1u : 0u;
+  out->wide = m.wide ? 1u : 0u;
   for (size_t a = 0; a < m.array_base.size() && a < 64; ++a) {
     out->array_base[a] = m.array_base[a];
     out->array_cells[a] = m.array_cells[a];
@@ -983,6 +1192,13 @@ rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t
   if (!m || !bytes) return RC_E_INVALID;
   rc_model* mm = const_cast<rc_model*>(m);
   const rc_check_opts o = resolve_opts(&mm, 1, opts);
+  if (use_chunked(m->m, &o)) {
+    ChunkGeometry g;
+    const rc_status s = chunk_geometry(m->m, &o, &g);
+    if (s != RC_OK) return s;
+    *bytes = chunked_workspace_size(m->m, &o);
+    return RC_OK;
+  }
   rc::WorkspacePlan p;
   rc::plan_workspace(m->m, &o, &p);
   *bytes = p.total;
@@ -993,11 +1209,15 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
                    rc_ticket* ticket) {
   if (!m || !ticket) return RC_E_INVALID;
   *ticket = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc_check_opts o = resolve_opts(&m, 1, opts);
+  if (use_chunked(m->m, &o)) {
+    if (!opts || opts->path != RC_PATH_HASH) o.path = RC_PATH_SORT;   // chunks take the sort path
+    return enqueue_chunked(m, &o, static_cast<uint8_t*>(workspace), ws_bytes, st, ticket);
+  }
   rc_ticket_s* t = ticket_get(1);
   if (!t) return RC_E_NOMEM;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool want_times = opts && (opts->flags & RC_OPT_STAGE_TIMES);
-  rc_check_opts o = resolve_opts(&m, 1, opts);
   if (opts && opts->path == RC_PATH_AUTO) {
     // a tuned choice that needs more workspace than given falls back to the sort path
     size_t need = 0;
@@ -1027,8 +1247,10 @@ bool batch_is_sequential(const rc_check_opts* opts) { return opts && opts->path 
 
 rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_check_opts* opts_in, size_t* bytes) {
   if (!bytes || (n && !models)) return RC_E_INVALID;
-  for (size_t i = 0; i < n; ++i)
+  for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
+    if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
+  }
   const rc_check_opts ro = resolve_opts(models, n, opts_in);
   const rc_check_opts* opts = &ro;
   if (batch_is_sequential(opts)) {
@@ -1052,8 +1274,10 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
                          size_t ws_bytes, void* stream, rc_ticket* ticket) {
   if (!ticket || (n && !models)) return RC_E_INVALID;
   *ticket = nullptr;
-  for (size_t i = 0; i < n; ++i)
+  for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
+    if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
+  }
   rc_check_opts ro = resolve_opts(models, n, opts_in);
   if (opts_in && opts_in->path == RC_PATH_AUTO) {
     size_t need = 0;
@@ -1089,8 +1313,10 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
 rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts, void* workspace, size_t ws_bytes,
                   void* stream, rc_check_opts* best) {
   if (!best || !models || n == 0) return RC_E_INVALID;
-  for (size_t i = 0; i < n; ++i)
+  for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
+    if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // a wide model has one path: chunked sort
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   rc_check_opts base{};
@@ -1197,6 +1423,11 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
       return RC_E_CUDA;
     }
   }
+  if (t->chunked) {
+    decode_chunked(t, out);
+    ticket_put(t);
+    return RC_OK;
+  }
   for (size_t i = 0; i < t->n; ++i) {
     const rc::Model& m = t->models[i]->m;
     if (t->cell_base.empty())
@@ -1236,6 +1467,7 @@ rc_status rc_expand_keys(rc_model* mm, void* workspace, size_t ws_bytes, uint64_
                          void* stream) {
   if (!mm || !keys_dev || !count_dev) return RC_E_INVALID;
   const rc::Model& m = mm->m;
+  if (m.wide) return RC_E_KEY_OVERFLOW;   // its cells do not fit one key
   rc::WorkspacePlan p;
   rc::plan_workspace(m, nullptr, &p);
   uint8_t* ws = static_cast<uint8_t*>(workspace);

@@ -279,7 +279,8 @@ def _offset_expr(rng: SplitMix64, depth: int, row_len: int) -> Expr:
 
 def random_affine(seed: int, n_blocks: int = 4096, block: int = 256, n_stmts: int = 36,
                   n_phases: int = 8, max_depth: int = 2, max_trip: int = 16,
-                  plant: Optional[bool] = None, n_threads: Optional[int] = None) -> Model:
+                  plant: Optional[bool] = None, n_threads: Optional[int] = None,
+                  row_global: int = RANDOM_AFFINE_ROW_GLOBAL) -> Model:
     """Seeded random affine kernel model, race-free unless a race is planted.
 
     Arrays (rows of ``RANDOM_AFFINE_ROW_GLOBAL`` cells, one row per thread):
@@ -299,11 +300,14 @@ def random_affine(seed: int, n_blocks: int = 4096, block: int = 256, n_stmts: in
     and row ``g``, both at offset ``off0``; this makes exactly ``T`` cells racy.
 
     ``n_threads`` (default ``n_blocks * block``) may be smaller than the grid;
-    then threads with ``gtid >= n_threads`` are guarded off.
+    then threads with ``gtid >= n_threads`` are guarded off.  ``row_global``
+    sets the row length of the global arrays (a long row makes a sparse cell
+    space: with rows of 2^40 cells and more the packed key needs more than 63
+    bits and the model is checked in cell-range chunks).
     """
     rng = SplitMix64(seed)
     T = n_blocks * block if n_threads is None else int(n_threads)
-    RG, RS = RANDOM_AFFINE_ROW_GLOBAL, RANDOM_AFFINE_ROW_SHARED
+    RG, RS = int(row_global), RANDOM_AFFINE_ROW_SHARED
     arrays = [
         Array("A0", GLOBAL, (T, RG)),
         Array("A1", GLOBAL, (T, RG)),
