@@ -319,6 +319,74 @@ def run_native(args):
 
 
 # ---------------------------------------------------------------------------
+# a model wider than one key: checked in cell-range chunks
+# ---------------------------------------------------------------------------
+def run_wide(args):
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+    from paper_2503_08946_gb300 import distributed as D
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+    model = w.random_affine(args.seed + rank, n_blocks=args.blocks, row_global=args.wide_row)
+    h = rc.rc_model_create(model)
+    lay = rc.rc_model_layout(h)
+    assert lay["wide"] == 1, "the row length does not make the key wider than 63 bits"
+    ws = rc.workspace(rc.rc_workspace_size(h, None))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        r = rc.rc_report(rc.rc_check(h, None, ws, stream))[0]
+        if r.status != rc.RC_OK:
+            raise RuntimeError(f"check failed: {rc.rc_status_str(r.status)}")
+        return r
+
+    for _ in range(max(3, args.warmup)):
+        res = step()
+    sampler = ClockSampler(gpu_index(local))
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total, t_max, value = D.weak_scaling_rate(res.instances * args.steps, ev0.elapsed_time(ev1), device="cuda")
+    if rank == 0:
+        line = {
+            "metric": METRIC + ", wide keys", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("4096 blocks", f"{args.blocks} blocks")
+                       + f", global rows of {args.wide_row} cells (packed key "
+                       f"{lay['cell_shift'] + lay['total_cells'].bit_length()} bits: cell-range chunks)",
+                       "seed": args.seed, "instances_per_rank": res.instances, "total_cells": lay["total_cells"],
+                       "chunk_cell_bits": lay["cell_bits"], "path": "chunked sort",
+                       "l2": "inputs larger than L2", "parallelism": f"independent models per rank x{world}"},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # batched check of many small models vs one check per model
 # ---------------------------------------------------------------------------
 BATCH_WORKLOAD = ("10,000 seeded random models: threads log-uniform 32..65,536 (multiple of 32, block "
@@ -563,7 +631,7 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve"],
+    ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve", "wide"],
                     help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models; "
                          "serve: Poisson request stream through the request server")
     ap.add_argument("--batch-models", type=int, default=10000)
@@ -572,11 +640,15 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--pool-gb", type=int, default=8)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--wide-row", type=int, default=1 << 20,
+                    help="wide: cells per global-array row (2^20 makes a 66-bit key at 4096 blocks)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "wide":
+        return run_wide(args)
     if args.workload == "serve":
         return run_serve(args)
     return run_native(args)

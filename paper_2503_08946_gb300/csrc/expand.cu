@@ -53,24 +53,38 @@ struct CountSink {
   __device__ __forceinline__ void pad(uint64_t) {}
 };
 
-// Key pass of a chunked check: the keys of cells in [lo, lo + span) are
-// appended (in no particular order) with their cell field rebased to cell - lo,
-// which fits the field even when the model's cells do not.  The lanes that
-// append together reserve their positions with one atomic add; a position at or
-// past `cap` is not written and flags kErrChunkOverflow.
-struct CompactSink {
-  uint64_t* keys;
-  unsigned long long* count;
-  uint64_t cap, lo, span, low_mask;
-  uint32_t cell_shift;
+// Key pass of a chunked check, for one wave of chunks (consecutive chunks
+// whose keys fit the workspace together): the key of a cell in a chunk of the
+// wave is appended to that chunk's segment with its cell field rebased to the
+// chunk start, which fits the field even when the model's cells do not.  The
+// chunk of a cell comes from its bucket (chunks are whole buckets).  The lanes
+// that append to one chunk together reserve their positions with one atomic
+// add; a position past the chunk's segment is not written and flags
+// kErrChunkOverflow.
+struct RouteSink {
+  RouteArgs r;
   unsigned int* err;
   __device__ __forceinline__ void put(uint64_t, uint64_t key, uint64_t cell) {
-    if (key == kSentinel || cell - lo >= span) return;
+    if (key == kSentinel) return;
+    const uint64_t rel = cell - r.lo;
+    if (rel >= r.span) return;
+    const uint64_t bk = (rel >> r.bshift) - r.b0;
+    if (bk >= r.n_buckets) return;
+    const uint32_t k = r.chunk_of[bk];
+    if (k == 0xffffffffu) return;
+    const uint64_t out = ((cell - r.c_lo[k]) << r.cell_shift) | (key & r.low_mask);
     cg::coalesced_group g = cg::coalesced_threads();
-    unsigned long long base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(count, (unsigned long long)g.size());
-    const unsigned long long pos = g.shfl(base, 0) + g.thread_rank();
-    if (pos < cap) keys[pos] = ((cell - lo) << cell_shift) | (key & low_mask);
+    const uint32_t k0 = g.shfl(k, 0);
+    unsigned long long pos;
+    if (g.all(k == k0)) {
+      unsigned long long base = 0;
+      if (g.thread_rank() == 0) base = atomicAdd(r.c_ctr + k0, (unsigned long long)g.size());
+      pos = g.shfl(base, 0) + g.thread_rank();
+    } else {
+      pos = atomicAdd(r.c_ctr + k, 1ull);
+    }
+    pos += r.c_base[k];
+    if (pos < r.c_end[k]) r.keys[pos] = out;
     else atomicOr(err, (unsigned int)kErrChunkOverflow);
   }
   __device__ __forceinline__ void pad(uint64_t) {}
@@ -247,11 +261,9 @@ cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n
   return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, CountSink{counts, lo, span, bshift}, st);
 }
 
-cudaError_t launch_expand_compact(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
-                                  uint32_t cell_shift, uint64_t* keys, unsigned long long* count, uint64_t cap,
-                                  uint64_t lo, uint64_t span, DevResult* res, cudaStream_t st) {
-  CompactSink k{keys, count, cap, lo, span, (1ull << cell_shift) - 1ull, cell_shift, &res->err};
-  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, k, st);
+cudaError_t launch_expand_route(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                const RouteArgs& r, DevResult* res, cudaStream_t st) {
+  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, RouteSink{r, &res->err}, st);
 }
 
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st) {

@@ -114,6 +114,7 @@ int log2i(int64_t d) {
 
 struct Gen {
   const Model& m;
+  bool chunked = false;   // count / route kernel of chunked checks instead of the slot kernel
   const uint8_t* img;
   const DevStmt* stmts;
   const DevAccess* accs;
@@ -168,8 +169,13 @@ struct Gen {
     const DevStmt& S = stmts[s];
     const uint64_t T = m.host.n_threads;
     o << "    case " << s << ": {\n";
-    if (S.dense) o << "      unsigned long long slot = " << ulit(S.slot_base) << " + g;\n";
-    else o << "      unsigned long long off = unit_offset[" << ulit(S.slot_base) << " + g];\n";
+    if (chunked) {
+      // keys go to chunk_put; no slots
+    } else if (S.dense) {
+      o << "      unsigned long long slot = " << ulit(S.slot_base) << " + g;\n";
+    } else {
+      o << "      unsigned long long off = unit_offset[" << ulit(S.slot_base) << " + g];\n";
+    }
     emit_terms(S, 0, "      ");
     std::string ind = "      ";
     for (int l = 0; l < S.n_loops; ++l) {
@@ -205,6 +211,18 @@ struct Gen {
       std::string cell = ulit(arr.base) + " + (unsigned long long)(" + e + ")";
       if (arr.shared) cell += " + b * " + ulit(arr.cells);
       const uint64_t pack = ((unsigned long long)s << 51) | ((unsigned long long)a << 45);
+      if (chunked) {
+        // the whole cell goes to the sink beside the key, whose cell field may not hold it
+        o << in3 << "unsigned long long key = ~0ull, cl = ~0ull;\n";
+        o << in3 << "if (dc != 0xFFFFFFFFu) atomicMin(oob, " << ulit(pack) << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc);\n";
+        o << in3 << "else { cl = " << cell << ";\n";
+        o << in3 << "  key = (cl << " << m.host.cell_shift << ") | ((unsigned long long)ph << " << m.host.phase_shift
+          << ") | low | " << ulit((uint64_t)A.kind) << "; }\n";
+        if (A.key_idx < 0) o << in3 << "(void)key; (void)cl;\n";
+        else o << in3 << "chunk_put(a, key, cl);\n";
+        o << in2 << "}\n";
+        continue;
+      }
       o << in3 << "unsigned long long key;\n";
       o << in3 << "if (dc != 0xFFFFFFFFu) { atomicMin(oob, " << ulit(pack)
         << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc); key = ~0ull; }\n";
@@ -218,9 +236,11 @@ struct Gen {
       o << in2 << "}\n";
     }
     o << in2 << "cnt += " << S.n_acc << ";\n";
-    if (!S.dense) o << in2 << "off += " << S.n_key << ";\n";
+    if (!S.dense && !chunked) o << in2 << "off += " << S.n_key << ";\n";
     o << ind << "}";
-    if (S.dense) {
+    if (chunked) {
+      o << "\n";
+    } else if (S.dense) {
       o << " else {\n";
       for (int kq = 0; kq < S.n_key; ++kq) o << in2 << "keys[slot + " << ulit((uint64_t)kq * T) << "] = ~0ull;\n";
       o << ind << "}\n";
@@ -244,9 +264,61 @@ struct Gen {
     o << "__device__ __forceinline__ long long tload_c(const long long* t, unsigned long long off, "
          "unsigned long long len, long long i) {\n"
          "  return (i < 0 || (unsigned long long)i >= len) ? 0LL : t[off + (unsigned long long)i];\n}\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
-         "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
-         "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata) {\n";
+    if (chunked) {
+      // same layout as rc::ChunkJitArgs
+      o << "struct ChunkJitArgs {\n"
+           "  unsigned long long* oob; unsigned long long* inst; const long long* tdata;\n"
+           "  int mode; int pad;\n"
+           "  unsigned long long* counts; unsigned long long lo, span; unsigned bshift, cell_shift;\n"
+           "  unsigned long long* keys; const unsigned* chunk_of; const unsigned long long* c_lo;\n"
+           "  const unsigned long long* c_base; const unsigned long long* c_end; unsigned long long* c_ctr;\n"
+           "  unsigned long long b0, n_buckets, low_mask; unsigned* err;\n};\n";
+      // mode 0: count keys per bucket; mode 1: route keys to their chunk's segment
+      o << "__device__ __forceinline__ void chunk_put(const ChunkJitArgs& a, unsigned long long key, "
+           "unsigned long long cell) {\n"
+           "  if (key == ~0ull) return;\n"
+           "  const unsigned long long rel = cell - a.lo;\n"
+           "  if (rel >= a.span) return;\n"
+           "  const unsigned long long bucket = rel >> a.bshift;\n"
+           "  const unsigned lane = threadIdx.x & 31u;\n"
+           "  if (a.mode == 0) {\n"
+           "    const unsigned act = __activemask();\n"
+           "    const int leader = __ffs(act) - 1;\n"
+           "    const unsigned long long b0 = __shfl_sync(act, bucket, leader);\n"
+           "    if (__all_sync(act, bucket == b0)) {\n"
+           "      if ((int)lane == leader) atomicAdd(a.counts + b0, (unsigned long long)__popc(act));\n"
+           "    } else {\n"
+           "      atomicAdd(a.counts + bucket, 1ull);\n"
+           "    }\n"
+           "    return;\n"
+           "  }\n"
+           "  const unsigned long long bk = bucket - a.b0;\n"
+           "  if (bk >= a.n_buckets) return;\n"
+           "  const unsigned k = a.chunk_of[bk];\n"
+           "  if (k == 0xffffffffu) return;\n"
+           "  const unsigned long long out = ((cell - a.c_lo[k]) << a.cell_shift) | (key & a.low_mask);\n"
+           "  const unsigned act = __activemask();\n"
+           "  const int leader = __ffs(act) - 1;\n"
+           "  const unsigned k0 = __shfl_sync(act, k, leader);\n"
+           "  unsigned long long pos;\n"
+           "  if (__all_sync(act, k == k0)) {\n"
+           "    unsigned long long base = 0;\n"
+           "    if ((int)lane == leader) base = atomicAdd(a.c_ctr + k0, (unsigned long long)__popc(act));\n"
+           "    pos = __shfl_sync(act, base, leader) + __popc(act & ((1u << lane) - 1u));\n"
+           "  } else {\n"
+           "    pos = atomicAdd(a.c_ctr + k, 1ull);\n"
+           "  }\n"
+           "  pos += a.c_base[k];\n"
+           "  if (pos < a.c_end[k]) a.keys[pos] = out;\n"
+           "  else atomicOr(a.err, " + std::to_string((unsigned)kErrChunkOverflow) + "u);\n"
+           "}\n";
+      o << "extern \"C\" __global__ void __launch_bounds__(128) rc_chunk_jit(const ChunkJitArgs a) {\n";
+      o << "  unsigned long long* oob = a.oob;\n  const long long* tdata = a.tdata;\n  (void)tdata;\n";
+    } else {
+      o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
+           "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
+           "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata) {\n";
+    }
     o << "  const unsigned long long g = (unsigned long long)blockIdx.x * 128ull + threadIdx.x;\n";
     o << "  unsigned long long cnt = 0;\n";
     o << "  if (g < " << ulit(h.n_threads) << ") {\n";
@@ -263,7 +335,7 @@ struct Gen {
     for (uint32_t s = 0; s < h.n_stmts; ++s) emit_stmt(s);
     o << "    default: break;\n    }\n  }\n";
     o << "  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);\n";
-    o << "  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(inst, cnt);\n";
+    o << "  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(" << (chunked ? "a.inst" : "inst") << ", cnt);\n";
     o << "}\n";
     return o.str();
   }
@@ -276,33 +348,31 @@ std::string jit_expand_source(const Model& m) {
   return g.source();
 }
 
-// Compile (or fetch from the cache) the model's expansion kernel for the
-// current device.  Returns false if NVRTC, the driver or the compile fails.
-bool jit_expand_build(Model* m) {
-  const char* env = std::getenv("RC_JIT");
-  if (env && env[0] == '0') return false;
-  const bool force = env && env[0] == '1';
-  if (!force && m->key_slots < kJitMinKeys) return false;
-  if (m->wide) return false;   // chunked checks run the interpreted count and compact passes
-  if (m->host.n_stmts == 0 || m->host.n_threads == 0) return false;
+std::string jit_chunk_source(const Model& m) {
+  Gen g(m);
+  g.chunked = true;
+  return g.source();
+}
+
+namespace {
+
+// Compile `src` for the current device (or fetch it from the cache) and return
+// its kernel `name`, or null if NVRTC, the driver or the compile fails.
+void* jit_compile(const std::string& src, const char* name) {
   std::lock_guard<std::mutex> lk(g_jit_mu);
   Nvrtc& nv = nvrtc();
   Driver& dr = driver();
-  if (!nv.ok || !dr.ok) return false;
+  if (!nv.ok || !dr.ok) return nullptr;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  const std::string src = jit_expand_source(*m);
-  const std::string key = std::to_string(dev) + "\n" + src;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  const std::string key = std::to_string(dev) + "\n" + name + "\n" + src;
   auto it = g_cache.find(key);
-  if (it != g_cache.end()) {
-    m->jit_fn = it->second;
-    return true;
-  }
+  if (it != g_cache.end()) return it->second;
   cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return nullptr;
   const std::string arch = "--gpu-architecture=sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
   nvrtcProgram prog;
-  if (nv.create(&prog, src.c_str(), "rc_expand_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
+  if (nv.create(&prog, src.c_str(), "rc_expand_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return nullptr;
   const char* opts[] = {arch.c_str(), "--std=c++17"};
   bool ok = nv.compile(prog, 2, opts) == NVRTC_SUCCESS;
   std::vector<char> cubin;
@@ -315,14 +385,47 @@ bool jit_expand_build(Model* m) {
     }
   }
   nv.destroy(&prog);
-  if (!ok) return false;
+  if (!ok) return nullptr;
   CUmodule mod;
   CUfunction fn;
-  if (dr.load(&mod, cubin.data()) != CUDA_SUCCESS) return false;
-  if (dr.get(&fn, mod, "rc_expand_jit") != CUDA_SUCCESS) return false;
+  if (dr.load(&mod, cubin.data()) != CUDA_SUCCESS) return nullptr;
+  if (dr.get(&fn, mod, name) != CUDA_SUCCESS) return nullptr;
   g_cache[key] = reinterpret_cast<void*>(fn);
-  m->jit_fn = reinterpret_cast<void*>(fn);
-  return true;
+  return reinterpret_cast<void*>(fn);
+}
+
+// RC_JIT=0 disables generated kernels, RC_JIT=1 forces them for every model
+bool jit_wanted(const Model& m) {
+  const char* env = std::getenv("RC_JIT");
+  if (env && env[0] == '0') return false;
+  const bool force = env && env[0] == '1';
+  if (!force && m.key_slots < kJitMinKeys) return false;
+  return m.host.n_stmts != 0 && m.host.n_threads != 0;
+}
+
+}  // namespace
+
+// The model's generated kernel: the slot kernel of the ordinary check, or for
+// a wide model the count / route kernel of its chunked checks.  Returns false
+// (the interpreted kernels stay in use) if NVRTC, the driver or the compile fails.
+bool jit_expand_build(Model* m) {
+  if (!jit_wanted(*m)) return false;
+  if (m->wide) {
+    m->jit_chunk_fn = jit_compile(jit_chunk_source(*m), "rc_chunk_jit");
+    return m->jit_chunk_fn != nullptr;
+  }
+  m->jit_fn = jit_compile(jit_expand_source(*m), "rc_expand_jit");
+  return m->jit_fn != nullptr;
+}
+
+cudaError_t jit_chunk_launch(const Model& m, const ChunkJitArgs& a, cudaStream_t st) {
+  Driver& dr = driver();
+  CUfunction fn = reinterpret_cast<CUfunction>(m.jit_chunk_fn);
+  ChunkJitArgs args = a;
+  void* params[] = {&args};
+  const unsigned gx = (unsigned)((m.host.n_threads + 127) / 128);
+  const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
 cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo,

@@ -17,11 +17,23 @@ cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threa
 cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
                                 DevResult* res, unsigned long long* counts, uint64_t lo, uint64_t span,
                                 uint32_t bshift, cudaStream_t st);
-// Key pass of a chunked check: the keys of cells in [lo, lo + span), cell field
-// rebased to cell - lo, appended at keys[*count++] (at most cap).
-cudaError_t launch_expand_compact(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
-                                  uint32_t cell_shift, uint64_t* keys, unsigned long long* count, uint64_t cap,
-                                  uint64_t lo, uint64_t span, DevResult* res, cudaStream_t st);
+// Key pass of a chunked check for one wave of chunks: the keys of cells in the
+// wave's chunks, cell field rebased to the chunk start, appended to their
+// chunk's segment of `keys`.
+struct RouteArgs {
+  uint64_t* keys;
+  const uint32_t* chunk_of;    // chunk (in the wave) of bucket b0 + i; ~0 = not in the wave
+  const uint64_t* c_lo;        // per chunk: first cell
+  const uint64_t* c_base;      // per chunk: first key position of its segment
+  const uint64_t* c_end;       // per chunk: one past its segment
+  unsigned long long* c_ctr;   // per chunk: keys appended (cleared before the pass)
+  uint64_t lo, span;           // checked cell range [lo, lo + span)
+  uint64_t b0, n_buckets;      // the wave's buckets [b0, b0 + n_buckets)
+  uint64_t low_mask;           // key bits below the cell field
+  uint32_t bshift, cell_shift;
+};
+cudaError_t launch_expand_route(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,
+                                const RouteArgs& r, DevResult* res, cudaStream_t st);
 cudaError_t launch_count(const DevModel* dm, uint64_t n_units, uint64_t* counts, cudaStream_t st);
 size_t scan_u64_temp_bytes(uint64_t n);
 cudaError_t scan_u64_exclusive(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t add, uint64_t* temp,

@@ -352,21 +352,47 @@ struct Model {
   // sections of the program image (byte offsets), for the kernel generator
   size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null
+  void* jit_chunk_fn = nullptr;   // wide models: generated count / route kernel, or null
   uint64_t max_iter_per_unit = 0;
 };
 
 // implemented in jit.cpp
 constexpr uint64_t kJitMinKeys = 1ull << 22;   // models with fewer keys keep the interpreted expansion
+// Arguments of the generated count / route kernel of chunked checks (the
+// generated source declares the same struct).
+struct ChunkJitArgs {
+  unsigned long long* oob;
+  unsigned long long* inst;
+  const int64_t* tdata;
+  int32_t mode;                       // 0 = count keys per bucket, 1 = route keys to chunk segments
+  int32_t pad;
+  unsigned long long* counts;
+  uint64_t lo, span;
+  uint32_t bshift, cell_shift;
+  uint64_t* keys;
+  const uint32_t* chunk_of;
+  const uint64_t* c_lo;
+  const uint64_t* c_base;
+  const uint64_t* c_end;
+  unsigned long long* c_ctr;
+  uint64_t b0, n_buckets, low_mask;
+  unsigned int* err;
+};
 std::string jit_expand_source(const Model& m);
+std::string jit_chunk_source(const Model& m);
 bool jit_expand_build(Model* m);
+cudaError_t jit_chunk_launch(const Model& m, const ChunkJitArgs& a, cudaStream_t st);
 cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo = 0,
                               uint64_t cell_hi = ~0ull);
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);
 void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p);
-// the sort-path plan for n keys whose cell field has cell_bits bits
-void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits, WorkspacePlan* p);
+// the sort-path plan for n keys whose cell field has cell_bits bits; the
+// look-back region holds digits of at least min_lookback_bits bits (so that a
+// narrower sort of fewer bits, whose widest digit may be wider, fits it)
+void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits, WorkspacePlan* p,
+                         uint32_t min_lookback_bits = 0);
 void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp);
 uint32_t bit_length(uint64_t v);
 

@@ -171,7 +171,7 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
 }
 
 void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits,
-                         WorkspacePlan* p) {
+                         WorkspacePlan* p, uint32_t min_lookback_bits) {
   std::memset(p, 0, sizeof(*p));
   p->n_keys = n;
   const uint32_t hi = m.host.cell_shift + cell_bits;
@@ -189,7 +189,7 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   p->hist_off = off;
   off = align256(off + (size_t)16 * kMaxRadix * 8);
   p->lookback_off = off;
-  off = align256(off + (size_t)p->n_tiles * ((size_t)1 << plan_max_bits(p->sort)) * 8);
+  off = align256(off + (size_t)p->n_tiles * ((size_t)1 << std::max(plan_max_bits(p->sort), min_lookback_bits)) * 8);
   p->tilectr_off = off;
   off = align256(off + 16 * sizeof(unsigned int));
   p->scanctr_off = off;
@@ -438,12 +438,13 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
 // A count pass expands the whole model (all instances are counted and
 // bounds-checked) and histograms its keys over buckets of 2^bshift cells of the
 // checked range.  The host then cuts the range into chunks of whole buckets,
-// each with at most `cap` keys (what the workspace holds) and a cell span that
-// fits the key's cell field; each chunk expands the model again, keeping (and
-// compacting) only its own keys with their cells rebased to the chunk start,
-// and runs the ordinary sort, scan and witness stages on them.  A cell races or
-// not on its own, so the chunk counts add up and the smallest racing pair is
-// the one of the first chunk with a race.
+// each with a cell span that fits the key's cell field and at most `cap` keys
+// (what the workspace holds), and groups consecutive chunks into waves whose
+// keys fit the workspace together.  Per wave one expansion routes every key of
+// the wave's chunks to its chunk's segment, with its cell rebased to the chunk
+// start; then each chunk runs the ordinary sort, scan and witness stages on its
+// segment.  A cell races or not on its own, so the chunk counts add up and the
+// smallest racing pair is the one of the first chunk with a race.
 constexpr uint64_t kMaxChunkBuckets = 1ull << 20;
 constexpr size_t kMaxChunks = 1u << 16;
 
@@ -452,7 +453,8 @@ struct ChunkGeometry {
   uint32_t bshift = 0;         // bucket = (cell - lo) >> bshift
   uint64_t n_buckets = 0;
   uint64_t max_span = 0;       // cells one chunk may span
-  size_t counts_off = 0, ctr_off = 0, region_off = 0;
+  // workspace: bucket counts | chunk of each bucket | per chunk (lo, base, end, counter) | region
+  size_t counts_off = 0, table_off = 0, chunks_off = 0, region_off = 0;
 };
 
 rc_status chunk_geometry(const rc::Model& m, const rc_check_opts* opts, ChunkGeometry* g) {
@@ -469,21 +471,34 @@ rc_status chunk_geometry(const rc::Model& m, const rc_check_opts* opts, ChunkGeo
   if (bs > 0 && (1ull << bs) > g->max_span) return RC_E_KEY_OVERFLOW;   // would need too many chunks
   g->bshift = bs;
   g->n_buckets = g->span ? ((g->span - 1) >> bs) + 1 : 0;
-  g->ctr_off = 0;
-  g->counts_off = 256;
-  g->region_off = align256(g->counts_off + (size_t)(g->n_buckets ? g->n_buckets : 1) * 8);
+  const size_t nb = g->n_buckets ? g->n_buckets : 1;
+  g->counts_off = 0;
+  g->table_off = align256(g->counts_off + nb * 8);
+  g->chunks_off = align256(g->table_off + nb * 4);
+  g->region_off = align256(g->chunks_off + kMaxChunks * 4 * 8);
   return RC_OK;
 }
 
-// keys one chunk's region can hold in `bytes`
+// widest digit any chunk's sort may use (plan_sort's clamp of the digit width)
+uint32_t chunk_digit_bits(const rc_check_opts* opts) {
+  const uint32_t d = (opts && opts->digit_bits) ? opts->digit_bits : 8u;
+  return d < 4 ? 4u : (d > 11 ? 11u : d);
+}
+
+// the region's layout for n keys
+void chunk_region_plan(const rc::Model& m, const rc_check_opts* opts, uint64_t n, rc::WorkspacePlan* p) {
+  rc::plan_workspace_keys(m, opts, n, m.host.cell_bits, p, chunk_digit_bits(opts));
+}
+
+// keys one region can hold in `bytes` (~0 if not even its fixed part fits)
 uint64_t chunk_capacity(const rc::Model& m, const rc_check_opts* opts, size_t bytes, uint64_t upper) {
   rc::WorkspacePlan p;
   uint64_t lo = 0, hi = upper;
-  rc::plan_workspace_keys(m, opts, 0, m.host.cell_bits, &p);
-  if (p.total > bytes) return ~0ull;   // not even the fixed part fits
+  chunk_region_plan(m, opts, 0, &p);
+  if (p.total > bytes) return ~0ull;
   while (lo < hi) {
     const uint64_t mid = lo + (hi - lo + 1) / 2;
-    rc::plan_workspace_keys(m, opts, mid, m.host.cell_bits, &p);
+    chunk_region_plan(m, opts, mid, &p);
     if (p.total <= bytes) lo = mid;
     else hi = mid - 1;
   }
@@ -494,7 +509,7 @@ size_t chunked_workspace_size(const rc::Model& m, const rc_check_opts* opts) {
   ChunkGeometry g;
   if (chunk_geometry(m, opts, &g) != RC_OK) return 0;
   rc::WorkspacePlan p;
-  rc::plan_workspace_keys(m, opts, m.key_slots, m.host.cell_bits, &p);
+  chunk_region_plan(m, opts, m.key_slots, &p);
   return g.region_off + p.total;
 }
 
@@ -502,7 +517,7 @@ bool use_chunked(const rc::Model& m, const rc_check_opts* opts) {
   return m.wide || (opts && (opts->flags & RC_OPT_CHUNKED));
 }
 
-// Count pass, planning (one host synchronisation) and the enqueued chunks.
+// Count pass, planning (one host synchronisation) and the enqueued waves.
 rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
                           cudaStream_t st, rc_ticket_s** out) {
   const rc::Model& m = model->m;
@@ -518,29 +533,48 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
   if (cap == ~0ull) return RC_E_NOMEM;
   uint8_t* region = ws + g.region_off;
   auto* counts = reinterpret_cast<unsigned long long*>(ws + g.counts_off);
-  auto* ctr = reinterpret_cast<unsigned long long*>(ws + g.ctr_off);
   const rc::DevModel* dm = reinterpret_cast<const rc::DevModel*>(m.dev_program);
-  rc::WorkspacePlan p0;
-  rc::plan_workspace_keys(m, opts, 0, m.host.cell_bits, &p0);
-  auto* res = reinterpret_cast<rc::DevResult*>(region + p0.result_off);
+  // the region's layout for a full wave; each chunk uses a prefix of its scratch
+  rc::WorkspacePlan pc;
+  chunk_region_plan(m, opts, cap, &pc);
+  auto* res = reinterpret_cast<rc::DevResult*>(region + pc.result_off);
 
   // count pass
   rc::DevResult r0;
   std::vector<unsigned long long> hc(g.n_buckets);
   s = cuda_status(rc::launch_init_result(res, st));
   if (s == RC_OK && g.n_buckets) s = cuda_status(cudaMemsetAsync(counts, 0, g.n_buckets * 8, st));
-  if (s == RC_OK)
-    s = cuda_status(rc::launch_expand_count(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops, res, counts,
-                                            g.lo, g.span, g.bshift, st));
+  rc::ChunkJitArgs ja;
+  std::memset(&ja, 0, sizeof(ja));
+  ja.oob = &res->oob_code;
+  ja.inst = &res->instances;
+  ja.tdata = m.host.tdata;
+  ja.counts = counts;
+  ja.lo = g.lo;
+  ja.span = g.span;
+  ja.bshift = g.bshift;
+  ja.cell_shift = m.host.cell_shift;
+  ja.err = &res->err;
+  if (s == RC_OK) {
+    if (m.jit_chunk_fn)
+      s = cuda_status(rc::jit_chunk_launch(m, ja, st));
+    else
+      s = cuda_status(rc::launch_expand_count(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops, res, counts,
+                                              g.lo, g.span, g.bshift, st));
+  }
   if (s == RC_OK) s = cuda_status(cudaMemcpyAsync(&r0, res, sizeof(r0), cudaMemcpyDeviceToHost, st));
   if (s == RC_OK && g.n_buckets)
     s = cuda_status(cudaMemcpyAsync(hc.data(), counts, g.n_buckets * 8, cudaMemcpyDeviceToHost, st));
   if (s == RC_OK) s = cuda_status(cudaStreamSynchronize(st));
   if (s != RC_OK) return s;
 
-  // chunks of whole buckets: at most `cap` keys and `max_span` cells each
-  struct Chunk { uint64_t lo, span, n; };
+  // chunks of whole buckets (at most `cap` keys, `max_span` cells), then waves
+  // of consecutive chunks with at most `cap` keys together
+  struct Chunk { uint64_t lo, span, n, b0, b1, base; };
+  struct Wave { size_t k0, k1; uint64_t b0, b1; };
   std::vector<Chunk> chunks;
+  std::vector<Wave> waves;
+  std::vector<uint32_t> chunk_of(g.n_buckets, 0xffffffffu);
   if (r0.oob_code == ~0ull && r0.err == 0) {
     const uint64_t per = g.max_span >> g.bshift;   // buckets one chunk may span (>= 1)
     uint64_t i = 0;
@@ -550,10 +584,22 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
       const uint64_t start = i;
       uint64_t n = 0;
       while (i < g.n_buckets && i - start < per && n + hc[i] <= cap) n += hc[i++];
+      if (chunks.size() == kMaxChunks) return RC_E_NOMEM;
       const uint64_t clo = g.lo + (start << g.bshift);
       const uint64_t cend = std::min(g.lo + (i << g.bshift), g.lo + g.span);
-      chunks.push_back(Chunk{clo, cend - clo, n});
-      if (chunks.size() > kMaxChunks) return RC_E_NOMEM;
+      for (uint64_t b = start; b < i; ++b) chunk_of[b] = (uint32_t)chunks.size();
+      chunks.push_back(Chunk{clo, cend - clo, n, start, i, 0});
+    }
+    uint64_t used = 0;
+    for (size_t k = 0; k < chunks.size(); ++k) {
+      if (waves.empty() || used + chunks[k].n > cap) {
+        waves.push_back(Wave{k, k, chunks[k].b0, chunks[k].b0});
+        used = 0;
+      }
+      chunks[k].base = used;
+      used += chunks[k].n;
+      waves.back().k1 = k + 1;
+      waves.back().b1 = chunks[k].b1;
     }
   }
   rc_ticket_s* t = ticket_get(chunks.size() + 1);
@@ -561,29 +607,88 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
   t->models.assign(chunks.size() + 1, model);
   t->chunked = true;
   t->host[0] = r0;
-  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
-  for (size_t k = 0; k < chunks.size() && s == RC_OK; ++k) {
-    const Chunk& c = chunks[k];
-    t->chunk_lo.push_back(c.lo);
-    rc::WorkspacePlan p;
-    rc::plan_workspace_keys(m, opts, c.n, std::max<uint32_t>(1u, rc::bit_length(c.span - 1)), &p);
-    uint64_t* k0 = reinterpret_cast<uint64_t*>(region + p.keys_off[0]);
-    uint64_t* k1 = reinterpret_cast<uint64_t*>(region + p.keys_off[1]);
-    s = cuda_status(cudaMemsetAsync(region + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
-    if (s == RC_OK) s = cuda_status(cudaMemsetAsync(ctr, 0, 8, st));
-    if (s == RC_OK) s = cuda_status(rc::launch_init_result(res, st));
-    if (s == RC_OK)
-      s = cuda_status(rc::launch_expand_compact(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
-                                                m.host.cell_shift, k0, ctr, c.n, c.lo, c.span, res, st));
-    int sorted = 0;
-    if (s == RC_OK) s = enqueue_sort(p, region, k0, k1, spin, opts ? opts->test_flags : 0u, st, &sorted, nullptr, true);
-    if (s == RC_OK && c.n > 0) {
-      rc::ScanArgs sa = scan_args(m, p, region, sorted);
-      s = cuda_status(rc::launch_scan(sa, st));
-      if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
+  for (const Chunk& c : chunks) t->chunk_lo.push_back(c.lo);
+  if (!chunks.empty()) {
+    // tables of the route pass: chunk of each bucket; per chunk lo, base, end, counter
+    const size_t K = chunks.size();
+    std::vector<uint64_t> arr(4 * K, 0);
+    for (size_t k = 0; k < K; ++k) {
+      arr[k] = chunks[k].lo;
+      arr[K + k] = chunks[k].base;
+      arr[2 * K + k] = chunks[k].base + chunks[k].n;
     }
+    s = cuda_status(cudaMemcpyAsync(ws + g.table_off, chunk_of.data(), g.n_buckets * 4, cudaMemcpyHostToDevice, st));
     if (s == RC_OK)
-      s = cuda_status(cudaMemcpyAsync(t->host + 1 + k, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+      s = cuda_status(cudaMemcpyAsync(ws + g.chunks_off, arr.data(), arr.size() * 8, cudaMemcpyHostToDevice, st));
+  }
+  const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
+  uint64_t* keys0 = reinterpret_cast<uint64_t*>(region + pc.keys_off[0]);
+  uint64_t* keys1 = reinterpret_cast<uint64_t*>(region + pc.keys_off[1]);
+  const size_t K = chunks.size();
+  auto* c_lo = reinterpret_cast<const uint64_t*>(ws + g.chunks_off);
+  for (const Wave& wv : waves) {
+    if (s != RC_OK) break;
+    rc::RouteArgs ra;
+    ra.keys = keys0;
+    ra.chunk_of = reinterpret_cast<const uint32_t*>(ws + g.table_off) + wv.b0;
+    ra.c_lo = c_lo;
+    ra.c_base = c_lo + K;
+    ra.c_end = c_lo + 2 * K;
+    ra.c_ctr = reinterpret_cast<unsigned long long*>(ws + g.chunks_off) + 3 * K;
+    ra.lo = g.lo;
+    ra.span = g.span;
+    ra.b0 = wv.b0;
+    ra.n_buckets = wv.b1 - wv.b0;
+    ra.low_mask = (1ull << m.host.cell_shift) - 1ull;
+    ra.bshift = g.bshift;
+    ra.cell_shift = m.host.cell_shift;
+    s = cuda_status(cudaMemsetAsync(ra.c_ctr + wv.k0, 0, (wv.k1 - wv.k0) * 8, st));
+    if (s == RC_OK) s = cuda_status(rc::launch_init_result(res, st));
+    if (s == RC_OK && m.jit_chunk_fn) {
+      rc::ChunkJitArgs jr = ja;
+      jr.mode = 1;
+      jr.keys = ra.keys;
+      jr.chunk_of = ra.chunk_of;
+      jr.c_lo = ra.c_lo;
+      jr.c_base = ra.c_base;
+      jr.c_end = ra.c_end;
+      jr.c_ctr = ra.c_ctr;
+      jr.b0 = ra.b0;
+      jr.n_buckets = ra.n_buckets;
+      jr.low_mask = ra.low_mask;
+      s = cuda_status(rc::jit_chunk_launch(m, jr, st));
+    } else if (s == RC_OK) {
+      s = cuda_status(rc::launch_expand_route(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops, ra, res, st));
+    }
+    for (size_t k = wv.k0; k < wv.k1 && s == RC_OK; ++k) {
+      const Chunk& c = chunks[k];
+      rc::WorkspacePlan p = pc;
+      p.n_keys = c.n;
+      p.n_tiles = (c.n + rc::kSortTile - 1) / rc::kSortTile;
+      p.scan_warps = scan_warps_for(c.n);
+      const uint32_t hi = m.host.cell_shift + std::max<uint32_t>(1u, rc::bit_length(c.span - 1));
+      rc::plan_sort(m.host.sort_lo < hi ? m.host.sort_lo : hi, hi, opts ? opts->digit_bits : 0, &p.sort);
+      // clear the digit histograms, the look-back words this chunk uses and the counters
+      const size_t lb_used = (size_t)p.n_tiles * ((size_t)1 << rc::plan_max_bits(p.sort)) * 8;
+      if (p.lookback_off + lb_used > pc.tilectr_off) s = RC_E_INVALID;   // cannot happen: sized for the widest digit
+      if (s == RC_OK) s = cuda_status(cudaMemsetAsync(region + p.hist_off, 0, p.lookback_off - p.hist_off + lb_used, st));
+      if (s == RC_OK) s = cuda_status(cudaMemsetAsync(region + p.tilectr_off, 0, p.zero_hi - p.tilectr_off, st));
+      // a fresh record per chunk; the first chunk of a wave keeps the route
+      // pass's error bits, which the report checks in every record
+      if (k > wv.k0 && s == RC_OK) s = cuda_status(rc::launch_init_result(res, st));
+      int sorted = 0;
+      if (s == RC_OK)
+        s = enqueue_sort(p, region, keys0 + c.base, keys1 + c.base, spin, opts ? opts->test_flags : 0u, st, &sorted,
+                         nullptr, true);
+      if (s == RC_OK && c.n > 0) {
+        rc::ScanArgs sa = scan_args(m, p, region, sorted);
+        sa.keys = (sorted ? keys1 : keys0) + c.base;
+        s = cuda_status(rc::launch_scan(sa, st));
+        if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
+      }
+      if (s == RC_OK)
+        s = cuda_status(cudaMemcpyAsync(t->host + 1 + k, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+    }
   }
   if (s == RC_OK) s = cuda_status(cudaEventRecord(t->done, st));
   if (s != RC_OK) {
@@ -1163,7 +1268,7 @@ rc_status rc_model_layout(const rc_model* mm, rc_layout* out) {
   out->n_threads_per_block = m.host.bs;
   out->n_blocks = m.host.n_blocks;
   out->program_bytes = m.dev_bytes;
-  out->expand_jit = m.jit_fn ? 1u : 0u;
+  out->expand_jit = (m.jit_fn || m.jit_chunk_fn) ? 1u : 0u;
   out->wide = m.wide ? 1u : 0u;
   for (size_t a = 0; a < m.array_base.size() && a < 64; ++a) {
     out->array_base[a] = m.array_base[a];
@@ -1178,7 +1283,7 @@ rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, siz
   std::vector<int32_t> general;
   const rc_status st = rc::lower_model(desc, &m, &general);
   if (st != RC_OK) return st;
-  const std::string src = rc::jit_expand_source(m);
+  const std::string src = m.wide ? rc::jit_chunk_source(m) : rc::jit_expand_source(m);
   *len = src.size();
   if (cap) {
     const size_t n = src.size() < cap - 1 ? src.size() : cap - 1;

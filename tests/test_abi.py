@@ -113,7 +113,7 @@ def test_validation_key_overflow(rc):
     # as a wide model (checked in cell-range chunks)
     big = [Array("g", "global", (1 << 20, 1 << 20))]
     m = Model((1 << 20, 1, 1), (1024, 1, 1), big, [Stmt([Access(0, W, (tid.x, bid.x))])], n_phases=4)
-    assert "rc_expand_jit" in rc.rc_kernel_source(m)   # host lowering succeeds
+    assert "rc_chunk_jit" in rc.rc_kernel_source(m)   # host lowering succeeds: the chunked kernel
     assert _status(rc, m) not in (rc.RC_E_KEY_OVERFLOW, rc.RC_E_INVALID, rc.RC_E_UNSUPPORTED)
     # a cell space of 2^62 cells cannot be addressed at all
     huge = [Array("g", "global", (1 << 31, 1 << 31))]
@@ -131,10 +131,11 @@ def test_generated_kernels_compile(rc, tmp_path):
                  [Stmt([Access(0, W, ((tid.x + it(0) + it(1) + it(2) + it(3) + it(4)) % 64,))],
                        loops=[Loop(0, 2)] * 5)])
     csr = w.ge_spmm_csr(w.csr_row_lengths(1, 8), N=64, K=2)
+    wide = w.random_affine(1, n_blocks=8, block=64, n_stmts=12, row_global=1 << 44)
     for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep, csr,
-                           w.tiny_random_tables(3)]):
+                           w.tiny_random_tables(3), wide]):
         src = rc.rc_kernel_source(m)
-        assert "rc_expand_jit" in src
+        assert ("rc_chunk_jit" if m is wide else "rc_expand_jit") in src
         f = tmp_path / f"k{i}.cu"
         f.write_text(src)
         r = subprocess.run([nvcc, "-c", str(f), "-o", str(tmp_path / f"k{i}.o"), "-std=c++17",

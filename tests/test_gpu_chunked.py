@@ -63,15 +63,21 @@ def test_wide_layout(rc):
 
 
 @pytest.mark.parametrize("seed", range(8))
-def test_wide_random(rc, seed):
+@pytest.mark.parametrize("jit", ["0", "1"])
+def test_wide_random(rc, seed, jit, monkeypatch):
+    monkeypatch.setenv("RC_JIT", jit)   # interpreted / generated count and route passes
     m = wide_model(seed)
     same(rc.check(m), oracle.check(m))
 
 
 @pytest.mark.parametrize("seed", [0, 3])
-def test_wide_planted(rc, seed):
+@pytest.mark.parametrize("jit", ["0", "1"])
+def test_wide_planted(rc, seed, jit, monkeypatch):
+    monkeypatch.setenv("RC_JIT", jit)
     m = wide_model(seed, plant=True)
-    g = rc.check(m)
+    h = rc.binding.rc_model_create(m)
+    assert rc.binding.rc_model_layout(h)["expand_jit"] == int(jit)
+    g = rc.check(h)
     same(g, oracle.check(m))
     assert g.racy_cells == 8 * 64
 
@@ -80,6 +86,19 @@ def test_wide_planted(rc, seed):
 def test_wide_row_lengths(rc, row_bits):
     m = wide_model(5, plant=True, row_bits=row_bits)
     same(rc.check(m), oracle.check(m))
+
+
+@pytest.mark.parametrize("frac", [0.6, 0.3])   # the shared array (one bucket) holds ~1/4 of the keys
+@pytest.mark.parametrize("jit", ["0", "1"])
+def test_wide_small_workspace(rc, frac, jit, monkeypatch):
+    """Span-limited chunks grouped into several waves by a small workspace."""
+    monkeypatch.setenv("RC_JIT", jit)
+    model = wide_model(6, plant=True)
+    b = rc.binding
+    m = b.rc_model_create(model)
+    full = b.rc_workspace_size(m)
+    keys = b.rc_model_layout(m)["key_slots"]
+    same(check_ws(rc, model, None, int(full - 16 * keys * (1 - frac))), oracle.check(model))
 
 
 def test_cell_space_beyond_2_62(rc):
@@ -98,9 +117,22 @@ def test_wide_shared_and_phases(rc):
               for k in range(0, n, 7)]
     m = Model((16, 1, 1), (64, 1, 1), [big, sh], stmts, n_phases=n, name="wide_phases")
     same(rc.check(m), oracle.check(m))
+    m2 = Model((16, 1, 1), (64, 1, 1), [big, sh], stmts, n_phases=n, name="wide_phases_jit")
+    import os
+    old = os.environ.get("RC_JIT")
+    os.environ["RC_JIT"] = "1"
+    try:
+        same(rc.check(m2), oracle.check(m2))
+    finally:
+        if old is None:
+            del os.environ["RC_JIT"]
+        else:
+            os.environ["RC_JIT"] = old
 
 
-def test_wide_out_of_bounds(rc):
+@pytest.mark.parametrize("jit", ["0", "1"])
+def test_wide_out_of_bounds(rc, jit, monkeypatch):
+    monkeypatch.setenv("RC_JIT", jit)
     big = Array("G", "global", (1 << 30, 1 << 30))
     m = Model((4, 1, 1), (32, 1, 1), [big],
               [Stmt([Access(0, W, (tid.x, it(0)))], loops=[Loop(0, 4)]),
