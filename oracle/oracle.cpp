@@ -16,7 +16,8 @@
 //        x = (array a, scope instance s, element e, block b, phase p, thread t, kind k)
 //    with s = b for shared arrays and s = 0 for global arrays, e the row-major
 //    element index, p the value of the statement's barrier-interval expression
-//    and k in {R=0, W=1}.  gtid = b * blockSize + t.
+//    and k in {R=0, W=1, A=2} (A: an atomic read-modify-write).  gtid = b *
+//    blockSize + t.
 //  * Dependences: the paper's RaW / WaW / WaR relations (Section "Using ISCC in
 //    Formal Analysis", the dependence test of the appendix listing) pair two
 //    instances that touch the same array cell with at least one write.  The
@@ -24,8 +25,11 @@
 //    reading adopted here is: two instances are *concurrent* iff they belong to
 //    different threads and (different blocks, or the same barrier interval).
 //    Hence x, y race iff
-//        (a, s, e) equal  and  gtid_x != gtid_y  and  (k_x = W or k_y = W)
-//        and (b_x != b_y or p_x = p_y).
+//        (a, s, e) equal  and  gtid_x != gtid_y  and  conflict(k_x, k_y)
+//        and (b_x != b_y or p_x = p_y),
+//    where two kinds conflict iff one is W, or one is A and the other R: an
+//    atomic modifies the cell (so it conflicts with plain reads and writes), and
+//    two atomics on one cell are ordered by the memory system (no race).
 //    Shared cells have s = b, so they can only race inside one block and one
 //    interval; global cells also race across blocks in any interval.
 //  * Result: verdict = some pair races; count = number of distinct racy cells
@@ -40,13 +44,17 @@
 //    (dimcode 0 = the interval, d+1 = index dimension d).
 //
 // Per cell the oracle uses the equivalent cell-level test
-//     racy(cell) <=> (>= 2 distinct blocks and >= 1 W in the cell)
-//                 or (some (b, p) group has >= 2 distinct threads and >= 1 W),
+//     racy(cell) <=> (>= 2 distinct blocks and conf(cell))
+//                 or (some (b, p) group G has >= 2 distinct threads and conf(G)),
+//     conf(S) = (S has a W) or (S has an A and an R),
 // which follows from the pair predicate: a W in a multi-block cell races with an
 // instance of any other block, and a W in a (b, p) group with >= 2 threads races
-// with an instance of another thread of that group; conversely every racing
-// pair is of one of the two kinds.  oracle_brute() applies the pair predicate to
-// every pair instead, so the two can be compared on small models.
+// with an instance of another thread of that group.  Without a W, if a set
+// spread over two blocks (threads) holds an A and an R, some A and some R lie in
+// different blocks (threads): if all A and all R sat in one block, the other
+// block's instances could only be W.  Conversely every racing pair is of one of
+// the two kinds.  oracle_brute() applies the pair predicate to every pair
+// instead, so the two can be compared on small models.
 #include <algorithm>
 #include <cctype>
 #include <cstdint>
@@ -224,8 +232,8 @@ struct Parser {
       for (int64_t k = 0; k < nacc; ++k) {
         Access a;
         const std::string kd = next();
-        if (kd != "R" && kd != "W") throw std::runtime_error("bad access kind");
-        a.kind = kd == "W";
+        if (kd != "R" && kd != "W" && kd != "A") throw std::runtime_error("bad access kind");
+        a.kind = kd == "W" ? 1 : (kd == "A" ? 2 : 0);
         a.array = (int)integer();
         if (a.array < 0 || a.array >= (int)m.arrays.size()) throw std::runtime_error("bad array");
         int64_t nd = integer();
@@ -434,29 +442,44 @@ void put_witness(int64_t* out, const Inst& x, const Inst& y) {
   out[F_Y_BLOCK] = y.b; out[F_Y_THREAD] = y.t; out[F_Y_PHASE] = y.p; out[F_Y_KIND] = y.k;
 }
 
+enum { K_R = 0, K_W = 1, K_A = 2 };
+
+bool conflict(int64_t kx, int64_t ky) {
+  return kx == K_W || ky == K_W || (kx == K_A && ky == K_R) || (kx == K_R && ky == K_A);
+}
+
 bool races(const Inst& x, const Inst& y, int64_t bsize) {
   if (!x.same_cell(y)) return false;
   if (x.b * bsize + x.t == y.b * bsize + y.t) return false;
-  if (!(x.k == 1 || y.k == 1)) return false;
+  if (!conflict(x.k, y.k)) return false;
   return x.b != y.b || x.p == y.p;
 }
 
+// kinds present in a set of instances
+struct Kinds {
+  bool r = false, w = false, a = false;
+  void add(int64_t k) { r |= k == K_R; w |= k == K_W; a |= k == K_A; }
+  bool conf() const { return w || (a && r); }
+};
+
 // Cell-level test on one cell's sorted, duplicate-free instances [lo, hi).
 bool cell_racy(const std::vector<Inst>& v, size_t lo, size_t hi) {
-  bool two_blocks = false, anyW = false;
-  for (size_t i = lo; i < hi; ++i) { two_blocks |= v[i].b != v[lo].b; anyW |= v[i].k == 1; }
-  if (two_blocks && anyW) return true;
+  bool two_blocks = false;
+  Kinds all;
+  for (size_t i = lo; i < hi; ++i) { two_blocks |= v[i].b != v[lo].b; all.add(v[i].k); }
+  if (two_blocks && all.conf()) return true;
   // (b, p) groups are contiguous because the instances are sorted by (b, p, t, k)
   size_t g = lo;
   while (g < hi) {
     size_t h = g;
-    bool two_threads = false, gW = false;
+    bool two_threads = false;
+    Kinds gk;
     while (h < hi && v[h].b == v[g].b && v[h].p == v[g].p) {
       two_threads |= v[h].t != v[g].t;
-      gW |= v[h].k == 1;
+      gk.add(v[h].k);
       ++h;
     }
-    if (two_threads && gW) return true;
+    if (two_threads && gk.conf()) return true;
     g = h;
   }
   return false;
@@ -478,28 +501,27 @@ void cell_witness(const std::vector<Inst>& v, size_t lo, size_t hi, int64_t bsiz
         }
     throw std::runtime_error("cell_witness called on a race-free cell");
   }
-  // large cells: decide "x has a partner" from per-cell and per-(b, p) sets
-  std::map<int64_t, int64_t> block_count, wblock_count;
-  std::map<std::pair<int64_t, int64_t>, std::set<int64_t>> g_threads, g_wthreads;
+  // large cells: decide "x has a partner" from the blocks holding each kind and
+  // the threads holding each kind per (b, p) group
+  std::set<int64_t> kblocks[3];
+  std::map<std::pair<int64_t, int64_t>, std::set<int64_t>> kthreads[3];
   for (size_t i = lo; i < hi; ++i) {
-    block_count[v[i].b]++;
-    if (v[i].k == 1) wblock_count[v[i].b]++;
-    g_threads[{v[i].b, v[i].p}].insert(v[i].t);
-    if (v[i].k == 1) g_wthreads[{v[i].b, v[i].p}].insert(v[i].t);
+    kblocks[v[i].k].insert(v[i].b);
+    kthreads[v[i].k][{v[i].b, v[i].p}].insert(v[i].t);
   }
+  auto other = [](const std::set<int64_t>& s, int64_t mine) {
+    for (int64_t x : s) if (x != mine) return true;
+    return false;
+  };
   for (size_t i = lo; i < hi; ++i) {
     const Inst& c = v[i];
-    bool other_block = block_count.size() >= 2;   // some instance in a block != c.b
-    bool other_block_w = false;                   // some W in a block != c.b
-    for (auto& kv : wblock_count) if (kv.first != c.b) { other_block_w = true; break; }
-    bool cross = c.k == 1 ? other_block : other_block_w;
-    const std::set<int64_t>& th = g_threads[{c.b, c.p}];
-    bool other_thread = th.size() >= 2;
-    bool other_thread_w = false;
-    auto it = g_wthreads.find({c.b, c.p});
-    if (it != g_wthreads.end())
-      for (int64_t t : it->second) if (t != c.t) { other_thread_w = true; break; }
-    bool same = c.k == 1 ? other_thread : other_thread_w;
+    bool cross = false, same = false;
+    for (int k = 0; k < 3; ++k) {
+      if (!conflict(c.k, k)) continue;
+      cross |= other(kblocks[k], c.b);                       // a partner in another block
+      auto it = kthreads[k].find({c.b, c.p});
+      if (it != kthreads[k].end()) same |= other(it->second, c.t);   // another thread of the group
+    }
     if (cross || same) {
       x = c;
       for (size_t j = lo; j < hi; ++j)

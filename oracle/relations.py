@@ -24,6 +24,11 @@ interval), and a race is a conflicting pair that is concurrent:
 
     Race := ((Write . Read^-1) + (Write . Write^-1) + (Read . Write^-1)) * Concurrent
 
+Atomic read-modify-write accesses form a third relation, *Atomic*, which
+conflicts with plain reads and writes but not with itself (two atomics on one
+cell are ordered by the memory system): the conflicting pairs gain
+``(Atomic . Read^-1) + (Read . Atomic^-1) + (Atomic . Write^-1) + (Write . Atomic^-1)``.
+
 Nothing here is shared with the CUDA path or with ``oracle.cpp``: the
 statement instances are enumerated by this module's own expression evaluator.
 Only ``tests/`` import it.  Cost is quadratic in the instances of one cell, so
@@ -154,6 +159,7 @@ class SimtInstances:
         self.phase: Dict[Tuple, int] = {}
         self.read = Relation()
         self.write = Relation()
+        self.atomic = Relation()
         self.out_of_bounds: List[Tuple] = []
 
 
@@ -164,7 +170,7 @@ def simt_instances(m) -> SimtInstances:
     bs = bx_ * by_ * bz_
     tables = getattr(m, "tables", [])
     out = SimtInstances()
-    reads, writes = set(), set()
+    reads, writes, atomics = set(), set(), set()
     for bz, by, bx in product(range(gz), range(gy), range(gx)):
         b = bx + gx * (by + gy * bz)
         for tz, ty, tx in product(range(bz_), range(by_), range(bx_)):
@@ -202,10 +208,10 @@ def simt_instances(m) -> SimtInstances:
                         for v, n in zip(idx, arr.extents):
                             e = e * n + v
                         cell = (ac.array, b if arr.scope == "shared" else 0, e)
-                        (writes if ac.kind == "W" else reads).add((x, cell))
+                        {"W": writes, "A": atomics}.get(ac.kind, reads).add((x, cell))
 
                 visit(0)
-    out.read, out.write = Relation(reads), Relation(writes)
+    out.read, out.write, out.atomic = Relation(reads), Relation(writes), Relation(atomics)
     return out
 
 
@@ -213,9 +219,10 @@ def simt_instances(m) -> SimtInstances:
 # races as relations
 # ---------------------------------------------------------------------------
 def conflicts(inst: SimtInstances):
-    """The conflicting pairs with the cell they meet at and their access kinds:
-    a set of (x, kind_x, cell, y, kind_y) from ``Write . Read^-1`` (W, R),
-    ``Write . Write^-1`` (W, W) and ``Read . Write^-1`` (R, W).  The cell is
+    """The conflicting pairs with the cell they meet at and their access kinds
+    (R=0, W=1, A=2): a set of (x, kind_x, cell, y, kind_y) from ``Write .
+    Read^-1`` (W, R), ``Write . Write^-1`` (W, W), ``Read . Write^-1`` (R, W)
+    and the atomic compositions (A, R), (R, A), (A, W), (W, A).  The cell is
     kept (a composition through it) so that racy cells can be counted."""
     def through(a: Relation, b_inv: Relation, ka: int, kb: int):
         by_cell: Dict = {}
@@ -228,6 +235,10 @@ def conflicts(inst: SimtInstances):
     out.update(through(inst.write, inst.read.inverse(), 1, 0))
     out.update(through(inst.write, inst.write.inverse(), 1, 1))
     out.update(through(inst.read, inst.write.inverse(), 0, 1))
+    out.update(through(inst.atomic, inst.read.inverse(), 2, 0))
+    out.update(through(inst.read, inst.atomic.inverse(), 0, 2))
+    out.update(through(inst.atomic, inst.write.inverse(), 2, 1))
+    out.update(through(inst.write, inst.atomic.inverse(), 1, 2))
     return out
 
 

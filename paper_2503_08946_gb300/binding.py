@@ -34,7 +34,7 @@ STATUS_NAMES = {RC_OK: "RC_OK", RC_E_INVALID: "RC_E_INVALID", RC_E_KEY_OVERFLOW:
 RC_OP_CONST, RC_OP_TID, RC_OP_BID, RC_OP_PARAM, RC_OP_ITER, RC_OP_ADD, RC_OP_MUL, RC_OP_FDIV, \
     RC_OP_MOD, RC_OP_LOAD = range(10)
 RC_SCOPE_GLOBAL, RC_SCOPE_SHARED = 0, 1
-RC_READ, RC_WRITE = 0, 1
+RC_READ, RC_WRITE, RC_ATOMIC = 0, 1, 2
 RC_PATH_AUTO, RC_PATH_SORT, RC_PATH_HASH = 0, 1, 2
 RC_TEST_STALL_LOOKBACK = 1
 RC_TEST_FEW_SCAN_WARPS = 2
@@ -316,7 +316,7 @@ class _Desc:
                     idx[j] = self.expr(ie)
                 self.keep.append(idx)
                 accs[k].array = int(ac.array)
-                accs[k].kind = RC_WRITE if ac.kind == "W" else RC_READ
+                accs[k].kind = {"W": RC_WRITE, "A": RC_ATOMIC}.get(ac.kind, RC_READ)
                 accs[k].index = idx
             self.keep.append(accs)
             st.accesses = accs

@@ -70,7 +70,7 @@ def instances(m):
                             if bad:
                                 continue
                             s = b if arr.scope == "shared" else 0
-                            out.append((ac.array, s, e, b, p, t, 1 if ac.kind == "W" else 0))
+                            out.append((ac.array, s, e, b, p, t, {"W": 1, "A": 2}.get(ac.kind, 0)))
                         return
                     lp = st.loops[level]
                     v = ev(lp.lower, env)
@@ -83,14 +83,20 @@ def instances(m):
     return out, oob
 
 
+def conflict(kx, ky):
+    """Kinds R=0, W=1, A=2 (atomic): a W conflicts with everything, an A with
+    an R; two atomics do not conflict."""
+    return kx == 1 or ky == 1 or {kx, ky} == {0, 2}
+
+
 def race(x, y, bs):
-    """The pair predicate: same cell, different threads, a write, and
-    concurrent (different blocks or the same barrier interval)."""
+    """The pair predicate: same cell, different threads, conflicting kinds,
+    and concurrent (different blocks or the same barrier interval)."""
     if x[:3] != y[:3]:
         return False
     if x[3] * bs + x[5] == y[3] * bs + y[5]:
         return False
-    if not (x[6] == 1 or y[6] == 1):
+    if not conflict(x[6], y[6]):
         return False
     return x[3] != y[3] or x[4] == y[4]
 

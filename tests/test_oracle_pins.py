@@ -297,3 +297,65 @@ def test_gespmm_csr_uniform_rows_equal_uniform_model(L):
         a = oracle.check(w.ge_spmm_uniform(3, 64, 4, L, trailing_barrier=bar))
         b = oracle.check(w.ge_spmm_csr([L] * 3, 64, 4, trailing_barrier=bar))
         assert (a.status, a.instances, a.racy_cells, a.witness) == (b.status, b.instances, b.racy_cells, b.witness)
+
+
+# --------------------------------------------------------------------------
+# atomics: an atomic conflicts with plain reads and writes, not with atomics
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T,B,nb,bar,rb,plain,exp", [
+    (8, 4, 1, False, True, False, 4),     # two threads per bin: update vs read-back
+    (8, 4, 3, False, True, False, 12),
+    (8, 4, 1, True, True, False, 0),      # the barrier orders update and read-back
+    (4, 4, 1, False, True, False, 0),     # one thread per bin
+    (8, 4, 1, False, False, False, 0),    # atomics alone never race
+    (64, 8, 2, False, False, False, 0),
+    (8, 4, 1, True, True, True, 4),       # plain read-modify-write updates race
+])
+def test_atomic_histogram_closed_form(T, B, nb, bar, rb, plain, exp):
+    m = w.atomic_histogram(T, B, n_blocks=nb, barrier=bar, read_back=rb, plain=plain)
+    r = oracle.check(m)
+    assert r.racy_cells == exp
+    assert pyref.check(m)[1] == exp
+    assert oracle.brute(m).racy_cells == exp
+
+
+@pytest.mark.parametrize("T,nb,bar,exp", [(4, 1, True, 0), (4, 1, False, 1), (4, 2, True, 1), (1, 1, False, 0),
+                                          (1, 3, True, 1)])
+def test_atomic_counter_closed_form(T, nb, bar, exp):
+    m = w.atomic_counter(T, n_blocks=nb, barrier=bar)
+    assert oracle.check(m).racy_cells == exp
+    assert pyref.check(m)[1] == exp
+
+
+def test_atomic_counter_witness():
+    # one block, no barrier: thread 0's read (R) races with thread 1's increment (A)
+    r = oracle.check(w.atomic_counter(4, n_blocks=1, barrier=False))
+    assert r.witness == (0, 0, 0, (0, 0, 0, 0), (0, 0, 1, 2))
+
+
+@pytest.mark.parametrize("seed", range(120))
+def test_tiny_random_atomic_vs_python_bruteforce(seed):
+    m = w.tiny_random(seed, atomic=0.4)
+    st, cnt, best = pyref.check(m)
+    r = oracle.check(m)
+    rb = oracle.brute(m)
+    assert st == "ok" and r.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        exp = (x[0], x[1], x[2], (x[3], x[4], x[5], x[6]), (y[3], y[4], y[5], y[6]))
+        assert r.witness == exp == rb.witness
+
+
+def test_atomic_large_cell_witness():
+    """The oracle's summary witness path (cells of more than 4096 instances)
+    agrees with the pair-by-pair definition."""
+    for m, exp in [(w.atomic_counter(1024, n_blocks=6, barrier=True), 1),
+                   (w.atomic_counter(1024, n_blocks=1, barrier=False), 1),
+                   (w.atomic_histogram(1024, 1, n_blocks=5, barrier=False), 5)]:   # one shared bin per block
+        r, rb = oracle.check(m), oracle.brute(m)
+        assert r.racy_cells == rb.racy_cells == exp
+        assert r.witness == rb.witness

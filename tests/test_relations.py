@@ -145,3 +145,15 @@ def test_tiny_random_tables_relations_match(seed):
     assert got[0] == exp[0]
     if got[0] == "ok":
         assert got[1:] == exp[1:]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_tiny_random_atomic_relations_match(seed):
+    m = w.tiny_random(seed, atomic=0.4)
+    assert rel.race_check(m) == pyref.check(m)
+
+
+def test_atomic_closed_forms_as_relations():
+    assert rel.race_check(w.atomic_histogram(8, 4, barrier=False))[1] == 4
+    assert rel.race_check(w.atomic_histogram(8, 4, barrier=False, read_back=False))[1] == 0
+    assert rel.race_check(w.atomic_counter(4, n_blocks=2))[1] == 1

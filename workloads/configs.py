@@ -30,12 +30,13 @@ import math
 from typing import List, Optional, Tuple
 
 from .rng import SplitMix64
-from .spec import (GLOBAL, SHARED, Access, Array, Expr, Loop, Model, R, Stmt, W,
+from .spec import (GLOBAL, SHARED, A, Access, Array, Expr, Loop, Model, R, Stmt, W,
                    bid, const, it, load, param, tid)
 
 __all__ = [
     "reduction_tree", "transpose", "random_affine", "batch_models", "request_stream",
     "neighbor_write_read", "polyhedral_product", "ge_spmm_uniform", "ge_spmm_csr", "csr_row_lengths",
+    "atomic_histogram", "atomic_counter",
     "tiny_random", "tiny_random_tables",
     "RANDOM_AFFINE_ROW_GLOBAL", "RANDOM_AFFINE_ROW_SHARED",
 ]
@@ -78,6 +79,40 @@ def polyhedral_product(n: int, init_stmt: bool = False) -> Model:
         stmts = [S, T]
     return Model((1, 1, 1), (n, 1, 1), [A, B, C], stmts, n_phases=2 if init_stmt else 1,
                  name=f"polyprod_n{n}")
+
+
+def atomic_histogram(T: int, B: int, n_blocks: int = 1, barrier: bool = True, read_back: bool = True,
+                     plain: bool = False) -> Model:
+    """Per-block shared histogram: thread t adds to bin ``t mod B`` atomically
+    (a plain read-modify-write ``R`` + ``W`` with ``plain``), then reads its bin
+    back (``read_back``), after a barrier or in the same interval.
+
+    Racy cells: none with the barrier, none without a read-back of atomics;
+    otherwise ``n_blocks * B`` when ``T >= 2B`` (every bin has two threads, one
+    update races with the other's read), else none (one thread per bin).  With
+    ``plain`` updates and ``T >= 2B`` the bins race in any case (two writes)."""
+    hist = Array("hist", SHARED, (B,))
+    b_ = tid.x % B
+    upd = [Access(0, R, (b_,)), Access(0, W, (b_,))] if plain else [Access(0, A, (b_,))]
+    stmts = [Stmt(upd, phase=const(0), name="add")]
+    if read_back:
+        stmts.append(Stmt([Access(0, R, (b_,))], phase=const(1 if barrier else 0), name="read"))
+    return Model((n_blocks, 1, 1), (T, 1, 1), [hist], stmts, n_phases=2 if barrier else 1,
+                 name=f"hist_T{T}_B{B}_{'bar' if barrier else 'nobar'}{'_plain' if plain else ''}")
+
+
+def atomic_counter(T: int, n_blocks: int = 1, barrier: bool = True) -> Model:
+    """Every thread increments one global counter atomically; thread 0 of each
+    block then reads it (after a barrier, or in the same interval).
+
+    Racy cells: 1 if the read can meet another thread's increment -- always
+    with two blocks or more (a barrier orders one block only), and in one
+    block without the barrier when ``T >= 2`` -- else 0."""
+    ctr = Array("counter", GLOBAL, (1,))
+    stmts = [Stmt([Access(0, A, (const(0),))], phase=const(0), name="inc"),
+             Stmt([Access(0, R, (const(0),))], guards=[-1 * tid.x], phase=const(1 if barrier else 0), name="read")]
+    return Model((n_blocks, 1, 1), (T, 1, 1), [ctr], stmts, n_phases=2 if barrier else 1,
+                 name=f"counter_T{T}_G{n_blocks}_{'bar' if barrier else 'nobar'}")
 
 
 def reduction_tree(barriers: bool = True, load_phase: bool = False, T: int = 256) -> Model:
@@ -412,12 +447,14 @@ def _tiny_expr(rng: SplitMix64, n_iter: int, allow_tid: bool = True, n_params: i
     return e
 
 
-def tiny_random(seed: int) -> Model:
+def tiny_random(seed: int, atomic: float = 0.0) -> Model:
     """A tiny random model (a few hundred instances at most) that exercises
     2-D grids and blocks, shared and global arrays, multi-dimensional indices,
     loops whose bounds depend on tid / bid / outer iterators, steps > 1, guards,
     floor division and modulo, and phases that depend on bid and uniform loop
-    iterators.  Every index is reduced modulo its extent, so it is in bounds."""
+    iterators.  Every index is reduced modulo its extent, so it is in bounds.
+    With ``atomic`` > 0 an access is atomic with that probability, a write
+    with probability 0.2 and a read otherwise."""
     rng = SplitMix64(0x7111 ^ (seed * 0x9E3779B97F4A7C15))
     grid = (rng.uniform_int(1, 3), rng.uniform_int(1, 2), 1)
     block = (rng.uniform_int(1, 4), rng.uniform_int(1, 3), rng.uniform_int(1, 2))
@@ -461,7 +498,12 @@ def tiny_random(seed: int) -> Model:
         for _ in range(rng.uniform_int(1, 3)):
             a = rng.below(n_arr)
             idx = tuple(_tiny_expr(rng, depth) % e for e in arrays[a].extents)
-            accs.append(Access(a, W if rng.chance(0.4) else R, idx))
+            if atomic > 0.0:
+                u = rng.random()
+                kind = A if u < atomic else (W if u < atomic + 0.2 else R)
+            else:
+                kind = W if rng.chance(0.4) else R
+            accs.append(Access(a, kind, idx))
         stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, name=f"t{s}"))
     return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tiny{seed}")
 

@@ -26,11 +26,12 @@ from typing import List, Sequence, Tuple, Union
 
 __all__ = [
     "Expr", "E", "tid", "bid", "param", "it", "const", "load",
-    "Array", "Loop", "Access", "Stmt", "Model", "R", "W", "GLOBAL", "SHARED",
+    "Array", "Loop", "Access", "Stmt", "Model", "R", "W", "A", "GLOBAL", "SHARED",
 ]
 
 R = "R"
 W = "W"
+A = "A"   # atomic read-modify-write: conflicts with plain reads and writes, not with atomics
 GLOBAL = "global"
 SHARED = "shared"
 
@@ -204,15 +205,16 @@ class Loop:
 
 @dataclass
 class Access:
-    """One access relation ``Stmt[iters] -> array[index]`` of kind R or W."""
+    """One access relation ``Stmt[iters] -> array[index]`` of kind R, W or A
+    (atomic read-modify-write)."""
     array: int
     kind: str
     index: Tuple[Expr, ...]
 
     def __post_init__(self):
         self.index = tuple(Expr.wrap(e) for e in self.index)
-        if self.kind not in (R, W):
-            raise ValueError("kind must be 'R' or 'W'")
+        if self.kind not in (R, W, A):
+            raise ValueError("kind must be 'R', 'W' or 'A'")
 
 
 @dataclass
