@@ -17,14 +17,17 @@
  * SIMT threads this library reads concurrency as the CUDA barrier rule):
  *   instances x, y race  iff  same (array, scope instance, element)
  *                          and gtid_x != gtid_y
- *                          and (x writes or y writes)
- *                          and (block_x != block_y or phase_x == phase_y).
+ *                          and their kinds conflict
+ *                          and (block_x != block_y or phase_x == phase_y),
+ * where kinds are R (read), W (write) and A (atomic read-modify-write) and two
+ * kinds conflict iff one is W, or one is A and the other R (two atomics on one
+ * cell are ordered by the memory system).
  * A shared array has one instance per block (indexed block-locally), a global
  * array one for the grid.  The phase of an instance is the number of block
  * barriers its thread passed before it; blocks are never ordered against each
  * other.  Count = number of distinct racy cells.  Witness = the
  * lexicographically smallest racing pair (x, y), x < y, in the order
- * (array, scope instance, element, block, phase, thread, kind R<W).
+ * (array, scope instance, element, block, phase, thread, kind R<W<A).
  *
  * Conventions for every entry point:
  *  - All calls return an rc_status; none aborts, throws or prints.
@@ -104,7 +107,7 @@ typedef struct rc_insn { int32_t op; int32_t arg; int64_t imm; } rc_insn;
 typedef struct rc_expr { const rc_insn* code; uint32_t len; } rc_expr;
 
 enum { RC_SCOPE_GLOBAL = 0, RC_SCOPE_SHARED = 1 };
-enum { RC_READ = 0, RC_WRITE = 1 };
+enum { RC_READ = 0, RC_WRITE = 1, RC_ATOMIC = 2 };
 
 /* for (v = lower; v < upper; v += step): bounds may use tid, bid, params and
  * the iterators of outer loops; step > 0. */
@@ -113,7 +116,10 @@ typedef struct rc_loop { rc_expr lower; rc_expr upper; int64_t step; } rc_loop;
 /* One access relation: array[index[0]]...[index[ndims-1]], row-major. */
 typedef struct rc_access {
   uint32_t array;          /* index into rc_model_desc.arrays                     */
-  uint32_t kind;           /* RC_READ or RC_WRITE                                 */
+  uint32_t kind;           /* RC_READ, RC_WRITE or RC_ATOMIC.  A model with atomic
+                              accesses has a 2-bit kind field (R = 0, W = 1, A = 2)
+                              and at most 16 barrier intervals (RC_E_UNSUPPORTED
+                              otherwise)                                           */
   const rc_expr* index;    /* ndims expressions (ndims of the array)              */
 } rc_access;
 
@@ -267,7 +273,7 @@ enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2, RC_OPT_CHUNKED = 4 };
 typedef struct rc_inst {
   uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
   uint32_t thread;         /* linear thread index in the block tx + bx*(ty + by*tz) */
-  uint32_t kind;           /* RC_READ / RC_WRITE                                   */
+  uint32_t kind;           /* RC_READ / RC_WRITE / RC_ATOMIC                       */
   int64_t phase;
   uint64_t gtid;           /* block * blockSize + thread                           */
 } rc_inst;

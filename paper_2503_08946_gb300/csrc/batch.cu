@@ -32,14 +32,14 @@ static_assert(kExpandThreadsHost == kExpandThreads, "host and device chunk sizes
 struct BatchSink {
   uint64_t* keys;
   uint64_t cell_base;
-  uint32_t mcs, mps, mbs;            // model field shifts (thread field at bit 1)
+  uint32_t mcs, mps, mbs, mts;       // model field shifts (thread field at mts = its kind bits)
   uint64_t pm, bm, tm;               // model field masks
-  uint32_t bcs, bps, bbs;            // batch field shifts
+  uint32_t bcs, bps, bbs, bts;       // batch field shifts
   __device__ __forceinline__ void put(uint64_t i, uint64_t key, uint64_t) {
     if (key != kSentinel) {
       const uint64_t cell = key >> mcs;
-      const uint64_t ph = (key >> mps) & pm, b = (key >> mbs) & bm, t = (key >> 1) & tm;
-      key = ((cell_base + cell) << bcs) | (ph << bps) | (b << bbs) | (t << 1) | (key & 1ull);
+      const uint64_t ph = (key >> mps) & pm, b = (key >> mbs) & bm, t = (key >> mts) & tm;
+      key = ((cell_base + cell) << bcs) | (ph << bps) | (b << bbs) | (t << bts) | (key & ((1ull << mts) - 1ull));
     }
     keys[i] = key;
   }
@@ -90,12 +90,14 @@ __global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchAr
         sink.mcs = B.cell_shift;
         sink.mps = B.phase_shift;
         sink.mbs = B.block_shift;
+        sink.mts = B.thread_shift;
         sink.pm = (1ull << B.phase_bits) - 1;
         sink.bm = (1ull << B.block_bits) - 1;
         sink.tm = (1ull << B.thread_bits) - 1;
         sink.bcs = a.cell_shift;
         sink.bps = a.phase_shift;
         sink.bbs = a.block_shift;
+        sink.bts = a.thread_shift;
         const ThreadVars tv = thread_vars(M, g);
         for (uint32_t s = 0; s < B.n_stmts; ++s) {
           const DevStmt& S = M.stmts[s];

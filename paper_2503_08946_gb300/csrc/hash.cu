@@ -3,13 +3,13 @@
 //
 // Every access instance (cell, phase, block, thread, kind) updates two
 // lock-free tables (linear probing, keys claimed by atomicCAS):
-//   group table, keyed by (cell, phase):  word = [gtid0 | W | MULTI | VALID]
-//   cell table,  keyed by cell:           word = [block0 | RACY | W | MULTI_B | VALID]
+//   group table, keyed by (cell, phase):  word = [gtid0 | R | A | RACY | W | MULTI | VALID]
+//   cell table,  keyed by cell:           word = [block0 | R | A | RACY | W | MULTI_B | VALID]
 // Words only gain bits, by atomicCAS, so the instance whose CAS first makes a
-// group "two threads and a write" (MULTI & W) or a cell "two blocks and a
-// write" (MULTI_B & W) sees that transition, and it alone sets the cell's RACY
-// bit with atomicOr and counts the cell.  This is the cell-level form of the
-// pair rule (include/rc.h); it gives the same verdict as the sort path, and
+// group "two threads and a conflict" (MULTI and (W, or A and R)) or a cell "two
+// blocks and a conflict" sees that transition, and it alone sets the cell's
+// RACY bit with atomicOr and counts the cell.  This is the cell-level form of
+// the pair rule (include/rc.h); it gives the same verdict as the sort path, and
 // without early exit the same count.  The smallest racy cell is kept with
 // atomicMin; its instances are then collected by a filtered re-expansion and
 // the K4 witness reductions run on them.
@@ -27,7 +27,14 @@ namespace rc {
 namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
-constexpr unsigned long long kValid = 1ull, kMulti = 2ull, kWrite = 4ull, kRacy = 8ull;
+constexpr unsigned long long kValid = 1ull, kMulti = 2ull, kWrite = 4ull, kRacy = 8ull, kAtomic = 16ull,
+                             kRead = 32ull;
+constexpr int kIdShift = 6;   // identity (gtid or block) above the flags
+
+// two identities and a conflict: a write, or an atomic and a plain read
+__device__ __forceinline__ bool word_racy(unsigned long long w) {
+  return (w & kMulti) && ((w & kWrite) || ((w & kAtomic) && (w & kRead)));
+}
 
 // SplitMix64 finalizer as the table hash (Steele, Lea, Flood 2014).
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -52,17 +59,17 @@ __device__ __forceinline__ int64_t find_slot(unsigned long long* keys, uint64_t 
   return -1;
 }
 
-// Fold identity `id` (stored from bit `id_shift`) and kind w into a word; true if
-// this call made the word reach (MULTI & WRITE).
-__device__ __forceinline__ bool word_update(unsigned long long* word, uint64_t id, int id_shift, bool w) {
+// Fold identity `id` and the kind flag kf (kWrite, kAtomic or kRead) into a
+// word; true if this call made the word racy (word_racy).
+__device__ __forceinline__ bool word_update(unsigned long long* word, uint64_t id, unsigned long long kf) {
   unsigned long long old = __ldcg(word);
   while (true) {
     unsigned long long nw;
-    if (!(old & kValid)) nw = kValid | ((unsigned long long)id << id_shift) | (w ? kWrite : 0ull);
-    else nw = old | (((old >> id_shift) != id) ? kMulti : 0ull) | (w ? kWrite : 0ull);
+    if (!(old & kValid)) nw = kValid | ((unsigned long long)id << kIdShift) | kf;
+    else nw = old | (((old >> kIdShift) != id) ? kMulti : 0ull) | kf;
     if (nw == old) return false;
     const unsigned long long prev = atomicCAS(word, old, nw);
-    if (prev == old) return (nw & (kMulti | kWrite)) == (kMulti | kWrite) && (old & (kMulti | kWrite)) != (kMulti | kWrite);
+    if (prev == old) return word_racy(nw) && !word_racy(old);
     old = prev;
   }
 }
@@ -77,13 +84,15 @@ struct HashSink {
     const uint64_t cp = key >> m.phase_shift;
     const uint64_t b = (key >> m.block_shift) & ((1ull << m.block_bits) - 1ull);
     const uint64_t t = (key >> m.thread_shift) & ((1ull << m.thread_bits) - 1ull);
-    const bool w = (key & 1ull) != 0;
+    // kind field: R = 0, W = 1, A = 2 (thread_shift bits wide)
+    const unsigned kd = (unsigned)(key & ((1ull << m.thread_shift) - 1ull));
+    const unsigned long long kf = kd == 1u ? kWrite : (kd == 2u ? kAtomic : kRead);
     const int64_t gs = find_slot(h.gkey, h.gmask, cp, &h.res->err);
     const int64_t cs = find_slot(h.ckey, h.cmask, cell, &h.res->err);
     if (gs < 0 || cs < 0) return;
-    // group identity: gtid (stored from bit 3 in a word whose low bits are flags)
-    const bool bg = word_update(h.gword + gs, b * m.bs + t, 3, w);
-    const bool bc = word_update(h.cword + cs, b, 4, w);
+    // group identity: gtid; cell identity: block
+    const bool bg = word_update(h.gword + gs, b * m.bs + t, kf);
+    const bool bc = word_update(h.cword + cs, b, kf);
     if (bg || bc) {
       const unsigned long long old = atomicOr(h.cword + cs, kRacy);
       if (!(old & kRacy)) {

@@ -50,6 +50,7 @@ struct BatchModel {              // one model of a batch (device table entry)
   uint32_t n_stmts, n_chunks;    // statements, thread chunks (expansion units)
   uint32_t cell_shift, phase_shift, block_shift;   // the model's key layout
   uint32_t phase_bits, block_bits, thread_bits;
+  uint32_t thread_shift;         // = the model's kind field bits
 };
 struct BatchArgs {
   const BatchModel* models;
@@ -59,6 +60,7 @@ struct BatchArgs {
   uint64_t* keys;                // batch key buffer
   DevResult* res;                // one per model
   uint32_t cell_shift, phase_shift, block_shift;   // batch key layout
+  uint32_t thread_shift;                           // = the batch's kind field bits
 };
 cudaError_t launch_batch_expand(const BatchArgs& a, cudaStream_t st);
 cudaError_t launch_batch_errors(const DevResult* pack, DevResult* res, uint32_t n, cudaStream_t st);

@@ -277,15 +277,23 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   }
   m->total_cells = cells_total;
 
-  // key layout [cell | phase | block | thread | kind]
+  // key layout [cell | phase | block | thread | kind]; the kind field is 2 bits
+  // (R = 0, W = 1, A = 2) when some access is atomic, else 1 bit
+  bool has_atomic = false;
+  for (uint32_t s = 0; s < d->n_stmts; ++s)
+    for (uint32_t a = 0; a < d->stmts[s].n_accesses && d->stmts[s].accesses; ++a)
+      if (d->stmts[s].accesses[a].kind == RC_ATOMIC) has_atomic = true;
+  m->has_atomic = has_atomic;
   h.kind_shift = 0;
-  h.thread_shift = 1;
+  h.thread_shift = has_atomic ? 2 : 1;
   h.thread_bits = bit_length(bs - 1);
   h.block_shift = h.thread_shift + h.thread_bits;
   h.block_bits = bit_length(nb - 1);
   h.phase_shift = h.block_shift + h.block_bits;
   h.phase_bits = bit_length((uint64_t)d->n_phases - 1);
   if (h.phase_bits > (uint32_t)kMaxPhaseBits) return RC_E_UNSUPPORTED;
+  // atomics are scanned by the phase-table scan only (at most 16 intervals)
+  if (has_atomic && h.phase_bits > (uint32_t)kScanTablePhaseBits) return RC_E_UNSUPPORTED;
   h.cell_shift = h.phase_shift + h.phase_bits;
   // one more value than the cells so the all-ones cell field is never a valid cell
   h.cell_bits = bit_length(cells_total);
@@ -299,12 +307,13 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.sort_lo = h.phase_bits <= kScanTablePhaseBits ? h.cell_shift : h.phase_shift;
   h.sort_hi = h.cell_shift + h.cell_bits;
 
-  // arrays that some statement writes; a cell of any other array has no write
-  // and cannot race, so its instances are counted and bounds-checked but make no key
+  // arrays that some statement writes or updates atomically; a cell of any
+  // other array is only read and cannot race, so its instances are counted and
+  // bounds-checked but make no key
   std::vector<bool> written(d->n_arrays, false);
   for (uint32_t s = 0; s < d->n_stmts; ++s)
     for (uint32_t a = 0; a < d->stmts[s].n_accesses && d->stmts[s].accesses; ++a)
-      if (d->stmts[s].accesses[a].kind == RC_WRITE && d->stmts[s].accesses[a].array < d->n_arrays)
+      if (d->stmts[s].accesses[a].kind != RC_READ && d->stmts[s].accesses[a].array < d->n_arrays)
         written[d->stmts[s].accesses[a].array] = true;
 
   // statements
@@ -353,7 +362,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     std::vector<std::vector<Lin>> idx(S.n_accesses);
     for (uint32_t a = 0; a < S.n_accesses; ++a) {
       const rc_access& A = S.accesses[a];
-      if (A.array >= d->n_arrays || (A.kind != RC_READ && A.kind != RC_WRITE) || !A.index)
+      if (A.array >= d->n_arrays || (A.kind != RC_READ && A.kind != RC_WRITE && A.kind != RC_ATOMIC) || !A.index)
         return RC_E_INVALID;
       idx[a].resize(d->arrays[A.array].ndims);
       for (uint32_t k = 0; k < d->arrays[A.array].ndims; ++k)

@@ -156,6 +156,8 @@ struct DevResult {
   unsigned long long x_rank;       // witness x as (p, t, k) packed; ~0 = none
   unsigned long long y_rank;       // witness y as (b, p, t, k) packed; ~0 = none
   unsigned int minb, maxb, minWb, maxWb, anyW, err;
+  // witness summary of atomic and plain-read instances (blocks holding each)
+  unsigned int minAb, maxAb, anyA, minRb, maxRb, anyR;
   unsigned long long n_keys;       // keys in the sorted buffer
   unsigned long long sorted_buf;   // index (0/1) of the buffer that holds the sorted keys
   unsigned long long hash_cell;    // hash path: smallest racy cell found; ~0 = none
@@ -164,6 +166,10 @@ struct DevResult {
   unsigned long long pad[2];
 };
 static_assert(sizeof(DevResult) <= 256, "result record must fit its slot");
+
+// words of one witness phase-group record (scan.cu): [mint, maxt] and per
+// access kind (R, W, A) [min thread, max thread, any]
+constexpr unsigned kWitnessGroupWords = 11;
 
 enum DevError : unsigned int {
   kErrLookbackTimeout = 1u,
@@ -349,6 +355,7 @@ struct Model {
   // kKeyBits: checks run in cell-range chunks whose rebased cell field has
   // host.cell_bits bits (the width left beside the other fields)
   bool wide = false;
+  bool has_atomic = false;        // some access is atomic: 2-bit kind field
   // sections of the program image (byte offsets), for the kernel generator
   size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null

@@ -163,7 +163,7 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
     p->nfilt_off = off;
     off = align256(off + 8);
     p->group_off = off;
-    off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
+    off = align256(off + ((size_t)1 << m.host.phase_bits) * rc::kWitnessGroupWords * sizeof(unsigned int));
     p->total = off;
     return;
   }
@@ -203,7 +203,7 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   p->long_off = off;   // cells handed to the long-cell pass
   off = align256(off + (size_t)p->long_cap * 8);
   p->group_off = off;
-  off = align256(off + ((size_t)1 << m.host.phase_bits) * 5 * sizeof(unsigned int));
+  off = align256(off + ((size_t)1 << m.host.phase_bits) * rc::kWitnessGroupWords * sizeof(unsigned int));
   p->total = off;
 }
 
@@ -383,10 +383,11 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   return RC_OK;
 }
 
-// cell_base: first batch cell of the model (0 for a single check); tb / pb:
-// thread and phase widths of the keys the witness ranks were taken from.
+// cell_base: first batch cell of the model (0 for a single check); tb / pb /
+// kb: thread, phase and kind widths of the keys the witness ranks were taken
+// from.
 void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, uint64_t cell_base, uint32_t tb,
-                   uint32_t pb) {
+                   uint32_t pb, uint32_t kb = 1) {
   std::memset(out, 0, sizeof(*out));
   out->instances = r.instances;
   if (r.err & rc::kErrLookbackTimeout) {
@@ -418,17 +419,17 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
   out->w_array = (uint32_t)a;
   out->w_scope = m.array_shared[a] ? rem / m.array_cells[a] : 0;
   out->w_addr = m.array_shared[a] ? rem % m.array_cells[a] : rem;
-  const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1;
+  const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1, kmask = (1ull << kb) - 1;
   const uint64_t bs = m.host.bs;
   out->x.block = r.minb;
-  out->x.kind = (uint32_t)(r.x_rank & 1ull);
-  out->x.thread = (uint32_t)((r.x_rank >> 1) & tmask);
-  out->x.phase = (int64_t)((r.x_rank >> (tb + 1)) & pmask);
+  out->x.kind = (uint32_t)(r.x_rank & kmask);
+  out->x.thread = (uint32_t)((r.x_rank >> kb) & tmask);
+  out->x.phase = (int64_t)((r.x_rank >> (tb + kb)) & pmask);
   out->x.gtid = out->x.block * bs + out->x.thread;
-  out->y.kind = (uint32_t)(r.y_rank & 1ull);
-  out->y.thread = (uint32_t)((r.y_rank >> 1) & tmask);
-  out->y.phase = (int64_t)((r.y_rank >> (tb + 1)) & pmask);
-  out->y.block = r.y_rank >> (pb + tb + 1);
+  out->y.kind = (uint32_t)(r.y_rank & kmask);
+  out->y.thread = (uint32_t)((r.y_rank >> kb) & tmask);
+  out->y.phase = (int64_t)((r.y_rank >> (tb + kb)) & pmask);
+  out->y.block = r.y_rank >> (pb + tb + kb);
   out->y.gtid = out->y.block * bs + out->y.thread;
 }
 
@@ -702,7 +703,7 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
 // Merge of a chunked ticket's records into one result.
 void decode_chunked(const rc_ticket_s* t, rc_result* out) {
   const rc::Model& m = t->models[0]->m;
-  decode_result(t->host[0], m, out, 0, m.host.thread_bits, m.host.phase_bits);
+  decode_result(t->host[0], m, out, 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift);
   if (out->status != RC_OK) return;
   const uint64_t instances = out->instances;
   out->racy_cells = 0;
@@ -711,7 +712,8 @@ void decode_chunked(const rc_ticket_s* t, rc_result* out) {
   for (size_t k = 0; k + 1 < t->n; ++k) {
     rc_result part;
     // cell_base = -chunk start: the scan's cells are relative to the chunk
-    decode_result(t->host[1 + k], m, &part, (uint64_t)0 - t->chunk_lo[k], m.host.thread_bits, m.host.phase_bits);
+    decode_result(t->host[1 + k], m, &part, (uint64_t)0 - t->chunk_lo[k], m.host.thread_bits, m.host.phase_bits,
+                  m.host.thread_shift);
     if (t->host[1 + k].err & rc::kErrChunkOverflow) part.status = RC_E_NOMEM;
     if (part.status != RC_OK) {
       std::memset(out, 0, sizeof(*out));
@@ -737,6 +739,7 @@ void decode_chunked(const rc_ticket_s* t, rc_result* out) {
 struct BatchPack {
   size_t i0 = 0, i1 = 0;               // models [i0, i1)
   uint32_t tb = 0, bb = 0, pb = 0, cell_bits = 0;
+  uint32_t kb = 1;                     // kind field bits (2 if some model has atomics)
   uint64_t total_cells = 0, n_keys = 0, n_units = 0;
   rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
 };
@@ -762,10 +765,13 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     if (open) {
       const uint32_t tb = std::max(cur.tb, h.thread_bits), bb = std::max(cur.bb, h.block_bits);
       const uint32_t pb = std::max(cur.pb, h.phase_bits);
+      const uint32_t kb = std::max(cur.kb, h.thread_shift);
       const uint64_t cells = cur.total_cells + m.total_cells;
       const uint32_t cb = rc::bit_length(cells);
-      if (cells >= cur.total_cells && 1 + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
-        cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.total_cells = cells; cur.cell_bits = cb;
+      // a model with atomics joins only a pack scanned with phase tables
+      const bool table_ok = kb == 1 || pb <= (uint32_t)rc::kScanTablePhaseBits;
+      if (cells >= cur.total_cells && table_ok && kb + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
+        cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.kb = kb; cur.total_cells = cells; cur.cell_bits = cb;
         cur.n_keys += m.key_slots;
         cur.n_units += chunks_of(m);
         cur.i1 = i + 1;
@@ -776,7 +782,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur = BatchPack();
     cur.i0 = i;
     cur.i1 = i + 1;
-    cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits;
+    cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits; cur.kb = h.thread_shift;
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
@@ -803,7 +809,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     rc::WorkspacePlan& p = k.p;
     std::memset(&p, 0, sizeof(p));
     p.n_keys = k.n_keys;
-    const uint32_t ps = 1 + k.tb + k.bb;
+    const uint32_t ps = k.kb + k.tb + k.bb;
     const uint32_t lo = k.pb <= rc::kScanTablePhaseBits ? ps + k.pb : ps;   // cell-only sort with phase tables
     plan_sort(lo, ps + k.pb + k.cell_bits, opts ? opts->digit_bits : 0, &p.sort);
     p.n_tiles = (k.n_keys + rc::kSortTile - 1) / rc::kSortTile;
@@ -832,7 +838,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     p.long_off = o;
     o = align256(o + (size_t)p.long_cap * 8);
     p.group_off = o;
-    o = align256(o + (k.i1 - k.i0) * ((size_t)1 << k.pb) * 5 * sizeof(unsigned int));
+    o = align256(o + (k.i1 - k.i0) * ((size_t)1 << k.pb) * rc::kWitnessGroupWords * sizeof(unsigned int));
     p.total = o;
     need = std::max(need, o);
   }
@@ -868,9 +874,10 @@ void fill_batch_tables(rc_model* const* models, const BatchLayout& L, void* uplo
       b.phase_bits = h.phase_bits;
       b.block_bits = h.block_bits;
       b.thread_bits = h.thread_bits;
+      b.thread_shift = h.thread_shift;
       cbase[i] = cb;
       (*cell_base)[i] = cb;
-      (*field_bits)[i] = k.tb | (k.pb << 8);
+      (*field_bits)[i] = k.tb | (k.pb << 8) | (k.kb << 16);
       key_base += m.key_slots;
       cb += m.total_cells;
       unit_base += b.n_chunks;
@@ -905,8 +912,9 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     ba.queue = queue;
     ba.keys = reinterpret_cast<uint64_t*>(ws + p.keys_off[0]);
     ba.res = res + k.i0;
-    ba.phase_shift = 1 + k.tb + k.bb;
-    ba.block_shift = 1 + k.tb;
+    ba.thread_shift = k.kb;
+    ba.phase_shift = k.kb + k.tb + k.bb;
+    ba.block_shift = k.kb + k.tb;
     ba.cell_shift = ba.phase_shift + k.pb;
     s = cuda_status(rc::launch_batch_expand(ba, st));
     if (s != RC_OK) break;
@@ -921,7 +929,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.cell_shift = ba.cell_shift;
     sa.phase_shift = ba.phase_shift;
     sa.block_shift = ba.block_shift;
-    sa.thread_shift = 1;
+    sa.thread_shift = k.kb;
     sa.phase_bits = k.pb;
     sa.block_bits = k.bb;
     sa.thread_bits = k.tb;
@@ -1536,9 +1544,10 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
   for (size_t i = 0; i < t->n; ++i) {
     const rc::Model& m = t->models[i]->m;
     if (t->cell_base.empty())
-      decode_result(t->host[i], m, &out[i], 0, m.host.thread_bits, m.host.phase_bits);
+      decode_result(t->host[i], m, &out[i], 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift);
     else
-      decode_result(t->host[i], m, &out[i], t->cell_base[i], t->field_bits[i] & 0xFFu, t->field_bits[i] >> 8);
+      decode_result(t->host[i], m, &out[i], t->cell_base[i], t->field_bits[i] & 0xFFu, (t->field_bits[i] >> 8) & 0xFFu,
+                    t->field_bits[i] >> 16);
   }
   ticket_put(t);
   return RC_OK;

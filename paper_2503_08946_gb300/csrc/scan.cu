@@ -6,7 +6,9 @@
 // sort, the instances of a cell are contiguous and grouped by phase.  A cell is
 // racy iff it has a write and (two blocks meet in it, or inside one block some
 // phase group holds two threads and a write) -- the cell-level form of the
-// pair rule in include/rc.h.
+// pair rule in include/rc.h.  With atomic accesses (models with a 2-bit kind
+// field, phase-table scan only) "a write" widens to "a conflict": a write, or
+// an atomic and a plain read.
 //
 // K3a (scan_cells_kernel): each warp owns a contiguous range of segments of
 //      32 x kScanRun keys, staged through shared memory with coalesced loads.
@@ -467,18 +469,27 @@ struct TFold {
   uint64_t fk;       // first key
   uint64_t start;    // its position
   unsigned bt0;      // its (block, thread)
-  unsigned f;        // kTW | kTMB
+  unsigned f;        // kTW | kTMB | kTA | kTR
   unsigned vmask;    // phases seen
   unsigned gm;       // phases with two (block, thread)
   unsigned gw;       // phases with a write
+  unsigned ga, gr;   // phases with an atomic / a plain read (atomic models only)
 };
-constexpr unsigned kTW = 1u, kTMB = 2u;
+constexpr unsigned kTW = 1u, kTMB = 2u, kTA = 4u, kTR = 8u;
 constexpr int kTabPhases = 1 << kScanTablePhaseBits;
 constexpr int kTabStride = 2 * kTabPhases + 1;     // per lane: prefix table, own table, pad
 
-__device__ __forceinline__ bool tfold_racy(const TFold& x) {
-  return (x.f & kTW) && ((x.f & kTMB) || (x.gm & x.gw) != 0u);
+__device__ __forceinline__ void tfold_clear(TFold& x) {
+  x.fk = 0; x.start = 0; x.bt0 = 0; x.f = 0; x.vmask = x.gm = x.gw = x.ga = x.gr = 0;
 }
+template <bool AT>
+__device__ __forceinline__ bool tfold_racy(const TFold& x) {
+  if (!AT) return (x.f & kTW) && ((x.f & kTMB) || (x.gm & x.gw) != 0u);
+  // a conflict across blocks, or in a phase group with two (block, thread)
+  const bool conf = (x.f & kTW) || ((x.f & kTA) && (x.f & kTR));
+  return (conf && (x.f & kTMB)) || (x.gm & (x.gw | (x.ga & x.gr))) != 0u;
+}
+template <bool AT>
 __device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
   TFold r;
   r.fk = __shfl_sync(FULL, s.fk, src);
@@ -488,12 +499,19 @@ __device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
   r.vmask = __shfl_sync(FULL, s.vmask, src);
   r.gm = __shfl_sync(FULL, s.gm, src);
   r.gw = __shfl_sync(FULL, s.gw, src);
+  if (AT) {
+    r.ga = __shfl_sync(FULL, s.ga, src);
+    r.gr = __shfl_sync(FULL, s.gr, src);
+  } else {
+    r.ga = r.gr = 0;
+  }
   return r;
 }
 // o (table otab) followed by p (table ptab), a part of the same cell; one lane
+template <bool AT>
 __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFold& p, const unsigned* ptab,
                                             uint32_t tb) {
-  unsigned f = o.f | (p.f & kTW);
+  unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
   if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   unsigned m = p.vmask;
   while (m) {
@@ -510,14 +528,19 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
     }
   }
   o.gw |= p.gw;
+  if (AT) {
+    o.ga |= p.ga;
+    o.gr |= p.gr;
+  }
   o.f = f;
 }
 // the warp's carried cell (warp-uniform state, table ctab) followed by p of
 // lane src (table ptab); all lanes, one phase per lane
+template <bool AT>
 __device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const TFold& p, const unsigned* ptab,
                                                  uint32_t tb) {
   const int lane = threadIdx.x & 31;
-  unsigned f = o.f | (p.f & kTW);
+  unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
   if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   bool g = false;
   if (lane < kTabPhases && (p.vmask >> lane) & 1u) {
@@ -532,11 +555,18 @@ __device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const
   o.gm |= __ballot_sync(FULL, g);
   o.vmask |= p.vmask;
   o.gw |= p.gw;
+  if (AT) {
+    o.ga |= p.ga;
+    o.gr |= p.gr;
+  }
   o.f = f;
   __syncwarp();
 }
 
+// AT: the model has atomic accesses (2-bit kind field: R = 0, W = 1, A = 2)
+template <bool AT>
 __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(ScanArgs a) {
+  constexpr uint32_t kKindBits = AT ? 2 : 1;
   __shared__ unsigned tabs[kScanWarps][32 * kTabStride];
   __shared__ unsigned ctabs[kScanWarps][kTabPhases];
   const uint32_t ps = a.phase_shift, tb = a.thread_bits;
@@ -552,7 +582,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
   unsigned long long count = 0, minstart = ~0ull;
   auto report = [&](const TFold& x) {
-    if (!tfold_racy(x)) return;
+    if (!tfold_racy<AT>(x)) return;
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
@@ -565,7 +595,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   bool carry = false;
   int carried = 0;
   TFold cc;
-  cc.fk = 0; cc.start = 0; cc.bt0 = 0; cc.f = 0; cc.vmask = cc.gm = cc.gw = 0;
+  tfold_clear(cc);
   for (uint64_t seg = seg0; seg < seg1; ++seg) {
     const uint64_t S = seg * kSegKeys;
     // (1) fold the run (prefix part in table 0, own cells in table 1)
@@ -574,7 +604,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     const uint64_t s = S + (uint64_t)lane * kScanRun;
     const uint64_t kp = (s > 0 && s - 1 < a.n) ? __ldg(a.keys + s - 1) : kSentinel;
     TFold P, cur;
-    P.fk = 0; P.start = 0; P.bt0 = 0; P.f = 0; P.vmask = P.gm = P.gw = 0;
+    tfold_clear(P);
     cur = P;
     cur.fk = kp;
     bool hasP = false, term = false, cur_empty = true, cur_prefix = true;
@@ -583,7 +613,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const uint64_t k = s + q < a.n ? __ldg(a.keys + s + q) : kSentinel;
       term |= k == kSentinel;
       const bool valid = !term;
-      const unsigned bt = (unsigned)(k >> 1) & btm;
+      const unsigned bt = (unsigned)(k >> kKindBits) & btm;
       const unsigned ph = (unsigned)(k >> ps) & pm;
       const bool same_cell = ((k ^ cur.fk) & cell_mask) == 0ull;
       const bool do_start = !same_cell || cur_empty;
@@ -609,6 +639,13 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         unsigned f = do_start ? 0u : cur.f;
         if (!do_start && ((bt ^ cur.bt0) >> tb) != 0u) f |= kTMB;
         if (k & 1ull) f |= kTW;
+        if (AT) {
+          const bool at = (k & 2ull) != 0ull, rd = (k & 3ull) == 0ull;
+          cur.ga = (do_start ? 0u : cur.ga) | (at ? bit : 0u);
+          cur.gr = (do_start ? 0u : cur.gr) | (rd ? bit : 0u);
+          if (at) f |= kTA;
+          if (rd) f |= kTR;
+        }
         cur.f = f;
         cur.fk = do_start ? k : cur.fk;
         cur.bt0 = do_start ? bt : cur.bt0;
@@ -635,8 +672,8 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       for (int src = 0; src < 32 && open; ++src) {
         const bool h = __shfl_sync(FULL, hasP, src);
         const bool full = __shfl_sync(FULL, pfull, src);
-        const TFold pp = tfold_shfl(P, src);
-        if (h) tfold_merge_warp(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
+        const TFold pp = tfold_shfl<AT>(P, src);
+        if (h) tfold_merge_warp<AT>(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
         if (!full) open = false;
       }
       if (!open) {
@@ -658,13 +695,13 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const int src = lane + d < 32 ? lane + d : 31;
       const bool h = __shfl_sync(FULL, hasP, src);
       const bool full = __shfl_sync(FULL, pfull, src);
-      const TFold pp = tfold_shfl(P, src);
+      const TFold pp = tfold_shfl<AT>(P, src);
       if (open) {
         if (lane + d >= 32) {
           open = false;
           open_end = true;
         } else {
-          if (h) tfold_merge(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
+          if (h) tfold_merge<AT>(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
           if (!full) {
             report(O);
             open = false;
@@ -676,7 +713,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     const unsigned OE = __ballot_sync(FULL, open_end);
     if (OE) {
       const int src = __ffs(OE) - 1;
-      cc = tfold_shfl(O, src);
+      cc = tfold_shfl<AT>(O, src);
       if (lane < kTabPhases) ctab[lane] = tabs[w][src * kTabStride + kTabPhases + lane];
       carry = true;
       carried = 0;
@@ -702,7 +739,9 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
 // thread) and write flags in shared memory.
 __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs a) {
   __shared__ unsigned mn[kTabPhases], mx[kTabPhases];
-  __shared__ unsigned s_gw, s_minb, s_maxb, s_w;
+  __shared__ unsigned s_gw, s_ga, s_gr, s_minb, s_maxb, s_w;
+  const uint32_t kb = a.thread_shift;   // kind field bits (R = 0, W = 1, A = 2)
+  const uint64_t kmask = (1ull << kb) - 1ull;
   const unsigned pm = (1u << a.phase_bits) - 1u;
   const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
   const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
@@ -714,7 +753,7 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
       mx[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) {
-      s_gw = 0;
+      s_gw = s_ga = s_gr = 0;
       s_minb = 0xffffffffu;
       s_maxb = 0;
       s_w = 0;
@@ -727,27 +766,32 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
         const uint64_t k = a.keys[pos];
         end = k == kSentinel || (k >> a.cell_shift) != cell;
         if (!end) {
-          const unsigned bt = (unsigned)(k >> 1) & btm;
+          const unsigned bt = (unsigned)(k >> kb) & btm;
           const unsigned ph = (unsigned)(k >> a.phase_shift) & pm;
+          const unsigned kd = (unsigned)(k & kmask);
           atomicMin(&mn[ph], bt);
           atomicMax(&mx[ph], bt);
           atomicMin(&s_minb, bt >> a.thread_bits);
           atomicMax(&s_maxb, bt >> a.thread_bits);
-          if (k & 1ull) {
+          if (kd == 1u) {
             atomicOr(&s_gw, 1u << ph);
             s_w = 1;
+          } else if (kd == 2u) {
+            atomicOr(&s_ga, 1u << ph);
+          } else {
+            atomicOr(&s_gr, 1u << ph);
           }
         }
       }
       if (__syncthreads_or(end)) break;
     }
     if (threadIdx.x == 0) {
-      bool racy = false;
-      if (s_w) {
-        racy = s_minb != s_maxb;
-        for (int ph = 0; ph < kTabPhases; ++ph)
-          if (((s_gw >> ph) & 1u) && mn[ph] != mx[ph]) racy = true;
-      }
+      // a conflict across blocks, or in a phase group with two (block, thread)
+      const bool conf = s_w || (s_ga && s_gr);
+      bool racy = conf && s_minb != s_maxb;
+      const unsigned gconf = s_gw | (s_ga & s_gr);
+      for (int ph = 0; ph < kTabPhases; ++ph)
+        if (((gconf >> ph) & 1u) && mn[ph] != mx[ph]) racy = true;
       if (racy) {
         DevResult* r = result_of(a, cell);
         atomicAdd(&r->racy_cells, 1ull);
@@ -774,25 +818,33 @@ __global__ void scan_finish_kernel(ScanArgs a) {
 // ---------------------------------------------------------------------------
 // K4 witness passes over [min_start, seg_end)
 // ---------------------------------------------------------------------------
+// Kind field (a.thread_shift bits): R = 0, W = 1, A = 2 (atomic).  Two kinds
+// conflict iff one is W, or one is A and the other R.
 struct Fields {
   unsigned b, p, t, k;
 };
 __device__ __forceinline__ Fields fields(const ScanArgs& a, uint64_t key) {
   Fields f;
-  f.k = (unsigned)(key & 1ull);
+  f.k = (unsigned)(key & ((1ull << a.thread_shift) - 1ull));
   f.t = (unsigned)(key >> a.thread_shift) & ((1u << a.thread_bits) - 1u);
   f.b = (unsigned)(key >> a.block_shift) & ((1u << a.block_bits) - 1u);
   f.p = (unsigned)(key >> a.phase_shift) & ((1u << a.phase_bits) - 1u);
   return f;
 }
+__device__ __forceinline__ bool kinds_conflict(unsigned kx, unsigned ky) {
+  return kx == 1u || ky == 1u || (kx ^ ky) == 2u;
+}
 
-// group record: [mint, maxt, minWt, maxWt, anyW]
+// group record of one phase of the lowest block: [mint, maxt] over all
+// instances, then per kind K (R, W, A) [minKt, maxKt, anyK]
+constexpr unsigned kGroupWords = kWitnessGroupWords;
 // Each kernel handles result blockIdx.y (one per model of a batch) with the
 // blocks of its x dimension.
 __device__ __forceinline__ unsigned* groups_of(const ScanArgs& a) {
-  return a.groups + (size_t)blockIdx.y * 5u * (1u << a.phase_bits);
+  return a.groups + (size_t)blockIdx.y * kGroupWords * (1u << a.phase_bits);
 }
 
+// the cell summary: blocks of all instances and of each kind
 __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
   const uint64_t s = r->min_start;
@@ -800,35 +852,50 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
   unsigned* groups = groups_of(a);
   if (s == ~0ull) return;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
-    groups[g * 5 + 0] = 0xffffffffu;
-    groups[g * 5 + 1] = 0;
-    groups[g * 5 + 2] = 0xffffffffu;
-    groups[g * 5 + 3] = 0;
-    groups[g * 5 + 4] = 0;
+    unsigned* gr = groups + g * kGroupWords;
+    gr[0] = 0xffffffffu;
+    gr[1] = 0;
+    for (int k = 0; k < 3; ++k) {
+      gr[2 + 3 * k] = 0xffffffffu;
+      gr[3 + 3 * k] = 0;
+      gr[4 + 3 * k] = 0;
+    }
   }
   const uint64_t e = r->seg_end;
-  unsigned minb = 0xffffffffu, maxb = 0, minWb = 0xffffffffu, maxWb = 0, anyW = 0;
+  unsigned minb = 0xffffffffu, maxb = 0;
+  unsigned kmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, kmax[3] = {0, 0, 0}, kany[3] = {0, 0, 0};
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     minb = min(minb, f.b);
     maxb = max(maxb, f.b);
-    if (f.k) {
-      minWb = min(minWb, f.b);
-      maxWb = max(maxWb, f.b);
-      anyW = 1;
-    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (f.k == (unsigned)k) {
+        kmin[k] = min(kmin[k], f.b);
+        kmax[k] = max(kmax[k], f.b);
+        kany[k] = 1;
+      }
   }
   minb = __reduce_min_sync(FULL, minb);
   maxb = __reduce_max_sync(FULL, maxb);
-  minWb = __reduce_min_sync(FULL, minWb);
-  maxWb = __reduce_max_sync(FULL, maxWb);
-  anyW = __reduce_or_sync(FULL, anyW);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    kmin[k] = __reduce_min_sync(FULL, kmin[k]);
+    kmax[k] = __reduce_max_sync(FULL, kmax[k]);
+    kany[k] = __reduce_or_sync(FULL, kany[k]);
+  }
   if ((threadIdx.x & 31) == 0) {
     atomicMin(&r->minb, minb);
     atomicMax(&r->maxb, maxb);
-    atomicMin(&r->minWb, minWb);
-    atomicMax(&r->maxWb, maxWb);
-    if (anyW) atomicOr(&r->anyW, 1u);
+    unsigned* mn[3] = {&r->minRb, &r->minWb, &r->minAb};
+    unsigned* mx[3] = {&r->maxRb, &r->maxWb, &r->maxAb};
+    unsigned* an[3] = {&r->anyR, &r->anyW, &r->anyA};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(mn[k], kmin[k]);
+      atomicMax(mx[k], kmax[k]);
+      if (kany[k]) atomicOr(an[k], 1u);
+    }
   }
 }
 
@@ -842,14 +909,13 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     if (f.b != b0) continue;
-    unsigned* g = groups + f.p * 5;
+    unsigned* g = groups + f.p * kGroupWords;
     atomicMin(&g[0], f.t);
     atomicMax(&g[1], f.t);
-    if (f.k) {
-      atomicMin(&g[2], f.t);
-      atomicMax(&g[3], f.t);
-      atomicOr(&g[4], 1u);
-    }
+    unsigned* gk = g + 2 + 3 * f.k;
+    atomicMin(&gk[0], f.t);
+    atomicMax(&gk[1], f.t);
+    atomicOr(&gk[2], 1u);
   }
 }
 
@@ -859,19 +925,28 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t e = r->seg_end;
-  const unsigned b0 = r->minb, maxb = r->maxb, minWb = r->minWb, maxWb = r->maxWb, anyW = r->anyW;
+  const unsigned b0 = r->minb;
+  const unsigned kminb[3] = {r->minRb, r->minWb, r->minAb}, kmaxb[3] = {r->maxRb, r->maxWb, r->maxAb};
+  const unsigned kany[3] = {r->anyR, r->anyW, r->anyA};
+  const uint32_t kb = a.thread_shift;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     if (f.b != b0) continue;
-    // a partner in another block (global cells; a shared cell has one block)
-    const bool cross = f.k ? (b0 != maxb) : (anyW && (minWb != f.b || maxWb != f.b));
-    // a partner of another thread in the same block and phase
-    const unsigned* g = groups + f.p * 5;
-    const bool same = f.k ? (g[0] != g[1]) : (g[4] && (g[2] != f.t || g[3] != f.t));
+    const unsigned* g = groups + f.p * kGroupWords;
+    bool cross = false, same = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (!kinds_conflict(f.k, (unsigned)k)) continue;
+      // a conflicting instance in another block (global cells; a shared cell has one block)
+      cross |= kany[k] && (kminb[k] != b0 || kmaxb[k] != b0);
+      // a conflicting instance of another thread in the same block and phase
+      const unsigned* gk = g + 2 + 3 * k;
+      same |= gk[2] && (gk[0] != f.t || gk[1] != f.t);
+    }
     if (cross || same) {
-      const unsigned long long rank = ((unsigned long long)f.p << (a.thread_bits + 1)) |
-                                      ((unsigned long long)f.t << 1) | f.k;
+      const unsigned long long rank = ((unsigned long long)f.p << (a.thread_bits + kb)) |
+                                      ((unsigned long long)f.t << kb) | f.k;
       best = rank < best ? rank : best;
     }
   }
@@ -890,20 +965,20 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;
   const unsigned b0 = r->minb;
+  const uint32_t kb = a.thread_shift;
   const unsigned long long xr = r->x_rank;
-  const unsigned xk = (unsigned)(xr & 1ull);
-  const unsigned xt = (unsigned)(xr >> 1) & ((1u << a.thread_bits) - 1u);
-  const unsigned xp = (unsigned)(xr >> (a.thread_bits + 1));
+  const unsigned xk = (unsigned)(xr & ((1ull << kb) - 1ull));
+  const unsigned xt = (unsigned)(xr >> kb) & ((1u << a.thread_bits) - 1u);
+  const unsigned xp = (unsigned)(xr >> (a.thread_bits + kb));
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     const bool other_thread = f.b != b0 || f.t != xt;
-    const bool write = xk || f.k;
     const bool concurrent = f.b != b0 || f.p == xp;
-    if (other_thread && write && concurrent) {
+    if (other_thread && kinds_conflict(xk, f.k) && concurrent) {
       const unsigned long long rank =
-          ((unsigned long long)f.b << (a.phase_bits + a.thread_bits + 1)) |
-          ((unsigned long long)f.p << (a.thread_bits + 1)) | ((unsigned long long)f.t << 1) | f.k;
+          ((unsigned long long)f.b << (a.phase_bits + a.thread_bits + kb)) |
+          ((unsigned long long)f.p << (a.thread_bits + kb)) | ((unsigned long long)f.t << kb) | f.k;
       best = rank < best ? rank : best;
     }
   }
@@ -932,6 +1007,9 @@ __global__ void init_result_kernel(DevResult* res, uint32_t n) {
     r->minWb = 0xffffffffu;
     r->maxWb = 0;
     r->anyW = 0;
+    r->minAb = r->minRb = 0xffffffffu;
+    r->maxAb = r->maxRb = 0;
+    r->anyA = r->anyR = 0;
     r->err = 0;
     r->n_keys = 0;
     r->sorted_buf = 0;
@@ -951,7 +1029,8 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   if (a.n > 0) {
     const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
-    if (a.phase_table) scan_cells_table_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
+    if (a.phase_table && a.thread_shift == 2) scan_cells_table_kernel<true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+    else if (a.phase_table) scan_cells_table_kernel<false><<<blocks, kScanWarps * 32, 0, st>>>(a);
     else scan_cells_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
