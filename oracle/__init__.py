@@ -34,6 +34,7 @@ FIELDS = [
     "x_block", "x_thread", "x_phase", "x_kind",
     "y_block", "y_thread", "y_phase", "y_kind",
     "oob_stmt", "oob_access", "oob_gtid", "oob_dim",
+    "x_wphase", "y_wphase",
 ]
 STATUS_OK, STATUS_INVALID, STATUS_OOB = 0, 1, 3
 
@@ -109,7 +110,10 @@ def model_text(m) -> str:
            "grid %d %d %d" % tuple(m.grid),
            "block %d %d %d" % tuple(m.block),
            "params %d %s" % (len(m.params), " ".join(str(int(p)) for p in m.params)),
-           "phases %d" % m.n_phases]
+           "phases %d" % m.n_phases,
+           "wphases %d" % getattr(m, "n_warp_phases", 1)]
+    gp = list(getattr(m, "grid_phase", None) or [])
+    out.append("gridphase %d %s" % (len(gp), " ".join(str(int(g)) for g in gp)))
     tables = getattr(m, "tables", None) or []
     out.append("tables %d" % len(tables))
     for t in tables:
@@ -122,6 +126,8 @@ def model_text(m) -> str:
     for s in m.stmts:
         out.append("stmt")
         out.append("phase " + _expr_text(s.phase))
+        wp = getattr(s, "warp_phase", None)
+        out.append("wphase " + (_expr_text(wp) if wp is not None else "0"))
         out.append("loops %d" % len(s.loops))
         for lp in s.loops:
             out.append("%s %s %d" % (_expr_text(lp.lower), _expr_text(lp.upper), lp.step))
@@ -158,6 +164,8 @@ class OracleResult:
     oob_access: int
     oob_gtid: int
     oob_dim: int
+    x_wphase: int
+    y_wphase: int
 
     @property
     def witness(self):

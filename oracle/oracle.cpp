@@ -17,7 +17,12 @@
 //    with s = b for shared arrays and s = 0 for global arrays, e the row-major
 //    element index, p the value of the statement's barrier-interval expression
 //    and k in {R=0, W=1, A=2} (A: an atomic read-modify-write).  gtid = b *
-//    blockSize + t.
+//    blockSize + t.  Each instance also carries its warp interval w (the
+//    number of warp barriers, __syncwarp, its thread passed inside the current
+//    block interval) and, through a table of the model, the grid interval
+//    g(p) of its block interval (the number of grid-wide barriers before it;
+//    a grid barrier also ends a block interval, so g is non-decreasing in p).
+//    The full tuple is (a, s, e, b, p, t, k, w), ordered in that order.
 //  * Dependences: the paper's RaW / WaW / WaR relations (Section "Using ISCC in
 //    Formal Analysis", the dependence test of the appendix listing) pair two
 //    instances that touch the same array cell with at least one write.  The
@@ -26,7 +31,12 @@
 //    different threads and (different blocks, or the same barrier interval).
 //    Hence x, y race iff
 //        (a, s, e) equal  and  gtid_x != gtid_y  and  conflict(k_x, k_y)
-//        and (b_x != b_y or p_x = p_y),
+//        and (b_x != b_y ? g(p_x) = g(p_y)
+//                        : p_x = p_y and (warp_x != warp_y or w_x = w_y)),
+//    with warp = t / 32: blocks are ordered only by grid barriers, two warps of
+//    one block only by block barriers, the threads of one warp also by warp
+//    barriers.  Without warp or grid barriers (w = 0, g = 0) this is
+//    (b_x != b_y or p_x = p_y).
 //    where two kinds conflict iff one is W, or one is A and the other R: an
 //    atomic modifies the cell (so it conflicts with plain reads and writes), and
 //    two atomics on one cell are ordered by the memory system (no race).
@@ -44,9 +54,14 @@
 //    (dimcode 0 = the interval, d+1 = index dimension d).
 //
 // Per cell the oracle uses the equivalent cell-level test
-//     racy(cell) <=> (>= 2 distinct blocks and conf(cell))
-//                 or (some (b, p) group G has >= 2 distinct threads and conf(G)),
+//     racy(cell) <=> (some grid interval G has >= 2 distinct blocks and conf(G))
+//                 or (some (b, p) group has >= 2 distinct warps and conf)
+//                 or (some (b, p, w) group has >= 2 distinct threads and conf),
 //     conf(S) = (S has a W) or (S has an A and an R),
+// (without warp and grid barriers: >= 2 blocks and conf(cell), or some (b, p)
+// group with >= 2 threads and conf).  The three kinds of groups are exactly the
+// sets whose members are pairwise concurrent across blocks, across warps, and
+// within one warp interval,
 // which follows from the pair predicate: a W in a multi-block cell races with an
 // instance of any other block, and a W in a (b, p) group with >= 2 threads races
 // with an instance of another thread of that group.  Without a W, if a set
@@ -89,6 +104,7 @@ struct Loop { Expr lower, upper; int64_t step; };
 struct Access { int kind; int array; std::vector<Expr> index; };
 struct Stmt {
   Expr phase;
+  Expr wphase;          // warp interval (empty: 0)
   std::vector<Loop> loops;
   std::vector<Expr> guards;
   std::vector<Access> accesses;
@@ -98,6 +114,8 @@ struct Model {
   int64_t grid[3], block[3];
   std::vector<int64_t> params;
   int64_t n_phases = 1;
+  int64_t n_wphases = 1;                      // warp intervals per block interval
+  std::vector<int64_t> grid_phase;            // grid interval of each block interval
   std::vector<std::vector<int64_t>> tables;   // integer tables read by loads (0 outside)
   std::vector<Array> arrays;
   std::vector<Stmt> stmts;
@@ -187,6 +205,13 @@ struct Parser {
     for (int64_t i = 0; i < np; ++i) m.params.push_back(integer());
     expect("phases");
     m.n_phases = integer();
+    expect("wphases");
+    m.n_wphases = integer();
+    expect("gridphase");
+    const int64_t ng = integer();
+    for (int64_t i = 0; i < ng; ++i) m.grid_phase.push_back(integer());
+    if (m.n_wphases < 1 || (ng != 0 && ng != m.n_phases)) throw std::runtime_error("bad sync description");
+    if (ng == 0) m.grid_phase.assign((size_t)m.n_phases, 0);
     expect("tables");
     int64_t nt = integer();
     for (int64_t t = 0; t < nt; ++t) {
@@ -214,6 +239,8 @@ struct Parser {
       expect("stmt");
       expect("phase");
       s.phase = expr();
+      expect("wphase");
+      s.wphase = expr();
       expect("loops");
       int64_t nl = integer();
       for (int64_t l = 0; l < nl; ++l) {
@@ -302,7 +329,7 @@ int64_t eval(const Expr& e, const Env& env) { return eval(e, e.root, env); }
 // instances
 // ----------------------------------------------------------------------------
 struct Inst {
-  int64_t a, s, e, b, p, t, k;
+  int64_t a, s, e, b, p, t, k, w;
   bool operator<(const Inst& o) const {
     if (a != o.a) return a < o.a;
     if (s != o.s) return s < o.s;
@@ -310,10 +337,11 @@ struct Inst {
     if (b != o.b) return b < o.b;
     if (p != o.p) return p < o.p;
     if (t != o.t) return t < o.t;
-    return k < o.k;
+    if (k != o.k) return k < o.k;
+    return w < o.w;
   }
   bool operator==(const Inst& o) const {
-    return a == o.a && s == o.s && e == o.e && b == o.b && p == o.p && t == o.t && k == o.k;
+    return a == o.a && s == o.s && e == o.e && b == o.b && p == o.p && t == o.t && k == o.k && w == o.w;
   }
   bool same_cell(const Inst& o) const { return a == o.a && s == o.s && e == o.e; }
 };
@@ -357,12 +385,17 @@ struct Enumerator {
 
   void emit(int64_t si, const Stmt& st, Env& env, int64_t b, int64_t t, int64_t gtid) {
     int64_t phase = eval(st.phase, env);
+    const int64_t wphase = st.wphase.root < 0 ? 0 : eval(st.wphase, env);
     for (size_t ai = 0; ai < st.accesses.size(); ++ai) {
       const Access& ac = st.accesses[ai];
       const Array& arr = m.arrays[ac.array];
       enumerated++;
       bool bad = false;
-      if (phase < 0 || phase >= m.n_phases) { oob.offer(si, (int64_t)ai, gtid, 0); bad = true; }
+      // an interval outside its range (block or warp interval) has dimcode 0
+      if (phase < 0 || phase >= m.n_phases || wphase < 0 || wphase >= m.n_wphases) {
+        oob.offer(si, (int64_t)ai, gtid, 0);
+        bad = true;
+      }
       int64_t e = 0;
       for (size_t d = 0; d < ac.index.size(); ++d) {
         int64_t v = eval(ac.index[d], env);
@@ -378,6 +411,7 @@ struct Enumerator {
       x.p = phase;
       x.t = t;
       x.k = ac.kind;
+      x.w = wphase;
       if (!range.all) {
         int64_t lin = cell_base[x.a] + x.s * cell_size[x.a] + x.e;
         if (lin < range.lo || lin >= range.hi) continue;
@@ -432,6 +466,7 @@ enum {
   F_X_BLOCK, F_X_THREAD, F_X_PHASE, F_X_KIND,
   F_Y_BLOCK, F_Y_THREAD, F_Y_PHASE, F_Y_KIND,
   F_OOB_STMT, F_OOB_ACCESS, F_OOB_GTID, F_OOB_DIM,
+  F_X_WPHASE, F_Y_WPHASE,
   F_COUNT
 };
 enum { ST_OK = 0, ST_INVALID = 1, ST_OOB = 3 };
@@ -440,6 +475,7 @@ void put_witness(int64_t* out, const Inst& x, const Inst& y) {
   out[F_W_ARRAY] = x.a; out[F_W_SCOPE] = x.s; out[F_W_ADDR] = x.e;
   out[F_X_BLOCK] = x.b; out[F_X_THREAD] = x.t; out[F_X_PHASE] = x.p; out[F_X_KIND] = x.k;
   out[F_Y_BLOCK] = y.b; out[F_Y_THREAD] = y.t; out[F_Y_PHASE] = y.p; out[F_Y_KIND] = y.k;
+  out[F_X_WPHASE] = x.w; out[F_Y_WPHASE] = y.w;
 }
 
 enum { K_R = 0, K_W = 1, K_A = 2 };
@@ -448,11 +484,19 @@ bool conflict(int64_t kx, int64_t ky) {
   return kx == K_W || ky == K_W || (kx == K_A && ky == K_R) || (kx == K_R && ky == K_A);
 }
 
-bool races(const Inst& x, const Inst& y, int64_t bsize) {
+constexpr int64_t kWarpSize = 32;
+
+// concurrency of two instances of distinct threads (see the header)
+bool concurrent(const Inst& x, const Inst& y, const Model& m) {
+  if (x.b != y.b) return m.grid_phase[x.p] == m.grid_phase[y.p];
+  return x.p == y.p && (x.t / kWarpSize != y.t / kWarpSize || x.w == y.w);
+}
+
+bool races(const Inst& x, const Inst& y, int64_t bsize, const Model& m) {
   if (!x.same_cell(y)) return false;
   if (x.b * bsize + x.t == y.b * bsize + y.t) return false;
   if (!conflict(x.k, y.k)) return false;
-  return x.b != y.b || x.p == y.p;
+  return concurrent(x, y, m);
 }
 
 // kinds present in a set of instances
@@ -462,8 +506,9 @@ struct Kinds {
   bool conf() const { return w || (a && r); }
 };
 
-// Cell-level test on one cell's sorted, duplicate-free instances [lo, hi).
-bool cell_racy(const std::vector<Inst>& v, size_t lo, size_t hi) {
+// Cell-level test without warp or grid barriers: two blocks and a conflict in
+// the cell, or a (b, p) group with two threads and a conflict.
+bool cell_racy_plain(const std::vector<Inst>& v, size_t lo, size_t hi) {
   bool two_blocks = false;
   Kinds all;
   for (size_t i = lo; i < hi; ++i) { two_blocks |= v[i].b != v[lo].b; all.add(v[i].k); }
@@ -485,14 +530,51 @@ bool cell_racy(const std::vector<Inst>& v, size_t lo, size_t hi) {
   return false;
 }
 
+bool has_sync_scopes(const Model& m) {
+  if (m.n_wphases > 1) return true;
+  for (int64_t g : m.grid_phase) if (g != 0) return true;
+  return false;
+}
+
+// Cell-level test on one cell's sorted, duplicate-free instances [lo, hi).
+bool cell_racy(const std::vector<Inst>& v, size_t lo, size_t hi, const Model& m) {
+  if (!has_sync_scopes(m)) return cell_racy_plain(v, lo, hi);
+  // grid intervals: two blocks and a conflict
+  std::map<int64_t, std::set<int64_t>> g_blocks;
+  std::map<int64_t, Kinds> g_kinds;
+  // (b, p) groups: two warps and a conflict; (b, p, w) groups: two threads and a conflict
+  std::map<std::pair<int64_t, int64_t>, std::set<int64_t>> bp_warps;
+  std::map<std::pair<int64_t, int64_t>, Kinds> bp_kinds;
+  std::map<std::tuple<int64_t, int64_t, int64_t>, std::set<int64_t>> bpw_threads;
+  std::map<std::tuple<int64_t, int64_t, int64_t>, Kinds> bpw_kinds;
+  for (size_t i = lo; i < hi; ++i) {
+    const Inst& x = v[i];
+    const int64_t g = m.grid_phase[x.p];
+    g_blocks[g].insert(x.b);
+    g_kinds[g].add(x.k);
+    bp_warps[{x.b, x.p}].insert(x.t / kWarpSize);
+    bp_kinds[{x.b, x.p}].add(x.k);
+    bpw_threads[std::make_tuple(x.b, x.p, x.w)].insert(x.t);
+    bpw_kinds[std::make_tuple(x.b, x.p, x.w)].add(x.k);
+  }
+  for (auto& kv : g_blocks)
+    if (kv.second.size() >= 2 && g_kinds[kv.first].conf()) return true;
+  for (auto& kv : bp_warps)
+    if (kv.second.size() >= 2 && bp_kinds[kv.first].conf()) return true;
+  for (auto& kv : bpw_threads)
+    if (kv.second.size() >= 2 && bpw_kinds[kv.first].conf()) return true;
+  return false;
+}
+
 // Smallest racing pair inside one racy cell [lo, hi).
-void cell_witness(const std::vector<Inst>& v, size_t lo, size_t hi, int64_t bsize, Inst& x, Inst& y) {
+void cell_witness(const std::vector<Inst>& v, size_t lo, size_t hi, int64_t bsize, const Model& m, Inst& x,
+                  Inst& y) {
   const size_t n = hi - lo;
   if (n <= 4096) {
     // by the definition: first x with any partner, then its first partner
     for (size_t i = lo; i < hi; ++i)
       for (size_t j = lo; j < hi; ++j)
-        if (races(v[i], v[j], bsize)) {
+        if (races(v[i], v[j], bsize, m)) {
           // v[i] is the smallest instance with a partner; every partner of the
           // smallest participant is larger than it, so the first j found is y.
           x = v[i];
@@ -501,31 +583,34 @@ void cell_witness(const std::vector<Inst>& v, size_t lo, size_t hi, int64_t bsiz
         }
     throw std::runtime_error("cell_witness called on a race-free cell");
   }
-  // large cells: decide "x has a partner" from the blocks holding each kind and
-  // the threads holding each kind per (b, p) group
-  std::set<int64_t> kblocks[3];
-  std::map<std::pair<int64_t, int64_t>, std::set<int64_t>> kthreads[3];
+  // large cells: decide "x has a partner" from the blocks holding each kind
+  // per grid interval and the (thread, warp interval) pairs holding each kind
+  // per (b, p) group
+  std::map<int64_t, std::set<int64_t>> kblocks[3];
+  std::map<std::pair<int64_t, int64_t>, std::set<std::pair<int64_t, int64_t>>> kthreads[3];
   for (size_t i = lo; i < hi; ++i) {
-    kblocks[v[i].k].insert(v[i].b);
-    kthreads[v[i].k][{v[i].b, v[i].p}].insert(v[i].t);
+    kblocks[v[i].k][m.grid_phase[v[i].p]].insert(v[i].b);
+    kthreads[v[i].k][{v[i].b, v[i].p}].insert({v[i].t, v[i].w});
   }
-  auto other = [](const std::set<int64_t>& s, int64_t mine) {
-    for (int64_t x : s) if (x != mine) return true;
-    return false;
-  };
   for (size_t i = lo; i < hi; ++i) {
     const Inst& c = v[i];
     bool cross = false, same = false;
     for (int k = 0; k < 3; ++k) {
       if (!conflict(c.k, k)) continue;
-      cross |= other(kblocks[k], c.b);                       // a partner in another block
+      // a partner in another block of the same grid interval
+      auto bt = kblocks[k].find(m.grid_phase[c.p]);
+      if (bt != kblocks[k].end())
+        for (int64_t b : bt->second) if (b != c.b) { cross = true; break; }
+      // another thread of the (b, p) group in another warp or in the same warp interval
       auto it = kthreads[k].find({c.b, c.p});
-      if (it != kthreads[k].end()) same |= other(it->second, c.t);   // another thread of the group
+      if (it != kthreads[k].end())
+        for (const auto& tw : it->second)
+          if (tw.first != c.t && (tw.first / kWarpSize != c.t / kWarpSize || tw.second == c.w)) { same = true; break; }
     }
     if (cross || same) {
       x = c;
       for (size_t j = lo; j < hi; ++j)
-        if (races(c, v[j], bsize)) { y = v[j]; return; }
+        if (races(c, v[j], bsize, m)) { y = v[j]; return; }
       throw std::runtime_error("inconsistent partner summary");
     }
   }
@@ -558,11 +643,11 @@ int check_model(const Model& m, CellRange range, int64_t* out) {
   while (i < v.size()) {
     size_t j = i;
     while (j < v.size() && v[j].same_cell(v[i])) ++j;
-    if (cell_racy(v, i, j)) {
+    if (cell_racy(v, i, j, m)) {
       racy++;
       if (!have_witness) {
         Inst x{}, y{};
-        cell_witness(v, i, j, bsize, x, y);
+        cell_witness(v, i, j, bsize, m, x, y);
         put_witness(out, x, y);
         have_witness = true;
       }
@@ -652,7 +737,7 @@ int oracle_brute(const char* text, int64_t* out) {
     Inst bx{}, by{};
     for (size_t i = 0; i < v.size(); ++i)
       for (size_t j = i + 1; j < v.size(); ++j)
-        if (races(v[i], v[j], bsize)) {
+        if (races(v[i], v[j], bsize, m)) {
           racy_cells.insert(std::make_tuple(v[i].a, v[i].s, v[i].e));
           // v is sorted, so (i, j) pairs come in lexicographic order
           if (!have) { bx = v[i]; by = v[j]; have = true; }

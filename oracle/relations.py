@@ -19,8 +19,10 @@ is a plain Python set of pairs and each operator is the textbook set operation.
 
 For a SIMT kernel model the sequential ``Before`` is replaced by the
 concurrency relation of the barrier rule (two statement instances of distinct
-threads are concurrent iff they are in different blocks or in the same barrier
-interval), and a race is a conflicting pair that is concurrent:
+threads are concurrent iff they are in different blocks of the same grid
+interval, or in the same block and barrier interval and in different warps or
+the same warp interval; without warp and grid barriers: different blocks or the
+same barrier interval), and a race is a conflicting pair that is concurrent:
 
     Race := ((Write . Read^-1) + (Write . Write^-1) + (Read . Write^-1)) * Concurrent
 
@@ -157,6 +159,9 @@ class SimtInstances:
         self.block: Dict[Tuple, int] = {}
         self.thread: Dict[Tuple, int] = {}
         self.phase: Dict[Tuple, int] = {}
+        self.wphase: Dict[Tuple, int] = {}
+        self.grid_phase: List[int] = []
+        self.sync = False   # warp or grid barriers: witness tuples carry the warp interval
         self.read = Relation()
         self.write = Relation()
         self.atomic = Relation()
@@ -170,6 +175,9 @@ def simt_instances(m) -> SimtInstances:
     bs = bx_ * by_ * bz_
     tables = getattr(m, "tables", [])
     out = SimtInstances()
+    n_wp = getattr(m, "n_warp_phases", 1)
+    out.grid_phase = list(getattr(m, "grid_phase", None) or []) or [0] * m.n_phases
+    out.sync = n_wp > 1 or any(out.grid_phase)
     reads, writes, atomics = set(), set(), set()
     for bz, by, bx in product(range(gz), range(gy), range(gx)):
         b = bx + gx * (by + gy * bz)
@@ -198,6 +206,10 @@ def simt_instances(m) -> SimtInstances:
                     out.domain.append(x)
                     out.block[x], out.thread[x] = b, t
                     out.phase[x] = _ev(st.phase, tid, bid, m.params, its, tables)
+                    wp = getattr(st, "warp_phase", None)
+                    out.wphase[x] = _ev(wp, tid, bid, m.params, its, tables) if wp is not None else 0
+                    if not (0 <= out.phase[x] < m.n_phases) or not (0 <= out.wphase[x] < n_wp):
+                        out.out_of_bounds.append((si, 0, gtid))
                     for ai, ac in enumerate(st.accesses):
                         arr = m.arrays[ac.array]
                         idx = [_ev(e, tid, bid, m.params, its, tables) for e in ac.index]
@@ -244,12 +256,20 @@ def conflicts(inst: SimtInstances):
 
 def concurrent_pairs(inst: SimtInstances, pairs: Iterable[Tuple]) -> Relation:
     """The part of ``pairs`` in the concurrency relation of the barrier rule:
-    distinct threads, and different blocks or the same barrier interval."""
+    distinct threads, and either different blocks of the same grid interval,
+    or the same block and barrier interval and (different warps or the same
+    warp interval)."""
     keep = []
+    g = inst.grid_phase
     for x, y in pairs:
         if x[2] == y[2]:
             continue
-        if inst.block[x] != inst.block[y] or inst.phase[x] == inst.phase[y]:
+        if inst.block[x] != inst.block[y]:
+            ok = g[inst.phase[x]] == g[inst.phase[y]]
+        else:
+            ok = inst.phase[x] == inst.phase[y] and (
+                inst.thread[x] // 32 != inst.thread[y] // 32 or inst.wphase[x] == inst.wphase[y])
+        if ok:
             keep.append((x, y))
     return Relation(keep)
 
@@ -275,6 +295,8 @@ def race_check(m) -> Tuple[str, object, Optional[Tuple]]:
     for x, kx, c, y, ky in rs:
         X = c + (inst.block[x], inst.phase[x], inst.thread[x], kx)
         Y = c + (inst.block[y], inst.phase[y], inst.thread[y], ky)
+        if inst.sync:
+            X, Y = X + (inst.wphase[x],), Y + (inst.wphase[y],)
         pair = (X, Y) if X < Y else (Y, X)
         if best is None or pair < best:
             best = pair

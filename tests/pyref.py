@@ -35,9 +35,17 @@ def ev(e, env):
     raise ValueError(op)
 
 
+def has_sync_scopes(m):
+    return getattr(m, "n_warp_phases", 1) > 1 or any(getattr(m, "grid_phase", None) or [])
+
+
 def instances(m):
-    """List of (a, s, e, b, p, t, k) for every in-bounds access instance, and
-    the list of out-of-bounds records (stmt, access, gtid, dimcode)."""
+    """List of (a, s, e, b, p, t, k) for every in-bounds access instance --
+    with the warp interval w appended, (a, s, e, b, p, t, k, w), when the model
+    has warp or grid barriers -- and the list of out-of-bounds records (stmt,
+    access, gtid, dimcode)."""
+    sync = has_sync_scopes(m)
+    n_wp = getattr(m, "n_warp_phases", 1)
     gx, gy, gz = m.grid
     bx_, by_, bz_ = m.block
     bs = bx_ * by_ * bz_
@@ -54,10 +62,11 @@ def instances(m):
                         if any(ev(g, env) < 0 for g in st.guards):
                             return
                         p = ev(st.phase, env)
+                        wp = ev(st.warp_phase, env) if hasattr(st, "warp_phase") else 0
                         for ai, ac in enumerate(st.accesses):
                             arr = m.arrays[ac.array]
                             bad = False
-                            if not (0 <= p < m.n_phases):
+                            if not (0 <= p < m.n_phases) or not (0 <= wp < n_wp):
                                 oob.append((si, ai, b * bs + t, 0))
                                 bad = True
                             e = 0
@@ -70,7 +79,8 @@ def instances(m):
                             if bad:
                                 continue
                             s = b if arr.scope == "shared" else 0
-                            out.append((ac.array, s, e, b, p, t, {"W": 1, "A": 2}.get(ac.kind, 0)))
+                            x = (ac.array, s, e, b, p, t, {"W": 1, "A": 2}.get(ac.kind, 0))
+                            out.append(x + (wp,) if sync else x)
                         return
                     lp = st.loops[level]
                     v = ev(lp.lower, env)
@@ -89,16 +99,24 @@ def conflict(kx, ky):
     return kx == 1 or ky == 1 or {kx, ky} == {0, 2}
 
 
-def race(x, y, bs):
+def race(x, y, bs, grid_phase=None):
     """The pair predicate: same cell, different threads, conflicting kinds,
-    and concurrent (different blocks or the same barrier interval)."""
+    and concurrent: different blocks in the same grid interval, or the same
+    block and barrier interval and (different warps or the same warp
+    interval).  Tuples without a warp interval (no warp or grid barriers):
+    different blocks or the same barrier interval."""
     if x[:3] != y[:3]:
         return False
     if x[3] * bs + x[5] == y[3] * bs + y[5]:
         return False
     if not conflict(x[6], y[6]):
         return False
-    return x[3] != y[3] or x[4] == y[4]
+    if len(x) == 7:
+        return x[3] != y[3] or x[4] == y[4]
+    g = grid_phase or [0] * (max(x[4], y[4]) + 1)
+    if x[3] != y[3]:
+        return g[x[4]] == g[y[4]]
+    return x[4] == y[4] and (x[5] // 32 != y[5] // 32 or x[7] == y[7])
 
 
 def check(m):
@@ -117,7 +135,7 @@ def check(m):
     for cell, xs in by_cell.items():
         for i in range(len(xs)):
             for j in range(i + 1, len(xs)):
-                if race(xs[i], xs[j], bs):
+                if race(xs[i], xs[j], bs, getattr(m, "grid_phase", None)):
                     racy.add(cell)
                     if best is None or (xs[i], xs[j]) < best:
                         best = (xs[i], xs[j])

@@ -359,3 +359,72 @@ def test_atomic_large_cell_witness():
         r, rb = oracle.check(m), oracle.brute(m)
         assert r.racy_cells == rb.racy_cells == exp
         assert r.witness == rb.witness
+
+
+# --------------------------------------------------------------------------
+# warp and grid barriers: blocks are ordered only by grid barriers, two warps
+# of one block only by block barriers, the threads of one warp also by warp
+# barriers
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nw,bar,shared,exp", [
+    (2, True, False, 0),      # warp barriers order the stages inside each warp
+    (2, False, False, 30),    # 15 cells per warp without them
+    (1, False, False, 15),
+    (2, True, True, 16),      # warps meet on cells 0..15: warp barriers do not order warps
+    (3, False, True, 16),
+    (1, True, True, 0),
+])
+def test_warp_reduction_closed_form(nw, bar, shared, exp):
+    m = w.warp_reduction(n_warps=nw, warp_barriers=bar, shared_half=shared)
+    assert oracle.check(m).racy_cells == exp
+    assert pyref.check(m)[1] == exp
+    assert oracle.brute(m).racy_cells == exp
+
+
+@pytest.mark.parametrize("nb,bs,grid,exp", [(4, 8, True, 0), (4, 8, False, 4), (1, 8, False, 0), (3, 33, False, 3),
+                                            (3, 33, True, 0)])
+def test_grid_neighbor_closed_form(nb, bs, grid, exp):
+    m = w.grid_neighbor(nb, bs, grid_barrier=grid)
+    assert oracle.check(m).racy_cells == exp
+    assert pyref.check(m)[1] == exp
+
+
+def test_grid_neighbor_witness():
+    # cell 0: written by block 0's thread 0 in interval 0, read by block 1's last
+    # thread (gtid 15, (15 + 1) mod 16 = 0) in interval 1 -- one grid interval
+    r = oracle.check(w.grid_neighbor(2, 8, grid_barrier=False))
+    assert r.witness == (0, 0, 0, (0, 0, 0, 1), (1, 1, 7, 0))
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_tiny_random_sync_vs_python_bruteforce(seed):
+    m = w.tiny_random_sync(seed)
+    st, cnt, best = pyref.check(m)
+    r, rb = oracle.check(m), oracle.brute(m)
+    assert st == "ok" and r.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        assert r.witness == (x[0], x[1], x[2], x[3:7], y[3:7]) == rb.witness
+        if len(x) == 8:
+            assert (r.x_wphase, r.y_wphase) == (x[7], y[7]) == (rb.x_wphase, rb.y_wphase)
+
+
+def test_sync_large_cell_witness():
+    """The summary witness path (more than 4096 instances in the cell) with
+    warp and grid barriers agrees with the pair-by-pair definition."""
+    from workloads.spec import Access, Array, Model, Stmt, const, tid, R, W, A
+    c = Array("c", "global", (2,))
+    lane0 = [-1 * (tid.x % 32)]
+    stmts = [Stmt([Access(0, R, (const(0),))], phase=const(0), warp_phase=(tid.x // 32) % 2),
+             Stmt([Access(0, A, (const(0),))], guards=lane0, phase=const(0), warp_phase=const(1)),
+             Stmt([Access(0, W, (const(1),))], guards=lane0, phase=const(1), warp_phase=const(0)),
+             Stmt([Access(0, R, (const(1),))], phase=const(2))]
+    for gp in ([0, 0, 0], [0, 0, 1], [0, 1, 2]):
+        m = Model((40, 1, 1), (128, 1, 1), [c], stmts, n_phases=3, n_warp_phases=2, grid_phase=gp)
+        r, rb = oracle.check(m), oracle.brute(m)
+        assert r.racy_cells == rb.racy_cells
+        assert r.witness == rb.witness and (r.x_wphase, r.y_wphase) == (rb.x_wphase, rb.y_wphase)

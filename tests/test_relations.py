@@ -157,3 +157,16 @@ def test_atomic_closed_forms_as_relations():
     assert rel.race_check(w.atomic_histogram(8, 4, barrier=False))[1] == 4
     assert rel.race_check(w.atomic_histogram(8, 4, barrier=False, read_back=False))[1] == 0
     assert rel.race_check(w.atomic_counter(4, n_blocks=2))[1] == 1
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_tiny_random_sync_relations_match(seed):
+    m = w.tiny_random_sync(seed)
+    assert rel.race_check(m) == pyref.check(m)
+
+
+def test_sync_closed_forms_as_relations():
+    assert rel.race_check(w.warp_reduction(2, warp_barriers=True))[1] == 0
+    assert rel.race_check(w.warp_reduction(2, warp_barriers=False))[1] == 30
+    assert rel.race_check(w.grid_neighbor(4, 8, grid_barrier=False))[1] == 4
+    assert rel.race_check(w.grid_neighbor(4, 8, grid_barrier=True))[1] == 0

@@ -36,7 +36,7 @@ from .spec import (GLOBAL, SHARED, A, Access, Array, Expr, Loop, Model, R, Stmt,
 __all__ = [
     "reduction_tree", "transpose", "random_affine", "batch_models", "request_stream",
     "neighbor_write_read", "polyhedral_product", "ge_spmm_uniform", "ge_spmm_csr", "csr_row_lengths",
-    "atomic_histogram", "atomic_counter",
+    "atomic_histogram", "atomic_counter", "warp_reduction", "grid_neighbor", "tiny_random_sync",
     "tiny_random", "tiny_random_tables",
     "RANDOM_AFFINE_ROW_GLOBAL", "RANDOM_AFFINE_ROW_SHARED",
 ]
@@ -113,6 +113,50 @@ def atomic_counter(T: int, n_blocks: int = 1, barrier: bool = True) -> Model:
              Stmt([Access(0, R, (const(0),))], guards=[-1 * tid.x], phase=const(1 if barrier else 0), name="read")]
     return Model((n_blocks, 1, 1), (T, 1, 1), [ctr], stmts, n_phases=2 if barrier else 1,
                  name=f"counter_T{T}_G{n_blocks}_{'bar' if barrier else 'nobar'}")
+
+
+def warp_reduction(n_warps: int = 2, warp_barriers: bool = True, shared_half: bool = False) -> Model:
+    """Warp-level tree reduction (the CWM style of Ge-SpMM: warps synchronise
+    with ``__syncwarp`` only): in one block of ``32 * n_warps`` threads, stage k
+    = 0..4 lets lane l < 16 >> k of every warp add ``s[base + l + (16 >> k)]``
+    into ``s[base + l]``, with ``base = 32 * warp`` (``shared_half``: every warp
+    uses base 0).  With ``warp_barriers`` stage k is warp interval k.
+
+    Racy cells: 0 with warp barriers and private bases; without them 15 per
+    warp (cells 1..15 of its slice: written at a stage by lane c, read at an
+    earlier stage by a lane of the same warp); with a shared base and two warps
+    or more, the warps write cells 0..15 in one barrier interval and warp
+    barriers do not order warps, so those 16 cells race with or without them
+    (cells 16..31 are only read)."""
+    T = 32 * n_warps
+    s_ = Array("s", SHARED, (T,))
+    lane = tid.x % 32
+    base = const(0) if shared_half else (tid.x // 32) * 32
+    stmts = []
+    for k in range(5):
+        stride = 16 >> k
+        stmts.append(Stmt([Access(0, R, (base + lane,)), Access(0, R, (base + lane + stride,)),
+                           Access(0, W, (base + lane,))],
+                          guards=[(stride - 1) - lane], phase=const(0),
+                          warp_phase=const(k if warp_barriers else 0), name=f"stage{k}"))
+    return Model((1, 1, 1), (T, 1, 1), [s_], stmts, n_phases=1, n_warp_phases=5 if warp_barriers else 1,
+                 name=f"warpred_W{n_warps}_{'sync' if warp_barriers else 'nosync'}{'_shared' if shared_half else ''}")
+
+
+def grid_neighbor(n_blocks: int, block: int, grid_barrier: bool = True) -> Model:
+    """Thread g writes ``out[g]``; after a barrier it reads ``out[(g + 1) mod
+    T]``.  With a grid-wide barrier (grid intervals 0, 1) the kernel is
+    race-free; with a block barrier only, the read of the first cell of every
+    block by the last thread of the previous block is unordered: ``n_blocks``
+    racy cells (for two blocks or more)."""
+    T = n_blocks * block
+    out = Array("out", GLOBAL, (T,))
+    g = bid.x * block + tid.x
+    stmts = [Stmt([Access(0, W, (g,))], phase=const(0), name="write"),
+             Stmt([Access(0, R, ((g + 1) % T,))], phase=const(1), name="read")]
+    return Model((n_blocks, 1, 1), (block, 1, 1), [out], stmts, n_phases=2,
+                 grid_phase=[0, 1] if grid_barrier else [0, 0],
+                 name=f"gridnb_{n_blocks}x{block}_{'grid' if grid_barrier else 'block'}")
 
 
 def reduction_tree(barriers: bool = True, load_phase: bool = False, T: int = 256) -> Model:
@@ -506,6 +550,52 @@ def tiny_random(seed: int, atomic: float = 0.0) -> Model:
             accs.append(Access(a, kind, idx))
         stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, name=f"t{s}"))
     return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tiny{seed}")
+
+
+def tiny_random_sync(seed: int) -> Model:
+    """A small random model with warp and grid barriers: one to three blocks of
+    33..80 threads (so two or three warps), up to three barrier intervals
+    mapped to up to three grid intervals, up to three warp intervals per
+    statement (a constant, a warp-uniform ``tid.x // 32`` term or a uniform
+    loop iterator), shared and global arrays, R / W / A accesses."""
+    rng = SplitMix64(0x5C3A ^ (seed * 0x9E3779B97F4A7C15))
+    n_blocks = rng.uniform_int(1, 3)
+    T = rng.uniform_int(33, 80)
+    n_phases = rng.uniform_int(1, 3)
+    gp, g = [], 0
+    for _ in range(n_phases):
+        gp.append(g)
+        if rng.chance(0.4):
+            g += 1
+    n_wp = rng.uniform_int(1, 3)
+    arrays = [Array("sh", SHARED, (rng.uniform_int(4, 40),)), Array("gl", GLOBAL, (rng.uniform_int(4, 60),))]
+    stmts = []
+    for si in range(rng.uniform_int(1, 5)):
+        depth = rng.below(2)
+        loops = [Loop(0, rng.uniform_int(1, 3))] if depth else []
+        ph = const(rng.below(n_phases))
+        u = rng.below(3)
+        if u == 0 or n_wp == 1:
+            wp = const(rng.below(n_wp))
+        elif u == 1:
+            wp = (tid.x // 32 + rng.below(n_wp)) % n_wp
+        else:
+            wp = (it(0) + rng.below(n_wp)) % n_wp if depth else const(rng.below(n_wp))
+        accs = []
+        for _ in range(rng.uniform_int(1, 3)):
+            a = rng.below(2)
+            ext = arrays[a].extents[0]
+            e = rng.uniform_int(0, 5) + rng.uniform_int(0, 3) * tid.x + rng.uniform_int(0, 2) * bid.x
+            if depth:
+                e = e + rng.uniform_int(0, 3) * it(0)
+            if rng.chance(0.3):
+                e = e // rng.uniform_int(2, 8)
+            u2 = rng.random()
+            kind = A if u2 < 0.25 else (W if u2 < 0.55 else R)
+            accs.append(Access(a, kind, (e % ext,)))
+        stmts.append(Stmt(accs, loops=loops, phase=ph, warp_phase=wp, name=f"y{si}"))
+    return Model((n_blocks, 1, 1), (T, 1, 1), arrays, stmts, n_phases=n_phases, n_warp_phases=n_wp,
+                 grid_phase=gp, name=f"tinysync_{seed}")
 
 
 def tiny_random_tables(seed: int) -> Model:

@@ -221,15 +221,19 @@ class Access:
 class Stmt:
     """A labelled code section: its loop nest, its guards (each ``>= 0``), its
     barrier phase (may use bid, parameters and iterators of thread-uniform
-    loops, never tid) and its accesses."""
+    loops, never tid), its warp interval (the number of warp barriers,
+    ``__syncwarp``, its thread passed inside the current barrier phase; 0
+    without warp barriers) and its accesses."""
     accesses: List[Access]
     loops: List[Loop] = field(default_factory=list)
     guards: List[Expr] = field(default_factory=list)
     phase: Expr = field(default_factory=lambda: const(0))
     name: str = ""
+    warp_phase: Expr = field(default_factory=lambda: const(0))
 
     def __post_init__(self):
         self.phase = Expr.wrap(self.phase)
+        self.warp_phase = Expr.wrap(self.warp_phase)
         self.guards = [Expr.wrap(g) for g in self.guards]
 
 
@@ -243,12 +247,21 @@ class Model:
     n_phases: int = 1
     name: str = ""
     tables: List[List[int]] = field(default_factory=list)
+    # warp intervals per barrier phase (statements' warp_phase in [0, n)), and
+    # the grid interval of each barrier phase (grid-wide barriers; empty = none)
+    n_warp_phases: int = 1
+    grid_phase: List[int] = field(default_factory=list)
 
     def __post_init__(self):
         self.grid = tuple(int(v) for v in (list(self.grid) + [1, 1, 1])[:3])
         self.block = tuple(int(v) for v in (list(self.block) + [1, 1, 1])[:3])
         self.params = [int(p) for p in self.params]
         self.tables = [[int(v) for v in t] for t in self.tables]
+        self.grid_phase = [int(v) for v in self.grid_phase]
+        if self.grid_phase and len(self.grid_phase) != self.n_phases:
+            raise ValueError("grid_phase needs one entry per barrier phase")
+        if any(b < a for a, b in zip(self.grid_phase, self.grid_phase[1:])):
+            raise ValueError("grid phases must not decrease (a grid barrier also ends a block interval)")
 
     @property
     def n_blocks(self) -> int:
