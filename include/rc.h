@@ -18,16 +18,24 @@
  *   instances x, y race  iff  same (array, scope instance, element)
  *                          and gtid_x != gtid_y
  *                          and their kinds conflict
- *                          and (block_x != block_y or phase_x == phase_y),
+ *                          and they are concurrent:
+ *     block_x != block_y:  grid_phase[phase_x] == grid_phase[phase_y]
+ *     same block:          phase_x == phase_y and
+ *                          (warp_x != warp_y or warp_phase_x == warp_phase_y),
+ * with warp = thread / 32.  Without warp or grid barriers (every warp_phase and
+ * grid_phase 0) this is: block_x != block_y or phase_x == phase_y.
  * where kinds are R (read), W (write) and A (atomic read-modify-write) and two
  * kinds conflict iff one is W, or one is A and the other R (two atomics on one
  * cell are ordered by the memory system).
  * A shared array has one instance per block (indexed block-locally), a global
  * array one for the grid.  The phase of an instance is the number of block
  * barriers its thread passed before it; blocks are never ordered against each
- * other.  Count = number of distinct racy cells.  Witness = the
- * lexicographically smallest racing pair (x, y), x < y, in the order
- * (array, scope instance, element, block, phase, thread, kind R<W<A).
+ * other except by grid-wide barriers (a grid interval per block interval,
+ * rc_model_desc.grid_phase); the warp phase counts the warp barriers
+ * (__syncwarp) a thread passed inside its block interval.  Count = number of
+ * distinct racy cells.  Witness = the lexicographically smallest racing pair
+ * (x, y), x < y, in the order (array, scope instance, element, block, phase,
+ * thread, kind R<W<A, warp phase).
  *
  * Conventions for every entry point:
  *  - All calls return an rc_status; none aborts, throws or prints.
@@ -132,6 +140,8 @@ typedef struct rc_stmt {
   const rc_loop* loops;     uint32_t n_loops;
   const rc_expr* guards;    uint32_t n_guards;
   const rc_access* accesses; uint32_t n_accesses;
+  rc_expr warp_phase;       /* warp barriers passed in the block interval, in
+                               [0, n_warp_phases); len 0 = 0                     */
 } rc_stmt;
 
 typedef struct rc_array {
@@ -155,6 +165,13 @@ typedef struct rc_model_desc {
   const rc_array* arrays;  uint32_t n_arrays;
   const rc_stmt* stmts;    uint32_t n_stmts;
   const rc_table* tables;  uint32_t n_tables;   /* for RC_OP_LOAD; may be 0     */
+  uint32_t n_warp_phases;  /* warp intervals per block interval; 0 or 1 = none   */
+  const uint32_t* grid_phase;  /* n_phases entries, non-decreasing: the grid
+                               interval of each block interval (grid-wide
+                               barriers); NULL = none.  With warp or grid
+                               barriers n_phases * n_warp_phases <= 16 and the
+                               model is checked alone on the sort path (hash
+                               path and batches: RC_E_UNSUPPORTED)                */
 } rc_model_desc;
 
 /* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED
@@ -276,6 +293,8 @@ typedef struct rc_inst {
   uint32_t kind;           /* RC_READ / RC_WRITE / RC_ATOMIC                       */
   int64_t phase;
   uint64_t gtid;           /* block * blockSize + thread                           */
+  uint32_t warp_phase;
+  uint32_t reserved;
 } rc_inst;
 
 typedef struct rc_result {

@@ -80,7 +80,8 @@ class rc_stmt(Structure):
     _fields_ = [("phase", rc_expr),
                 ("loops", POINTER(rc_loop)), ("n_loops", c_uint32),
                 ("guards", POINTER(rc_expr)), ("n_guards", c_uint32),
-                ("accesses", POINTER(rc_access)), ("n_accesses", c_uint32)]
+                ("accesses", POINTER(rc_access)), ("n_accesses", c_uint32),
+                ("warp_phase", rc_expr)]
 
 
 class rc_array(Structure):
@@ -97,7 +98,8 @@ class rc_model_desc(Structure):
                 ("n_phases", c_uint32),
                 ("arrays", POINTER(rc_array)), ("n_arrays", c_uint32),
                 ("stmts", POINTER(rc_stmt)), ("n_stmts", c_uint32),
-                ("tables", POINTER(rc_table)), ("n_tables", c_uint32)]
+                ("tables", POINTER(rc_table)), ("n_tables", c_uint32),
+                ("n_warp_phases", c_uint32), ("grid_phase", POINTER(c_uint32))]
 
 
 class rc_limits(Structure):
@@ -129,7 +131,7 @@ class rc_stage_times(Structure):
 
 class rc_inst(Structure):
     _fields_ = [("block", c_uint64), ("thread", c_uint32), ("kind", c_uint32), ("phase", c_int64),
-                ("gtid", c_uint64)]
+                ("gtid", c_uint64), ("warp_phase", c_uint32), ("reserved", c_uint32)]
 
 
 class rc_result(Structure):
@@ -321,6 +323,9 @@ class _Desc:
             self.keep.append(accs)
             st.accesses = accs
             st.n_accesses = len(s.accesses)
+            wp = getattr(s, "warp_phase", None)
+            if wp is not None and not (wp.op == "const" and wp.args[0] == 0):
+                st.warp_phase = self.expr(wp)
         self.keep.append(stmts)
         d.stmts = stmts
         d.n_stmts = len(model.stmts)
@@ -335,6 +340,12 @@ class _Desc:
             self.keep.append(tabs)
             d.tables = tabs
         d.n_tables = len(tables)
+        d.n_warp_phases = int(getattr(model, "n_warp_phases", 1))
+        gp = list(getattr(model, "grid_phase", None) or [])
+        if gp:
+            ga = (c_uint32 * len(gp))(*[int(v) for v in gp])
+            self.keep.append(ga)
+            d.grid_phase = ctypes.cast(ga, POINTER(c_uint32))
         self.desc = d
 
     def expr(self, e) -> rc_expr:
@@ -522,6 +533,8 @@ class Result:
     oob_access: int
     oob_gtid: int
     oob_dim: int
+    x_wphase: int = 0     # warp phases of the witness pair (models with warp barriers)
+    y_wphase: int = 0
 
     @property
     def witness(self):
@@ -534,7 +547,7 @@ class Result:
 def _result(r: rc_result) -> Result:
     return Result(r.status, r.verdict, r.racy_cells, r.instances, r.w_array, r.w_scope, r.w_addr,
                   (r.x.block, r.x.phase, r.x.thread, r.x.kind), (r.y.block, r.y.phase, r.y.thread, r.y.kind),
-                  r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim)
+                  r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim, r.x.warp_phase, r.y.warp_phase)
 
 
 class NotReady(Exception):

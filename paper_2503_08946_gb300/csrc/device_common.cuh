@@ -108,6 +108,15 @@ __device__ __forceinline__ bool guards_hold(const DevModel& M, const DevStmt& S,
 
 // The key of access `a` of statement `s` at this point, or kSentinel when the
 // instance is out of bounds (the smallest offending code is folded into *oob).
+// The fine interval of a statement instance (phase * n_wphases + warp phase),
+// or -1 if its block or warp interval is out of range.
+__device__ __forceinline__ int64_t fine_phase(const DevModel& M, const DevStmt& S, const ThreadVars& tv,
+                                              const int64_t* it, const int64_t* term) {
+  const int64_t p = eval_row(M, S.row_phase, tv, it, term);
+  const int64_t w = S.row_wphase >= 0 ? eval_row(M, S.row_wphase, tv, it, term) : 0;
+  return (p < 0 || p >= M.n_phases || w < 0 || w >= M.n_wphases) ? -1 : p * M.n_wphases + w;
+}
+
 // The key of one access instance (kSentinel if it is out of bounds); *cell_out
 // receives its linear cell (all ones if out of bounds), which the key's cell
 // field may not hold whole when the model is wider than one key.
@@ -117,7 +126,7 @@ __device__ __forceinline__ uint64_t make_key(const DevModel& M, const DevStmt& S
   const DevAccess A = M.accs[S.acc0 + a];
   const DevArray& arr = M.arrays[A.array];
   bool bad = false;
-  if (phase < 0 || phase >= M.n_phases) {
+  if (phase < 0 || phase >= M.n_phases * M.n_wphases) {
     atomicMin(oob, oob_pack(s, (uint32_t)a, tv.gtid, 0));
     bad = true;
   }

@@ -106,8 +106,11 @@ __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const i
   const DevStmt& S = *c.S;
   for (int g = 0; g < S.n_guards; ++g)
     if (point_row<L>(c, S.guard_row0 + g, it) < 0) return false;
-  const int64_t phase = point_row<L>(c, S.row_phase, it);
-  const bool phase_bad = phase < 0 || phase >= M.n_phases;
+  // the key's phase field: the fine interval phase * n_wphases + warp phase
+  const int64_t bphase = point_row<L>(c, S.row_phase, it);
+  const int64_t wphase = S.row_wphase >= 0 ? point_row<L>(c, S.row_wphase, it) : 0;
+  const bool phase_bad = bphase < 0 || bphase >= M.n_phases || wphase < 0 || wphase >= M.n_wphases;
+  const int64_t phase = bphase * M.n_wphases + wphase;
   for (int a = 0; a < S.n_acc; ++a) {
     const DevAccess* A = M.accs + S.acc0 + a;
     const int arr_i = __ldg(&A->array), nd = __ldg(&A->ndims), row0 = __ldg(&A->row0), kind = __ldg(&A->kind);
@@ -159,6 +162,7 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
   };
   for (int g2 = 0; g2 < S.n_guards; ++g2) cache_row(S.guard_row0 + g2);
   cache_row(S.row_phase);
+  if (S.row_wphase >= 0) cache_row(S.row_wphase);
   for (int a = 0; a < S.n_acc; ++a) {
     const DevAccess* A = M.accs + S.acc0 + a;
     const int nd = __ldg(&A->ndims), row0 = __ldg(&A->row0);
@@ -217,7 +221,7 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
     walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
       const uint64_t slot = S.slot_base + j * (uint64_t)S.n_key * T + g;
       if (guards_hold(M, S, tv, it, term)) {
-        const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
+        const int64_t phase = fine_phase(M, S, tv, it, term);
         for (int a = 0; a < S.n_acc; ++a) {
           uint64_t cell;
           const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code, &cell);
@@ -234,7 +238,7 @@ __device__ void expand_unit_generic(const DevModel& M, uint32_t s, uint64_t g, D
     uint64_t off = M.unit_offset[S.slot_base + g];
     walk_nest(M, S, tv, [&](const int64_t* it, const int64_t* term) {
       if (!guards_hold(M, S, tv, it, term)) return;
-      const int64_t phase = eval_row(M, S.row_phase, tv, it, term);
+      const int64_t phase = fine_phase(M, S, tv, it, term);
       for (int a = 0; a < S.n_acc; ++a) {
         uint64_t cell;
         const uint64_t key = make_key(M, S, s, a, phase, tv, it, term, &res->oob_code, &cell);

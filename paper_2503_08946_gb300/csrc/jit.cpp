@@ -189,7 +189,16 @@ struct Gen {
     for (int gi = 0; gi < S.n_guards; ++gi) gcond += " && " + row(S.guard_row0 + gi) + " >= 0";
     o << ind << "if (" << gcond << ") {\n";
     const std::string in2 = ind + "  ";
-    o << in2 << "const long long ph = " << row(S.row_phase) << ";\n";
+    const bool fine = S.row_wphase >= 0 || m.host.n_wphases > 1;
+    if (fine) {
+      // the fine interval phase * n_wphases + warp phase; -1 if either is out of range
+      o << in2 << "const long long ph0 = " << row(S.row_phase) << ";\n";
+      o << in2 << "const long long wph = " << (S.row_wphase >= 0 ? row(S.row_wphase) : std::string("0LL")) << ";\n";
+      o << in2 << "const long long ph = (ph0 < 0 || ph0 >= " << lit(m.host.n_phases) << " || wph < 0 || wph >= "
+        << lit(m.host.n_wphases) << ") ? -1LL : ph0 * " << lit(m.host.n_wphases) << " + wph;\n";
+    } else {
+      o << in2 << "const long long ph = " << row(S.row_phase) << ";\n";
+    }
     for (int a = 0; a < S.n_acc; ++a) {
       const DevAccess& A = accs[S.acc0 + a];
       const DevArray& arr = arrays[A.array];
@@ -197,7 +206,7 @@ struct Gen {
       const std::string in3 = in2 + "  ";
       for (int d = 0; d < A.ndims; ++d) o << in3 << "const long long v" << d << " = " << row(A.row0 + d) << ";\n";
       o << in3 << "unsigned dc = 0xFFFFFFFFu;\n";
-      o << in3 << "if (ph < 0 || ph >= " << lit(m.host.n_phases) << ") dc = 0u;\n";
+      o << in3 << "if (ph < 0 || ph >= " << lit(m.host.n_phases * m.host.n_wphases) << ") dc = 0u;\n";
       for (int d = 0; d < A.ndims; ++d)
         o << in3 << "else if (v" << d << " < 0 || v" << d << " >= " << lit(arr.ext[d]) << ") dc = " << d + 1 << "u;\n";
       // row-major element index

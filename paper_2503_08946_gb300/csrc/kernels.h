@@ -124,13 +124,19 @@ struct ScanArgs {
   uint32_t n_warps;                    // warps of the cell scan
   DevResult* res;                      // the result, or one per model of a batch
   unsigned int* err;                   // error flags of the whole check
-  unsigned int* groups;                // per result: (1 << phase_bits) x 5 words for the witness
+  unsigned int* groups;                // per result: (1 << phase_bits) x kWitnessGroupWords for the witness
   unsigned long long* long_list;       // first positions of cells handed to the long-cell pass
   unsigned long long* long_count;      // starts at 0
   uint64_t long_cap;                   // scan_long_capacity(n, n_warps)
   const uint64_t* cell_base;           // batch: first batch cell of each model (ascending)
   uint32_t n_models;                   // batch: number of models (0 = single model)
   uint32_t phase_table;                // keys sorted by cell only (phase_bits <= kScanTablePhaseBits)
+  // warp and grid barriers: the phase field is a fine interval q; block
+  // interval and grid interval of q (4 bits per q); warp intervals per block
+  // interval and their bit width (0 without warp barriers)
+  uint32_t sync_scopes;
+  uint32_t n_wp, wp_bits;
+  uint64_t coarse_tab, grid_tab;
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);

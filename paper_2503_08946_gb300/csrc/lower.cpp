@@ -243,6 +243,19 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.n_threads = nt;
   h.n_stmts = d->n_stmts;
   h.n_phases = d->n_phases;
+  // warp and grid barriers: the key's phase field holds the fine interval
+  // q = phase * n_wphases + warp_phase; the scan maps q to its block interval
+  // and its grid interval through two 16-entry tables
+  const uint32_t n_wp = d->n_warp_phases ? d->n_warp_phases : 1u;
+  h.n_wphases = n_wp;
+  bool grid_sync = false;
+  if (d->grid_phase) {
+    for (uint32_t p = 0; p < d->n_phases; ++p) {
+      if (p && d->grid_phase[p] < d->grid_phase[p - 1]) return RC_E_INVALID;   // a grid barrier ends a block interval
+      grid_sync |= d->grid_phase[p] != 0;
+    }
+  }
+  m->sync_scopes = n_wp > 1 || grid_sync;
 
   // arrays and the linear cell space
   std::vector<DevArray> arrays(d->n_arrays);
@@ -290,8 +303,19 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.block_shift = h.thread_shift + h.thread_bits;
   h.block_bits = bit_length(nb - 1);
   h.phase_shift = h.block_shift + h.block_bits;
-  h.phase_bits = bit_length((uint64_t)d->n_phases - 1);
+  uint64_t n_fine = 0;
+  if (!mul_ok((uint64_t)d->n_phases, (uint64_t)n_wp, &n_fine)) return RC_E_UNSUPPORTED;
+  h.phase_bits = bit_length(n_fine - 1);
   if (h.phase_bits > (uint32_t)kMaxPhaseBits) return RC_E_UNSUPPORTED;
+  // warp / grid barriers are scanned with phase tables only (at most 16 fine intervals)
+  if (m->sync_scopes && n_fine > (1u << kScanTablePhaseBits)) return RC_E_UNSUPPORTED;
+  m->coarse_tab = m->grid_tab = 0;
+  for (uint64_t q = 0; q < n_fine && q < 16; ++q) {
+    const uint64_t p = q / n_wp;
+    m->coarse_tab |= (p & 15u) << (4 * q);
+    m->grid_tab |= ((uint64_t)(d->grid_phase ? d->grid_phase[p] : 0u) & 15u) << (4 * q);
+    if (d->grid_phase && d->grid_phase[p] > 15u) return RC_E_UNSUPPORTED;
+  }
   // atomics are scanned by the phase-table scan only (at most 16 intervals)
   if (has_atomic && h.phase_bits > (uint32_t)kScanTablePhaseBits) return RC_E_UNSUPPORTED;
   h.cell_shift = h.phase_shift + h.phase_bits;
@@ -335,7 +359,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     b.desc = d;
     b.loop_tid.assign(kMaxLoops, false);
     std::vector<Lin> lo(S.n_loops), hi(S.n_loops), guards(S.n_guards);
-    Lin phase;
+    Lin phase, wphase;
     bool dense = true;
     for (uint32_t l = 0; l < S.n_loops; ++l) {
       if (S.loops[l].step <= 0) return RC_E_INVALID;
@@ -359,6 +383,8 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
       if (!b.compile(S.guards[g], nl, &guards[g])) return b.err;
     if (!b.compile(S.phase, nl, &phase)) return b.err;
     if (b.depends_on_tid(phase)) return RC_E_INVALID;   // a barrier interval is block-uniform
+    const bool has_wp = S.warp_phase.len > 0;
+    if (has_wp && !b.compile(S.warp_phase, nl, &wphase)) return b.err;
     std::vector<std::vector<Lin>> idx(S.n_accesses);
     for (uint32_t a = 0; a < S.n_accesses; ++a) {
       const rc_access& A = S.accesses[a];
@@ -388,6 +414,11 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     for (auto& g : guards) put_point_row(g);
     D.row_phase = (int32_t)rows.size();
     put_point_row(phase);
+    D.row_wphase = -1;
+    if (has_wp) {
+      D.row_wphase = (int32_t)rows.size();
+      put_point_row(wphase);
+    }
     D.acc0 = (int32_t)accs.size();
     int n_key = 0;
     for (uint32_t a = 0; a < S.n_accesses; ++a) {

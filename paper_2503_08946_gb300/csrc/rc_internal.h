@@ -100,6 +100,8 @@ struct DevStmt {
   int32_t row_upper[kMaxLoops];
   int64_t step[kMaxLoops];
   int32_t row_phase;
+  int32_t row_wphase;   // warp interval row, -1 = 0
+  int32_t pad_w;
   int32_t guard_row0;   // guards are rows [guard_row0, guard_row0 + n_guards)
   int32_t acc0;         // first DevAccess
   int32_t term0;        // first Term
@@ -117,7 +119,8 @@ struct DevModel {
   uint64_t n_blocks;
   uint64_t n_threads;     // n_blocks * bs
   int64_t n_phases;
-  // key layout
+  int64_t n_wphases;      // warp intervals per block interval (1 = no warp barriers)
+  // key layout; the phase field holds phase * n_wphases + warp phase
   uint32_t kind_shift, thread_shift, block_shift, phase_shift, cell_shift;
   uint32_t thread_bits, block_bits, phase_bits, cell_bits;
   uint32_t sort_lo, sort_hi;
@@ -167,9 +170,10 @@ struct DevResult {
 };
 static_assert(sizeof(DevResult) <= 256, "result record must fit its slot");
 
-// words of one witness phase-group record (scan.cu): [mint, maxt] and per
-// access kind (R, W, A) [min thread, max thread, any]
-constexpr unsigned kWitnessGroupWords = 11;
+// words of one witness phase-group record (scan.cu): [mint, maxt], per access
+// kind (R, W, A) [min thread, max thread, any] in the lowest block, and per kind
+// [min block, max block] over all blocks
+constexpr unsigned kWitnessGroupWords = 17;
 
 enum DevError : unsigned int {
   kErrLookbackTimeout = 1u,
@@ -356,6 +360,9 @@ struct Model {
   // host.cell_bits bits (the width left beside the other fields)
   bool wide = false;
   bool has_atomic = false;        // some access is atomic: 2-bit kind field
+  bool sync_scopes = false;       // warp or grid barriers
+  uint64_t coarse_tab = 0;        // fine interval q -> block interval (4 bits per q)
+  uint64_t grid_tab = 0;          // fine interval q -> grid interval (4 bits per q)
   // sections of the program image (byte offsets), for the kernel generator
   size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null

@@ -232,6 +232,11 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.cell_base = nullptr;
   a.n_models = 0;
   a.phase_table = m.host.phase_bits <= rc::kScanTablePhaseBits ? 1u : 0u;
+  a.sync_scopes = m.sync_scopes ? 1u : 0u;
+  a.n_wp = (uint32_t)m.host.n_wphases;
+  a.wp_bits = rc::bit_length((uint64_t)m.host.n_wphases - 1);
+  a.coarse_tab = m.coarse_tab;
+  a.grid_tab = m.grid_tab;
   return a;
 }
 
@@ -287,6 +292,8 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
 rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
                         cudaStream_t st, rc::DevResult* host_out, rc_ticket_s* timed = nullptr) {
   const rc::Model& m = model->m;
+  // the hash tables key groups by (cell, phase) only: no warp or grid barriers
+  if (rc::use_hash_path(m, opts) && m.sync_scopes) return RC_E_UNSUPPORTED;
   rc::WorkspacePlan p;
   rc::plan_workspace(m, opts, &p);
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
@@ -387,7 +394,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
 // kb: thread, phase and kind widths of the keys the witness ranks were taken
 // from.
 void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, uint64_t cell_base, uint32_t tb,
-                   uint32_t pb, uint32_t kb = 1) {
+                   uint32_t pb, uint32_t kb = 1, uint32_t wb = 0) {
   std::memset(out, 0, sizeof(*out));
   out->instances = r.instances;
   if (r.err & rc::kErrLookbackTimeout) {
@@ -419,17 +426,21 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
   out->w_array = (uint32_t)a;
   out->w_scope = m.array_shared[a] ? rem / m.array_cells[a] : 0;
   out->w_addr = m.array_shared[a] ? rem % m.array_cells[a] : rem;
+  // ranks: (phase, thread, kind, warp phase) and (block, phase, thread, kind, warp phase)
   const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1, kmask = (1ull << kb) - 1;
+  const uint64_t wmask = (1ull << wb) - 1;
   const uint64_t bs = m.host.bs;
   out->x.block = r.minb;
-  out->x.kind = (uint32_t)(r.x_rank & kmask);
-  out->x.thread = (uint32_t)((r.x_rank >> kb) & tmask);
-  out->x.phase = (int64_t)((r.x_rank >> (tb + kb)) & pmask);
+  out->x.warp_phase = (uint32_t)(r.x_rank & wmask);
+  out->x.kind = (uint32_t)((r.x_rank >> wb) & kmask);
+  out->x.thread = (uint32_t)((r.x_rank >> (wb + kb)) & tmask);
+  out->x.phase = (int64_t)((r.x_rank >> (wb + tb + kb)) & pmask);
   out->x.gtid = out->x.block * bs + out->x.thread;
-  out->y.kind = (uint32_t)(r.y_rank & kmask);
-  out->y.thread = (uint32_t)((r.y_rank >> kb) & tmask);
-  out->y.phase = (int64_t)((r.y_rank >> (tb + kb)) & pmask);
-  out->y.block = r.y_rank >> (pb + tb + kb);
+  out->y.warp_phase = (uint32_t)(r.y_rank & wmask);
+  out->y.kind = (uint32_t)((r.y_rank >> wb) & kmask);
+  out->y.thread = (uint32_t)((r.y_rank >> (wb + kb)) & tmask);
+  out->y.phase = (int64_t)((r.y_rank >> (wb + tb + kb)) & pmask);
+  out->y.block = r.y_rank >> (pb + tb + kb + wb);
   out->y.gtid = out->y.block * bs + out->y.thread;
 }
 
@@ -703,7 +714,8 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
 // Merge of a chunked ticket's records into one result.
 void decode_chunked(const rc_ticket_s* t, rc_result* out) {
   const rc::Model& m = t->models[0]->m;
-  decode_result(t->host[0], m, out, 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift);
+  decode_result(t->host[0], m, out, 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift,
+                    rc::bit_length((uint64_t)m.host.n_wphases - 1));
   if (out->status != RC_OK) return;
   const uint64_t instances = out->instances;
   out->racy_cells = 0;
@@ -713,7 +725,7 @@ void decode_chunked(const rc_ticket_s* t, rc_result* out) {
     rc_result part;
     // cell_base = -chunk start: the scan's cells are relative to the chunk
     decode_result(t->host[1 + k], m, &part, (uint64_t)0 - t->chunk_lo[k], m.host.thread_bits, m.host.phase_bits,
-                  m.host.thread_shift);
+                  m.host.thread_shift, rc::bit_length((uint64_t)m.host.n_wphases - 1));
     if (t->host[1 + k].err & rc::kErrChunkOverflow) part.status = RC_E_NOMEM;
     if (part.status != RC_OK) {
       std::memset(out, 0, sizeof(*out));
@@ -944,6 +956,10 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.cell_base = dcbase + k.i0;
     sa.n_models = nm;
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
+    sa.sync_scopes = 0;   // models with warp or grid barriers are not batched
+    sa.n_wp = 1;
+    sa.wp_bits = 0;
+    sa.coarse_tab = sa.grid_tab = 0;
     s = cuda_status(rc::launch_scan(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
@@ -1324,6 +1340,8 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   *ticket = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc_check_opts o = resolve_opts(&m, 1, opts);
+  // warp / grid barriers take the sort path unless the hash path is asked for
+  if (m->m.sync_scopes && (!opts || opts->path != RC_PATH_HASH)) o.path = RC_PATH_SORT;
   if (use_chunked(m->m, &o)) {
     if (!opts || opts->path != RC_PATH_HASH) o.path = RC_PATH_SORT;   // chunks take the sort path
     return enqueue_chunked(m, &o, static_cast<uint8_t*>(workspace), ws_bytes, st, ticket);
@@ -1363,6 +1381,7 @@ rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_ch
   for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
     if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
+    if (models[i]->m.sync_scopes) return RC_E_UNSUPPORTED;   // warp / grid barriers: checked alone
   }
   const rc_check_opts ro = resolve_opts(models, n, opts_in);
   const rc_check_opts* opts = &ro;
@@ -1390,6 +1409,7 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
   for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
     if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
+    if (models[i]->m.sync_scopes) return RC_E_UNSUPPORTED;   // warp / grid barriers: checked alone
   }
   rc_check_opts ro = resolve_opts(models, n, opts_in);
   if (opts_in && opts_in->path == RC_PATH_AUTO) {
@@ -1544,7 +1564,8 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
   for (size_t i = 0; i < t->n; ++i) {
     const rc::Model& m = t->models[i]->m;
     if (t->cell_base.empty())
-      decode_result(t->host[i], m, &out[i], 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift);
+      decode_result(t->host[i], m, &out[i], 0, m.host.thread_bits, m.host.phase_bits, m.host.thread_shift,
+                    rc::bit_length((uint64_t)m.host.n_wphases - 1));
     else
       decode_result(t->host[i], m, &out[i], t->cell_base[i], t->field_bits[i] & 0xFFu, (t->field_bits[i] >> 8) & 0xFFu,
                     t->field_bits[i] >> 16);

@@ -474,13 +474,14 @@ struct TFold {
   unsigned gm;       // phases with two (block, thread)
   unsigned gw;       // phases with a write
   unsigned ga, gr;   // phases with an atomic / a plain read (atomic models only)
+  unsigned gmb, gmw; // phases with two blocks / two warps of one block (warp or grid barriers only)
 };
 constexpr unsigned kTW = 1u, kTMB = 2u, kTA = 4u, kTR = 8u;
 constexpr int kTabPhases = 1 << kScanTablePhaseBits;
 constexpr int kTabStride = 2 * kTabPhases + 1;     // per lane: prefix table, own table, pad
 
 __device__ __forceinline__ void tfold_clear(TFold& x) {
-  x.fk = 0; x.start = 0; x.bt0 = 0; x.f = 0; x.vmask = x.gm = x.gw = x.ga = x.gr = 0;
+  x.fk = 0; x.start = 0; x.bt0 = 0; x.f = 0; x.vmask = x.gm = x.gw = x.ga = x.gr = x.gmb = x.gmw = 0;
 }
 template <bool AT>
 __device__ __forceinline__ bool tfold_racy(const TFold& x) {
@@ -489,7 +490,55 @@ __device__ __forceinline__ bool tfold_racy(const TFold& x) {
   const bool conf = (x.f & kTW) || ((x.f & kTA) && (x.f & kTR));
   return (conf && (x.f & kTMB)) || (x.gm & (x.gw | (x.ga & x.gr))) != 0u;
 }
+
+// With warp or grid barriers the phase field is a fine interval q (block
+// interval c(q), warp interval, grid interval g(q)).  A cell races iff some
+// fine interval holds two (block, thread) and a conflict, some block interval
+// holds two warps of one block and a conflict, or some grid interval holds two
+// blocks and a conflict.  The two coarser tests combine the fine intervals'
+// masks with their first (block, thread) in `tab` (a difference between two
+// fine intervals of one block interval in the block is covered by the grid
+// test, as the block interval lies in one grid interval).
 template <bool AT>
+__device__ bool tfold_racy_sync(const TFold& x, const unsigned* tab, uint64_t coarse_tab, uint64_t grid_tab,
+                                uint32_t tb) {
+  const unsigned confq = x.gw | (AT ? (x.ga & x.gr) : 0u);
+  if (x.gm & confq) return true;
+  unsigned cseen = 0, cmw = 0, cw = 0, ca = 0, cr = 0, gseen = 0, gmb = 0, gw = 0, ga = 0, gr = 0;
+  unsigned cfirst[kTabPhases], gfirst[kTabPhases];
+  const unsigned tmask = (1u << tb) - 1u;
+  unsigned m = x.vmask;
+  while (m) {
+    const int q = __ffs(m) - 1;
+    m &= m - 1;
+    const unsigned qb = 1u << q;
+    const unsigned c = (unsigned)(coarse_tab >> (4 * q)) & 15u, g = (unsigned)(grid_tab >> (4 * q)) & 15u;
+    const unsigned cb = 1u << c, gb = 1u << g;
+    const unsigned bt = tab[q];
+    const unsigned blk = bt >> tb, wrp = (bt & tmask) >> 5;
+    if (!(cseen & cb)) {
+      cseen |= cb;
+      cfirst[c] = bt;
+    } else if ((cfirst[c] >> tb) == blk && ((cfirst[c] & tmask) >> 5) != wrp) {
+      cmw |= cb;
+    }
+    if (x.gmw & qb) cmw |= cb;
+    if (!(gseen & gb)) {
+      gseen |= gb;
+      gfirst[g] = blk;
+    } else if (gfirst[g] != blk) {
+      gmb |= gb;
+    }
+    if (x.gmb & qb) gmb |= gb;
+    if (x.gw & qb) { cw |= cb; gw |= gb; }
+    if (AT) {
+      if (x.ga & qb) { ca |= cb; ga |= gb; }
+      if (x.gr & qb) { cr |= cb; gr |= gb; }
+    }
+  }
+  return (cmw & (cw | (ca & cr))) != 0u || (gmb & (gw | (ga & gr))) != 0u;
+}
+template <bool AT, bool SY>
 __device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
   TFold r;
   r.fk = __shfl_sync(FULL, s.fk, src);
@@ -505,10 +554,22 @@ __device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
   } else {
     r.ga = r.gr = 0;
   }
+  if (SY) {
+    r.gmb = __shfl_sync(FULL, s.gmb, src);
+    r.gmw = __shfl_sync(FULL, s.gmw, src);
+  } else {
+    r.gmb = r.gmw = 0;
+  }
   return r;
 }
 // o (table otab) followed by p (table ptab), a part of the same cell; one lane
-template <bool AT>
+// two first (block, thread) of one fine interval: mark two blocks / two warps
+__device__ __forceinline__ void mark_pair(unsigned a, unsigned b, unsigned bit, uint32_t tb, unsigned& gmb,
+                                          unsigned& gmw) {
+  if ((a ^ b) >> tb) gmb |= bit;
+  else if ((((a ^ b) & ((1u << tb) - 1u)) >> 5) != 0u) gmw |= bit;
+}
+template <bool AT, bool SY>
 __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFold& p, const unsigned* ptab,
                                             uint32_t tb) {
   unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
@@ -521,6 +582,7 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
     const unsigned pv = ptab[ph];
     if (o.vmask & bit) {
       if ((p.gm & bit) || pv != otab[ph]) o.gm |= bit;
+      if (SY && pv != otab[ph]) mark_pair(pv, otab[ph], bit, tb, o.gmb, o.gmw);
     } else {
       otab[ph] = pv;
       o.vmask |= bit;
@@ -532,27 +594,37 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
     o.ga |= p.ga;
     o.gr |= p.gr;
   }
+  if (SY) {
+    o.gmb |= p.gmb;
+    o.gmw |= p.gmw;
+  }
   o.f = f;
 }
 // the warp's carried cell (warp-uniform state, table ctab) followed by p of
 // lane src (table ptab); all lanes, one phase per lane
-template <bool AT>
+template <bool AT, bool SY>
 __device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const TFold& p, const unsigned* ptab,
                                                  uint32_t tb) {
   const int lane = threadIdx.x & 31;
   unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
   if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   bool g = false;
+  unsigned mb = 0, mw = 0;
   if (lane < kTabPhases && (p.vmask >> lane) & 1u) {
     const unsigned pv = ptab[lane];
     if ((o.vmask >> lane) & 1u) {
       g = ((p.gm >> lane) & 1u) || pv != ctab[lane];
+      if (SY && pv != ctab[lane]) mark_pair(pv, ctab[lane], 1u, tb, mb, mw);
     } else {
       ctab[lane] = pv;
       g = (p.gm >> lane) & 1u;
     }
   }
   o.gm |= __ballot_sync(FULL, g);
+  if (SY) {
+    o.gmb |= __ballot_sync(FULL, mb != 0u) | p.gmb;
+    o.gmw |= __ballot_sync(FULL, mw != 0u) | p.gmw;
+  }
   o.vmask |= p.vmask;
   o.gw |= p.gw;
   if (AT) {
@@ -563,8 +635,9 @@ __device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const
   __syncwarp();
 }
 
-// AT: the model has atomic accesses (2-bit kind field: R = 0, W = 1, A = 2)
-template <bool AT>
+// AT: the model has atomic accesses (2-bit kind field: R = 0, W = 1, A = 2);
+// SY: it has warp or grid barriers (fine intervals, tfold_racy_sync)
+template <bool AT, bool SY>
 __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(ScanArgs a) {
   constexpr uint32_t kKindBits = AT ? 2 : 1;
   __shared__ unsigned tabs[kScanWarps][32 * kTabStride];
@@ -581,8 +654,8 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
   unsigned long long count = 0, minstart = ~0ull;
-  auto report = [&](const TFold& x) {
-    if (!tfold_racy<AT>(x)) return;
+  auto report = [&](const TFold& x, const unsigned* xtab) {
+    if (SY ? !tfold_racy_sync<AT>(x, xtab, a.coarse_tab, a.grid_tab, tb) : !tfold_racy<AT>(x)) return;
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
@@ -622,7 +695,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
           P = cur;
           hasP = true;
         } else {
-          report(cur);
+          report(cur, mytab + kTabPhases);
         }
       }
       const bool np = cur_prefix && same_cell;
@@ -634,6 +707,11 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         if (!seen) tab[ph] = bt;
         const unsigned wb = (k & 1ull) ? bit : 0u;
         cur.gm = (do_start ? 0u : cur.gm) | ((seen && old != bt) ? bit : 0u);
+        if (SY) {
+          cur.gmb = do_start ? 0u : cur.gmb;
+          cur.gmw = do_start ? 0u : cur.gmw;
+          if (seen && old != bt) mark_pair(old, bt, bit, tb, cur.gmb, cur.gmw);
+        }
         cur.vmask = (do_start ? 0u : cur.vmask) | bit;
         cur.gw = (do_start ? 0u : cur.gw) | wb;
         unsigned f = do_start ? 0u : cur.f;
@@ -672,12 +750,12 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       for (int src = 0; src < 32 && open; ++src) {
         const bool h = __shfl_sync(FULL, hasP, src);
         const bool full = __shfl_sync(FULL, pfull, src);
-        const TFold pp = tfold_shfl<AT>(P, src);
-        if (h) tfold_merge_warp<AT>(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
+        const TFold pp = tfold_shfl<AT, SY>(P, src);
+        if (h) tfold_merge_warp<AT, SY>(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
         if (!full) open = false;
       }
       if (!open) {
-        if (lane == 0) report(cc);
+        if (lane == 0) report(cc, ctab);
         carry = false;
       } else if (++carried > kCarryMaxSegs) {
         if (lane == 0) hand_over(a, cc.start);
@@ -688,22 +766,22 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     bool open = hasO;
     bool open_end = false;
     if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= a.n)) {
-      report(O);
+      report(O, mytab + kTabPhases);
       open = false;
     }
     for (int d = 1; __any_sync(FULL, open); ++d) {
       const int src = lane + d < 32 ? lane + d : 31;
       const bool h = __shfl_sync(FULL, hasP, src);
       const bool full = __shfl_sync(FULL, pfull, src);
-      const TFold pp = tfold_shfl<AT>(P, src);
+      const TFold pp = tfold_shfl<AT, SY>(P, src);
       if (open) {
         if (lane + d >= 32) {
           open = false;
           open_end = true;
         } else {
-          if (h) tfold_merge<AT>(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
+          if (h) tfold_merge<AT, SY>(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
           if (!full) {
-            report(O);
+            report(O, mytab + kTabPhases);
             open = false;
           }
         }
@@ -713,7 +791,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     const unsigned OE = __ballot_sync(FULL, open_end);
     if (OE) {
       const int src = __ffs(OE) - 1;
-      cc = tfold_shfl<AT>(O, src);
+      cc = tfold_shfl<AT, SY>(O, src);
       if (lane < kTabPhases) ctab[lane] = tabs[w][src * kTabStride + kTabPhases + lane];
       carry = true;
       carried = 0;
@@ -788,10 +866,39 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
     if (threadIdx.x == 0) {
       // a conflict across blocks, or in a phase group with two (block, thread)
       const bool conf = s_w || (s_ga && s_gr);
-      bool racy = conf && s_minb != s_maxb;
       const unsigned gconf = s_gw | (s_ga & s_gr);
+      bool racy = false;
       for (int ph = 0; ph < kTabPhases; ++ph)
         if (((gconf >> ph) & 1u) && mn[ph] != mx[ph]) racy = true;
+      if (!a.sync_scopes) {
+        racy = racy || (conf && s_minb != s_maxb);
+      } else {
+        // warp / grid barriers: two warps of one block in a block interval, or
+        // two blocks in a grid interval, each with a conflict (fine intervals q
+        // mapped by the interval tables; mn / mx are (block, thread) extremes)
+        const unsigned tmask = (1u << a.thread_bits) - 1u;
+        unsigned cmin[kTabPhases], cmax[kTabPhases], gmin[kTabPhases], gmax[kTabPhases];
+        unsigned cseen = 0, gseen = 0, cc = 0, gc = 0, cwm = 0, cam = 0, crm = 0, gwm = 0, gam = 0, grm = 0;
+        for (int q = 0; q < kTabPhases; ++q) {
+          if (mn[q] == 0xffffffffu) continue;
+          const unsigned c = (unsigned)(a.coarse_tab >> (4 * q)) & 15u, g = (unsigned)(a.grid_tab >> (4 * q)) & 15u;
+          if (!((cseen >> c) & 1u)) { cseen |= 1u << c; cmin[c] = mn[q]; cmax[c] = mx[q]; }
+          else { cmin[c] = min(cmin[c], mn[q]); cmax[c] = max(cmax[c], mx[q]); }
+          if (!((gseen >> g) & 1u)) { gseen |= 1u << g; gmin[g] = mn[q] >> a.thread_bits; gmax[g] = mx[q] >> a.thread_bits; }
+          else { gmin[g] = min(gmin[g], mn[q] >> a.thread_bits); gmax[g] = max(gmax[g], mx[q] >> a.thread_bits); }
+          if ((s_gw >> q) & 1u) { cwm |= 1u << c; gwm |= 1u << g; }
+          if ((s_ga >> q) & 1u) { cam |= 1u << c; gam |= 1u << g; }
+          if ((s_gr >> q) & 1u) { crm |= 1u << c; grm |= 1u << g; }
+        }
+        cc = cwm | (cam & crm);
+        gc = gwm | (gam & grm);
+        for (int c = 0; c < kTabPhases; ++c)
+          if (((cc >> c) & 1u) && (cmin[c] >> a.thread_bits) == (cmax[c] >> a.thread_bits) &&
+              ((cmin[c] & tmask) >> 5) != ((cmax[c] & tmask) >> 5))
+            racy = true;
+        for (int g = 0; g < kTabPhases; ++g)
+          if (((gc >> g) & 1u) && gmin[g] != gmax[g]) racy = true;
+      }
       if (racy) {
         DevResult* r = result_of(a, cell);
         atomicAdd(&r->racy_cells, 1ull);
@@ -859,6 +966,8 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
       gr[2 + 3 * k] = 0xffffffffu;
       gr[3 + 3 * k] = 0;
       gr[4 + 3 * k] = 0;
+      gr[11 + 2 * k] = 0xffffffffu;
+      gr[12 + 2 * k] = 0;
     }
   }
   const uint64_t e = r->seg_end;
@@ -908,8 +1017,13 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   const unsigned b0 = r->minb;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
-    if (f.b != b0) continue;
     unsigned* g = groups + f.p * kGroupWords;
+    if (a.sync_scopes) {
+      // blocks holding each kind per fine interval (cross-block partners of one grid interval)
+      atomicMin(&g[11 + 2 * f.k], f.b);
+      atomicMax(&g[12 + 2 * f.k], f.b);
+    }
+    if (f.b != b0) continue;
     atomicMin(&g[0], f.t);
     atomicMax(&g[1], f.t);
     unsigned* gk = g + 2 + 3 * f.k;
@@ -938,15 +1052,34 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (!kinds_conflict(f.k, (unsigned)k)) continue;
-      // a conflicting instance in another block (global cells; a shared cell has one block)
-      cross |= kany[k] && (kminb[k] != b0 || kmaxb[k] != b0);
-      // a conflicting instance of another thread in the same block and phase
+      // a conflicting instance of another thread in the same block and (fine) phase
       const unsigned* gk = g + 2 + 3 * k;
       same |= gk[2] && (gk[0] != f.t || gk[1] != f.t);
+      if (!a.sync_scopes) {
+        // a conflicting instance in another block (global cells; a shared cell has one block)
+        cross |= kany[k] && (kminb[k] != b0 || kmaxb[k] != b0);
+        continue;
+      }
+      // warp / grid barriers: another block of the same grid interval, or another
+      // warp of this block in the same block interval
+      const unsigned xc = (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u, xg = (unsigned)(a.grid_tab >> (4 * f.p)) & 15u;
+      for (unsigned q = 0; q < (1u << a.phase_bits); ++q) {
+        const unsigned* gq = groups + q * kGroupWords;
+        if ((((unsigned)(a.grid_tab >> (4 * q)) & 15u) == xg) && gq[11 + 2 * k] != 0xffffffffu &&
+            (gq[11 + 2 * k] != b0 || gq[12 + 2 * k] != b0))
+          cross = true;
+        if (q != f.p && (((unsigned)(a.coarse_tab >> (4 * q)) & 15u) == xc)) {
+          const unsigned* gqk = gq + 2 + 3 * k;
+          if (gqk[2] && ((gqk[0] >> 5) != (f.t >> 5) || (gqk[1] >> 5) != (f.t >> 5))) same = true;
+        }
+      }
     }
     if (cross || same) {
-      const unsigned long long rank = ((unsigned long long)f.p << (a.thread_bits + kb)) |
-                                      ((unsigned long long)f.t << kb) | f.k;
+      // rank in the tuple order (phase, thread, kind, warp phase)
+      const unsigned p = a.sync_scopes ? (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u : f.p;
+      const unsigned wv = f.p - p * a.n_wp;
+      const unsigned long long rank = ((((unsigned long long)p << (a.thread_bits + kb)) |
+                                        ((unsigned long long)f.t << kb) | f.k) << a.wp_bits) | wv;
       best = rank < best ? rank : best;
     }
   }
@@ -967,18 +1100,27 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   const unsigned b0 = r->minb;
   const uint32_t kb = a.thread_shift;
   const unsigned long long xr = r->x_rank;
-  const unsigned xk = (unsigned)(xr & ((1ull << kb) - 1ull));
-  const unsigned xt = (unsigned)(xr >> kb) & ((1u << a.thread_bits) - 1u);
-  const unsigned xp = (unsigned)(xr >> (a.thread_bits + kb));
+  const uint32_t wb = a.wp_bits;
+  const unsigned xw = (unsigned)(xr & ((1ull << wb) - 1ull));
+  const unsigned xk = (unsigned)(xr >> wb) & ((1u << kb) - 1u);
+  const unsigned xt = (unsigned)(xr >> (wb + kb)) & ((1u << a.thread_bits) - 1u);
+  const unsigned xp = (unsigned)(xr >> (wb + kb + a.thread_bits));
+  const unsigned xq = xp * a.n_wp + xw;
+  const unsigned xg = (unsigned)(a.grid_tab >> (4 * xq)) & 15u;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
+    const unsigned yp = a.sync_scopes ? (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u : f.p;
+    const unsigned yw = f.p - yp * a.n_wp;
     const bool other_thread = f.b != b0 || f.t != xt;
-    const bool concurrent = f.b != b0 || f.p == xp;
+    bool concurrent;
+    if (!a.sync_scopes) concurrent = f.b != b0 || f.p == xp;
+    else if (f.b != b0) concurrent = ((unsigned)(a.grid_tab >> (4 * f.p)) & 15u) == xg;
+    else concurrent = yp == xp && ((f.t >> 5) != (xt >> 5) || yw == xw);
     if (other_thread && kinds_conflict(xk, f.k) && concurrent) {
       const unsigned long long rank =
-          ((unsigned long long)f.b << (a.phase_bits + a.thread_bits + kb)) |
-          ((unsigned long long)f.p << (a.thread_bits + kb)) | ((unsigned long long)f.t << kb) | f.k;
+          ((((unsigned long long)f.b << (a.phase_bits + a.thread_bits + kb)) |
+            ((unsigned long long)yp << (a.thread_bits + kb)) | ((unsigned long long)f.t << kb) | f.k) << wb) | yw;
       best = rank < best ? rank : best;
     }
   }
@@ -1029,8 +1171,13 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   if (a.n > 0) {
     const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
-    if (a.phase_table && a.thread_shift == 2) scan_cells_table_kernel<true><<<blocks, kScanWarps * 32, 0, st>>>(a);
-    else if (a.phase_table) scan_cells_table_kernel<false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+    if (a.phase_table) {
+      const bool at = a.thread_shift == 2, sy = a.sync_scopes != 0;
+      if (at && sy) scan_cells_table_kernel<true, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      else if (at) scan_cells_table_kernel<true, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      else if (sy) scan_cells_table_kernel<false, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      else scan_cells_table_kernel<false, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+    }
     else scan_cells_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

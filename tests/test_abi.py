@@ -133,7 +133,7 @@ def test_generated_kernels_compile(rc, tmp_path):
     csr = w.ge_spmm_csr(w.csr_row_lengths(1, 8), N=64, K=2)
     wide = w.random_affine(1, n_blocks=8, block=64, n_stmts=12, row_global=1 << 44)
     for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep, csr,
-                           w.tiny_random_tables(3), wide]):
+                           w.tiny_random_tables(3), wide, w.tiny_random_sync(2), w.warp_reduction(2)]):
         src = rc.rc_kernel_source(m)
         assert ("rc_chunk_jit" if m is wide else "rc_expand_jit") in src
         f = tmp_path / f"k{i}.cu"

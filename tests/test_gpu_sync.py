@@ -1,0 +1,100 @@
+"""Warp-scope (__syncwarp) and grid-wide barriers on the CUDA path: blocks are
+ordered only by grid barriers, two warps of one block only by block barriers,
+the threads of one warp also by warp barriers.  Parity with the oracle (count,
+instance count, witness and the witness's warp phases bit-exact) on the sort
+path with interpreted and generated expansion, and in chunked checks."""
+import pytest
+import torch
+
+import oracle
+import workloads as w
+from workloads.spec import A, Access, Array, Model, Stmt, const, tid, R, W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rc():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_08946_gb300 import build as b
+    b.build()
+    oracle.build()
+    import paper_2503_08946_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def compare(rc, model, opts=None):
+    got = rc.check(model, opts)
+    exp = oracle.check(model)
+    assert got.status == exp.status, (model.name, got, exp)
+    assert got.instances == exp.instances
+    if exp.status == oracle.STATUS_OOB:
+        assert (got.oob_stmt, got.oob_access, got.oob_gtid, got.oob_dim) == \
+               (exp.oob_stmt, exp.oob_access, exp.oob_gtid, exp.oob_dim)
+        return got
+    assert (got.verdict, got.racy_cells) == (exp.verdict, exp.racy_cells), (model.name, got, exp)
+    assert got.witness == exp.witness, (model.name, got.witness, exp.witness)
+    if exp.verdict:
+        assert (got.x_wphase, got.y_wphase) == (exp.x_wphase, exp.y_wphase)
+    return got
+
+
+@pytest.mark.parametrize("nw,bar,shared,exp", [(2, True, False, 0), (2, False, False, 30), (1, False, False, 15),
+                                               (2, True, True, 16), (3, False, True, 16), (1, True, True, 0),
+                                               (16, True, False, 0), (16, False, False, 240)])
+def test_warp_reduction(rc, nw, bar, shared, exp):
+    g = compare(rc, w.warp_reduction(n_warps=nw, warp_barriers=bar, shared_half=shared))
+    assert g.racy_cells == exp
+
+
+@pytest.mark.parametrize("nb,bs,grid,exp", [(4, 8, True, 0), (4, 8, False, 4), (1, 8, False, 0), (3, 33, False, 3),
+                                            (256, 256, False, 256), (256, 256, True, 0)])
+def test_grid_neighbor(rc, nb, bs, grid, exp):
+    g = compare(rc, w.grid_neighbor(nb, bs, grid_barrier=grid))
+    assert g.racy_cells == exp
+
+
+@pytest.mark.parametrize("seed", range(150))
+@pytest.mark.parametrize("jit", ["0", "1"])
+def test_tiny_random_sync(rc, seed, jit, monkeypatch):
+    monkeypatch.setenv("RC_JIT", jit)   # interpreted / generated expansion
+    compare(rc, w.tiny_random_sync(seed))
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_tiny_random_sync_chunked(rc, seed):
+    compare(rc, w.tiny_random_sync(seed), {"flags": rc.binding.RC_OPT_CHUNKED})
+
+
+@pytest.mark.parametrize("gp", [[0, 0, 0], [0, 0, 1], [0, 1, 2]])
+def test_long_cells(rc, gp):
+    """Cells of tens of thousands of keys (the long-cell pass and the witness on them)."""
+    c = Array("c", "global", (2,))
+    lane0 = [-1 * (tid.x % 32)]
+    stmts = [Stmt([Access(0, R, (const(0),))], phase=const(0), warp_phase=(tid.x // 32) % 2),
+             Stmt([Access(0, A, (const(0),))], guards=lane0, phase=const(0), warp_phase=const(1)),
+             Stmt([Access(0, W, (const(1),))], guards=lane0, phase=const(1), warp_phase=const(0)),
+             Stmt([Access(0, R, (const(1),))], phase=const(2))]
+    m = Model((200, 1, 1), (128, 1, 1), [c], stmts, n_phases=3, n_warp_phases=2, grid_phase=gp, name="sync_long")
+    compare(rc, m)
+
+
+def test_out_of_range_warp_phase(rc):
+    m = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
+              [Stmt([Access(0, W, (tid.x,))], warp_phase=tid.x // 32 + 1)], n_warp_phases=2, name="wp_oob")
+    compare(rc, m)
+
+
+def test_sync_models_rejected_where_unsupported(rc):
+    b = rc.binding
+    h = b.rc_model_create(w.warp_reduction(2))
+    with pytest.raises(b.RcError) as e:
+        b.rc_batch_workspace_size([h])
+    assert e.value.status == b.RC_E_UNSUPPORTED
+    with pytest.raises(b.RcError) as e:
+        b.rc_check(h, {"path": b.RC_PATH_HASH}, b.workspace(1 << 20))
+    assert e.value.status == b.RC_E_UNSUPPORTED
+    too_many = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
+                     [Stmt([Access(0, W, (tid.x,))], phase=const(0))], n_phases=5, n_warp_phases=4)
+    assert b.rc_model_create_status(too_many) == b.RC_E_UNSUPPORTED
