@@ -131,12 +131,16 @@ struct ScanArgs {
   const uint64_t* cell_base;           // batch: first batch cell of each model (ascending)
   uint32_t n_models;                   // batch: number of models (0 = single model)
   uint32_t phase_table;                // keys sorted by cell only (phase_bits <= kScanTablePhaseBits)
-  // warp and grid barriers: the phase field is a fine interval q; block
-  // interval and grid interval of q (4 bits per q); warp intervals per block
-  // interval and their bit width (0 without warp barriers)
-  uint32_t sync_scopes;
-  uint32_t n_wp, wp_bits;
-  uint64_t coarse_tab, grid_tab;
+  // warp and grid barriers (null without them): the phase field is a fine
+  // interval q; device words [block interval of q, grid interval of q (4 bits
+  // per q each), warp intervals per block interval | their bit width << 32]
+  const uint64_t* sync_tabs;
+};
+// the interval tables of a scan (no warp or grid barriers: q is the phase)
+struct SyncTabs {
+  uint64_t coarse = 0, grid = 0;
+  uint32_t n_wp = 1, wp_bits = 0;
+  bool on = false;
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);

@@ -316,6 +316,9 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     m->grid_tab |= ((uint64_t)(d->grid_phase ? d->grid_phase[p] : 0u) & 15u) << (4 * q);
     if (d->grid_phase && d->grid_phase[p] > 15u) return RC_E_UNSUPPORTED;
   }
+  h.sync_tab[0] = m->coarse_tab;
+  h.sync_tab[1] = m->grid_tab;
+  h.sync_tab[2] = (uint64_t)n_wp | ((uint64_t)bit_length((uint64_t)n_wp - 1) << 32);
   // atomics are scanned by the phase-table scan only (at most 16 intervals)
   if (has_atomic && h.phase_bits > (uint32_t)kScanTablePhaseBits) return RC_E_UNSUPPORTED;
   h.cell_shift = h.phase_shift + h.phase_bits;

@@ -137,6 +137,9 @@ struct DevModel {
   const uint64_t* tables;       // per table: offset into tdata, length (2 words each)
   const int64_t* tdata;         // table values
   uint32_t n_tables, pad_t;
+  // warp / grid barriers: block interval and grid interval of each fine
+  // interval (4 bits per interval), warp intervals | their bit width << 32
+  uint64_t sync_tab[3];
 };
 
 // Value of a table load: tables read as 0 outside [0, len), so a load is a

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdlib>
 #include <map>
 #include <cstring>
@@ -232,11 +233,10 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.cell_base = nullptr;
   a.n_models = 0;
   a.phase_table = m.host.phase_bits <= rc::kScanTablePhaseBits ? 1u : 0u;
-  a.sync_scopes = m.sync_scopes ? 1u : 0u;
-  a.n_wp = (uint32_t)m.host.n_wphases;
-  a.wp_bits = rc::bit_length((uint64_t)m.host.n_wphases - 1);
-  a.coarse_tab = m.coarse_tab;
-  a.grid_tab = m.grid_tab;
+  // the interval tables live in the uploaded program header
+  a.sync_tabs = m.sync_scopes ? reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(m.dev_program) +
+                                                                  offsetof(rc::DevModel, sync_tab))
+                              : nullptr;
   return a;
 }
 
@@ -956,10 +956,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.cell_base = dcbase + k.i0;
     sa.n_models = nm;
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
-    sa.sync_scopes = 0;   // models with warp or grid barriers are not batched
-    sa.n_wp = 1;
-    sa.wp_bits = 0;
-    sa.coarse_tab = sa.grid_tab = 0;
+    sa.sync_tabs = nullptr;   // models with warp or grid barriers are not batched
     s = cuda_status(rc::launch_scan(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));

@@ -84,6 +84,19 @@ __device__ __forceinline__ DevResult* result_of(const ScanArgs& a, uint64_t cell
   return a.res + lo;
 }
 
+// The interval tables of models with warp or grid barriers (see ScanArgs).
+__device__ __forceinline__ SyncTabs sync_tabs_of(const ScanArgs& a) {
+  SyncTabs t;
+  if (a.sync_tabs) {
+    t.coarse = a.sync_tabs[0];
+    t.grid = a.sync_tabs[1];
+    t.n_wp = (uint32_t)a.sync_tabs[2];
+    t.wp_bits = (uint32_t)(a.sync_tabs[2] >> 32);
+    t.on = true;
+  }
+  return t;
+}
+
 // Fold state of a run of keys of one cell (a whole cell, or a part of one).
 // Keys are compared through masks: same cell iff ((k ^ k') & cell_mask) == 0,
 // same phase group iff ((k ^ k') & group_mask) == 0.  bt = the (block, thread)
@@ -474,14 +487,21 @@ struct TFold {
   unsigned gm;       // phases with two (block, thread)
   unsigned gw;       // phases with a write
   unsigned ga, gr;   // phases with an atomic / a plain read (atomic models only)
-  unsigned gmb, gmw; // phases with two blocks / two warps of one block (warp or grid barriers only)
 };
+// the fold of models with warp or grid barriers
+struct TFoldSync : TFold {
+  unsigned gmb, gmw; // phases with two blocks / two warps of one block
+};
+template <bool SY> struct FoldOf { using type = TFold; };
+template <> struct FoldOf<true> { using type = TFoldSync; };
 constexpr unsigned kTW = 1u, kTMB = 2u, kTA = 4u, kTR = 8u;
 constexpr int kTabPhases = 1 << kScanTablePhaseBits;
 constexpr int kTabStride = 2 * kTabPhases + 1;     // per lane: prefix table, own table, pad
 
-__device__ __forceinline__ void tfold_clear(TFold& x) {
-  x.fk = 0; x.start = 0; x.bt0 = 0; x.f = 0; x.vmask = x.gm = x.gw = x.ga = x.gr = x.gmb = x.gmw = 0;
+template <class F>
+__device__ __forceinline__ void tfold_clear(F& x) {
+  x.fk = 0; x.start = 0; x.bt0 = 0; x.f = 0; x.vmask = x.gm = x.gw = x.ga = x.gr = 0;
+  if constexpr (sizeof(F) != sizeof(TFold)) x.gmb = x.gmw = 0;
 }
 template <bool AT>
 __device__ __forceinline__ bool tfold_racy(const TFold& x) {
@@ -500,7 +520,7 @@ __device__ __forceinline__ bool tfold_racy(const TFold& x) {
 // fine intervals of one block interval in the block is covered by the grid
 // test, as the block interval lies in one grid interval).
 template <bool AT>
-__device__ bool tfold_racy_sync(const TFold& x, const unsigned* tab, uint64_t coarse_tab, uint64_t grid_tab,
+__device__ bool tfold_racy_sync(const TFoldSync& x, const unsigned* tab, uint64_t coarse_tab, uint64_t grid_tab,
                                 uint32_t tb) {
   const unsigned confq = x.gw | (AT ? (x.ga & x.gr) : 0u);
   if (x.gm & confq) return true;
@@ -539,8 +559,8 @@ __device__ bool tfold_racy_sync(const TFold& x, const unsigned* tab, uint64_t co
   return (cmw & (cw | (ca & cr))) != 0u || (gmb & (gw | (ga & gr))) != 0u;
 }
 template <bool AT, bool SY>
-__device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
-  TFold r;
+__device__ __forceinline__ typename FoldOf<SY>::type tfold_shfl(const typename FoldOf<SY>::type& s, int src) {
+  typename FoldOf<SY>::type r;
   r.fk = __shfl_sync(FULL, s.fk, src);
   r.start = __shfl_sync(FULL, s.start, src);
   r.bt0 = __shfl_sync(FULL, s.bt0, src);
@@ -554,11 +574,9 @@ __device__ __forceinline__ TFold tfold_shfl(const TFold& s, int src) {
   } else {
     r.ga = r.gr = 0;
   }
-  if (SY) {
+  if constexpr (SY) {
     r.gmb = __shfl_sync(FULL, s.gmb, src);
     r.gmw = __shfl_sync(FULL, s.gmw, src);
-  } else {
-    r.gmb = r.gmw = 0;
   }
   return r;
 }
@@ -570,8 +588,8 @@ __device__ __forceinline__ void mark_pair(unsigned a, unsigned b, unsigned bit, 
   else if ((((a ^ b) & ((1u << tb) - 1u)) >> 5) != 0u) gmw |= bit;
 }
 template <bool AT, bool SY>
-__device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFold& p, const unsigned* ptab,
-                                            uint32_t tb) {
+__device__ __forceinline__ void tfold_merge(typename FoldOf<SY>::type& o, unsigned* otab,
+                                            const typename FoldOf<SY>::type& p, const unsigned* ptab, uint32_t tb) {
   unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
   if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   unsigned m = p.vmask;
@@ -582,7 +600,9 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
     const unsigned pv = ptab[ph];
     if (o.vmask & bit) {
       if ((p.gm & bit) || pv != otab[ph]) o.gm |= bit;
-      if (SY && pv != otab[ph]) mark_pair(pv, otab[ph], bit, tb, o.gmb, o.gmw);
+      if constexpr (SY) {
+        if (pv != otab[ph]) mark_pair(pv, otab[ph], bit, tb, o.gmb, o.gmw);
+      }
     } else {
       otab[ph] = pv;
       o.vmask |= bit;
@@ -594,7 +614,7 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
     o.ga |= p.ga;
     o.gr |= p.gr;
   }
-  if (SY) {
+  if constexpr (SY) {
     o.gmb |= p.gmb;
     o.gmw |= p.gmw;
   }
@@ -603,8 +623,8 @@ __device__ __forceinline__ void tfold_merge(TFold& o, unsigned* otab, const TFol
 // the warp's carried cell (warp-uniform state, table ctab) followed by p of
 // lane src (table ptab); all lanes, one phase per lane
 template <bool AT, bool SY>
-__device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const TFold& p, const unsigned* ptab,
-                                                 uint32_t tb) {
+__device__ __forceinline__ void tfold_merge_warp(typename FoldOf<SY>::type& o, unsigned* ctab,
+                                                 const typename FoldOf<SY>::type& p, const unsigned* ptab, uint32_t tb) {
   const int lane = threadIdx.x & 31;
   unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
   if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
@@ -614,14 +634,16 @@ __device__ __forceinline__ void tfold_merge_warp(TFold& o, unsigned* ctab, const
     const unsigned pv = ptab[lane];
     if ((o.vmask >> lane) & 1u) {
       g = ((p.gm >> lane) & 1u) || pv != ctab[lane];
-      if (SY && pv != ctab[lane]) mark_pair(pv, ctab[lane], 1u, tb, mb, mw);
+      if constexpr (SY) {
+        if (pv != ctab[lane]) mark_pair(pv, ctab[lane], 1u, tb, mb, mw);
+      }
     } else {
       ctab[lane] = pv;
       g = (p.gm >> lane) & 1u;
     }
   }
   o.gm |= __ballot_sync(FULL, g);
-  if (SY) {
+  if constexpr (SY) {
     o.gmb |= __ballot_sync(FULL, mb != 0u) | p.gmb;
     o.gmw |= __ballot_sync(FULL, mw != 0u) | p.gmw;
   }
@@ -654,8 +676,16 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
   unsigned long long count = 0, minstart = ~0ull;
-  auto report = [&](const TFold& x, const unsigned* xtab) {
-    if (SY ? !tfold_racy_sync<AT>(x, xtab, a.coarse_tab, a.grid_tab, tb) : !tfold_racy<AT>(x)) return;
+  using TF = typename FoldOf<SY>::type;
+  SyncTabs syt;
+  if constexpr (SY) syt = sync_tabs_of(a);
+  auto report = [&](const TF& x, const unsigned* xtab) {
+    if constexpr (SY) {
+      if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
+    } else {
+      (void)xtab;
+      if (!tfold_racy<AT>(x)) return;
+    }
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
@@ -667,7 +697,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   };
   bool carry = false;
   int carried = 0;
-  TFold cc;
+  TF cc;
   tfold_clear(cc);
   for (uint64_t seg = seg0; seg < seg1; ++seg) {
     const uint64_t S = seg * kSegKeys;
@@ -676,7 +706,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     // lines of a run are shared by its consecutive loads through L1)
     const uint64_t s = S + (uint64_t)lane * kScanRun;
     const uint64_t kp = (s > 0 && s - 1 < a.n) ? __ldg(a.keys + s - 1) : kSentinel;
-    TFold P, cur;
+    TF P, cur;
     tfold_clear(P);
     cur = P;
     cur.fk = kp;
@@ -707,7 +737,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         if (!seen) tab[ph] = bt;
         const unsigned wb = (k & 1ull) ? bit : 0u;
         cur.gm = (do_start ? 0u : cur.gm) | ((seen && old != bt) ? bit : 0u);
-        if (SY) {
+        if constexpr (SY) {
           cur.gmb = do_start ? 0u : cur.gmb;
           cur.gmw = do_start ? 0u : cur.gmw;
           if (seen && old != bt) mark_pair(old, bt, bit, tb, cur.gmb, cur.gmw);
@@ -733,7 +763,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       }
     }
     bool hasO = false;
-    TFold O = cur;
+    TF O = cur;
     if (!cur_empty) {
       if (cur_prefix) {
         P = cur;
@@ -750,7 +780,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       for (int src = 0; src < 32 && open; ++src) {
         const bool h = __shfl_sync(FULL, hasP, src);
         const bool full = __shfl_sync(FULL, pfull, src);
-        const TFold pp = tfold_shfl<AT, SY>(P, src);
+        const TF pp = tfold_shfl<AT, SY>(P, src);
         if (h) tfold_merge_warp<AT, SY>(cc, ctab, pp, tabs[w] + src * kTabStride, tb);
         if (!full) open = false;
       }
@@ -773,7 +803,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const int src = lane + d < 32 ? lane + d : 31;
       const bool h = __shfl_sync(FULL, hasP, src);
       const bool full = __shfl_sync(FULL, pfull, src);
-      const TFold pp = tfold_shfl<AT, SY>(P, src);
+      const TF pp = tfold_shfl<AT, SY>(P, src);
       if (open) {
         if (lane + d >= 32) {
           open = false;
@@ -820,6 +850,7 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
   __shared__ unsigned s_gw, s_ga, s_gr, s_minb, s_maxb, s_w;
   const uint32_t kb = a.thread_shift;   // kind field bits (R = 0, W = 1, A = 2)
   const uint64_t kmask = (1ull << kb) - 1ull;
+  const SyncTabs syt = sync_tabs_of(a);
   const unsigned pm = (1u << a.phase_bits) - 1u;
   const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
   const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
@@ -870,7 +901,7 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
       bool racy = false;
       for (int ph = 0; ph < kTabPhases; ++ph)
         if (((gconf >> ph) & 1u) && mn[ph] != mx[ph]) racy = true;
-      if (!a.sync_scopes) {
+      if (!syt.on) {
         racy = racy || (conf && s_minb != s_maxb);
       } else {
         // warp / grid barriers: two warps of one block in a block interval, or
@@ -881,7 +912,7 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
         unsigned cseen = 0, gseen = 0, cc = 0, gc = 0, cwm = 0, cam = 0, crm = 0, gwm = 0, gam = 0, grm = 0;
         for (int q = 0; q < kTabPhases; ++q) {
           if (mn[q] == 0xffffffffu) continue;
-          const unsigned c = (unsigned)(a.coarse_tab >> (4 * q)) & 15u, g = (unsigned)(a.grid_tab >> (4 * q)) & 15u;
+          const unsigned c = (unsigned)(syt.coarse >> (4 * q)) & 15u, g = (unsigned)(syt.grid >> (4 * q)) & 15u;
           if (!((cseen >> c) & 1u)) { cseen |= 1u << c; cmin[c] = mn[q]; cmax[c] = mx[q]; }
           else { cmin[c] = min(cmin[c], mn[q]); cmax[c] = max(cmax[c], mx[q]); }
           if (!((gseen >> g) & 1u)) { gseen |= 1u << g; gmin[g] = mn[q] >> a.thread_bits; gmax[g] = mx[q] >> a.thread_bits; }
@@ -1010,6 +1041,7 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
+  const SyncTabs syt = sync_tabs_of(a);
   unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
@@ -1018,7 +1050,7 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
     unsigned* g = groups + f.p * kGroupWords;
-    if (a.sync_scopes) {
+    if (syt.on) {
       // blocks holding each kind per fine interval (cross-block partners of one grid interval)
       atomicMin(&g[11 + 2 * f.k], f.b);
       atomicMax(&g[12 + 2 * f.k], f.b);
@@ -1035,6 +1067,7 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
+  const SyncTabs syt = sync_tabs_of(a);
   const unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
@@ -1055,20 +1088,20 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
       // a conflicting instance of another thread in the same block and (fine) phase
       const unsigned* gk = g + 2 + 3 * k;
       same |= gk[2] && (gk[0] != f.t || gk[1] != f.t);
-      if (!a.sync_scopes) {
+      if (!syt.on) {
         // a conflicting instance in another block (global cells; a shared cell has one block)
         cross |= kany[k] && (kminb[k] != b0 || kmaxb[k] != b0);
         continue;
       }
       // warp / grid barriers: another block of the same grid interval, or another
       // warp of this block in the same block interval
-      const unsigned xc = (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u, xg = (unsigned)(a.grid_tab >> (4 * f.p)) & 15u;
+      const unsigned xc = (unsigned)(syt.coarse >> (4 * f.p)) & 15u, xg = (unsigned)(syt.grid >> (4 * f.p)) & 15u;
       for (unsigned q = 0; q < (1u << a.phase_bits); ++q) {
         const unsigned* gq = groups + q * kGroupWords;
-        if ((((unsigned)(a.grid_tab >> (4 * q)) & 15u) == xg) && gq[11 + 2 * k] != 0xffffffffu &&
+        if ((((unsigned)(syt.grid >> (4 * q)) & 15u) == xg) && gq[11 + 2 * k] != 0xffffffffu &&
             (gq[11 + 2 * k] != b0 || gq[12 + 2 * k] != b0))
           cross = true;
-        if (q != f.p && (((unsigned)(a.coarse_tab >> (4 * q)) & 15u) == xc)) {
+        if (q != f.p && (((unsigned)(syt.coarse >> (4 * q)) & 15u) == xc)) {
           const unsigned* gqk = gq + 2 + 3 * k;
           if (gqk[2] && ((gqk[0] >> 5) != (f.t >> 5) || (gqk[1] >> 5) != (f.t >> 5))) same = true;
         }
@@ -1076,10 +1109,10 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
     }
     if (cross || same) {
       // rank in the tuple order (phase, thread, kind, warp phase)
-      const unsigned p = a.sync_scopes ? (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u : f.p;
-      const unsigned wv = f.p - p * a.n_wp;
+      const unsigned p = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
+      const unsigned wv = f.p - p * syt.n_wp;
       const unsigned long long rank = ((((unsigned long long)p << (a.thread_bits + kb)) |
-                                        ((unsigned long long)f.t << kb) | f.k) << a.wp_bits) | wv;
+                                        ((unsigned long long)f.t << kb) | f.k) << syt.wp_bits) | wv;
       best = rank < best ? rank : best;
     }
   }
@@ -1094,28 +1127,29 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
+  const SyncTabs syt = sync_tabs_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;
   const unsigned b0 = r->minb;
   const uint32_t kb = a.thread_shift;
   const unsigned long long xr = r->x_rank;
-  const uint32_t wb = a.wp_bits;
+  const uint32_t wb = syt.wp_bits;
   const unsigned xw = (unsigned)(xr & ((1ull << wb) - 1ull));
   const unsigned xk = (unsigned)(xr >> wb) & ((1u << kb) - 1u);
   const unsigned xt = (unsigned)(xr >> (wb + kb)) & ((1u << a.thread_bits) - 1u);
   const unsigned xp = (unsigned)(xr >> (wb + kb + a.thread_bits));
-  const unsigned xq = xp * a.n_wp + xw;
-  const unsigned xg = (unsigned)(a.grid_tab >> (4 * xq)) & 15u;
+  const unsigned xq = xp * syt.n_wp + xw;
+  const unsigned xg = (unsigned)(syt.grid >> (4 * xq)) & 15u;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
-    const unsigned yp = a.sync_scopes ? (unsigned)(a.coarse_tab >> (4 * f.p)) & 15u : f.p;
-    const unsigned yw = f.p - yp * a.n_wp;
+    const unsigned yp = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
+    const unsigned yw = f.p - yp * syt.n_wp;
     const bool other_thread = f.b != b0 || f.t != xt;
     bool concurrent;
-    if (!a.sync_scopes) concurrent = f.b != b0 || f.p == xp;
-    else if (f.b != b0) concurrent = ((unsigned)(a.grid_tab >> (4 * f.p)) & 15u) == xg;
+    if (!syt.on) concurrent = f.b != b0 || f.p == xp;
+    else if (f.b != b0) concurrent = ((unsigned)(syt.grid >> (4 * f.p)) & 15u) == xg;
     else concurrent = yp == xp && ((f.t >> 5) != (xt >> 5) || yw == xw);
     if (other_thread && kinds_conflict(xk, f.k) && concurrent) {
       const unsigned long long rank =
@@ -1172,7 +1206,7 @@ cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   if (a.n > 0) {
     const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
     if (a.phase_table) {
-      const bool at = a.thread_shift == 2, sy = a.sync_scopes != 0;
+      const bool at = a.thread_shift == 2, sy = a.sync_tabs != nullptr;
       if (at && sy) scan_cells_table_kernel<true, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
       else if (at) scan_cells_table_kernel<true, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
       else if (sy) scan_cells_table_kernel<false, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
