@@ -283,10 +283,10 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
 // ---------------------------------------------------------------------------
 // unstable partition pass (the first pass of a check's sort: its input is the
 // expansion order, which carries no meaning, so equal digits may come out in
-// any order).  Each tile ranks its keys with block-wide digit counters (the
-// lowest lane of each group adds the group size with one atomic that returns
-// the base), claims each digit's output range from a global cursor (started at
-// the digit's offset), stages the keys in digit order and scatters them.  No
+// any order).  Each tile ranks its keys with block-wide digit counters (one
+// shared atomic per key, or per warp when the warp holds a single digit),
+// claims each digit's output range from a global cursor (started at the
+// digit's offset), stages the keys in digit order and scatters them.  No
 // look-back and no waiting: tiles are independent.
 // ---------------------------------------------------------------------------
 template <int RB>
@@ -318,18 +318,24 @@ __global__ void __launch_bounds__(kSortThreads, 3) partition_kernel(SortArgs a) 
     const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
     k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
   }
+  // ranks within the tile's digit buckets in any order: one shared atomic per
+  // lane, or one per warp when the whole warp holds one digit (frequent: the 32
+  // keys of a warp come from one access of 32 consecutive threads)
   unsigned short r[kSortItems];
-  const unsigned int lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
-    const unsigned int peers = digit_peers<RB>(d, valid);
-    const unsigned int leader = __ffs(peers) - 1;
-    unsigned int base = 0;
-    if (lane == leader && valid) base = atomicAdd(&cnt[d], (unsigned int)__popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    r[i] = (unsigned short)(base + __popc(peers & lt));
+    const unsigned int d0 = __shfl_sync(0xffffffffu, d, 0);
+    unsigned int rank = 0;
+    if (__all_sync(0xffffffffu, valid && d == d0)) {
+      unsigned int base = 0;
+      if (lane == 0) base = atomicAdd(&cnt[d0], 32u);
+      rank = __shfl_sync(0xffffffffu, base, 0) + (unsigned int)lane;
+    } else if (valid) {
+      rank = atomicAdd(&cnt[d], 1u);
+    }
+    r[i] = (unsigned short)rank;
   }
   __syncthreads();
   // per digit dg = q * kSortThreads + tid: claim the output range, tile offsets
