@@ -17,9 +17,32 @@ struct ThreadVars {
   uint64_t gtid;
 };
 
+// a / d for a < 2^32 by the multiply-high reciprocal of d (magic 0: d = 1)
+__device__ __forceinline__ uint64_t div_small(uint64_t a, uint64_t magic) {
+  return magic ? __umul64hi(magic, a) : a;
+}
+
 __device__ __forceinline__ ThreadVars thread_vars(const DevModel& M, uint64_t gtid) {
   ThreadVars tv;
   tv.gtid = gtid;
+  if (M.n_threads < (1ull << 32)) {
+    // every quotient and remainder below has operands under 2^32
+    const uint64_t* mg = M.div_magic;
+    const uint64_t b = div_small(gtid, mg[0]);
+    const uint32_t t = (uint32_t)(gtid - b * M.bs);
+    tv.b = b;
+    tv.t = t;
+    const uint64_t bx = M.block[0], by = M.block[1], gx = M.grid[0], gy = M.grid[1];
+    const uint64_t q1 = div_small(t, mg[1]);
+    tv.v[0] = (int64_t)(t - q1 * bx);
+    tv.v[1] = (int64_t)(q1 - div_small(q1, mg[2]) * by);
+    tv.v[2] = (int64_t)div_small(t, mg[3]);
+    const uint64_t q2 = div_small(b, mg[4]);
+    tv.v[3] = (int64_t)(b - q2 * gx);
+    tv.v[4] = (int64_t)(q2 - div_small(q2, mg[5]) * gy);
+    tv.v[5] = (int64_t)div_small(b, mg[6]);
+    return tv;
+  }
   uint64_t b = gtid / M.bs;
   uint32_t t = (uint32_t)(gtid - b * M.bs);
   tv.b = b;

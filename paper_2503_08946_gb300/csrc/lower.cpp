@@ -241,6 +241,11 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   h.bs = (uint32_t)bs;
   h.n_blocks = nb;
   h.n_threads = nt;
+  {
+    const uint64_t dv[7] = {bs, d->block[0], d->block[1], (uint64_t)d->block[0] * d->block[1], d->grid[0],
+                            d->grid[1], (uint64_t)d->grid[0] * d->grid[1]};
+    for (int i = 0; i < 7; ++i) h.div_magic[i] = fastdiv_magic((int64_t)dv[i]);
+  }
   h.n_stmts = d->n_stmts;
   h.n_phases = d->n_phases;
   // warp and grid barriers: the key's phase field holds the fine interval

@@ -140,6 +140,9 @@ struct DevModel {
   // warp / grid barriers: block interval and grid interval of each fine
   // interval (4 bits per interval), warp intervals | their bit width << 32
   uint64_t sync_tab[3];
+  // multiply-high reciprocals (fastdiv_magic) of bs, block.x, block.y,
+  // block.x * block.y, grid.x, grid.y, grid.x * grid.y for thread_vars
+  uint64_t div_magic[7];
 };
 
 // Value of a table load: tables read as 0 outside [0, len), so a load is a
