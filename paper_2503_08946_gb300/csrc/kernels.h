@@ -117,7 +117,7 @@ uint32_t radix_bits_for(uint32_t bits);
 constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)
 constexpr uint32_t kScanMaxWarps = 152 * 12 * 4;
 struct ScanArgs {
-  const uint64_t* keys;
+  const uint64_t* keys;                // 16-byte aligned (the phase-table scan reads pairs)
   uint64_t n;
   uint32_t cell_shift, phase_shift, block_shift, thread_shift;
   uint32_t phase_bits, block_bits, thread_bits;

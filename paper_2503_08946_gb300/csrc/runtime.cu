@@ -602,12 +602,14 @@ rc_status enqueue_chunked(rc_model* model, const rc_check_opts* opts, uint8_t* w
       for (uint64_t b = start; b < i; ++b) chunk_of[b] = (uint32_t)chunks.size();
       chunks.push_back(Chunk{clo, cend - clo, n, start, i, 0});
     }
+    // segments start at even key positions (the scan reads 16-byte pairs)
     uint64_t used = 0;
     for (size_t k = 0; k < chunks.size(); ++k) {
-      if (waves.empty() || used + chunks[k].n > cap) {
+      if (waves.empty() || ((used + 1) & ~1ull) + chunks[k].n > cap) {
         waves.push_back(Wave{k, k, chunks[k].b0, chunks[k].b0});
         used = 0;
       }
+      used = (used + 1) & ~1ull;
       chunks[k].base = used;
       used += chunks[k].n;
       waves.back().k1 = k + 1;

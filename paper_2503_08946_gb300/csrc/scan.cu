@@ -711,9 +711,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     cur = P;
     cur.fk = kp;
     bool hasP = false, term = false, cur_empty = true, cur_prefix = true;
-#pragma unroll 8
-    for (int q = 0; q < kScanRun; ++q) {
-      const uint64_t k = s + q < a.n ? __ldg(a.keys + s + q) : kSentinel;
+    auto fold_key = [&](const uint64_t k, const int q) {
       term |= k == kSentinel;
       const bool valid = !term;
       const unsigned bt = (unsigned)(k >> kKindBits) & btm;
@@ -760,6 +758,19 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         cur.start = do_start ? s + q : cur.start;
         cur_prefix = np;
         cur_empty = false;
+      }
+    };
+    // pairs of keys by 16-byte loads (the key array is 16-byte aligned and runs
+    // start at even positions; launch_scan checks the alignment)
+#pragma unroll 1
+    for (int q = 0; q < kScanRun; q += 2) {
+      if (s + q + 1 < a.n) {
+        const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s + q));
+        fold_key(kk.x, q);
+        fold_key(kk.y, q + 1);
+      } else {
+        fold_key(s + q < a.n ? __ldg(a.keys + s + q) : kSentinel, q);
+        fold_key(kSentinel, q + 1);
       }
     }
     bool hasO = false;
@@ -1203,6 +1214,8 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
 }
 
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
+  // the phase-table scan reads keys in 16-byte pairs
+  if (a.phase_table && (reinterpret_cast<uintptr_t>(a.keys) & 15u) != 0u) return cudaErrorMisalignedAddress;
   if (a.n > 0) {
     const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
     if (a.phase_table) {
