@@ -131,7 +131,10 @@ constexpr size_t onesweep_smem() {
 template <int RB>
 __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel(SortArgs a) {
   constexpr int R = 1 << RB;
-  constexpr int DPT = R / kSortThreads;   // digits per thread in the per-digit phases
+  // digits per thread in the per-digit phases (fewer digits than threads: one
+  // digit for each of the first R threads)
+  constexpr bool kAllThreads = R >= kSortThreads;
+  constexpr int DPT = kAllThreads ? R / kSortThreads : 1;
   constexpr int kWarps = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
@@ -184,14 +187,17 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   __syncthreads();
 
   // (2) per digit: tile count, publication, and the tile's exclusive digit offsets
+  const bool has_digits = kAllThreads || (int)threadIdx.x < R;
   unsigned int cnt[DPT];
   unsigned int tsum = 0;
 #pragma unroll
   for (int q = 0; q < DPT; ++q) {
     const int dg = threadIdx.x * DPT + q;
     unsigned int c = 0;
+    if (has_digits) {
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) c += cnt16[ww * R + dg];
+      for (int ww = 0; ww < kWarps; ++ww) c += cnt16[ww * R + dg];
+    }
     cnt[q] = c;
     tsum += c;
   }
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
 #pragma unroll
   for (int q = 0; q < DPT; ++q) {
     const int dg = threadIdx.x * DPT + q;
-    lb[tile * R + dg] = status_word(tile == 0 ? kFlagPrefix : kFlagAggregate, a.epoch, cnt[q]);
+    if (has_digits) lb[tile * R + dg] = status_word(tile == 0 ? kFlagPrefix : kFlagAggregate, a.epoch, cnt[q]);
   }
   {
     unsigned int x = tsum;
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
     for (int i = 0; i < w; ++i) base += s_wt[i];
     unsigned int run = base + x - tsum;
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) {
+    for (int q = 0; q < DPT && has_digits; ++q) {
       const int dg = threadIdx.x * DPT + q;
       tile_excl[dg] = run;
       // staging offset of warp ww's keys of digit dg = tile offset + earlier warps' counts
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
 
   // (3) decoupled look-back for this thread's digits
 #pragma unroll
-  for (int q = 0; q < DPT; ++q) {
+  for (int q = 0; q < DPT && has_digits; ++q) {
     const int dg = threadIdx.x * DPT + q;
     unsigned long long excl = 0;
     if (tile > 0) {
@@ -416,7 +422,8 @@ cudaError_t launch_rb(const SortArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-uint32_t radix_bits_for(uint32_t bits) { return bits <= 8 ? 8 : bits; }
+// 7-bit digits take the 128-counter kernel (7 ballots per key instead of 8)
+uint32_t radix_bits_for(uint32_t bits) { return bits <= 7 ? 7 : (bits <= 8 ? 8 : bits); }
 
 cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
                              cudaStream_t st) {
@@ -444,6 +451,7 @@ cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long l
 cudaError_t launch_partition(const SortArgs& a, uint32_t radix_bits, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   switch (radix_bits) {
+    case 7: return launch_partition_rb<7>(a, st);
     case 8: return launch_partition_rb<8>(a, st);
     case 9: return launch_partition_rb<9>(a, st);
     case 10: return launch_partition_rb<10>(a, st);
@@ -455,6 +463,7 @@ cudaError_t launch_partition(const SortArgs& a, uint32_t radix_bits, cudaStream_
 cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   switch (radix_bits) {
+    case 7: return launch_rb<7>(a, st);
     case 8: return launch_rb<8>(a, st);
     case 9: return launch_rb<9>(a, st);
     case 10: return launch_rb<10>(a, st);
