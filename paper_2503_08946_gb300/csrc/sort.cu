@@ -43,10 +43,14 @@ __device__ __forceinline__ unsigned int lanemask_lt() {
 
 // Lanes of the warp whose digit equals this lane's (among lanes with `valid`
 // set; an invalid lane gets only itself): one ballot per digit bit, ANDed with
-// the bit's sense -- measured cheaper than __match_any_sync on this GPU.
+// the bit's sense -- measured cheaper than __match_any_sync on this GPU.  In a
+// full tile (block-uniform `full`) every lane is valid and the validity ballot
+// is skipped.
 template <int RB>
-__device__ __forceinline__ unsigned int digit_peers(unsigned int d, bool valid) {
-  unsigned int m = __ballot_sync(0xffffffffu, valid);
+__device__ __forceinline__ unsigned int digit_peers(unsigned int d, bool valid, bool full) {
+  // (the skip costs the 256-counter kernel a register spill, so it takes it only
+  // for narrower digits)
+  unsigned int m = (RB <= 7 && full) ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
     const bool bit = (d >> b) & 1u;
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   for (int i = 0; i < kSortItems; ++i) {
     const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
-    const unsigned int peers = digit_peers<RB>(d, valid);
+    const unsigned int peers = digit_peers<RB>(d, valid, full_tile);
     const unsigned int leader = __ffs(peers) - 1;
     unsigned int prev = 0;
     if (lane == leader && valid) {
