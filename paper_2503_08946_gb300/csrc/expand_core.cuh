@@ -56,9 +56,11 @@ __device__ __forceinline__ int64_t row_eval(const FastCtx& c, int r, const int64
   return x;
 }
 
-// value of a row evaluated at every point: cached if thread-constant
-template <int L>
+// value of a row evaluated at every point: cached if thread-constant (NC: a
+// statement without loops has one point, so its rows are evaluated directly)
+template <int L, bool NC = false>
 __device__ __forceinline__ int64_t point_row(const FastCtx& c, int r, const int64_t (&it)[L]) {
+  if (NC) return row_eval<L>(c, r, it);
   const int slot = __ldg(&c.M->rows[r].cache);
   return slot >= 0 ? c.cache[slot * kExpandThreads] : row_eval<L>(c, r, it);
 }
@@ -99,16 +101,16 @@ __device__ __forceinline__ void nest(const FastCtx& c, int64_t (&it)[LA], Body& 
 // One statement instance point: guards, phase, and one key per access, each
 // handed to sink(a, key, cell) (key = kSentinel and cell = all ones for an
 // out-of-bounds instance).
-template <int L, class Sink>
+template <int L, bool NC, class Sink>
 __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const int64_t (&it)[L], uint64_t low,
                                            unsigned long long* oob, Sink& sink) {
   const DevModel& M = *c.M;
   const DevStmt& S = *c.S;
   for (int g = 0; g < S.n_guards; ++g)
-    if (point_row<L>(c, S.guard_row0 + g, it) < 0) return false;
+    if (point_row<L, NC>(c, S.guard_row0 + g, it) < 0) return false;
   // the key's phase field: the fine interval phase * n_wphases + warp phase
-  const int64_t bphase = point_row<L>(c, S.row_phase, it);
-  const int64_t wphase = S.row_wphase >= 0 ? point_row<L>(c, S.row_wphase, it) : 0;
+  const int64_t bphase = point_row<L, NC>(c, S.row_phase, it);
+  const int64_t wphase = S.row_wphase >= 0 ? point_row<L, NC>(c, S.row_wphase, it) : 0;
   const bool phase_bad = bphase < 0 || bphase >= M.n_phases || wphase < 0 || wphase >= M.n_wphases;
   const int64_t phase = bphase * M.n_wphases + wphase;
   for (int a = 0; a < S.n_acc; ++a) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool point_keys(const FastCtx& c, uint32_t s, const i
     if (phase_bad) atomicMin(oob, oob_pack(s, (uint32_t)a, c.tv.gtid, 0));
     uint64_t e = 0;
     for (int d = 0; d < nd; ++d) {
-      const int64_t v = point_row<L>(c, row0 + d, it);
+      const int64_t v = point_row<L, NC>(c, row0 + d, it);
       const int64_t ext = __ldg(&arr->ext[d]);
       if (v < 0 || v >= ext) {
         atomicMin(oob, oob_pack(s, (uint32_t)a, c.tv.gtid, (uint32_t)d + 1));
@@ -155,18 +157,21 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
   for (int l = 0; l < LA; ++l) it[l] = 0;
   // thread-constant terms and rows
   terms_at_level<LA>(c, 0, it);
-  const Row* rows = M.rows;
-  auto cache_row = [&](int r) {
-    const int slot = __ldg(&rows[r].cache);
-    if (slot >= 0) c.cache[slot * kExpandThreads] = row_eval<LA>(c, r, it);
-  };
-  for (int g2 = 0; g2 < S.n_guards; ++g2) cache_row(S.guard_row0 + g2);
-  cache_row(S.row_phase);
-  if (S.row_wphase >= 0) cache_row(S.row_wphase);
-  for (int a = 0; a < S.n_acc; ++a) {
-    const DevAccess* A = M.accs + S.acc0 + a;
-    const int nd = __ldg(&A->ndims), row0 = __ldg(&A->row0);
-    for (int d = 0; d < nd; ++d) cache_row(row0 + d);
+  constexpr bool NC = L == 0;   // one point: rows are evaluated where used, not cached
+  if (!NC) {
+    const Row* rows = M.rows;
+    auto cache_row = [&](int r) {
+      const int slot = __ldg(&rows[r].cache);
+      if (slot >= 0) c.cache[slot * kExpandThreads] = row_eval<LA>(c, r, it);
+    };
+    for (int g2 = 0; g2 < S.n_guards; ++g2) cache_row(S.guard_row0 + g2);
+    cache_row(S.row_phase);
+    if (S.row_wphase >= 0) cache_row(S.row_wphase);
+    for (int a = 0; a < S.n_acc; ++a) {
+      const DevAccess* A = M.accs + S.acc0 + a;
+      const int nd = __ldg(&A->ndims), row0 = __ldg(&A->row0);
+      for (int d = 0; d < nd; ++d) cache_row(row0 + d);
+    }
   }
   const uint64_t low = (c.tv.b << M.block_shift) | ((uint64_t)c.tv.t << M.thread_shift);
   const uint64_t T = M.n_threads;
@@ -175,7 +180,7 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
     const uint64_t step_pt = (uint64_t)S.n_key * T;
     auto body = [&](const int64_t (&itv)[LA]) {
       auto put = [&](int kidx, uint64_t key, uint64_t cell) { sink.put(slot + (uint64_t)kidx * T, key, cell); };
-      if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
+      if (point_keys<LA, NC>(c, s, itv, low, &res->oob_code, put)) {
         count += (unsigned long long)S.n_acc;
       } else {
         for (int kq = 0; kq < S.n_key; ++kq) sink.pad(slot + (uint64_t)kq * T);
@@ -187,7 +192,7 @@ __device__ void expand_unit_fast(const FastCtx& c, uint32_t s, uint64_t g, DevRe
     uint64_t off = M.unit_offset[S.slot_base + g];
     auto body = [&](const int64_t (&itv)[LA]) {
       auto put = [&](int kidx, uint64_t key, uint64_t cell) { sink.put(off + (uint64_t)kidx, key, cell); };
-      if (point_keys<LA>(c, s, itv, low, &res->oob_code, put)) {
+      if (point_keys<LA, NC>(c, s, itv, low, &res->oob_code, put)) {
         off += (uint64_t)S.n_key;
         count += (unsigned long long)S.n_acc;
       }
