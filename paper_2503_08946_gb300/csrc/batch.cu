@@ -46,9 +46,12 @@ struct BatchSink {
   __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
 };
 
-__global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchArgs a) {
+// LF: every statement of the pack is loop-free -- only the one-point
+// expansion is compiled (fewer registers, no row cache: more resident warps)
+template <bool LF>
+__global__ void __launch_bounds__(kExpandThreads, LF ? 6 : 4) batch_expand_kernel(BatchArgs a) {
   __shared__ int64_t s_tval[kMaxTerms * kExpandThreads];
-  __shared__ int64_t s_cache[kFastCache * kExpandThreads];
+  __shared__ int64_t s_cache[LF ? 1 : kFastCache * kExpandThreads];
   __shared__ unsigned long long s_u;
   __shared__ uint32_t s_model;
   for (;;) {
@@ -101,7 +104,15 @@ __global__ void __launch_bounds__(kExpandThreads, 4) batch_expand_kernel(BatchAr
         const ThreadVars tv = thread_vars(M, g);
         for (uint32_t s = 0; s < B.n_stmts; ++s) {
           const DevStmt& S = M.stmts[s];
-          if (S.n_loops > kFastLoops) {
+          if (LF) {
+            FastCtx c;
+            c.M = B.dm;
+            c.S = &S;
+            c.tv = tv;
+            c.tval = s_tval + threadIdx.x;
+            c.cache = s_cache;   // not read: a loop-free statement evaluates its rows where used
+            expand_unit_fast<0>(c, s, g, res, count, sink);
+          } else if (S.n_loops > kFastLoops) {
             expand_unit_generic(M, s, g, res, count, sink);
           } else {
             FastCtx c;
@@ -136,17 +147,19 @@ cudaError_t launch_batch_errors(const DevResult* pack, DevResult* res, uint32_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_expand(const BatchArgs& a, cudaStream_t st) {
+cudaError_t launch_batch_expand(const BatchArgs& a, bool loop_free, cudaStream_t st) {
   if (a.n_units == 0) return cudaSuccess;
   int dev = 0, sms = 152, per_sm = 4;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_expand_kernel, kExpandThreads, 0);
+  if (loop_free) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_expand_kernel<true>, kExpandThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_expand_kernel<false>, kExpandThreads, 0);
   if (per_sm < 1) per_sm = 1;
   uint64_t grid = (uint64_t)sms * per_sm;
   const uint64_t need = (a.n_units + kUnitsPerGrab - 1) / kUnitsPerGrab;
   if (grid > need) grid = need;
-  batch_expand_kernel<<<(unsigned)grid, kExpandThreads, 0, st>>>(a);
+  if (loop_free) batch_expand_kernel<true><<<(unsigned)grid, kExpandThreads, 0, st>>>(a);
+  else batch_expand_kernel<false><<<(unsigned)grid, kExpandThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -62,7 +62,8 @@ struct BatchArgs {
   uint32_t cell_shift, phase_shift, block_shift;   // batch key layout
   uint32_t thread_shift;                           // = the batch's kind field bits
 };
-cudaError_t launch_batch_expand(const BatchArgs& a, cudaStream_t st);
+// loop_free: every statement of the pack's models has no loops
+cudaError_t launch_batch_expand(const BatchArgs& a, bool loop_free, cudaStream_t st);
 cudaError_t launch_batch_errors(const DevResult* pack, DevResult* res, uint32_t n, cudaStream_t st);
 
 // hash.cu

@@ -387,6 +387,7 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
     }
     int nl = (int)S.n_loops;
     if (nl > kFastLoops) m->has_deep_loops = true;
+    if (nl > 0) m->loop_free = false;
     for (uint32_t g = 0; g < S.n_guards; ++g)
       if (!b.compile(S.guards[g], nl, &guards[g])) return b.err;
     if (!b.compile(S.phase, nl, &phase)) return b.err;

@@ -361,6 +361,7 @@ struct Model {
   std::vector<uint32_t> array_shared;
   uint32_t n_general_stmts = 0;
   bool has_deep_loops = false;    // some statement has more than kFastLoops loops
+  bool loop_free = true;          // no statement has a loop
   // the packed key [cell | phase | block | thread | kind] needs more than
   // kKeyBits: checks run in cell-range chunks whose rebased cell field has
   // host.cell_bits bits (the width left beside the other fields)

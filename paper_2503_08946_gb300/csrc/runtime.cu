@@ -754,6 +754,7 @@ struct BatchPack {
   size_t i0 = 0, i1 = 0;               // models [i0, i1)
   uint32_t tb = 0, bb = 0, pb = 0, cell_bits = 0;
   uint32_t kb = 1;                     // kind field bits (2 if some model has atomics)
+  bool loop_free = true;               // every model of the pack is loop-free
   uint64_t total_cells = 0, n_keys = 0, n_units = 0;
   rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
 };
@@ -786,6 +787,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
       const bool table_ok = kb == 1 || pb <= (uint32_t)rc::kScanTablePhaseBits;
       if (cells >= cur.total_cells && table_ok && kb + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
         cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.kb = kb; cur.total_cells = cells; cur.cell_bits = cb;
+        cur.loop_free = cur.loop_free && m.loop_free;
         cur.n_keys += m.key_slots;
         cur.n_units += chunks_of(m);
         cur.i1 = i + 1;
@@ -797,6 +799,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur.i0 = i;
     cur.i1 = i + 1;
     cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits; cur.kb = h.thread_shift;
+    cur.loop_free = m.loop_free;
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
@@ -930,7 +933,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     ba.phase_shift = k.kb + k.tb + k.bb;
     ba.block_shift = k.kb + k.tb;
     ba.cell_shift = ba.phase_shift + k.pb;
-    s = cuda_status(rc::launch_batch_expand(ba, st));
+    s = cuda_status(rc::launch_batch_expand(ba, k.loop_free, st));
     if (s != RC_OK) break;
     int sorted = 0;
     s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
