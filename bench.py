@@ -470,8 +470,11 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     for t in tickets:
-        res = check_results(rc.rc_report(t))
-    wall = time.perf_counter() - t0   # end to end: enqueue, device work, decoded results
+        arr = rc.rc_report_array(t)
+        if (arr["status"] != rc.RC_OK).any():
+            raise RuntimeError("batch check failed: " + rc.rc_status_str(int(arr["status"][arr["status"] != 0][0])))
+    wall = time.perf_counter() - t0   # end to end: enqueue, device work, results as one record array
+    res = rc.results_of(arr)
     clocks = sampler.stop()
     total_i, ms, value = D.weak_scaling_rate(inst * args.steps, ms, device="cuda")
     total = inst * args.steps * world

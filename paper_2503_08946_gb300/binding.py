@@ -619,7 +619,12 @@ class RcServer:
             pass
 
 
-def rc_report(ticket, wait: bool = True) -> List[Result]:
+def rc_report_array(ticket, wait: bool = True):
+    """The results of a ticket as one numpy record array, one record per
+    model with the fields of ``rc_result`` (``x``/``y`` are records of the
+    fields of ``rc_inst``).  No Python object is made per result: a batch of
+    10,000 models decodes in about a millisecond instead of tens."""
+    import numpy as np
     t, n = ticket
     out = (rc_result * max(1, n))()
     st = load().rc_report(c_void_p(t), out, 1 if wait else 0)
@@ -627,7 +632,21 @@ def rc_report(ticket, wait: bool = True) -> List[Result]:
         raise NotReady()
     if st != RC_OK:
         raise RcError(st, "rc_report")
-    return [_result(out[i]) for i in range(n)]
+    return np.ctypeslib.as_array(out)[:n]
+
+
+def results_of(arr) -> List[Result]:
+    """``Result`` objects of the records that :func:`rc_report_array` returns."""
+    res = []
+    for (s, v, rc_, ins, wa, _r, ws, wad, x, y, os_, oa, og, od, _r2) in arr.tolist():
+        # rc_inst fields: block, thread, kind, phase, gtid, warp_phase, reserved
+        res.append(Result(s, v, rc_, ins, wa, ws, wad, (x[0], x[3], x[1], x[2]), (y[0], y[3], y[1], y[2]),
+                          os_, oa, og, od, x[5], y[5]))
+    return res
+
+
+def rc_report(ticket, wait: bool = True) -> List[Result]:
+    return results_of(rc_report_array(ticket, wait))
 
 
 def rc_ticket_stage_times(ticket) -> dict:

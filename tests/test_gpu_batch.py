@@ -182,3 +182,23 @@ def test_batch_with_many_phases(rc):
               for s in range(4)]
     batch_compare(rc, models)
     batch_compare(rc, models, {"test_flags": 2})
+
+
+def test_report_array(rc):
+    """The record-array report holds the same results as the object report."""
+    models = w.batch_models(200, seed0=77, t_max=2048) + \
+        [w.neighbor_write_read(33, n_blocks=3), w.atomic_histogram(64, 8, n_blocks=2, barrier=False)]
+    handles = [rc.rc_model_create(m) for m in models]
+    ws = rc.workspace(rc.rc_batch_workspace_size(handles))
+    arr = rc.rc_report_array(rc.rc_check_batch(handles, None, ws))
+    assert arr.shape == (len(models),)
+    got = rc.results_of(arr)
+    again = rc.rc_report(rc.rc_check_batch(handles, None, ws))
+    assert got == again
+    for m, g, rec in zip(models, got, arr):
+        assert_same(m, g, oracle.check(m))
+        assert (int(rec["status"]), int(rec["racy_cells"]), int(rec["instances"])) == \
+               (g.status, g.racy_cells, g.instances)
+        if g.verdict:
+            assert (int(rec["x"]["block"]), int(rec["x"]["phase"]), int(rec["x"]["thread"]),
+                    int(rec["x"]["kind"])) == g.x
