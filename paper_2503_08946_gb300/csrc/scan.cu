@@ -482,7 +482,7 @@ struct TFold {
   uint64_t fk;       // first key
   uint64_t start;    // its position
   unsigned bt0;      // its (block, thread)
-  unsigned f;        // kTW | kTMB | kTA | kTR
+  unsigned f;        // kTMB: two blocks (writes, atomics and reads are the masks below)
   unsigned vmask;    // phases seen
   unsigned gm;       // phases with two (block, thread)
   unsigned gw;       // phases with a write
@@ -494,7 +494,7 @@ struct TFoldSync : TFold {
 };
 template <bool SY> struct FoldOf { using type = TFold; };
 template <> struct FoldOf<true> { using type = TFoldSync; };
-constexpr unsigned kTW = 1u, kTMB = 2u, kTA = 4u, kTR = 8u;
+constexpr unsigned kTMB = 2u;
 constexpr int kTabPhases = 1 << kScanTablePhaseBits;
 constexpr int kTabStride = 2 * kTabPhases + 1;     // per lane: prefix table, own table, pad
 
@@ -505,9 +505,9 @@ __device__ __forceinline__ void tfold_clear(F& x) {
 }
 template <bool AT>
 __device__ __forceinline__ bool tfold_racy(const TFold& x) {
-  if (!AT) return (x.f & kTW) && ((x.f & kTMB) || (x.gm & x.gw) != 0u);
+  if (!AT) return x.gw != 0u && ((x.f & kTMB) || (x.gm & x.gw) != 0u);
   // a conflict across blocks, or in a phase group with two (block, thread)
-  const bool conf = (x.f & kTW) || ((x.f & kTA) && (x.f & kTR));
+  const bool conf = x.gw != 0u || (x.ga != 0u && x.gr != 0u);
   return (conf && (x.f & kTMB)) || (x.gm & (x.gw | (x.ga & x.gr))) != 0u;
 }
 
@@ -590,8 +590,8 @@ __device__ __forceinline__ void mark_pair(unsigned a, unsigned b, unsigned bit, 
 template <bool AT, bool SY>
 __device__ __forceinline__ void tfold_merge(typename FoldOf<SY>::type& o, unsigned* otab,
                                             const typename FoldOf<SY>::type& p, const unsigned* ptab, uint32_t tb) {
-  unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
-  if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
+  unsigned f = o.f | p.f;
+  if (((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   unsigned m = p.vmask;
   while (m) {
     const int ph = __ffs(m) - 1;
@@ -626,8 +626,8 @@ template <bool AT, bool SY>
 __device__ __forceinline__ void tfold_merge_warp(typename FoldOf<SY>::type& o, unsigned* ctab,
                                                  const typename FoldOf<SY>::type& p, const unsigned* ptab, uint32_t tb) {
   const int lane = threadIdx.x & 31;
-  unsigned f = o.f | (p.f & (AT ? (kTW | kTA | kTR) : kTW));
-  if ((p.f & kTMB) || ((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
+  unsigned f = o.f | p.f;
+  if (((p.bt0 ^ o.bt0) >> tb) != 0u) f |= kTMB;
   bool g = false;
   unsigned mb = 0, mw = 0;
   if (lane < kTabPhases && (p.vmask >> lane) & 1u) {
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   using TF = typename FoldOf<SY>::type;
   SyncTabs syt;
   if constexpr (SY) syt = sync_tabs_of(a);
-  auto report = [&](const TF& x, const unsigned* xtab) {
+  auto report = [&](const TF& x, const unsigned* xtab, const uint64_t start) {
     if constexpr (SY) {
       if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
     } else {
@@ -689,10 +689,10 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
-      atomicMin(&r->min_start, (unsigned long long)x.start);
+      atomicMin(&r->min_start, (unsigned long long)start);
     } else {
       ++count;
-      minstart = min(minstart, (unsigned long long)x.start);
+      minstart = min(minstart, (unsigned long long)start);
     }
   };
   bool carry = false;
@@ -711,19 +711,23 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     cur = P;
     cur.fk = kp;
     bool hasP = false, term = false, cur_empty = true, cur_prefix = true;
-    auto fold_key = [&](const uint64_t k, const int q) {
-      term |= k == kSentinel;
-      const bool valid = !term;
+    unsigned q0 = 0;   // run position of the current cell's first key
+    // first: the run's first key (it starts the current part); check: the run
+    // may end past n or hold sentinels (keys are ascending and a sentinel is
+    // above every key, so a run whose last key is below it holds none)
+    auto fold_key = [&](const uint64_t k, const int q, const bool first, const bool check) {
+      if (check) term |= k == kSentinel;
+      const bool valid = !check || !term;
       const unsigned bt = (unsigned)(k >> kKindBits) & btm;
       const unsigned ph = (unsigned)(k >> ps) & pm;
       const bool same_cell = ((k ^ cur.fk) & cell_mask) == 0ull;
-      const bool do_start = !same_cell || cur_empty;
-      if (valid && !same_cell && !cur_empty) {
+      const bool do_start = first || !same_cell;
+      if (!first && valid && !same_cell) {
         if (cur_prefix) {
           P = cur;
           hasP = true;
         } else {
-          report(cur, mytab + kTabPhases);
+          report(cur, mytab + kTabPhases, s + q0);
         }
       }
       const bool np = cur_prefix && same_cell;
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const bool seen = !do_start && (cur.vmask & bit);
       if (valid) {
         if (!seen) tab[ph] = bt;
-        const unsigned wb = (k & 1ull) ? bit : 0u;
+        const unsigned wb = (unsigned)(k & 1ull) << ph;
         cur.gm = (do_start ? 0u : cur.gm) | ((seen && old != bt) ? bit : 0u);
         if constexpr (SY) {
           cur.gmb = do_start ? 0u : cur.gmb;
@@ -742,39 +746,40 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         }
         cur.vmask = (do_start ? 0u : cur.vmask) | bit;
         cur.gw = (do_start ? 0u : cur.gw) | wb;
-        unsigned f = do_start ? 0u : cur.f;
-        if (!do_start && ((bt ^ cur.bt0) >> tb) != 0u) f |= kTMB;
-        if (k & 1ull) f |= kTW;
+        cur.f = do_start ? 0u : (((bt ^ cur.bt0) >> tb) != 0u ? kTMB : cur.f);
         if (AT) {
           const bool at = (k & 2ull) != 0ull, rd = (k & 3ull) == 0ull;
           cur.ga = (do_start ? 0u : cur.ga) | (at ? bit : 0u);
           cur.gr = (do_start ? 0u : cur.gr) | (rd ? bit : 0u);
-          if (at) f |= kTA;
-          if (rd) f |= kTR;
         }
-        cur.f = f;
         cur.fk = do_start ? k : cur.fk;
         cur.bt0 = do_start ? bt : cur.bt0;
-        cur.start = do_start ? s + q : cur.start;
+        q0 = do_start ? (unsigned)q : q0;
         cur_prefix = np;
-        cur_empty = false;
+        if (first) cur_empty = false;
       }
     };
     // pairs of keys by 16-byte loads (the key array is 16-byte aligned and runs
     // start at even positions; launch_scan checks the alignment)
+    const bool full_run = s + kScanRun <= a.n && __ldg(a.keys + s + kScanRun - 1) != kSentinel;
+    if (full_run) {
+      const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s));
+      fold_key(k0.x, 0, true, false);
+      fold_key(k0.y, 1, false, false);
 #pragma unroll 1
-    for (int q = 0; q < kScanRun; q += 2) {
-      if (s + q + 1 < a.n) {
+      for (int q = 2; q < kScanRun; q += 2) {
         const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s + q));
-        fold_key(kk.x, q);
-        fold_key(kk.y, q + 1);
-      } else {
-        fold_key(s + q < a.n ? __ldg(a.keys + s + q) : kSentinel, q);
-        fold_key(kSentinel, q + 1);
+        fold_key(kk.x, q, false, false);
+        fold_key(kk.y, q + 1, false, false);
       }
+    } else {
+      fold_key(s < a.n ? __ldg(a.keys + s) : kSentinel, 0, true, true);
+#pragma unroll 1
+      for (int q = 1; q < kScanRun; ++q) fold_key(s + q < a.n ? __ldg(a.keys + s + q) : kSentinel, q, false, true);
     }
     bool hasO = false;
     TF O = cur;
+    O.start = s + q0;
     if (!cur_empty) {
       if (cur_prefix) {
         P = cur;
@@ -796,7 +801,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         if (!full) open = false;
       }
       if (!open) {
-        if (lane == 0) report(cc, ctab);
+        if (lane == 0) report(cc, ctab, cc.start);
         carry = false;
       } else if (++carried > kCarryMaxSegs) {
         if (lane == 0) hand_over(a, cc.start);
@@ -807,7 +812,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     bool open = hasO;
     bool open_end = false;
     if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= a.n)) {
-      report(O, mytab + kTabPhases);
+      report(O, mytab + kTabPhases, O.start);
       open = false;
     }
     for (int d = 1; __any_sync(FULL, open); ++d) {
@@ -822,7 +827,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         } else {
           if (h) tfold_merge<AT, SY>(O, mytab + kTabPhases, pp, tabs[w] + src * kTabStride, tb);
           if (!full) {
-            report(O, mytab + kTabPhases);
+            report(O, mytab + kTabPhases, O.start);
             open = false;
           }
         }
