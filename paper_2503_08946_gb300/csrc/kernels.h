@@ -104,8 +104,13 @@ struct SortArgs {
   unsigned int* err;
   unsigned long long* cursor;               // partition pass: next output position per digit
 };
+// digit counts of every pass (any number of passes, any key alignment)
 cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
                              cudaStream_t st);
+// histogram.cu: the same counts by a kernel compiled per pass count (plans of
+// up to 6 passes over 16-byte aligned keys; others take launch_histogram)
+cudaError_t launch_digit_counts(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist,
+                                cudaStream_t st);
 cudaError_t launch_digit_offsets(const unsigned long long* hist, unsigned long long* digoff, const SortPlan& sp,
                                  cudaStream_t st);
 // radix_bits: counters of the onesweep kernel (radix_bits_for(pass bits))

@@ -252,7 +252,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
   auto* hist = reinterpret_cast<unsigned long long*>(ws + p.hist_off);
   auto* digoff = reinterpret_cast<unsigned long long*>(ws + p.digoff_off);
   auto* res = reinterpret_cast<rc::DevResult*>(ws + p.result_off);
-  rc_status s = cuda_status(rc::launch_histogram(bufs[0], p.n_keys, p.sort, hist, st));
+  rc_status s = cuda_status(rc::launch_digit_counts(bufs[0], p.n_keys, p.sort, hist, st));
   if (s != RC_OK) return s;
   s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort, st));
   if (s != RC_OK) return s;

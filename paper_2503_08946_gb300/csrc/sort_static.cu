@@ -74,7 +74,7 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
   st = as_status(cudaMemsetAsync(s + kOffHist, 0, kOffDigoff - kOffHist, cs));
   if (st == RC_OK) st = as_status(rc::launch_init_result(res, cs));
   if (st == RC_OK) st = as_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, cs));
-  if (st == RC_OK) st = as_status(rc::launch_histogram(keys_out, n, sp, hist, cs));
+  if (st == RC_OK) st = as_status(rc::launch_digit_counts(keys_out, n, sp, hist, cs));
   if (st == RC_OK) st = as_status(rc::launch_digit_offsets(hist, digoff, sp, cs));
   uint64_t* bufs[2] = {keys_out, pong};
   int cur = 0;
