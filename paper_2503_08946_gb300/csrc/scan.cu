@@ -679,13 +679,8 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   using TF = typename FoldOf<SY>::type;
   SyncTabs syt;
   if constexpr (SY) syt = sync_tabs_of(a);
-  auto report = [&](const TF& x, const unsigned* xtab, const uint64_t start) {
-    if constexpr (SY) {
-      if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
-    } else {
-      (void)xtab;
-      if (!tfold_racy<AT>(x)) return;
-    }
+  // count a racy cell and keep the first
+  auto record = [&](const TF& x, const uint64_t start) {
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
@@ -694,6 +689,15 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       ++count;
       minstart = min(minstart, (unsigned long long)start);
     }
+  };
+  auto report = [&](const TF& x, const unsigned* xtab, const uint64_t start) {
+    if constexpr (SY) {
+      if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
+    } else {
+      (void)xtab;
+      if (!tfold_racy<AT>(x)) return;
+    }
+    record(x, start);
   };
   bool carry = false;
   int carried = 0;
@@ -722,13 +726,16 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const unsigned ph = (unsigned)(k >> ps) & pm;
       const bool same_cell = ((k ^ cur.fk) & cell_mask) == 0ull;
       const bool do_start = first || !same_cell;
-      if (!first && valid && !same_cell) {
-        if (cur_prefix) {
-          P = cur;
-          hasP = true;
-        } else {
-          report(cur, mytab + kTabPhases, s + q0);
-        }
+      const bool close = !first && valid && !same_cell;
+      if (close && cur_prefix) {
+        P = cur;
+        hasP = true;
+      }
+      if constexpr (SY) {
+        if (close && !cur_prefix) report(cur, mytab + kTabPhases, s + q0);
+      } else {
+        // the racy test without a branch; only a racy cell branches
+        if (close && !cur_prefix && tfold_racy<AT>(cur)) record(cur, s + q0);
       }
       const bool np = cur_prefix && same_cell;
       unsigned* tab = mytab + (np ? 0 : kTabPhases);
@@ -766,7 +773,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
       const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s));
       fold_key(k0.x, 0, true, false);
       fold_key(k0.y, 1, false, false);
-#pragma unroll 1
+#pragma unroll 3
       for (int q = 2; q < kScanRun; q += 2) {
         const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s + q));
         fold_key(kk.x, q, false, false);
