@@ -170,8 +170,10 @@ typedef struct rc_model_desc {
                                interval of each block interval (grid-wide
                                barriers); NULL = none.  With warp or grid
                                barriers n_phases * n_warp_phases <= 16 and the
-                               model is checked alone on the sort path (hash
-                               path and batches: RC_E_UNSUPPORTED)                */
+                               model is checked on the sort path, alone or in
+                               a batch (in a batch it shares a pack only with
+                               models of at most 16 barrier intervals); the
+                               hash path returns RC_E_UNSUPPORTED               */
 } rc_model_desc;
 
 /* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED

@@ -139,7 +139,9 @@ struct ScanArgs {
   uint32_t phase_table;                // keys sorted by cell only (phase_bits <= kScanTablePhaseBits)
   // warp and grid barriers (null without them): the phase field is a fine
   // interval q; device words [block interval of q, grid interval of q (4 bits
-  // per q each), warp intervals per block interval | their bit width << 32]
+  // per q each), warp intervals per block interval | their bit width << 32],
+  // one triple per model of a batch (a model without such barriers: q = its
+  // phase, one grid interval, one warp interval)
   const uint64_t* sync_tabs;
 };
 // the interval tables of a scan (no warp or grid barriers: q is the phase)

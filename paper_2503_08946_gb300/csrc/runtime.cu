@@ -755,14 +755,15 @@ struct BatchPack {
   uint32_t tb = 0, bb = 0, pb = 0, cell_bits = 0;
   uint32_t kb = 1;                     // kind field bits (2 if some model has atomics)
   bool loop_free = true;               // every model of the pack is loop-free
+  bool sy = false;                     // some model has warp or grid barriers
   uint64_t total_cells = 0, n_keys = 0, n_units = 0;
   rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
 };
 
 struct BatchLayout {
   std::vector<BatchPack> packs;
-  size_t res_off = 0, packres_off = 0, table_off = 0, cellbase_off = 0, queue_off = 0;
-  size_t upload_bytes = 0;             // table + cell bases, staged through pinned memory
+  size_t res_off = 0, packres_off = 0, table_off = 0, cellbase_off = 0, synctab_off = 0, queue_off = 0;
+  size_t upload_bytes = 0;             // table, cell bases, interval tables; staged through pinned memory
   size_t total = 0;
 };
 
@@ -783,11 +784,15 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
       const uint32_t kb = std::max(cur.kb, h.thread_shift);
       const uint64_t cells = cur.total_cells + m.total_cells;
       const uint32_t cb = rc::bit_length(cells);
-      // a model with atomics joins only a pack scanned with phase tables
-      const bool table_ok = kb == 1 || pb <= (uint32_t)rc::kScanTablePhaseBits;
+      // a model with atomics or with warp / grid barriers joins only a pack
+      // scanned with phase tables, and a pack holding one takes only models
+      // that fit them
+      const bool sy = cur.sy || m.sync_scopes;
+      const bool table_ok = (kb == 1 && !sy) || pb <= (uint32_t)rc::kScanTablePhaseBits;
       if (cells >= cur.total_cells && table_ok && kb + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
         cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.kb = kb; cur.total_cells = cells; cur.cell_bits = cb;
         cur.loop_free = cur.loop_free && m.loop_free;
+        cur.sy = sy;
         cur.n_keys += m.key_slots;
         cur.n_units += chunks_of(m);
         cur.i1 = i + 1;
@@ -800,6 +805,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur.i1 = i + 1;
     cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits; cur.kb = h.thread_shift;
     cur.loop_free = m.loop_free;
+    cur.sy = m.sync_scopes;
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
@@ -817,7 +823,9 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
   off = align256(off + n * sizeof(rc::BatchModel));
   L->cellbase_off = off;
   off = align256(off + n * 8);
-  L->upload_bytes = L->cellbase_off + n * 8 - L->table_off;
+  L->synctab_off = off;
+  off = align256(off + n * 24);
+  L->upload_bytes = L->synctab_off + n * 24 - L->table_off;
   L->queue_off = off;
   off = align256(off + 8);
   const size_t region = off;
@@ -870,6 +878,7 @@ void fill_batch_tables(rc_model* const* models, const BatchLayout& L, void* uplo
   const size_t n = L.packs.empty() ? 0 : L.packs.back().i1;
   auto* table = static_cast<rc::BatchModel*>(upload);
   auto* cbase = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(upload) + (L.cellbase_off - L.table_off));
+  auto* stabs = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(upload) + (L.synctab_off - L.table_off));
   cell_base->assign(n, 0);
   field_bits->assign(n, 0);
   for (const BatchPack& k : L.packs) {
@@ -893,6 +902,9 @@ void fill_batch_tables(rc_model* const* models, const BatchLayout& L, void* uplo
       b.thread_bits = h.thread_bits;
       b.thread_shift = h.thread_shift;
       cbase[i] = cb;
+      // interval tables (a model without warp or grid barriers: block interval
+      // = phase, one grid interval, one warp interval)
+      for (int q = 0; q < 3; ++q) stabs[3 * i + q] = h.sync_tab[q];
       (*cell_base)[i] = cb;
       (*field_bits)[i] = k.tb | (k.pb << 8) | (k.kb << 16);
       key_base += m.key_slots;
@@ -910,6 +922,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
   auto* pres = reinterpret_cast<rc::DevResult*>(ws + L.packres_off);
   const auto* dtable = reinterpret_cast<const rc::BatchModel*>(ws + L.table_off);
   const auto* dcbase = reinterpret_cast<const uint64_t*>(ws + L.cellbase_off);
+  const auto* dstabs = reinterpret_cast<const uint64_t*>(ws + L.synctab_off);
   auto* queue = reinterpret_cast<unsigned long long*>(ws + L.queue_off);
   const uint64_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1ull << 20);
   rc_status s = cuda_status(cudaMemcpyAsync(ws + L.table_off, upload, L.upload_bytes, cudaMemcpyHostToDevice, st));
@@ -961,7 +974,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.cell_base = dcbase + k.i0;
     sa.n_models = nm;
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
-    sa.sync_tabs = nullptr;   // models with warp or grid barriers are not batched
+    sa.sync_tabs = k.sy ? dstabs + 3 * k.i0 : nullptr;
     s = cuda_status(rc::launch_scan(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
@@ -1148,6 +1161,8 @@ rc_check_opts resolve_opts(rc_model* const* models, size_t n, const rc_check_opt
   if (opts) o = *opts;
   if (o.path != RC_PATH_AUTO) return o;
   o.path = RC_PATH_SORT;
+  for (size_t i = 0; i < n; ++i)
+    if (models[i] && models[i]->m.sync_scopes) return o;   // warp / grid barriers: sort path only
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned.find(tune_key(models, n));
   if (it != g_tuned.end()) {
@@ -1383,7 +1398,6 @@ rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_ch
   for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
     if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
-    if (models[i]->m.sync_scopes) return RC_E_UNSUPPORTED;   // warp / grid barriers: checked alone
   }
   const rc_check_opts ro = resolve_opts(models, n, opts_in);
   const rc_check_opts* opts = &ro;
@@ -1411,7 +1425,6 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
   for (size_t i = 0; i < n; ++i) {
     if (!models[i]) return RC_E_INVALID;
     if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
-    if (models[i]->m.sync_scopes) return RC_E_UNSUPPORTED;   // warp / grid barriers: checked alone
   }
   rc_check_opts ro = resolve_opts(models, n, opts_in);
   if (opts_in && opts_in->path == RC_PATH_AUTO) {
@@ -1570,7 +1583,7 @@ rc_status rc_report(rc_ticket t, rc_result* out, int wait) {
                     rc::bit_length((uint64_t)m.host.n_wphases - 1));
     else
       decode_result(t->host[i], m, &out[i], t->cell_base[i], t->field_bits[i] & 0xFFu, (t->field_bits[i] >> 8) & 0xFFu,
-                    t->field_bits[i] >> 16);
+                    t->field_bits[i] >> 16, rc::bit_length((uint64_t)m.host.n_wphases - 1));
   }
   ticket_put(t);
   return RC_OK;

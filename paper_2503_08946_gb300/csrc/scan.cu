@@ -73,25 +73,31 @@ __device__ uint64_t warp_cell_end(const uint64_t* keys, uint64_t n, uint32_t cs,
 
 // Result record of the model whose cell range holds `cell` (batch), else the
 // single result.
-__device__ __forceinline__ DevResult* result_of(const ScanArgs& a, uint64_t cell) {
-  if (a.n_models == 0) return a.res;
+// the model of a batch cell (binary search of the models' first cells); 0 for one model
+__device__ __forceinline__ uint32_t model_of(const ScanArgs& a, uint64_t cell) {
+  if (a.n_models == 0) return 0;
   uint32_t lo = 0, hi = a.n_models;
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
     if (__ldg(&a.cell_base[mid]) <= cell) lo = mid;
     else hi = mid;
   }
-  return a.res + lo;
+  return lo;
+}
+__device__ __forceinline__ DevResult* result_of(const ScanArgs& a, uint64_t cell) {
+  return a.res + model_of(a, cell);
 }
 
-// The interval tables of models with warp or grid barriers (see ScanArgs).
-__device__ __forceinline__ SyncTabs sync_tabs_of(const ScanArgs& a) {
+// The interval tables of model mi (one model: mi = 0) when the check has warp
+// or grid barriers (see ScanArgs).
+__device__ __forceinline__ SyncTabs sync_tabs_of(const ScanArgs& a, uint32_t mi = 0) {
   SyncTabs t;
   if (a.sync_tabs) {
-    t.coarse = a.sync_tabs[0];
-    t.grid = a.sync_tabs[1];
-    t.n_wp = (uint32_t)a.sync_tabs[2];
-    t.wp_bits = (uint32_t)(a.sync_tabs[2] >> 32);
+    const uint64_t* w = a.sync_tabs + 3 * (size_t)mi;
+    t.coarse = w[0];
+    t.grid = w[1];
+    t.n_wp = (uint32_t)w[2];
+    t.wp_bits = (uint32_t)(w[2] >> 32);
     t.on = true;
   }
   return t;
@@ -692,6 +698,16 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   };
   auto report = [&](const TF& x, const unsigned* xtab, const uint64_t start) {
     if constexpr (SY) {
+      if (a.n_models) {
+        // a batch: the tables of the cell's model
+        const uint32_t mi = model_of(a, x.fk >> a.cell_shift);
+        const SyncTabs mt = sync_tabs_of(a, mi);
+        if (!tfold_racy_sync<AT>(x, xtab, mt.coarse, mt.grid, tb)) return;
+        DevResult* r = a.res + mi;
+        atomicAdd(&r->racy_cells, 1ull);
+        atomicMin(&r->min_start, (unsigned long long)start);
+        return;
+      }
       if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
     } else {
       (void)xtab;
@@ -873,13 +889,13 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
   __shared__ unsigned s_gw, s_ga, s_gr, s_minb, s_maxb, s_w;
   const uint32_t kb = a.thread_shift;   // kind field bits (R = 0, W = 1, A = 2)
   const uint64_t kmask = (1ull << kb) - 1ull;
-  const SyncTabs syt = sync_tabs_of(a);
   const unsigned pm = (1u << a.phase_bits) - 1u;
   const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
   const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
   for (unsigned long long i = blockIdx.x; i < n_long; i += gridDim.x) {
     const uint64_t start = a.long_list[i];
     const uint64_t cell = a.keys[start] >> a.cell_shift;
+    const SyncTabs syt = sync_tabs_of(a, model_of(a, cell));
     if (threadIdx.x < kTabPhases) {
       mn[threadIdx.x] = 0xffffffffu;
       mx[threadIdx.x] = 0;
@@ -1064,7 +1080,7 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
-  const SyncTabs syt = sync_tabs_of(a);
+  const SyncTabs syt = sync_tabs_of(a, blockIdx.y);
   unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
@@ -1090,7 +1106,7 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
-  const SyncTabs syt = sync_tabs_of(a);
+  const SyncTabs syt = sync_tabs_of(a, blockIdx.y);
   const unsigned* groups = groups_of(a);
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
@@ -1150,7 +1166,7 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
 
 __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
-  const SyncTabs syt = sync_tabs_of(a);
+  const SyncTabs syt = sync_tabs_of(a, blockIdx.y);
   const uint64_t s = r->min_start;
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;

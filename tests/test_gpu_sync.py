@@ -2,7 +2,9 @@
 ordered only by grid barriers, two warps of one block only by block barriers,
 the threads of one warp also by warp barriers.  Parity with the oracle (count,
 instance count, witness and the witness's warp phases bit-exact) on the sort
-path with interpreted and generated expansion, and in chunked checks."""
+path with interpreted and generated expansion, in chunked checks and in
+batches (one interval table per model; a pack with such a model holds only
+models of at most 16 intervals)."""
 import pytest
 import torch
 
@@ -90,11 +92,92 @@ def test_sync_models_rejected_where_unsupported(rc):
     b = rc.binding
     h = b.rc_model_create(w.warp_reduction(2))
     with pytest.raises(b.RcError) as e:
-        b.rc_batch_workspace_size([h])
-    assert e.value.status == b.RC_E_UNSUPPORTED
-    with pytest.raises(b.RcError) as e:
         b.rc_check(h, {"path": b.RC_PATH_HASH}, b.workspace(1 << 20))
+    assert e.value.status == b.RC_E_UNSUPPORTED
+    # a batch on the hash path checks its models one by one: the same answer
+    with pytest.raises(b.RcError) as e:
+        b.rc_check_batch([h], {"path": b.RC_PATH_HASH}, b.workspace(1 << 20))
     assert e.value.status == b.RC_E_UNSUPPORTED
     too_many = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
                      [Stmt([Access(0, W, (tid.x,))], phase=const(0))], n_phases=5, n_warp_phases=4)
     assert b.rc_model_create_status(too_many) == b.RC_E_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+
+def check_batch(rc, models, opts=None):
+    b = rc.binding
+    hs = [b.rc_model_create(m) for m in models]
+    ws = b.workspace(b.rc_batch_workspace_size(hs, opts))
+    got = b.rc_report(b.rc_check_batch(hs, opts, ws), wait=True)
+    assert len(got) == len(models)
+    for m, g in zip(models, got):
+        exp = oracle.check(m)
+        assert g.status == exp.status, (m.name, g, exp)
+        assert g.instances == exp.instances, m.name
+        if exp.status == oracle.STATUS_OOB:
+            continue
+        assert (g.verdict, g.racy_cells) == (exp.verdict, exp.racy_cells), (m.name, g, exp)
+        assert g.witness == exp.witness, (m.name, g.witness, exp.witness)
+        if exp.verdict:
+            assert (g.x_wphase, g.y_wphase) == (exp.x_wphase, exp.y_wphase), m.name
+    return got
+
+
+def _interleave(*groups):
+    out = []
+    for i in range(max(len(g) for g in groups)):
+        out += [g[i] for g in groups if i < len(g)]
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_mixed_sync_and_plain(rc, graph):
+    """Models with warp / grid barriers, plain models and atomic models in one
+    batch: every result equals the oracle's, warp phases of the witness included."""
+    opts = {"flags": rc.binding.RC_OPT_GRAPH} if graph else None
+    sync = [w.tiny_random_sync(s) for s in range(80)]
+    plain = [w.tiny_random(s) for s in range(50)]
+    atomic = [w.tiny_random(s, atomic=0.4) for s in range(20)]
+    named = [w.warp_reduction(2, warp_barriers=False), w.warp_reduction(16, warp_barriers=True),
+             w.warp_reduction(3, warp_barriers=False, shared_half=True), w.grid_neighbor(4, 8, grid_barrier=False),
+             w.grid_neighbor(256, 256, grid_barrier=True), w.grid_neighbor(3, 33, grid_barrier=False),
+             w.neighbor_write_read(64), w.reduction_tree(False)]
+    models = _interleave(sync, plain, atomic, named)
+    got = check_batch(rc, models, opts)
+    assert sum(g.verdict for g in got) > 10
+
+
+def test_batch_sync_with_many_phase_models(rc):
+    """Models of more than 16 barrier intervals go to packs of their own."""
+    many = [Model((2, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
+                  [Stmt([Access(0, W, ((tid.x + k + j) % 64,)), Access(0, R, ((tid.x + k + 1) % 64,))],
+                        phase=const(k)) for k in range(20)], n_phases=20, name=f"many_phases_{j}")
+            for j in range(4)]
+    sync = [w.tiny_random_sync(s) for s in range(200, 212)]
+    check_batch(rc, _interleave(sync, many))
+
+
+def test_batch_sync_long_cells(rc):
+    """Cells of tens of thousands of keys in a batch (the long-cell pass reads
+    the tables of the cell's model)."""
+    c = Array("c", "global", (2,))
+    lane0 = [-1 * (tid.x % 32)]
+    out = []
+    for gp in ([0, 0, 0], [0, 0, 1], [0, 1, 2]):
+        stmts = [Stmt([Access(0, R, (const(0),))], phase=const(0), warp_phase=(tid.x // 32) % 2),
+                 Stmt([Access(0, A, (const(0),))], guards=lane0, phase=const(0), warp_phase=const(1)),
+                 Stmt([Access(0, W, (const(1),))], guards=lane0, phase=const(1), warp_phase=const(0)),
+                 Stmt([Access(0, R, (const(1),))], phase=const(2))]
+        out.append(Model((200, 1, 1), (128, 1, 1), [c], stmts, n_phases=3, n_warp_phases=2, grid_phase=gp,
+                         name=f"sync_long_{gp}"))
+    check_batch(rc, _interleave(out, [w.tiny_random(s) for s in range(6)]))
+
+
+def test_batch_sync_equals_single(rc):
+    models = [w.tiny_random_sync(s) for s in range(300, 340)]
+    got = check_batch(rc, models)
+    for m, g in zip(models, got):
+        assert g == rc.check(m), m.name
