@@ -299,19 +299,26 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
 // digit's offset), stages the keys in digit order and scatters them.  No
 // look-back and no waiting: tiles are independent.
 // ---------------------------------------------------------------------------
+// The partition pass's tile: 12 keys per thread.  It has no look-back, so its
+// tile size is free of the stable passes'; at 12 keys a thread fits in 64
+// registers and 4 blocks stay resident per SM (measured on the 4096 x 256 model:
+// 4.24 ms against 5.35 ms for 16 keys at 3 blocks).
+constexpr int kPartItems = 12;
+constexpr int kPartTile = kSortThreads * kPartItems;
+
 template <int RB>
 constexpr size_t partition_smem() {
-  return (size_t)kSortTile * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
+  return (size_t)kPartTile * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
 }
 
 template <int RB>
-__global__ void __launch_bounds__(kSortThreads, 3) partition_kernel(SortArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 4) partition_kernel(SortArgs a) {
   constexpr int R = 1 << RB;
   constexpr int DPT = (R + kSortThreads - 1) / kSortThreads;
   constexpr int kWarps = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
-  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kSortTile);           // [R]
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kPartTile);           // [R]
   unsigned int* excl = cnt + R;                                                       // [R]
   unsigned long long* delta = reinterpret_cast<unsigned long long*>(excl + R);        // [R]
   __shared__ unsigned int s_wt[kWarps];
@@ -320,20 +327,20 @@ __global__ void __launch_bounds__(kSortThreads, 3) partition_kernel(SortArgs a) 
   const unsigned int dmask = (1u << a.bits) - 1u;
   for (int i = threadIdx.x; i < R; i += kSortThreads) cnt[i] = 0;
   __syncthreads();
-  const uint64_t wbase = tile * kSortTile + (uint64_t)w * (32 * kSortItems);
-  const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
-  uint64_t k[kSortItems];
+  const uint64_t wbase = tile * kPartTile + (uint64_t)w * (32 * kPartItems);
+  const bool full_tile = (tile + 1) * (uint64_t)kPartTile <= a.n;
+  uint64_t k[kPartItems];
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
+  for (int i = 0; i < kPartItems; ++i) {
     const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
     k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
   }
   // ranks within the tile's digit buckets in any order: one shared atomic per
   // lane, or one per warp when the whole warp holds one digit (frequent: the 32
   // keys of a warp come from one access of 32 consecutive threads)
-  unsigned short r[kSortItems];
+  unsigned short r[kPartItems];
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
+  for (int i = 0; i < kPartItems; ++i) {
     const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
     const unsigned int d0 = __shfl_sync(0xffffffffu, d, 0);
@@ -378,15 +385,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) partition_kernel(SortArgs a) 
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
+  for (int i = 0; i < kPartItems; ++i) {
     if (full_tile || wbase + (uint64_t)i * 32 + lane < a.n) {
       const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
       s_keys[excl[d] + r[i]] = k[i];
     }
   }
   __syncthreads();
-  const uint64_t t0 = tile * kSortTile;
-  const int n_here = full_tile ? kSortTile : (int)(a.n - t0);
+  const uint64_t t0 = tile * kPartTile;
+  const int n_here = full_tile ? kPartTile : (int)(a.n - t0);
   for (int pos = threadIdx.x; pos < n_here; pos += kSortThreads) {
     const uint64_t key = s_keys[pos];
     const unsigned int dd = (unsigned int)(key >> a.shift) & dmask;
@@ -404,7 +411,7 @@ cudaError_t launch_partition_rb(const SortArgs& a, cudaStream_t st) {
                          cudaSharedmemCarveoutMaxShared);
     attr_set = true;
   }
-  const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
+  const uint64_t n_tiles = (a.n + kPartTile - 1) / kPartTile;
   partition_kernel<RB><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
