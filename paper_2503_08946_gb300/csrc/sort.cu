@@ -132,8 +132,19 @@ constexpr size_t onesweep_smem() {
          (size_t)(1 << RB) * 4;
 }
 
-template <int RB>
-__global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel(SortArgs a) {
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// SK (staged keys): the tile is first copied into shared memory (cp.async), the
+// ranking reads its digits from there and the keys come back into registers
+// only to be staged in digit order, so 16 keys per thread fit in 64 registers
+// and 4 blocks stay resident per SM (instead of 80 registers and 3 blocks)
+template <int RB, bool SK>
+__global__ void __launch_bounds__(kSortThreads, SK ? 4 : (RB <= 9 ? 3 : 2)) onesweep_kernel(SortArgs a) {
   constexpr int R = 1 << RB;
   // digits per thread in the per-digit phases (fewer digits than threads: one
   // digit for each of the first R threads)
@@ -160,12 +171,34 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   const unsigned int dmask = (1u << a.bits) - 1u;
   const uint64_t wbase = tile * kSortTile + (uint64_t)w * (32 * kSortItems);
   const bool full_tile = (tile + 1) * (uint64_t)kSortTile <= a.n;
-  uint64_t k[kSortItems];
+  uint64_t k[SK ? 1 : kSortItems];
+  // item i of this lane in the tile (and in the staged copy)
+  const int lpos = w * (32 * kSortItems) + lane;
+  if constexpr (SK) {
+    const uint64_t t0 = tile * kSortTile;
+    if (full_tile && (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u) {
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-    k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
+      for (int m = 0; m < kSortTile / 2 / kSortThreads; ++m) {
+        const int j = m * kSortThreads + (int)threadIdx.x;   // pair j: keys 2j, 2j + 1
+        cp_async16(s_keys + 2 * j, a.keys_in + t0 + 2 * j);
+      }
+      cp_async_wait_all();
+    } else {
+      for (int j = threadIdx.x; j < kSortTile; j += kSortThreads)
+        s_keys[j] = t0 + (uint64_t)j < a.n ? a.keys_in[t0 + j] : ~0ull;
+    }
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+      const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+      k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
+    }
   }
+  auto key_of = [&](int i) -> uint64_t {
+    if constexpr (SK) return s_keys[lpos + i * 32];
+    else return k[i];
+  };
 
   // (1) ranking: per item the peer mask, then the rank through the warp's counters
   unsigned short r[kSortItems];
@@ -173,7 +206,7 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   unsigned short* my_cnt = cnt16 + w * R;
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+    const unsigned int d = (unsigned int)(key_of(i) >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
     const unsigned int peers = digit_peers<RB>(d, valid, full_tile);
     const unsigned int leader = __ffs(peers) - 1;
@@ -240,13 +273,18 @@ __global__ void __launch_bounds__(kSortThreads, RB <= 9 ? 3 : 2) onesweep_kernel
   }
   __syncthreads();
 
-  // stage the keys in digit order (stable)
+  // stage the keys in digit order (stable); with SK the keys come back from
+  // the tile copy first, and all are read before any is overwritten
   const unsigned short* my_off = cnt16 + w * R;
+  uint64_t kk[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) kk[i] = key_of(i);
+  if constexpr (SK) __syncthreads();
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     if (full_tile || wbase + (uint64_t)i * 32 + lane < a.n) {
-      const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
-      s_keys[my_off[d] + r[i]] = k[i];
+      const unsigned int d = (unsigned int)(kk[i] >> a.shift) & dmask;
+      s_keys[my_off[d] + r[i]] = kk[i];
     }
   }
 
@@ -420,14 +458,15 @@ template <int RB>
 cudaError_t launch_rb(const SortArgs& a, cudaStream_t st) {
   static bool attr_set = false;
   constexpr size_t smem = onesweep_smem<RB>();
+  constexpr bool SK = RB <= 8;   // staged keys for the 7- and 8-bit kernels
   if (!attr_set) {
-    cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(onesweep_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(onesweep_kernel<RB, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(onesweep_kernel<RB, SK>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     attr_set = true;
   }
   const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
-  onesweep_kernel<RB><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
+  onesweep_kernel<RB, SK><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
