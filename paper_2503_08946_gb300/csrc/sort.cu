@@ -350,7 +350,7 @@ constexpr size_t partition_smem() {
 }
 
 template <int RB>
-__global__ void __launch_bounds__(kSortThreads, 4) partition_kernel(SortArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 5) partition_kernel(SortArgs a) {
   constexpr int R = 1 << RB;
   constexpr int DPT = (R + kSortThreads - 1) / kSortThreads;
   constexpr int kWarps = kSortThreads / 32;
@@ -367,19 +367,32 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_kernel(SortArgs a) 
   __syncthreads();
   const uint64_t wbase = tile * kPartTile + (uint64_t)w * (32 * kPartItems);
   const bool full_tile = (tile + 1) * (uint64_t)kPartTile <= a.n;
-  uint64_t k[kPartItems];
+  // the tile is copied into shared memory (cp.async for full tiles of a
+  // 16-byte aligned key array) and ranked from there; the keys come back into
+  // registers only to be staged
+  {
+    const uint64_t t0 = tile * kPartTile;
+    if (full_tile && (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u) {
 #pragma unroll
-  for (int i = 0; i < kPartItems; ++i) {
-    const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-    k[i] = (full_tile || pos < a.n) ? a.keys_in[pos] : ~0ull;
+      for (int m = 0; m < kPartTile / 2 / kSortThreads; ++m) {
+        const int j = m * kSortThreads + (int)threadIdx.x;   // pair j: keys 2j, 2j + 1
+        cp_async16(s_keys + 2 * j, a.keys_in + t0 + 2 * j);
+      }
+      cp_async_wait_all();
+    } else {
+      for (int j = threadIdx.x; j < kPartTile; j += kSortThreads)
+        s_keys[j] = t0 + (uint64_t)j < a.n ? a.keys_in[t0 + j] : ~0ull;
+    }
   }
+  __syncthreads();
+  const int lpos = w * (32 * kPartItems) + lane;
   // ranks within the tile's digit buckets in any order: one shared atomic per
   // lane, or one per warp when the whole warp holds one digit (frequent: the 32
   // keys of a warp come from one access of 32 consecutive threads)
   unsigned short r[kPartItems];
 #pragma unroll
   for (int i = 0; i < kPartItems; ++i) {
-    const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
+    const unsigned int d = (unsigned int)(s_keys[lpos + i * 32] >> a.shift) & dmask;
     const bool valid = full_tile || wbase + (uint64_t)i * 32 + lane < a.n;
     const unsigned int d0 = __shfl_sync(0xffffffffu, d, 0);
     unsigned int rank = 0;
@@ -422,11 +435,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) partition_kernel(SortArgs a) 
     carry += tot;
   }
   __syncthreads();
+  uint64_t kk[kPartItems];
+#pragma unroll
+  for (int i = 0; i < kPartItems; ++i) kk[i] = s_keys[lpos + i * 32];
+  __syncthreads();   // every key read before any is overwritten
 #pragma unroll
   for (int i = 0; i < kPartItems; ++i) {
     if (full_tile || wbase + (uint64_t)i * 32 + lane < a.n) {
-      const unsigned int d = (unsigned int)(k[i] >> a.shift) & dmask;
-      s_keys[excl[d] + r[i]] = k[i];
+      const unsigned int d = (unsigned int)(kk[i] >> a.shift) & dmask;
+      s_keys[excl[d] + r[i]] = kk[i];
     }
   }
   __syncthreads();
