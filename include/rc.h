@@ -169,11 +169,11 @@ typedef struct rc_model_desc {
   const uint32_t* grid_phase;  /* n_phases entries, non-decreasing: the grid
                                interval of each block interval (grid-wide
                                barriers); NULL = none.  With warp or grid
-                               barriers n_phases * n_warp_phases <= 16 and the
-                               model is checked on the sort path, alone or in
-                               a batch (in a batch it shares a pack only with
-                               models of at most 16 barrier intervals); the
-                               hash path returns RC_E_UNSUPPORTED               */
+                               barriers n_phases * n_warp_phases <= 16; such
+                               a model is checked on the sort path by default
+                               (alone or in a batch, where it shares a pack
+                               only with models of at most 16 barrier
+                               intervals) or on the hash path on request        */
 } rc_model_desc;
 
 /* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED

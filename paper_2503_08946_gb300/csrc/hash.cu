@@ -14,6 +14,19 @@
 // atomicMin; its instances are then collected by a filtered re-expansion and
 // the K4 witness reductions run on them.
 //
+// With warp or grid barriers the phase field is a fine interval q, and an
+// instance updates three groups of the group table, one per kind of set whose
+// members are pairwise concurrent: (cell, q) with the gtid as identity (two
+// threads of one fine interval), (cell, grid interval of q) with the block as
+// identity (two blocks of one grid interval; tag bit 62), and (cell, block
+// interval of q, block) with the warp as identity (two warps of one block in
+// one block interval; tag bit 63, only for blocks of more than 32 threads).
+// The untagged keys are below 2^62 (the key's cell and phase fields shifted
+// down by at least one bit), the grid keys too before their tag, and the warp
+// keys below 2^62 before theirs (cell, block interval and block fields of a
+// key without its thread and kind fields); none is all ones, as the all-ones
+// cell field is never a cell.  The cell table then only holds the RACY bit.
+//
 // No wait in these kernels depends on another thread: a probe sequence is at
 // most the table size, and a CAS loop retries only after another thread
 // changed the word, which happens a bounded number of times per word.
@@ -90,9 +103,27 @@ struct HashSink {
     const int64_t gs = find_slot(h.gkey, h.gmask, cp, &h.res->err);
     const int64_t cs = find_slot(h.ckey, h.cmask, cell, &h.res->err);
     if (gs < 0 || cs < 0) return;
-    // group identity: gtid; cell identity: block
+    // group identity: gtid
     const bool bg = word_update(h.gword + gs, b * m.bs + t, kf);
-    const bool bc = word_update(h.cword + cs, b, kf);
+    bool bc;
+    if (h.sync) {
+      const uint64_t q = cp & ((1ull << m.phase_bits) - 1ull);
+      const uint64_t c = (m.sync_tab[0] >> (4 * q)) & 15u, g = (m.sync_tab[1] >> (4 * q)) & 15u;
+      const uint64_t cq = cp >> m.phase_bits;   // the cell
+      const uint64_t kgrid = (1ull << 62) | (cq << m.phase_bits) | g;
+      const int64_t s2 = find_slot(h.gkey, h.gmask, kgrid, &h.res->err);
+      if (s2 < 0) return;
+      bc = word_update(h.gword + s2, b, kf);
+      if (m.bs > 32u) {
+        const uint64_t kwarp = (1ull << 63) | ((((cq << m.phase_bits) | c) << m.block_bits) | b);
+        const int64_t s3 = find_slot(h.gkey, h.gmask, kwarp, &h.res->err);
+        if (s3 < 0) return;
+        bc = word_update(h.gword + s3, t >> 5, kf) || bc;
+      }
+    } else {
+      // cell identity: block
+      bc = word_update(h.cword + cs, b, kf);
+    }
     if (bg || bc) {
       const unsigned long long old = atomicOr(h.cword + cs, kRacy);
       if (!(old & kRacy)) {

@@ -79,6 +79,7 @@ struct HashArgs {
   uint64_t* filtered;          // keys of the smallest racy cell
   unsigned long long* n_filtered;
   uint64_t cell_lo, cell_hi;   // only cells in [cell_lo, cell_hi) are inserted
+  uint32_t sync;               // warp or grid barriers: three groups per instance (see hash.cu)
 };
 cudaError_t launch_hash(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, const HashArgs& h,
                         cudaStream_t st);

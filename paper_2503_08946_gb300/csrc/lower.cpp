@@ -314,12 +314,20 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   if (h.phase_bits > (uint32_t)kMaxPhaseBits) return RC_E_UNSUPPORTED;
   // warp / grid barriers are scanned with phase tables only (at most 16 fine intervals)
   if (m->sync_scopes && n_fine > (1u << kScanTablePhaseBits)) return RC_E_UNSUPPORTED;
+  // grid intervals are compared only for equality, so they are numbered
+  // densely (0, 1, ... in block-interval order, the descriptor's numbers being
+  // non-decreasing): a grid interval is then below n_phases and fits the
+  // phase field (the hash path packs it there)
   m->coarse_tab = m->grid_tab = 0;
   for (uint64_t q = 0; q < n_fine && q < 16; ++q) {
     const uint64_t p = q / n_wp;
+    uint64_t g = 0;
+    if (d->grid_phase) {
+      if (d->grid_phase[p] > 15u) return RC_E_UNSUPPORTED;
+      for (uint64_t p2 = 1; p2 <= p; ++p2) g += d->grid_phase[p2] != d->grid_phase[p2 - 1] ? 1u : 0u;
+    }
     m->coarse_tab |= (p & 15u) << (4 * q);
-    m->grid_tab |= ((uint64_t)(d->grid_phase ? d->grid_phase[p] : 0u) & 15u) << (4 * q);
-    if (d->grid_phase && d->grid_phase[p] > 15u) return RC_E_UNSUPPORTED;
+    m->grid_tab |= (g & 15u) << (4 * q);
   }
   h.sync_tab[0] = m->coarse_tab;
   h.sync_tab[1] = m->grid_tab;

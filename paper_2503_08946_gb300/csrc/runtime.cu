@@ -143,10 +143,12 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
   p->n_keys = n;
   if (use_hash_path(m, opts)) {
     // tables of at least 1.5x the instances (an upper bound on distinct groups
-    // and cells), the keys of the first racy cell, witness phase groups
+    // and cells; three groups per instance with warp or grid barriers), the
+    // keys of the first racy cell, witness phase groups
     p->hash = true;
+    const uint64_t groups = m.sync_scopes ? 3 * n : n;
     uint64_t cap = 1024;
-    while (cap < n + n / 2) cap <<= 1;
+    while (cap < groups + groups / 2) cap <<= 1;
     p->hash_cap = cap;
     size_t off = 0;
     p->result_off = off;
@@ -292,8 +294,6 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
 rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
                         cudaStream_t st, rc::DevResult* host_out, rc_ticket_s* timed = nullptr) {
   const rc::Model& m = model->m;
-  // the hash tables key groups by (cell, phase) only: no warp or grid barriers
-  if (rc::use_hash_path(m, opts) && m.sync_scopes) return RC_E_UNSUPPORTED;
   rc::WorkspacePlan p;
   rc::plan_workspace(m, opts, &p);
   if (!ws || ws_bytes < p.total) return RC_E_NOMEM;
@@ -329,6 +329,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     h.n_filtered = reinterpret_cast<unsigned long long*>(ws + p.nfilt_off);
     h.cell_lo = cell_lo;
     h.cell_hi = cell_hi;
+    h.sync = m.sync_scopes ? 1u : 0u;
     s = cuda_status(cudaMemsetAsync(h.gkey, 0xFF, p.hash_cap * 8, st));
     if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.ckey, 0xFF, p.hash_cap * 8, st));
     if (s == RC_OK) s = cuda_status(cudaMemsetAsync(h.gword, 0, p.hash_cap * 8, st));

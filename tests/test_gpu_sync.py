@@ -4,7 +4,8 @@ the threads of one warp also by warp barriers.  Parity with the oracle (count,
 instance count, witness and the witness's warp phases bit-exact) on the sort
 path with interpreted and generated expansion, in chunked checks and in
 batches (one interval table per model; a pack with such a model holds only
-models of at most 16 intervals)."""
+models of at most 16 intervals), and on the hash path (three groups per
+instance)."""
 import pytest
 import torch
 
@@ -90,14 +91,6 @@ def test_out_of_range_warp_phase(rc):
 
 def test_sync_models_rejected_where_unsupported(rc):
     b = rc.binding
-    h = b.rc_model_create(w.warp_reduction(2))
-    with pytest.raises(b.RcError) as e:
-        b.rc_check(h, {"path": b.RC_PATH_HASH}, b.workspace(1 << 20))
-    assert e.value.status == b.RC_E_UNSUPPORTED
-    # a batch on the hash path checks its models one by one: the same answer
-    with pytest.raises(b.RcError) as e:
-        b.rc_check_batch([h], {"path": b.RC_PATH_HASH}, b.workspace(1 << 20))
-    assert e.value.status == b.RC_E_UNSUPPORTED
     too_many = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
                      [Stmt([Access(0, W, (tid.x,))], phase=const(0))], n_phases=5, n_warp_phases=4)
     assert b.rc_model_create_status(too_many) == b.RC_E_UNSUPPORTED
@@ -181,3 +174,59 @@ def test_batch_sync_equals_single(rc):
     got = check_batch(rc, models)
     for m, g in zip(models, got):
         assert g == rc.check(m), m.name
+
+
+# ---------------------------------------------------------------------------
+# hash path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(120))
+def test_tiny_random_sync_hash(rc, seed):
+    """Count, instances and witness bit-exact without early exit."""
+    compare(rc, w.tiny_random_sync(seed), {"path": rc.RC_PATH_HASH, "early_exit": 0})
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_tiny_random_sync_hash_early_exit(rc, seed):
+    m = w.tiny_random_sync(seed)
+    got = rc.check(m, {"path": rc.RC_PATH_HASH, "early_exit": 1})
+    exp = oracle.check(m)
+    assert got.status == exp.status, (m.name, got, exp)
+    if exp.status == oracle.STATUS_OK:
+        assert got.verdict == exp.verdict, m.name
+
+
+@pytest.mark.parametrize("nw,bar,shared,exp", [(2, True, False, 0), (2, False, False, 30), (3, False, True, 16),
+                                               (16, False, False, 240)])
+def test_warp_reduction_hash(rc, nw, bar, shared, exp):
+    g = compare(rc, w.warp_reduction(n_warps=nw, warp_barriers=bar, shared_half=shared),
+                {"path": rc.RC_PATH_HASH, "early_exit": 0})
+    assert g.racy_cells == exp
+
+
+@pytest.mark.parametrize("nb,bs,grid,exp", [(4, 8, True, 0), (4, 8, False, 4), (256, 256, False, 256),
+                                            (256, 256, True, 0)])
+def test_grid_neighbor_hash(rc, nb, bs, grid, exp):
+    g = compare(rc, w.grid_neighbor(nb, bs, grid_barrier=grid), {"path": rc.RC_PATH_HASH, "early_exit": 0})
+    assert g.racy_cells == exp
+
+
+@pytest.mark.parametrize("gp", [[0, 0, 0], [0, 0, 1], [0, 1, 2], [3, 3, 9]])
+def test_long_cells_hash(rc, gp):
+    """Hot cells (the hash words of one cell take every update) and grid
+    intervals numbered sparsely by the descriptor."""
+    c = Array("c", "global", (2,))
+    lane0 = [-1 * (tid.x % 32)]
+    stmts = [Stmt([Access(0, R, (const(0),))], phase=const(0), warp_phase=(tid.x // 32) % 2),
+             Stmt([Access(0, A, (const(0),))], guards=lane0, phase=const(0), warp_phase=const(1)),
+             Stmt([Access(0, W, (const(1),))], guards=lane0, phase=const(1), warp_phase=const(0)),
+             Stmt([Access(0, R, (const(1),))], phase=const(2))]
+    m = Model((200, 1, 1), (128, 1, 1), [c], stmts, n_phases=3, n_warp_phases=2, grid_phase=gp, name="sync_long_h")
+    compare(rc, m, {"path": rc.RC_PATH_HASH, "early_exit": 0})
+    compare(rc, m)
+
+
+def test_batch_sync_hash_path(rc):
+    """A batch on the hash path checks its models one by one."""
+    models = [w.tiny_random_sync(s) for s in range(400, 430)] + [w.tiny_random(s) for s in range(10)]
+    check_batch(rc, models, {"path": rc.RC_PATH_HASH, "early_exit": 0})
