@@ -141,3 +141,27 @@ def test_generated_kernels_compile(rc, tmp_path):
         r = subprocess.run([nvcc, "-c", str(f), "-o", str(tmp_path / f"k{i}.o"), "-std=c++17",
                             "-gencode", "arch=compute_103a,code=sm_103a"], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr[:2000]
+
+
+def test_record_array_decoding(rc):
+    """rc_report_array's records decode to the same Result objects as the
+    per-record decoder (field order of rc_result / rc_inst, witness tuples
+    ordered (block, phase, thread, kind))."""
+    import numpy as np
+    b = rc.binding
+    n = 5
+    out = (b.rc_result * n)()
+    for i in range(n):
+        r = out[i]
+        r.status, r.verdict, r.racy_cells, r.instances = i % 2, 1, 10 * i + 1, 1000 + i
+        r.w_array, r.w_scope, r.w_addr = i, 7 * i, (1 << 40) + i
+        r.x.block, r.x.thread, r.x.kind, r.x.phase, r.x.gtid, r.x.warp_phase = 3 + i, 17, 1, 2, 99, 1
+        r.y.block, r.y.thread, r.y.kind, r.y.phase, r.y.gtid, r.y.warp_phase = 4 + i, 18, 2, 3, 100, 0
+        r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim = i, i + 1, (1 << 41) + i, -1 if i else 2
+    arr = np.ctypeslib.as_array(out)[:n]
+    got = b.results_of(arr)
+    exp = [b._result(out[i]) for i in range(n)]
+    assert got == exp
+    assert got[2].witness == (2, 14, (1 << 40) + 2, (5, 2, 17, 1), (6, 3, 18, 2))
+    assert (got[3].x_wphase, got[3].y_wphase) == (1, 0)
+    assert b.results_of(arr[:0]) == []
