@@ -397,6 +397,60 @@ def test_grid_neighbor_witness():
     assert r.witness == (0, 0, 0, (0, 0, 0, 1), (1, 1, 7, 0))
 
 
+@pytest.mark.parametrize("nb,bs", [(3, 1), (5, 1), (2, 1), (2, 2), (3, 2), (4, 3), (7, 33)])
+def test_grid_late_partner_closed_form(nb, bs):
+    """The smallest racing instance lies outside the cell's lowest block: block
+    0 reads before the grid barrier, the later blocks write after it
+    (tests/golden/closed_forms.md)."""
+    m = w.grid_late_partner(nb, bs)
+    r, rb = oracle.check(m), oracle.brute(m)
+    racy = (nb - 1) * bs >= 2
+    assert r.racy_cells == rb.racy_cells == (1 if racy else 0)
+    if not racy:
+        assert r.witness is None and rb.witness is None
+        return
+    y = (1, 1, 1, 1) if bs >= 2 else (2, 1, 0, 1)
+    assert r.witness == rb.witness == (0, 0, 0, (1, 1, 0, 1), y)
+    st, cnt, best = pyref.check(m)
+    assert cnt == 1 and best[0][3:7] == (1, 1, 0, 1) and best[1][3:7] == y
+
+
+def _x_outside_lowest_block(m, best):
+    """The pairwise reference's smallest racing instance lies in a block above
+    the lowest block of its cell."""
+    if best is None:
+        return False
+    x = best[0]
+    insts, _ = pyref.instances(m)
+    return x[3] != min(i[3] for i in insts if i[:3] == x[:3])
+
+
+@pytest.mark.parametrize("seed", range(600))
+def test_tiny_random_sync_block_guards_vs_python_bruteforce(seed):
+    """Statements limited to some blocks (and threads), mostly global cells and
+    grid barriers: the witness may lie above the cell's lowest block."""
+    m = w.tiny_random_sync(seed, block_guards=True)
+    st, cnt, best = pyref.check(m)
+    r, rb = oracle.check(m), oracle.brute(m)
+    assert st == "ok" and r.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        assert r.witness == (x[0], x[1], x[2], x[3:7], y[3:7]) == rb.witness
+        if len(x) == 8:   # (the reference adds warp phases only to models with such barriers)
+            assert (r.x_wphase, r.y_wphase) == (x[7], y[7]) == (rb.x_wphase, rb.y_wphase)
+
+
+def test_block_guard_models_reach_the_late_witness():
+    """The block-guarded generator produces the shape above often enough for
+    the GPU tests over the same seeds to exercise it."""
+    hits = [s for s in range(600) if _x_outside_lowest_block(w.tiny_random_sync(s, block_guards=True),
+                                                              pyref.check(w.tiny_random_sync(s, block_guards=True))[2])]
+    assert len(hits) >= 6, hits
+
+
 @pytest.mark.parametrize("seed", range(150))
 def test_tiny_random_sync_vs_python_bruteforce(seed):
     m = w.tiny_random_sync(seed)

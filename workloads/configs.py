@@ -36,7 +36,7 @@ from .spec import (GLOBAL, SHARED, A, Access, Array, Expr, Loop, Model, R, Stmt,
 __all__ = [
     "reduction_tree", "transpose", "random_affine", "batch_models", "request_stream",
     "neighbor_write_read", "polyhedral_product", "ge_spmm_uniform", "ge_spmm_csr", "csr_row_lengths",
-    "atomic_histogram", "atomic_counter", "warp_reduction", "grid_neighbor", "tiny_random_sync",
+    "atomic_histogram", "atomic_counter", "warp_reduction", "grid_neighbor", "grid_late_partner", "tiny_random_sync",
     "tiny_random", "tiny_random_tables",
     "RANDOM_AFFINE_ROW_GLOBAL", "RANDOM_AFFINE_ROW_SHARED",
 ]
@@ -157,6 +157,23 @@ def grid_neighbor(n_blocks: int, block: int, grid_barrier: bool = True) -> Model
     return Model((n_blocks, 1, 1), (block, 1, 1), [out], stmts, n_phases=2,
                  grid_phase=[0, 1] if grid_barrier else [0, 0],
                  name=f"gridnb_{n_blocks}x{block}_{'grid' if grid_barrier else 'block'}")
+
+
+def grid_late_partner(n_blocks: int = 3, block: int = 1) -> Model:
+    """Global ``c[1]``: block 0 reads ``c[0]`` in barrier interval 0 (grid
+    interval 0); every later block writes it in interval 1 (grid interval 1).
+    The grid barrier orders block 0's read before every write, so the read has
+    no partner; the writes of two later blocks share grid interval 1 and race.
+    For ``n_blocks >= 3``: one racy cell, whose smallest racing instance lies in
+    block 1 (not in the cell's lowest block, 0); its partner is the write of
+    block 2 by thread 0 (writes in one block by several threads also race, but
+    the smallest partner is taken in tuple order: block 1's other threads come
+    first when ``block > 1``)."""
+    c = Array("c", GLOBAL, (1,))
+    stmts = [Stmt([Access(0, R, (const(0),))], guards=[-1 * bid.x], phase=const(0), name="read0"),
+             Stmt([Access(0, W, (const(0),))], guards=[bid.x - 1], phase=const(1), name="write")]
+    return Model((n_blocks, 1, 1), (block, 1, 1), [c], stmts, n_phases=2, grid_phase=[0, 1],
+                 name=f"gridlate_{n_blocks}x{block}")
 
 
 def reduction_tree(barriers: bool = True, load_phase: bool = False, T: int = 256) -> Model:
@@ -552,20 +569,25 @@ def tiny_random(seed: int, atomic: float = 0.0) -> Model:
     return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tiny{seed}")
 
 
-def tiny_random_sync(seed: int) -> Model:
+def tiny_random_sync(seed: int, block_guards: bool = False) -> Model:
     """A small random model with warp and grid barriers: one to three blocks of
     33..80 threads (so two or three warps), up to three barrier intervals
     mapped to up to three grid intervals, up to three warp intervals per
     statement (a constant, a warp-uniform ``tid.x // 32`` term or a uniform
-    loop iterator), shared and global arrays, R / W / A accesses."""
+    loop iterator), shared and global arrays, R / W / A accesses.
+
+    ``block_guards``: two to four blocks, and about half of the statements run
+    in a subset of the blocks only (a guard ``bid.x - c >= 0`` or
+    ``c - bid.x >= 0``), so that the lowest block of a cell may hold no racing
+    instance while later blocks of one grid interval do."""
     rng = SplitMix64(0x5C3A ^ (seed * 0x9E3779B97F4A7C15))
-    n_blocks = rng.uniform_int(1, 3)
+    n_blocks = rng.uniform_int(2, 4) if block_guards else rng.uniform_int(1, 3)
     T = rng.uniform_int(33, 80)
     n_phases = rng.uniform_int(1, 3)
     gp, g = [], 0
     for _ in range(n_phases):
         gp.append(g)
-        if rng.chance(0.4):
+        if rng.chance(0.8 if block_guards else 0.4):
             g += 1
     n_wp = rng.uniform_int(1, 3)
     arrays = [Array("sh", SHARED, (rng.uniform_int(4, 40),)), Array("gl", GLOBAL, (rng.uniform_int(4, 60),))]
@@ -583,7 +605,8 @@ def tiny_random_sync(seed: int) -> Model:
             wp = (it(0) + rng.below(n_wp)) % n_wp if depth else const(rng.below(n_wp))
         accs = []
         for _ in range(rng.uniform_int(1, 3)):
-            a = rng.below(2)
+            # (with block guards mostly the global array: a shared cell has one block)
+            a = 1 if (block_guards and rng.chance(0.8)) else rng.below(2)
             ext = arrays[a].extents[0]
             e = rng.uniform_int(0, 5) + rng.uniform_int(0, 3) * tid.x + rng.uniform_int(0, 2) * bid.x
             if depth:
@@ -593,9 +616,15 @@ def tiny_random_sync(seed: int) -> Model:
             u2 = rng.random()
             kind = A if u2 < 0.25 else (W if u2 < 0.55 else R)
             accs.append(Access(a, kind, (e % ext,)))
-        stmts.append(Stmt(accs, loops=loops, phase=ph, warp_phase=wp, name=f"y{si}"))
+        guards = []
+        if block_guards and rng.chance(0.9):
+            c0 = rng.below(n_blocks)
+            guards = [bid.x - c0] if rng.chance(0.5) else [c0 - bid.x]
+            if rng.chance(0.7):
+                guards.append(const(rng.below(2)) - tid.x)   # the first one or two threads only
+        stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, warp_phase=wp, name=f"y{si}"))
     return Model((n_blocks, 1, 1), (T, 1, 1), arrays, stmts, n_phases=n_phases, n_warp_phases=n_wp,
-                 grid_phase=gp, name=f"tinysync_{seed}")
+                 grid_phase=gp, name=f"tinysync_{seed}{'_bg' if block_guards else ''}")
 
 
 def tiny_random_tables(seed: int) -> Model:
