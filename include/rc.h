@@ -173,7 +173,13 @@ typedef struct rc_model_desc {
                                a model is checked on the sort path by default
                                (alone or in a batch, where it shares a pack
                                only with models of at most 16 barrier
-                               intervals) or on the hash path on request        */
+                               intervals) or on the hash path on request.
+                               With more than one grid interval the witness
+                               keeps a record per (block, fine interval), so
+                               such a model needs bit_length(blocks - 1) +
+                               bit_length(n_phases * n_warp_phases - 1) <= 20
+                               (RC_E_UNSUPPORTED otherwise) and its workspace
+                               grows by 68 bytes per record                    */
 } rc_model_desc;
 
 /* Build limits of this library (rc_model_create returns RC_E_UNSUPPORTED
@@ -461,10 +467,27 @@ rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes)
 
 /* Stable LSD radix sort (onesweep) of n uint64 keys on bits [lo_bit, hi_bit):
  * reads keys_in_dev, writes keys_out_dev (distinct buffers, n keys each).
- * Keys with equal bits in the range keep their input order. */
+ * Keys with equal bits in the range keep their input order.  Asynchronous on
+ * `stream`; the returned status covers the enqueue only (RC_E_INVALID,
+ * RC_E_NOMEM, RC_E_CUDA).  Errors of the device work itself -- a bounded
+ * look-back wait that ran out (RC_E_TIMEOUT: the keys are then in a wrong
+ * order) or inconsistent digit counts because the input changed while the sort
+ * ran (RC_E_INVALID: nothing was written outside keys_out_dev) -- are read
+ * with rc_sort_status(workspace_dev, stream) after the call. */
 rc_status rc_sort_keys(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint64_t n,
                        uint32_t lo_bit, uint32_t hi_bit, uint32_t digit_bits,
                        void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Status of the device work of the last sort that used `workspace_dev`
+ * (rc_sort_keys), or, with workspace_dev == NULL, of the last
+ * rc_sort_keys_static call on the current device.  Synchronises `stream` (the
+ * stream the sort ran on), then reads the sort's error word: RC_OK,
+ * RC_E_TIMEOUT (a look-back wait ran out; the output order is wrong) or
+ * RC_E_INVALID (the digit counts and the ranks disagreed: the input changed
+ * during the sort; stores that would have left the output were skipped), or
+ * RC_E_CUDA.  The paper has no counterpart (this is the sort stage's error
+ * report, as rc_report is the check's). */
+rc_status rc_sort_status(const void* workspace_dev, void* stream);
 
 /* The same sort for callers that cannot allocate device memory when they sort:
  * code whose device memory is entirely reserved up front by another allocator
@@ -484,7 +507,9 @@ rc_status rc_sort_keys(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint
  * keeps the last call's contents (the counters that must start at zero are
  * cleared on every call), so calls whose work overlaps on the GPU (different
  * streams, or host threads on one device) race: serialise them.
- * Errors: RC_E_INVALID, RC_E_UNSUPPORTED, RC_E_CUDA. */
+ * Errors of the enqueue: RC_E_INVALID, RC_E_UNSUPPORTED, RC_E_CUDA; errors of
+ * the device work (RC_E_TIMEOUT, RC_E_INVALID, as for rc_sort_keys) are read
+ * with rc_sort_status(NULL, stream) after the call. */
 #define RC_SORT_STATIC_MAX_KEYS (1u << 20)
 rc_status rc_sort_keys_static(const uint64_t* keys_in_dev, uint64_t* keys_out_dev, uint64_t n,
                               uint32_t lo_bit, uint32_t hi_bit, uint32_t digit_bits, void* stream);

@@ -16,7 +16,7 @@ from .binding import (RC_OK, RC_E_INVALID, RC_E_KEY_OVERFLOW, RC_E_OOB, RC_E_NOM
                       RC_PATH_HASH, EXPORTS, NotReady, RcError, RcModel, RcServer, Result, check, load,
                       rc_batch_workspace_size, rc_check, rc_check_batch, rc_expand_keys, rc_get_limits,
                       rc_model_create, rc_model_create_status, rc_kernel_source, rc_model_destroy, rc_model_layout,
-                      rc_report, rc_report_array, results_of, rc_sort_keys, rc_sort_keys_static, rc_ticket_stage_times, rc_sort_workspace_size, rc_status_str,
+                      rc_report, rc_report_array, results_of, rc_sort_keys, rc_sort_keys_static, rc_sort_status, rc_ticket_stage_times, rc_sort_workspace_size, rc_status_str,
                       rc_tune, rc_workspace_size, workspace)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -46,7 +46,7 @@ RC_OPT_CHUNKED = 4
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
            "rc_workspace_size", "rc_check", "rc_batch_workspace_size", "rc_check_batch", "rc_report",
            "rc_expand_keys", "rc_sort_workspace_size", "rc_sort_keys", "rc_ticket_stage_times",
-           "rc_sort_keys_static", "rc_kernel_source", "rc_tune", "rc_server_create",
+           "rc_sort_keys_static", "rc_sort_status", "rc_kernel_source", "rc_tune", "rc_server_create",
            "rc_server_submit", "rc_server_poll", "rc_server_stats", "rc_server_destroy"]
 RC_SORT_STATIC_MAX_KEYS = 1 << 20
 
@@ -217,6 +217,8 @@ def load():
         lib.rc_kernel_source.restype = c_int
         lib.rc_sort_keys_static.argtypes = [c_void_p, c_void_p, c_uint64, c_uint32, c_uint32, c_uint32, c_void_p]
         lib.rc_sort_keys_static.restype = c_int
+        lib.rc_sort_status.argtypes = [c_void_p, c_void_p]
+        lib.rc_sort_status.restype = c_int
         lib.rc_ticket_stage_times.argtypes = [c_void_p, POINTER(rc_stage_times)]
         lib.rc_ticket_stage_times.restype = c_int
         _lib = lib
@@ -696,6 +698,17 @@ def rc_sort_keys_static(keys_in, keys_out, n: int, lo_bit: int, hi_bit: int, dig
                                     c_void_p(_stream(stream)))
     if st != RC_OK:
         raise RcError(st, "rc_sort_keys_static")
+
+
+def rc_sort_status(workspace=None, stream=None) -> int:
+    """Status of the device work of the last sort on ``workspace`` (None: the
+    last rc_sort_keys_static call on the current device); waits for ``stream``.
+    Returns RC_OK, RC_E_TIMEOUT or RC_E_INVALID; raises on RC_E_CUDA."""
+    st = load().rc_sort_status(c_void_p(_ptr(workspace) if workspace is not None else None),
+                               c_void_p(_stream(stream)))
+    if st == RC_E_CUDA:
+        raise RcError(st, "rc_sort_status")
+    return st
 
 
 # ---------------------------------------------------------------------------

@@ -59,13 +59,9 @@ __global__ void __launch_bounds__(256) histogram_np_kernel(const uint64_t* __res
 template <int NP>
 cudaError_t launch_np(const uint64_t* keys, uint64_t n, const SortPlan& sp, unsigned long long* hist, size_t smem,
                       cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(histogram_np_kernel<NP>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, NP * kMaxRadix * 4);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const cudaError_t e =
+      ensure_kernel_smem(reinterpret_cast<const void*>(histogram_np_kernel<NP>), NP * kMaxRadix * 4, false);
+  if (e != cudaSuccess) return e;
   uint64_t g = (n / 2 + 255) / 256;
   if (g < 1) g = 1;
   if (g > 152ull * 8) g = 152ull * 8;

@@ -56,11 +56,10 @@ struct Driver {
 
 std::mutex g_jit_mu;
 
-Nvrtc& nvrtc() {
-  static Nvrtc n;
-  static bool tried = false;
-  if (tried) return n;
-  tried = true;
+// The NVRTC entry points, looked up once per process (a function-local static
+// is initialised once even when several host threads get here together).
+Nvrtc load_nvrtc() {
+  Nvrtc n;
   const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
                          "/usr/local/cuda/lib64/libnvrtc.so"};
   void* h = nullptr;
@@ -75,12 +74,13 @@ Nvrtc& nvrtc() {
   n.ok = n.create && n.compile && n.cubin_size && n.cubin && n.destroy;
   return n;
 }
+Nvrtc& nvrtc() {
+  static Nvrtc n = load_nvrtc();
+  return n;
+}
 
-Driver& driver() {
-  static Driver d;
-  static bool tried = false;
-  if (tried) return d;
-  tried = true;
+Driver load_driver() {
+  Driver d;
   auto get = [](const char* sym, void** fn) {
     cudaDriverEntryPointQueryResult q;
     return cudaGetDriverEntryPointByVersion(sym, fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
@@ -91,6 +91,10 @@ Driver& driver() {
   d.load = reinterpret_cast<decltype(d.load)>(a);
   d.get = reinterpret_cast<decltype(d.get)>(b);
   d.launch = reinterpret_cast<decltype(d.launch)>(c);
+  return d;
+}
+Driver& driver() {
+  static Driver d = load_driver();
   return d;
 }
 

@@ -7,6 +7,12 @@
 
 namespace rc {
 
+// runtime.cu: sets a kernel's dynamic shared-memory limit to `smem_bytes` (and,
+// with max_carveout, its preferred carveout to the largest shared-memory share)
+// once per (device, kernel), with the current device; thread-safe; returns the
+// first failing CUDA call's error (and retries on the next launch).
+cudaError_t ensure_kernel_smem(const void* func, size_t smem_bytes, bool max_carveout = true);
+
 // expand.cu
 // has_deep: some statement has more than kFastLoops loops (runs the generic kernel too)
 // keys whose cell lies outside [cell_lo, cell_hi) are written as padding
@@ -119,6 +125,19 @@ cudaError_t launch_onesweep(const SortArgs& a, uint32_t radix_bits, cudaStream_t
 // unstable pass (any order among equal digits); a.cursor starts at the digit offsets
 cudaError_t launch_partition(const SortArgs& a, uint32_t radix_bits, cudaStream_t st);
 uint32_t radix_bits_for(uint32_t bits);
+// runtime.cu: byte ranges (offset, length) of a sort's scratch that must start
+// at zero -- the digit counts of its passes, the look-back words of its tiles
+// at its widest radix, its tile counters
+void sort_clear_ranges(const SortPlan& sp, uint64_t n, size_t hist_off, size_t lookback_off, size_t tilectr_off,
+                       size_t (*ranges)[2]);
+// Test hook of the sort entry points: with RC_TEST_SORT_STALL=1 in the
+// environment every look-back waits for a status epoch that no pass publishes,
+// so its bounded wait runs out (after a short spin limit) and the error word is
+// set; every access stays in bounds.
+bool sort_stall_requested();
+// sort_static.cu: device address of the static scratch's result record on the
+// current device (looked up once per device)
+rc_status sort_static_record(const void** rec);
 
 // scan.cu
 constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)
@@ -144,6 +163,10 @@ struct ScanArgs {
   // one triple per model of a batch (a model without such barriers: q = its
   // phase, one grid interval, one warp interval)
   const uint64_t* sync_tabs;
+  // witness group records per result: 2^(wit_block_bits + phase_bits), indexed
+  // (block, fine interval) when wit_block_bits > 0 (models with more than one
+  // grid interval), else by fine interval for the cell's lowest block only
+  uint32_t wit_block_bits;
 };
 // the interval tables of a scan (no warp or grid barriers: q is the phase)
 struct SyncTabs {

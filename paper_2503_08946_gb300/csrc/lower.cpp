@@ -331,6 +331,10 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   }
   h.sync_tab[0] = m->coarse_tab;
   h.sync_tab[1] = m->grid_tab;
+  // more than one grid interval: the witness keeps per-block group records
+  // (2^(block bits + phase bits) of them), so the grid is bounded
+  m->multi_grid = m->grid_tab != 0;
+  if (m->multi_grid && h.block_bits + h.phase_bits > kWitnessBlockGroupBits) return RC_E_UNSUPPORTED;
   h.sync_tab[2] = (uint64_t)n_wp | ((uint64_t)bit_length((uint64_t)n_wp - 1) << 32);
   // atomics are scanned by the phase-table scan only (at most 16 intervals)
   if (has_atomic && h.phase_bits > (uint32_t)kScanTablePhaseBits) return RC_E_UNSUPPORTED;

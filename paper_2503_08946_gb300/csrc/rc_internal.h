@@ -177,9 +177,13 @@ struct DevResult {
 static_assert(sizeof(DevResult) <= 256, "result record must fit its slot");
 
 // words of one witness phase-group record (scan.cu): [mint, maxt], per access
-// kind (R, W, A) [min thread, max thread, any] in the lowest block, and per kind
+// kind (R, W, A) [min thread, max thread, any] in one block, and per kind
 // [min block, max block] over all blocks
 constexpr unsigned kWitnessGroupWords = 17;
+// Models with more than one grid interval keep one record per (block, fine
+// interval) -- the smallest racing instance may lie above the cell's lowest
+// block -- so their block and phase bits are bounded: 2^20 records of 68 bytes.
+constexpr uint32_t kWitnessBlockGroupBits = 20;
 
 enum DevError : unsigned int {
   kErrLookbackTimeout = 1u,
@@ -187,6 +191,8 @@ enum DevError : unsigned int {
   kErrHashFull = 4u,
   kErrScanLongFull = 8u,
   kErrChunkOverflow = 16u,   // a chunk produced more keys than its count pass planned
+  kErrSortRange = 32u,       // a sort pass computed a destination outside the output (its digit
+                             // counts and its ranks disagree: the input changed while it ran)
 };
 
 // packed out-of-bounds code: stmt (12 bits) | access (6) | gtid (42) | dimcode (3)
@@ -368,6 +374,7 @@ struct Model {
   bool wide = false;
   bool has_atomic = false;        // some access is atomic: 2-bit kind field
   bool sync_scopes = false;       // warp or grid barriers
+  bool multi_grid = false;        // more than one grid interval (grid barriers)
   uint64_t coarse_tab = 0;        // fine interval q -> block interval (4 bits per q)
   uint64_t grid_tab = 0;          // fine interval q -> grid interval (4 bits per q)
   // sections of the program image (byte offsets), for the kernel generator

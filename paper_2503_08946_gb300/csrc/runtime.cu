@@ -134,6 +134,38 @@ uint32_t scan_warps_for(uint64_t n) {
 
 namespace rc {
 
+namespace {
+struct SmemAttr {
+  int device;
+  const void* func;
+};
+std::mutex g_attr_mu;
+std::vector<SmemAttr> g_attr_done;
+}  // namespace
+
+cudaError_t ensure_kernel_smem(const void* func, size_t smem_bytes, bool max_carveout) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const SmemAttr& d : g_attr_done)
+    if (d.device == dev && d.func == func) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e == cudaSuccess && max_carveout)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  g_attr_done.push_back({dev, func});
+  return cudaSuccess;
+}
+
+// Witness group records of one check: one per fine interval of the cell's
+// lowest block, or one per (block, fine interval) with more than one grid
+// interval (the smallest racing instance may then lie in a later block).
+size_t witness_group_bytes(const Model& m) {
+  const uint32_t bits = m.host.phase_bits + (m.multi_grid ? m.host.block_bits : 0u);
+  return ((size_t)1 << bits) * kWitnessGroupWords * sizeof(unsigned int);
+}
+
 // The path a check takes: RC_PATH_HASH on request, otherwise the sort path.
 bool use_hash_path(const Model&, const rc_check_opts* opts) { return opts && opts->path == RC_PATH_HASH; }
 
@@ -166,7 +198,7 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
     p->nfilt_off = off;
     off = align256(off + 8);
     p->group_off = off;
-    off = align256(off + ((size_t)1 << m.host.phase_bits) * rc::kWitnessGroupWords * sizeof(unsigned int));
+    off = align256(off + witness_group_bytes(m));
     p->total = off;
     return;
   }
@@ -206,7 +238,7 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   p->long_off = off;   // cells handed to the long-cell pass
   off = align256(off + (size_t)p->long_cap * 8);
   p->group_off = off;
-  off = align256(off + ((size_t)1 << m.host.phase_bits) * rc::kWitnessGroupWords * sizeof(unsigned int));
+  off = align256(off + witness_group_bytes(m));
   p->total = off;
 }
 
@@ -239,6 +271,7 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
   a.sync_tabs = m.sync_scopes ? reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(m.dev_program) +
                                                                   offsetof(rc::DevModel, sync_tab))
                               : nullptr;
+  a.wit_block_bits = m.multi_grid ? m.host.block_bits : 0u;
   return a;
 }
 
@@ -406,6 +439,10 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
     out->status = RC_E_NOMEM;
     return;
   }
+  if (r.err & rc::kErrSortRange) {   // (the sort's guard against an out-of-range store fired)
+    out->status = RC_E_CUDA;
+    return;
+  }
   if (r.oob_code != ~0ull) {
     out->status = RC_E_OOB;
     out->oob_stmt = (uint32_t)(r.oob_code >> 51);
@@ -427,11 +464,11 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
   out->w_array = (uint32_t)a;
   out->w_scope = m.array_shared[a] ? rem / m.array_cells[a] : 0;
   out->w_addr = m.array_shared[a] ? rem % m.array_cells[a] : rem;
-  // ranks: (phase, thread, kind, warp phase) and (block, phase, thread, kind, warp phase)
+  // ranks of x and y: (block, phase, thread, kind, warp phase)
   const uint64_t tmask = (1ull << tb) - 1, pmask = (1ull << pb) - 1, kmask = (1ull << kb) - 1;
   const uint64_t wmask = (1ull << wb) - 1;
   const uint64_t bs = m.host.bs;
-  out->x.block = r.minb;
+  out->x.block = r.x_rank >> (pb + tb + kb + wb);
   out->x.warp_phase = (uint32_t)(r.x_rank & wmask);
   out->x.kind = (uint32_t)((r.x_rank >> wb) & kmask);
   out->x.thread = (uint32_t)((r.x_rank >> (wb + kb)) & tmask);
@@ -757,6 +794,7 @@ struct BatchPack {
   uint32_t kb = 1;                     // kind field bits (2 if some model has atomics)
   bool loop_free = true;               // every model of the pack is loop-free
   bool sy = false;                     // some model has warp or grid barriers
+  bool mg = false;                     // its models have more than one grid interval (per-block witness groups)
   uint64_t total_cells = 0, n_keys = 0, n_units = 0;
   rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
 };
@@ -790,7 +828,11 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
       // that fit them
       const bool sy = cur.sy || m.sync_scopes;
       const bool table_ok = (kb == 1 && !sy) || pb <= (uint32_t)rc::kScanTablePhaseBits;
-      if (cells >= cur.total_cells && table_ok && kb + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
+      // models with several grid intervals share a pack only with each other, and
+      // its per-(model, block, fine interval) witness records stay bounded
+      const bool mg_ok = cur.mg == m.multi_grid &&
+                         (!cur.mg || ((uint64_t)(i + 1 - cur.i0) << (bb + pb)) <= (1ull << rc::kWitnessBlockGroupBits));
+      if (cells >= cur.total_cells && table_ok && mg_ok && kb + tb + bb + pb + cb <= (uint32_t)rc::kKeyBits) {
         cur.tb = tb; cur.bb = bb; cur.pb = pb; cur.kb = kb; cur.total_cells = cells; cur.cell_bits = cb;
         cur.loop_free = cur.loop_free && m.loop_free;
         cur.sy = sy;
@@ -807,6 +849,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur.tb = h.thread_bits; cur.bb = h.block_bits; cur.pb = h.phase_bits; cur.kb = h.thread_shift;
     cur.loop_free = m.loop_free;
     cur.sy = m.sync_scopes;
+    cur.mg = m.multi_grid;
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
@@ -864,7 +907,8 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     p.long_off = o;
     o = align256(o + (size_t)p.long_cap * 8);
     p.group_off = o;
-    o = align256(o + (k.i1 - k.i0) * ((size_t)1 << k.pb) * rc::kWitnessGroupWords * sizeof(unsigned int));
+    o = align256(o + (k.i1 - k.i0) * ((size_t)1 << (k.pb + (k.mg ? k.bb : 0u))) * rc::kWitnessGroupWords *
+                         sizeof(unsigned int));
     p.total = o;
     need = std::max(need, o);
   }
@@ -976,6 +1020,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.n_models = nm;
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
     sa.sync_tabs = k.sy ? dstabs + 3 * k.i0 : nullptr;
+    sa.wit_block_bits = k.mg ? k.bb : 0u;
     s = cuda_status(rc::launch_scan(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
@@ -1651,6 +1696,33 @@ rc_status rc_sort_workspace_size(uint64_t n, uint32_t digit_bits, size_t* bytes)
   return RC_OK;
 }
 
+}  // extern "C"
+
+namespace rc {
+bool sort_stall_requested() {
+  const char* v = std::getenv("RC_TEST_SORT_STALL");
+  return v && v[0] == '1';
+}
+
+// The byte ranges of a sort's scratch that must start at zero: the digit
+// counts of its passes, the look-back words of its tiles at the widest radix of
+// its passes, and its tile counters.
+void sort_clear_ranges(const SortPlan& sp, uint64_t n, size_t hist_off, size_t lookback_off, size_t tilectr_off,
+                       size_t (*ranges)[2]) {
+  uint32_t rb = 0;
+  for (uint32_t k = 0; k < sp.n_pass; ++k) rb = std::max(rb, radix_bits_for(sp.bits[k]));
+  const uint64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+  ranges[0][0] = hist_off;
+  ranges[0][1] = (size_t)sp.n_pass * kMaxRadix * 8;
+  ranges[1][0] = lookback_off;
+  ranges[1][1] = (size_t)n_tiles * ((size_t)1 << rb) * 8;
+  ranges[2][0] = tilectr_off;
+  ranges[2][1] = 16 * sizeof(unsigned int);
+}
+}  // namespace rc
+
+extern "C" {
+
 rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t lo_bit, uint32_t hi_bit,
                        uint32_t digit_bits, void* workspace, size_t ws_bytes, void* stream) {
   if (hi_bit > 64 || lo_bit > hi_bit || (n && (!keys_in || !keys_out || keys_in == keys_out))) return RC_E_INVALID;
@@ -1679,10 +1751,11 @@ rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, 
   p.digoff_off = off;
   off = align256(off + (size_t)16 * rc::kMaxRadix * 8);
   const size_t pong = off;
-  if (n == 0) return RC_OK;
-  rc_status s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
-  if (s != RC_OK) return s;
-  s = cuda_status(rc::launch_init_result(reinterpret_cast<rc::DevResult*>(ws + p.result_off), st));
+  rc_status s = cuda_status(rc::launch_init_result(reinterpret_cast<rc::DevResult*>(ws + p.result_off), st));
+  if (s != RC_OK || n == 0) return s;
+  size_t clear[3][2];
+  rc::sort_clear_ranges(p.sort, n, p.hist_off, p.lookback_off, p.tilectr_off, clear);
+  for (int r = 0; r < 3 && s == RC_OK; ++r) s = cuda_status(cudaMemsetAsync(ws + clear[r][0], 0, clear[r][1], st));
   if (s != RC_OK) return s;
   // Stage the input in the output buffer and ping-pong with the workspace
   // buffer; with an odd number of passes the result lands in the workspace
@@ -1690,10 +1763,29 @@ rc_status rc_sort_keys(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, 
   s = cuda_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st));
   if (s != RC_OK) return s;
   int sorted = 0;
-  s = enqueue_sort(p, ws, keys_out, reinterpret_cast<uint64_t*>(ws + pong), 1ull << 20, 0u, st, &sorted);
+  const bool stall = rc::sort_stall_requested();
+  s = enqueue_sort(p, ws, keys_out, reinterpret_cast<uint64_t*>(ws + pong), stall ? 4096ull : (1ull << 20),
+                   stall ? (uint32_t)RC_TEST_STALL_LOOKBACK : 0u, st, &sorted);
   if (s != RC_OK) return s;
   if (sorted == 1) s = cuda_status(cudaMemcpyAsync(keys_out, ws + pong, n * 8, cudaMemcpyDeviceToDevice, st));
   return s;
+}
+
+rc_status rc_sort_status(const void* workspace, void* stream) {
+  const void* rec = workspace;
+  if (!rec) {
+    rc_status s = rc::sort_static_record(&rec);
+    if (s != RC_OK) return s;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RC_E_CUDA;
+  unsigned int err = 0;
+  if (cudaMemcpy(&err, static_cast<const uint8_t*>(rec) + offsetof(rc::DevResult, err), sizeof(err),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RC_E_CUDA;
+  if (err & rc::kErrLookbackTimeout) return RC_E_TIMEOUT;
+  if (err & rc::kErrSortRange) return RC_E_INVALID;
+  return RC_OK;
 }
 
 }  // extern "C"

@@ -1012,20 +1012,37 @@ __device__ __forceinline__ bool kinds_conflict(unsigned kx, unsigned ky) {
   return kx == 1u || ky == 1u || (kx ^ ky) == 2u;
 }
 
-// group record of one phase of the lowest block: [mint, maxt] over all
-// instances, then per kind K (R, W, A) [minKt, maxKt, anyK]
+// group record of one fine interval q of one block: [mint, maxt] over all its
+// instances, then per kind K (R, W, A) [minKt, maxKt, anyK]; words 11.. of the
+// record (block 0, q) hold per kind the [min, max] block holding K in q (warp or
+// grid barriers).  Without per-block records (a.wit_block_bits == 0) the thread
+// words describe the cell's lowest block only: with at most one grid interval
+// the smallest racing instance always lies there (a block barrier orders
+// nothing across blocks, so the lowest block's instances meet every other
+// block's).  With several grid intervals the lowest block's instances may all
+// be ordered before the racing ones, so every block keeps its records.
 constexpr unsigned kGroupWords = kWitnessGroupWords;
 // Each kernel handles result blockIdx.y (one per model of a batch) with the
 // blocks of its x dimension.
 __device__ __forceinline__ unsigned* groups_of(const ScanArgs& a) {
-  return a.groups + (size_t)blockIdx.y * kGroupWords * (1u << a.phase_bits);
+  return a.groups + (size_t)blockIdx.y * kGroupWords * ((size_t)1 << (a.phase_bits + a.wit_block_bits));
+}
+// the record of (block b, fine interval q)
+__device__ __forceinline__ unsigned* group_rec(const ScanArgs& a, unsigned* groups, unsigned b, unsigned q) {
+  const size_t i = a.wit_block_bits ? (((size_t)b << a.phase_bits) | q) : q;
+  return groups + i * kGroupWords;
+}
+__device__ __forceinline__ const unsigned* group_rec(const ScanArgs& a, const unsigned* groups, unsigned b,
+                                                     unsigned q) {
+  const size_t i = a.wit_block_bits ? (((size_t)b << a.phase_bits) | q) : q;
+  return groups + i * kGroupWords;
 }
 
 // the cell summary: blocks of all instances and of each kind
 __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
   DevResult* r = a.res + blockIdx.y;
   const uint64_t s = r->min_start;
-  const uint32_t n_groups = 1u << a.phase_bits;
+  const uint32_t n_groups = 1u << (a.phase_bits + a.wit_block_bits);
   unsigned* groups = groups_of(a);
   if (s == ~0ull) return;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
@@ -1088,13 +1105,14 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   const unsigned b0 = r->minb;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
-    unsigned* g = groups + f.p * kGroupWords;
     if (syt.on) {
       // blocks holding each kind per fine interval (cross-block partners of one grid interval)
-      atomicMin(&g[11 + 2 * f.k], f.b);
-      atomicMax(&g[12 + 2 * f.k], f.b);
+      unsigned* g0 = group_rec(a, groups, 0u, f.p);
+      atomicMin(&g0[11 + 2 * f.k], f.b);
+      atomicMax(&g0[12 + 2 * f.k], f.b);
     }
-    if (f.b != b0) continue;
+    if (!a.wit_block_bits && f.b != b0) continue;
+    unsigned* g = group_rec(a, groups, f.b, f.p);
     atomicMin(&g[0], f.t);
     atomicMax(&g[1], f.t);
     unsigned* gk = g + 2 + 3 * f.k;
@@ -1118,8 +1136,10 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const Fields f = fields(a, a.keys[i]);
-    if (f.b != b0) continue;
-    const unsigned* g = groups + f.p * kGroupWords;
+    // candidates: the lowest block's instances, or every block's with per-block records
+    if (!a.wit_block_bits && f.b != b0) continue;
+    const unsigned xb = f.b;
+    const unsigned* g = group_rec(a, groups, xb, f.p);
     bool cross = false, same = false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -1136,22 +1156,24 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
       // warp of this block in the same block interval
       const unsigned xc = (unsigned)(syt.coarse >> (4 * f.p)) & 15u, xg = (unsigned)(syt.grid >> (4 * f.p)) & 15u;
       for (unsigned q = 0; q < (1u << a.phase_bits); ++q) {
-        const unsigned* gq = groups + q * kGroupWords;
+        const unsigned* gq = group_rec(a, groups, 0u, q);
         if ((((unsigned)(syt.grid >> (4 * q)) & 15u) == xg) && gq[11 + 2 * k] != 0xffffffffu &&
-            (gq[11 + 2 * k] != b0 || gq[12 + 2 * k] != b0))
+            (gq[11 + 2 * k] != xb || gq[12 + 2 * k] != xb))
           cross = true;
         if (q != f.p && (((unsigned)(syt.coarse >> (4 * q)) & 15u) == xc)) {
-          const unsigned* gqk = gq + 2 + 3 * k;
+          const unsigned* gqk = group_rec(a, groups, xb, q) + 2 + 3 * k;
           if (gqk[2] && ((gqk[0] >> 5) != (f.t >> 5) || (gqk[1] >> 5) != (f.t >> 5))) same = true;
         }
       }
     }
     if (cross || same) {
-      // rank in the tuple order (phase, thread, kind, warp phase)
+      // rank in the tuple order (block, phase, thread, kind, warp phase)
       const unsigned p = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
       const unsigned wv = f.p - p * syt.n_wp;
-      const unsigned long long rank = ((((unsigned long long)p << (a.thread_bits + kb)) |
-                                        ((unsigned long long)f.t << kb) | f.k) << syt.wp_bits) | wv;
+      const unsigned long long rank =
+          ((((unsigned long long)xb << (a.phase_bits + a.thread_bits + kb)) |
+            ((unsigned long long)p << (a.thread_bits + kb)) | ((unsigned long long)f.t << kb) | f.k) << syt.wp_bits) |
+          wv;
       best = rank < best ? rank : best;
     }
   }
@@ -1170,14 +1192,14 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   const uint64_t s = r->min_start;
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;
-  const unsigned b0 = r->minb;
   const uint32_t kb = a.thread_shift;
   const unsigned long long xr = r->x_rank;
   const uint32_t wb = syt.wp_bits;
   const unsigned xw = (unsigned)(xr & ((1ull << wb) - 1ull));
   const unsigned xk = (unsigned)(xr >> wb) & ((1u << kb) - 1u);
   const unsigned xt = (unsigned)(xr >> (wb + kb)) & ((1u << a.thread_bits) - 1u);
-  const unsigned xp = (unsigned)(xr >> (wb + kb + a.thread_bits));
+  const unsigned xp = (unsigned)(xr >> (wb + kb + a.thread_bits)) & ((1u << a.phase_bits) - 1u);
+  const unsigned b0 = (unsigned)(xr >> (wb + kb + a.thread_bits + a.phase_bits));   // x's block
   const unsigned xq = xp * syt.n_wp + xw;
   const unsigned xg = (unsigned)(syt.grid >> (4 * xq)) & 15u;
   unsigned long long best = ~0ull;

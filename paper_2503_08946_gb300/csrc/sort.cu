@@ -324,7 +324,11 @@ __global__ void __launch_bounds__(kSortThreads, SK ? 4 : (RB <= 9 ? 3 : 2)) ones
   for (int pos = threadIdx.x; pos < n_here; pos += kSortThreads) {
     const uint64_t key = s_keys[pos];
     const unsigned int dd = (unsigned int)(key >> a.shift) & dmask;
-    a.keys_out[delta[dd] + (unsigned long long)pos] = key;
+    const unsigned long long dst = delta[dd] + (unsigned long long)pos;
+    // in range whenever the digit counts match the ranks; a mismatch (input
+    // changed under the sort) is reported instead of written out of bounds
+    if (dst < a.n) a.keys_out[dst] = key;
+    else atomicOr(a.err, (unsigned int)kErrSortRange);
   }
 }
 
@@ -452,20 +456,17 @@ __global__ void __launch_bounds__(kSortThreads, 5) partition_kernel(SortArgs a) 
   for (int pos = threadIdx.x; pos < n_here; pos += kSortThreads) {
     const uint64_t key = s_keys[pos];
     const unsigned int dd = (unsigned int)(key >> a.shift) & dmask;
-    a.keys_out[delta[dd] + (unsigned long long)pos] = key;
+    const unsigned long long dst = delta[dd] + (unsigned long long)pos;
+    if (dst < a.n) a.keys_out[dst] = key;   // (see the onesweep scatter)
+    else atomicOr(a.err, (unsigned int)kErrSortRange);
   }
 }
 
 template <int RB>
 cudaError_t launch_partition_rb(const SortArgs& a, cudaStream_t st) {
-  static bool attr_set = false;
   constexpr size_t smem = partition_smem<RB>();
-  if (!attr_set) {
-    cudaFuncSetAttribute(partition_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(partition_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    attr_set = true;
-  }
+  const cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void*>(partition_kernel<RB>), smem);
+  if (e != cudaSuccess) return e;
   const uint64_t n_tiles = (a.n + kPartTile - 1) / kPartTile;
   partition_kernel<RB><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -473,15 +474,10 @@ cudaError_t launch_partition_rb(const SortArgs& a, cudaStream_t st) {
 
 template <int RB>
 cudaError_t launch_rb(const SortArgs& a, cudaStream_t st) {
-  static bool attr_set = false;
   constexpr size_t smem = onesweep_smem<RB>();
   constexpr bool SK = RB <= 8;   // staged keys for the 7- and 8-bit kernels
-  if (!attr_set) {
-    cudaFuncSetAttribute(onesweep_kernel<RB, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(onesweep_kernel<RB, SK>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    attr_set = true;
-  }
+  const cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void*>(onesweep_kernel<RB, SK>), smem);
+  if (e != cudaSuccess) return e;
   const uint64_t n_tiles = (a.n + kSortTile - 1) / kSortTile;
   onesweep_kernel<RB, SK><<<(unsigned)n_tiles, kSortThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -497,11 +493,8 @@ cudaError_t launch_histogram(const uint64_t* keys, uint64_t n, const SortPlan& s
   if (n == 0 || sp.n_pass == 0) return cudaSuccess;
   size_t smem = 0;
   for (uint32_t p = 0; p < sp.n_pass; ++p) smem += (size_t)4 << sp.bits[p];
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(histogram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kMaxRadix * 4);
-    attr_set = true;
-  }
+  const cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void*>(histogram_kernel), 16 * kMaxRadix * 4, false);
+  if (e != cudaSuccess) return e;
   uint64_t g = (n + 255) / 256;
   if (g > 152ull * 8) g = 152ull * 8;
   histogram_kernel<<<(unsigned)g, 256, smem, st>>>(keys, n, sp, hist);

@@ -55,6 +55,15 @@ rc_status as_status(cudaError_t e) { return e == cudaSuccess ? RC_OK : RC_E_CUDA
 
 }  // namespace
 
+namespace rc {
+rc_status sort_static_record(const void** rec) {
+  uint8_t* s = nullptr;
+  const rc_status st = scratch_for_current_device(&s);
+  if (st == RC_OK) *rec = s + kOffResult;
+  return st;
+}
+}  // namespace rc
+
 extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t lo_bit,
                                          uint32_t hi_bit, uint32_t digit_bits, void* stream) {
   if (hi_bit > 64 || lo_bit > hi_bit || (n && (!keys_in || !keys_out || keys_in == keys_out))) return RC_E_INVALID;
@@ -62,21 +71,26 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
   uint8_t* s = nullptr;
   rc_status st = scratch_for_current_device(&s);
   if (st != RC_OK) return st;
-  if (n == 0) return RC_OK;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  auto* res = reinterpret_cast<rc::DevResult*>(s + kOffResult);
+  // the error word read by rc_sort_status starts clear for every call
+  st = as_status(rc::launch_init_result(res, cs));
+  if (st != RC_OK || n == 0) return st;
   rc::SortPlan sp;
   rc::plan_sort(lo_bit, hi_bit, digit_bits, &sp);
-  auto* res = reinterpret_cast<rc::DevResult*>(s + kOffResult);
   auto* hist = reinterpret_cast<unsigned long long*>(s + kOffHist);
   auto* digoff = reinterpret_cast<unsigned long long*>(s + kOffDigoff);
   uint64_t* pong = reinterpret_cast<uint64_t*>(s + kOffPong);
-  // the array keeps the previous call's contents: clear the counters that start at zero
-  st = as_status(cudaMemsetAsync(s + kOffHist, 0, kOffDigoff - kOffHist, cs));
-  if (st == RC_OK) st = as_status(rc::launch_init_result(res, cs));
+  // the array keeps the previous call's contents: clear what must start at
+  // zero (this call's digit counts, look-back words and tile counters)
+  size_t clear[3][2];
+  rc::sort_clear_ranges(sp, n, kOffHist, kOffLookback, kOffTileCtr, clear);
+  for (int r = 0; r < 3 && st == RC_OK; ++r) st = as_status(cudaMemsetAsync(s + clear[r][0], 0, clear[r][1], cs));
   if (st == RC_OK) st = as_status(cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, cs));
   if (st == RC_OK) st = as_status(rc::launch_digit_counts(keys_out, n, sp, hist, cs));
   if (st == RC_OK) st = as_status(rc::launch_digit_offsets(hist, digoff, sp, cs));
   uint64_t* bufs[2] = {keys_out, pong};
+  const bool stall = rc::sort_stall_requested();
   int cur = 0;
   for (uint32_t k = 0; k < sp.n_pass && st == RC_OK; ++k) {
     rc::SortArgs a;
@@ -89,8 +103,8 @@ extern "C" rc_status rc_sort_keys_static(const uint64_t* keys_in, uint64_t* keys
     a.lookback = reinterpret_cast<unsigned long long*>(s + kOffLookback);
     a.tile_counter = reinterpret_cast<unsigned int*>(s + kOffTileCtr) + k;
     a.epoch = k + 1;
-    a.wait_epoch = k + 1;
-    a.spin_limit = 1ull << 20;
+    a.wait_epoch = stall ? (k + 1) ^ 0x8000u : k + 1;   // (the test hook: a wait nothing ends)
+    a.spin_limit = stall ? 4096ull : (1ull << 20);
     a.err = &res->err;
     a.cursor = nullptr;
     st = as_status(rc::launch_onesweep(a, rc::radix_bits_for(a.bits), cs));

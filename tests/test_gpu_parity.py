@@ -282,6 +282,28 @@ def test_sort_stable(rc, n, bits):
         torch.cuda.synchronize()
         got = dout.cpu().numpy().view(np.uint64)
         assert np.array_equal(got, exp), (n, bits, db)
+        assert rc.rc_sort_status(ws) == rc.RC_OK
+
+
+def test_sort_timeout_is_reported_and_context_survives(rc, monkeypatch):
+    """A look-back wait of the sort entry point that runs out (the test hook
+    makes every wait look for a status epoch nothing publishes) is reported by
+    rc_sort_status; the next sort is exact."""
+    n = 300_000
+    g = torch.Generator().manual_seed(77)
+    x = torch.randint(-(1 << 62), 1 << 62, (n,), generator=g, dtype=torch.int64)
+    keys = x.numpy().view(np.uint64)
+    exp = keys[np.argsort((keys >> np.uint64(4)) & np.uint64((1 << 24) - 1), kind="stable")]
+    din = x.cuda()
+    dout = torch.empty_like(din)
+    ws = rc.workspace(rc.rc_sort_workspace_size(n, 8))
+    monkeypatch.setenv("RC_TEST_SORT_STALL", "1")
+    rc.rc_sort_keys(din, dout, n, 4, 28, 8, ws)
+    assert rc.rc_sort_status(ws) == rc.RC_E_TIMEOUT
+    monkeypatch.delenv("RC_TEST_SORT_STALL")
+    rc.rc_sort_keys(din, dout, n, 4, 28, 8, ws)
+    assert rc.rc_sort_status(ws) == rc.RC_OK
+    assert np.array_equal(dout.cpu().numpy().view(np.uint64), exp)
 
 
 # ---------------------------------------------------------------------------

@@ -230,3 +230,45 @@ def test_batch_sync_hash_path(rc):
     """A batch on the hash path checks its models one by one."""
     models = [w.tiny_random_sync(s) for s in range(400, 430)] + [w.tiny_random(s) for s in range(10)]
     check_batch(rc, models, {"path": rc.RC_PATH_HASH, "early_exit": 0})
+
+
+# ---------------------------------------------------------------------------
+# witnesses above the cell's lowest block (several grid intervals)
+# ---------------------------------------------------------------------------
+
+LATE = [(3, 1), (5, 1), (2, 1), (2, 2), (3, 2), (4, 3), (7, 33), (64, 64)]
+
+
+@pytest.mark.parametrize("nb,bs", LATE)
+@pytest.mark.parametrize("path", ["sort", "hash", "chunked"])
+def test_grid_late_partner(rc, nb, bs, path):
+    """Block 0 reads before the grid barrier, the later blocks write after it:
+    the smallest racing instance is block 1's write, not an instance of the
+    cell's lowest block."""
+    opts = {"sort": None, "hash": {"path": rc.RC_PATH_HASH, "early_exit": 0},
+            "chunked": {"flags": rc.binding.RC_OPT_CHUNKED}}[path]
+    g = compare(rc, w.grid_late_partner(nb, bs), opts)
+    if (nb - 1) * bs >= 2:
+        assert g.witness[3][0] == 1   # x in block 1
+
+
+@pytest.mark.parametrize("seed", range(600))
+def test_tiny_random_sync_block_guards(rc, seed):
+    compare(rc, w.tiny_random_sync(seed, block_guards=True))
+
+
+@pytest.mark.parametrize("seed", range(0, 600, 3))
+def test_tiny_random_sync_block_guards_hash(rc, seed):
+    compare(rc, w.tiny_random_sync(seed, block_guards=True), {"path": rc.RC_PATH_HASH, "early_exit": 0})
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_block_guards(rc, graph):
+    """Models with several grid intervals (per-block witness records) share
+    packs only with each other; mixed with other models in one batch."""
+    opts = {"flags": rc.binding.RC_OPT_GRAPH} if graph else None
+    guarded = [w.tiny_random_sync(s, block_guards=True) for s in range(200)]
+    late = [w.grid_late_partner(nb, bs) for nb, bs in LATE]
+    other = [w.tiny_random_sync(s) for s in range(40)] + [w.tiny_random(s) for s in range(40)]
+    got = check_batch(rc, _interleave(guarded, late, other), opts)
+    assert sum(g.verdict for g in got) > 100
