@@ -41,6 +41,7 @@ WORKLOAD = ("seeded random affine kernel model: 4096 blocks x 256 threads, 36 st
 METRIC = "access instances checked/sec (G/s)"
 UNIT = "G inst/s"
 CPU_SAMPLE_BLOCKS = 128       # oracle baseline: same generator and seed, 128 of the 4096 blocks
+CPU_SAMPLE_BLOCKS_ALL = 256   # all-cores oracle baseline: 256 of the 4096 blocks
 REF_STEP_BLOCKS = 32          # reference arm: per-step sample
 
 
@@ -138,15 +139,32 @@ def gpu_index(local_rank: int) -> int:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (test infrastructure, timed as it stands)
 # ---------------------------------------------------------------------------
-def oracle_rate(seed: int, blocks: int):
+def oracle_rate(seed: int, blocks: int, threads: int = 1):
+    """The oracle on a sample of the benchmark model (same generator and seed,
+    fewer blocks): one thread, or `threads` workers over cell ranges."""
     import oracle
     import workloads as w
     oracle.build()
     m = w.random_affine(seed, n_blocks=blocks, block=256)
     t0 = time.perf_counter()
-    r = oracle.check(m)
+    r = oracle.check(m) if threads == 1 else oracle.check_parallel(m, threads)
     dt = time.perf_counter() - t0
     return r.instances, dt, m
+
+
+def cpu_baselines(seed: int):
+    """Single-core and all-core oracle rates on bounded samples (~5-15 s each)."""
+    n1, dt1, _ = oracle_rate(seed, CPU_SAMPLE_BLOCKS)
+    cores = os.cpu_count() or 1
+    nn, dtn, _ = oracle_rate(seed, CPU_SAMPLE_BLOCKS_ALL, cores)
+    single = {"value": n1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"same generator and seed with {CPU_SAMPLE_BLOCKS} of the 4096 blocks "
+                        f"({n1} instances, {dt1:.1f} s)"}
+    return {"value": nn / dtn / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"same generator and seed with {CPU_SAMPLE_BLOCKS_ALL} of the 4096 blocks ({nn} instances, "
+                      f"{dtn:.1f} s): the oracle over {cores} equal cell ranges on std::thread workers "
+                      "(each enumerates the whole sample and keeps its own cells)",
+            "single_core": single}
 
 
 def run_reference(args):
@@ -198,6 +216,9 @@ def run_native(args):
 
     seed = args.seed + rank
     model = w.random_affine(seed, n_blocks=args.blocks)
+    # the generator's closed form: race-free by construction, or exactly T racy
+    # cells when a race is planted (T = threads)
+    expect_racy = model.n_model_threads if model.planted else 0
     h = rc.rc_model_create(model)
     lay = rc.rc_model_layout(h)
     opts = {"digit_bits": args.digit_bits, "flags": rc.binding.RC_OPT_STAGE_TIMES}
@@ -210,6 +231,9 @@ def run_native(args):
         res = rc.rc_report(t)[0]
         if res.status != rc.RC_OK:
             raise RuntimeError(f"check failed: {rc.rc_status_str(res.status)}")
+        if res.racy_cells != expect_racy:
+            raise RuntimeError(f"check result {res.racy_cells} racy cells, the generator's closed form "
+                               f"gives {expect_racy}")
         return res, st
 
     for _ in range(max(3, args.warmup)):
@@ -279,7 +303,8 @@ def run_native(args):
             hm = rc.rc_model_create(model)          # host lowering + upload of the program
             t = rc.rc_check(hm, {"digit_bits": args.digit_bits}, ws, stream)
             r = rc.rc_report(t)[0]                  # device-to-host copy of the result record
-            assert r.status == rc.RC_OK
+            if r.status != rc.RC_OK or r.racy_cells != expect_racy:
+                raise RuntimeError(f"end-to-end check gave {r}")
             hm.close()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -291,12 +316,25 @@ def run_native(args):
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(lay["program_bytes"]),
                "d2h_bytes_per_step": 256, "steps": n_e2e}
 
+    result = {"racy_cells": res.racy_cells, "verdict": res.verdict, "instances": instances,
+              "expected_racy_cells": expect_racy, "checked": "every step against the generator's closed form"}
+
+    # sub-records (not part of the headline): the hash path on the same model,
+    # a batch of 10,000 small models against one check per model, a Poisson
+    # request stream through the server
+    subs = {}
+    if not args.no_sub:
+        del ws
+        torch.cuda.empty_cache()
+        subs["hash"] = hash_measure(rc, h, model, expect_racy, stream, steps=3)
+        torch.cuda.empty_cache()
+        subs["batch"] = batch_measure(args, rc, w, torch, rank, world, dist, steps=5, pm_steps=1, compact=True)
+        torch.cuda.empty_cache()
+        subs["serve"] = serve_measure(args, rc, w, torch, rank, world, dist, n_requests=2000, compact=True)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dt, _ = oracle_rate(args.seed, CPU_SAMPLE_BLOCKS)
-        cpu = {"value": n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"same generator and seed with {CPU_SAMPLE_BLOCKS} of the 4096 blocks "
-                         f"({n} instances, {dt:.1f} s)"}
+        cpu = cpu_baselines(args.seed)
 
     if rank == 0:
         line = {
@@ -308,10 +346,12 @@ def run_native(args):
                        "keys": n_keys, "sort_bits": lay["sort_hi"] - lay["sort_lo"], "sort_passes": n_pass,
                        "path": "sort", "l2": "inputs larger than L2 (key buffers ~9 GB)",
                        "parallelism": f"independent models per rank x{world}"},
+            "result": result,
             "roofline": roofline, "pipeline": pipeline, "stages_ms": st_mean,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": (11 + n_pass) * args.steps,
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -393,21 +433,22 @@ BATCH_WORKLOAD = ("10,000 seeded random models: threads log-uniform 32..65,536 (
                   "min(T, 256)), 1-8 loop-free access statements, 4 arrays, 8 barrier intervals, 1% planted races")
 
 
-def run_batch(args):
-    import torch
-    import workloads as w
-    import paper_2503_08946_gb300 as rc
-    from paper_2503_08946_gb300 import build as b
-    from paper_2503_08946_gb300 import distributed as D
+def batch_closed_form(models, results):
+    """Every model's result against the generator's closed form (T racy cells
+    when a race is planted, else none); returns the number of racy models."""
+    racy = 0
+    for m, r in zip(models, results):
+        exp = m.n_model_threads if m.planted else 0
+        if r.racy_cells != exp:
+            raise RuntimeError(f"{m.name}: {r.racy_cells} racy cells, the closed form gives {exp}")
+        racy += r.verdict
+    return racy
 
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    b.build()
-    rc.load()
+
+def batch_measure(args, rc, w, torch, rank, world, dist, steps, pm_steps, compact=False):
+    """Config 4: 10,000 small models checked as one batch (CUDA graph replay),
+    against one check per model on one stream."""
+    from paper_2503_08946_gb300 import distributed as D
     models = w.batch_models(args.batch_models, seed0=args.seed * 1000003 + rank * 100003)
     handles = [rc.rc_model_create(m) for m in models]
     opts = {"digit_bits": args.digit_bits, "flags": rc.binding.RC_OPT_GRAPH}   # captured once, replayed
@@ -432,14 +473,14 @@ def run_batch(args):
         out += [rc.rc_report(t)[0] for t in window]
         return out
 
-    def timed(fn, steps):
+    def timed(fn, n):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         ev0.record(stream)
-        for _ in range(steps):
+        for _ in range(n):
             r = fn()
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -453,10 +494,12 @@ def run_batch(args):
 
     for _ in range(max(3, args.warmup)):
         res = batched()
+    racy_models = batch_closed_form(models, res)
     inst = sum(r.instances for r in res)
-    sampler = ClockSampler(gpu_index(local))
-    time.sleep(0.25)
-    # device throughput: the K batches are enqueued back to back (each one graph
+    sampler = ClockSampler(gpu_index(env_rank()[2])) if not compact else None
+    if sampler:
+        time.sleep(0.25)
+    # device throughput: the batches are enqueued back to back (each one graph
     # launch plus its result copy), so the host work of one overlaps the GPU work
     # of the previous; the results are decoded after the timed region
     torch.cuda.synchronize()
@@ -465,7 +508,7 @@ def run_batch(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     ev0.record(stream)
-    tickets = [rc.rc_check_batch(handles, opts, ws, stream) for _ in range(args.steps)]
+    tickets = [rc.rc_check_batch(handles, opts, ws, stream) for _ in range(steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -475,36 +518,62 @@ def run_batch(args):
             raise RuntimeError("batch check failed: " + rc.rc_status_str(int(arr["status"][arr["status"] != 0][0])))
     wall = time.perf_counter() - t0   # end to end: enqueue, device work, results as one record array
     res = rc.results_of(arr)
-    clocks = sampler.stop()
-    total_i, ms, value = D.weak_scaling_rate(inst * args.steps, ms, device="cuda")
-    total = inst * args.steps * world
+    batch_closed_form(models, res)
+    clocks = sampler.stop() if sampler else None
+    total_i, ms, value = D.weak_scaling_rate(inst * steps, ms, device="cuda")
+    total = inst * steps * world
 
     # one check per model on one stream, same workspace reused (sized for the largest model)
     pm = None
     if not args.no_per_model:
+        del ws
         ws1 = rc.workspace(max(rc.rc_workspace_size(h, opts) for h in handles))
         ref = per_model(ws1)
         same = all((a.status, a.instances, a.verdict, a.racy_cells, a.witness) ==
                    (b_.status, b_.instances, b_.verdict, b_.racy_cells, b_.witness) for a, b_ in zip(res, ref))
-        pm_steps = max(1, min(3, args.steps))
         _, pm_ms, pm_wall = timed(lambda: per_model(ws1), pm_steps)
         pm_value = inst * pm_steps * world / (pm_ms / 1e3) / 1e9
         pm = {"value": pm_value, "unit": UNIT, "ms_per_step": pm_ms / pm_steps, "steps": pm_steps,
               "results_identical": same}
+    out = {
+        "value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+        "config": {"workload": BATCH_WORKLOAD, "models": len(models), "instances_per_rank": inst,
+                   "racy_models": racy_models, "results_checked": "every model against the generator's closed form",
+                   "cuda_graph": True, "l2": "key buffers larger than L2",
+                   "parallelism": f"independent batches per rank x{world}"},
+        "per_model": pm,
+        "speedup_vs_per_model": (value / pm["value"]) if pm else None,
+        "e2e": {"value": total / wall / 1e9, "unit": UNIT, "h2d_bytes_per_step": 80 * len(models),
+                "d2h_bytes_per_step": 136 * len(models)},
+    }
+    if clocks is not None:
+        out["clocks"] = clocks
+    for h in handles:
+        h.close()
+    return out
+
+
+def run_batch(args):
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+    m = batch_measure(args, rc, w, torch, rank, world, dist, steps=args.steps, pm_steps=max(1, min(3, args.steps)))
     if rank == 0:
-        line = {
-            "metric": METRIC + ", batched", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "models": len(models), "instances_per_rank": inst,
-                       "racy_models": sum(1 for r in res if r.verdict), "cuda_graph": True,
-                       "l2": "key buffers larger than L2", "parallelism": f"independent batches per rank x{world}"},
-            "per_model": pm,
-            "speedup_vs_per_model": (value / pm["value"]) if pm else None,
-            "e2e": {"value": total / wall / 1e9, "unit": UNIT, "h2d_bytes_per_step": 80 * len(models),
-                    "d2h_bytes_per_step": 136 * len(models)},
-            "clocks": clocks,
-        }
+        line = {"metric": METRIC + ", batched", "value": m["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": m["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic"}
+        line.update({k: v for k, v in m.items() if k not in line})
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -519,22 +588,12 @@ SERVE_WORKLOAD = ("Poisson arrivals at {rate:g} req/s of seeded random models (t
                   "workspace pool and {slots} stream slots")
 
 
-def run_serve(args):
+def serve_measure(args, rc, w, torch, rank, world, dist, n_requests, compact=False):
+    """Config 5: a Poisson request stream through the continuous-batching server
+    (latency percentiles, sustained rate), then the same requests at once
+    (capacity); every result checked against the generator's closed form."""
     import threading
-    import torch
-    import workloads as w
-    import paper_2503_08946_gb300 as rc
-    from paper_2503_08946_gb300 import build as b
-
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    b.build()
-    rc.load()
-    stream = w.request_stream(args.requests, rate_hz=args.rate, seed=args.seed + rank)
+    stream = w.request_stream(n_requests, rate_hz=args.rate, seed=args.seed + rank)
     handles = [rc.rc_model_create(m) for _, m in stream]
     srv = rc.RcServer(memory_bytes=args.pool_gb << 30, slots=args.slots)
 
@@ -552,8 +611,9 @@ def run_serve(args):
     drain(len(warm))
     if dist:
         dist.barrier()
-    sampler = ClockSampler(gpu_index(local))
-    time.sleep(0.25)
+    sampler = ClockSampler(gpu_index(env_rank()[2])) if not compact else None
+    if sampler:
+        time.sleep(0.25)
     ids = [None] * len(handles)
 
     def submitter():
@@ -568,11 +628,12 @@ def run_serve(args):
     th.start()
     got = drain(len(handles))
     th.join()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     recs = [got[i] for i in ids]
     bad = [r for r in recs if r.result.status != rc.RC_OK]
     if bad:
         raise RuntimeError(f"request failed: {rc.rc_status_str(bad[0].result.status)}")
+    batch_closed_form([m for _, m in stream], [r.result for r in recs])
     # capacity: the same requests submitted at once (offered load far above capacity)
     burst_ids = [srv.submit(h) for h in handles]
     burst = drain(len(burst_ids))
@@ -599,27 +660,86 @@ def run_serve(args):
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         value = float(tot[0]) / float(mx[1]) / 1e9
     srv.close()
+    for h in handles:
+        h.close()
+    sizes = [r.batch_size for r in recs]
+    out = {
+        "value": value, "unit": UNIT, "steps": len(recs), "warmup": len(warm), "ms_per_step": span * 1e3 / len(recs),
+        "config": {"workload": SERVE_WORKLOAD.format(rate=args.rate, mem=args.pool_gb, slots=args.slots),
+                   "requests": len(recs), "instances": inst,
+                   "offered_rate_hz": args.rate, "achieved_rate_hz": len(recs) / span,
+                   "results_checked": "every request against the generator's closed form",
+                   "l2": "requests are small; pool reused", "parallelism": f"independent streams per rank x{world}"},
+        "latency_ms": {"p50": q(0.50), "p90": q(0.90), "p99": q(0.99), "max": lat[-1],
+                       "mean": sum(lat) / len(lat)},
+        "batch_size": {"mean": sum(sizes) / len(sizes), "max": max(sizes)},
+        "capacity": capacity,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 96, "d2h_bytes_per_step": 160},
+    }
+    if clocks is not None:
+        out["clocks"] = clocks
+    return out
+
+
+def run_serve(args):
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    b.build()
+    rc.load()
+    m = serve_measure(args, rc, w, torch, rank, world, dist, n_requests=args.requests)
     if rank == 0:
-        sizes = [r.batch_size for r in recs]
-        line = {
-            "metric": METRIC + ", served", "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": len(recs), "warmup": len(warm), "ms_per_step": span * 1e3 / len(recs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": SERVE_WORKLOAD.format(rate=args.rate, mem=args.pool_gb, slots=args.slots),
-                       "requests": len(recs), "instances": inst,
-                       "offered_rate_hz": args.rate, "achieved_rate_hz": len(recs) / span,
-                       "l2": "requests are small; pool reused", "parallelism": f"independent streams per rank x{world}"},
-            "latency_ms": {"p50": q(0.50), "p90": q(0.90), "p99": q(0.99), "max": lat[-1],
-                           "mean": sum(lat) / len(lat)},
-            "batch_size": {"mean": sum(sizes) / len(sizes), "max": max(sizes)},
-            "capacity": capacity,
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 96, "d2h_bytes_per_step": 160},
-            "clocks": clocks,
-        }
+        line = {"metric": METRIC + ", served", "value": m["value"], "unit": UNIT, "n_gpus": world,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic"}
+        line.update({k: v for k, v in m.items() if k not in line})
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the hash path (K5) on the benchmark model
+# ---------------------------------------------------------------------------
+def hash_measure(rc, h, model, expect_racy, stream, steps):
+    """The hash path (fused expansion into global group / cell tables) on the
+    benchmark model, without early exit (full count); bytes per instance: the
+    8-byte key and one 8-byte table word read and written at least once each."""
+    import torch
+    opts = {"path": rc.RC_PATH_HASH, "early_exit": 0}
+    ws = rc.workspace(rc.rc_workspace_size(h, opts))
+    r = None
+    for _ in range(1):
+        r = rc.rc_report(rc.rc_check(h, opts, ws, stream))[0]
+    if r.status != rc.RC_OK or r.racy_cells != expect_racy:
+        raise RuntimeError(f"hash path gave {r}")
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        r = rc.rc_report(rc.rc_check(h, opts, ws, stream))[0]
+        if r.status != rc.RC_OK or r.racy_cells != expect_racy:
+            raise RuntimeError(f"hash path gave {r}")
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    del ws
+    n = r.instances
+    peak, kind = load_peaks()
+    return {"value": n / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "racy_cells": r.racy_cells, "early_exit": False,
+            "roofline": {"bound": "hbm", "kernel": "hash_expand_kernel", "alg_bytes_per_instance": 16,
+                         "achieved": 16.0 * n / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": 16.0 * n / (ms / 1e3) / 1e9 / peak, "peak_source": f"{kind} hbm_gbs"}}
 
 
 def main():
@@ -634,6 +754,8 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload: skip the hash, batch and serve sub-records")
     ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve", "wide"],
                     help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models; "
                          "serve: Poisson request stream through the request server")

@@ -63,6 +63,8 @@ def _load():
             lib.oracle_check.restype = ctypes.c_int
             lib.oracle_check_cells.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_int64, p64]
             lib.oracle_check_cells.restype = ctypes.c_int
+            lib.oracle_check_parallel.argtypes = [ctypes.c_char_p, ctypes.c_int, p64]
+            lib.oracle_check_parallel.restype = ctypes.c_int
             lib.oracle_cell_count.argtypes = [ctypes.c_char_p]
             lib.oracle_cell_count.restype = ctypes.c_int64
             lib.oracle_brute.argtypes = [ctypes.c_char_p, p64]
@@ -201,6 +203,16 @@ def check_cells(m, lo: int, hi: int) -> OracleResult:
     lib = _load()
     buf = (ctypes.c_int64 * len(FIELDS))()
     lib.oracle_check_cells(model_text(m).encode(), int(lo), int(hi), buf)
+    return _result(buf)
+
+
+def check_parallel(m, n_threads: Optional[int] = None) -> OracleResult:
+    """The full check on ``n_threads`` host threads (default: every core):
+    equal cell ranges checked concurrently and merged (counts add up, the
+    lowest racy range gives the witness)."""
+    n = int(n_threads or os.cpu_count() or 1)
+    buf = (ctypes.c_int64 * len(FIELDS))()
+    _load().oracle_check_parallel(model_text(m).encode(), n, buf)
     return _result(buf)
 
 

@@ -79,6 +79,7 @@
 #include <set>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -689,6 +690,69 @@ int oracle_check_cells(const char* text, int64_t lo, int64_t hi, int64_t* out) {
     CellRange r;
     r.all = false; r.lo = lo; r.hi = hi;
     return check_model(m, r, out);
+  } catch (const std::exception&) {
+    clear(out);
+    out[F_STATUS] = ST_INVALID;
+    return ST_INVALID;
+  }
+}
+
+// The same check as oracle_check on n_threads host threads (std::thread): the
+// linear cells are cut into n_threads ranges of equal length, each thread runs
+// the cell-range check of its range (every thread enumerates the whole model
+// and keeps the instances of its own cells), and the partial results merge by
+// the decomposition the cell-range check is pinned to: racy cells and distinct
+// instances add up (a cell races or not on its own), and the witness is that of
+// the lowest range that holds a racy cell (ranges ascend in cell order).
+int oracle_check_parallel(const char* text, int n_threads, int64_t* out) {
+  try {
+    Parser p(text);
+    Model m = p.model();
+    if (n_threads < 1) n_threads = 1;
+    Enumerator en(m, CellRange{});
+    const int64_t nblocks = m.grid[0] * m.grid[1] * m.grid[2];
+    int64_t total = 0;
+    if (!m.arrays.empty()) {
+      const size_t last = m.arrays.size() - 1;
+      total = en.cell_base[last] + en.cell_size[last] * (m.arrays[last].shared ? nblocks : 1);
+    }
+    std::vector<std::vector<int64_t>> part(n_threads, std::vector<int64_t>(F_COUNT, 0));
+    std::vector<int> status(n_threads, ST_OK);
+    std::vector<std::thread> pool;
+    const int64_t per = (total + n_threads - 1) / n_threads;
+    for (int k = 0; k < n_threads; ++k)
+      pool.emplace_back([&, k] {
+        try {
+          CellRange r;
+          r.all = false;
+          r.lo = std::min(total, (int64_t)k * per);
+          r.hi = std::min(total, r.lo + per);
+          status[k] = check_model(m, r, part[k].data());
+        } catch (const std::exception&) {
+          status[k] = ST_INVALID;
+        }
+      });
+    for (std::thread& t : pool) t.join();
+    clear(out);
+    for (int k = 0; k < n_threads; ++k)
+      if (status[k] != ST_OK) {
+        for (int f = 0; f < F_COUNT; ++f) out[f] = part[k][f];
+        out[F_STATUS] = status[k];
+        return status[k];
+      }
+    out[F_INSTANCES] = part[0][F_INSTANCES];
+    bool have = false;
+    for (int k = 0; k < n_threads; ++k) {
+      out[F_RACY_CELLS] += part[k][F_RACY_CELLS];
+      out[F_DISTINCT] += part[k][F_DISTINCT];
+      if (!have && part[k][F_RACY_CELLS] > 0) {
+        for (int f = F_W_ARRAY; f < F_COUNT; ++f) out[f] = part[k][f];
+        have = true;
+      }
+    }
+    out[F_VERDICT] = out[F_RACY_CELLS] > 0;
+    out[F_STATUS] = ST_OK;
+    return ST_OK;
   } catch (const std::exception&) {
     clear(out);
     out[F_STATUS] = ST_INVALID;

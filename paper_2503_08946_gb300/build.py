@@ -19,7 +19,8 @@ LIB = os.path.join(BUILD, "librc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 CUDA_INCLUDE = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
-CUDA_SOURCES = ["expand.cu", "sort.cu", "histogram.cu", "scan.cu", "runtime.cu", "sort_static.cu", "hash.cu", "batch.cu"]
+CUDA_SOURCES = ["expand.cu", "sort.cu", "histogram.cu", "scan.cu", "bucket.cu", "runtime.cu", "sort_static.cu", "hash.cu",
+                "batch.cu"]
 HOST_SOURCES = ["lower.cpp", "jit.cpp", "server.cpp"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -1,0 +1,702 @@
+// The bucket path of the grouping step: the keys are grouped by cell without a
+// stable sort.
+//
+// The scan of a race check needs the keys of each cell together, in any order
+// (its per-cell fold keeps per-barrier-interval masks, so the order of phases,
+// blocks and threads inside a cell does not matter).  The cell field is mapped
+// by the bijection h(c) = c * kCellHashMul mod 2^cb (an odd multiplier is
+// invertible modulo a power of two), which spreads any set of cells evenly over
+// the top bits of h, and the keys are moved by their top bits of h:
+//   pass A  partition of all keys by the top dA bits of h (padding keys of
+//           guard-false slots dropped); tiles claim their output ranges per
+//           digit with one atomic add each on per-digit cursors: no look-back;
+//   pass B  partition of every A-bucket by the next dB bits, tiles lying inside
+//           one A-bucket;
+//   fold    every bucket (top D = dA + dB bits of h: all keys of its cells, on
+//           average kBucketTarget) is counting-sorted by the remaining bits of
+//           h in shared memory and folded cell by cell (fold.cuh), one thread
+//           per cell, the whole block for cells of more than kSmallCell keys.
+// A bucket larger than shared memory is counting-sorted into the other key
+// buffer (free at that point) and folded from there.  The smallest racy cell is
+// kept by value (DevResult.hash_cell); bucket_finish points the witness kernels
+// at its bucket, whose keys they filter by cell.
+#include <cuda_runtime.h>
+
+#include "fold.cuh"
+#include "kernels.h"
+
+namespace rc {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t cell_hash_of(uint64_t cell, uint64_t cmask) {
+  return (cell * kCellHashMul) & cmask;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned int d = static_cast<unsigned int>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the A-bucket d of tile t: tpref ascending, tpref[d] <= t < tpref[d + 1]
+__device__ __forceinline__ uint32_t tile_bucket(const unsigned long long* tpref, uint32_t nd, uint64_t t) {
+  uint32_t lo = 0, hi = nd;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tpref[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// pass-A histogram: valid keys per top-dA-bit digit of h
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bucket_hist_a_kernel(BucketArgs a) {
+  __shared__ unsigned h[1 << kBucketMaxDigitBits];
+  const unsigned nd = 1u << a.dA;
+  const uint32_t sh = a.cb - a.dA;
+  for (unsigned i = threadIdx.x; i < nd; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  auto count = [&](uint64_t k) {
+    if (k != kSentinel) atomicAdd(&h[(unsigned)(cell_hash_of(k >> a.cell_shift, a.cmask) >> sh)], 1u);
+  };
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if ((reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u) {
+    const uint64_t np = a.n / 2;
+    const ulonglong2* kp = reinterpret_cast<const ulonglong2*>(a.keys_in);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < np; i += stride) {
+      const ulonglong2 k = __ldg(kp + i);
+      count(k.x);
+      count(k.y);
+    }
+    if ((a.n & 1u) && blockIdx.x == 0 && threadIdx.x == 0) count(__ldg(a.keys_in + a.n - 1));
+  } else {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += stride) count(__ldg(a.keys_in + i));
+  }
+  __syncthreads();
+  for (unsigned d = threadIdx.x; d < nd; d += blockDim.x)
+    if (h[d]) atomicAdd(&a.hist_a[d], (unsigned long long)h[d]);
+}
+
+// Exclusive scan by 1024 threads of one value per thread (block-wide); returns
+// the thread's exclusive prefix and sets *total.
+__device__ __forceinline__ unsigned long long block_excl_1024(unsigned long long v, unsigned long long* total) {
+  __shared__ unsigned long long wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long s = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s;   // inclusive over warps
+  }
+  __syncthreads();
+  const unsigned long long before = w ? wsum[w - 1] : 0ull;
+  *total = wsum[31];
+  __syncthreads();
+  return before + x - v;
+}
+
+// A-bucket offsets and cursors, the tile prefixes of pass B and of its
+// histogram, and (one partition pass) the bucket offsets of the fold
+__global__ void __launch_bounds__(1024) bucket_scan_a_kernel(BucketArgs a) {
+  const unsigned nd = 1u << a.dA;
+  const unsigned d = threadIdx.x;
+  const unsigned long long c = d < nd ? a.hist_a[d] : 0ull;
+  const unsigned long long tb = (c + kPartTileHost - 1) / kPartTileHost;
+  const unsigned long long th = (c + kBucketHistTile - 1) / kBucketHistTile;
+  unsigned long long tot_c, tot_b, tot_h;
+  const unsigned long long ec = block_excl_1024(c, &tot_c);
+  const unsigned long long eb = block_excl_1024(tb, &tot_b);
+  const unsigned long long eh = block_excl_1024(th, &tot_h);
+  if (d < nd) {
+    a.off_a[d] = ec;
+    a.cur_a[d] = ec;
+    a.tpref_b[d] = eb;
+    a.tpref_h[d] = eh;
+    if (a.dB == 0) a.boff[d] = ec;
+  }
+  if (d == 0) {
+    a.off_a[nd] = tot_c;
+    a.tpref_b[nd] = tot_b;
+    a.tpref_h[nd] = tot_h;
+    if (a.dB == 0) a.boff[nd] = tot_c;
+  }
+}
+
+__global__ void bucket_whole_kernel(unsigned long long* boff, uint64_t n) {
+  boff[0] = 0;
+  boff[1] = n;
+}
+
+// ---------------------------------------------------------------------------
+// partition passes (unstable: equal digits in any order).  Per tile of
+// kPTile keys: ranks from one shared atomic per key (one per warp when the
+// warp holds one digit), per-digit output ranges claimed from the cursors,
+// keys staged in digit order in shared memory, then stored so that the keys
+// of one digit go to consecutive addresses.
+//   B = false: pass A over all keys (tile t = keys [t * kPTile, ...)), digit =
+//              top dA bits of h, padding keys dropped;
+//   B = true:  pass B, tiles inside one A-bucket (tpref_b), digit = next dB
+//              bits, cursors of that A-bucket's buckets.
+// ---------------------------------------------------------------------------
+constexpr int kPThreads = kSortThreads;
+constexpr int kPItems = 12;
+constexpr int kPTile = kPThreads * kPItems;
+static_assert(kPTile == kPartTileHost, "pass-B tiles are planned with the host's tile size");
+
+template <int RB>
+constexpr size_t bpart_smem() {
+  return (size_t)kPTile * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
+}
+
+template <int RB, bool B>
+__global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketArgs a) {
+  constexpr int R = 1 << RB;
+  constexpr int DPT = (R + kPThreads - 1) / kPThreads;
+  constexpr int kWarps = kPThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kPTile);           // [R]
+  unsigned int* excl = cnt + R;                                                     // [R]
+  unsigned long long* delta = reinterpret_cast<unsigned long long*>(excl + R);      // [R]
+  __shared__ unsigned int s_wt[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+
+  // tile geometry (block-uniform)
+  uint64_t t0, len;
+  unsigned long long* cursor;
+  uint32_t sh, dbits;
+  if (!B) {
+    t0 = (uint64_t)blockIdx.x * kPTile;
+    if (t0 >= a.n) return;
+    len = min((uint64_t)kPTile, a.n - t0);
+    cursor = a.cur_a;
+    sh = a.cb - a.dA;
+    dbits = a.dA;
+  } else {
+    const unsigned nd = 1u << a.dA;
+    const uint64_t t = blockIdx.x;
+    if (t >= a.tpref_b[nd]) return;
+    const uint32_t d1 = tile_bucket(a.tpref_b, nd, t);
+    t0 = a.off_a[d1] + (t - a.tpref_b[d1]) * kPTile;
+    len = min((uint64_t)kPTile, (uint64_t)(a.off_a[d1 + 1] - t0));
+    cursor = a.cur_b + ((uint64_t)d1 << a.dB);
+    sh = a.cb - a.dA - a.dB;
+    dbits = a.dB;
+  }
+  const unsigned dmask = (1u << dbits) - 1u;
+  auto digit = [&](uint64_t k) { return (unsigned)(cell_hash_of(k >> a.cell_shift, a.cmask) >> sh) & dmask; };
+
+  for (int i = threadIdx.x; i < R; i += kPThreads) cnt[i] = 0;
+  // the tile into shared memory: 16-byte copies for a full tile at an even
+  // key position of a 16-byte aligned buffer, else 8-byte copies
+  const bool full = len == (uint64_t)kPTile;
+  if (full && (t0 & 1u) == 0u && (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u) {
+#pragma unroll
+    for (int m = 0; m < kPTile / 2 / kPThreads; ++m) {
+      const int j = m * kPThreads + (int)threadIdx.x;
+      cp_async16(s_keys + 2 * j, a.keys_in + t0 + 2 * j);
+    }
+  } else {
+    for (int j = threadIdx.x; j < (int)len; j += kPThreads) cp_async8(s_keys + j, a.keys_in + t0 + j);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const int lpos = w * (32 * kPItems) + lane;
+  unsigned short r[kPItems];
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    const int j = lpos + i * 32;
+    const uint64_t k = j < (int)len ? s_keys[j] : kSentinel;
+    const bool valid = j < (int)len && (B || k != kSentinel);
+    const unsigned d = valid ? digit(k) : 0u;
+    const unsigned d0 = __shfl_sync(FULL, d, 0);
+    unsigned rank = 0;
+    if (__all_sync(FULL, valid && d == d0)) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(&cnt[d0], 32u);
+      rank = __shfl_sync(FULL, base, 0) + (unsigned)lane;
+    } else if (valid) {
+      rank = atomicAdd(&cnt[d], 1u);
+    }
+    r[i] = (unsigned short)rank;
+  }
+  __syncthreads();
+  // per digit: claim the output range, tile offsets
+  unsigned carry = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int dg = q * kPThreads + threadIdx.x;
+    const unsigned c = dg < R ? cnt[dg] : 0u;
+    const unsigned long long claim = c ? atomicAdd(&cursor[dg], (unsigned long long)c) : 0ull;
+    unsigned x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wt[w] = x;
+    __syncthreads();
+    unsigned base = carry, tot = 0;
+    for (int i = 0; i < kWarps; ++i) {
+      if (i < w) base += s_wt[i];
+      tot += s_wt[i];
+    }
+    __syncthreads();
+    if (dg < R) {
+      const unsigned e = base + x - c;
+      excl[dg] = e;
+      delta[dg] = claim - e;
+    }
+    carry += tot;
+  }
+  __syncthreads();
+  uint64_t kk[kPItems];
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    const int j = lpos + i * 32;
+    kk[i] = j < (int)len ? s_keys[j] : kSentinel;
+  }
+  __syncthreads();   // every key read before any is overwritten
+#pragma unroll
+  for (int i = 0; i < kPItems; ++i) {
+    const int j = lpos + i * 32;
+    if (j < (int)len && (B || kk[i] != kSentinel)) s_keys[excl[digit(kk[i])] + r[i]] = kk[i];
+  }
+  __syncthreads();
+  // carry = valid keys of the tile
+  for (int pos = threadIdx.x; pos < (int)carry; pos += kPThreads) {
+    const uint64_t key = s_keys[pos];
+    const unsigned long long dst = delta[digit(key)] + (unsigned long long)pos;
+    // in range whenever the histogram and the ranks agree (see sort.cu)
+    if (dst < a.n) a.keys_out[dst] = key;
+    else atomicOr(a.err, (unsigned int)kErrSortRange);
+  }
+}
+
+template <int RB, bool B>
+cudaError_t launch_bpart_rb(const BucketArgs& a, uint64_t grid, cudaStream_t st) {
+  constexpr size_t smem = bpart_smem<RB>();
+  const cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void*>(bucket_partition_kernel<RB, B>), smem);
+  if (e != cudaSuccess) return e;
+  bucket_partition_kernel<RB, B><<<(unsigned)grid, kPThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool B>
+cudaError_t launch_bpart(const BucketArgs& a, uint32_t bits, uint64_t grid, cudaStream_t st) {
+  if (grid == 0) return cudaSuccess;
+  if (grid > 0x7fffffffull) return cudaErrorInvalidValue;
+  if (bits <= 7) return launch_bpart_rb<7, B>(a, grid, st);
+  if (bits == 8) return launch_bpart_rb<8, B>(a, grid, st);
+  if (bits == 9) return launch_bpart_rb<9, B>(a, grid, st);
+  if (bits == 10) return launch_bpart_rb<10, B>(a, grid, st);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// pass-B histogram: keys per (A-bucket, next dB bits), tiles inside A-buckets
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
+  __shared__ unsigned h[1 << kBucketMaxDigitBits];
+  const unsigned nd = 1u << a.dA, nb = 1u << a.dB;
+  const uint64_t t = blockIdx.x;
+  if (t >= a.tpref_h[nd]) return;
+  const uint32_t d1 = tile_bucket(a.tpref_h, nd, t);
+  const uint64_t s = a.off_a[d1] + (t - a.tpref_h[d1]) * kBucketHistTile;
+  const uint64_t e = min(s + kBucketHistTile, (uint64_t)a.off_a[d1 + 1]);
+  const uint32_t sh = a.cb - a.dA - a.dB;
+  for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+    const uint64_t k = __ldg(a.keys_in + i);
+    atomicAdd(&h[(unsigned)(cell_hash_of(k >> a.cell_shift, a.cmask) >> sh) & (nb - 1u)], 1u);
+  }
+  __syncthreads();
+  for (unsigned d = threadIdx.x; d < nb; d += blockDim.x)
+    if (h[d]) atomicAdd(&a.hist_b[((uint64_t)d1 << a.dB) | d], (unsigned long long)h[d]);
+}
+
+// ---------------------------------------------------------------------------
+// fold
+// ---------------------------------------------------------------------------
+constexpr int kFoldThreads = 512;
+constexpr int kSmallCell = 256;   // bins with more keys are folded by the whole block
+constexpr int kBigCap = 64;       // such bins per bucket listed in shared memory (more: folded by one thread)
+constexpr int kGrab = 4;          // bins a thread takes per grab
+
+size_t fold_smem(uint32_t rbin) {
+  return (size_t)kFoldCap * 8 + ((size_t)4 << rbin) + (size_t)kTabPhases * kFoldThreads * 4;
+}
+
+// exclusive scan in place of n (a multiple of kFoldThreads, or less) counters
+__device__ __forceinline__ void fold_bin_scan(unsigned* bin, unsigned n) {
+  __shared__ unsigned wsum[kFoldThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned per = (n + kFoldThreads - 1) / kFoldThreads;
+  const unsigned b0 = threadIdx.x * per;
+  unsigned s = 0;
+  for (unsigned i = 0; i < per; ++i)
+    if (b0 + i < n) s += bin[b0 + i];
+  unsigned x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  unsigned base = 0;
+  for (int i = 0; i < w; ++i) base += wsum[i];
+  unsigned run = base + x - s;
+  for (unsigned i = 0; i < per; ++i)
+    if (b0 + i < n) {
+      const unsigned c = bin[b0 + i];
+      bin[b0 + i] = run;
+      run += c;
+    }
+}
+
+template <bool AT, bool SY>
+__global__ void __launch_bounds__(kFoldThreads, 2) bucket_fold_kernel(FoldArgs fa) {
+  const ScanArgs& a = fa.s;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
+  unsigned* s_bin = reinterpret_cast<unsigned*>(s_keys + kFoldCap);
+  unsigned* my_tab = s_bin + (1u << fa.rbin) + threadIdx.x;   // interval q at my_tab[q * kFoldThreads]
+  __shared__ unsigned s_big[kBigCap];
+  __shared__ unsigned s_nbig, s_next;
+  // whole-block fold of one cell (per interval (block, thread) extremes)
+  __shared__ unsigned bmn[kTabPhases], bmx[kTabPhases];
+  __shared__ unsigned bgw, bga, bgr, bminb, bmaxb, bw;
+  __shared__ unsigned long long s_cell;
+  __shared__ unsigned long long s_red[kFoldThreads / 32];
+
+  const uint32_t cs = a.cell_shift, ps = a.phase_shift, tb = a.thread_bits;
+  const uint32_t kb = a.thread_shift;
+  const unsigned pm = (1u << a.phase_bits) - 1u;
+  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  const unsigned nbins = 1u << fa.rbin;
+  const uint32_t bin_shift = fa.r - fa.rbin;
+  const bool multi = fa.rbin < fa.r;   // a bin may hold several cells
+  const uint64_t nb = 1ull << fa.D;
+  const int tid = threadIdx.x;
+  SyncTabs syt;
+  if constexpr (SY) syt = sync_tabs_of(a);
+  unsigned long long count = 0, minc = ~0ull;
+  using TF = typename FoldOf<SY>::type;
+
+  auto bin_of = [&](uint64_t k) -> unsigned {
+    return (unsigned)(cell_hash_of(k >> cs, fa.cmask) >> bin_shift) & (nbins - 1u);
+  };
+  auto record = [&](uint64_t cell) {
+    if (a.n_models) {
+      DevResult* r = result_of(a, cell);
+      atomicAdd(&r->racy_cells, 1ull);
+      atomicMin(&r->hash_cell, (unsigned long long)cell);
+    } else {
+      ++count;
+      minc = cell < minc ? cell : minc;
+    }
+  };
+  // one thread: the cells of keys dst[s, e), each cell contiguous
+  auto fold_runs = [&](const uint64_t* dst, unsigned s, unsigned e) {
+    unsigned i = s;
+    while (i < e) {
+      const uint64_t k0 = dst[i];
+      const uint64_t c = k0 >> cs;
+      TF x;
+      tfold_clear(x);
+      x.fk = k0;
+      x.bt0 = (unsigned)(k0 >> kb) & btm;
+      unsigned j = i;
+      do {
+        const uint64_t k = dst[j];
+        const unsigned bt = (unsigned)(k >> kb) & btm;
+        const unsigned ph = (unsigned)(k >> ps) & pm;
+        const unsigned bit = 1u << ph;
+        if (!(x.vmask & bit)) {
+          my_tab[ph * kFoldThreads] = bt;
+          x.vmask |= bit;
+        } else {
+          const unsigned old = my_tab[ph * kFoldThreads];
+          if (old != bt) {
+            x.gm |= bit;
+            if constexpr (SY) mark_pair(old, bt, bit, tb, x.gmb, x.gmw);
+          }
+        }
+        x.gw |= (unsigned)(k & 1ull) << ph;
+        if (((bt ^ x.bt0) >> tb) != 0u) x.f |= kTMB;
+        if (AT) {
+          if (k & 2ull) x.ga |= bit;
+          if ((k & 3ull) == 0ull) x.gr |= bit;
+        }
+        ++j;
+      } while (j < e && (dst[j] >> cs) == c);
+      bool racy;
+      if constexpr (SY) {
+        const SyncTabs mt = a.n_models ? sync_tabs_of(a, model_of(a, c)) : syt;
+        racy = tfold_racy_sync<AT, kFoldThreads>(x, my_tab, mt.coarse, mt.grid, tb);
+      } else {
+        racy = tfold_racy<AT>(x);
+      }
+      if (racy) record(c);
+      i = j;
+    }
+  };
+  // the whole block: the keys of cell `c` among dst[s, e)
+  auto block_fold_cell = [&](const uint64_t* dst, unsigned s, unsigned e, uint64_t c) {
+    if (tid < kTabPhases) {
+      bmn[tid] = 0xffffffffu;
+      bmx[tid] = 0;
+    }
+    if (tid == 0) {
+      bgw = bga = bgr = 0;
+      bminb = 0xffffffffu;
+      bmaxb = 0;
+      bw = 0;
+    }
+    __syncthreads();
+    for (unsigned i = s + tid; i < e; i += kFoldThreads) {
+      const uint64_t k = dst[i];
+      if ((k >> cs) != c) continue;
+      const unsigned bt = (unsigned)(k >> kb) & btm;
+      const unsigned ph = (unsigned)(k >> ps) & pm;
+      const unsigned kd = (unsigned)(k & ((1ull << kb) - 1ull));
+      atomicMin(&bmn[ph], bt);
+      atomicMax(&bmx[ph], bt);
+      atomicMin(&bminb, bt >> tb);
+      atomicMax(&bmaxb, bt >> tb);
+      if (kd == 1u) {
+        atomicOr(&bgw, 1u << ph);
+        bw = 1;
+      } else if (kd == 2u) {
+        atomicOr(&bga, 1u << ph);
+      } else {
+        atomicOr(&bgr, 1u << ph);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const SyncTabs mt = a.n_models ? sync_tabs_of(a, model_of(a, c)) : syt;
+      if (summary_racy(bmn, bmx, bgw, bga, bgr, bw != 0u, bminb, bmaxb, mt, tb)) record(c);
+    }
+    __syncthreads();
+  };
+  // the smallest cell above `above` among dst[s, e) (~0: none), block-wide
+  auto block_next_cell = [&](const uint64_t* dst, unsigned s, unsigned e, uint64_t above, bool first) {
+    unsigned long long m = ~0ull;
+    for (unsigned i = s + tid; i < e; i += kFoldThreads) {
+      const uint64_t c = dst[i] >> cs;
+      if ((first || c > above) && c < m) m = c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(FULL, m, o);
+      m = y < m ? y : m;
+    }
+    if ((tid & 31) == 0) s_red[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long t = ~0ull;
+      for (int i = 0; i < kFoldThreads / 32; ++i) t = s_red[i] < t ? s_red[i] : t;
+      s_cell = t;
+    }
+    __syncthreads();
+    const unsigned long long r = s_cell;
+    __syncthreads();
+    return r;
+  };
+
+  for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint64_t lo = fa.boff[b], hi = fa.boff[b + 1];
+    if (hi <= lo) continue;
+    const uint64_t len = hi - lo;
+    const bool in_smem = len <= (uint64_t)kFoldCap;
+    const uint64_t* src = a.keys + lo;
+    uint64_t* dst = in_smem ? s_keys : fa.scratch + lo;
+    for (unsigned i = tid; i < nbins; i += kFoldThreads) s_bin[i] = 0;
+    if (tid == 0) {
+      s_nbig = 0;
+      s_next = 0;
+    }
+    __syncthreads();
+    // counting sort by bin (padding keys skipped: the unpartitioned single bucket holds them)
+    for (uint64_t i = tid; i < len; i += kFoldThreads) {
+      const uint64_t k = src[i];
+      if (k != kSentinel) atomicAdd(&s_bin[bin_of(k)], 1u);
+    }
+    __syncthreads();
+    fold_bin_scan(s_bin, nbins);
+    __syncthreads();
+    for (uint64_t i = tid; i < len; i += kFoldThreads) {
+      const uint64_t k = src[i];
+      if (k != kSentinel) dst[atomicAdd(&s_bin[bin_of(k)], 1u)] = k;
+    }
+    __syncthreads();
+    // s_bin[g] is now the end of bin g; bins are taken kGrab at a time
+    while (true) {
+      unsigned g0 = 0;
+      g0 = atomicAdd(&s_next, (unsigned)kGrab);
+      if (g0 >= nbins) break;
+      const unsigned g1 = min(g0 + (unsigned)kGrab, nbins);
+      for (unsigned g = g0; g < g1; ++g) {
+        const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
+        if (e <= s) continue;
+        if (e - s > (unsigned)kSmallCell) {
+          const unsigned i = atomicAdd(&s_nbig, 1u);
+          if (i < (unsigned)kBigCap) {
+            s_big[i] = g;
+            continue;
+          }
+        }
+        if (multi && e - s > 1u) {
+          // several cells may share the bin: order it by cell (insertion sort)
+          for (unsigned i = s + 1; i < e; ++i) {
+            const uint64_t v = dst[i];
+            unsigned j = i;
+            while (j > s && (dst[j - 1] >> cs) > (v >> cs)) {
+              dst[j] = dst[j - 1];
+              --j;
+            }
+            dst[j] = v;
+          }
+        }
+        fold_runs(dst, s, e);
+      }
+    }
+    __syncthreads();
+    const unsigned nbig = min(s_nbig, (unsigned)kBigCap);
+    for (unsigned q = 0; q < nbig; ++q) {
+      const unsigned g = s_big[q];
+      const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
+      if (!multi) {
+        block_fold_cell(dst, s, e, dst[s] >> cs);
+      } else {
+        uint64_t c = block_next_cell(dst, s, e, 0, true);
+        while (c != ~0ull) {
+          block_fold_cell(dst, s, e, c);
+          c = block_next_cell(dst, s, e, c, false);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (a.n_models == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      count += __shfl_xor_sync(FULL, count, o);
+      const unsigned long long y = __shfl_xor_sync(FULL, minc, o);
+      minc = y < minc ? y : minc;
+    }
+    if ((tid & 31) == 0) {
+      if (count) atomicAdd(&a.res->racy_cells, count);
+      if (minc != ~0ull) atomicMin(&a.res->hash_cell, minc);
+    }
+  }
+}
+
+// one thread per result: the bucket of its smallest racy cell
+__global__ void bucket_finish_kernel(FoldArgs fa) {
+  const uint32_t nr = fa.s.n_models ? fa.s.n_models : 1u;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  DevResult* r = fa.s.res + i;
+  const unsigned long long c = r->hash_cell;
+  if (c == ~0ull) return;
+  const uint64_t b = fa.D ? (cell_hash_of(c, fa.cmask) >> (fa.cb - fa.D)) : 0ull;
+  r->min_start = fa.boff[b];
+  r->seg_end = fa.boff[b + 1];
+  r->cell = c;
+}
+
+}  // namespace
+
+cudaError_t launch_bucket_hist_a(const BucketArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  uint64_t g = (a.n / 2 + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 152ull * 8) g = 152ull * 8;
+  bucket_hist_a_kernel<<<(unsigned)g, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_scan_a(const BucketArgs& a, cudaStream_t st) {
+  bucket_scan_a_kernel<<<1, 1024, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_pass_a(const BucketArgs& a, cudaStream_t st) {
+  return launch_bpart<false>(a, a.dA, (a.n + kPTile - 1) / kPTile, st);
+}
+
+cudaError_t launch_bucket_hist_b(const BucketArgs& a, uint64_t tiles_h, cudaStream_t st) {
+  if (tiles_h == 0) return cudaSuccess;
+  if (tiles_h > 0x7fffffffull) return cudaErrorInvalidValue;
+  bucket_hist_b_kernel<<<(unsigned)tiles_h, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_scan_b(const BucketArgs& a, cudaStream_t st) {
+  const uint64_t nb = 1ull << (a.dA + a.dB);
+  cudaError_t e = scan_u64_exclusive(reinterpret_cast<const uint64_t*>(a.hist_b), reinterpret_cast<uint64_t*>(a.boff),
+                                     nb, 0, reinterpret_cast<uint64_t*>(a.temp),
+                                     reinterpret_cast<uint64_t*>(a.boff + nb), st);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(a.cur_b, a.boff, nb * 8, cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t launch_bucket_pass_b(const BucketArgs& a, uint64_t tiles_b, cudaStream_t st) {
+  return launch_bpart<true>(a, a.dB, tiles_b, st);
+}
+
+cudaError_t launch_bucket_whole(unsigned long long* boff, uint64_t n, cudaStream_t st) {
+  bucket_whole_kernel<<<1, 1, 0, st>>>(boff, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_fold(const FoldArgs& fa, cudaStream_t st) {
+  const size_t smem = fold_smem(fa.rbin);
+  const bool at = fa.s.thread_shift == 2, sy = fa.s.sync_tabs != nullptr;
+  const void* fn = at ? (sy ? reinterpret_cast<const void*>(bucket_fold_kernel<true, true>)
+                            : reinterpret_cast<const void*>(bucket_fold_kernel<true, false>))
+                      : (sy ? reinterpret_cast<const void*>(bucket_fold_kernel<false, true>)
+                            : reinterpret_cast<const void*>(bucket_fold_kernel<false, false>));
+  cudaError_t e = ensure_kernel_smem(fn, fold_smem(kFoldBinBits));
+  if (e != cudaSuccess) return e;
+  const uint64_t nb = 1ull << fa.D;
+  const unsigned grid = (unsigned)(nb < 152ull * 2 ? nb : 152ull * 2);
+  if (at && sy) bucket_fold_kernel<true, true><<<grid, kFoldThreads, smem, st>>>(fa);
+  else if (at) bucket_fold_kernel<true, false><<<grid, kFoldThreads, smem, st>>>(fa);
+  else if (sy) bucket_fold_kernel<false, true><<<grid, kFoldThreads, smem, st>>>(fa);
+  else bucket_fold_kernel<false, false><<<grid, kFoldThreads, smem, st>>>(fa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_finish(const FoldArgs& fa, cudaStream_t st) {
+  const uint32_t nr = fa.s.n_models ? fa.s.n_models : 1u;
+  bucket_finish_kernel<<<(nr + 127) / 128, 128, 0, st>>>(fa);
+  return cudaGetLastError();
+}
+
+}  // namespace rc

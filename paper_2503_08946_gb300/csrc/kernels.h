@@ -139,6 +139,63 @@ bool sort_stall_requested();
 // current device (looked up once per device)
 rc_status sort_static_record(const void** rec);
 
+// bucket.cu: the bucket path of the grouping step.  The cell field of a key is
+// mapped by the bijection h(cell) = cell * kCellHashMul mod 2^cb (cb = cell
+// bits); the keys are partitioned by the top dA bits of h (pass A, padding keys
+// dropped), then each A-bucket by the next dB bits (pass B), without look-back;
+// every resulting bucket (top D = dA + dB bits of h) holds all keys of its cells
+// and is grouped by cell and folded in shared memory (bucket_fold_kernel).
+constexpr uint64_t kCellHashMul = 0x9E3779B97F4A7C15ull;
+constexpr uint32_t kBucketMaxDigitBits = 10;        // per partition pass
+constexpr uint32_t kBucketMaxBits = 2 * kBucketMaxDigitBits;
+constexpr int kFoldCap = 8192;                      // keys of a bucket folded in shared memory
+constexpr uint32_t kFoldBinBits = 12;               // counting-sort bins of a bucket (at most)
+constexpr uint64_t kBucketTarget = kFoldCap / 2 + kFoldCap / 16;   // planned mean keys per bucket
+constexpr int kBucketHistTile = 16384;              // keys per block of the pass-B histogram
+constexpr int kPartTileHost = kSortThreads * 12;    // keys per tile of the partition passes
+
+struct BucketPlan {
+  bool on = false;
+  uint32_t cb = 0, dA = 0, dB = 0, D = 0, r = 0, rbin = 0;
+  uint64_t n = 0;                 // key slots (padding included)
+  uint64_t tiles_b = 0, tiles_h = 0;   // grid bounds of pass B and its histogram
+  // workspace offsets (bytes) of the bucket section
+  size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, hist_b = 0, boff = 0, cur_b = 0, temp = 0;
+  size_t zero_lo = 0, zero_hi = 0;    // cleared at the start of a check (the two histograms)
+  size_t end = 0;
+};
+// host (runtime.cu): whether the bucket path applies to n keys of cb cell bits
+// (at most 2^kBucketMaxBits buckets of about kBucketTarget keys), its digit
+// widths, and its workspace section laid out from byte offset `off`
+bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp);
+
+struct BucketArgs {
+  const uint64_t* keys_in;
+  uint64_t* keys_out;
+  uint64_t n;                       // keys of keys_in (pass A: padding included)
+  uint32_t cell_shift, cb;
+  uint64_t cmask;                   // 2^cb - 1
+  uint32_t dA, dB;
+  unsigned long long* hist_a;       // [2^dA] valid keys per A-bucket
+  unsigned long long* off_a;        // [2^dA + 1] A-bucket offsets (exclusive, then the total)
+  unsigned long long* cur_a;        // [2^dA] pass-A output cursors
+  unsigned long long* tpref_b;      // [2^dA + 1] pass-B tiles before each A-bucket
+  unsigned long long* tpref_h;      // [2^dA + 1] histogram tiles before each A-bucket
+  unsigned long long* hist_b;       // [2^D] keys per bucket
+  unsigned long long* boff;         // [2^D + 1] bucket offsets
+  unsigned long long* cur_b;        // [2^D] pass-B output cursors
+  unsigned long long* temp;         // scan scratch
+  unsigned int* err;
+};
+cudaError_t launch_bucket_hist_a(const BucketArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_scan_a(const BucketArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_pass_a(const BucketArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_hist_b(const BucketArgs& a, uint64_t tiles_h, cudaStream_t st);
+cudaError_t launch_bucket_scan_b(const BucketArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_pass_b(const BucketArgs& a, uint64_t tiles_b, cudaStream_t st);
+// D == 0: the single bucket [0, n) of the unpartitioned keys (padding included)
+cudaError_t launch_bucket_whole(unsigned long long* boff, uint64_t n, cudaStream_t st);
+
 // scan.cu
 constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)
 constexpr uint32_t kScanMaxWarps = 152 * 12 * 4;
@@ -176,6 +233,21 @@ struct SyncTabs {
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);
+// bucket.cu: the fold of the bucket path over s.keys (grouped by bucket:
+// bucket b = keys [boff[b], boff[b+1]), b < 2^D); `scratch` is the other key
+// buffer (buckets larger than kFoldCap are grouped there).  Counts racy cells
+// and keeps the smallest racy cell in DevResult.hash_cell (per model in a
+// batch); bucket_finish then sets [min_start, seg_end) to that cell's bucket
+// and `cell` to the cell, for the witness kernels.
+struct FoldArgs {
+  ScanArgs s;
+  const unsigned long long* boff;
+  uint64_t* scratch;
+  uint64_t cmask;
+  uint32_t cb, D, rbin, r;
+};
+cudaError_t launch_bucket_fold(const FoldArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_finish(const FoldArgs& a, cudaStream_t st);
 cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n = 1);
 uint64_t scan_long_capacity(uint64_t n, uint32_t n_warps);
 

@@ -49,6 +49,26 @@ def test_partial_checks_merge_to_whole(k):
         assert merged(m, k) == whole(m), m.name
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 16])
+def test_parallel_oracle_equals_whole_check(k):
+    """The all-cores oracle (cell ranges on std::thread workers) gives the full
+    result of the single-threaded check, witness and instance counts included."""
+    extra = [w.tiny_random_sync(s, block_guards=True) for s in range(0, 60, 7)] + \
+            [w.tiny_random(s, atomic=0.4) for s in range(5)] + [w.grid_late_partner(4, 3)]
+    for m in models() + extra:
+        a, b = oracle.check(m), oracle.check_parallel(m, k)
+        assert (a.status, a.instances, a.distinct, a.verdict, a.racy_cells, a.witness, a.x_wphase, a.y_wphase) == \
+               (b.status, b.instances, b.distinct, b.verdict, b.racy_cells, b.witness, b.x_wphase, b.y_wphase), m.name
+
+
+def test_parallel_oracle_reports_out_of_bounds():
+    from workloads.spec import Access, Array, Model, Stmt, tid, W
+    m = Model((2, 1, 1), (8, 1, 1), [Array("s", "shared", (4,))], [Stmt([Access(0, W, (tid.x,))])])
+    a, b = oracle.check(m), oracle.check_parallel(m, 3)
+    assert a.status == b.status == oracle.STATUS_OOB
+    assert (a.oob_stmt, a.oob_access, a.oob_gtid, a.oob_dim) == (b.oob_stmt, b.oob_access, b.oob_gtid, b.oob_dim)
+
+
 def test_merge_keeps_errors():
     from paper_2503_08946_gb300 import binding as B
     ok = B.Result(0, 1, 3, 10, 0, 0, 5, (0, 0, 1, 0), (0, 0, 2, 1), 0, 0, 0, 0)
