@@ -293,7 +293,15 @@ enum { RC_TEST_STALL_LOOKBACK = 1,
  * graph on later calls with the same arguments; rc_model_destroy drops the
  * captured graphs.  Not a library convenience of the paper: the paper has no
  * batching. */
-enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2, RC_OPT_CHUNKED = 4 };
+enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2, RC_OPT_CHUNKED = 4, RC_OPT_LSD = 8 };
+/* Grouping step of the sort path.  By default a check (or a batch pack) whose
+ * keys carry at most 16 barrier intervals groups its keys by cell with the
+ * bucket path: two look-back-free partition passes on the top bits of a
+ * bijective hash of the cell field, then per bucket a counting sort and the
+ * cell fold in shared memory; its result is identical to the ordered scan's.
+ * RC_OPT_LSD (or a non-zero digit_bits, or any test flag) selects the stable
+ * LSD radix sort followed by the ordered scan instead; models of more than 16
+ * intervals, chunked checks and rc_sort_keys always take that path. */
 
 typedef struct rc_inst {
   uint64_t block;          /* linear block index bx + gx*(by + gy*bz)             */
@@ -437,13 +445,17 @@ rc_status rc_report(rc_ticket ticket, rc_result* out, int wait);
  * Errors: RC_E_INVALID (no stage times were recorded), RC_E_CUDA. */
 typedef struct rc_stage_times {
   float expand_ms;         /* K1 expansion                                         */
-  float histogram_ms;      /* digit histograms + digit offsets                     */
-  float sort_ms[16];       /* K2 onesweep, one entry per pass                      */
+  float histogram_ms;      /* digit histograms + digit offsets (bucket path: the
+                              pass-A histogram and its offsets)                    */
+  float sort_ms[16];       /* K2, one entry per pass (bucket path: partition
+                              passes A and B)                                      */
   uint32_t n_sort_passes;
-  float scan_ms;           /* K3 scan + fold                                       */
+  float scan_ms;           /* K3 scan + fold (bucket path: the bucket fold)        */
   float witness_ms;        /* K4 witness                                           */
   float total_ms;          /* from the first to the last event                     */
   uint64_t n_keys;         /* keys sorted and scanned                              */
+  float histogram2_ms;     /* bucket path: the pass-B histogram and its offsets    */
+  uint32_t bucketed;       /* 1: bucket path, 0: LSD radix sort and ordered scan   */
 } rc_stage_times;
 rc_status rc_ticket_stage_times(rc_ticket ticket, rc_stage_times* out);
 

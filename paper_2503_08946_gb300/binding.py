@@ -41,6 +41,7 @@ RC_TEST_FEW_SCAN_WARPS = 2
 RC_OPT_STAGE_TIMES = 1
 RC_OPT_GRAPH = 2
 RC_OPT_CHUNKED = 4
+RC_OPT_LSD = 8
 
 # every entry point declared in include/rc.h
 EXPORTS = ["rc_status_str", "rc_get_limits", "rc_model_create", "rc_model_destroy", "rc_model_layout",
@@ -126,7 +127,8 @@ class rc_check_opts(Structure):
 class rc_stage_times(Structure):
     _fields_ = [("expand_ms", ctypes.c_float), ("histogram_ms", ctypes.c_float),
                 ("sort_ms", ctypes.c_float * 16), ("n_sort_passes", c_uint32), ("scan_ms", ctypes.c_float),
-                ("witness_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("n_keys", c_uint64)]
+                ("witness_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("n_keys", c_uint64),
+                ("histogram2_ms", ctypes.c_float), ("bucketed", c_uint32)]
 
 
 class rc_inst(Structure):
@@ -661,7 +663,8 @@ def rc_ticket_stage_times(ticket) -> dict:
         raise RcError(st, "rc_ticket_stage_times")
     return {"expand_ms": st_.expand_ms, "histogram_ms": st_.histogram_ms,
             "sort_ms": [st_.sort_ms[i] for i in range(st_.n_sort_passes)], "scan_ms": st_.scan_ms,
-            "witness_ms": st_.witness_ms, "total_ms": st_.total_ms, "n_keys": st_.n_keys}
+            "witness_ms": st_.witness_ms, "total_ms": st_.total_ms, "n_keys": st_.n_keys,
+            "histogram2_ms": st_.histogram2_ms, "bucketed": bool(st_.bucketed)}
 
 
 def rc_expand_keys(m: RcModel, workspace, keys, count, stream=None):

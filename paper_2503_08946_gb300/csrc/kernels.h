@@ -92,6 +92,7 @@ cudaError_t launch_hash(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads
 
 // sort.cu
 constexpr int kSortThreads = 256;
+static_assert(kSortThreads == (int)kSortThreadsHost, "one block size for the sort kernels");
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;   // keys per onesweep tile
 constexpr int kMaxRadixBits = 11;
@@ -145,30 +146,6 @@ rc_status sort_static_record(const void** rec);
 // dropped), then each A-bucket by the next dB bits (pass B), without look-back;
 // every resulting bucket (top D = dA + dB bits of h) holds all keys of its cells
 // and is grouped by cell and folded in shared memory (bucket_fold_kernel).
-constexpr uint64_t kCellHashMul = 0x9E3779B97F4A7C15ull;
-constexpr uint32_t kBucketMaxDigitBits = 10;        // per partition pass
-constexpr uint32_t kBucketMaxBits = 2 * kBucketMaxDigitBits;
-constexpr int kFoldCap = 8192;                      // keys of a bucket folded in shared memory
-constexpr uint32_t kFoldBinBits = 12;               // counting-sort bins of a bucket (at most)
-constexpr uint64_t kBucketTarget = kFoldCap / 2 + kFoldCap / 16;   // planned mean keys per bucket
-constexpr int kBucketHistTile = 16384;              // keys per block of the pass-B histogram
-constexpr int kPartTileHost = kSortThreads * 12;    // keys per tile of the partition passes
-
-struct BucketPlan {
-  bool on = false;
-  uint32_t cb = 0, dA = 0, dB = 0, D = 0, r = 0, rbin = 0;
-  uint64_t n = 0;                 // key slots (padding included)
-  uint64_t tiles_b = 0, tiles_h = 0;   // grid bounds of pass B and its histogram
-  // workspace offsets (bytes) of the bucket section
-  size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, hist_b = 0, boff = 0, cur_b = 0, temp = 0;
-  size_t zero_lo = 0, zero_hi = 0;    // cleared at the start of a check (the two histograms)
-  size_t end = 0;
-};
-// host (runtime.cu): whether the bucket path applies to n keys of cb cell bits
-// (at most 2^kBucketMaxBits buckets of about kBucketTarget keys), its digit
-// widths, and its workspace section laid out from byte offset `off`
-bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp);
-
 struct BucketArgs {
   const uint64_t* keys_in;
   uint64_t* keys_out;

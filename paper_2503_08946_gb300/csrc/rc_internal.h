@@ -332,6 +332,33 @@ inline uint32_t plan_max_bits(const SortPlan& sp) {
   return b;
 }
 
+// The bucket path of the grouping step (bucket.cu): see kernels.h.
+constexpr uint32_t kSortThreadsHost = 256;
+constexpr uint64_t kCellHashMul = 0x9E3779B97F4A7C15ull;
+constexpr uint32_t kBucketMaxDigitBits = 10;        // per partition pass
+constexpr uint32_t kBucketMaxBits = 2 * kBucketMaxDigitBits;
+constexpr int kFoldCap = 8192;                      // keys of a bucket folded in shared memory
+constexpr uint32_t kFoldBinBits = 12;               // counting-sort bins of a bucket (at most)
+constexpr uint64_t kBucketTarget = kFoldCap / 2 + kFoldCap / 16;   // planned mean keys per bucket
+constexpr int kBucketHistTile = 16384;              // keys per block of the pass-B histogram
+constexpr int kPartTileHost = kSortThreadsHost * 12;    // keys per tile of the partition passes
+
+struct BucketPlan {
+  bool on = false;
+  uint32_t cb = 0, dA = 0, dB = 0, D = 0, r = 0, rbin = 0;
+  uint64_t n = 0;                 // key slots (padding included)
+  uint64_t tiles_b = 0, tiles_h = 0;   // grid bounds of pass B and its histogram
+  // workspace offsets (bytes) of the bucket section
+  size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, hist_b = 0, boff = 0, cur_b = 0, temp = 0;
+  size_t zero_lo = 0, zero_hi = 0;    // cleared at the start of a check (the two histograms)
+  size_t end = 0;
+};
+// host (runtime.cu): whether the bucket path applies to n keys of cb cell bits
+// (at most 2^kBucketMaxBits buckets of about kBucketTarget keys), its digit
+// widths, and its workspace section laid out from byte offset `off`
+bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp);
+
+
 struct WorkspacePlan {
   size_t result_off;      // DevResult
   size_t keys_off[2];     // ping-pong key buffers
@@ -350,6 +377,7 @@ struct WorkspacePlan {
   uint64_t n_tiles;
   uint32_t scan_warps;
   SortPlan sort;
+  BucketPlan bucket;      // bucket path (bucket.on) instead of the LSD sections
   // hash path
   bool hash;
   uint64_t hash_cap;      // slots per table (power of two)
@@ -420,7 +448,9 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
 // look-back region holds digits of at least min_lookback_bits bits (so that a
 // narrower sort of fewer bits, whose widest digit may be wider, fits it)
 void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits, WorkspacePlan* p,
-                         uint32_t min_lookback_bits = 0);
+                         uint32_t min_lookback_bits = 0, bool allow_bucket = true);
+// whether options and a key layout of phase_bits phase bits admit the bucket path
+bool bucket_path_allowed(uint32_t phase_bits, const rc_check_opts* opts);
 void plan_sort(uint32_t lo, uint32_t hi, uint32_t digit_bits, SortPlan* sp);
 uint32_t bit_length(uint64_t v);
 

@@ -41,8 +41,11 @@ struct StageTimer {
 struct rc_ticket_s {
   StageTimer timer;
   bool timed = false;
-  int i_start = 0, i_expand = 0, i_hist = 0, i_pass0 = 0, i_scan = 0, i_wit = 0;
+  int i_start = 0, i_expand = 0, i_hist = 0, i_scan = 0, i_wit = 0;
   uint32_t n_pass = 0;
+  int i_pass_from[16] = {}, i_pass_to[16] = {};   // events around each sort / partition pass
+  int i_hist2_from = -1, i_hist2_to = -1;        // bucket path: the pass-B histogram
+  bool bucketed = false;
   uint64_t n_keys = 0;
   cudaEvent_t done = nullptr;
   rc::DevResult* host = nullptr;   // pinned, `cap` records
@@ -84,6 +87,8 @@ rc_ticket_s* ticket_get(size_t n) {
         t->timed = false;
         t->timer.n = 0;
         t->timer.ok = true;
+        t->i_hist2_from = t->i_hist2_to = -1;
+        t->bucketed = false;
         return t;
       }
     }
@@ -205,8 +210,55 @@ void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p)
   plan_workspace_keys(m, opts, n, m.host.cell_bits, p);
 }
 
+bool bucket_path_allowed(uint32_t phase_bits, const rc_check_opts* opts) {
+  if (phase_bits > kScanTablePhaseBits) return false;   // the fold keeps per-interval masks of 16 intervals
+  if (opts && ((opts->flags & RC_OPT_LSD) || opts->digit_bits || opts->test_flags)) return false;
+  return true;
+}
+
+bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp) {
+  *bp = BucketPlan();
+  if (n == 0 || n >= (1ull << 32) || cb == 0 || cb > 62) return false;
+  uint32_t D = 0;
+  while (D < cb && D < kBucketMaxBits && (n >> D) > kBucketTarget) ++D;
+  if (D == kBucketMaxBits && D < cb && (n >> D) > kBucketTarget) return false;   // more keys than the buckets hold
+  bp->on = true;
+  bp->n = n;
+  bp->cb = cb;
+  bp->D = D;
+  bp->dA = D <= kBucketMaxDigitBits ? D : (D + 1) / 2;
+  bp->dB = D - bp->dA;
+  bp->r = cb - D;
+  bp->rbin = bp->r < kFoldBinBits ? bp->r : kFoldBinBits;
+  const uint64_t na = 1ull << bp->dA, nb = 1ull << D;
+  bp->tiles_b = n / kPartTileHost + na + 1;
+  bp->tiles_h = n / kBucketHistTile + na + 1;
+  bp->zero_lo = off;
+  bp->hist_a = off;
+  off = align256(off + na * 8);
+  bp->hist_b = off;
+  off = align256(off + nb * 8);
+  bp->zero_hi = off;
+  bp->off_a = off;
+  off = align256(off + (na + 1) * 8);
+  bp->cur_a = off;
+  off = align256(off + na * 8);
+  bp->tpref_b = off;
+  off = align256(off + (na + 1) * 8);
+  bp->tpref_h = off;
+  off = align256(off + (na + 1) * 8);
+  bp->boff = off;
+  off = align256(off + (nb + 1) * 8);
+  bp->cur_b = off;
+  off = align256(off + nb * 8);
+  bp->temp = off;
+  off = align256(off + scan_u64_temp_bytes(nb));
+  bp->end = off;
+  return true;
+}
+
 void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, uint32_t cell_bits,
-                         WorkspacePlan* p, uint32_t min_lookback_bits) {
+                         WorkspacePlan* p, uint32_t min_lookback_bits, bool allow_bucket) {
   std::memset(p, 0, sizeof(*p));
   p->n_keys = n;
   const uint32_t hi = m.host.cell_shift + cell_bits;
@@ -220,6 +272,16 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   off = align256(off + n * 8);
   p->keys_off[1] = off;
   off = align256(off + n * 8);
+  if (allow_bucket && bucket_path_allowed(m.host.phase_bits, opts) && plan_buckets(n, cell_bits, off, &p->bucket)) {
+    // the bucket path: its own section instead of the radix-sort and scan sections
+    p->zero_lo = p->bucket.zero_lo;
+    p->zero_hi = p->bucket.zero_hi;
+    off = p->bucket.end;
+    p->group_off = off;
+    off = align256(off + witness_group_bytes(m));
+    p->total = off;
+    return;
+  }
   p->zero_lo = off;
   p->hist_off = off;
   off = align256(off + (size_t)16 * kMaxRadix * 8);
@@ -292,6 +354,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
   s = cuda_status(rc::launch_digit_offsets(hist, digoff, p.sort, st));
   if (s != RC_OK) return s;
   if (tm) tm->mark();
+  const int i_first = tm ? tm->n - 1 : 0;
   int cur = 0;
   for (uint32_t k = 0; k < p.sort.n_pass; ++k) {
     rc::SortArgs a;
@@ -320,8 +383,91 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
     if (tm) tm->mark();
     cur = 1 - cur;
   }
+  (void)i_first;
   *sorted_buf = cur;
   return RC_OK;
+}
+
+// Enqueue the bucket path (bucket.cu) over p.n_keys keys in buf0: partition
+// passes, bucket fold and the finish that points the witness at the smallest
+// racy cell's bucket.  `sa` carries the key layout, results and tables; on
+// return *final_keys is the buffer the witness reads.  Stage events: after the
+// pass-A histogram (i_hist), around each pass, around the pass-B histogram.
+rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, uint64_t* buf1,
+                           const rc::ScanArgs& sa, cudaStream_t st, const uint64_t** final_keys,
+                           rc_ticket_s* timed = nullptr) {
+  const rc::BucketPlan& bp = p.bucket;
+  StageTimer* tm = timed ? &timed->timer : nullptr;
+  auto u64 = [&](size_t off) { return reinterpret_cast<unsigned long long*>(ws + off); };
+  rc::BucketArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = p.n_keys;
+  a.cell_shift = sa.cell_shift;
+  a.cb = bp.cb;
+  a.cmask = bp.cb >= 64 ? ~0ull : ((1ull << bp.cb) - 1ull);
+  a.dA = bp.dA;
+  a.dB = bp.dB;
+  a.hist_a = u64(bp.hist_a);
+  a.off_a = u64(bp.off_a);
+  a.cur_a = u64(bp.cur_a);
+  a.tpref_b = u64(bp.tpref_b);
+  a.tpref_h = u64(bp.tpref_h);
+  a.hist_b = u64(bp.hist_b);
+  a.boff = u64(bp.boff);
+  a.cur_b = u64(bp.cur_b);
+  a.temp = u64(bp.temp);
+  a.err = sa.err;
+  uint64_t* fin = buf0;
+  uint64_t* scratch = buf1;
+  uint32_t n_pass = 0;
+  rc_status s = RC_OK;
+  if (bp.D == 0) {
+    s = cuda_status(rc::launch_bucket_whole(a.boff, p.n_keys, st));
+    if (tm) { timed->i_hist = tm->n; tm->mark(); }
+  } else {
+    a.keys_in = buf0;
+    a.keys_out = buf1;
+    s = cuda_status(rc::launch_bucket_hist_a(a, st));
+    if (s == RC_OK) s = cuda_status(rc::launch_bucket_scan_a(a, st));
+    if (tm) { timed->i_hist = tm->n; tm->mark(); }
+    if (s == RC_OK) s = cuda_status(rc::launch_bucket_pass_a(a, st));
+    if (tm) { timed->i_pass_from[0] = tm->n - 1; timed->i_pass_to[0] = tm->n; tm->mark(); }
+    n_pass = 1;
+    fin = buf1;
+    scratch = buf0;
+    if (bp.dB && s == RC_OK) {
+      a.keys_in = buf1;
+      a.keys_out = buf0;
+      s = cuda_status(rc::launch_bucket_hist_b(a, bp.tiles_h, st));
+      if (s == RC_OK) s = cuda_status(rc::launch_bucket_scan_b(a, st));
+      if (tm) { timed->i_hist2_from = tm->n - 1; timed->i_hist2_to = tm->n; tm->mark(); }
+      if (s == RC_OK) s = cuda_status(rc::launch_bucket_pass_b(a, bp.tiles_b, st));
+      if (tm) { timed->i_pass_from[1] = tm->n - 1; timed->i_pass_to[1] = tm->n; tm->mark(); }
+      n_pass = 2;
+      fin = buf0;
+      scratch = buf1;
+    }
+  }
+  if (s != RC_OK) return s;
+  rc::FoldArgs fa;
+  fa.s = sa;
+  fa.s.keys = fin;
+  fa.s.n = p.n_keys;
+  fa.boff = a.boff;
+  fa.scratch = scratch;
+  fa.cmask = a.cmask;
+  fa.cb = bp.cb;
+  fa.D = bp.D;
+  fa.rbin = bp.rbin;
+  fa.r = bp.r;
+  s = cuda_status(rc::launch_bucket_fold(fa, st));
+  if (s == RC_OK) s = cuda_status(rc::launch_bucket_finish(fa, st));
+  if (timed) {
+    timed->n_pass = n_pass;
+    timed->bucketed = true;
+  }
+  *final_keys = fin;
+  return s;
 }
 
 rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws, size_t ws_bytes,
@@ -374,7 +520,6 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     if (s != RC_OK) return s;
     if (tm) {
       timed->i_expand = timed->i_hist = timed->i_scan = tm->n;
-      timed->i_pass0 = tm->n;
       timed->n_pass = 0;
       tm->mark();
     }
@@ -398,8 +543,29 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
                                       reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
   if (s != RC_OK) return s;
   if (tm) { timed->i_expand = tm->n; tm->mark(); }
+  if (p.bucket.on) {
+    // the bucket path: partition passes and the bucket fold
+    const uint64_t* fin = nullptr;
+    rc::ScanArgs sa = scan_args(m, p, ws, 0);
+    s = enqueue_bucketed(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
+                         reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), sa, st, &fin, timed);
+    if (s != RC_OK) return s;
+    if (tm) { timed->i_scan = tm->n; tm->mark(); }
+    sa.keys = fin;
+    s = cuda_status(rc::launch_witness(sa, st));
+    if (s != RC_OK) return s;
+    if (tm) { timed->i_wit = tm->n; tm->mark(); }
+    if (host_out) s = cuda_status(cudaMemcpyAsync(host_out, res, sizeof(rc::DevResult), cudaMemcpyDeviceToHost, st));
+    return s;
+  }
   int sorted = 0;
-  if (tm) { timed->i_hist = tm->n; timed->i_pass0 = tm->n + 1; }
+  if (tm) {
+    timed->i_hist = tm->n;
+    for (uint32_t k = 0; k < p.sort.n_pass && k < 16; ++k) {
+      timed->i_pass_from[k] = tm->n + (int)k;
+      timed->i_pass_to[k] = tm->n + (int)k + 1;
+    }
+  }
   s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
                    reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin,
                    opts ? opts->test_flags : 0u, st, &sorted, tm, true);
@@ -537,7 +703,7 @@ uint32_t chunk_digit_bits(const rc_check_opts* opts) {
 
 // the region's layout for n keys
 void chunk_region_plan(const rc::Model& m, const rc_check_opts* opts, uint64_t n, rc::WorkspacePlan* p) {
-  rc::plan_workspace_keys(m, opts, n, m.host.cell_bits, p, chunk_digit_bits(opts));
+  rc::plan_workspace_keys(m, opts, n, m.host.cell_bits, p, chunk_digit_bits(opts), false);
 }
 
 // keys one region can hold in `bytes` (~0 if not even its fixed part fits)
@@ -889,6 +1055,17 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     o = align256(o + k.n_keys * 8);
     p.keys_off[1] = o;
     o = align256(o + k.n_keys * 8);
+    if (rc::bucket_path_allowed(k.pb, opts) && rc::plan_buckets(k.n_keys, k.cell_bits, o, &p.bucket)) {
+      p.zero_lo = p.bucket.zero_lo;
+      p.zero_hi = p.bucket.zero_hi;
+      o = p.bucket.end;
+      p.group_off = o;
+      o = align256(o + (k.i1 - k.i0) * ((size_t)1 << (k.pb + (k.mg ? k.bb : 0u))) * rc::kWitnessGroupWords *
+                           sizeof(unsigned int));
+      p.total = o;
+      need = std::max(need, o);
+      continue;
+    }
     p.zero_lo = o;
     p.hist_off = o;
     o = align256(o + (size_t)16 * rc::kMaxRadix * 8);
@@ -994,11 +1171,14 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     s = cuda_status(rc::launch_batch_expand(ba, k.loop_free, st));
     if (s != RC_OK) break;
     int sorted = 0;
-    s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
-                     reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin, opts ? opts->test_flags : 0u, st,
-                     &sorted, nullptr, true);
-    if (s != RC_OK) break;
+    if (!p.bucket.on) {
+      s = enqueue_sort(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
+                       reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), spin, opts ? opts->test_flags : 0u, st,
+                       &sorted, nullptr, true);
+      if (s != RC_OK) break;
+    }
     rc::ScanArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
     sa.keys = reinterpret_cast<const uint64_t*>(ws + p.keys_off[sorted]);
     sa.n = k.n_keys;
     sa.cell_shift = ba.cell_shift;
@@ -1021,7 +1201,14 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
     sa.sync_tabs = k.sy ? dstabs + 3 * k.i0 : nullptr;
     sa.wit_block_bits = k.mg ? k.bb : 0u;
-    s = cuda_status(rc::launch_scan(sa, st));
+    if (p.bucket.on) {
+      const uint64_t* fin = nullptr;
+      s = enqueue_bucketed(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
+                           reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), sa, st, &fin);
+      sa.keys = fin;
+    } else {
+      s = cuda_status(rc::launch_scan(sa, st));
+    }
     if (s == RC_OK) s = cuda_status(rc::launch_witness(sa, st));
     if (s == RC_OK) s = cuda_status(rc::launch_batch_errors(pres, res + k.i0, nm, st));
   }
@@ -1519,9 +1706,16 @@ rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts, 
   base.early_exit = 0;
   const TuneKey key = tune_key(models, n);
   const uint32_t sort_bits = n == 1 ? models[0]->m.host.sort_hi - models[0]->m.host.sort_lo : key.sort_bits;
-  // candidates: every distinct number of sort passes for digits of 6..11 bits, and the hash path
+  // candidates: the bucket path (where it applies), every distinct number of
+  // LSD sort passes for digits of 6..11 bits, and the hash path
   std::vector<rc_check_opts> cands;
   std::vector<uint32_t> passes;
+  if (!(base.flags & RC_OPT_LSD)) {
+    rc_check_opts o = base;
+    o.path = RC_PATH_SORT;
+    o.digit_bits = 0;
+    cands.push_back(o);
+  }
   for (uint32_t d = 6; d <= 11; ++d) {
     rc::SortPlan sp;
     rc::plan_sort(0, sort_bits, d, &sp);
@@ -1649,9 +1843,11 @@ rc_status rc_ticket_stage_times(rc_ticket t, rc_stage_times* out) {
   out->n_sort_passes = t->n_pass;
   int prev = t->i_hist;
   for (uint32_t k = 0; k < t->n_pass && k < 16; ++k) {
-    out->sort_ms[k] = ms(prev, t->i_pass0 + (int)k);
-    prev = t->i_pass0 + (int)k;
+    out->sort_ms[k] = ms(t->i_pass_from[k], t->i_pass_to[k]);
+    prev = t->i_pass_to[k];
   }
+  if (t->i_hist2_from >= 0) out->histogram2_ms = ms(t->i_hist2_from, t->i_hist2_to);
+  out->bucketed = t->bucketed ? 1u : 0u;
   out->scan_ms = ms(prev, t->i_scan);
   out->witness_ms = ms(t->i_scan, t->i_wit);
   out->total_ms = ms(t->i_start, t->i_wit);

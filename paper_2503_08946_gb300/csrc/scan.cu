@@ -907,10 +907,13 @@ __global__ void __launch_bounds__(256) witness_cell_kernel(ScanArgs a) {
     }
   }
   const uint64_t e = r->seg_end;
+  const uint64_t wcell = r->cell;
   unsigned minb = 0xffffffffu, maxb = 0;
   unsigned kmin[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, kmax[3] = {0, 0, 0}, kany[3] = {0, 0, 0};
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Fields f = fields(a, a.keys[i]);
+    const uint64_t key = a.keys[i];
+    if ((key >> a.cell_shift) != wcell) continue;   // the bucket path's range holds other cells too
+    const Fields f = fields(a, key);
     minb = min(minb, f.b);
     maxb = max(maxb, f.b);
 #pragma unroll
@@ -951,9 +954,12 @@ __global__ void __launch_bounds__(256) witness_group_kernel(ScanArgs a) {
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t e = r->seg_end;
+  const uint64_t wcell = r->cell;
   const unsigned b0 = r->minb;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Fields f = fields(a, a.keys[i]);
+    const uint64_t key = a.keys[i];
+    if ((key >> a.cell_shift) != wcell) continue;   // the bucket path's range holds other cells too
+    const Fields f = fields(a, key);
     if (syt.on) {
       // blocks holding each kind per fine interval (cross-block partners of one grid interval)
       unsigned* g0 = group_rec(a, groups, 0u, f.p);
@@ -978,13 +984,16 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
   const uint64_t s = r->min_start;
   if (s == ~0ull) return;
   const uint64_t e = r->seg_end;
+  const uint64_t wcell = r->cell;
   const unsigned b0 = r->minb;
   const unsigned kminb[3] = {r->minRb, r->minWb, r->minAb}, kmaxb[3] = {r->maxRb, r->maxWb, r->maxAb};
   const unsigned kany[3] = {r->anyR, r->anyW, r->anyA};
   const uint32_t kb = a.thread_shift;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Fields f = fields(a, a.keys[i]);
+    const uint64_t key = a.keys[i];
+    if ((key >> a.cell_shift) != wcell) continue;   // the bucket path's range holds other cells too
+    const Fields f = fields(a, key);
     // candidates: the lowest block's instances, or every block's with per-block records
     if (!a.wit_block_bits && f.b != b0) continue;
     const unsigned xb = f.b;
@@ -1041,6 +1050,7 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   const uint64_t s = r->min_start;
   if (s == ~0ull || r->x_rank == ~0ull) return;
   const uint64_t e = r->seg_end;
+  const uint64_t wcell = r->cell;
   const uint32_t kb = a.thread_shift;
   const unsigned long long xr = r->x_rank;
   const uint32_t wb = syt.wp_bits;
@@ -1053,7 +1063,9 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   const unsigned xg = (unsigned)(syt.grid >> (4 * xq)) & 15u;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
-    const Fields f = fields(a, a.keys[i]);
+    const uint64_t key = a.keys[i];
+    if ((key >> a.cell_shift) != wcell) continue;   // the bucket path's range holds other cells too
+    const Fields f = fields(a, key);
     const unsigned yp = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
     const unsigned yw = f.p - yp * syt.n_wp;
     const bool other_thread = f.b != b0 || f.t != xt;
