@@ -63,7 +63,8 @@ def test_path_selection(rc):
     m = w.random_affine(3, n_blocks=64, block=256)
     assert plan_of(rc, m) == (True, 2)                         # ~17M keys: two partition passes
     assert plan_of(rc, w.random_affine(3, n_blocks=1, block=256))[0]   # small: one pass or none
-    assert plan_of(rc, w.reduction_tree(False)) == (True, 0)   # 765 keys: one bucket, no pass
+    assert plan_of(rc, w.neighbor_write_read(64)) == (True, 0)  # 128 key slots: one bucket, no pass
+    assert plan_of(rc, w.reduction_tree(False)) == (True, 1)   # 6,144 key slots: one pass
     assert plan_of(rc, m, {"flags": b.RC_OPT_LSD})[0] is False
     assert plan_of(rc, m, {"digit_bits": 8})[0] is False
     many = Model((2, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
