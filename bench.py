@@ -58,22 +58,29 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the onesweep kernel's source file (the ncu traffic figure is
-    only used while it matches)."""
+KERNEL_SOURCES = {"onesweep": "sort.cu", "partition": "sort.cu", "partition_a": "bucket.cu",
+                  "partition_b": "bucket.cu", "local_sort": "bucket.cu", "histogram_b": "bucket.cu",
+                  "scan": "scan.cu", "expand": "jit.cpp", "histogram": "bucket.cu"}
+
+
+def kernel_source_hash(kernel="onesweep"):
+    """Hash of a kernel's source file (an ncu traffic figure is only used
+    while it matches)."""
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2503_08946_gb300", "csrc", "sort.cu"), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_2503_08946_gb300", "csrc", KERNEL_SOURCES.get(kernel, "sort.cu")),
+                  "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_key():
-    """DRAM bytes per key of one onesweep pass from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "onesweep_traffic.json")
+def ncu_traffic_per_key(kernel="onesweep"):
+    """DRAM bytes per key of one launch of `kernel` from the committed ncu
+    summary (profiles/<kernel>_traffic.json), if it was taken on the current
+    kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(kernel):
         return None
     return float(d["dram_bytes_per_key"])
 
@@ -265,33 +272,50 @@ def run_native(args):
     n_keys = stages[0]["n_keys"]
     n_pass = len(stages[0]["sort_ms"])
     mean = lambda xs: sum(xs) / len(xs)
+    bucketed = bool(stages[0].get("bucketed"))
     st_mean = {
         "expand_ms": mean([s["expand_ms"] for s in stages]),
         "histogram_ms": mean([s["histogram_ms"] for s in stages]),
         "sort_pass_ms": [mean([s["sort_ms"][k] for s in stages]) for k in range(n_pass)],
+        "histogram2_ms": mean([s.get("histogram2_ms", 0.0) for s in stages]),
         "scan_ms": mean([s["scan_ms"] for s in stages]),
         "witness_ms": mean([s["witness_ms"] for s in stages]),
         "check_ms": mean([s["total_ms"] for s in stages]),
     }
-    pass_ms = mean(st_mean["sort_pass_ms"]) if n_pass else float("nan")
-    totals = {"onesweep": sum(st_mean["sort_pass_ms"]), "expand": st_mean["expand_ms"],
-              "histogram": st_mean["histogram_ms"], "scan": st_mean["scan_ms"]}
-    dominant = max(totals, key=totals.get)
     peak, peak_kind = load_peaks()
-    # algorithmic bytes per launch: onesweep pass reads and writes every key once (16 B/key)
-    per_launch = {"onesweep": (16.0 * n_keys, pass_ms), "expand": (8.0 * n_keys, st_mean["expand_ms"]),
-                  "histogram": (8.0 * n_keys, st_mean["histogram_ms"]), "scan": (8.0 * n_keys, st_mean["scan_ms"])}
-    alg_bytes, dur_ms = per_launch[dominant]
+    # per kernel: (algorithmic bytes per launch, mean launch ms).  Every pass
+    # (partition, local sort, radix pass) reads and writes each key once (16 B
+    # per key); expansion writes 8 B, histograms and the scan read 8 B.
+    if bucketed:
+        names = {3: ["partition_a", "partition_b", "local_sort"], 2: ["partition_a", "local_sort"],
+                 1: ["local_sort"]}[n_pass]
+        kern = {nm: (16.0 * n_keys, st_mean["sort_pass_ms"][i]) for i, nm in enumerate(names)}
+        kern["histogram_b"] = (8.0 * n_keys, st_mean["histogram2_ms"])
+    else:
+        kern = {"onesweep": (16.0 * n_keys, mean(st_mean["sort_pass_ms"][1:] or st_mean["sort_pass_ms"]))}
+        if n_pass:
+            kern["partition"] = (16.0 * n_keys, st_mean["sort_pass_ms"][0])
+    kern["expand"] = (8.0 * n_keys, st_mean["expand_ms"])
+    kern["histogram"] = (8.0 * n_keys, st_mean["histogram_ms"])
+    kern["scan"] = (8.0 * n_keys, st_mean["scan_ms"])
+    launches = {"onesweep": max(1, n_pass - 1)} if not bucketed else {}
+    dominant = max(kern, key=lambda k: kern[k][1] * launches.get(k, 1))
+    alg_bytes, dur_ms = kern[dominant]
     achieved = alg_bytes / (dur_ms / 1e3) / 1e9
-    tpk = ncu_traffic_per_key() if dominant == "onesweep" else None
+    tpk = ncu_traffic_per_key(dominant)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                 "alg_bytes_per_launch": alg_bytes, "launch_ms": dur_ms,
                 "traffic": (tpk * n_keys) if tpk is not None else None}
-    pipeline_bytes = (8 + 8 + 16 * n_pass + 8) * n_keys
-    pipeline = {"alg_bytes_per_key": 8 + 8 + 16 * n_pass + 8,
+    per_kernel = {k: {"ms": v[1], "alg_bytes_per_key": v[0] / n_keys,
+                      "frac": v[0] / (v[1] / 1e3) / 1e9 / peak if v[1] > 0 else None} for k, v in kern.items()}
+    # the whole check: expansion 8, histograms 8 each, passes 16 each, scan 8 bytes per key
+    pk = 8 + 8 + 16 * n_pass + 8 + (8 if bucketed and n_pass == 3 else 0)
+    pipeline_bytes = pk * n_keys
+    pipeline = {"alg_bytes_per_key": pk,
                 "gbs": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9,
-                "frac": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9 / peak}
+                "frac": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9 / peak,
+                "per_kernel": per_kernel}
 
     # end to end through the public calls from host descriptors
     e2e = None
@@ -344,12 +368,15 @@ def run_native(args):
             "config": {"workload": WORKLOAD if args.blocks == 4096 else WORKLOAD.replace("4096 blocks", f"{args.blocks} blocks"),
                        "seed": args.seed, "instances_per_rank": instances,
                        "keys": n_keys, "sort_bits": lay["sort_hi"] - lay["sort_lo"], "sort_passes": n_pass,
-                       "path": "sort", "l2": "inputs larger than L2 (key buffers ~9 GB)",
+                       "path": "bucket" if bucketed else "lsd sort", "l2": "inputs larger than L2 (key buffers ~9 GB)",
                        "parallelism": f"independent models per rank x{world}"},
             "result": result,
             "roofline": roofline, "pipeline": pipeline, "stages_ms": st_mean,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": (11 + n_pass) * args.steps,
+            # our kernels per check: bucket path 20 with two partition passes (init, expansion,
+            # 2 x (histogram, offsets), 2 passes, local sort, tail, scan (3), finish, witness (4);
+            # offsets of pass B: 3); LSD path 11 + passes
+            "gpu_launches": ({3: 20, 2: 15, 1: 13}[n_pass] if bucketed else (11 + n_pass)) * args.steps,
         }
         line.update(subs)
         print(json.dumps(line), flush=True)

@@ -12,14 +12,14 @@
 //           digit with one atomic add each on per-digit cursors: no look-back;
 //   pass B  partition of every A-bucket by the next dB bits, tiles lying inside
 //           one A-bucket;
-//   fold    every bucket (top D = dA + dB bits of h: all keys of its cells, on
-//           average kBucketTarget) is counting-sorted by the remaining bits of
-//           h in shared memory and folded cell by cell (fold.cuh), one thread
-//           per cell, the whole block for cells of more than kSmallCell keys.
-// A bucket larger than shared memory is counting-sorted into the other key
-// buffer (free at that point) and folded from there.  The smallest racy cell is
-// kept by value (DevResult.hash_cell); bucket_finish points the witness kernels
-// at its bucket, whose keys they filter by cell.
+//   local   every bucket (top D = dA + dB bits of h: all keys of its cells, on
+//   sort    average kBucketTarget) is counting-sorted by the remaining bits of
+//           h in shared memory and written back, so that the keys of every
+//           cell are contiguous (the cells are in h order, not in cell order).
+// The ordered cell scan (scan.cu) then folds the cells; it needs each cell's
+// keys together, in any order, and with `by_cell` keeps the smallest racy cell
+// by value (DevResult.hash_cell); bucket_finish points the witness kernels at
+// its bucket, whose keys they filter by cell.
 #include <cuda_runtime.h>
 
 #include "fold.cuh"
@@ -338,22 +338,18 @@ __global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// fold
+// local sort: every bucket put in cell order (by the remaining bits of h)
 // ---------------------------------------------------------------------------
-constexpr int kFoldThreads = 512;
-constexpr int kSmallCell = 256;   // bins with more keys are folded by the whole block
-constexpr int kBigCap = 64;       // such bins per bucket listed in shared memory (more: folded by one thread)
-constexpr int kGrab = 4;          // bins a thread takes per grab
+constexpr int kLocThreads = 512;
+constexpr int kLocKPT = (kFoldCap + kLocThreads - 1) / kLocThreads;   // keys per thread of a bucket in registers
 
-size_t fold_smem(uint32_t rbin) {
-  return (size_t)kFoldCap * 8 + ((size_t)4 << rbin) + (size_t)kTabPhases * kFoldThreads * 4;
-}
+size_t local_smem(uint32_t rbin) { return (size_t)kFoldCap * 8 + ((size_t)4 << rbin); }
 
-// exclusive scan in place of n (a multiple of kFoldThreads, or less) counters
-__device__ __forceinline__ void fold_bin_scan(unsigned* bin, unsigned n) {
-  __shared__ unsigned wsum[kFoldThreads / 32];
+// exclusive scan in place of n counters by the block
+__device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n) {
+  __shared__ unsigned wsum[kLocThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned per = (n + kFoldThreads - 1) / kFoldThreads;
+  const unsigned per = (n + kLocThreads - 1) / kLocThreads;
   const unsigned b0 = threadIdx.x * per;
   unsigned s = 0;
   for (unsigned i = 0; i < per; ++i)
@@ -366,9 +362,17 @@ __device__ __forceinline__ void fold_bin_scan(unsigned* bin, unsigned n) {
   }
   if (lane == 31) wsum[w] = x;
   __syncthreads();
-  unsigned base = 0;
-  for (int i = 0; i < w; ++i) base += wsum[i];
-  unsigned run = base + x - s;
+  if (w == 0) {
+    unsigned t = lane < kLocThreads / 32 ? wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(FULL, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kLocThreads / 32) wsum[lane] = t;   // inclusive over warps
+  }
+  __syncthreads();
+  unsigned run = (w ? wsum[w - 1] : 0u) + x - s;
   for (unsigned i = 0; i < per; ++i)
     if (b0 + i < n) {
       const unsigned c = bin[b0 + i];
@@ -377,251 +381,123 @@ __device__ __forceinline__ void fold_bin_scan(unsigned* bin, unsigned n) {
     }
 }
 
-template <bool AT, bool SY>
-__global__ void __launch_bounds__(kFoldThreads, 2) bucket_fold_kernel(FoldArgs fa) {
-  const ScanArgs& a = fa.s;
+// Each bucket [boff[b], boff[b+1]) of keys_in is counting-sorted by the rbin
+// bits of h below the bucket bits (cells with equal h are equal, so a bin holds
+// one cell when rbin == r; otherwise a bin holding several cells is put in cell
+// order by insertion sort) and written to the same positions of keys_out.  A
+// bucket of at most kFoldCap keys is read once into registers and sorted in
+// shared memory; a larger one is read twice and scattered to keys_out.
+// Padding keys (the unpartitioned single bucket holds them) are dropped; the
+// positions [boff[nb], n) of keys_out are filled with padding (bucket_tail).
+// H32: cb <= 32, so h is computed in 32-bit arithmetic (the same value: the
+// product modulo 2^cb depends only on the low 32 bits of each factor).
+template <bool H32>
+__global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(LocalSortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
   unsigned* s_bin = reinterpret_cast<unsigned*>(s_keys + kFoldCap);
-  unsigned* my_tab = s_bin + (1u << fa.rbin) + threadIdx.x;   // interval q at my_tab[q * kFoldThreads]
-  __shared__ unsigned s_big[kBigCap];
-  __shared__ unsigned s_nbig, s_next;
-  // whole-block fold of one cell (per interval (block, thread) extremes)
-  __shared__ unsigned bmn[kTabPhases], bmx[kTabPhases];
-  __shared__ unsigned bgw, bga, bgr, bminb, bmaxb, bw;
-  __shared__ unsigned long long s_cell;
-  __shared__ unsigned long long s_red[kFoldThreads / 32];
-
-  const uint32_t cs = a.cell_shift, ps = a.phase_shift, tb = a.thread_bits;
-  const uint32_t kb = a.thread_shift;
-  const unsigned pm = (1u << a.phase_bits) - 1u;
-  const unsigned btm = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
-  const unsigned nbins = 1u << fa.rbin;
-  const uint32_t bin_shift = fa.r - fa.rbin;
-  const bool multi = fa.rbin < fa.r;   // a bin may hold several cells
-  const uint64_t nb = 1ull << fa.D;
+  const unsigned nbins = 1u << a.rbin;
+  const uint32_t bin_shift = a.r - a.rbin;
+  const bool multi = a.rbin < a.r;
+  const uint32_t cs = a.cell_shift;
+  const uint64_t nb = 1ull << a.D;
   const int tid = threadIdx.x;
-  SyncTabs syt;
-  if constexpr (SY) syt = sync_tabs_of(a);
-  unsigned long long count = 0, minc = ~0ull;
-  using TF = typename FoldOf<SY>::type;
-
   auto bin_of = [&](uint64_t k) -> unsigned {
-    return (unsigned)(cell_hash_of(k >> cs, fa.cmask) >> bin_shift) & (nbins - 1u);
+    if constexpr (H32) {
+      const uint32_t h = (uint32_t)(k >> cs) * (uint32_t)kCellHashMul;
+      return (h >> bin_shift) & (nbins - 1u);
+    }
+    return (unsigned)(cell_hash_of(k >> cs, a.cmask) >> bin_shift) & (nbins - 1u);
   };
-  auto record = [&](uint64_t cell) {
-    if (a.n_models) {
-      DevResult* r = result_of(a, cell);
-      atomicAdd(&r->racy_cells, 1ull);
-      atomicMin(&r->hash_cell, (unsigned long long)cell);
-    } else {
-      ++count;
-      minc = cell < minc ? cell : minc;
-    }
-  };
-  // one thread: the cells of keys dst[s, e), each cell contiguous
-  auto fold_runs = [&](const uint64_t* dst, unsigned s, unsigned e) {
-    unsigned i = s;
-    while (i < e) {
-      const uint64_t k0 = dst[i];
-      const uint64_t c = k0 >> cs;
-      TF x;
-      tfold_clear(x);
-      x.fk = k0;
-      x.bt0 = (unsigned)(k0 >> kb) & btm;
-      unsigned j = i;
-      do {
-        const uint64_t k = dst[j];
-        const unsigned bt = (unsigned)(k >> kb) & btm;
-        const unsigned ph = (unsigned)(k >> ps) & pm;
-        const unsigned bit = 1u << ph;
-        if (!(x.vmask & bit)) {
-          my_tab[ph * kFoldThreads] = bt;
-          x.vmask |= bit;
-        } else {
-          const unsigned old = my_tab[ph * kFoldThreads];
-          if (old != bt) {
-            x.gm |= bit;
-            if constexpr (SY) mark_pair(old, bt, bit, tb, x.gmb, x.gmw);
-          }
-        }
-        x.gw |= (unsigned)(k & 1ull) << ph;
-        if (((bt ^ x.bt0) >> tb) != 0u) x.f |= kTMB;
-        if (AT) {
-          if (k & 2ull) x.ga |= bit;
-          if ((k & 3ull) == 0ull) x.gr |= bit;
-        }
-        ++j;
-      } while (j < e && (dst[j] >> cs) == c);
-      bool racy;
-      if constexpr (SY) {
-        const SyncTabs mt = a.n_models ? sync_tabs_of(a, model_of(a, c)) : syt;
-        racy = tfold_racy_sync<AT, kFoldThreads>(x, my_tab, mt.coarse, mt.grid, tb);
-      } else {
-        racy = tfold_racy<AT>(x);
-      }
-      if (racy) record(c);
-      i = j;
-    }
-  };
-  // the whole block: the keys of cell `c` among dst[s, e)
-  auto block_fold_cell = [&](const uint64_t* dst, unsigned s, unsigned e, uint64_t c) {
-    if (tid < kTabPhases) {
-      bmn[tid] = 0xffffffffu;
-      bmx[tid] = 0;
-    }
-    if (tid == 0) {
-      bgw = bga = bgr = 0;
-      bminb = 0xffffffffu;
-      bmaxb = 0;
-      bw = 0;
-    }
-    __syncthreads();
-    for (unsigned i = s + tid; i < e; i += kFoldThreads) {
-      const uint64_t k = dst[i];
-      if ((k >> cs) != c) continue;
-      const unsigned bt = (unsigned)(k >> kb) & btm;
-      const unsigned ph = (unsigned)(k >> ps) & pm;
-      const unsigned kd = (unsigned)(k & ((1ull << kb) - 1ull));
-      atomicMin(&bmn[ph], bt);
-      atomicMax(&bmx[ph], bt);
-      atomicMin(&bminb, bt >> tb);
-      atomicMax(&bmaxb, bt >> tb);
-      if (kd == 1u) {
-        atomicOr(&bgw, 1u << ph);
-        bw = 1;
-      } else if (kd == 2u) {
-        atomicOr(&bga, 1u << ph);
-      } else {
-        atomicOr(&bgr, 1u << ph);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const SyncTabs mt = a.n_models ? sync_tabs_of(a, model_of(a, c)) : syt;
-      if (summary_racy(bmn, bmx, bgw, bga, bgr, bw != 0u, bminb, bmaxb, mt, tb)) record(c);
-    }
-    __syncthreads();
-  };
-  // the smallest cell above `above` among dst[s, e) (~0: none), block-wide
-  auto block_next_cell = [&](const uint64_t* dst, unsigned s, unsigned e, uint64_t above, bool first) {
-    unsigned long long m = ~0ull;
-    for (unsigned i = s + tid; i < e; i += kFoldThreads) {
-      const uint64_t c = dst[i] >> cs;
-      if ((first || c > above) && c < m) m = c;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long y = __shfl_xor_sync(FULL, m, o);
-      m = y < m ? y : m;
-    }
-    if ((tid & 31) == 0) s_red[tid >> 5] = m;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long t = ~0ull;
-      for (int i = 0; i < kFoldThreads / 32; ++i) t = s_red[i] < t ? s_red[i] : t;
-      s_cell = t;
-    }
-    __syncthreads();
-    const unsigned long long r = s_cell;
-    __syncthreads();
-    return r;
-  };
-
   for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint64_t lo = fa.boff[b], hi = fa.boff[b + 1];
+    const uint64_t lo = a.boff[b], hi = a.boff[b + 1];
     if (hi <= lo) continue;
     const uint64_t len = hi - lo;
     const bool in_smem = len <= (uint64_t)kFoldCap;
-    const uint64_t* src = a.keys + lo;
-    uint64_t* dst = in_smem ? s_keys : fa.scratch + lo;
-    for (unsigned i = tid; i < nbins; i += kFoldThreads) s_bin[i] = 0;
-    if (tid == 0) {
-      s_nbig = 0;
-      s_next = 0;
-    }
+    const uint64_t* src = a.keys_in + lo;
+    uint64_t* out = a.keys_out + lo;
+    uint64_t* dst = in_smem ? s_keys : out;
+    for (unsigned i = tid; i < nbins; i += kLocThreads) s_bin[i] = 0;
     __syncthreads();
-    // counting sort by bin (padding keys skipped: the unpartitioned single bucket holds them)
-    for (uint64_t i = tid; i < len; i += kFoldThreads) {
-      const uint64_t k = src[i];
-      if (k != kSentinel) atomicAdd(&s_bin[bin_of(k)], 1u);
-    }
-    __syncthreads();
-    fold_bin_scan(s_bin, nbins);
-    __syncthreads();
-    for (uint64_t i = tid; i < len; i += kFoldThreads) {
-      const uint64_t k = src[i];
-      if (k != kSentinel) dst[atomicAdd(&s_bin[bin_of(k)], 1u)] = k;
-    }
-    __syncthreads();
-    // s_bin[g] is now the end of bin g; bins are taken kGrab at a time
-    while (true) {
-      unsigned g0 = 0;
-      g0 = atomicAdd(&s_next, (unsigned)kGrab);
-      if (g0 >= nbins) break;
-      const unsigned g1 = min(g0 + (unsigned)kGrab, nbins);
-      for (unsigned g = g0; g < g1; ++g) {
-        const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
-        if (e <= s) continue;
-        if (e - s > (unsigned)kSmallCell) {
-          const unsigned i = atomicAdd(&s_nbig, 1u);
-          if (i < (unsigned)kBigCap) {
-            s_big[i] = g;
-            continue;
-          }
-        }
-        if (multi && e - s > 1u) {
-          // several cells may share the bin: order it by cell (insertion sort)
-          for (unsigned i = s + 1; i < e; ++i) {
-            const uint64_t v = dst[i];
-            unsigned j = i;
-            while (j > s && (dst[j - 1] >> cs) > (v >> cs)) {
-              dst[j] = dst[j - 1];
-              --j;
-            }
-            dst[j] = v;
-          }
-        }
-        fold_runs(dst, s, e);
-      }
-    }
-    __syncthreads();
-    const unsigned nbig = min(s_nbig, (unsigned)kBigCap);
-    for (unsigned q = 0; q < nbig; ++q) {
-      const unsigned g = s_big[q];
-      const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
-      if (!multi) {
-        block_fold_cell(dst, s, e, dst[s] >> cs);
-      } else {
-        uint64_t c = block_next_cell(dst, s, e, 0, true);
-        while (c != ~0ull) {
-          block_fold_cell(dst, s, e, c);
-          c = block_next_cell(dst, s, e, c, false);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (a.n_models == 0) {
+    if (in_smem) {
+      uint64_t kr[kLocKPT];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      count += __shfl_xor_sync(FULL, count, o);
-      const unsigned long long y = __shfl_xor_sync(FULL, minc, o);
-      minc = y < minc ? y : minc;
+      for (int q = 0; q < kLocKPT; ++q) {
+        const uint64_t i = (uint64_t)q * kLocThreads + tid;
+        kr[q] = i < len ? __ldg(src + i) : kSentinel;
+      }
+#pragma unroll
+      for (int q = 0; q < kLocKPT; ++q)
+        if (kr[q] != kSentinel) atomicAdd(&s_bin[bin_of(kr[q])], 1u);
+      __syncthreads();
+      bin_scan(s_bin, nbins);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kLocKPT; ++q)
+        if (kr[q] != kSentinel) s_keys[atomicAdd(&s_bin[bin_of(kr[q])], 1u)] = kr[q];
+    } else {
+      for (uint64_t i = tid; i < len; i += kLocThreads) {
+        const uint64_t k = src[i];
+        if (k != kSentinel) atomicAdd(&s_bin[bin_of(k)], 1u);
+      }
+      __syncthreads();
+      bin_scan(s_bin, nbins);
+      __syncthreads();
+      for (uint64_t i = tid; i < len; i += kLocThreads) {
+        const uint64_t k = src[i];
+        if (k != kSentinel) dst[atomicAdd(&s_bin[bin_of(k)], 1u)] = k;
+      }
     }
-    if ((tid & 31) == 0) {
-      if (count) atomicAdd(&a.res->racy_cells, count);
-      if (minc != ~0ull) atomicMin(&a.res->hash_cell, minc);
+    __syncthreads();
+    // s_bin[g] is now the end of bin g; total = keys kept
+    const unsigned total = s_bin[nbins - 1];
+    if (multi) {
+      for (unsigned g = tid; g < nbins; g += kLocThreads) {
+        const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
+        bool one = true;
+        for (unsigned i = s + 1; i < e && one; ++i) one = (dst[i] >> cs) == (dst[s] >> cs);
+        if (one) continue;
+        for (unsigned i = s + 1; i < e; ++i) {
+          const uint64_t v = dst[i];
+          unsigned j = i;
+          while (j > s && (dst[j - 1] >> cs) > (v >> cs)) {
+            dst[j] = dst[j - 1];
+            --j;
+          }
+          dst[j] = v;
+        }
+      }
+      __syncthreads();
     }
+    if (in_smem) {
+      // coalesced copy out (16-byte stores where the bucket starts at an even position)
+      if ((lo & 1u) == 0u && (reinterpret_cast<uintptr_t>(a.keys_out) & 15u) == 0u) {
+        const unsigned np = total / 2;
+        for (unsigned i = tid; i < np; i += kLocThreads)
+          reinterpret_cast<ulonglong2*>(out)[i] = reinterpret_cast<const ulonglong2*>(s_keys)[i];
+        if ((total & 1u) && tid == 0) out[total - 1] = s_keys[total - 1];
+      } else {
+        for (unsigned i = tid; i < total; i += kLocThreads) out[i] = s_keys[i];
+      }
+    }
+    __syncthreads();
   }
 }
 
+// padding at [boff[nb], n): the scan ends at the first padding key
+__global__ void __launch_bounds__(256) bucket_tail_kernel(uint64_t* keys, const unsigned long long* end_pos,
+                                                          uint64_t n) {
+  const uint64_t from = *end_pos;
+  for (uint64_t i = from + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    keys[i] = kSentinel;
+}
+
 // one thread per result: the bucket of its smallest racy cell
-__global__ void bucket_finish_kernel(FoldArgs fa) {
-  const uint32_t nr = fa.s.n_models ? fa.s.n_models : 1u;
+__global__ void bucket_finish_kernel(FinishArgs fa) {
+  const uint32_t nr = fa.n_models ? fa.n_models : 1u;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nr) return;
-  DevResult* r = fa.s.res + i;
+  DevResult* r = fa.res + i;
   const unsigned long long c = r->hash_cell;
   if (c == ~0ull) return;
   const uint64_t b = fa.D ? (cell_hash_of(c, fa.cmask) >> (fa.cb - fa.D)) : 0ull;
@@ -675,26 +551,25 @@ cudaError_t launch_bucket_whole(unsigned long long* boff, uint64_t n, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_fold(const FoldArgs& fa, cudaStream_t st) {
-  const size_t smem = fold_smem(fa.rbin);
-  const bool at = fa.s.thread_shift == 2, sy = fa.s.sync_tabs != nullptr;
-  const void* fn = at ? (sy ? reinterpret_cast<const void*>(bucket_fold_kernel<true, true>)
-                            : reinterpret_cast<const void*>(bucket_fold_kernel<true, false>))
-                      : (sy ? reinterpret_cast<const void*>(bucket_fold_kernel<false, true>)
-                            : reinterpret_cast<const void*>(bucket_fold_kernel<false, false>));
-  cudaError_t e = ensure_kernel_smem(fn, fold_smem(kFoldBinBits));
+cudaError_t launch_bucket_local_sort(const LocalSortArgs& a, cudaStream_t st) {
+  const bool h32 = a.cb <= 32;
+  const void* fn = h32 ? reinterpret_cast<const void*>(bucket_local_sort_kernel<true>)
+                       : reinterpret_cast<const void*>(bucket_local_sort_kernel<false>);
+  cudaError_t e = ensure_kernel_smem(fn, local_smem(kFoldBinBits));
   if (e != cudaSuccess) return e;
-  const uint64_t nb = 1ull << fa.D;
+  const uint64_t nb = 1ull << a.D;
   const unsigned grid = (unsigned)(nb < 152ull * 2 ? nb : 152ull * 2);
-  if (at && sy) bucket_fold_kernel<true, true><<<grid, kFoldThreads, smem, st>>>(fa);
-  else if (at) bucket_fold_kernel<true, false><<<grid, kFoldThreads, smem, st>>>(fa);
-  else if (sy) bucket_fold_kernel<false, true><<<grid, kFoldThreads, smem, st>>>(fa);
-  else bucket_fold_kernel<false, false><<<grid, kFoldThreads, smem, st>>>(fa);
+  const size_t smem = local_smem(a.rbin);
+  if (h32) bucket_local_sort_kernel<true><<<grid, kLocThreads, smem, st>>>(a);
+  else bucket_local_sort_kernel<false><<<grid, kLocThreads, smem, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bucket_tail_kernel<<<152, 256, 0, st>>>(a.keys_out, a.boff + nb, a.n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_finish(const FoldArgs& fa, cudaStream_t st) {
-  const uint32_t nr = fa.s.n_models ? fa.s.n_models : 1u;
+cudaError_t launch_bucket_finish(const FinishArgs& fa, cudaStream_t st) {
+  const uint32_t nr = fa.n_models ? fa.n_models : 1u;
   bucket_finish_kernel<<<(nr + 127) / 128, 128, 0, st>>>(fa);
   return cudaGetLastError();
 }

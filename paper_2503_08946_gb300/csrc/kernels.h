@@ -201,6 +201,9 @@ struct ScanArgs {
   // (block, fine interval) when wit_block_bits > 0 (models with more than one
   // grid interval), else by fine interval for the cell's lowest block only
   uint32_t wit_block_bits;
+  // keys grouped by cell but not in cell order (bucket path): the first racy
+  // cell is kept by value in DevResult.hash_cell (phase-table scan only)
+  uint32_t by_cell;
 };
 // the interval tables of a scan (no warp or grid barriers: q is the phase)
 struct SyncTabs {
@@ -210,21 +213,30 @@ struct SyncTabs {
 };
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);
-// bucket.cu: the fold of the bucket path over s.keys (grouped by bucket:
-// bucket b = keys [boff[b], boff[b+1]), b < 2^D); `scratch` is the other key
-// buffer (buckets larger than kFoldCap are grouped there).  Counts racy cells
-// and keeps the smallest racy cell in DevResult.hash_cell (per model in a
-// batch); bucket_finish then sets [min_start, seg_end) to that cell's bucket
-// and `cell` to the cell, for the witness kernels.
-struct FoldArgs {
-  ScanArgs s;
+// bucket.cu: the local sort of the bucket path: every bucket b = keys
+// [boff[b], boff[b+1]) of keys_in (b < 2^D) put in cell order by the remaining
+// bits of h and written to the same positions of keys_out (padding dropped;
+// keys_out[boff[2^D], n) filled with padding), so that the ordered cell scan
+// can fold it (with ScanArgs.by_cell).
+struct LocalSortArgs {
+  const uint64_t* keys_in;
+  uint64_t* keys_out;
+  uint64_t n;                       // key slots of both buffers
   const unsigned long long* boff;
-  uint64_t* scratch;
   uint64_t cmask;
-  uint32_t cb, D, rbin, r;
+  uint32_t cell_shift, cb, D, rbin, r;
 };
-cudaError_t launch_bucket_fold(const FoldArgs& a, cudaStream_t st);
-cudaError_t launch_bucket_finish(const FoldArgs& a, cudaStream_t st);
+cudaError_t launch_bucket_local_sort(const LocalSortArgs& a, cudaStream_t st);
+// per result: [min_start, seg_end) = the bucket of its smallest racy cell
+// (DevResult.hash_cell) and `cell` = that cell, for the witness kernels
+struct FinishArgs {
+  DevResult* res;
+  uint32_t n_models;                // 0: one result
+  const unsigned long long* boff;
+  uint64_t cmask;
+  uint32_t cb, D;
+};
+cudaError_t launch_bucket_finish(const FinishArgs& a, cudaStream_t st);
 cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n = 1);
 uint64_t scan_long_capacity(uint64_t n, uint32_t n_warps);
 

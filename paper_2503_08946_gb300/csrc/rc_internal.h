@@ -337,7 +337,7 @@ constexpr uint32_t kSortThreadsHost = 256;
 constexpr uint64_t kCellHashMul = 0x9E3779B97F4A7C15ull;
 constexpr uint32_t kBucketMaxDigitBits = 10;        // per partition pass
 constexpr uint32_t kBucketMaxBits = 2 * kBucketMaxDigitBits;
-constexpr int kFoldCap = 8192;                      // keys of a bucket folded in shared memory
+constexpr int kFoldCap = 7680;                      // keys of a bucket folded in shared memory
 constexpr uint32_t kFoldBinBits = 12;               // counting-sort bins of a bucket (at most)
 constexpr uint64_t kBucketTarget = kFoldCap / 2 + kFoldCap / 16;   // planned mean keys per bucket
 constexpr int kBucketHistTile = 16384;              // keys per block of the pass-B histogram
@@ -350,6 +350,7 @@ struct BucketPlan {
   uint64_t tiles_b = 0, tiles_h = 0;   // grid bounds of pass B and its histogram
   // workspace offsets (bytes) of the bucket section
   size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, hist_b = 0, boff = 0, cur_b = 0, temp = 0;
+  size_t scan_ctr = 0;            // the ordered scan's long-cell counter (in the cleared range)
   size_t zero_lo = 0, zero_hi = 0;    // cleared at the start of a check (the two histograms)
   size_t end = 0;
 };

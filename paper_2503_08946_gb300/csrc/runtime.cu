@@ -238,6 +238,8 @@ bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp) {
   off = align256(off + na * 8);
   bp->hist_b = off;
   off = align256(off + nb * 8);
+  bp->scan_ctr = off;
+  off = align256(off + 8);
   bp->zero_hi = off;
   bp->off_a = off;
   off = align256(off + (na + 1) * 8);
@@ -273,10 +275,14 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   p->keys_off[1] = off;
   off = align256(off + n * 8);
   if (allow_bucket && bucket_path_allowed(m.host.phase_bits, opts) && plan_buckets(n, cell_bits, off, &p->bucket)) {
-    // the bucket path: its own section instead of the radix-sort and scan sections
+    // the bucket path: its own section instead of the radix-sort sections
     p->zero_lo = p->bucket.zero_lo;
     p->zero_hi = p->bucket.zero_hi;
     off = p->bucket.end;
+    p->scanctr_off = p->bucket.scan_ctr;
+    p->long_cap = scan_long_capacity(n, p->scan_warps);
+    p->long_off = off;
+    off = align256(off + (size_t)p->long_cap * 8);
     p->group_off = off;
     off = align256(off + witness_group_bytes(m));
     p->total = off;
@@ -334,6 +340,7 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
                                                                   offsetof(rc::DevModel, sync_tab))
                               : nullptr;
   a.wit_block_bits = m.multi_grid ? m.host.block_bits : 0u;
+  a.by_cell = 0;
   return a;
 }
 
@@ -449,23 +456,41 @@ rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* bu
     }
   }
   if (s != RC_OK) return s;
-  rc::FoldArgs fa;
-  fa.s = sa;
-  fa.s.keys = fin;
-  fa.s.n = p.n_keys;
+  // the local sort into the other buffer, then the ordered cell scan with the
+  // first racy cell kept by value, then its bucket for the witness
+  rc::LocalSortArgs ls;
+  ls.keys_in = fin;
+  ls.keys_out = scratch;
+  ls.n = p.n_keys;
+  ls.boff = a.boff;
+  ls.cmask = a.cmask;
+  ls.cell_shift = sa.cell_shift;
+  ls.cb = bp.cb;
+  ls.D = bp.D;
+  ls.rbin = bp.rbin;
+  ls.r = bp.r;
+  s = cuda_status(rc::launch_bucket_local_sort(ls, st));
+  if (tm) { timed->i_pass_from[n_pass] = tm->n - 1; timed->i_pass_to[n_pass] = tm->n; tm->mark(); }
+  ++n_pass;
+  rc::ScanArgs sc = sa;
+  sc.keys = scratch;
+  sc.n = p.n_keys;
+  sc.by_cell = 1;
+  sc.phase_table = 1;
+  if (s == RC_OK) s = cuda_status(rc::launch_scan(sc, st));
+  rc::FinishArgs fa;
+  fa.res = sa.res;
+  fa.n_models = sa.n_models;
   fa.boff = a.boff;
-  fa.scratch = scratch;
   fa.cmask = a.cmask;
   fa.cb = bp.cb;
   fa.D = bp.D;
-  fa.rbin = bp.rbin;
-  fa.r = bp.r;
-  s = cuda_status(rc::launch_bucket_fold(fa, st));
   if (s == RC_OK) s = cuda_status(rc::launch_bucket_finish(fa, st));
   if (timed) {
     timed->n_pass = n_pass;
     timed->bucketed = true;
   }
+  fin = scratch;
   *final_keys = fin;
   return s;
 }
@@ -1059,6 +1084,11 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
       p.zero_lo = p.bucket.zero_lo;
       p.zero_hi = p.bucket.zero_hi;
       o = p.bucket.end;
+      p.scan_warps = scan_warps_for(k.n_keys);
+      p.scanctr_off = p.bucket.scan_ctr;
+      p.long_cap = rc::scan_long_capacity(k.n_keys, p.scan_warps);
+      p.long_off = o;
+      o = align256(o + (size_t)p.long_cap * 8);
       p.group_off = o;
       o = align256(o + (k.i1 - k.i0) * ((size_t)1 << (k.pb + (k.mg ? k.bb : 0u))) * rc::kWitnessGroupWords *
                            sizeof(unsigned int));

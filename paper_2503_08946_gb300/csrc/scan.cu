@@ -547,8 +547,11 @@ __device__ __forceinline__ void tfold_merge_warp(typename FoldOf<SY>::type& o, u
 }
 
 // AT: the model has atomic accesses (2-bit kind field: R = 0, W = 1, A = 2);
-// SY: it has warp or grid barriers (fine intervals, tfold_racy_sync)
-template <bool AT, bool SY>
+// SY: it has warp or grid barriers (fine intervals, tfold_racy_sync);
+// MC: the first racy cell is the smallest by cell value (DevResult.hash_cell),
+// for keys grouped by cell but not in cell order (the bucket path), else the
+// one at the smallest position (min_start, keys in cell order)
+template <bool AT, bool SY, bool MC>
 __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(ScanArgs a) {
   constexpr uint32_t kKindBits = AT ? 2 : 1;
   __shared__ unsigned tabs[kScanWarps][32 * kTabStride];
@@ -570,13 +573,14 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   if constexpr (SY) syt = sync_tabs_of(a);
   // count a racy cell and keep the first
   auto record = [&](const TF& x, const uint64_t start) {
+    const unsigned long long first = MC ? (unsigned long long)(x.fk >> a.cell_shift) : (unsigned long long)start;
     if (a.n_models) {
       DevResult* r = result_of(a, x.fk >> a.cell_shift);
       atomicAdd(&r->racy_cells, 1ull);
-      atomicMin(&r->min_start, (unsigned long long)start);
+      atomicMin(MC ? &r->hash_cell : &r->min_start, first);
     } else {
       ++count;
-      minstart = min(minstart, (unsigned long long)start);
+      minstart = min(minstart, first);
     }
   };
   auto report = [&](const TF& x, const unsigned* xtab, const uint64_t start) {
@@ -588,7 +592,8 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         if (!tfold_racy_sync<AT>(x, xtab, mt.coarse, mt.grid, tb)) return;
         DevResult* r = a.res + mi;
         atomicAdd(&r->racy_cells, 1ull);
-        atomicMin(&r->min_start, (unsigned long long)start);
+        if (MC) atomicMin(&r->hash_cell, (unsigned long long)(x.fk >> a.cell_shift));
+        else atomicMin(&r->min_start, (unsigned long long)start);
         return;
       }
       if (!tfold_racy_sync<AT>(x, xtab, syt.coarse, syt.grid, tb)) return;
@@ -760,7 +765,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     }
     if (lane == 0) {
       if (count) atomicAdd(&a.res->racy_cells, count);
-      if (minstart != ~0ull) atomicMin(&a.res->min_start, minstart);
+      if (minstart != ~0ull) atomicMin(MC ? &a.res->hash_cell : &a.res->min_start, minstart);
     }
   }
 }
@@ -821,7 +826,8 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
       if (racy) {
         DevResult* r = result_of(a, cell);
         atomicAdd(&r->racy_cells, 1ull);
-        atomicMin(&r->min_start, (unsigned long long)start);
+        if (a.by_cell) atomicMin(&r->hash_cell, (unsigned long long)cell);
+        else atomicMin(&r->min_start, (unsigned long long)start);
       }
     }
     __syncthreads();
@@ -1131,10 +1137,18 @@ cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
     const unsigned blocks = (a.n_warps + kScanWarps - 1) / kScanWarps;
     if (a.phase_table) {
       const bool at = a.thread_shift == 2, sy = a.sync_tabs != nullptr;
-      if (at && sy) scan_cells_table_kernel<true, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
-      else if (at) scan_cells_table_kernel<true, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
-      else if (sy) scan_cells_table_kernel<false, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
-      else scan_cells_table_kernel<false, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      const bool mc = a.by_cell != 0;
+      if (mc) {
+        if (at && sy) scan_cells_table_kernel<true, true, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else if (at) scan_cells_table_kernel<true, false, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else if (sy) scan_cells_table_kernel<false, true, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else scan_cells_table_kernel<false, false, true><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      } else {
+        if (at && sy) scan_cells_table_kernel<true, true, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else if (at) scan_cells_table_kernel<true, false, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else if (sy) scan_cells_table_kernel<false, true, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+        else scan_cells_table_kernel<false, false, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
+      }
     }
     else scan_cells_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();

@@ -1,6 +1,7 @@
 """The bucket path of the grouping step (partition passes on a bijective hash
-of the cell, then a counting sort and the cell fold per bucket in shared
-memory) against the CPU oracle, bit-exact: verdict, racy-cell count, instance
+of the cell, then a counting sort of every bucket in shared memory, then the
+ordered cell scan with the first racy cell kept by value) against the CPU
+oracle, bit-exact: verdict, racy-cell count, instance
 count and witness.  Covers the partition plans (no pass, one pass, two
 passes), bins holding several cells (cell spaces wider than the bucket and bin
 bits), buckets larger than shared memory (grouped in the other key buffer),
@@ -61,10 +62,11 @@ def plan_of(rc, model, opts=None):
 def test_path_selection(rc):
     b = rc.binding
     m = w.random_affine(3, n_blocks=64, block=256)
-    assert plan_of(rc, m) == (True, 2)                         # ~17M keys: two partition passes
+    # passes: the partition passes, then the local sort of every bucket
+    assert plan_of(rc, m) == (True, 3)                         # ~17M keys: two partition passes
     assert plan_of(rc, w.random_affine(3, n_blocks=1, block=256))[0]   # small: one pass or none
-    assert plan_of(rc, w.neighbor_write_read(64)) == (True, 0)  # 128 key slots: one bucket, no pass
-    assert plan_of(rc, w.reduction_tree(False)) == (True, 1)   # 6,144 key slots: one pass
+    assert plan_of(rc, w.neighbor_write_read(64)) == (True, 1)  # 128 key slots: one bucket, no pass
+    assert plan_of(rc, w.reduction_tree(False)) == (True, 2)   # 6,144 key slots: one pass
     assert plan_of(rc, m, {"flags": b.RC_OPT_LSD})[0] is False
     assert plan_of(rc, m, {"digit_bits": 8})[0] is False
     many = Model((2, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
