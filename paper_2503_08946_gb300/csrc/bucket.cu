@@ -343,17 +343,33 @@ __global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
 constexpr int kLocThreads = 512;
 constexpr int kLocKPT = (kFoldCap + kLocThreads - 1) / kLocThreads;   // keys per thread of a bucket in registers
 
-size_t local_smem(uint32_t rbin) { return (size_t)kFoldCap * 8 + ((size_t)4 << rbin); }
+size_t local_smem(uint32_t rbin) { return (size_t)kFoldCap * 8 + ((size_t)8 << rbin); }   // keys, bins, cursors
 
-// exclusive scan in place of n counters by the block
-__device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n) {
-  __shared__ unsigned wsum[kLocThreads / 32];
+// Exclusive scan in place of n counters by a block of NT threads (each thread
+// a run of consecutive counters, read and written 16 bytes at a time when the
+// run is a multiple of 4); *total receives the sum.
+template <int NT>
+__device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n, unsigned* total) {
+  static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, at most 32");
+  __shared__ unsigned wsum[NT / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned per = (n + kLocThreads - 1) / kLocThreads;
+  const unsigned per = (n + NT - 1) / NT;
   const unsigned b0 = threadIdx.x * per;
+  const bool vec = (per & 3u) == 0u && b0 + per <= n;
+  unsigned v[8];
   unsigned s = 0;
-  for (unsigned i = 0; i < per; ++i)
-    if (b0 + i < n) s += bin[b0 + i];
+  if (vec && per <= 8) {
+#pragma unroll
+    for (unsigned i = 0; i < 8; i += 4)
+      if (i < per) {
+        const uint4 x = *reinterpret_cast<const uint4*>(bin + b0 + i);
+        v[i] = x.x; v[i + 1] = x.y; v[i + 2] = x.z; v[i + 3] = x.w;
+        s += x.x + x.y + x.z + x.w;
+      }
+  } else {
+    for (unsigned i = 0; i < per; ++i)
+      if (b0 + i < n) s += bin[b0 + i];
+  }
   unsigned x = s;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -363,22 +379,36 @@ __device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n) {
   if (lane == 31) wsum[w] = x;
   __syncthreads();
   if (w == 0) {
-    unsigned t = lane < kLocThreads / 32 ? wsum[lane] : 0u;
+    unsigned t = lane < NT / 32 ? wsum[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(FULL, t, o);
       if (lane >= o) t += y;
     }
-    if (lane < kLocThreads / 32) wsum[lane] = t;   // inclusive over warps
+    if (lane < NT / 32) wsum[lane] = t;   // inclusive over warps
+    if (lane == NT / 32 - 1) *total = t;
   }
   __syncthreads();
   unsigned run = (w ? wsum[w - 1] : 0u) + x - s;
-  for (unsigned i = 0; i < per; ++i)
-    if (b0 + i < n) {
-      const unsigned c = bin[b0 + i];
-      bin[b0 + i] = run;
-      run += c;
-    }
+  if (vec && per <= 8) {
+#pragma unroll
+    for (unsigned i = 0; i < 8; i += 4)
+      if (i < per) {
+        uint4 o;
+        o.x = run; run += v[i];
+        o.y = run; run += v[i + 1];
+        o.z = run; run += v[i + 2];
+        o.w = run; run += v[i + 3];
+        *reinterpret_cast<uint4*>(bin + b0 + i) = o;
+      }
+  } else {
+    for (unsigned i = 0; i < per; ++i)
+      if (b0 + i < n) {
+        const unsigned c = bin[b0 + i];
+        bin[b0 + i] = run;
+        run += c;
+      }
+  }
 }
 
 // Each bucket [boff[b], boff[b+1]) of keys_in is counting-sorted by the rbin
@@ -402,6 +432,7 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
   const uint32_t cs = a.cell_shift;
   const uint64_t nb = 1ull << a.D;
   const int tid = threadIdx.x;
+  __shared__ unsigned s_total;
   auto bin_of = [&](uint64_t k) -> unsigned {
     if constexpr (H32) {
       const uint32_t h = (uint32_t)(k >> cs) * (uint32_t)kCellHashMul;
@@ -409,6 +440,9 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
     }
     return (unsigned)(cell_hash_of(k >> cs, a.cmask) >> bin_shift) & (nbins - 1u);
   };
+  // bin g's keys after the scatter: [bin_start(g), bin_end(g))
+  auto bin_start = [&](unsigned g) { return s_bin[g]; };
+  auto bin_end = [&](unsigned g) { return g + 1 < nbins ? s_bin[g + 1] : s_total; };
   for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const uint64_t lo = a.boff[b], hi = a.boff[b + 1];
     if (hi <= lo) continue;
@@ -417,9 +451,14 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
     const uint64_t* src = a.keys_in + lo;
     uint64_t* out = a.keys_out + lo;
     uint64_t* dst = in_smem ? s_keys : out;
-    for (unsigned i = tid; i < nbins; i += kLocThreads) s_bin[i] = 0;
+    if ((nbins & 3u) == 0u) {
+      for (unsigned i = 4 * tid; i < nbins; i += 4 * kLocThreads) *reinterpret_cast<uint4*>(s_bin + i) = make_uint4(0, 0, 0, 0);
+    } else {
+      for (unsigned i = tid; i < nbins; i += kLocThreads) s_bin[i] = 0;
+    }
     __syncthreads();
     if (in_smem) {
+      // one read of the bucket into registers, all loads in flight together
       uint64_t kr[kLocKPT];
 #pragma unroll
       for (int q = 0; q < kLocKPT; ++q) {
@@ -430,30 +469,37 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
       for (int q = 0; q < kLocKPT; ++q)
         if (kr[q] != kSentinel) atomicAdd(&s_bin[bin_of(kr[q])], 1u);
       __syncthreads();
-      bin_scan(s_bin, nbins);
+      bin_scan<kLocThreads>(s_bin, nbins, &s_total);
+      __syncthreads();
+      // the cursors live in the bins' copy: starts stay in s_bin for the ranges below
+      unsigned* cur = s_bin + nbins;
+      for (unsigned i = tid; i < nbins; i += kLocThreads) cur[i] = s_bin[i];
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < kLocKPT; ++q)
-        if (kr[q] != kSentinel) s_keys[atomicAdd(&s_bin[bin_of(kr[q])], 1u)] = kr[q];
+        if (kr[q] != kSentinel) s_keys[atomicAdd(&cur[bin_of(kr[q])], 1u)] = kr[q];
     } else {
+      // read twice from global memory; the cursors live in the (unused) key buffer
+      unsigned* cur = reinterpret_cast<unsigned*>(s_keys);
       for (uint64_t i = tid; i < len; i += kLocThreads) {
         const uint64_t k = src[i];
         if (k != kSentinel) atomicAdd(&s_bin[bin_of(k)], 1u);
       }
       __syncthreads();
-      bin_scan(s_bin, nbins);
+      bin_scan<kLocThreads>(s_bin, nbins, &s_total);
+      __syncthreads();
+      for (unsigned i = tid; i < nbins; i += kLocThreads) cur[i] = s_bin[i];
       __syncthreads();
       for (uint64_t i = tid; i < len; i += kLocThreads) {
         const uint64_t k = src[i];
-        if (k != kSentinel) dst[atomicAdd(&s_bin[bin_of(k)], 1u)] = k;
+        if (k != kSentinel) dst[atomicAdd(&cur[bin_of(k)], 1u)] = k;
       }
     }
     __syncthreads();
-    // s_bin[g] is now the end of bin g; total = keys kept
-    const unsigned total = s_bin[nbins - 1];
+    const unsigned total = s_total;
     if (multi) {
       for (unsigned g = tid; g < nbins; g += kLocThreads) {
-        const unsigned s = g ? s_bin[g - 1] : 0u, e = s_bin[g];
+        const unsigned s = bin_start(g), e = bin_end(g);
         bool one = true;
         for (unsigned i = s + 1; i < e && one; ++i) one = (dst[i] >> cs) == (dst[s] >> cs);
         if (one) continue;
@@ -480,6 +526,9 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
         for (unsigned i = tid; i < total; i += kLocThreads) out[i] = s_keys[i];
       }
     }
+    // padding keys dropped from the bucket: its tail becomes padding (only the
+    // unpartitioned single bucket, the last one, holds any)
+    for (uint64_t i = total + tid; i < len; i += kLocThreads) out[i] = kSentinel;
     __syncthreads();
   }
 }

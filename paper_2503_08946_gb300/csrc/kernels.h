@@ -225,6 +225,7 @@ struct LocalSortArgs {
   const unsigned long long* boff;
   uint64_t cmask;
   uint32_t cell_shift, cb, D, rbin, r;
+  unsigned int* err;
 };
 cudaError_t launch_bucket_local_sort(const LocalSortArgs& a, cudaStream_t st);
 // per result: [min_start, seg_end) = the bucket of its smallest racy cell

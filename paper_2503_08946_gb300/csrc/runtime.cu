@@ -469,6 +469,7 @@ rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* bu
   ls.D = bp.D;
   ls.rbin = bp.rbin;
   ls.r = bp.r;
+  ls.err = sa.err;
   s = cuda_status(rc::launch_bucket_local_sort(ls, st));
   if (tm) { timed->i_pass_from[n_pass] = tm->n - 1; timed->i_pass_to[n_pass] = tm->n; tm->mark(); }
   ++n_pass;

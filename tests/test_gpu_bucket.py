@@ -198,3 +198,21 @@ def test_batch_bucket_path(rc, graph):
     lo = {"flags": b.RC_OPT_LSD}
     lsd = b.rc_report(b.rc_check_batch(hs, lo, b.workspace(b.rc_batch_workspace_size(hs, lo))), wait=True)
     assert [full(a) for a in got] == [full(x) for x in lsd]
+
+
+def test_padding_with_reused_workspace(rc):
+    """Models with guard-false padding slots checked one after another in one
+    workspace: the bucket's dropped padding must not leave earlier keys in the
+    scanned range (the single unpartitioned bucket, one partition pass)."""
+    b = rc.binding
+    models = [w.atomic_counter(256, 1, True), w.reduction_tree(True), w.atomic_counter(256, 1, False),
+              w.random_affine(3, n_blocks=2, block=256, n_threads=300), w.neighbor_write_read(64),
+              w.atomic_counter(1024, 4, True)]
+    hs = [b.rc_model_create(m) for m in models]
+    ws = b.workspace(max(b.rc_workspace_size(h, None) for h in hs))
+    ws.fill_(0x5A)   # stale contents
+    for rep in range(2):
+        for m, h in zip(models, hs):
+            g = b.rc_report(b.rc_check(h, None, ws), wait=True)[0]
+            exp = oracle.check(m)
+            assert full(g) == full(exp), (rep, m.name, g, exp)
