@@ -159,23 +159,26 @@ __global__ void bucket_whole_kernel(unsigned long long* boff, uint64_t n) {
 //              bits, cursors of that A-bucket's buckets.
 // ---------------------------------------------------------------------------
 constexpr int kPThreads = kSortThreads;
-constexpr int kPItems = 12;
+constexpr int kPItems = 16;
 constexpr int kPTile = kPThreads * kPItems;
 static_assert(kPTile == kPartTileHost, "pass-B tiles are planned with the host's tile size");
 
 template <int RB>
 constexpr size_t bpart_smem() {
-  return (size_t)kPTile * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
+  return (size_t)(kPTile + 2) * 8 + (size_t)(1 << RB) * (4 + 4 + 8);
 }
 
-template <int RB, bool B>
-__global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketArgs a) {
+// H32: the cell field has at most 32 bits, so h is computed in 32-bit
+// arithmetic (the product modulo 2^cb depends only on the low 32 bits of each
+// factor).
+template <int RB, bool B, bool H32>
+__global__ void __launch_bounds__(kPThreads, 4) bucket_partition_kernel(BucketArgs a) {
   constexpr int R = 1 << RB;
   constexpr int DPT = (R + kPThreads - 1) / kPThreads;
   constexpr int kWarps = kPThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);
-  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kPTile);           // [R]
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(smem);                            // [kPTile + 2]
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(s_keys + kPTile + 2);       // [R]
   unsigned int* excl = cnt + R;                                                     // [R]
   unsigned long long* delta = reinterpret_cast<unsigned long long*>(excl + R);      // [R]
   __shared__ unsigned int s_wt[kWarps];
@@ -204,18 +207,30 @@ __global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketAr
     dbits = a.dB;
   }
   const unsigned dmask = (1u << dbits) - 1u;
-  auto digit = [&](uint64_t k) { return (unsigned)(cell_hash_of(k >> a.cell_shift, a.cmask) >> sh) & dmask; };
+  const uint32_t cs = a.cell_shift;
+  auto digit = [&](uint64_t k) -> unsigned {
+    if constexpr (H32) return (((uint32_t)(k >> cs) * (uint32_t)kCellHashMul) >> sh) & dmask;
+    return (unsigned)(cell_hash_of(k >> cs, a.cmask) >> sh) & dmask;
+  };
 
   for (int i = threadIdx.x; i < R; i += kPThreads) cnt[i] = 0;
-  // the tile into shared memory: 16-byte copies for a full tile at an even
-  // key position of a 16-byte aligned buffer, else 8-byte copies
+  // the tile into shared memory by 16-byte copies where it can be: a full tile
+  // of a 16-byte aligned buffer at an even key position, or at an odd one
+  // widened by a key on each side (kept inside the buffer: the key after the
+  // tile exists); else 8-byte copies.  Key j of the tile is s_keys[off + j].
   const bool full = len == (uint64_t)kPTile;
-  if (full && (t0 & 1u) == 0u && (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u) {
+  const bool al16 = (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u;
+  int off = 0;
+  if (full && al16 && (t0 & 1u) == 0u) {
 #pragma unroll
     for (int m = 0; m < kPTile / 2 / kPThreads; ++m) {
       const int j = m * kPThreads + (int)threadIdx.x;
       cp_async16(s_keys + 2 * j, a.keys_in + t0 + 2 * j);
     }
+  } else if (full && al16 && t0 + kPTile < a.n) {
+    off = 1;
+    for (int j = threadIdx.x; j < kPTile / 2 + 1; j += kPThreads)
+      cp_async16(s_keys + 2 * j, a.keys_in + (t0 - 1) + 2 * j);
   } else {
     for (int j = threadIdx.x; j < (int)len; j += kPThreads) cp_async8(s_keys + j, a.keys_in + t0 + j);
   }
@@ -223,11 +238,11 @@ __global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketAr
   __syncthreads();
 
   const int lpos = w * (32 * kPItems) + lane;
-  unsigned short r[kPItems];
+  unsigned short r[kPItems];   // rank inside the digit (0xffff: no key)
 #pragma unroll
   for (int i = 0; i < kPItems; ++i) {
     const int j = lpos + i * 32;
-    const uint64_t k = j < (int)len ? s_keys[j] : kSentinel;
+    const uint64_t k = j < (int)len ? s_keys[off + j] : kSentinel;
     const bool valid = j < (int)len && (B || k != kSentinel);
     const unsigned d = valid ? digit(k) : 0u;
     const unsigned d0 = __shfl_sync(FULL, d, 0);
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketAr
     } else if (valid) {
       rank = atomicAdd(&cnt[d], 1u);
     }
-    r[i] = (unsigned short)rank;
+    r[i] = valid ? (unsigned short)rank : (unsigned short)0xffffu;
   }
   __syncthreads();
   // per digit: claim the output range, tile offsets
@@ -275,14 +290,12 @@ __global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketAr
 #pragma unroll
   for (int i = 0; i < kPItems; ++i) {
     const int j = lpos + i * 32;
-    kk[i] = j < (int)len ? s_keys[j] : kSentinel;
+    kk[i] = j < (int)len ? s_keys[off + j] : kSentinel;
   }
   __syncthreads();   // every key read before any is overwritten
 #pragma unroll
-  for (int i = 0; i < kPItems; ++i) {
-    const int j = lpos + i * 32;
-    if (j < (int)len && (B || kk[i] != kSentinel)) s_keys[excl[digit(kk[i])] + r[i]] = kk[i];
-  }
+  for (int i = 0; i < kPItems; ++i)
+    if (r[i] != 0xffffu) s_keys[excl[digit(kk[i])] + r[i]] = kk[i];
   __syncthreads();
   // carry = valid keys of the tile
   for (int pos = threadIdx.x; pos < (int)carry; pos += kPThreads) {
@@ -297,9 +310,13 @@ __global__ void __launch_bounds__(kPThreads, 5) bucket_partition_kernel(BucketAr
 template <int RB, bool B>
 cudaError_t launch_bpart_rb(const BucketArgs& a, uint64_t grid, cudaStream_t st) {
   constexpr size_t smem = bpart_smem<RB>();
-  const cudaError_t e = ensure_kernel_smem(reinterpret_cast<const void*>(bucket_partition_kernel<RB, B>), smem);
+  const bool h32 = a.cb <= 32;
+  const void* fn = h32 ? reinterpret_cast<const void*>(bucket_partition_kernel<RB, B, true>)
+                       : reinterpret_cast<const void*>(bucket_partition_kernel<RB, B, false>);
+  const cudaError_t e = ensure_kernel_smem(fn, smem);
   if (e != cudaSuccess) return e;
-  bucket_partition_kernel<RB, B><<<(unsigned)grid, kPThreads, smem, st>>>(a);
+  if (h32) bucket_partition_kernel<RB, B, true><<<(unsigned)grid, kPThreads, smem, st>>>(a);
+  else bucket_partition_kernel<RB, B, false><<<(unsigned)grid, kPThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -326,12 +343,26 @@ __global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
   const uint64_t s = a.off_a[d1] + (t - a.tpref_h[d1]) * kBucketHistTile;
   const uint64_t e = min(s + kBucketHistTile, (uint64_t)a.off_a[d1 + 1]);
   const uint32_t sh = a.cb - a.dA - a.dB;
+  const uint32_t cs = a.cell_shift;
+  const bool h32 = a.cb <= 32;
   for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
   __syncthreads();
-  for (uint64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-    const uint64_t k = __ldg(a.keys_in + i);
-    atomicAdd(&h[(unsigned)(cell_hash_of(k >> a.cell_shift, a.cmask) >> sh) & (nb - 1u)], 1u);
+  auto count = [&](uint64_t k) {
+    const unsigned d = h32 ? (((uint32_t)(k >> cs) * (uint32_t)kCellHashMul) >> sh)
+                           : (unsigned)(cell_hash_of(k >> cs, a.cmask) >> sh);
+    atomicAdd(&h[d & (nb - 1u)], 1u);
+  };
+  // eight loads of each thread in flight together
+  constexpr int kU = 8;
+  uint64_t i = s + threadIdx.x;
+  for (; i + (kU - 1) * 256 < e; i += kU * 256) {
+    uint64_t k[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) k[u] = __ldg(a.keys_in + i + u * 256);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) count(k[u]);
   }
+  for (; i < e; i += 256) count(__ldg(a.keys_in + i));
   __syncthreads();
   for (unsigned d = threadIdx.x; d < nb; d += blockDim.x)
     if (h[d]) atomicAdd(&a.hist_b[((uint64_t)d1 << a.dB) | d], (unsigned long long)h[d]);

@@ -341,7 +341,7 @@ constexpr int kFoldCap = 7680;                      // keys of a bucket folded i
 constexpr uint32_t kFoldBinBits = 12;               // counting-sort bins of a bucket (at most)
 constexpr uint64_t kBucketTarget = kFoldCap / 2 + kFoldCap / 16;   // planned mean keys per bucket
 constexpr int kBucketHistTile = 16384;              // keys per block of the pass-B histogram
-constexpr int kPartTileHost = kSortThreadsHost * 12;    // keys per tile of the partition passes
+constexpr int kPartTileHost = kSortThreadsHost * 16;    // keys per tile of the partition passes
 
 struct BucketPlan {
   bool on = false;
