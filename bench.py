@@ -347,13 +347,17 @@ def run_native(args):
     # a batch of 10,000 small models against one check per model, a Poisson
     # request stream through the server
     subs = {}
-    if not args.no_sub:
+    which = [] if args.no_sub else [x for x in args.sub.split(",") if x]
+    if which:
         del ws
         torch.cuda.empty_cache()
+    if "hash" in which:
         subs["hash"] = hash_measure(rc, h, model, expect_racy, stream, steps=3)
         torch.cuda.empty_cache()
+    if "batch" in which:
         subs["batch"] = batch_measure(args, rc, w, torch, rank, world, dist, steps=5, pm_steps=1, compact=True)
         torch.cuda.empty_cache()
+    if "serve" in which:
         subs["serve"] = serve_measure(args, rc, w, torch, rank, world, dist, n_requests=2000, compact=True)
 
     cpu = None
@@ -781,6 +785,8 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sub", default="hash,batch,serve",
+                    help="default workload: which sub-records to add (comma-separated of hash, batch, serve)")
     ap.add_argument("--no-sub", action="store_true",
                     help="default workload: skip the hash, batch and serve sub-records")
     ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve", "wide"],
