@@ -103,7 +103,8 @@ const char* rc_status_str(rc_status s);
  *   RC_OP_LOAD   pop a, push tables[arg].data[a]: a data-dependent value such as
  *                the row bounds rowPtr[i], rowPtr[i + 1] of a sparse matrix (the
  *                paper's rs / re of Ge-SpMM, Section "Problems to deal with",
- *                made concrete instead of over-approximated by a superset).
+ *                made concrete; a table with superset = 1 over-approximates
+ *                them instead, see rc_table).
  *                A table reads as 0 outside [0, len) (a total function, so a
  *                load needs no out-of-bounds report).
  * A well-formed expression leaves exactly one value. */
@@ -151,10 +152,27 @@ typedef struct rc_array {
   int64_t extent[4];       /* sizes of the dimensions, each >= 1                  */
 } rc_array;
 
-/* A read-only integer table for RC_OP_LOAD (copied by rc_model_create). */
+/* A read-only integer table for RC_OP_LOAD (copied by rc_model_create).
+ *
+ * superset = 0: the loads read the values (concrete bounds).
+ * superset = 1: the values are unknown, only their range [lo, hi] is stated:
+ *   the paper's superset domain for bounds that depend on data (Section
+ *   "Problems to deal with"; the free rs, re of the Ge-SpMM Domain).  In every
+ *   statement each distinct load of this table (distinct by its expression:
+ *   the same expression twice is one parameter) is replaced by a free
+ *   parameter that ranges over [lo, hi], and the statement has an instance for
+ *   every value of its free parameters.  The checked domain is a superset of
+ *   every concrete one whose values lie in [lo, hi]: race-free means race-free
+ *   for all such data, a race may be a false positive.  Different statements
+ *   get independent parameters.  data may be NULL and len 0 (the values are
+ *   not read).  Each free parameter takes one loop level (the statement's
+ *   loops plus its free parameters <= max_loops, RC_E_UNSUPPORTED otherwise);
+ *   lo > hi, or a bound outside [-2^62, 2^62], is RC_E_INVALID. */
 typedef struct rc_table {
   const int64_t* data;     /* host memory, len values                             */
   uint64_t len;
+  uint32_t superset;       /* 0 or 1 (above)                                      */
+  int64_t lo, hi;          /* the stated value range (superset = 1 only)          */
 } rc_table;
 
 typedef struct rc_model_desc {

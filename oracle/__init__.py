@@ -116,10 +116,16 @@ def model_text(m) -> str:
            "wphases %d" % getattr(m, "n_warp_phases", 1)]
     gp = list(getattr(m, "grid_phase", None) or [])
     out.append("gridphase %d %s" % (len(gp), " ".join(str(int(g)) for g in gp)))
-    tables = getattr(m, "tables", None) or []
-    out.append("tables %d" % len(tables))
-    for t in tables:
-        out.append("%d %s" % (len(t), " ".join(str(int(v)) for v in t)))
+    tables = list(getattr(m, "tables", None) or [])
+    free = dict(getattr(m, "superset", None) or {})
+    n_tab = max([len(tables)] + [int(t) + 1 for t in free])
+    out.append("tables %d" % n_tab)
+    for i in range(n_tab):
+        if i in free:
+            out.append("free %d %d" % (int(free[i][0]), int(free[i][1])))
+        else:
+            t = tables[i] if i < len(tables) else []
+            out.append("%d %s" % (len(t), " ".join(str(int(v)) for v in t)))
     out.append("arrays %d" % len(m.arrays))
     for a in m.arrays:
         out.append("%s %d %s" % ("S" if a.scope == "shared" else "G", len(a.extents),

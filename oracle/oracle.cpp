@@ -48,6 +48,13 @@
 //    instance.  Quasi-affine floor division rounds toward minus infinity and
 //    modulo is Euclidean (result in [0, d)), as in the Presburger
 //    floor/mod of the paper's Ge-SpMM model (j % 32).
+//  * Data-dependent values: a load reads an integer table of the model (0
+//    outside it).  A table whose values are unknown and only bounded, lo <= v
+//    <= hi, gives the paper's superset domain (Section "Problems to deal
+//    with"; the free rs, re, ptr of the Ge-SpMM Domain listing): each of its
+//    loads in a statement is a free parameter of that statement, loads with
+//    the same expression being one parameter, and the statement has an
+//    instance for every value in [lo, hi] of every free parameter.
 //  * Errors: an index outside its extent, or an interval outside
 //    [0, n_phases), makes the status OUT_OF_BOUNDS; the smallest
 //    (statement, access, gtid, dimcode) over the offending instances is reported
@@ -88,11 +95,11 @@ namespace {
 // ----------------------------------------------------------------------------
 // model
 // ----------------------------------------------------------------------------
-enum Op { C_CONST, C_TID, C_BID, C_PARAM, C_ITER, C_ADD, C_MUL, C_FDIV, C_MOD, C_LOAD };
+enum Op { C_CONST, C_TID, C_BID, C_PARAM, C_ITER, C_ADD, C_MUL, C_FDIV, C_MOD, C_LOAD, C_FREE };
 
 struct Node {
   Op op;
-  int64_t v;   // constant, axis, parameter number, loop level, multiplier, divisor or table
+  int64_t v;   // constant, axis, parameter number, loop level, multiplier, divisor, table or free parameter
   int a, b;    // operand node indices (or -1)
 };
 
@@ -109,6 +116,7 @@ struct Stmt {
   std::vector<Loop> loops;
   std::vector<Expr> guards;
   std::vector<Access> accesses;
+  std::vector<int64_t> free_lo, free_hi;   // ranges of the statement's free parameters (superset tables)
 };
 struct Array { bool shared; std::vector<int64_t> ext; };
 struct Model {
@@ -118,6 +126,8 @@ struct Model {
   int64_t n_wphases = 1;                      // warp intervals per block interval
   std::vector<int64_t> grid_phase;            // grid interval of each block interval
   std::vector<std::vector<int64_t>> tables;   // integer tables read by loads (0 outside)
+  std::vector<bool> table_free;               // superset tables: values unknown, in [lo, hi]
+  std::vector<int64_t> table_lo, table_hi;
   std::vector<Array> arrays;
   std::vector<Stmt> stmts;
 };
@@ -216,10 +226,23 @@ struct Parser {
     expect("tables");
     int64_t nt = integer();
     for (int64_t t = 0; t < nt; ++t) {
-      int64_t len = integer();
       std::vector<int64_t> v;
+      if (next() == "free") {
+        const int64_t lo = integer(), hi = integer();
+        if (lo > hi) throw std::runtime_error("empty superset range");
+        m.tables.push_back(v);
+        m.table_free.push_back(true);
+        m.table_lo.push_back(lo);
+        m.table_hi.push_back(hi);
+        continue;
+      }
+      pos--;
+      int64_t len = integer();
       for (int64_t k = 0; k < len; ++k) v.push_back(integer());
       m.tables.push_back(v);
+      m.table_free.push_back(false);
+      m.table_lo.push_back(0);
+      m.table_hi.push_back(0);
     }
     n_tables = m.tables.size();
     expect("arrays");
@@ -269,10 +292,55 @@ struct Parser {
         for (int64_t d = 0; d < nd; ++d) a.index.push_back(expr());
         s.accesses.push_back(a);
       }
+      free_parameters(m, s);
       m.stmts.push_back(s);
     }
     expect("end");
     return m;
+  }
+
+  // The superset domain (Section "Problems to deal with"): a load of a table
+  // whose values are unknown is a free parameter of the statement, ranging
+  // over the table's stated [lo, hi].  Loads written the same way (the same
+  // expression) are one parameter; the node of each outermost such load
+  // becomes a reference to its parameter.
+  static std::string text_of(const Expr& e, int n) {
+    const Node& x = e.nodes[n];
+    std::string r = "(" + std::to_string((int)x.op) + ":" + std::to_string(x.v);
+    if (x.a >= 0) r += " " + text_of(e, x.a);
+    if (x.b >= 0) r += " " + text_of(e, x.b);
+    return r + ")";
+  }
+  static void free_in(const Model& m, Expr& e, int n, std::vector<std::string>& seen, Stmt& s) {
+    if (n < 0) return;
+    Node& x = e.nodes[n];
+    if (x.op == C_LOAD && m.table_free[(size_t)x.v]) {
+      const std::string key = text_of(e, n);
+      size_t id = 0;
+      while (id < seen.size() && seen[id] != key) ++id;
+      if (id == seen.size()) {
+        seen.push_back(key);
+        s.free_lo.push_back(m.table_lo[(size_t)x.v]);
+        s.free_hi.push_back(m.table_hi[(size_t)x.v]);
+      }
+      x.op = C_FREE;
+      x.v = (int64_t)id;
+      return;
+    }
+    const int a = x.a, b = x.b;
+    free_in(m, e, a, seen, s);
+    free_in(m, e, b, seen, s);
+  }
+  static void free_parameters(const Model& m, Stmt& s) {
+    std::vector<std::string> seen;
+    auto one = [&](Expr& e) { free_in(m, e, e.root, seen, s); };
+    one(s.phase);
+    one(s.wphase);
+    for (Loop& l : s.loops) { one(l.lower); one(l.upper); }
+    for (Expr& g : s.guards) one(g);
+    for (Access& a : s.accesses)
+      for (Expr& x : a.index) one(x);
+    if (s.free_lo.size() > 16) throw std::runtime_error("too many free parameters");
   }
 };
 
@@ -285,6 +353,7 @@ struct Env {
   const std::vector<int64_t>* params;
   const std::vector<std::vector<int64_t>>* tables;
   int64_t iter[16];
+  int64_t free[16];   // values of the statement's free parameters
 };
 
 int64_t wrap_add(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
@@ -321,6 +390,7 @@ int64_t eval(const Expr& e, int n, const Env& env) {
       const int64_t i = eval(e, x.a, env);
       return (i < 0 || i >= (int64_t)t.size()) ? 0 : t[i];
     }
+    case C_FREE: return env.free[x.v];
   }
   return 0;
 }
@@ -436,6 +506,18 @@ struct Enumerator {
     }
   }
 
+  // every value of every free parameter, then the loop nest
+  void frees(int64_t si, const Stmt& st, size_t k, Env& env, int64_t b, int64_t t, int64_t gtid) {
+    if (k == st.free_lo.size()) {
+      loops(si, st, 0, env, b, t, gtid);
+      return;
+    }
+    for (int64_t v = st.free_lo[k]; v <= st.free_hi[k]; ++v) {
+      env.free[k] = v;
+      frees(si, st, k + 1, env, b, t, gtid);
+    }
+  }
+
   void run() {
     const int64_t bsize = m.block[0] * m.block[1] * m.block[2];
     Env env;
@@ -452,7 +534,7 @@ struct Enumerator {
                 const int64_t t = tx + m.block[0] * (ty + m.block[1] * tz);
                 env.tid[0] = tx; env.tid[1] = ty; env.tid[2] = tz;
                 for (size_t si = 0; si < m.stmts.size(); ++si)
-                  loops((int64_t)si, m.stmts[si], 0, env, b, t, b * bsize + t);
+                  frees((int64_t)si, m.stmts[si], 0, env, b, t, b * bsize + t);
               }
         }
   }

@@ -90,7 +90,8 @@ class rc_array(Structure):
 
 
 class rc_table(Structure):
-    _fields_ = [("data", POINTER(c_int64)), ("len", c_uint64)]
+    _fields_ = [("data", POINTER(c_int64)), ("len", c_uint64), ("superset", c_uint32), ("lo", c_int64),
+                ("hi", c_int64)]
 
 
 class rc_model_desc(Structure):
@@ -333,17 +334,23 @@ class _Desc:
         self.keep.append(stmts)
         d.stmts = stmts
         d.n_stmts = len(model.stmts)
-        tables = getattr(model, "tables", None) or []
-        if tables:
-            tabs = (rc_table * len(tables))()
-            for i, t in enumerate(tables):
+        tables = list(getattr(model, "tables", None) or [])
+        superset = dict(getattr(model, "superset", None) or {})
+        n_tab = max([len(tables)] + [int(t) + 1 for t in superset])
+        if n_tab:
+            tabs = (rc_table * n_tab)()
+            for i in range(n_tab):
+                t = tables[i] if i < len(tables) else []
                 data = (c_int64 * max(1, len(t)))(*[int(v) for v in t])
                 self.keep.append(data)
                 tabs[i].data = ctypes.cast(data, POINTER(c_int64))
                 tabs[i].len = len(t)
+                if i in superset:
+                    tabs[i].superset = 1
+                    tabs[i].lo, tabs[i].hi = (int(v) for v in superset[i])
             self.keep.append(tabs)
             d.tables = tabs
-        d.n_tables = len(tables)
+        d.n_tables = n_tab
         d.n_warp_phases = int(getattr(model, "n_warp_phases", 1))
         gp = list(getattr(model, "grid_phase", None) or [])
         if gp:

@@ -13,6 +13,7 @@
 // 64-bit key layout [cell | phase | block | thread | kind].
 #include <algorithm>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <tuple>
 
@@ -216,10 +217,205 @@ bool mul_ok(uint64_t a, uint64_t b, uint64_t* r) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// ---------------------------------------------------------------------------
+// The superset domain (Section "Problems to deal with"; the free rs, re of the
+// Ge-SpMM Domain): every distinct load of a table flagged superset becomes a
+// free parameter of its statement, ranging over the table's stated [lo, hi].
+// The rewrite makes each parameter an outermost loop of the statement (lower
+// lo, upper hi + 1, step 1) and replaces the load's whole subexpression by
+// that loop's iterator; the statement's own loops move inward.  Where in the
+// nest a parameter's loop sits does not change the instance set: an instance
+// is fixed by its loop point and the one value of each parameter it uses.
+// ---------------------------------------------------------------------------
+struct SupersetDesc {
+  rc_model_desc desc;
+  std::vector<rc_table> tables;
+  std::vector<rc_stmt> stmts;
+  std::deque<std::vector<rc_insn>> code;      // owned expression code (stable addresses)
+  std::deque<std::vector<rc_loop>> loops;
+  std::deque<std::vector<rc_expr>> exprs;     // guards and access indices
+  std::deque<std::vector<rc_access>> accs;
+};
+
+int insn_inputs(int32_t op) {
+  switch (op) {
+    case RC_OP_ADD: return 2;
+    case RC_OP_MUL: case RC_OP_FDIV: case RC_OP_MOD: case RC_OP_LOAD: return 1;
+    default: return 0;
+  }
+}
+
+bool insn_equal(const rc_insn& a, const rc_insn& b) {
+  if (a.op != b.op) return false;
+  switch (a.op) {
+    case RC_OP_CONST: return a.imm == b.imm;
+    case RC_OP_MUL: case RC_OP_FDIV: case RC_OP_MOD: return a.imm == b.imm;
+    default: return a.arg == b.arg;
+  }
+}
+
+// First instruction of the subexpression that ends at position p (postfix
+// code), or -1 for malformed code.
+int64_t subexpr_start(const rc_expr& e, int64_t p) {
+  int64_t need = 1;
+  for (int64_t q = p; q >= 0; --q) {
+    need += insn_inputs(e.code[q].op) - 1;
+    if (need == 0) return q;
+  }
+  return -1;
+}
+
+struct FreeParams {
+  const rc_model_desc* d;
+  std::vector<std::vector<rc_insn>> keys;   // the distinct load subexpressions, first-appearance order
+  std::vector<uint32_t> table;              // their tables
+
+  bool is_free_load(const rc_insn& in) const {
+    return in.op == RC_OP_LOAD && in.arg >= 0 && (uint32_t)in.arg < d->n_tables && d->tables[in.arg].superset;
+  }
+  // The outermost free loads of e: (start, end) ranges, none inside another.
+  bool segments(const rc_expr& e, std::vector<std::pair<int64_t, int64_t>>* out) const {
+    out->clear();
+    for (int64_t p = (int64_t)e.len - 1; p >= 0; --p) {
+      if (!is_free_load(e.code[p])) continue;
+      const int64_t st = subexpr_start(e, p);
+      if (st < 0) return false;
+      out->push_back({st, p});
+      p = st;   // the loop's --p moves before this subexpression: inner loads are part of it
+    }
+    std::reverse(out->begin(), out->end());
+    return true;
+  }
+  int id_of(const rc_insn* c, int64_t n) {
+    for (size_t k = 0; k < keys.size(); ++k) {
+      if ((int64_t)keys[k].size() != n) continue;
+      bool eq = true;
+      for (int64_t i = 0; i < n && eq; ++i) eq = insn_equal(keys[k][i], c[i]);
+      if (eq) return (int)k;
+    }
+    keys.emplace_back(c, c + n);
+    table.push_back((uint32_t)c[n - 1].arg);
+    return (int)keys.size() - 1;
+  }
+  bool collect(const rc_expr& e) {
+    if (e.len == 0) return true;
+    if (!e.code) return false;
+    std::vector<std::pair<int64_t, int64_t>> seg;
+    if (!segments(e, &seg)) return false;
+    for (auto& sg : seg) id_of(e.code + sg.first, sg.second - sg.first + 1);
+    return true;
+  }
+  // e with every outermost free load replaced by its parameter's iterator and
+  // every other iterator moved inward past the parameters
+  rc_expr rewrite(const rc_expr& e, SupersetDesc* sd) {
+    if (e.len == 0) return e;
+    std::vector<std::pair<int64_t, int64_t>> seg;
+    segments(e, &seg);
+    std::vector<rc_insn> out;
+    size_t next = 0;
+    for (int64_t i = 0; i < (int64_t)e.len; ++i) {
+      if (next < seg.size() && seg[next].first == i) {
+        rc_insn it{RC_OP_ITER, id_of(e.code + i, seg[next].second - i + 1), 0};
+        out.push_back(it);
+        i = seg[next].second;
+        ++next;
+        continue;
+      }
+      rc_insn in = e.code[i];
+      if (in.op == RC_OP_ITER) in.arg += (int32_t)keys.size();
+      out.push_back(in);
+    }
+    sd->code.push_back(std::move(out));
+    return rc_expr{sd->code.back().data(), (uint32_t)sd->code.back().size()};
+  }
+};
+
+// Fills sd with the rewritten descriptor when some table is flagged superset;
+// *used = false (and d stays as it is) otherwise.
+rc_status superset_rewrite(const rc_model_desc* d, SupersetDesc* sd, bool* used) {
+  *used = false;
+  if (d->n_tables && !d->tables) return RC_E_INVALID;
+  const int64_t kLim = (int64_t)1 << 62;
+  for (uint32_t t = 0; t < d->n_tables; ++t) {
+    const rc_table& T = d->tables[t];
+    if (T.superset > 1) return RC_E_INVALID;
+    if (!T.superset) continue;
+    if (T.lo > T.hi || T.lo < -kLim || T.hi > kLim) return RC_E_INVALID;
+    *used = true;
+  }
+  if (!*used) return RC_OK;
+  if (d->n_stmts && !d->stmts) return RC_E_INVALID;
+  sd->desc = *d;
+  sd->tables.assign(d->tables, d->tables + d->n_tables);
+  for (rc_table& T : sd->tables)
+    if (T.superset) { T.data = nullptr; T.len = 0; T.superset = 0; }   // no load reads it any more
+  sd->desc.tables = sd->tables.data();
+  sd->stmts.assign(d->stmts, d->stmts + d->n_stmts);
+  for (uint32_t s = 0; s < d->n_stmts; ++s) {
+    const rc_stmt& S = d->stmts[s];
+    if ((S.n_loops && !S.loops) || (S.n_guards && !S.guards) || (S.n_accesses && !S.accesses)) return RC_E_INVALID;
+    FreeParams fp;
+    fp.d = d;
+    bool ok = true;
+    for (uint32_t l = 0; l < S.n_loops; ++l) ok = ok && fp.collect(S.loops[l].lower) && fp.collect(S.loops[l].upper);
+    for (uint32_t g = 0; g < S.n_guards; ++g) ok = ok && fp.collect(S.guards[g]);
+    ok = ok && fp.collect(S.phase) && fp.collect(S.warp_phase);
+    for (uint32_t a = 0; a < S.n_accesses && ok; ++a) {
+      const rc_access& A = S.accesses[a];
+      if (A.array >= d->n_arrays || !A.index || !d->arrays) return RC_E_INVALID;
+      for (uint32_t k = 0; k < d->arrays[A.array].ndims && k < (uint32_t)kMaxDims; ++k) ok = ok && fp.collect(A.index[k]);
+    }
+    if (!ok) return RC_E_INVALID;
+    if (fp.keys.empty()) continue;
+    const size_t nf = fp.keys.size();
+    if (nf + S.n_loops > (size_t)kMaxLoops) return RC_E_UNSUPPORTED;
+    rc_stmt& D = sd->stmts[s];
+    std::vector<rc_loop> loops;
+    for (size_t f = 0; f < nf; ++f) {
+      const rc_table& T = d->tables[fp.table[f]];
+      sd->code.push_back({rc_insn{RC_OP_CONST, 0, T.lo}});
+      const rc_expr lo{sd->code.back().data(), 1};
+      sd->code.push_back({rc_insn{RC_OP_CONST, 0, T.hi + 1}});
+      const rc_expr hi{sd->code.back().data(), 1};
+      loops.push_back(rc_loop{lo, hi, 1});
+    }
+    for (uint32_t l = 0; l < S.n_loops; ++l)
+      loops.push_back(rc_loop{fp.rewrite(S.loops[l].lower, sd), fp.rewrite(S.loops[l].upper, sd), S.loops[l].step});
+    sd->loops.push_back(std::move(loops));
+    D.loops = sd->loops.back().data();
+    D.n_loops = (uint32_t)sd->loops.back().size();
+    std::vector<rc_expr> guards;
+    for (uint32_t g = 0; g < S.n_guards; ++g) guards.push_back(fp.rewrite(S.guards[g], sd));
+    sd->exprs.push_back(std::move(guards));
+    D.guards = sd->exprs.back().data();
+    D.phase = fp.rewrite(S.phase, sd);
+    D.warp_phase = fp.rewrite(S.warp_phase, sd);
+    std::vector<rc_access> accs(S.accesses, S.accesses + S.n_accesses);
+    for (uint32_t a = 0; a < S.n_accesses; ++a) {
+      std::vector<rc_expr> idx;
+      for (uint32_t k = 0; k < d->arrays[accs[a].array].ndims && k < (uint32_t)kMaxDims; ++k)
+        idx.push_back(fp.rewrite(S.accesses[a].index[k], sd));
+      sd->exprs.push_back(std::move(idx));
+      accs[a].index = sd->exprs.back().data();
+    }
+    sd->accs.push_back(std::move(accs));
+    D.accesses = sd->accs.back().data();
+  }
+  sd->desc.stmts = sd->stmts.data();
+  return RC_OK;
+}
+
 }  // namespace
 
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_ids) {
   if (!d || !m) return RC_E_INVALID;
+  SupersetDesc sd;
+  bool superset = false;
+  {
+    const rc_status st = superset_rewrite(d, &sd, &superset);
+    if (st != RC_OK) return st;
+  }
+  if (superset) d = &sd.desc;
   for (int i = 0; i < 3; ++i)
     if (d->grid[i] == 0 || d->block[i] == 0) return RC_E_INVALID;
   if (d->n_phases == 0) return RC_E_INVALID;

@@ -29,10 +29,51 @@ def ev(e, env):
     if op == "mod":
         return ev(a[0], env) % a[1]
     if op == "load":
+        if a[0] in env.get("free", {}):
+            return env["free"][a[0]][expr_key(e)]   # a free parameter of the superset domain
         t = env["tables"][a[0]]
         i = ev(a[1], env)
         return t[i] if 0 <= i < len(t) else 0
     raise ValueError(op)
+
+
+def expr_key(e):
+    """The expression as a nested tuple (equal expressions, equal keys)."""
+    return (e.op,) + tuple(expr_key(x) if hasattr(x, "op") else x for x in e.args)
+
+
+def free_loads(st, superset):
+    """The superset domain: the distinct loads of tables with unknown values
+    in a statement, as (table, key) pairs; a load inside such a load is part
+    of it."""
+    found = []
+
+    def walk(e):
+        if e.op == "load" and e.args[0] in superset:
+            k = (e.args[0], expr_key(e))
+            if k not in found:
+                found.append(k)
+            return
+        for x in e.args:
+            if hasattr(x, "op"):
+                walk(x)
+    exprs = [st.phase, getattr(st, "warp_phase", None)] + [x for lp in st.loops for x in (lp.lower, lp.upper)]
+    exprs += list(st.guards) + [ie for ac in st.accesses for ie in ac.index]
+    for e in exprs:
+        if e is not None:
+            walk(e)
+    return found
+
+
+def free_values(st, superset):
+    """Every assignment of values to the statement's free parameters, as
+    {table: {key: value}} (one empty assignment without superset tables)."""
+    fl = free_loads(st, superset)
+    for vals in product(*[range(superset[t][0], superset[t][1] + 1) for t, _ in fl]):
+        out = {t: {} for t in superset}
+        for (t, k), v in zip(fl, vals):
+            out[t][k] = v
+        yield out
 
 
 def has_sync_scopes(m):
@@ -56,7 +97,10 @@ def instances(m):
             t = tx + bx_ * (ty + by_ * tz)
             env = {"tid": (tx, ty, tz), "bid": (bx, by, bz), "params": m.params, "iter": [0] * 8,
                    "tables": getattr(m, "tables", [])}
-            for si, st in enumerate(m.stmts):
+            superset = getattr(m, "superset", {}) or {}
+            for si, st, free in ((si, st, free) for si, st in enumerate(m.stmts)
+                                 for free in free_values(st, superset)):
+                env["free"] = free
                 def rec(level):
                     if level == len(st.loops):
                         if any(ev(g, env) < 0 for g in st.guards):

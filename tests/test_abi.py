@@ -108,6 +108,21 @@ def test_validation_rejects_malformed(rc):
     assert _status(rc, m) == rc.RC_E_UNSUPPORTED
 
 
+def test_validation_superset_tables(rc):
+    """Superset tables: an empty range is invalid, and each free parameter
+    takes a loop level (7 loops + 2 free parameters exceed 8)."""
+    from workloads.spec import load
+    arr = [Array("a", "shared", (64,))]
+    one = Stmt([Access(0, W, (load(0, tid.x) % 64,))])
+    assert _status(rc, Model((1, 1, 1), (8, 1, 1), arr, [one], tables=[[]], superset={0: (3, 2)})) == rc.RC_E_INVALID
+    assert "rc_expand_jit" in rc.rc_kernel_source(Model((1, 1, 1), (8, 1, 1), arr, [one], superset={0: (0, 7)}))
+    deep = Stmt([Access(0, W, ((load(0, tid.x) + load(0, tid.x + 1)) % 64,))], loops=[Loop(0, 2) for _ in range(7)])
+    m = Model((1, 1, 1), (8, 1, 1), arr, [deep], superset={0: (0, 3)})
+    assert _status(rc, m) == rc.RC_E_UNSUPPORTED
+    deep.loops = deep.loops[:6]
+    assert "rc_expand_jit" in rc.rc_kernel_source(m)
+
+
 def test_validation_key_overflow(rc):
     # 2^20 blocks x 1024 threads x 2^40 cells need 74 key bits: the model lowers
     # as a wide model (checked in cell-range chunks)
@@ -132,8 +147,9 @@ def test_generated_kernels_compile(rc, tmp_path):
                        loops=[Loop(0, 2)] * 5)])
     csr = w.ge_spmm_csr(w.csr_row_lengths(1, 8), N=64, K=2)
     wide = w.random_affine(1, n_blocks=8, block=64, n_stmts=12, row_global=1 << 44)
+    sup = w.ge_spmm_csr([3, 20, 7, 10], N=32, K=1, superset=True)
     for i, m in enumerate([w.random_affine(0), w.tiny_random(5), w.ge_spmm_uniform(), deep, csr,
-                           w.tiny_random_tables(3), wide, w.tiny_random_sync(2), w.warp_reduction(2)]):
+                           w.tiny_random_tables(3), wide, w.tiny_random_sync(2), w.warp_reduction(2), sup]):
         src = rc.rc_kernel_source(m)
         assert ("rc_chunk_jit" if m is wide else "rc_expand_jit") in src
         f = tmp_path / f"k{i}.cu"

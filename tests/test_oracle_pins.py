@@ -3,6 +3,7 @@ closed forms derived by hand (tests/golden/closed_forms.md), the verdict the
 paper states for Ge-SpMM (tests/golden/paper_verdicts.json), an independent
 pure-Python pairwise brute force on tiny random models, and invariances of the
 race definition (thread relabelling, statement order, array padding)."""
+import copy
 import json
 import os
 
@@ -509,3 +510,96 @@ def test_grid_interval_numbering_is_immaterial(seed):
         else:   # one warp interval: the added field is warp phase 0
             assert (best[0][:7], best[1][:7]) == (best2[0][:7], best2[1][:7])
             assert best2[0][7:] == best2[1][7:] == (0,)
+
+
+# --------------------------------------------------------------------------
+# the superset domain: tables whose values are unknown (free parameters)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_superset_gespmm_race_free(seed):
+    """The paper's verdict for Ge-SpMM holds on its superset domain: with rs,
+    re free over [0, nnz] and the barriers after F and after T, no race."""
+    golden = json.load(open(os.path.join(GOLDEN, "paper_verdicts.json")))["ge_spmm_superset"]
+    lens = w.csr_row_lengths(seed, 3, max_len=24)
+    r = oracle.check(w.ge_spmm_csr(lens, N=32, K=2, trailing_barrier=True, superset=True))
+    assert r.status == 0
+    assert (r.verdict == 0) == golden["expected_race_free"]
+
+
+@pytest.mark.parametrize("lens", [[3, 20, 7, 10], [32, 1, 0], [12, 12, 12]])
+def test_superset_gespmm_false_positive_closed_form(lens):
+    """Without the trailing barrier and with every row at most 32 long, the
+    concrete model is race-free (one chunk per row), but on the superset
+    domain re - rs may exceed 32: F of chunk 1 writes sm_k[c] / sm_v[c] (c <
+    nnz - 32) in the interval where T of chunk 0 reads them, so every block
+    has 2 * min(32, nnz - 32) racy shared cells.  The first: sm_k[0] of block
+    0, written by thread 0 (F, chunk 1) and read by thread 1 (T, chunk 0) in
+    interval 1."""
+    nnz, M = sum(lens), len(lens)
+    conc = oracle.check(w.ge_spmm_csr(lens, N=32, K=1, trailing_barrier=False))
+    sup = oracle.check(w.ge_spmm_csr(lens, N=32, K=1, trailing_barrier=False, superset=True))
+    assert (conc.status, conc.racy_cells) == (0, 0)
+    assert sup.status == 0 and sup.racy_cells == 2 * min(32, max(0, nnz - 32)) * M
+    assert sup.witness == (5, 0, 0, (0, 1, 0, 1), (0, 1, 1, 0))
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 64])
+def test_superset_permutation_scatter_closed_form(n):
+    """out[perm[t]] = ... is race-free for a permutation; with perm's values
+    unknown in [0, n-1] every thread may write every cell: n racy cells, n^2
+    instances, witness cell 0 written by threads 0 and 1."""
+    conc = oracle.check(w.permutation_scatter(n, seed=n))
+    sup = oracle.check(w.permutation_scatter(n, seed=n, superset=True))
+    assert (conc.status, conc.racy_cells, conc.instances) == (0, 0, n)
+    assert (sup.status, sup.racy_cells, sup.instances) == (0, n, n * n)
+    assert sup.witness == (0, 0, 0, (0, 0, 0, 1), (0, 0, 1, 1))
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_superset_of_one_value_is_the_concrete_model(seed):
+    """A free parameter whose range is the single value 0 is a load that reads
+    0: the superset model with range [0, 0] equals the concrete model with
+    empty tables (every load reads 0 outside its table), field for field."""
+    base = w.tiny_random_tables(seed)
+    zero = copy.deepcopy(base)
+    zero.tables = [[] for _ in base.tables]
+    one = copy.deepcopy(base)
+    one.superset = {t: (0, 0) for t in range(len(base.tables))}
+    a, b = oracle.check(zero), oracle.check(one)
+    assert a == b
+
+
+@pytest.mark.parametrize("seed", range(150))
+def test_superset_contains_the_concrete_model(seed):
+    """Table 0's range holds every value it gives (and 0), so the concrete
+    instances are a subset of the superset's: at least as many instances and
+    racy cells, and a concrete race is a superset race."""
+    c = oracle.check(w.tiny_random_tables(seed))
+    s = oracle.check(w.tiny_random_tables(seed, superset=True))
+    if c.status == 0 and s.status == 0:
+        assert s.instances >= c.instances and s.racy_cells >= c.racy_cells
+        assert s.verdict >= c.verdict
+    if c.status == oracle.STATUS_OOB:
+        assert s.status == oracle.STATUS_OOB
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_superset_tiny_tables_vs_python_bruteforce(seed):
+    m = w.tiny_random_tables(seed, superset=True)
+    r = oracle.check(m)
+    if r.instances > 4000:
+        pytest.skip("too large for the pairwise check")
+    st, cnt, best = pyref.check(m)
+    if st == "oob":
+        assert r.status == oracle.STATUS_OOB
+        assert (r.oob_stmt, r.oob_access, r.oob_gtid, r.oob_dim) == cnt
+        return
+    assert r.status == 0 and r.racy_cells == cnt
+    inst, _ = pyref.instances(m)
+    assert r.instances == len(inst) and r.distinct == len(set(inst))
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        assert r.witness == (x[0], x[1], x[2], (x[3], x[4], x[5], x[6]), (y[3], y[4], y[5], y[6]))

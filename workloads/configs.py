@@ -280,7 +280,8 @@ def ge_spmm_uniform(M: int = 4, N: int = 64, K: int = 8, L: int = 70,
                  name=f"gespmm_M{M}_N{N}_K{K}_L{L}_{'bar' if trailing_barrier else 'nobar'}")
 
 
-def ge_spmm_csr(row_lengths: List[int], N: int = 64, K: int = 8, trailing_barrier: bool = True) -> Model:
+def ge_spmm_csr(row_lengths: List[int], N: int = 64, K: int = 8, trailing_barrier: bool = True,
+                superset: bool = False) -> Model:
     """Ge-SpMM Algorithm 2 on a CSR matrix with the given row lengths.
 
     As :func:`ge_spmm_uniform`, but the row bounds are read from the row
@@ -291,6 +292,15 @@ def ge_spmm_csr(row_lengths: List[int], N: int = 64, K: int = 8, trailing_barrie
     with a superset (Section "Problems to deal with").  Without the trailing
     barrier each block row ``i`` has ``2 * min(32, max(0, L_i - 32))`` racy
     shared cells per 32-column slab; with it the model is race-free.
+
+    ``superset=True`` checks the paper's superset domain instead: the row
+    pointer's values are unknown, ``rs`` and ``re`` are free parameters over
+    ``[0, nnz]`` (the Domain's ``0 <= rs``, ``re <= A_S``), and the model has
+    enough barrier intervals for any row of up to ``nnz`` non-zeros.  With the
+    trailing barrier it stays race-free (the paper's verdict holds for every
+    matrix of that many non-zeros); without it every block has
+    ``2 * min(32, max(0, nnz - 32))`` racy shared cells, a false positive
+    whenever all rows are at most 32 long.
     """
     if N % 32:
         raise ValueError("N must be a multiple of 32")
@@ -333,10 +343,32 @@ def ge_spmm_csr(row_lengths: List[int], N: int = 64, K: int = 8, trailing_barrie
               loops=[Loop(0, n_ch), Loop(0, 32), Loop(0, K)],
               guards=[re - (ptr + kk) - 1],
               phase=(2 * m + 1) if trailing_barrier else (m + 1), name="T_B")
+    if superset:
+        max_ch = max(1, (row_ptr[-1] + 31) // 32)
     n_phases = 2 * max_ch if trailing_barrier else max_ch + 1
     return Model((M, N // 32, 1), (32, 1, 1), arrays, [I, F, T, TB], n_phases=n_phases,
-                 name=f"gespmm_csr_M{M}_N{N}_K{K}_{'bar' if trailing_barrier else 'nobar'}",
-                 tables=[row_ptr])
+                 name=f"gespmm_csr_M{M}_N{N}_K{K}_{'bar' if trailing_barrier else 'nobar'}"
+                      f"{'_superset' if superset else ''}",
+                 tables=[row_ptr], superset={0: (0, row_ptr[-1])} if superset else {})
+
+
+def permutation_scatter(n: int, seed: int = 0, superset: bool = False) -> Model:
+    """n threads of one block, thread t writes out[perm[t]] for a seeded
+    permutation held in table 0: race-free.  With ``superset=True`` the
+    table's values are unknown in [0, n-1] (the paper's superset domain), so
+    every thread may write every cell: all n cells are racy (n >= 2), a false
+    positive of the over-approximation; the witness is cell 0 with x = thread
+    0 and y = thread 1, both writes."""
+    rng = SplitMix64(0x5CA7 ^ seed)
+    perm = list(range(n))
+    for i in range(n - 1, 0, -1):
+        j = rng.below(i + 1)
+        perm[i], perm[j] = perm[j], perm[i]
+    out = Array("out", GLOBAL, (n,))
+    st = Stmt([Access(0, W, (load(0, tid.x),))], name="scatter")
+    return Model((1, 1, 1), (n, 1, 1), [out], [st], tables=[perm],
+                 superset={0: (0, n - 1)} if superset else {},
+                 name=f"perm_scatter_{n}{'_superset' if superset else ''}")
 
 
 def csr_row_lengths(seed: int, M: int, max_len: int = 150, empty: float = 0.1) -> List[int]:
@@ -627,11 +659,15 @@ def tiny_random_sync(seed: int, block_guards: bool = False) -> Model:
                  grid_phase=gp, name=f"tinysync_{seed}{'_bg' if block_guards else ''}")
 
 
-def tiny_random_tables(seed: int) -> Model:
+def tiny_random_tables(seed: int, superset: bool = False) -> Model:
     """A tiny random model whose loop bounds, guards and indices read small
     integer tables (data-dependent values; indices outside a table read 0):
     loop bounds such as ``T0[tid.x + i0]``, scatter writes such as
-    ``a[T1[tid.x] mod 4]``.  Indices of arrays are reduced modulo the extent."""
+    ``a[T1[tid.x] mod 4]``.  Indices of arrays are reduced modulo the extent.
+
+    ``superset=True``: the same model with table 0's values unknown in the
+    range of its values and 0 (the value read outside it), so the concrete
+    model's instances are a subset of the superset model's."""
     rng = SplitMix64(0x7AB1E ^ (seed * 0x9E3779B97F4A7C15))
     tables = [[rng.uniform_int(-2, 6) for _ in range(rng.uniform_int(2, 8))]
               for _ in range(rng.uniform_int(1, 2))]
@@ -663,6 +699,10 @@ def tiny_random_tables(seed: int) -> Model:
             idx = (maybe_load(_tiny_expr(rng, depth)) % arrays[a].extents[0],)
             accs.append(Access(a, W if rng.chance(0.45) else R, idx))
         stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, name=f"t{s_}"))
-    return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tinytab{seed}",
-                 tables=tables)
+    sup = {}
+    if superset:
+        vals = tables[0] + [0]
+        sup = {0: (min(vals), max(vals))}
+    return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases,
+                 name=f"tinytab{seed}{'_superset' if superset else ''}", tables=tables, superset=sup)
 

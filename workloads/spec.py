@@ -22,7 +22,7 @@ the paper's Ge-SpMM model uses (``j % 32``).
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Sequence, Tuple, Union
+from typing import Dict, List, Sequence, Tuple, Union
 
 __all__ = [
     "Expr", "E", "tid", "bid", "param", "it", "const", "load",
@@ -251,6 +251,10 @@ class Model:
     # the grid interval of each barrier phase (grid-wide barriers; empty = none)
     n_warp_phases: int = 1
     grid_phase: List[int] = field(default_factory=list)
+    # tables whose values are unknown, table -> (lo, hi): every distinct load
+    # of such a table in a statement is a free parameter over [lo, hi] (the
+    # paper's superset domain for data-dependent bounds)
+    superset: Dict[int, Tuple[int, int]] = field(default_factory=dict)
 
     def __post_init__(self):
         self.grid = tuple(int(v) for v in (list(self.grid) + [1, 1, 1])[:3])
@@ -258,6 +262,7 @@ class Model:
         self.params = [int(p) for p in self.params]
         self.tables = [[int(v) for v in t] for t in self.tables]
         self.grid_phase = [int(v) for v in self.grid_phase]
+        self.superset = {int(t): (int(r[0]), int(r[1])) for t, r in self.superset.items()}
         if self.grid_phase and len(self.grid_phase) != self.n_phases:
             raise ValueError("grid_phase needs one entry per barrier phase")
         if any(b < a for a, b in zip(self.grid_phase, self.grid_phase[1:])):
