@@ -126,9 +126,10 @@ typedef struct rc_loop { rc_expr lower; rc_expr upper; int64_t step; } rc_loop;
 typedef struct rc_access {
   uint32_t array;          /* index into rc_model_desc.arrays                     */
   uint32_t kind;           /* RC_READ, RC_WRITE or RC_ATOMIC.  A model with atomic
-                              accesses has a 2-bit kind field (R = 0, W = 1, A = 2)
-                              and at most 16 barrier intervals (RC_E_UNSUPPORTED
-                              otherwise)                                           */
+                              accesses has a 2-bit kind field (R = 0, W = 1, A = 2);
+                              with more than 16 barrier intervals it is checked
+                              on the sort path only (RC_E_UNSUPPORTED on the hash
+                              path)                                                */
   const rc_expr* index;    /* ndims expressions (ndims of the array)              */
 } rc_access;
 
@@ -186,12 +187,15 @@ typedef struct rc_model_desc {
   uint32_t n_warp_phases;  /* warp intervals per block interval; 0 or 1 = none   */
   const uint32_t* grid_phase;  /* n_phases entries, non-decreasing: the grid
                                interval of each block interval (grid-wide
-                               barriers); NULL = none.  With warp or grid
-                               barriers n_phases * n_warp_phases <= 16; such
-                               a model is checked on the sort path by default
-                               (alone or in a batch, where it shares a pack
-                               only with models of at most 16 barrier
-                               intervals) or on the hash path on request.
+                               barriers); NULL = none.  A model with warp or
+                               grid barriers is checked on the sort path by
+                               default (alone or in a batch, where it shares a
+                               pack only with models of at most 16 barrier
+                               intervals, and holds a pack alone when it has
+                               more than 16 fine intervals n_phases *
+                               n_warp_phases) or, with at most 16 fine
+                               intervals, on the hash path on request
+                               (RC_E_UNSUPPORTED beyond).
                                With more than one grid interval the witness
                                keeps a record per (block, fine interval), so
                                such a model needs bit_length(blocks - 1) +

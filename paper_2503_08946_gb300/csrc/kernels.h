@@ -204,6 +204,10 @@ struct ScanArgs {
   // keys grouped by cell but not in cell order (bucket path): the first racy
   // cell is kept by value in DevResult.hash_cell (phase-table scan only)
   uint32_t by_cell;
+  // keys sorted by (cell, fine interval) with warp or grid barriers: the grid
+  // interval of each block interval (null: the 4-bit table of sync_tabs,
+  // which covers fine intervals below 16)
+  const uint32_t* grid_of;
 };
 // the interval tables of a scan (no warp or grid barriers: q is the phase)
 struct SyncTabs {

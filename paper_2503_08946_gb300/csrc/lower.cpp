@@ -508,32 +508,29 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   if (!mul_ok((uint64_t)d->n_phases, (uint64_t)n_wp, &n_fine)) return RC_E_UNSUPPORTED;
   h.phase_bits = bit_length(n_fine - 1);
   if (h.phase_bits > (uint32_t)kMaxPhaseBits) return RC_E_UNSUPPORTED;
-  // warp / grid barriers are scanned with phase tables only (at most 16 fine intervals)
-  if (m->sync_scopes && n_fine > (1u << kScanTablePhaseBits)) return RC_E_UNSUPPORTED;
+  // up to 16 fine intervals the keys are sorted by cell only and scanned with
+  // phase tables; beyond, sorted by (cell, fine interval) and scanned in that
+  // order (block and grid intervals are then contiguous inside a cell)
   // grid intervals are compared only for equality, so they are numbered
   // densely (0, 1, ... in block-interval order, the descriptor's numbers being
   // non-decreasing): a grid interval is then below n_phases and fits the
   // phase field (the hash path packs it there)
   m->coarse_tab = m->grid_tab = 0;
+  std::vector<uint32_t> grid_of(d->n_phases, 0);   // dense grid interval of each block interval
+  if (d->grid_phase)
+    for (uint32_t p = 1; p < d->n_phases; ++p) grid_of[p] = grid_of[p - 1] + (d->grid_phase[p] != d->grid_phase[p - 1] ? 1u : 0u);
   for (uint64_t q = 0; q < n_fine && q < 16; ++q) {
     const uint64_t p = q / n_wp;
-    uint64_t g = 0;
-    if (d->grid_phase) {
-      if (d->grid_phase[p] > 15u) return RC_E_UNSUPPORTED;
-      for (uint64_t p2 = 1; p2 <= p; ++p2) g += d->grid_phase[p2] != d->grid_phase[p2 - 1] ? 1u : 0u;
-    }
     m->coarse_tab |= (p & 15u) << (4 * q);
-    m->grid_tab |= (g & 15u) << (4 * q);
+    m->grid_tab |= ((uint64_t)grid_of[p] & 15u) << (4 * q);
   }
   h.sync_tab[0] = m->coarse_tab;
   h.sync_tab[1] = m->grid_tab;
   // more than one grid interval: the witness keeps per-block group records
   // (2^(block bits + phase bits) of them), so the grid is bounded
-  m->multi_grid = m->grid_tab != 0;
+  m->multi_grid = grid_of.back() != 0;
   if (m->multi_grid && h.block_bits + h.phase_bits > kWitnessBlockGroupBits) return RC_E_UNSUPPORTED;
   h.sync_tab[2] = (uint64_t)n_wp | ((uint64_t)bit_length((uint64_t)n_wp - 1) << 32);
-  // atomics are scanned by the phase-table scan only (at most 16 intervals)
-  if (has_atomic && h.phase_bits > (uint32_t)kScanTablePhaseBits) return RC_E_UNSUPPORTED;
   h.cell_shift = h.phase_shift + h.phase_bits;
   // one more value than the cells so the all-ones cell field is never a valid cell
   h.cell_bits = bit_length(cells_total);
@@ -704,7 +701,11 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   }
   size_t off_tabidx = align256(off_terms + terms.size() * sizeof(Term));
   size_t off_tdata = align256(off_tabidx + tab_index.size() * 8);
-  size_t off_units = align256(off_tdata + (size_t)tab_words * 8);
+  // the grid interval of each block interval (models scanned in phase order
+  // with warp or grid barriers)
+  const bool want_gridof = m->sync_scopes && h.phase_bits > (uint32_t)kScanTablePhaseBits;
+  size_t off_gridof = align256(off_tdata + (size_t)tab_words * 8);
+  size_t off_units = want_gridof ? align256(off_gridof + grid_of.size() * 4) : off_gridof;
   size_t total = off_units;
   m->program.assign(total, 0);
   auto put = [&](size_t off, const void* src, size_t n) {
@@ -719,6 +720,8 @@ rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* ge
   put(off_tabidx, tab_index.data(), tab_index.size() * 8);
   for (uint32_t t = 0; t < d->n_tables; ++t)
     put(off_tdata + (size_t)tab_index[2 * t] * 8, d->tables[t].data, (size_t)d->tables[t].len * 8);
+  if (want_gridof) put(off_gridof, grid_of.data(), grid_of.size() * 4);
+  m->sec_gridof = want_gridof ? off_gridof : 0;
   // device pointers are stored as offsets here and relocated at upload
   h.arrays = reinterpret_cast<const DevArray*>(off_arrays);
   h.stmts = reinterpret_cast<const DevStmt*>(off_stmts);

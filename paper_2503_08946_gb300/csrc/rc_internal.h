@@ -404,10 +404,14 @@ struct Model {
   bool has_atomic = false;        // some access is atomic: 2-bit kind field
   bool sync_scopes = false;       // warp or grid barriers
   bool multi_grid = false;        // more than one grid interval (grid barriers)
-  uint64_t coarse_tab = 0;        // fine interval q -> block interval (4 bits per q)
-  uint64_t grid_tab = 0;          // fine interval q -> grid interval (4 bits per q)
+  uint64_t coarse_tab = 0;        // fine interval q -> block interval (4 bits per q, q < 16)
+  uint64_t grid_tab = 0;          // fine interval q -> grid interval (4 bits per q, q < 16)
   // sections of the program image (byte offsets), for the kernel generator
   size_t sec_arrays = 0, sec_stmts = 0, sec_accs = 0, sec_rows = 0, sec_lin = 0, sec_terms = 0, sec_tabidx = 0;
+  // grid interval (dense numbering) of every block interval, uint32 each: the
+  // phase-sorted scan of models with warp or grid barriers and more than 16
+  // fine intervals (0 = no such section)
+  size_t sec_gridof = 0;
   void* jit_fn = nullptr;         // generated expansion kernel (CUfunction), or null
   void* jit_chunk_fn = nullptr;   // wide models: generated count / route kernel, or null
   uint64_t max_iter_per_unit = 0;

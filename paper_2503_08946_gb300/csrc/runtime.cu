@@ -173,6 +173,11 @@ size_t witness_group_bytes(const Model& m) {
 
 // The path a check takes: RC_PATH_HASH on request, otherwise the sort path.
 bool use_hash_path(const Model&, const rc_check_opts* opts) { return opts && opts->path == RC_PATH_HASH; }
+// the hash path maps fine intervals through the 4-bit interval tables, so
+// with warp or grid barriers, or atomics, it covers at most 16 of them
+bool hash_path_fits(const Model& m) {
+  return !(m.sync_scopes || m.has_atomic) || m.host.phase_bits <= (uint32_t)kScanTablePhaseBits;
+}
 
 void plan_workspace(const Model& m, const rc_check_opts* opts, WorkspacePlan* p) {
   std::memset(p, 0, sizeof(*p));
@@ -341,6 +346,9 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
                               : nullptr;
   a.wit_block_bits = m.multi_grid ? m.host.block_bits : 0u;
   a.by_cell = 0;
+  a.grid_of = m.sec_gridof ? reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(m.dev_program) +
+                                                               m.sec_gridof)
+                           : nullptr;
   return a;
 }
 
@@ -987,6 +995,7 @@ struct BatchPack {
   bool loop_free = true;               // every model of the pack is loop-free
   bool sy = false;                     // some model has warp or grid barriers
   bool mg = false;                     // its models have more than one grid interval (per-block witness groups)
+  const uint32_t* grid_of = nullptr;   // phase-order scan with warp / grid barriers: its model's interval table
   uint64_t total_cells = 0, n_keys = 0, n_units = 0;
   rc::WorkspacePlan p;                 // sort / scan sections (offsets into the shared pack region)
 };
@@ -1042,6 +1051,10 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     cur.loop_free = m.loop_free;
     cur.sy = m.sync_scopes;
     cur.mg = m.multi_grid;
+    // (a model scanned in phase order with warp or grid barriers holds its pack alone)
+    cur.grid_of = m.sec_gridof ? reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(m.dev_program) +
+                                                                   m.sec_gridof)
+                               : nullptr;
     cur.total_cells = m.total_cells;
     cur.cell_bits = rc::bit_length(m.total_cells);
     cur.n_keys = m.key_slots;
@@ -1232,6 +1245,7 @@ rc_status enqueue_batch_device(const BatchLayout& L, size_t n, const rc_check_op
     sa.phase_table = k.pb <= rc::kScanTablePhaseBits ? 1u : 0u;
     sa.sync_tabs = k.sy ? dstabs + 3 * k.i0 : nullptr;
     sa.wit_block_bits = k.mg ? k.bb : 0u;
+    sa.grid_of = k.grid_of;
     if (p.bucket.on) {
       const uint64_t* fin = nullptr;
       s = enqueue_bucketed(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
@@ -1425,8 +1439,8 @@ rc_check_opts resolve_opts(rc_model* const* models, size_t n, const rc_check_opt
   if (opts) o = *opts;
   if (o.path != RC_PATH_AUTO) return o;
   o.path = RC_PATH_SORT;
-  for (size_t i = 0; i < n; ++i)
-    if (models[i] && models[i]->m.sync_scopes) return o;   // warp / grid barriers: sort path only
+  for (size_t i = 0; i < n; ++i)   // warp / grid barriers, or a model the hash path cannot take: sort path
+    if (models[i] && (models[i]->m.sync_scopes || !rc::hash_path_fits(models[i]->m))) return o;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned.find(tune_key(models, n));
   if (it != g_tuned.end()) {
@@ -1602,6 +1616,7 @@ rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t
   if (!m || !bytes) return RC_E_INVALID;
   rc_model* mm = const_cast<rc_model*>(m);
   const rc_check_opts o = resolve_opts(&mm, 1, opts);
+  if (o.path == RC_PATH_HASH && !rc::hash_path_fits(m->m)) return RC_E_UNSUPPORTED;
   if (use_chunked(m->m, &o)) {
     ChunkGeometry g;
     const rc_status s = chunk_geometry(m->m, &o, &g);
@@ -1621,6 +1636,7 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   *ticket = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc_check_opts o = resolve_opts(&m, 1, opts);
+  if (o.path == RC_PATH_HASH && !rc::hash_path_fits(m->m)) return RC_E_UNSUPPORTED;
   // warp / grid barriers take the sort path unless the hash path is asked for
   if (m->m.sync_scopes && (!opts || opts->path != RC_PATH_HASH)) o.path = RC_PATH_SORT;
   if (use_chunked(m->m, &o)) {
@@ -1665,6 +1681,9 @@ rc_status rc_batch_workspace_size(rc_model* const* models, size_t n, const rc_ch
   }
   const rc_check_opts ro = resolve_opts(models, n, opts_in);
   const rc_check_opts* opts = &ro;
+  if (ro.path == RC_PATH_HASH)
+    for (size_t i = 0; i < n; ++i)
+      if (!rc::hash_path_fits(models[i]->m)) return RC_E_UNSUPPORTED;
   if (batch_is_sequential(opts)) {
     size_t mx = 0;
     for (size_t i = 0; i < n; ++i) {
@@ -1691,6 +1710,9 @@ rc_status rc_check_batch(rc_model* const* models, size_t n, const rc_check_opts*
     if (models[i]->m.wide) return RC_E_KEY_OVERFLOW;   // wide models are checked alone, in chunks
   }
   rc_check_opts ro = resolve_opts(models, n, opts_in);
+  if (ro.path == RC_PATH_HASH)
+    for (size_t i = 0; i < n; ++i)
+      if (!rc::hash_path_fits(models[i]->m)) return RC_E_UNSUPPORTED;
   if (opts_in && opts_in->path == RC_PATH_AUTO) {
     size_t need = 0;
     rc_batch_workspace_size(models, n, &ro, &need);
@@ -1757,7 +1779,9 @@ rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts, 
     o.digit_bits = d;
     cands.push_back(o);
   }
-  {
+  bool hash_ok = true;
+  for (size_t i = 0; i < n; ++i) hash_ok = hash_ok && rc::hash_path_fits(models[i]->m);
+  if (hash_ok) {
     rc_check_opts o = base;
     o.path = RC_PATH_HASH;
     o.digit_bits = 0;

@@ -444,6 +444,240 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_kernel(ScanArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Phase-order scan of models with warp or grid barriers, or atomics, and more
+// than 16 fine intervals: the keys are sorted by (cell, fine interval q), so
+// inside a cell the keys of each fine interval, of each block interval
+// c = q / n_wp and of each grid interval g(c) are contiguous (all three are
+// non-decreasing in q).  Per interval the fold keeps the smallest and largest
+// (block, thread) and the kinds present.  A cell is racy iff a fine interval
+// holds two (block, thread) and a conflict, a block interval holds two warps
+// of one block and a conflict (its smallest and largest (block, thread) lie in
+// one block and in different warps; two blocks there are caught by the grid
+// test, a block interval lying in one grid interval), or a grid interval
+// holds two blocks and a conflict.  Without warp or grid barriers (atomics
+// only) every block interval is its fine interval and all lie in one grid
+// interval, which is the plain rule.  Conflict: a write, or an atomic and a
+// plain read.
+// K3s (scan_sorted_sync_kernel): each thread folds, one after another, the
+//      cells that begin in its 32 positions; a cell longer than
+//      kSyncSeqMax keys is handed to K3t by its first position.
+// K3t (scan_sorted_sync_long_kernel): one block per handed-over cell, folded
+//      as an ordered reduction of SyncPieces (below).
+// ---------------------------------------------------------------------------
+struct ISeg {
+  unsigned mn, mx;   // smallest and largest (block, thread)
+  unsigned f;        // kinds present: bit 0 R, bit 1 W, bit 2 A
+};
+struct SyncCtx {
+  uint32_t cs, ps, ts, tb;
+  unsigned pmask, btmask, kmask;
+  uint32_t n_wp;
+  const uint32_t* grid_of;   // per block interval (null: the 4-bit table, q < 16)
+  uint64_t grid_tab;
+};
+__device__ __forceinline__ SyncCtx sync_ctx(const ScanArgs& a, uint32_t mi) {
+  SyncCtx c;
+  c.cs = a.cell_shift;
+  c.ps = a.phase_shift;
+  c.ts = a.thread_shift;
+  c.tb = a.thread_bits;
+  c.pmask = (1u << a.phase_bits) - 1u;
+  c.btmask = (unsigned)((1ull << (a.block_bits + a.thread_bits)) - 1ull);
+  c.kmask = (1u << a.thread_shift) - 1u;
+  const SyncTabs t = sync_tabs_of(a, mi);
+  c.n_wp = t.on ? t.n_wp : 1u;
+  c.grid_of = t.on ? a.grid_of : nullptr;
+  c.grid_tab = t.on ? t.grid : 0ull;
+  return c;
+}
+// the interval ids of a key at the three levels (fine, block, grid)
+__device__ __forceinline__ void sync_ids(const SyncCtx& c, uint64_t k, unsigned id[3]) {
+  const unsigned q = (unsigned)(k >> c.ps) & c.pmask;
+  const unsigned p = q / c.n_wp;
+  id[0] = q;
+  id[1] = p;
+  id[2] = c.grid_of ? __ldg(c.grid_of + p) : (q < 16u ? (unsigned)(c.grid_tab >> (4 * q)) & 15u : 0u);
+}
+__device__ __forceinline__ ISeg iseg_of(const SyncCtx& c, uint64_t k) {
+  ISeg s;
+  s.mn = s.mx = (unsigned)(k >> c.ts) & c.btmask;
+  s.f = 1u << ((unsigned)k & c.kmask);
+  return s;
+}
+__device__ __forceinline__ ISeg iseg_join(const ISeg& a, const ISeg& b) {
+  ISeg s;
+  s.mn = min(a.mn, b.mn);
+  s.mx = max(a.mx, b.mx);
+  s.f = a.f | b.f;
+  return s;
+}
+__device__ __forceinline__ bool iseg_hot(const SyncCtx& c, int level, const ISeg& s) {
+  const bool conf = (s.f & 2u) || ((s.f & 5u) == 5u);
+  if (!conf) return false;
+  if (level == 0) return s.mn != s.mx;
+  const bool one_block = (s.mn >> c.tb) == (s.mx >> c.tb);
+  if (level == 2) return !one_block;
+  const unsigned tmask = (1u << c.tb) - 1u;
+  return one_block && ((s.mn & tmask) >> 5) != ((s.mx & tmask) >> 5);
+}
+
+// a contiguous piece of one cell's keys: per level its first and last interval
+// (bit L of `one`: the piece lies in one level-L interval), and whether an
+// interval closed on both sides inside it is racy
+struct SyncPiece {
+  uint64_t fk, lk;
+  ISeg first[3], last[3];
+  unsigned one, racy;
+};
+__device__ __forceinline__ SyncPiece sync_piece_of(const SyncCtx& c, uint64_t k) {
+  SyncPiece p;
+  p.fk = p.lk = k;
+  const ISeg s = iseg_of(c, k);
+#pragma unroll
+  for (int L = 0; L < 3; ++L) p.first[L] = p.last[L] = s;
+  p.one = 7u;
+  p.racy = 0u;
+  return p;
+}
+// a followed by b (both of one cell)
+__device__ __forceinline__ SyncPiece sync_piece_merge(const SyncCtx& c, const SyncPiece& a, const SyncPiece& b) {
+  SyncPiece r;
+  r.fk = a.fk;
+  r.lk = b.lk;
+  r.one = 0u;
+  r.racy = a.racy | b.racy;
+  unsigned ia[3], ib[3];
+  sync_ids(c, a.lk, ia);
+  sync_ids(c, b.fk, ib);
+#pragma unroll
+  for (int L = 0; L < 3; ++L) {
+    const bool ao = (a.one >> L) & 1u, bo = (b.one >> L) & 1u;
+    if (ia[L] == ib[L]) {
+      const ISeg j = iseg_join(a.last[L], b.first[L]);
+      r.first[L] = ao ? j : a.first[L];
+      r.last[L] = bo ? j : b.last[L];
+      if (ao && bo) r.one |= 1u << L;
+      if (!ao && !bo && iseg_hot(c, L, j)) r.racy = 1u;
+    } else {
+      if (!ao && iseg_hot(c, L, a.last[L])) r.racy = 1u;
+      if (!bo && iseg_hot(c, L, b.first[L])) r.racy = 1u;
+      r.first[L] = a.first[L];
+      r.last[L] = b.last[L];
+    }
+  }
+  return r;
+}
+__device__ __forceinline__ bool sync_piece_racy(const SyncCtx& c, const SyncPiece& p) {
+  bool r = p.racy != 0u;
+#pragma unroll
+  for (int L = 0; L < 3; ++L) r = r || iseg_hot(c, L, p.first[L]) || iseg_hot(c, L, p.last[L]);
+  return r;
+}
+
+constexpr int kSyncChunk = 32;                 // positions per thread of K3s
+constexpr uint64_t kSyncSeqMax = 8192;         // longer cells go to K3t (at most n / 8192 of them)
+static_assert(kSyncSeqMax >= (uint64_t)kCarryMaxSegs * kSegKeys, "the long-cell list is sized for this");
+
+__device__ __forceinline__ void sync_record(const ScanArgs& a, uint64_t cell, uint64_t start) {
+  DevResult* r = result_of(a, cell);
+  atomicAdd(&r->racy_cells, 1ull);
+  atomicMin(&r->min_start, (unsigned long long)start);
+}
+
+__global__ void __launch_bounds__(256) scan_sorted_sync_kernel(ScanArgs a) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kSyncChunk;
+  for (uint64_t c0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kSyncChunk; c0 < a.n; c0 += stride) {
+    const uint64_t c1 = min(c0 + (uint64_t)kSyncChunk, a.n);
+    uint64_t prev = c0 ? (a.keys[c0 - 1] >> a.cell_shift) : ~0ull;
+    for (uint64_t i = c0; i < c1; ++i) {
+      const uint64_t k = a.keys[i];
+      if (k == kSentinel) break;                 // padding sorts last
+      const uint64_t cell = k >> a.cell_shift;
+      if (cell == prev) continue;                // not the first key of its cell
+      prev = cell;
+      const SyncCtx c = sync_ctx(a, model_of(a, cell));
+      // one open interval per level; an interval is decided when it closes
+      unsigned id[3];
+      ISeg cur[3];
+      sync_ids(c, k, id);
+      cur[0] = cur[1] = cur[2] = iseg_of(c, k);
+      bool racy = false;
+      uint64_t j = i + 1;
+      for (; j < a.n && j - i < kSyncSeqMax; ++j) {
+        const uint64_t kj = a.keys[j];
+        if ((kj >> a.cell_shift) != cell) break;
+        unsigned idj[3];
+        sync_ids(c, kj, idj);
+        const ISeg sj = iseg_of(c, kj);
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {
+          if (idj[L] != id[L]) {
+            racy = racy || iseg_hot(c, L, cur[L]);
+            id[L] = idj[L];
+            cur[L] = sj;
+          } else {
+            cur[L] = iseg_join(cur[L], sj);
+          }
+        }
+      }
+      if (j < a.n && j - i >= kSyncSeqMax && (a.keys[j] >> a.cell_shift) == cell) {
+        hand_over(a, i);
+        continue;
+      }
+#pragma unroll
+      for (int L = 0; L < 3; ++L) racy = racy || iseg_hot(c, L, cur[L]);
+      if (racy) sync_record(a, cell, i);
+    }
+  }
+}
+
+// One block per handed-over cell: each thread folds kLongItems keys into a
+// piece, the block merges the pieces in order.
+__global__ void __launch_bounds__(kLongThreads) scan_sorted_sync_long_kernel(ScanArgs a) {
+  __shared__ SyncPiece part[kLongThreads];
+  __shared__ int part_empty[kLongThreads];
+  const unsigned long long n_long = min(*a.long_count, (unsigned long long)a.long_cap);
+  for (unsigned long long i = blockIdx.x; i < n_long; i += gridDim.x) {
+    const uint64_t start = a.long_list[i];
+    const uint64_t cell = a.keys[start] >> a.cell_shift;
+    const SyncCtx c = sync_ctx(a, model_of(a, cell));
+    SyncPiece acc;
+    bool acc_empty = true;
+    for (uint64_t base = start;; base += (uint64_t)kLongThreads * kLongItems) {
+      SyncPiece p;
+      bool empty = true, end = false;
+      for (int j = 0; j < kLongItems; ++j) {
+        const uint64_t pos = base + (uint64_t)threadIdx.x * kLongItems + j;
+        if (pos >= a.n) { end = true; break; }
+        const uint64_t k = a.keys[pos];
+        if (k == kSentinel || (k >> a.cell_shift) != cell) { end = true; break; }
+        const SyncPiece kp = sync_piece_of(c, k);
+        p = empty ? kp : sync_piece_merge(c, p, kp);
+        empty = false;
+      }
+      if (!empty) part[threadIdx.x] = p;
+      part_empty[threadIdx.x] = empty ? 1 : 0;
+      const bool any_end = __syncthreads_or(end) != 0;
+      for (int width = 1; width < kLongThreads; width <<= 1) {
+        if ((threadIdx.x % (2 * width)) == 0 && !part_empty[threadIdx.x + width]) {
+          part[threadIdx.x] = part_empty[threadIdx.x] ? part[threadIdx.x + width]
+                                                      : sync_piece_merge(c, part[threadIdx.x], part[threadIdx.x + width]);
+          part_empty[threadIdx.x] = 0;
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0 && !part_empty[0]) {
+        acc = acc_empty ? part[0] : sync_piece_merge(c, acc, part[0]);
+        acc_empty = false;
+      }
+      __syncthreads();
+      if (any_end) break;
+    }
+    if (threadIdx.x == 0 && !acc_empty && sync_piece_racy(c, acc)) sync_record(a, cell, start);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Phase-table variants: keys sorted by cell only.  With at most
 // 2^kScanTablePhaseBits barrier intervals the sort leaves out the phase bits,
 // and the phase groups of a cell are tracked in a small table per part
@@ -863,6 +1097,11 @@ __device__ __forceinline__ Fields fields(const ScanArgs& a, uint64_t key) {
   f.p = (unsigned)(key >> a.phase_shift) & ((1u << a.phase_bits) - 1u);
   return f;
 }
+// block interval and grid interval of fine interval q (warp or grid barriers)
+__device__ __forceinline__ unsigned coarse_q(const SyncTabs& t, unsigned q) { return q / t.n_wp; }
+__device__ __forceinline__ unsigned grid_q(const ScanArgs& a, const SyncTabs& t, unsigned q) {
+  return a.grid_of ? __ldg(a.grid_of + q / t.n_wp) : (unsigned)(t.grid >> (4 * q)) & 15u;
+}
 __device__ __forceinline__ bool kinds_conflict(unsigned kx, unsigned ky) {
   return kx == 1u || ky == 1u || (kx ^ ky) == 2u;
 }
@@ -1018,13 +1257,14 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
       }
       // warp / grid barriers: another block of the same grid interval, or another
       // warp of this block in the same block interval
-      const unsigned xc = (unsigned)(syt.coarse >> (4 * f.p)) & 15u, xg = (unsigned)(syt.grid >> (4 * f.p)) & 15u;
+      const unsigned xc = coarse_q(syt, f.p), xg = grid_q(a, syt, f.p);
       for (unsigned q = 0; q < (1u << a.phase_bits); ++q) {
         const unsigned* gq = group_rec(a, groups, 0u, q);
-        if ((((unsigned)(syt.grid >> (4 * q)) & 15u) == xg) && gq[11 + 2 * k] != 0xffffffffu &&
-            (gq[11 + 2 * k] != xb || gq[12 + 2 * k] != xb))
+        // (a record with a key of kind k: q is a fine interval of the model)
+        if (gq[11 + 2 * k] != 0xffffffffu && (gq[11 + 2 * k] != xb || gq[12 + 2 * k] != xb) &&
+            grid_q(a, syt, q) == xg)
           cross = true;
-        if (q != f.p && (((unsigned)(syt.coarse >> (4 * q)) & 15u) == xc)) {
+        if (q != f.p && coarse_q(syt, q) == xc) {
           const unsigned* gqk = group_rec(a, groups, xb, q) + 2 + 3 * k;
           if (gqk[2] && ((gqk[0] >> 5) != (f.t >> 5) || (gqk[1] >> 5) != (f.t >> 5))) same = true;
         }
@@ -1032,7 +1272,7 @@ __global__ void __launch_bounds__(256) witness_x_kernel(ScanArgs a) {
     }
     if (cross || same) {
       // rank in the tuple order (block, phase, thread, kind, warp phase)
-      const unsigned p = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
+      const unsigned p = syt.on ? coarse_q(syt, f.p) : f.p;
       const unsigned wv = f.p - p * syt.n_wp;
       const unsigned long long rank =
           ((((unsigned long long)xb << (a.phase_bits + a.thread_bits + kb)) |
@@ -1066,18 +1306,18 @@ __global__ void __launch_bounds__(256) witness_y_kernel(ScanArgs a) {
   const unsigned xp = (unsigned)(xr >> (wb + kb + a.thread_bits)) & ((1u << a.phase_bits) - 1u);
   const unsigned b0 = (unsigned)(xr >> (wb + kb + a.thread_bits + a.phase_bits));   // x's block
   const unsigned xq = xp * syt.n_wp + xw;
-  const unsigned xg = (unsigned)(syt.grid >> (4 * xq)) & 15u;
+  const unsigned xg = syt.on ? grid_q(a, syt, xq) : 0u;
   unsigned long long best = ~0ull;
   for (uint64_t i = s + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < e; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t key = a.keys[i];
     if ((key >> a.cell_shift) != wcell) continue;   // the bucket path's range holds other cells too
     const Fields f = fields(a, key);
-    const unsigned yp = syt.on ? (unsigned)(syt.coarse >> (4 * f.p)) & 15u : f.p;
+    const unsigned yp = syt.on ? coarse_q(syt, f.p) : f.p;
     const unsigned yw = f.p - yp * syt.n_wp;
     const bool other_thread = f.b != b0 || f.t != xt;
     bool concurrent;
     if (!syt.on) concurrent = f.b != b0 || f.p == xp;
-    else if (f.b != b0) concurrent = ((unsigned)(syt.grid >> (4 * f.p)) & 15u) == xg;
+    else if (f.b != b0) concurrent = grid_q(a, syt, f.p) == xg;
     else concurrent = yp == xp && ((f.t >> 5) != (xt >> 5) || yw == xw);
     if (other_thread && kinds_conflict(xk, f.k) && concurrent) {
       const unsigned long long rank =
@@ -1130,6 +1370,10 @@ cudaError_t launch_init_result(DevResult* res, cudaStream_t st, uint32_t n) {
   return cudaGetLastError();
 }
 
+// keys sorted by (cell, fine interval) of a check with warp or grid barriers
+// or atomics: the phase-order scan with interval summaries
+static bool phase_order_sync(const ScanArgs& a) { return !a.phase_table && (a.sync_tabs != nullptr || a.thread_shift == 2); }
+
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
   // the phase-table scan reads keys in 16-byte pairs
   if (a.phase_table && (reinterpret_cast<uintptr_t>(a.keys) & 15u) != 0u) return cudaErrorMisalignedAddress;
@@ -1150,10 +1394,15 @@ cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
         else scan_cells_table_kernel<false, false, false><<<blocks, kScanWarps * 32, 0, st>>>(a);
       }
     }
+    else if (phase_order_sync(a)) {
+      const uint64_t want = (a.n + 256ull * kSyncChunk - 1) / (256ull * kSyncChunk);
+      scan_sorted_sync_kernel<<<(unsigned)min(want, (uint64_t)152 * 16), 256, 0, st>>>(a);
+    }
     else scan_cells_kernel<<<blocks, kScanWarps * 32, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.phase_table) scan_long_table_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
+    else if (phase_order_sync(a)) scan_sorted_sync_long_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
     else scan_long_kernel<<<152 * 2, kLongThreads, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import workloads as w
-from workloads.spec import A, Access, Array, Model, Stmt, const, tid
+from workloads.spec import A, Access, Array, Model, Stmt, const, tid, R
 
 pytestmark = pytest.mark.gpu
 
@@ -89,7 +89,18 @@ def test_batch_mixed_atomic(rc):
         assert g.witness == exp.witness, m.name
 
 
-def test_atomics_need_phase_tables(rc):
+def test_atomics_beyond_phase_tables(rc):
+    """20 barrier intervals with atomics: keys sorted by (cell, interval) and
+    the phase-order scan; the hash path is refused for them."""
     m = Model((1, 1, 1), (8, 1, 1), [Array("c", "global", (4,))],
-              [Stmt([Access(0, A, (const(0),))], phase=const(19))], n_phases=20)
-    assert rc.binding.rc_model_create_status(m) == rc.binding.RC_E_UNSUPPORTED
+              [Stmt([Access(0, A, (const(0),))], phase=const(19)),
+               Stmt([Access(0, R, (const(0),))], guards=[-1 * tid.x], phase=const(19))], n_phases=20)
+    exp = oracle.check(m)
+    got = rc.check(m)
+    assert (got.racy_cells, got.witness) == (exp.racy_cells, exp.witness) and exp.racy_cells == 1
+    b = rc.binding
+    lay = b.rc_model_layout(b.rc_model_create(m))
+    assert lay["sort_lo"] == lay["phase_shift"]   # the sort takes the interval bits too
+    with pytest.raises(rc.RcError) as e:
+        rc.check(m, {"path": 2})
+    assert e.value.status == b.RC_E_UNSUPPORTED

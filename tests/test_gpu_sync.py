@@ -11,7 +11,7 @@ import torch
 
 import oracle
 import workloads as w
-from workloads.spec import A, Access, Array, Model, Stmt, const, tid, R, W
+from workloads.spec import A, Access, Array, Loop, Model, Stmt, bid, const, it, tid, R, W
 
 pytestmark = pytest.mark.gpu
 
@@ -89,11 +89,19 @@ def test_out_of_range_warp_phase(rc):
     compare(rc, m)
 
 
-def test_sync_models_rejected_where_unsupported(rc):
+def test_sync_models_beyond_phase_tables(rc):
+    """20 fine intervals with warp barriers: the phase-order scan; the hash
+    path is refused for them."""
     b = rc.binding
-    too_many = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
-                     [Stmt([Access(0, W, (tid.x,))], phase=const(0))], n_phases=5, n_warp_phases=4)
-    assert b.rc_model_create_status(too_many) == b.RC_E_UNSUPPORTED
+    many = Model((1, 1, 1), (64, 1, 1), [Array("s", "shared", (64,))],
+                 [Stmt([Access(0, W, (tid.x,))], phase=const(0)),
+                  Stmt([Access(0, R, ((tid.x + 32) % 64,))], phase=const(4), warp_phase=const(3))],
+                 n_phases=5, n_warp_phases=4)
+    assert b.rc_model_create_status(many) == b.RC_OK
+    compare(rc, many)
+    with pytest.raises(rc.RcError) as e:
+        rc.check(many, {"path": 2})
+    assert e.value.status == b.RC_E_UNSUPPORTED
 
 
 # ---------------------------------------------------------------------------
@@ -272,3 +280,77 @@ def test_batch_block_guards(rc, graph):
     other = [w.tiny_random_sync(s) for s in range(40)] + [w.tiny_random(s) for s in range(40)]
     got = check_batch(rc, _interleave(guarded, late, other), opts)
     assert sum(g.verdict for g in got) > 100
+
+
+# ---------------------------------------------------------------------------
+# more than 16 fine intervals: keys sorted by (cell, fine interval), the
+# phase-order scan (short cells per thread, long cells per block)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(200))
+def test_many_intervals(rc, seed):
+    compare(rc, w.tiny_random_sync(seed, many=True))
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_many_intervals_block_guards(rc, seed):
+    compare(rc, w.tiny_random_sync(seed, block_guards=True, many=True))
+
+
+@pytest.mark.parametrize("seed", range(100))
+def test_many_intervals_atomics_without_scopes(rc, seed):
+    compare(rc, w.tiny_random_sync(seed, many=True, scopes=False))
+
+
+def test_many_intervals_generated_kernel(rc, monkeypatch):
+    monkeypatch.setenv("RC_JIT", "1")
+    for seed in range(0, 200, 7):
+        compare(rc, w.tiny_random_sync(seed, many=True))
+        compare(rc, w.tiny_random_sync(seed, block_guards=True, many=True))
+
+
+def _interval_model(n_phases, n_wp, gp, blocks=64, racy=True):
+    """A hot counter cell and a spread array over n_phases x n_wp fine
+    intervals: every thread adds to c[0] in each barrier interval (warp
+    interval = its warp mod n_wp), lane 0 of each warp reads c[0] (racy with
+    the atomics of other warps in its block interval) unless `racy` is off,
+    and every thread writes then reads its neighbour's cell of d."""
+    c = Array("c", "global", (2,))
+    d = Array("d", "global", (blocks * 128 + 1,))
+    lane0 = [-1 * (tid.x % 32)]
+    gtid = bid.x * 128 + tid.x
+    stmts = [Stmt([Access(0, A, (const(0),))], loops=[Loop(0, n_phases)], phase=it(0),
+                  warp_phase=(tid.x // 32) % n_wp),
+             Stmt([Access(1, W, (gtid,))], phase=const(0), warp_phase=const(0)),
+             Stmt([Access(1, R, (gtid + 1,))], phase=const(n_phases - 1), warp_phase=const(n_wp - 1))]
+    if racy:
+        stmts.append(Stmt([Access(0, R, (const(0),))], guards=lane0, loops=[Loop(0, n_phases)], phase=it(0),
+                          warp_phase=const(0)))
+    return Model((blocks, 1, 1), (128, 1, 1), [c, d], stmts, n_phases=n_phases, n_warp_phases=n_wp,
+                 grid_phase=gp, name=f"intervals_{n_phases}x{n_wp}_{'racy' if racy else 'free'}")
+
+
+@pytest.mark.parametrize("n_phases,n_wp", [(10, 2), (10, 4), (5, 8)])
+@pytest.mark.parametrize("grid", ["none", "pairs", "each"])
+@pytest.mark.parametrize("racy", [True, False])
+def test_20_and_40_fine_intervals(rc, n_phases, n_wp, grid, racy):
+    """20 and 40 fine intervals; the hot cell has 64 x 128 x n_phases keys
+    (far above one thread's share: the long-cell pass)."""
+    gp = {"none": [0] * n_phases, "pairs": [p // 2 for p in range(n_phases)], "each": list(range(n_phases))}[grid]
+    compare(rc, _interval_model(n_phases, n_wp, gp, racy=racy))
+
+
+def test_many_intervals_chunked(rc):
+    for seed in range(0, 60, 3):
+        m = w.tiny_random_sync(seed, many=True)
+        compare(rc, m, {"flags": rc.binding.RC_OPT_CHUNKED})
+
+
+def test_many_intervals_in_batches(rc):
+    """Each model beyond 16 intervals holds its pack alone, beside packs of
+    ordinary and phase-table models."""
+    models = [w.tiny_random_sync(s, many=True) for s in range(30)] + [w.tiny_random_sync(s) for s in range(20)] + \
+             [w.tiny_random_sync(s, many=True, scopes=False) for s in range(15)] + \
+             [w.tiny_random(s) for s in range(10)] + [_interval_model(10, 4, [p // 2 for p in range(10)], blocks=8)]
+    for graph in (False, True):
+        check_batch(rc, models, {"flags": rc.binding.RC_OPT_GRAPH} if graph else None)

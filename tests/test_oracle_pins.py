@@ -603,3 +603,28 @@ def test_superset_tiny_tables_vs_python_bruteforce(seed):
     else:
         x, y = best
         assert r.witness == (x[0], x[1], x[2], (x[3], x[4], x[5], x[6]), (y[3], y[4], y[5], y[6]))
+
+
+# --------------------------------------------------------------------------
+# more than 16 fine intervals with warp / grid barriers or atomics
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(120))
+@pytest.mark.parametrize("kind", ["many", "many_bg", "noscopes"])
+def test_tiny_random_sync_many_intervals_vs_python_bruteforce(seed, kind):
+    m = w.tiny_random_sync(seed, block_guards=kind == "many_bg", many=True, scopes=kind != "noscopes")
+    assert m.n_phases * m.n_warp_phases > 16
+    r = oracle.check(m)
+    if r.instances > 6000:
+        pytest.skip("too large for the pairwise check")
+    st, cnt, best = pyref.check(m)
+    rb = oracle.brute(m)
+    assert st == "ok" and r.status == 0
+    assert r.racy_cells == cnt == rb.racy_cells
+    if best is None:
+        assert r.witness is None
+    else:
+        x, y = best
+        assert r.witness == (x[0], x[1], x[2], x[3:7], y[3:7]) == rb.witness
+        if len(x) == 8:
+            assert (r.x_wphase, r.y_wphase) == (x[7], y[7]) == (rb.x_wphase, rb.y_wphase)

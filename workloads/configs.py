@@ -601,7 +601,7 @@ def tiny_random(seed: int, atomic: float = 0.0) -> Model:
     return Model(grid, block, arrays, stmts, params=params, n_phases=n_phases, name=f"tiny{seed}")
 
 
-def tiny_random_sync(seed: int, block_guards: bool = False) -> Model:
+def tiny_random_sync(seed: int, block_guards: bool = False, many: bool = False, scopes: bool = True) -> Model:
     """A small random model with warp and grid barriers: one to three blocks of
     33..80 threads (so two or three warps), up to three barrier intervals
     mapped to up to three grid intervals, up to three warp intervals per
@@ -611,20 +611,31 @@ def tiny_random_sync(seed: int, block_guards: bool = False) -> Model:
     ``block_guards``: two to four blocks, and about half of the statements run
     in a subset of the blocks only (a guard ``bid.x - c >= 0`` or
     ``c - bid.x >= 0``), so that the lowest block of a cell may hold no racing
-    instance while later blocks of one grid interval do."""
+    instance while later blocks of one grid interval do.
+
+    ``many``: more than 16 fine intervals (6 to 14 barrier intervals of 3 or 4
+    warp intervals each, four to ten statements).  ``scopes=False`` (with
+    ``many``): no warp or grid barriers but 17 to 24 barrier intervals, with
+    atomics."""
     rng = SplitMix64(0x5C3A ^ (seed * 0x9E3779B97F4A7C15))
     n_blocks = rng.uniform_int(2, 4) if block_guards else rng.uniform_int(1, 3)
     T = rng.uniform_int(33, 80)
-    n_phases = rng.uniform_int(1, 3)
+    if many:
+        n_phases = rng.uniform_int(6, 14) if scopes else rng.uniform_int(17, 24)
+    else:
+        n_phases = rng.uniform_int(1, 3)
     gp, g = [], 0
     for _ in range(n_phases):
         gp.append(g)
-        if rng.chance(0.8 if block_guards else 0.4):
+        if rng.chance(0.8 if block_guards else 0.4) and scopes:
             g += 1
-    n_wp = rng.uniform_int(1, 3)
+    if many:
+        n_wp = rng.uniform_int(3, 4) if scopes else 1
+    else:
+        n_wp = rng.uniform_int(1, 3)
     arrays = [Array("sh", SHARED, (rng.uniform_int(4, 40),)), Array("gl", GLOBAL, (rng.uniform_int(4, 60),))]
     stmts = []
-    for si in range(rng.uniform_int(1, 5)):
+    for si in range(rng.uniform_int(4, 10) if many else rng.uniform_int(1, 5)):
         depth = rng.below(2)
         loops = [Loop(0, rng.uniform_int(1, 3))] if depth else []
         ph = const(rng.below(n_phases))
@@ -656,7 +667,9 @@ def tiny_random_sync(seed: int, block_guards: bool = False) -> Model:
                 guards.append(const(rng.below(2)) - tid.x)   # the first one or two threads only
         stmts.append(Stmt(accs, loops=loops, guards=guards, phase=ph, warp_phase=wp, name=f"y{si}"))
     return Model((n_blocks, 1, 1), (T, 1, 1), arrays, stmts, n_phases=n_phases, n_warp_phases=n_wp,
-                 grid_phase=gp, name=f"tinysync_{seed}{'_bg' if block_guards else ''}")
+                 grid_phase=gp if scopes else [],
+                 name=f"tinysync_{seed}{'_bg' if block_guards else ''}{'_many' if many else ''}"
+                      f"{'' if scopes else '_noscopes'}")
 
 
 def tiny_random_tables(seed: int, superset: bool = False) -> Model:
