@@ -380,7 +380,7 @@ def run_native(args):
             # our kernels per check: bucket path 20 with two partition passes (init, expansion,
             # 2 x (histogram, offsets), 2 passes, local sort, tail, scan (3), finish, witness (4);
             # offsets of pass B: 3); LSD path 11 + passes
-            "gpu_launches": ({3: 20, 2: 15, 1: 13}[n_pass] if bucketed else (11 + n_pass)) * args.steps,
+            "gpu_launches": ({3: 19, 2: 14, 1: 12}[n_pass] if bucketed else (11 + n_pass)) * args.steps,
         }
         line.update(subs)
         print(json.dumps(line), flush=True)
@@ -454,6 +454,62 @@ def run_wide(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# one model split by cell range, emulated on one GPU
+# ---------------------------------------------------------------------------
+def run_split(args):
+    """k-partition emulation of the one-model split (each rank checks the cells
+    of its range): the ranges of k ranks checked one after another on this
+    GPU, each timed alone with CUDA events.  The merged partial results must
+    equal the whole check; a rank's time is what it would take on its own GPU
+    (the k-rank job takes the slowest rank's)."""
+    import torch
+    import workloads as w
+    import paper_2503_08946_gb300 as rc
+    from paper_2503_08946_gb300 import build as b
+    from paper_2503_08946_gb300 import distributed as D
+
+    b.build()
+    rc.load()
+    model = w.random_affine(args.seed, n_blocks=args.blocks)
+    h = rc.rc_model_create(model)
+    total = rc.rc_model_layout(h)["total_cells"]
+    stream = torch.cuda.current_stream()
+    ws = rc.workspace(rc.rc_workspace_size(h, None))
+    whole = rc.rc_report(rc.rc_check(h, {"early_exit": 0}, ws, stream))[0]
+    steps = max(1, args.steps)
+    out = []
+    for k in [int(x) for x in args.parts.split(",")]:
+        per, parts = [], []
+        for lo, hi in D.cell_ranges(total, k):
+            o = {"early_exit": 0, "cell_lo": lo, "cell_hi": hi}
+            for _ in range(max(3, args.warmup)):
+                r = rc.rc_report(rc.rc_check(h, o, ws, stream))[0]
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                rc.rc_report(rc.rc_check(h, o, ws, stream))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            per.append(ev0.elapsed_time(ev1) / steps)
+            parts.append(r)
+        merged = D.merge_results(parts)
+        if (merged.racy_cells, merged.witness) != (whole.racy_cells, whole.witness):
+            raise RuntimeError(f"the merged {k}-way split differs from the whole check: {merged} vs {whole}")
+        out.append({"ranks": k, "rank_ms": [round(x, 3) for x in per], "slowest_rank_ms": round(max(per), 3),
+                    "speedup_vs_one": None})
+    base = out[0]["slowest_rank_ms"] if out and out[0]["ranks"] == 1 else None
+    for o in out:
+        o["speedup_vs_one"] = round(base / o["slowest_rank_ms"], 3) if base else None
+    print(json.dumps({"workload": "split", "config": {
+        "workload": WORKLOAD.replace("4096 blocks", f"{args.blocks} blocks"), "seed": args.seed,
+        "ranges": "equal cell ranges of the linear cell space (the read-only array's cells make no keys)",
+        "emulation": "ranks' ranges checked one after another on one GPU, each timed alone"},
+        "racy_cells": whole.racy_cells, "splits": out}), flush=True)
     return 0
 
 
@@ -789,7 +845,8 @@ def main():
                     help="default workload: which sub-records to add (comma-separated of hash, batch, serve)")
     ap.add_argument("--no-sub", action="store_true",
                     help="default workload: skip the hash, batch and serve sub-records")
-    ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve", "wide"],
+    ap.add_argument("--parts", default="1,2,4,8", help="split: the rank counts to emulate")
+    ap.add_argument("--workload", default="affine", choices=["affine", "batch", "serve", "wide", "split"],
                     help="affine: one ~1.1e9-instance model per step (default); batch: 10,000 small models; "
                          "serve: Poisson request stream through the request server")
     ap.add_argument("--batch-models", type=int, default=10000)
@@ -809,6 +866,8 @@ def main():
         return run_wide(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "split":
+        return run_split(args)
     return run_native(args)
 
 

@@ -564,13 +564,6 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
   }
 }
 
-// padding at [boff[nb], n): the scan ends at the first padding key
-__global__ void __launch_bounds__(256) bucket_tail_kernel(uint64_t* keys, const unsigned long long* end_pos,
-                                                          uint64_t n) {
-  const uint64_t from = *end_pos;
-  for (uint64_t i = from + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    keys[i] = kSentinel;
-}
 
 // one thread per result: the bucket of its smallest racy cell
 __global__ void bucket_finish_kernel(FinishArgs fa) {
@@ -642,9 +635,6 @@ cudaError_t launch_bucket_local_sort(const LocalSortArgs& a, cudaStream_t st) {
   const size_t smem = local_smem(a.rbin);
   if (h32) bucket_local_sort_kernel<true><<<grid, kLocThreads, smem, st>>>(a);
   else bucket_local_sort_kernel<false><<<grid, kLocThreads, smem, st>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  bucket_tail_kernel<<<152, 256, 0, st>>>(a.keys_out, a.boff + nb, a.n);
   return cudaGetLastError();
 }
 

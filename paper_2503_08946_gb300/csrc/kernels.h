@@ -204,6 +204,9 @@ struct ScanArgs {
   // keys grouped by cell but not in cell order (bucket path): the first racy
   // cell is kept by value in DevResult.hash_cell (phase-table scan only)
   uint32_t by_cell;
+  // phase-table scan: the number of keys on the device (the bucket path's
+  // kept keys, in front of the buffer), or null for n
+  const unsigned long long* n_dev;
   // keys sorted by (cell, fine interval) with warp or grid barriers: the grid
   // interval of each block interval (null: the 4-bit table of sync_tabs,
   // which covers fine intervals below 16)
@@ -219,9 +222,10 @@ cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_witness(const ScanArgs& a, cudaStream_t st);
 // bucket.cu: the local sort of the bucket path: every bucket b = keys
 // [boff[b], boff[b+1]) of keys_in (b < 2^D) put in cell order by the remaining
-// bits of h and written to the same positions of keys_out (padding dropped;
-// keys_out[boff[2^D], n) filled with padding), so that the ordered cell scan
-// can fold it (with ScanArgs.by_cell).
+// bits of h and written to the same positions of keys_out (padding dropped:
+// a bucket's kept keys come first in its range, padding after them), so that
+// the ordered cell scan can fold keys_out up to boff[2^D] (with
+// ScanArgs.by_cell and ScanArgs.n_dev; nothing behind it is read).
 struct LocalSortArgs {
   const uint64_t* keys_in;
   uint64_t* keys_out;

@@ -346,6 +346,7 @@ rc::ScanArgs scan_args(const rc::Model& m, const rc::WorkspacePlan& p, uint8_t* 
                               : nullptr;
   a.wit_block_bits = m.multi_grid ? m.host.block_bits : 0u;
   a.by_cell = 0;
+  a.n_dev = nullptr;
   a.grid_of = m.sec_gridof ? reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(m.dev_program) +
                                                                m.sec_gridof)
                            : nullptr;
@@ -484,6 +485,7 @@ rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* bu
   rc::ScanArgs sc = sa;
   sc.keys = scratch;
   sc.n = p.n_keys;
+  sc.n_dev = a.boff + ((size_t)1 << bp.D);   // the kept keys: the scan reads nothing behind them
   sc.by_cell = 1;
   sc.phase_table = 1;
   if (s == RC_OK) s = cuda_status(rc::launch_scan(sc, st));

@@ -370,6 +370,13 @@ __global__ void __launch_bounds__(kScanWarps * 32) scan_cells_kernel(ScanArgs a)
   }
 }
 
+// Keys of the scanned buffer: a.n, or fewer when the grouping step counted
+// them on the device (the bucket path keeps only guard-true keys of the
+// checked cell range, in front).
+__device__ __forceinline__ uint64_t scan_key_count(const ScanArgs& a) {
+  return a.n_dev ? min(a.n, (uint64_t)*a.n_dev) : a.n;
+}
+
 // One key as a CellPiece.
 __device__ __forceinline__ CellPiece key_piece(const ScanArgs& a, uint64_t k, uint64_t cell, uint64_t pos) {
   CellPiece c;
@@ -787,6 +794,7 @@ __device__ __forceinline__ void tfold_merge_warp(typename FoldOf<SY>::type& o, u
 // one at the smallest position (min_start, keys in cell order)
 template <bool AT, bool SY, bool MC>
 __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(ScanArgs a) {
+  const uint64_t n = scan_key_count(a);
   constexpr uint32_t kKindBits = AT ? 2 : 1;
   __shared__ unsigned tabs[kScanWarps][32 * kTabStride];
   __shared__ unsigned ctabs[kScanWarps][kTabPhases];
@@ -797,7 +805,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned* mytab = tabs[w] + lane * kTabStride;     // [0, 16): prefix part, [16, 32): own cells
   unsigned* ctab = ctabs[w];
-  const uint64_t n_seg = (a.n + kSegKeys - 1) / kSegKeys;
+  const uint64_t n_seg = (n + kSegKeys - 1) / kSegKeys;
   const uint64_t gw = (uint64_t)blockIdx.x * kScanWarps + w;
   const uint64_t per = (n_seg + a.n_warps - 1) / a.n_warps;
   const uint64_t seg0 = gw * per, seg1 = min(n_seg, seg0 + per);
@@ -847,7 +855,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     // each lane reads its own run of kScanRun consecutive keys directly (the
     // lines of a run are shared by its consecutive loads through L1)
     const uint64_t s = S + (uint64_t)lane * kScanRun;
-    const uint64_t kp = (s > 0 && s - 1 < a.n) ? __ldg(a.keys + s - 1) : kSentinel;
+    const uint64_t kp = (s > 0 && s - 1 < n) ? __ldg(a.keys + s - 1) : kSentinel;
     TF P, cur;
     tfold_clear(P);
     cur = P;
@@ -906,7 +914,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     };
     // pairs of keys by 16-byte loads (the key array is 16-byte aligned and runs
     // start at even positions; launch_scan checks the alignment)
-    const bool full_run = s + kScanRun <= a.n && __ldg(a.keys + s + kScanRun - 1) != kSentinel;
+    const bool full_run = s + kScanRun <= n && __ldg(a.keys + s + kScanRun - 1) != kSentinel;
     if (full_run) {
       const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(a.keys + s));
       fold_key(k0.x, 0, true, false);
@@ -918,9 +926,9 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
         fold_key(kk.y, q + 1, false, false);
       }
     } else {
-      fold_key(s < a.n ? __ldg(a.keys + s) : kSentinel, 0, true, true);
+      fold_key(s < n ? __ldg(a.keys + s) : kSentinel, 0, true, true);
 #pragma unroll 1
-      for (int q = 1; q < kScanRun; ++q) fold_key(s + q < a.n ? __ldg(a.keys + s + q) : kSentinel, q, false, true);
+      for (int q = 1; q < kScanRun; ++q) fold_key(s + q < n ? __ldg(a.keys + s + q) : kSentinel, q, false, true);
     }
     bool hasO = false;
     TF O = cur;
@@ -956,7 +964,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
     // (3) each lane's last cell continues through the following prefixes
     bool open = hasO;
     bool open_end = false;
-    if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= a.n)) {
+    if (open && (term || S + (uint64_t)(lane + 1) * kScanRun >= n)) {
       report(O, mytab + kTabPhases, O.start);
       open = false;
     }
@@ -1007,6 +1015,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 6) scan_cells_table_kernel(Sc
 // One block per handed-over cell, order-free: per-phase min / max (block,
 // thread) and write flags in shared memory.
 __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs a) {
+  const uint64_t n = scan_key_count(a);
   __shared__ unsigned mn[kTabPhases], mx[kTabPhases];
   __shared__ unsigned s_gw, s_ga, s_gr, s_minb, s_maxb, s_w;
   const uint32_t kb = a.thread_shift;   // kind field bits (R = 0, W = 1, A = 2)
@@ -1031,7 +1040,7 @@ __global__ void __launch_bounds__(kLongThreads) scan_long_table_kernel(ScanArgs 
     __syncthreads();
     for (uint64_t base = start;; base += kLongThreads) {
       const uint64_t pos = base + threadIdx.x;
-      bool end = pos >= a.n;
+      bool end = pos >= n;
       if (!end) {
         const uint64_t k = a.keys[pos];
         end = k == kSentinel || (k >> a.cell_shift) != cell;
