@@ -296,7 +296,9 @@ def run_native(args):
         if n_pass:
             kern["partition"] = (16.0 * n_keys, st_mean["sort_pass_ms"][0])
     kern["expand"] = (8.0 * n_keys, st_mean["expand_ms"])
-    kern["histogram"] = (8.0 * n_keys, st_mean["histogram_ms"])
+    hist_fused = bool(stages[0].get("histogram_fused"))
+    if not hist_fused:   # (else the expansion counted it: no pass over the keys)
+        kern["histogram"] = (8.0 * n_keys, st_mean["histogram_ms"])
     kern["scan"] = (8.0 * n_keys, st_mean["scan_ms"])
     launches = {"onesweep": max(1, n_pass - 1)} if not bucketed else {}
     dominant = max(kern, key=lambda k: kern[k][1] * launches.get(k, 1))
@@ -309,8 +311,9 @@ def run_native(args):
                 "traffic": (tpk * n_keys) if tpk is not None else None}
     per_kernel = {k: {"ms": v[1], "alg_bytes_per_key": v[0] / n_keys,
                       "frac": v[0] / (v[1] / 1e3) / 1e9 / peak if v[1] > 0 else None} for k, v in kern.items()}
-    # the whole check: expansion 8, histograms 8 each, passes 16 each, scan 8 bytes per key
-    pk = 8 + 8 + 16 * n_pass + 8 + (8 if bucketed and n_pass == 3 else 0)
+    # the whole check: expansion 8, histograms 8 each (none for a histogram the
+    # expansion counts), passes 16 each, scan 8 bytes per key
+    pk = 8 + (0 if hist_fused else 8) + 16 * n_pass + 8 + (8 if bucketed and n_pass == 3 else 0)
     pipeline_bytes = pk * n_keys
     pipeline = {"alg_bytes_per_key": pk,
                 "gbs": pipeline_bytes / (st_mean["check_ms"] / 1e3) / 1e9,
@@ -380,7 +383,7 @@ def run_native(args):
             # our kernels per check: bucket path 20 with two partition passes (init, expansion,
             # 2 x (histogram, offsets), 2 passes, local sort, tail, scan (3), finish, witness (4);
             # offsets of pass B: 3); LSD path 11 + passes
-            "gpu_launches": ({3: 19, 2: 14, 1: 12}[n_pass] if bucketed else (11 + n_pass)) * args.steps,
+            "gpu_launches": (({3: 19, 2: 14, 1: 12}[n_pass] - (1 if hist_fused else 0)) if bucketed else (11 + n_pass)) * args.steps,
         }
         line.update(subs)
         print(json.dumps(line), flush=True)

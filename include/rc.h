@@ -478,6 +478,9 @@ typedef struct rc_stage_times {
   uint64_t n_keys;         /* keys sorted and scanned                              */
   float histogram2_ms;     /* bucket path: the pass-B histogram and its offsets    */
   uint32_t bucketed;       /* 1: bucket path, 0: LSD radix sort and ordered scan   */
+  uint32_t histogram_fused;  /* 1: the generated expansion counted the pass-A
+                              histogram while writing the keys (histogram_ms then
+                              holds only its offsets)                              */
 } rc_stage_times;
 rc_status rc_ticket_stage_times(rc_ticket ticket, rc_stage_times* out);
 

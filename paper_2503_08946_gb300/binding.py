@@ -129,7 +129,7 @@ class rc_stage_times(Structure):
     _fields_ = [("expand_ms", ctypes.c_float), ("histogram_ms", ctypes.c_float),
                 ("sort_ms", ctypes.c_float * 16), ("n_sort_passes", c_uint32), ("scan_ms", ctypes.c_float),
                 ("witness_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("n_keys", c_uint64),
-                ("histogram2_ms", ctypes.c_float), ("bucketed", c_uint32)]
+                ("histogram2_ms", ctypes.c_float), ("bucketed", c_uint32), ("histogram_fused", c_uint32)]
 
 
 class rc_inst(Structure):
@@ -671,7 +671,8 @@ def rc_ticket_stage_times(ticket) -> dict:
     return {"expand_ms": st_.expand_ms, "histogram_ms": st_.histogram_ms,
             "sort_ms": [st_.sort_ms[i] for i in range(st_.n_sort_passes)], "scan_ms": st_.scan_ms,
             "witness_ms": st_.witness_ms, "total_ms": st_.total_ms, "n_keys": st_.n_keys,
-            "histogram2_ms": st_.histogram2_ms, "bucketed": bool(st_.bucketed)}
+            "histogram2_ms": st_.histogram2_ms, "bucketed": bool(st_.bucketed),
+            "histogram_fused": bool(st_.histogram_fused)}
 
 
 def rc_expand_keys(m: RcModel, workspace, keys, count, stream=None):

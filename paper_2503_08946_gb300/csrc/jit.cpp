@@ -243,9 +243,15 @@ struct Gen {
       o << in3 << "  key = (cl >= cell_lo && cl < cell_hi) ? ((cl << " << m.host.cell_shift
         << ") | ((unsigned long long)ph << " << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind)
         << ") : ~0ull; }\n";
-      if (A.key_idx < 0) o << in3 << "(void)key;\n";   // array never written: checked, no key
-      else if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)A.key_idx * T) << "] = key;\n";
-      else o << in3 << "keys[off + " << A.key_idx << "] = key;\n";
+      if (A.key_idx < 0) {
+        o << in3 << "(void)key;\n";   // array never written: checked, no key
+      } else {
+        // the pass-A histogram of the bucket path, counted as the keys are written
+        o << in3 << "if (hist_a != nullptr && key != ~0ull) atomicAdd(&hA[(unsigned)((((key >> "
+          << m.host.cell_shift << ") * " << ulit(kCellHashMul) << ") & hmask) >> hsh)], 1u);\n";
+        if (S.dense) o << in3 << "keys[slot + " << ulit((uint64_t)A.key_idx * T) << "] = key;\n";
+        else o << in3 << "keys[off + " << A.key_idx << "] = key;\n";
+      }
       o << in2 << "}\n";
     }
     o << in2 << "cnt += " << S.n_acc << ";\n";
@@ -328,12 +334,23 @@ struct Gen {
       o << "extern \"C\" __global__ void __launch_bounds__(128) rc_chunk_jit(const ChunkJitArgs a) {\n";
       o << "  unsigned long long* oob = a.oob;\n  const long long* tdata = a.tdata;\n  (void)tdata;\n";
     } else {
+      // hist_a: the bucket path's pass-A digit counts (null: not counted here);
+      // each block expands `units` consecutive 128-thread units of its
+      // statement, so that its shared histogram is flushed once for them all
       o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
            "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
-           "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata) {\n";
+           "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata, "
+           "unsigned long long* hist_a, unsigned long long hmask, unsigned hsh, unsigned hbins, unsigned units) {\n";
+      o << "  __shared__ unsigned hA[" << kBucketMaxHistBins << "];\n";
+      o << "  if (hist_a != nullptr) {\n"
+           "    for (unsigned i = threadIdx.x; i < hbins; i += 128u) hA[i] = 0u;\n"
+           "    __syncthreads();\n  }\n";
     }
-    o << "  const unsigned long long g = (unsigned long long)blockIdx.x * 128ull + threadIdx.x;\n";
     o << "  unsigned long long cnt = 0;\n";
+    if (!chunked) o << "  for (unsigned u = 0; u < units; ++u) {\n";
+    o << "  const unsigned long long g = " << (chunked ? "(unsigned long long)blockIdx.x" :
+                                                   "((unsigned long long)blockIdx.x * units + u)")
+      << " * 128ull + threadIdx.x;\n";
     o << "  if (g < " << ulit(h.n_threads) << ") {\n";
     o << "    const unsigned long long b = g / " << ulit(h.bs) << ";\n";
     o << "    const unsigned t = (unsigned)(g - b * " << ulit(h.bs) << ");\n";
@@ -347,8 +364,14 @@ struct Gen {
     o << "    switch (blockIdx.y) {\n";
     for (uint32_t s = 0; s < h.n_stmts; ++s) emit_stmt(s);
     o << "    default: break;\n    }\n  }\n";
+    if (!chunked) o << "  }\n";
     o << "  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);\n";
     o << "  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(" << (chunked ? "a.inst" : "inst") << ", cnt);\n";
+    if (!chunked)
+      o << "  if (hist_a != nullptr) {\n"
+           "    __syncthreads();\n"
+           "    for (unsigned i = threadIdx.x; i < hbins; i += 128u)\n"
+           "      if (hA[i]) atomicAdd(&hist_a[i], (unsigned long long)hA[i]);\n  }\n";
     o << "}\n";
     return o.str();
   }
@@ -442,7 +465,7 @@ cudaError_t jit_chunk_launch(const Model& m, const ChunkJitArgs& a, cudaStream_t
 }
 
 cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo,
-                              uint64_t cell_hi) {
+                              uint64_t cell_hi, const ExpandHist* eh) {
   Driver& dr = driver();
   CUfunction fn = reinterpret_cast<CUfunction>(m.jit_fn);
   unsigned long long* oob = &res->oob_code;
@@ -450,8 +473,15 @@ cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cu
   const uint64_t* uo = m.host.unit_offset;
   unsigned long long lo = cell_lo, hi = cell_hi;
   const int64_t* td = m.host.tdata;
-  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td};
-  const unsigned gx = (unsigned)((m.host.n_threads + 127) / 128);
+  unsigned long long* hist = eh ? eh->hist : nullptr;
+  unsigned long long hmask = eh ? eh->cmask : 0ull;
+  unsigned hsh = eh ? eh->shift : 0u, hbins = eh ? eh->bins : 0u;
+  if (hbins > (unsigned)kBucketMaxHistBins) return cudaErrorInvalidValue;
+  const uint64_t units_total = (m.host.n_threads + 127) / 128;
+  // with the histogram, blocks of kExpandHistUnits units (one flush per block)
+  unsigned units = eh ? kExpandHistUnits : 1u;
+  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td, &hist, &hmask, &hsh, &hbins, &units};
+  const unsigned gx = (unsigned)((units_total + units - 1) / units);
   const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }

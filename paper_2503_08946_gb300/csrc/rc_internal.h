@@ -443,8 +443,18 @@ std::string jit_expand_source(const Model& m);
 std::string jit_chunk_source(const Model& m);
 bool jit_expand_build(Model* m);
 cudaError_t jit_chunk_launch(const Model& m, const ChunkJitArgs& a, cudaStream_t st);
+// The bucket path's pass-A histogram counted by the generated expansion as it
+// writes the keys: digit = ((cell * kCellHashMul) & cmask) >> shift, bins
+// counters (at most kBucketMaxHistBins) added to hist.
+struct ExpandHist {
+  unsigned long long* hist;
+  uint64_t cmask;
+  uint32_t shift, bins;
+};
+constexpr int kBucketMaxHistBins = 1 << kBucketMaxDigitBits;
+constexpr unsigned kExpandHistUnits = 8;   // 128-thread units per block of a histogram-counting expansion
 cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo = 0,
-                              uint64_t cell_hi = ~0ull);
+                              uint64_t cell_hi = ~0ull, const ExpandHist* eh = nullptr);
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);

@@ -46,6 +46,7 @@ struct rc_ticket_s {
   int i_pass_from[16] = {}, i_pass_to[16] = {};   // events around each sort / partition pass
   int i_hist2_from = -1, i_hist2_to = -1;        // bucket path: the pass-B histogram
   bool bucketed = false;
+  bool hist_fused = false;                        // the expansion counted the pass-A histogram
   uint64_t n_keys = 0;
   cudaEvent_t done = nullptr;
   rc::DevResult* host = nullptr;   // pinned, `cap` records
@@ -89,6 +90,7 @@ rc_ticket_s* ticket_get(size_t n) {
         t->timer.ok = true;
         t->i_hist2_from = t->i_hist2_to = -1;
         t->bucketed = false;
+        t->hist_fused = false;
         return t;
       }
     }
@@ -411,7 +413,7 @@ rc_status enqueue_sort(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, 
 // pass-A histogram (i_hist), around each pass, around the pass-B histogram.
 rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* buf0, uint64_t* buf1,
                            const rc::ScanArgs& sa, cudaStream_t st, const uint64_t** final_keys,
-                           rc_ticket_s* timed = nullptr) {
+                           rc_ticket_s* timed = nullptr, bool hist_a_done = false) {
   const rc::BucketPlan& bp = p.bucket;
   StageTimer* tm = timed ? &timed->timer : nullptr;
   auto u64 = [&](size_t off) { return reinterpret_cast<unsigned long long*>(ws + off); };
@@ -443,7 +445,8 @@ rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* bu
   } else {
     a.keys_in = buf0;
     a.keys_out = buf1;
-    s = cuda_status(rc::launch_bucket_hist_a(a, st));
+    // (the generated expansion may have counted the pass-A histogram already)
+    if (!hist_a_done) s = cuda_status(rc::launch_bucket_hist_a(a, st));
     if (s == RC_OK) s = cuda_status(rc::launch_bucket_scan_a(a, st));
     if (tm) { timed->i_hist = tm->n; tm->mark(); }
     if (s == RC_OK) s = cuda_status(rc::launch_bucket_pass_a(a, st));
@@ -571,9 +574,20 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   s = cuda_status(cudaMemsetAsync(ws + p.zero_lo, 0, p.zero_hi - p.zero_lo, st));
   if (s != RC_OK) return s;
   if (tm) { timed->i_start = tm->n; tm->mark(); }
+  // the bucket path's pass-A histogram is counted by the generated expansion
+  // as it writes the keys (the interpreted expansion leaves it to its kernel)
+  rc::ExpandHist eh{};
+  const bool fuse_hist = p.bucket.on && p.bucket.D > 0 && m.jit_fn != nullptr && p.bucket.dA <= rc::kBucketMaxDigitBits;
+  if (fuse_hist) {
+    eh.hist = reinterpret_cast<unsigned long long*>(ws + p.bucket.hist_a);
+    eh.cmask = p.bucket.cb >= 64 ? ~0ull : ((1ull << p.bucket.cb) - 1ull);
+    eh.shift = p.bucket.cb - p.bucket.dA;
+    eh.bins = 1u << p.bucket.dA;
+  }
+  if (timed) timed->hist_fused = fuse_hist;
   if (m.jit_fn)
-    s = cuda_status(
-        rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
+    s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo,
+                                          cell_hi, fuse_hist ? &eh : nullptr));
   else
     s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
                                       reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
@@ -584,7 +598,7 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     const uint64_t* fin = nullptr;
     rc::ScanArgs sa = scan_args(m, p, ws, 0);
     s = enqueue_bucketed(p, ws, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]),
-                         reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), sa, st, &fin, timed);
+                         reinterpret_cast<uint64_t*>(ws + p.keys_off[1]), sa, st, &fin, timed, fuse_hist);
     if (s != RC_OK) return s;
     if (tm) { timed->i_scan = tm->n; tm->mark(); }
     sa.keys = fin;
@@ -1905,6 +1919,7 @@ rc_status rc_ticket_stage_times(rc_ticket t, rc_stage_times* out) {
   }
   if (t->i_hist2_from >= 0) out->histogram2_ms = ms(t->i_hist2_from, t->i_hist2_to);
   out->bucketed = t->bucketed ? 1u : 0u;
+  out->histogram_fused = t->hist_fused ? 1u : 0u;
   out->scan_ms = ms(prev, t->i_scan);
   out->witness_ms = ms(t->i_scan, t->i_wit);
   out->total_ms = ms(t->i_start, t->i_wit);

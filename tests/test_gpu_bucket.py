@@ -216,3 +216,35 @@ def test_padding_with_reused_workspace(rc):
             g = b.rc_report(b.rc_check(h, None, ws), wait=True)[0]
             exp = oracle.check(m)
             assert full(g) == full(exp), (rep, m.name, g, exp)
+
+
+def _stages(rc, model, opts=None):
+    b = rc.binding
+    h = b.rc_model_create(model)
+    o = dict(opts or {})
+    o["flags"] = o.get("flags", 0) | b.RC_OPT_STAGE_TIMES
+    ws = b.workspace(b.rc_workspace_size(h, o))
+    t = b.rc_check(h, o, ws)
+    st = b.rc_ticket_stage_times(t)
+    return st, b.rc_report(t, wait=True)[0]
+
+
+@pytest.mark.parametrize("seed,blocks,plant", [(3, 64, False), (5, 64, True), (9, 16, True)])
+def test_histogram_counted_by_expansion(rc, seed, blocks, plant, monkeypatch):
+    """The generated expansion counts the pass-A histogram as it writes the
+    keys; the interpreted expansion leaves it to the histogram kernel.  Both
+    give the oracle's result (a wrong count would misplace keys in pass A)."""
+    m = w.random_affine(seed, n_blocks=blocks, block=256, plant=plant)
+    monkeypatch.setenv("RC_JIT", "1")
+    st1, r1 = _stages(rc, m)
+    monkeypatch.setenv("RC_JIT", "0")
+    st0, r0 = _stages(rc, m)
+    assert st1["bucketed"] and st1["histogram_fused"] and not st0["histogram_fused"]
+    assert full(r1) == full(r0)
+    compare(rc, m)
+    # a cell range: only the kept keys are counted
+    lo = rc.binding.rc_model_layout(rc.binding.rc_model_create(m))["total_cells"] // 3
+    monkeypatch.setenv("RC_JIT", "1")
+    g = rc.check(m, {"cell_lo": lo, "cell_hi": 2 * lo})
+    exp = oracle.check_cells(m, lo, 2 * lo)
+    assert full(g) == full(exp)
