@@ -378,9 +378,10 @@ size_t local_smem(uint32_t rbin) { return (size_t)kFoldCap * 8 + ((size_t)8 << r
 
 // Exclusive scan in place of n counters by a block of NT threads (each thread
 // a run of consecutive counters, read and written 16 bytes at a time when the
-// run is a multiple of 4); *total receives the sum.
+// run is a multiple of 4); *total receives the sum, bin2 (if given) the same
+// exclusive prefix (the scatter's cursors).
 template <int NT>
-__device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n, unsigned* total) {
+__device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n, unsigned* total, unsigned* bin2 = nullptr) {
   static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, at most 32");
   __shared__ unsigned wsum[NT / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -431,12 +432,14 @@ __device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n, unsigned* to
         o.z = run; run += v[i + 2];
         o.w = run; run += v[i + 3];
         *reinterpret_cast<uint4*>(bin + b0 + i) = o;
+        if (bin2) *reinterpret_cast<uint4*>(bin2 + b0 + i) = o;
       }
   } else {
     for (unsigned i = 0; i < per; ++i)
       if (b0 + i < n) {
         const unsigned c = bin[b0 + i];
         bin[b0 + i] = run;
+        if (bin2) bin2[b0 + i] = run;
         run += c;
       }
   }
@@ -448,8 +451,10 @@ __device__ __forceinline__ void bin_scan(unsigned* bin, unsigned n, unsigned* to
 // order by insertion sort) and written to the same positions of keys_out.  A
 // bucket of at most kFoldCap keys is read once into registers and sorted in
 // shared memory; a larger one is read twice and scattered to keys_out.
-// Padding keys (the unpartitioned single bucket holds them) are dropped; the
-// positions [boff[nb], n) of keys_out are filled with padding (bucket_tail).
+// Padding keys (the unpartitioned single bucket holds them) are dropped and the
+// bucket's tail becomes padding; keys_out behind boff[nb] is left as it is (the
+// scan reads up to boff[nb]).  Each thread's key slots past the bucket's length
+// are skipped as a block (nq, block-uniform).
 // H32: cb <= 32, so h is computed in 32-bit arithmetic (the same value: the
 // product modulo 2^cb depends only on the low 32 bits of each factor).
 template <bool H32>
@@ -490,25 +495,29 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
     __syncthreads();
     if (in_smem) {
       // one read of the bucket into registers, all loads in flight together
+      const int nq = (int)((len + kLocThreads - 1) / kLocThreads);   // block-uniform
       uint64_t kr[kLocKPT];
 #pragma unroll
       for (int q = 0; q < kLocKPT; ++q) {
+        if (q >= nq) break;
         const uint64_t i = (uint64_t)q * kLocThreads + tid;
         kr[q] = i < len ? __ldg(src + i) : kSentinel;
       }
 #pragma unroll
-      for (int q = 0; q < kLocKPT; ++q)
+      for (int q = 0; q < kLocKPT; ++q) {
+        if (q >= nq) break;
         if (kr[q] != kSentinel) atomicAdd(&s_bin[bin_of(kr[q])], 1u);
-      __syncthreads();
-      bin_scan<kLocThreads>(s_bin, nbins, &s_total);
+      }
       __syncthreads();
       // the cursors live in the bins' copy: starts stay in s_bin for the ranges below
       unsigned* cur = s_bin + nbins;
-      for (unsigned i = tid; i < nbins; i += kLocThreads) cur[i] = s_bin[i];
+      bin_scan<kLocThreads>(s_bin, nbins, &s_total, cur);
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < kLocKPT; ++q)
+      for (int q = 0; q < kLocKPT; ++q) {
+        if (q >= nq) break;
         if (kr[q] != kSentinel) s_keys[atomicAdd(&cur[bin_of(kr[q])], 1u)] = kr[q];
+      }
     } else {
       // read twice from global memory; the cursors live in the (unused) key buffer
       unsigned* cur = reinterpret_cast<unsigned*>(s_keys);

@@ -478,9 +478,15 @@ cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cu
   unsigned hsh = eh ? eh->shift : 0u, hbins = eh ? eh->bins : 0u;
   if (hbins > (unsigned)kBucketMaxHistBins) return cudaErrorInvalidValue;
   const uint64_t units_total = (m.host.n_threads + 127) / 128;
-  // with the histogram, blocks of kExpandHistUnits units (one flush per block)
-  unsigned units = eh ? kExpandHistUnits : 1u;
-  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td, &hist, &hmask, &hsh, &hbins, &units};
+  // with the histogram, blocks of up to kExpandHistUnits units (one flush per
+  // block), as long as the grid keeps about 64 blocks per SM
+  uint64_t units = 1;
+  if (eh) {
+    units = units_total * m.host.n_stmts / (152ull * 64ull);
+    units = units < 1 ? 1 : (units > kExpandHistUnits ? kExpandHistUnits : units);
+  }
+  unsigned units32 = (unsigned)units;
+  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td, &hist, &hmask, &hsh, &hbins, &units32};
   const unsigned gx = (unsigned)((units_total + units - 1) / units);
   const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
