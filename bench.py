@@ -485,10 +485,12 @@ def run_split(args):
     whole = rc.rc_report(rc.rc_check(h, {"early_exit": 0}, ws, stream))[0]
     steps = max(1, args.steps)
     out = []
-    for k in [int(x) for x in args.parts.split(",")]:
+    for by, k in [(by, int(x)) for by in ("range", "hash") for x in args.parts.split(",")]:
         per, parts = [], []
-        for lo, hi in D.cell_ranges(total, k):
-            o = {"early_exit": 0, "cell_lo": lo, "cell_hi": hi}
+        for rank in range(k):
+            o = D.partition_opts(h, rank, k, {"early_exit": 0}, by=by)
+            if rc.rc_workspace_size(h, o) > ws.numel():   # (a part's plan needs no more than the whole check's)
+                raise RuntimeError("a partial check needs more workspace than the whole check")
             for _ in range(max(3, args.warmup)):
                 r = rc.rc_report(rc.rc_check(h, o, ws, stream))[0]
             torch.cuda.synchronize()
@@ -503,14 +505,15 @@ def run_split(args):
         merged = D.merge_results(parts)
         if (merged.racy_cells, merged.witness) != (whole.racy_cells, whole.witness):
             raise RuntimeError(f"the merged {k}-way split differs from the whole check: {merged} vs {whole}")
-        out.append({"ranks": k, "rank_ms": [round(x, 3) for x in per], "slowest_rank_ms": round(max(per), 3),
+        out.append({"by": by, "ranks": k, "rank_ms": [round(x, 3) for x in per], "slowest_rank_ms": round(max(per), 3),
                     "speedup_vs_one": None})
-    base = out[0]["slowest_rank_ms"] if out and out[0]["ranks"] == 1 else None
+    base = next((o["slowest_rank_ms"] for o in out if o["ranks"] == 1), None)
     for o in out:
         o["speedup_vs_one"] = round(base / o["slowest_rank_ms"], 3) if base else None
     print(json.dumps({"workload": "split", "config": {
         "workload": WORKLOAD.replace("4096 blocks", f"{args.blocks} blocks"), "seed": args.seed,
-        "ranges": "equal cell ranges of the linear cell space (the read-only array's cells make no keys)",
+        "partitions": "range: equal cell ranges of the linear cell space (the read-only array's cells make no keys); "
+                      "hash: the check options' hash parts of the cells",
         "emulation": "ranks' ranges checked one after another on one GPU, each timed alone"},
         "racy_cells": whole.racy_cells, "splits": out}), flush=True)
     return 0

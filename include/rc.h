@@ -293,6 +293,26 @@ typedef struct rc_check_opts {
                            /* the witness is the one of the lowest racy range      */
                            /* (a model split across processes or GPUs).  Ignored   */
                            /* by rc_check_batch.                                   */
+  uint32_t part_count;     /* partial check by hash part (0 or 1 = none; else a
+                              power of two 2^p with p <= rc_layout.cell_bits): only
+                              the cells c whose part
+                                ((c * 0x9E3779B97F4A7C15) mod 2^cb) >> (cb - p),
+                              cb = rc_layout.cell_bits, equals part_index are
+                              checked (with cell_lo / cell_hi both apply).  The
+                              multiplier is odd, so this is a bijection of the cell
+                              field: every cell has exactly one part, and the parts
+                              hold about equal shares of the keys whatever the
+                              access pattern, so part_count ranks taking parts
+                              0 .. part_count - 1 split one model evenly; their
+                              racy cells add up and the model's witness is the
+                              racy part's witness with the smallest cell.  (It is
+                              also the bucket path's hash, whose remaining cb - p
+                              bits the part groups by.)  Sort path of rc_check
+                              only (RC_E_UNSUPPORTED on the hash path, for chunked
+                              checks and wide models; ignored by rc_check_batch);
+                              a part count that is not a power of two, or
+                              part_index >= part_count, is RC_E_INVALID.          */
+  uint32_t part_index;
 } rc_check_opts;
 enum { RC_TEST_STALL_LOOKBACK = 1,
        RC_TEST_FEW_SCAN_WARPS = 2   /* scan with 3 warps (long ranges per warp) */ };

@@ -63,6 +63,8 @@ def _load():
             lib.oracle_check.restype = ctypes.c_int
             lib.oracle_check_cells.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_int64, p64]
             lib.oracle_check_cells.restype = ctypes.c_int
+            lib.oracle_check_part.argtypes = [ctypes.c_char_p, ctypes.c_int64, ctypes.c_int64, p64]
+            lib.oracle_check_part.restype = ctypes.c_int
             lib.oracle_check_parallel.argtypes = [ctypes.c_char_p, ctypes.c_int, p64]
             lib.oracle_check_parallel.restype = ctypes.c_int
             lib.oracle_cell_count.argtypes = [ctypes.c_char_p]
@@ -209,6 +211,15 @@ def check_cells(m, lo: int, hi: int) -> OracleResult:
     lib = _load()
     buf = (ctypes.c_int64 * len(FIELDS))()
     lib.oracle_check_cells(model_text(m).encode(), int(lo), int(hi), buf)
+    return _result(buf)
+
+
+def check_part(m, part_count: int, part_index: int) -> OracleResult:
+    """Oracle check restricted to the cells of one hash part (the check
+    options' part_count, a power of two, and part_index)."""
+    lib = _load()
+    buf = (ctypes.c_int64 * len(FIELDS))()
+    lib.oracle_check_part(model_text(m).encode(), int(part_count), int(part_index), buf)
     return _result(buf)
 
 

@@ -432,6 +432,11 @@ struct OobRecord {
 struct CellRange {
   bool all = true;
   int64_t lo = 0, hi = 0;
+  // hash part (part_count = 2^p > 1): the cells whose part, by the definition
+  // of the check options, ((cell * 0x9E3779B97F4A7C15) mod 2^cb) >> (cb - p)
+  // with cb = bit_length(number of cells), is part_index
+  uint64_t part_count = 0, part_index = 0;
+  uint32_t cb = 0;
 };
 
 struct Enumerator {
@@ -486,6 +491,13 @@ struct Enumerator {
       if (!range.all) {
         int64_t lin = cell_base[x.a] + x.s * cell_size[x.a] + x.e;
         if (lin < range.lo || lin >= range.hi) continue;
+        if (range.part_count > 1) {
+          uint32_t p = 0;
+          while ((1ull << p) < range.part_count) ++p;
+          uint64_t hsh = (uint64_t)lin * 0x9E3779B97F4A7C15ull;
+          if (range.cb < 64) hsh &= (1ull << range.cb) - 1ull;
+          if ((hsh >> (range.cb - p)) != range.part_index) continue;
+        }
       }
       out.push_back(x);
     }
@@ -771,6 +783,35 @@ int oracle_check_cells(const char* text, int64_t lo, int64_t hi, int64_t* out) {
     Model m = p.model();
     CellRange r;
     r.all = false; r.lo = lo; r.hi = hi;
+    return check_model(m, r, out);
+  } catch (const std::exception&) {
+    clear(out);
+    out[F_STATUS] = ST_INVALID;
+    return ST_INVALID;
+  }
+}
+
+// The same check restricted to the cells of one hash part (the partition of a
+// model over ranks by the check options' part_count / part_index).
+int oracle_check_part(const char* text, int64_t part_count, int64_t part_index, int64_t* out) {
+  try {
+    Parser p(text);
+    Model m = p.model();
+    CellRange r;
+    r.all = false;
+    r.lo = 0;
+    r.hi = INT64_MAX;
+    r.part_count = (uint64_t)part_count;
+    r.part_index = (uint64_t)part_index;
+    // cb: the bits of the number of cells (arrays in order, shared arrays once per block)
+    int64_t total = 0;
+    const int64_t nblocks = m.grid[0] * m.grid[1] * m.grid[2];
+    for (const Array& a : m.arrays) {
+      int64_t sz = 1;
+      for (int64_t e : a.ext) sz *= e;
+      total += sz * (a.shared ? nblocks : 1);
+    }
+    while (r.cb < 63 && (1ull << r.cb) <= (uint64_t)total) ++r.cb;
     return check_model(m, r, out);
   } catch (const std::exception&) {
     clear(out);

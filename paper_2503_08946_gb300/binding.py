@@ -122,7 +122,8 @@ class rc_layout(Structure):
 class rc_check_opts(Structure):
     _fields_ = [("path", c_uint32), ("digit_bits", c_uint32), ("early_exit", c_uint32),
                 ("test_flags", c_uint32), ("flags", c_uint32), ("reserved", c_uint32),
-                ("spin_limit", c_uint64), ("cell_lo", c_uint64), ("cell_hi", c_uint64)]
+                ("spin_limit", c_uint64), ("cell_lo", c_uint64), ("cell_hi", c_uint64),
+                ("part_count", c_uint32), ("part_index", c_uint32)]
 
 
 class rc_stage_times(Structure):

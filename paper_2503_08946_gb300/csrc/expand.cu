@@ -21,13 +21,15 @@ namespace cg = cooperative_groups;
 namespace {
 
 // Sort-path sink: keys go to their slot; guard-false dense slots get padding,
-// and so do keys whose cell lies outside [cell_lo, cell_hi) (a partial check
-// of a cell range).
+// and so do keys whose cell lies outside [cell_lo, cell_hi) or outside the
+// hash part of a partial check.
 struct SlotSink {
   uint64_t* keys;
   uint64_t cell_lo, cell_hi;
+  uint64_t pmask, pval;
   __device__ __forceinline__ void put(uint64_t i, uint64_t key, uint64_t cell) {
-    keys[i] = (cell >= cell_lo && cell < cell_hi) ? key : kSentinel;
+    const bool part_ok = pmask == 0ull || ((cell * kCellHashMul) & pmask) == pval;
+    keys[i] = (cell >= cell_lo && cell < cell_hi && part_ok) ? key : kSentinel;
   }
   __device__ __forceinline__ void pad(uint64_t i) { keys[i] = kSentinel; }
 };
@@ -251,8 +253,8 @@ int grid_for(uint64_t n_units) {
 }  // namespace
 
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
-                          DevResult* res, cudaStream_t st, uint64_t cell_lo, uint64_t cell_hi) {
-  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, SlotSink{keys, cell_lo, cell_hi}, st);
+                          DevResult* res, cudaStream_t st, const CellFilter& cf) {
+  return launch_expand_sink(dm, n_stmts, n_threads, has_deep, res, SlotSink{keys, cf.lo, cf.hi, cf.pmask, cf.pval}, st);
 }
 
 cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,

@@ -240,7 +240,8 @@ struct Gen {
       o << in3 << "if (dc != 0xFFFFFFFFu) { atomicMin(oob, " << ulit(pack)
         << " | ((g & 0x3FFFFFFFFFFull) << 3) | dc); key = ~0ull; }\n";
       o << in3 << "else { const unsigned long long cl = " << cell << ";\n";
-      o << in3 << "  key = (cl >= cell_lo && cl < cell_hi) ? ((cl << " << m.host.cell_shift
+      o << in3 << "  key = (cl >= cell_lo && cl < cell_hi && (part_mask == 0ull || ((cl * " << ulit(kCellHashMul)
+        << ") & part_mask) == part_val)) ? ((cl << " << m.host.cell_shift
         << ") | ((unsigned long long)ph << " << m.host.phase_shift << ") | low | " << ulit((uint64_t)A.kind)
         << ") : ~0ull; }\n";
       if (A.key_idx < 0) {
@@ -339,7 +340,8 @@ struct Gen {
       // statement, so that its shared histogram is flushed once for them all
       o << "extern \"C\" __global__ void __launch_bounds__(128) rc_expand_jit(unsigned long long* __restrict__ keys, "
            "unsigned long long* oob, unsigned long long* inst, const unsigned long long* __restrict__ unit_offset, "
-           "unsigned long long cell_lo, unsigned long long cell_hi, const long long* __restrict__ tdata, "
+           "unsigned long long cell_lo, unsigned long long cell_hi, unsigned long long part_mask, unsigned long long part_val, "
+           "const long long* __restrict__ tdata, "
            "unsigned long long* hist_a, unsigned long long hmask, unsigned hsh, unsigned hbins, unsigned units) {\n";
       o << "  __shared__ unsigned hA[" << kBucketMaxHistBins << "];\n";
       o << "  if (hist_a != nullptr) {\n"
@@ -464,14 +466,15 @@ cudaError_t jit_chunk_launch(const Model& m, const ChunkJitArgs& a, cudaStream_t
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 
-cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo,
-                              uint64_t cell_hi, const ExpandHist* eh) {
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, const CellFilter& cf,
+                              const ExpandHist* eh) {
   Driver& dr = driver();
   CUfunction fn = reinterpret_cast<CUfunction>(m.jit_fn);
   unsigned long long* oob = &res->oob_code;
   unsigned long long* inst = &res->instances;
   const uint64_t* uo = m.host.unit_offset;
-  unsigned long long lo = cell_lo, hi = cell_hi;
+  unsigned long long lo = cf.lo, hi = cf.hi;
+  unsigned long long pmask = cf.pmask, pval = cf.pval;
   const int64_t* td = m.host.tdata;
   unsigned long long* hist = eh ? eh->hist : nullptr;
   unsigned long long hmask = eh ? eh->cmask : 0ull;
@@ -486,7 +489,7 @@ cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cu
     units = units < 1 ? 1 : (units > kExpandHistUnits ? kExpandHistUnits : units);
   }
   unsigned units32 = (unsigned)units;
-  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &td, &hist, &hmask, &hsh, &hbins, &units32};
+  void* params[] = {&keys, &oob, &inst, &uo, &lo, &hi, &pmask, &pval, &td, &hist, &hmask, &hsh, &hbins, &units32};
   const unsigned gx = (unsigned)((units_total + units - 1) / units);
   const CUresult r = dr.launch(fn, gx, m.host.n_stmts, 1, 128, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

@@ -15,9 +15,9 @@ cudaError_t ensure_kernel_smem(const void* func, size_t smem_bytes, bool max_car
 
 // expand.cu
 // has_deep: some statement has more than kFastLoops loops (runs the generic kernel too)
-// keys whose cell lies outside [cell_lo, cell_hi) are written as padding
+// keys of cells the filter does not keep (a partial check) are written as padding
 cudaError_t launch_expand(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep, uint64_t* keys,
-                          DevResult* res, cudaStream_t st, uint64_t cell_lo = 0, uint64_t cell_hi = ~0ull);
+                          DevResult* res, cudaStream_t st, const CellFilter& cf = CellFilter());
 // Count pass of a chunked check: counts[(cell - lo) >> bshift] += keys of the
 // cells in [lo, lo + span) (instances and out-of-bounds reports go to res).
 cudaError_t launch_expand_count(const DevModel* dm, uint32_t n_stmts, uint64_t n_threads, bool has_deep,

@@ -335,6 +335,7 @@ inline uint32_t plan_max_bits(const SortPlan& sp) {
 // The bucket path of the grouping step (bucket.cu): see kernels.h.
 constexpr uint32_t kSortThreadsHost = 256;
 constexpr uint64_t kCellHashMul = 0x9E3779B97F4A7C15ull;
+
 constexpr uint32_t kBucketMaxDigitBits = 10;        // per partition pass
 constexpr uint32_t kBucketMaxBits = 2 * kBucketMaxDigitBits;
 constexpr int kFoldCap = 7680;                      // keys of a bucket folded in shared memory
@@ -357,7 +358,7 @@ struct BucketPlan {
 // host (runtime.cu): whether the bucket path applies to n keys of cb cell bits
 // (at most 2^kBucketMaxBits buckets of about kBucketTarget keys), its digit
 // widths, and its workspace section laid out from byte offset `off`
-bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp);
+bool plan_buckets(uint64_t n, uint64_t n_expect, uint32_t cb, size_t off, BucketPlan* bp);
 
 
 struct WorkspacePlan {
@@ -453,8 +454,14 @@ struct ExpandHist {
 };
 constexpr int kBucketMaxHistBins = 1 << kBucketMaxDigitBits;
 constexpr unsigned kExpandHistUnits = 8;   // 128-thread units per block of a histogram-counting expansion
-cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st, uint64_t cell_lo = 0,
-                              uint64_t cell_hi = ~0ull, const ExpandHist* eh = nullptr);
+// cells kept by a partial check: [lo, hi) and the hash part
+// ((c * kCellHashMul) & pmask) == pval (pmask = pval = 0: every part)
+struct CellFilter {
+  uint64_t lo = 0, hi = ~0ull;
+  uint64_t pmask = 0, pval = 0;
+};
+cudaError_t jit_expand_launch(const Model& m, uint64_t* keys, DevResult* res, cudaStream_t st,
+                              const CellFilter& cf = CellFilter(), const ExpandHist* eh = nullptr);
 
 // implemented in lower.cpp
 rc_status lower_model(const rc_model_desc* d, Model* m, std::vector<int32_t>* general_stmt_ids);

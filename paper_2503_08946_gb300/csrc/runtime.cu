@@ -223,12 +223,15 @@ bool bucket_path_allowed(uint32_t phase_bits, const rc_check_opts* opts) {
   return true;
 }
 
-bool plan_buckets(uint64_t n, uint32_t cb, size_t off, BucketPlan* bp) {
+// n key slots, of which about n_expect are kept (a hash-partitioned check keeps
+// its share): the bucket count is chosen for n_expect, the tile bounds for n
+bool plan_buckets(uint64_t n, uint64_t n_expect, uint32_t cb, size_t off, BucketPlan* bp) {
   *bp = BucketPlan();
   if (n == 0 || n >= (1ull << 32) || cb == 0 || cb > 62) return false;
+  if (n_expect == 0 || n_expect > n) n_expect = n;
   uint32_t D = 0;
-  while (D < cb && D < kBucketMaxBits && (n >> D) > kBucketTarget) ++D;
-  if (D == kBucketMaxBits && D < cb && (n >> D) > kBucketTarget) return false;   // more keys than the buckets hold
+  while (D < cb && D < kBucketMaxBits && (n_expect >> D) > kBucketTarget) ++D;
+  if (D == kBucketMaxBits && D < cb && (n_expect >> D) > kBucketTarget) return false;   // more keys than the buckets hold
   bp->on = true;
   bp->n = n;
   bp->cb = cb;
@@ -281,7 +284,14 @@ void plan_workspace_keys(const Model& m, const rc_check_opts* opts, uint64_t n, 
   off = align256(off + n * 8);
   p->keys_off[1] = off;
   off = align256(off + n * 8);
-  if (allow_bucket && bucket_path_allowed(m.host.phase_bits, opts) && plan_buckets(n, cell_bits, off, &p->bucket)) {
+  // a hash part keeps about 1 / part_count of the keys (the parts are
+  // near-equal; 1/16 more for the spread), all with the same top bits of the
+  // cell hash: its buckets are cut from the hash's remaining bits
+  const bool part = opts && opts->part_count > 1;
+  const uint32_t part_bits = part ? bit_length(opts->part_count - 1) : 0u;
+  const uint64_t n_expect = part ? n / opts->part_count + n / (16ull * opts->part_count) + 1 : n;
+  if (allow_bucket && bucket_path_allowed(m.host.phase_bits, opts) && cell_bits > part_bits &&
+      plan_buckets(n, n_expect, cell_bits - part_bits, off, &p->bucket)) {
     // the bucket path: its own section instead of the radix-sort sections
     p->zero_lo = p->bucket.zero_lo;
     p->zero_hi = p->bucket.zero_hi;
@@ -585,12 +595,20 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
     eh.bins = 1u << p.bucket.dA;
   }
   if (timed) timed->hist_fused = fuse_hist;
+  rc::CellFilter cf;
+  cf.lo = cell_lo;
+  cf.hi = cell_hi;
+  if (opts && opts->part_count > 1) {
+    const uint32_t pb = rc::bit_length(opts->part_count - 1), sh = m.host.cell_bits - pb;
+    cf.pmask = (((uint64_t)opts->part_count - 1) << sh);
+    cf.pval = (uint64_t)opts->part_index << sh;
+  }
   if (m.jit_fn)
-    s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo,
-                                          cell_hi, fuse_hist ? &eh : nullptr));
+    s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cf,
+                                          fuse_hist ? &eh : nullptr));
   else
     s = cuda_status(rc::launch_expand(dm, m.host.n_stmts, m.host.n_threads, m.has_deep_loops,
-                                      reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cell_lo, cell_hi));
+                                      reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cf));
   if (s != RC_OK) return s;
   if (tm) { timed->i_expand = tm->n; tm->mark(); }
   if (p.bucket.on) {
@@ -1110,7 +1128,7 @@ rc_status plan_batch(rc_model* const* models, size_t n, const rc_check_opts* opt
     o = align256(o + k.n_keys * 8);
     p.keys_off[1] = o;
     o = align256(o + k.n_keys * 8);
-    if (rc::bucket_path_allowed(k.pb, opts) && rc::plan_buckets(k.n_keys, k.cell_bits, o, &p.bucket)) {
+    if (rc::bucket_path_allowed(k.pb, opts) && rc::plan_buckets(k.n_keys, k.n_keys, k.cell_bits, o, &p.bucket)) {
       p.zero_lo = p.bucket.zero_lo;
       p.zero_hi = p.bucket.zero_hi;
       o = p.bucket.end;
@@ -1628,11 +1646,25 @@ rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, siz
   return RC_OK;
 }
 
+// A hash-partitioned check (rc_check_opts.part_count > 1) runs on the sort
+// path of a single, unchunked check.
+static rc_status partition_status(const rc::Model& m, const rc_check_opts& o) {
+  if (o.part_count <= 1) return RC_OK;
+  if ((o.part_count & (o.part_count - 1)) != 0 || o.part_index >= o.part_count) return RC_E_INVALID;
+  if (o.path == RC_PATH_HASH || use_chunked(m, &o)) return RC_E_UNSUPPORTED;
+  if (rc::bit_length(o.part_count - 1) > m.host.cell_bits) return RC_E_INVALID;
+  return RC_OK;
+}
+
 rc_status rc_workspace_size(const rc_model* m, const rc_check_opts* opts, size_t* bytes) {
   if (!m || !bytes) return RC_E_INVALID;
   rc_model* mm = const_cast<rc_model*>(m);
   const rc_check_opts o = resolve_opts(&mm, 1, opts);
   if (o.path == RC_PATH_HASH && !rc::hash_path_fits(m->m)) return RC_E_UNSUPPORTED;
+  {
+    const rc_status ps = partition_status(m->m, o);
+    if (ps != RC_OK) return ps;
+  }
   if (use_chunked(m->m, &o)) {
     ChunkGeometry g;
     const rc_status s = chunk_geometry(m->m, &o, &g);
@@ -1653,6 +1685,10 @@ rc_status rc_check(rc_model* m, const rc_check_opts* opts, void* workspace, size
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc_check_opts o = resolve_opts(&m, 1, opts);
   if (o.path == RC_PATH_HASH && !rc::hash_path_fits(m->m)) return RC_E_UNSUPPORTED;
+  {
+    const rc_status ps = partition_status(m->m, o);
+    if (ps != RC_OK) return ps;
+  }
   // warp / grid barriers take the sort path unless the hash path is asked for
   if (m->m.sync_scopes && (!opts || opts->path != RC_PATH_HASH)) o.path = RC_PATH_SORT;
   if (use_chunked(m->m, &o)) {
@@ -1795,7 +1831,7 @@ rc_status rc_tune(rc_model* const* models, size_t n, const rc_check_opts* opts, 
     o.digit_bits = d;
     cands.push_back(o);
   }
-  bool hash_ok = true;
+  bool hash_ok = !opts || opts->part_count <= 1;   // (a hash-partitioned check takes the sort path)
   for (size_t i = 0; i < n; ++i) hash_ok = hash_ok && rc::hash_path_fits(models[i]->m);
   if (hash_ok) {
     rc_check_opts o = base;

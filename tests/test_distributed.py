@@ -49,6 +49,28 @@ def test_partial_checks_merge_to_whole(k):
         assert merged(m, k) == whole(m), m.name
 
 
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_hash_parts_merge_to_whole(k):
+    """The hash parts of the check options partition the cells: the parts'
+    distinct instances and racy cells add up to the whole check's, and the
+    merge (the racy part with the smallest witness cell) gives its witness."""
+    for m in models():
+        parts = [oracle.check_part(m, k, r) for r in range(k)]
+        a = oracle.check(m)
+        r = D.merge_results(parts)
+        assert (r.status, r.instances, r.verdict, r.racy_cells, r.witness) == whole(m), m.name
+        if a.status == 0:
+            assert sum(p.distinct for p in parts) == a.distinct, m.name
+
+
+def test_hash_parts_are_balanced():
+    """Each of k parts holds about 1/k of the keys of a regular access pattern."""
+    m = w.neighbor_write_read(4096, n_blocks=4)
+    for k in (2, 4, 8):
+        d = [oracle.check_part(m, k, r).distinct for r in range(k)]
+        assert max(d) <= 1.1 * sum(d) / k, (k, d)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 7, 16])
 def test_parallel_oracle_equals_whole_check(k):
     """The all-cores oracle (cell ranges on std::thread workers) gives the full

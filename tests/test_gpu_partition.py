@@ -30,7 +30,7 @@ def test_partitions_merge_to_whole(rc, opts, k):
     for m in models():
         h = rc.rc_model_create(m)
         ws = rc.workspace(rc.rc_workspace_size(h, opts))
-        parts = [D.check_partition(h, r, k, ws, opts=opts) for r in range(k)]
+        parts = [D.check_partition(h, r, k, ws, opts=opts, by="range") for r in range(k)]
         got = D.merge_results(parts)
         exp = oracle.check(m)
         assert key(got) == (exp.status, exp.instances, exp.verdict, exp.racy_cells, exp.witness), m.name
@@ -43,6 +43,52 @@ def test_partitions_generated_kernel(rc, monkeypatch):
         h = rc.rc_model_create(m)
         assert rc.rc_model_layout(h)["expand_jit"] == 1
         ws = rc.workspace(rc.rc_workspace_size(h))
-        got = D.merge_results([D.check_partition(h, r, 3, ws) for r in range(3)])
+        got = D.merge_results([D.check_partition(h, r, 3, ws, by="range") for r in range(3)])
         exp = oracle.check(m)
         assert key(got) == (exp.status, exp.instances, exp.verdict, exp.racy_cells, exp.witness), m.name
+
+
+# ---------------------------------------------------------------------------
+# hash parts (rc_check_opts.part_count / part_index)
+# ---------------------------------------------------------------------------
+
+def full(r):
+    return (r.status, r.instances, r.verdict, r.racy_cells, r.witness)
+
+
+@pytest.mark.parametrize("opts", [None, {"flags": 8}])
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_hash_parts_equal_oracle_parts(rc, opts, k):
+    """Every part equals the oracle's check of that part, field for field, on
+    the bucket and the LSD path; the merged parts equal the whole check."""
+    for m in models():
+        h = rc.rc_model_create(m)
+        ws = rc.workspace(max(rc.rc_workspace_size(h, D.partition_opts(h, r, k, opts, by="hash")) for r in range(k)))
+        parts = [D.check_partition(h, r, k, ws, opts=opts, by="hash") for r in range(k)]
+        for r, p in enumerate(parts):
+            assert full(p) == full(oracle.check_part(m, k, r)), (m.name, r)
+        exp = oracle.check(m)
+        assert key(D.merge_results(parts)) == (exp.status, exp.instances, exp.verdict, exp.racy_cells, exp.witness)
+
+
+def test_hash_parts_generated_kernel(rc, monkeypatch):
+    monkeypatch.setenv("RC_JIT", "1")
+    for m in models()[::3] + [w.random_affine(8, n_blocks=64, block=256, plant=True)]:
+        h = rc.rc_model_create(m)
+        ws = rc.workspace(rc.rc_workspace_size(h, {"part_count": 4}))
+        for r in range(4):
+            got = D.check_partition(h, r, 4, ws, by="hash")
+            assert full(got) == full(oracle.check_part(m, 4, r)), (m.name, r)
+
+
+def test_hash_parts_rejected_where_unsupported(rc):
+    b = rc.binding
+    m = w.tiny_random(3)
+    for o in ({"part_count": 4, "part_index": 4}, {"part_count": 3, "part_index": 1}):
+        with pytest.raises(rc.RcError) as e:
+            rc.check(m, o)
+        assert e.value.status == b.RC_E_INVALID
+    for o in ({"path": 2}, {"flags": b.RC_OPT_CHUNKED}):
+        with pytest.raises(rc.RcError) as e:
+            rc.check(m, dict(o, part_count=4, part_index=1))
+        assert e.value.status == b.RC_E_UNSUPPORTED
