@@ -63,13 +63,22 @@ KERNEL_SOURCES = {"onesweep": "sort.cu", "partition": "sort.cu", "partition_a": 
                   "scan": "scan.cu", "expand": "jit.cpp", "histogram": "bucket.cu"}
 
 
+# the part of a source file that holds a kernel and its helpers (first line
+# starting with the first marker up to the line starting with the second); a
+# kernel without an entry is hashed with its whole file
+KERNEL_REGIONS = {"local_sort": ("// Exclusive scan in place of n counters", "// one thread per result: the bucket")}
+
+
 def kernel_source_hash(kernel="onesweep"):
-    """Hash of a kernel's source file (an ncu traffic figure is only used
-    while it matches)."""
-    h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2503_08946_gb300", "csrc", KERNEL_SOURCES.get(kernel, "sort.cu")),
-                  "rb").read())
-    return h.hexdigest()[:16]
+    """Hash of a kernel's source (its region of its file, else the file): an
+    ncu traffic figure is only used while it matches."""
+    text = open(os.path.join(ROOT, "paper_2503_08946_gb300", "csrc", KERNEL_SOURCES.get(kernel, "sort.cu")),
+                "rb").read()
+    if kernel in KERNEL_REGIONS:
+        a, b = (m.encode() for m in KERNEL_REGIONS[kernel])
+        i = text.index(a)
+        text = text[i:text.index(b, i)]
+    return hashlib.sha256(text).hexdigest()[:16]
 
 
 def ncu_traffic_per_key(kernel="onesweep"):

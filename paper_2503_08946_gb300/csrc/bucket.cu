@@ -45,6 +45,45 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// One bulk copy global -> shared memory (the TMA engine; 16-byte aligned
+// addresses, a size that is a multiple of 16) completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// the wait for a bulk copy, bounded: on running out the error word is flagged
+// and the copy still in flight is waited for once more (bounded again) before
+// the block goes on
+constexpr unsigned kBulkWaitTries = 1u << 20;
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned int* err) {
+  for (unsigned i = 0; i < kBulkWaitTries; ++i)
+    if (mbar_try_wait(bar, parity)) return;
+  atomicOr(err, (unsigned int)kErrCopyTimeout);
+  for (unsigned i = 0; i < kBulkWaitTries; ++i)
+    if (mbar_try_wait(bar, parity)) return;
+}
+// pass-B tiles by one bulk copy (pass B's tiles start at any key position; pass A's
+// start at even ones, where 16-byte cp.async per thread measured a little faster)
+constexpr bool kPartBulkCopy = true;
+
 // the A-bucket d of tile t: tpref ascending, tpref[d] <= t < tpref[d + 1]
 __device__ __forceinline__ uint32_t tile_bucket(const unsigned long long* tpref, uint32_t nd, uint64_t t) {
   uint32_t lo = 0, hi = nd;
@@ -221,7 +260,17 @@ __global__ void __launch_bounds__(kPThreads, 4) bucket_partition_kernel(BucketAr
   const bool full = len == (uint64_t)kPTile;
   const bool al16 = (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0u;
   int off = 0;
-  if (full && al16 && (t0 & 1u) == 0u) {
+  __shared__ __align__(8) unsigned long long s_bar;
+  if (kPartBulkCopy && B && full && al16 && ((t0 & 1u) == 0u || t0 + kPTile < a.n)) {
+    // one bulk copy by the TMA engine (the widened tile for an odd start)
+    off = (int)(t0 & 1u);
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1u);
+      bulk_load(s_keys, a.keys_in + (t0 - (uint64_t)off), (unsigned)((kPTile + 2 * off) * 8), &s_bar);
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    mbar_wait_bounded(&s_bar, 0u, a.err);
+  } else if (full && al16 && (t0 & 1u) == 0u) {
 #pragma unroll
     for (int m = 0; m < kPTile / 2 / kPThreads; ++m) {
       const int j = m * kPThreads + (int)threadIdx.x;

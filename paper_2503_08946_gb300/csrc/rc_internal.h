@@ -193,6 +193,7 @@ enum DevError : unsigned int {
   kErrChunkOverflow = 16u,   // a chunk produced more keys than its count pass planned
   kErrSortRange = 32u,       // a sort pass computed a destination outside the output (its digit
                              // counts and its ranks disagree: the input changed while it ran)
+  kErrCopyTimeout = 64u,     // a bulk copy into shared memory did not complete within its wait bound
 };
 
 // packed out-of-bounds code: stmt (12 bits) | access (6) | gtid (42) | dimcode (3)

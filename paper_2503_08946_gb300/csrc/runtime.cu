@@ -665,7 +665,7 @@ void decode_result(const rc::DevResult& r, const rc::Model& m, rc_result* out, u
                    uint32_t pb, uint32_t kb = 1, uint32_t wb = 0) {
   std::memset(out, 0, sizeof(*out));
   out->instances = r.instances;
-  if (r.err & rc::kErrLookbackTimeout) {
+  if (r.err & (rc::kErrLookbackTimeout | rc::kErrCopyTimeout)) {
     out->status = RC_E_TIMEOUT;
     return;
   }
