@@ -92,3 +92,23 @@ def test_hash_parts_rejected_where_unsupported(rc):
         with pytest.raises(rc.RcError) as e:
             rc.check(m, dict(o, part_count=4, part_index=1))
         assert e.value.status == b.RC_E_UNSUPPORTED
+
+
+def test_hash_parts_of_atomic_and_barrier_models(rc):
+    """Hash parts of models with atomics, warp and grid barriers (the phase-
+    table scan and its witness), each part equal to the oracle's."""
+    models = ([w.tiny_random(s, atomic=0.4) for s in range(0, 40, 3)] +
+              [w.tiny_random_sync(s) for s in range(0, 40, 3)] +
+              [w.tiny_random_sync(s, block_guards=True) for s in range(0, 60, 7)] +
+              [w.atomic_counter(1024, n_blocks=8, barrier=False), w.grid_late_partner(4, 3)])
+    for m in models:
+        h = rc.rc_model_create(m)
+        ws = rc.workspace(rc.rc_workspace_size(h, None))
+        parts = [D.check_partition(h, r, 4, ws, by="hash") for r in range(4)]
+        for r, p in enumerate(parts):
+            exp = oracle.check_part(m, 4, r)
+            assert full(p) == full(exp), (m.name, r, p, exp)
+            if exp.verdict:
+                assert (p.x_wphase, p.y_wphase) == (exp.x_wphase, exp.y_wphase), (m.name, r)
+        exp = oracle.check(m)
+        assert key(D.merge_results(parts)) == (exp.status, exp.instances, exp.verdict, exp.racy_cells, exp.witness)
