@@ -294,11 +294,13 @@ typedef struct rc_check_opts {
                            /* (a model split across processes or GPUs).  Ignored   */
                            /* by rc_check_batch.                                   */
   uint32_t part_count;     /* partial check by hash part (0 or 1 = none; else a
-                              power of two 2^p with p <= rc_layout.cell_bits): only
-                              the cells c whose part
-                                ((c * 0x9E3779B97F4A7C15) mod 2^cb) >> (cb - p),
+                              power of two 2^p, p <= 16): only the cells c whose
+                              part
+                                (((c * 0x9E3779B97F4A7C15) mod 2^cb) * 2^p) >> cb,
                               cb = rc_layout.cell_bits, equals part_index are
-                              checked (with cell_lo / cell_hi both apply).  The
+                              checked (with cell_lo / cell_hi both apply): the top
+                              p bits of the cb-bit hash (if p > cb, only every
+                              2^(p-cb)-th part holds cells).  The
                               multiplier is odd, so this is a bijection of the cell
                               field: every cell has exactly one part, and the parts
                               hold about equal shares of the keys whatever the

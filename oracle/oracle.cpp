@@ -433,7 +433,7 @@ struct CellRange {
   bool all = true;
   int64_t lo = 0, hi = 0;
   // hash part (part_count = 2^p > 1): the cells whose part, by the definition
-  // of the check options, ((cell * 0x9E3779B97F4A7C15) mod 2^cb) >> (cb - p)
+  // of the check options, (((cell * 0x9E3779B97F4A7C15) mod 2^cb) * 2^p) >> cb
   // with cb = bit_length(number of cells), is part_index
   uint64_t part_count = 0, part_index = 0;
   uint32_t cb = 0;
@@ -496,7 +496,8 @@ struct Enumerator {
           while ((1ull << p) < range.part_count) ++p;
           uint64_t hsh = (uint64_t)lin * 0x9E3779B97F4A7C15ull;
           if (range.cb < 64) hsh &= (1ull << range.cb) - 1ull;
-          if ((hsh >> (range.cb - p)) != range.part_index) continue;
+          const uint64_t part = p <= range.cb ? hsh >> (range.cb - p) : hsh << (p - range.cb);
+          if (part != range.part_index) continue;
         }
       }
       out.push_back(x);

@@ -599,9 +599,19 @@ rc_status enqueue_check(rc_model* model, const rc_check_opts* opts, uint8_t* ws,
   cf.lo = cell_lo;
   cf.hi = cell_hi;
   if (opts && opts->part_count > 1) {
-    const uint32_t pb = rc::bit_length(opts->part_count - 1), sh = m.host.cell_bits - pb;
-    cf.pmask = (((uint64_t)opts->part_count - 1) << sh);
-    cf.pval = (uint64_t)opts->part_index << sh;
+    // part = (h * 2^pb) >> cb of the cb-bit hash h: its top pb bits, or with
+    // pb > cb the hash shifted up (a part with any of the low pb - cb bits set
+    // is empty: a mask no hash meets)
+    const uint32_t pb = rc::bit_length(opts->part_count - 1), cb = m.host.cell_bits;
+    if (pb <= cb) {
+      cf.pmask = ((uint64_t)opts->part_count - 1) << (cb - pb);
+      cf.pval = (uint64_t)opts->part_index << (cb - pb);
+    } else if ((opts->part_index & ((1u << (pb - cb)) - 1u)) != 0u) {
+      cf.lo = cf.hi = 0;   // the part holds no cell: an empty range
+    } else {
+      cf.pmask = cb >= 64 ? ~0ull : (1ull << cb) - 1ull;
+      cf.pval = (uint64_t)(opts->part_index >> (pb - cb));
+    }
   }
   if (m.jit_fn)
     s = cuda_status(rc::jit_expand_launch(m, reinterpret_cast<uint64_t*>(ws + p.keys_off[0]), res, st, cf,
@@ -1651,8 +1661,8 @@ rc_status rc_kernel_source(const rc_model_desc* desc, char* buf, size_t cap, siz
 static rc_status partition_status(const rc::Model& m, const rc_check_opts& o) {
   if (o.part_count <= 1) return RC_OK;
   if ((o.part_count & (o.part_count - 1)) != 0 || o.part_index >= o.part_count) return RC_E_INVALID;
+  if (o.part_count > (1u << 16)) return RC_E_INVALID;
   if (o.path == RC_PATH_HASH || use_chunked(m, &o)) return RC_E_UNSUPPORTED;
-  if (rc::bit_length(o.part_count - 1) > m.host.cell_bits) return RC_E_INVALID;
   return RC_OK;
 }
 

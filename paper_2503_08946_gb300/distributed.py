@@ -66,7 +66,10 @@ def partition_opts(model: "binding.RcModel", rank: int, world: int, opts=None, b
 
 def check_partition(model: "binding.RcModel", rank: int, world: int, workspace, stream=None, opts=None,
                     by: str = "auto"):
-    """The partial check of `rank`: only the cells of its range or hash part."""
+    """The partial check of `rank`: only the cells of its range or hash part.
+    Size `workspace` with ``rc_workspace_size(model, partition_opts(...))``: a
+    part's plan may differ from the whole check's (a small cell space takes the
+    radix sort)."""
     o = partition_opts(model, rank, world, opts, by)
     return binding.rc_report(binding.rc_check(model, o, workspace, stream))[0]
 

@@ -103,7 +103,7 @@ def test_hash_parts_of_atomic_and_barrier_models(rc):
               [w.atomic_counter(1024, n_blocks=8, barrier=False), w.grid_late_partner(4, 3)])
     for m in models:
         h = rc.rc_model_create(m)
-        ws = rc.workspace(rc.rc_workspace_size(h, None))
+        ws = rc.workspace(max(rc.rc_workspace_size(h, D.partition_opts(h, r, 4, by="hash")) for r in range(4)))
         parts = [D.check_partition(h, r, 4, ws, by="hash") for r in range(4)]
         for r, p in enumerate(parts):
             exp = oracle.check_part(m, 4, r)
