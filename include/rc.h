@@ -341,8 +341,10 @@ enum { RC_OPT_STAGE_TIMES = 1, RC_OPT_GRAPH = 2, RC_OPT_CHUNKED = 4, RC_OPT_LSD 
 /* Grouping step of the sort path.  By default a check (or a batch pack) whose
  * keys carry at most 16 barrier intervals groups its keys by cell with the
  * bucket path: two look-back-free partition passes on the top bits of a
- * bijective hash of the cell field, then per bucket a counting sort and the
- * cell fold in shared memory; its result is identical to the ordered scan's.
+ * bijective hash of the cell field, then a counting sort of every bucket in
+ * shared memory on the hash's remaining bits, which leaves every cell's keys
+ * together (cells in hash order), then the cell scan; its result is identical
+ * to the radix-sorted check's.
  * RC_OPT_LSD (or a non-zero digit_bits, or any test flag) selects the stable
  * LSD radix sort followed by the ordered scan instead; models of more than 16
  * intervals, chunked checks and rc_sort_keys always take that path. */

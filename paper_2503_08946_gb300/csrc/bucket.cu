@@ -22,7 +22,6 @@
 // its bucket, whose keys they filter by cell.
 #include <cuda_runtime.h>
 
-#include "fold.cuh"
 #include "kernels.h"
 
 namespace rc {

@@ -1,5 +1,5 @@
-// Per-cell fold state shared by the ordered cell scan (scan.cu) and the
-// bucket fold (bucket.cu): the keys of one cell, taken in any order, reduce to
+// Per-cell fold state of the cell scans (scan.cu): the keys of one cell, taken
+// in any order, reduce to
 // per-barrier-interval masks (seen, two (block, thread), write, atomic, plain
 // read) plus the (block, thread) of each interval's first key, from which the
 // cell-level race rule of include/rc.h is decided.  A cell is racy iff it has a
