@@ -202,3 +202,21 @@ def test_report_array(rc):
         if g.verdict:
             assert (int(rec["x"]["block"]), int(rec["x"]["phase"]), int(rec["x"]["thread"]),
                     int(rec["x"]["kind"])) == g.x
+
+
+def test_full_batch_of_10000_models(rc):
+    """The benchmarked batch at its full size: 10,000 generator models in one
+    graph-replayed batch.  Every model's result has its generator's closed
+    form (T racy cells when a race is planted, else none); the planted models
+    and every 97th model are checked against the oracle field for field."""
+    models = w.batch_models(10000, seed0=0)
+    res = check_batch(rc, models, {"flags": rc.binding.RC_OPT_GRAPH})
+    planted = 0
+    for m, g in zip(models, res):
+        assert g.status == rc.RC_OK, m.name
+        assert g.racy_cells == (m.n_model_threads if m.planted else 0), m.name
+        planted += m.planted
+    assert planted > 0
+    for k, (m, g) in enumerate(zip(models, res)):
+        if m.planted or k % 97 == 0:
+            assert_same(m, g, oracle.check(m))
