@@ -9,9 +9,10 @@
  * (same cell, at least one write) against the schedule (appendix listing of the
  * dependence test).  This library answers it concretely: for a model with a
  * fixed grid and fixed parameters it expands every access instance into a
- * 64-bit key, groups keys by cell with a radix sort (or a hash table), and
- * reports whether any cell races, how many cells race and the smallest racing
- * pair.
+ * 64-bit key, groups keys by cell (partition passes on a bijective hash of the
+ * cell and a counting sort of every bucket; a radix sort where intervals must
+ * stay in order; or a hash table), and reports whether any cell races, how
+ * many cells race and the smallest racing pair.
  *
  * Race rule (the paper orders instances by a sequential Before relation; for
  * SIMT threads this library reads concurrency as the CUDA barrier rule):
