@@ -637,6 +637,17 @@ def batch_measure(args, rc, w, torch, rank, world, dist, steps, pm_steps, compac
         pm_value = inst * pm_steps * world / (pm_ms / 1e3) / 1e9
         pm = {"value": pm_value, "unit": UNIT, "ms_per_step": pm_ms / pm_steps, "steps": pm_steps,
               "results_identical": same}
+        # the hash path on the same batch (it checks a batch model by model, full
+        # counts without early exit), against the same closed forms
+        ho = {"path": rc.RC_PATH_HASH, "early_exit": 0}
+        del ws1
+        hws = rc.workspace(rc.rc_batch_workspace_size(handles, ho))
+        hres = rc.rc_report(rc.rc_check_batch(handles, ho, hws, stream))
+        batch_closed_form(models, hres)
+        _, h_ms, _ = timed(lambda: check_results(rc.rc_report(rc.rc_check_batch(handles, ho, hws, stream))), 1)
+        pm["hash_path"] = {"value": inst * world / (h_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": h_ms,
+                           "results_checked": "every model against the generator's closed form"}
+        del hws
     out = {
         "value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
         "config": {"workload": BATCH_WORKLOAD, "models": len(models), "instances_per_rank": inst,
