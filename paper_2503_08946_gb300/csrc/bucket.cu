@@ -83,17 +83,6 @@ __device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsig
 // start at even ones, where 16-byte cp.async per thread measured a little faster)
 constexpr bool kPartBulkCopy = true;
 
-// the A-bucket d of tile t: tpref ascending, tpref[d] <= t < tpref[d + 1]
-__device__ __forceinline__ uint32_t tile_bucket(const unsigned long long* tpref, uint32_t nd, uint64_t t) {
-  uint32_t lo = 0, hi = nd;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (tpref[mid] <= t) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // ---------------------------------------------------------------------------
 // pass-A histogram: valid keys per top-dA-bit digit of h
 // ---------------------------------------------------------------------------
@@ -178,6 +167,24 @@ __global__ void __launch_bounds__(1024) bucket_scan_a_kernel(BucketArgs a) {
     a.tpref_h[nd] = tot_h;
     if (a.dB == 0) a.boff[nd] = tot_c;
   }
+  if (a.dB == 0) return;
+  // the A-bucket of every pass-B tile and of every histogram tile, so that a
+  // block of either kernel finds its bucket with one load (the block-strided
+  // fill spreads a skewed bucket over all threads)
+  __shared__ unsigned long long s_eb[1024], s_eh[1024];
+  if (d < nd) { s_eb[d] = eb; s_eh[d] = eh; }
+  __syncthreads();
+  auto owner = [&](const unsigned long long* pref, unsigned long long t) {
+    unsigned lo = 0, hi = nd;
+    while (hi - lo > 1) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (pref[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  };
+  for (unsigned long long t = d; t < tot_b; t += blockDim.x) a.tile_a[t] = owner(s_eb, t);
+  for (unsigned long long t = d; t < tot_h; t += blockDim.x) a.tile_h[t] = owner(s_eh, t);
 }
 
 __global__ void bucket_whole_kernel(unsigned long long* boff, uint64_t n) {
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kPThreads, 4) bucket_partition_kernel(BucketAr
     const unsigned nd = 1u << a.dA;
     const uint64_t t = blockIdx.x;
     if (t >= a.tpref_b[nd]) return;
-    const uint32_t d1 = tile_bucket(a.tpref_b, nd, t);
+    const uint32_t d1 = a.tile_a[t];
     t0 = a.off_a[d1] + (t - a.tpref_b[d1]) * kPTile;
     len = min((uint64_t)kPTile, (uint64_t)(a.off_a[d1 + 1] - t0));
     cursor = a.cur_b + ((uint64_t)d1 << a.dB);
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
   const unsigned nd = 1u << a.dA, nb = 1u << a.dB;
   const uint64_t t = blockIdx.x;
   if (t >= a.tpref_h[nd]) return;
-  const uint32_t d1 = tile_bucket(a.tpref_h, nd, t);
+  const uint32_t d1 = a.tile_h[t];
   const uint64_t s = a.off_a[d1] + (t - a.tpref_h[d1]) * kBucketHistTile;
   const uint64_t e = min(s + kBucketHistTile, (uint64_t)a.off_a[d1 + 1]);
   const uint32_t sh = a.cb - a.dA - a.dB;
