@@ -534,39 +534,58 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
   // bin g's keys after the scatter: [bin_start(g), bin_end(g))
   auto bin_start = [&](unsigned g) { return s_bin[g]; };
   auto bin_end = [&](unsigned g) { return g + 1 < nbins ? s_bin[g + 1] : s_total; };
-  for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint64_t lo = a.boff[b], hi = a.boff[b + 1];
-    if (hi <= lo) continue;
-    const uint64_t len = hi - lo;
-    const bool in_smem = len <= (uint64_t)kFoldCap;
+  // The keys of a bucket that fits in shared memory are held in registers
+  // (kLocKPT slots a thread, nq of them used).  The next bucket's loads are
+  // issued as soon as the scatter has consumed this one's, so that they are in
+  // flight while the sorted bucket is copied out.
+  uint64_t kr[kLocKPT];
+  uint64_t lo = 0, hi = 0;
+  int nq = 0;   // block-uniform; 0 for an empty bucket or one read from global memory
+  auto fetch = [&](uint64_t bb) {
+    lo = bb < nb ? a.boff[bb] : 0ull;
+    hi = bb < nb ? a.boff[bb + 1] : 0ull;
+    const uint64_t len = hi > lo ? hi - lo : 0ull;
+    nq = len <= (uint64_t)kFoldCap ? (int)((len + kLocThreads - 1) / kLocThreads) : 0;
     const uint64_t* src = a.keys_in + lo;
-    uint64_t* out = a.keys_out + lo;
-    uint64_t* dst = in_smem ? s_keys : out;
+#pragma unroll
+    for (int q = 0; q < kLocKPT; ++q) {
+      if (q >= nq) break;
+      const unsigned i = (unsigned)q * kLocThreads + (unsigned)tid;
+      kr[q] = i < len ? __ldg(src + i) : kSentinel;
+    }
+  };
+  auto clear_bins = [&]() {
     if ((nbins & 3u) == 0u) {
       for (unsigned i = 4 * tid; i < nbins; i += 4 * kLocThreads) *reinterpret_cast<uint4*>(s_bin + i) = make_uint4(0, 0, 0, 0);
     } else {
       for (unsigned i = tid; i < nbins; i += kLocThreads) s_bin[i] = 0;
     }
-    __syncthreads();
+  };
+  clear_bins();
+  fetch(blockIdx.x);
+  __syncthreads();
+  for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (hi <= lo) {
+      // empty: the bins stay clear
+      fetch(b + gridDim.x);
+      continue;
+    }
+    const uint64_t blo = lo, len = hi - lo;   // (lo and hi move on to the next bucket below)
+    const bool in_smem = len <= (uint64_t)kFoldCap;
+    const uint64_t* src = a.keys_in + blo;
+    uint64_t* out = a.keys_out + blo;
+    uint64_t* dst = in_smem ? s_keys : out;
     if (in_smem) {
-      // one read of the bucket into registers, all loads in flight together
-      const int nq = (int)((len + kLocThreads - 1) / kLocThreads);   // block-uniform
-      uint64_t kr[kLocKPT];
-#pragma unroll
-      for (int q = 0; q < kLocKPT; ++q) {
-        if (q >= nq) break;
-        const uint64_t i = (uint64_t)q * kLocThreads + tid;
-        kr[q] = i < len ? __ldg(src + i) : kSentinel;
-      }
 #pragma unroll
       for (int q = 0; q < kLocKPT; ++q) {
         if (q >= nq) break;
         if (kr[q] != kSentinel) atomicAdd(&s_bin[bin_of(kr[q])], 1u);
       }
       __syncthreads();
-      // the cursors live in the bins' copy: starts stay in s_bin for the ranges below
-      unsigned* cur = s_bin + nbins;
-      bin_scan<kLocThreads>(s_bin, nbins, &s_total, cur);
+      // the scatter cursors: the bins themselves when each holds one cell, else
+      // a copy (the starts stay in s_bin for the in-bin ordering below)
+      unsigned* cur = multi ? s_bin + nbins : s_bin;
+      bin_scan<kLocThreads>(s_bin, nbins, &s_total, multi ? cur : nullptr);
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < kLocKPT; ++q) {
@@ -610,9 +629,13 @@ __global__ void __launch_bounds__(kLocThreads, 2) bucket_local_sort_kernel(Local
       }
       __syncthreads();
     }
+    // the bins are no longer read: the next bucket's loads and the cleared bins
+    // go ahead of this bucket's copy out
+    fetch(b + gridDim.x);
+    clear_bins();
     if (in_smem) {
       // coalesced copy out (16-byte stores where the bucket starts at an even position)
-      if ((lo & 1u) == 0u && (reinterpret_cast<uintptr_t>(a.keys_out) & 15u) == 0u) {
+      if ((blo & 1u) == 0u && (reinterpret_cast<uintptr_t>(a.keys_out) & 15u) == 0u) {
         const unsigned np = total / 2;
         for (unsigned i = tid; i < np; i += kLocThreads)
           reinterpret_cast<ulonglong2*>(out)[i] = reinterpret_cast<const ulonglong2*>(s_keys)[i];
