@@ -177,7 +177,9 @@ cudaError_t launch_bucket_whole(unsigned long long* boff, uint64_t n, cudaStream
 
 // scan.cu
 constexpr int kScanRun = 32;          // keys per lane run (multiple of 2)
-constexpr uint32_t kScanMaxWarps = 152 * 12 * 4;
+// at most four waves of 152 SMs x 6 resident blocks of 4 warps (measured a
+// little faster than two: the per-warp ranges are shorter at the tail)
+constexpr uint32_t kScanMaxWarps = 152 * 24 * 4;
 struct ScanArgs {
   const uint64_t* keys;                // 16-byte aligned (the phase-table scan reads pairs)
   uint64_t n;
