@@ -167,24 +167,6 @@ __global__ void __launch_bounds__(1024) bucket_scan_a_kernel(BucketArgs a) {
     a.tpref_h[nd] = tot_h;
     if (a.dB == 0) a.boff[nd] = tot_c;
   }
-  if (a.dB == 0) return;
-  // the A-bucket of every pass-B tile and of every histogram tile, so that a
-  // block of either kernel finds its bucket with one load (the block-strided
-  // fill spreads a skewed bucket over all threads)
-  __shared__ unsigned long long s_eb[1024], s_eh[1024];
-  if (d < nd) { s_eb[d] = eb; s_eh[d] = eh; }
-  __syncthreads();
-  auto owner = [&](const unsigned long long* pref, unsigned long long t) {
-    unsigned lo = 0, hi = nd;
-    while (hi - lo > 1) {
-      const unsigned mid = (lo + hi) >> 1;
-      if (pref[mid] <= t) lo = mid;
-      else hi = mid;
-    }
-    return lo;
-  };
-  for (unsigned long long t = d; t < tot_b; t += blockDim.x) a.tile_a[t] = owner(s_eb, t);
-  for (unsigned long long t = d; t < tot_h; t += blockDim.x) a.tile_h[t] = owner(s_eh, t);
 }
 
 __global__ void bucket_whole_kernel(unsigned long long* boff, uint64_t n) {
@@ -207,6 +189,9 @@ constexpr int kPThreads = kSortThreads;
 constexpr int kPItems = 16;
 constexpr int kPTile = kPThreads * kPItems;
 static_assert(kPTile == kPartTileHost, "pass-B tiles are planned with the host's tile size");
+// pass-B tiles per pass-B histogram tile (the histogram writes their A-bucket)
+constexpr int kHistPassTiles = kBucketHistTile / kPTile;
+static_assert(kHistPassTiles * kPTile == kBucketHistTile && kHistPassTiles <= 256, "whole pass-B tiles per histogram tile");
 
 template <int RB>
 constexpr size_t bpart_smem() {
@@ -394,9 +379,23 @@ __global__ void __launch_bounds__(256) bucket_hist_b_kernel(BucketArgs a) {
   const unsigned nd = 1u << a.dA, nb = 1u << a.dB;
   const uint64_t t = blockIdx.x;
   if (t >= a.tpref_h[nd]) return;
-  const uint32_t d1 = a.tile_h[t];
+  uint32_t d1 = 0;
+  {
+    uint32_t hi = nd;
+    while (hi - d1 > 1) {
+      const uint32_t mid = (d1 + hi) >> 1;
+      if (a.tpref_h[mid] <= t) d1 = mid;
+      else hi = mid;
+    }
+  }
   const uint64_t s = a.off_a[d1] + (t - a.tpref_h[d1]) * kBucketHistTile;
   const uint64_t e = min(s + kBucketHistTile, (uint64_t)a.off_a[d1 + 1]);
+  // the A-bucket of the pass-B tiles inside this one (both tilings start at
+  // the A-bucket's first key), so that a pass-B block finds it with one load
+  if (threadIdx.x < (unsigned)kHistPassTiles) {
+    const uint64_t tb = (uint64_t)a.tpref_b[d1] + (t - a.tpref_h[d1]) * kHistPassTiles + threadIdx.x;
+    if (tb < a.tpref_b[d1 + 1]) a.tile_a[tb] = d1;
+  }
   const uint32_t sh = a.cb - a.dA - a.dB;
   const uint32_t cs = a.cell_shift;
   const bool h32 = a.cb <= 32;

@@ -157,8 +157,7 @@ struct BucketArgs {
   unsigned long long* off_a;        // [2^dA + 1] A-bucket offsets (exclusive, then the total)
   unsigned long long* cur_a;        // [2^dA] pass-A output cursors
   unsigned long long* tpref_b;      // [2^dA + 1] pass-B tiles before each A-bucket
-  unsigned* tile_a;                 // [pass-B tiles] the A-bucket of each pass-B tile
-  unsigned* tile_h;                 // [histogram tiles] the A-bucket of each pass-B histogram tile
+  unsigned* tile_a;                 // [pass-B tiles] the A-bucket of each pass-B tile (written by the histogram)
   unsigned long long* tpref_h;      // [2^dA + 1] histogram tiles before each A-bucket
   unsigned long long* hist_b;       // [2^D] keys per bucket
   unsigned long long* boff;         // [2^D + 1] bucket offsets

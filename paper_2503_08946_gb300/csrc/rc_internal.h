@@ -351,7 +351,7 @@ struct BucketPlan {
   uint64_t n = 0;                 // key slots (padding included)
   uint64_t tiles_b = 0, tiles_h = 0;   // grid bounds of pass B and its histogram
   // workspace offsets (bytes) of the bucket section
-  size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, tile_a = 0, tile_h = 0;
+  size_t hist_a = 0, off_a = 0, cur_a = 0, tpref_b = 0, tpref_h = 0, tile_a = 0;
   size_t hist_b = 0, boff = 0, cur_b = 0, temp = 0;
   size_t scan_ctr = 0;            // the ordered scan's long-cell counter (in the cleared range)
   size_t zero_lo = 0, zero_hi = 0;    // cleared at the start of a check (the two histograms)

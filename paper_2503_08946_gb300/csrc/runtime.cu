@@ -261,8 +261,6 @@ bool plan_buckets(uint64_t n, uint64_t n_expect, uint32_t cb, size_t off, Bucket
   off = align256(off + bp->tiles_b * 4);
   bp->tpref_h = off;
   off = align256(off + (na + 1) * 8);
-  bp->tile_h = off;
-  off = align256(off + bp->tiles_h * 4);
   bp->boff = off;
   off = align256(off + (nb + 1) * 8);
   bp->cur_b = off;
@@ -444,7 +442,6 @@ rc_status enqueue_bucketed(const rc::WorkspacePlan& p, uint8_t* ws, uint64_t* bu
   a.cur_a = u64(bp.cur_a);
   a.tpref_b = u64(bp.tpref_b);
   a.tile_a = reinterpret_cast<unsigned*>(ws + bp.tile_a);
-  a.tile_h = reinterpret_cast<unsigned*>(ws + bp.tile_h);
   a.tpref_h = u64(bp.tpref_h);
   a.hist_b = u64(bp.hist_b);
   a.boff = u64(bp.boff);
