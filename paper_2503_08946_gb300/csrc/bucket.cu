@@ -232,6 +232,11 @@ __global__ void __launch_bounds__(kPThreads, B ? 4 : 5) bucket_partition_kernel(
     const uint64_t t = blockIdx.x;
     if (t >= a.tpref_b[nd]) return;
     const uint32_t d1 = a.tile_a[t];
+    // (every entry below tpref_b[nd] was written by the histogram of this check)
+    if (d1 >= nd) {
+      if (threadIdx.x == 0) atomicOr(a.err, (unsigned int)kErrSortRange);
+      return;
+    }
     t0 = a.off_a[d1] + (t - a.tpref_b[d1]) * kPTile;
     len = min((uint64_t)kPTile, (uint64_t)(a.off_a[d1 + 1] - t0));
     cursor = a.cur_b + ((uint64_t)d1 << a.dB);
