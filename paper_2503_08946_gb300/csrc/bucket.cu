@@ -201,10 +201,9 @@ constexpr size_t bpart_smem() {
 // H32: the cell field has at most 32 bits, so h is computed in 32-bit
 // arithmetic (the product modulo 2^cb depends only on the low 32 bits of each
 // factor).
-// Pass A runs 5 blocks per SM (48 registers, a 20-byte spill: 4.20 against 4.26
-// ms at 4); pass B keeps 4 (at 5 it spills 192 bytes).
+// 4 blocks per SM, without spills (5 blocks, 48 registers, spill in both passes)
 template <int RB, bool B, bool H32>
-__global__ void __launch_bounds__(kPThreads, B ? 4 : 5) bucket_partition_kernel(BucketArgs a) {
+__global__ void __launch_bounds__(kPThreads, 4) bucket_partition_kernel(BucketArgs a) {
   constexpr int R = 1 << RB;
   constexpr int DPT = (R + kPThreads - 1) / kPThreads;
   constexpr int kWarps = kPThreads / 32;
