@@ -101,6 +101,31 @@ def test_merge_keeps_errors():
     assert (r.racy_cells, r.verdict, r.witness) == (6, 1, ok.witness)
 
 
+def test_partition_opts(monkeypatch):
+    """A rank's split options: its hash part when the world is a power of two
+    (the default), else its cell range; the caller's options are kept and not
+    changed; an empty range keeps no cell."""
+    from paper_2503_08946_gb300 import binding as B
+    monkeypatch.setattr(B, "rc_model_layout", lambda model: {"total_cells": 10})
+    base = {"early_exit": 0}
+    for k in (1, 2, 4, 8):
+        for r in range(k):
+            assert D.partition_opts(None, r, k, base) == {"early_exit": 0, "part_count": k, "part_index": r}
+    assert base == {"early_exit": 0}
+    got = [D.partition_opts(None, r, 3) for r in range(3)]
+    assert [(o["cell_lo"], o["cell_hi"]) for o in got] == [(0, 4), (4, 7), (7, 10)]
+    assert D.partition_opts(None, 1, 2, by="range") == {"cell_lo": 5, "cell_hi": 10}
+    # more ranks than cells: one cell each for the first ten, a range past the
+    # last cell for the rest (cell_hi = 0 would mean every cell)
+    rs = [D.partition_opts(None, r, 12, by="range") for r in range(12)]
+    assert [(o["cell_lo"], o["cell_hi"]) for o in rs[:10]] == [(c, c + 1) for c in range(10)]
+    assert all(o["cell_hi"] > o["cell_lo"] >= 10 for o in rs[10:])
+    with pytest.raises(ValueError):
+        D.partition_opts(None, 0, 3, by="hash")
+    with pytest.raises(ValueError):
+        D.partition_opts(None, 0, 2, by="cells")
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
